@@ -1,0 +1,339 @@
+"""CPU oracle for SV-MPR gap filling (Lach & Zukovic, arXiv 2212.01317).
+
+TEST INFRASTRUCTURE ONLY. A plain FP64 C restatement of the method
+(``mpr_oracle.c``) plus this ctypes wrapper. Only the tests, the smoke check
+and the benchmark's CPU-baseline leg may import it; the library under
+``paper_2212_01317_gb300`` never does and shares no code with it.
+
+Every function here is argument marshalling around the C code, except
+``gapfill`` which strings the C steps together in the paper's order
+(transform, block statistics, calibration, realizations, mean,
+back-transform).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpr_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+TWO_PI = 2.0 * np.pi
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (OpenMP, no FP contraction, no fast-math)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                              os.path.getmtime(os.path.join(_HERE, "mpr_oracle.h")))):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Model(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("lb", C.c_int32),
+                ("nbx", C.c_int32), ("nby", C.c_int32), ("nblk", C.c_int32),
+                ("q", C.c_double), ("J", C.c_double),
+                ("key0", C.c_uint32), ("key1", C.c_uint32),
+                ("overrelax", C.c_int32), ("K", C.c_int32), ("threads", C.c_int32)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("dE", C.c_double), ("theta", C.c_double), ("phi_or", C.c_double),
+                ("R", C.c_double), ("phi_old", C.c_double), ("phi_prop", C.c_double),
+                ("accepted", C.c_int32), ("or_applied", C.c_int32)]
+
+
+DIAG_DTYPE = np.dtype([("dE", "f8"), ("theta", "f8"), ("phi_or", "f8"), ("R", "f8"),
+                       ("phi_old", "f8"), ("phi_prop", "f8"), ("accepted", "i4"),
+                       ("or_applied", "i4")])
+assert DIAG_DTYPE.itemsize == C.sizeof(Diag)
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.c_void_p
+        i32, i64, u32, u64, f64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+        MP = C.POINTER(Model)
+        sig = {
+            "orc_model_init": (None, [MP, i32, i32, i32, f64, f64, u64, u32]),
+            "orc_philox4x32_10": (None, [P, P, P]),
+            "orc_u01": (f64, [u32]),
+            "orc_site_uniforms": (None, [MP, i64, u32, u32, u32, P, P]),
+            "orc_transform": (C.c_int, [i64, P, P, P, P, P]),
+            "orc_backtransform": (None, [i64, P, P, P, f64, f64, P]),
+            "orc_block_stats": (None, [MP, P, P, P, P, P, P, P, P, P]),
+            "orc_block_energy": (None, [MP, P, P]),
+            "orc_total_energy": (f64, [MP, P]),
+            "orc_update_site": (None, [MP, P, P, i64, f64, u32, u32, u32, P]),
+            "orc_halfstep": (None, [MP, P, P, C.c_int, P, P, u32, u32, u32, P]),
+            "orc_init_block_mean": (None, [MP, P, P, P, P, f64]),
+            "orc_init_random": (None, [MP, P, P, u32]),
+            "orc_simulate_one": (C.c_int, [MP, P, P, P, P, P, P, P, i32, u32, P, P]),
+            "orc_stop_init": (None, [MP, P, P, P, P, P, P, P, P]),
+            "orc_stop_update": (C.c_int, [MP, i32, i32, P, P, P, P, P, P, P]),
+            "orc_calibrate": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, f64, f64, P, P]),
+            "orc_median_targeted": (f64, [i32, P, P]),
+            "orc_scores": (None, [i64, P, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def u01(x: int) -> float:
+    return lib().orc_u01(int(x) & 0xFFFFFFFF)
+
+
+@dataclass
+class BlockStats:
+    Es: np.ndarray
+    Nsp: np.ndarray
+    Nb: np.ndarray
+    mean_angle: np.ndarray
+    n_gap: np.ndarray
+    n_sample: np.ndarray
+    global_mean: float
+
+    @property
+    def es(self) -> np.ndarray:
+        out = np.zeros_like(self.Es)
+        t = self.Nsp > 0
+        out[t] = self.Es[t] / self.Nsp[t]
+        return out
+
+
+class Oracle:
+    """One grid geometry + model parameters; methods mirror the C functions."""
+
+    def __init__(self, H: int, W: int, lb: int, q: float = 0.5, J: float = 1.0,
+                 seed: int = 0, slice_id: int = 0, overrelax: bool = True, K: int = 0,
+                 threads: int = 0):
+        self.m = Model()
+        lib().orc_model_init(C.byref(self.m), H, W, lb, q, J, seed & (2**64 - 1), slice_id)
+        self.m.overrelax = 1 if overrelax else 0
+        self.m.K = int(K)
+        self.m.threads = int(threads)
+        self.H, self.W, self.lb = H, W, lb
+
+    @property
+    def nblk(self) -> int:
+        return self.m.nblk
+
+    @property
+    def nbx(self) -> int:
+        return self.m.nbx
+
+    def block_index(self) -> np.ndarray:
+        y, x = np.mgrid[0:self.H, 0:self.W]
+        return (y // self.lb) * self.m.nbx + x // self.lb
+
+    def site_uniforms(self, i: int, t: int, tag: int, r: int):
+        u0, u1 = C.c_double(), C.c_double()
+        lib().orc_site_uniforms(C.byref(self.m), i, t, tag, r, C.byref(u0), C.byref(u1))
+        return u0.value, u1.value
+
+    @staticmethod
+    def transform(values: np.ndarray, mask: np.ndarray):
+        v = np.ascontiguousarray(values, dtype=np.float32).ravel()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8).ravel()
+        phi = np.zeros(v.size, dtype=np.float64)
+        zmin, zmax = C.c_double(), C.c_double()
+        deg = lib().orc_transform(v.size, _p(v), _p(mk), C.byref(zmin), C.byref(zmax), _p(phi))
+        return phi.reshape(np.shape(values)), zmin.value, zmax.value, bool(deg)
+
+    @staticmethod
+    def backtransform(mean_phi, mask, values, zmin, zmax) -> np.ndarray:
+        mp = np.ascontiguousarray(mean_phi, dtype=np.float64).ravel()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8).ravel()
+        v = np.ascontiguousarray(values, dtype=np.float32).ravel()
+        out = np.zeros(mp.size, dtype=np.float32)
+        lib().orc_backtransform(mp.size, _p(mp), _p(mk), _p(v), zmin, zmax, _p(out))
+        return out.reshape(np.shape(mean_phi))
+
+    def block_stats(self, phi, mask) -> BlockStats:
+        ph = np.ascontiguousarray(phi, dtype=np.float64)
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        n = self.nblk
+        Es = np.zeros(n); Nsp = np.zeros(n, np.int64); Nb = np.zeros(n, np.int64)
+        ma = np.zeros(n); ng = np.zeros(n, np.int64); ns = np.zeros(n, np.int64)
+        gm = C.c_double()
+        lib().orc_block_stats(C.byref(self.m), _p(ph), _p(mk), _p(Es), _p(Nsp), _p(Nb), _p(ma),
+                              _p(ng), _p(ns), C.byref(gm))
+        return BlockStats(Es, Nsp, Nb, ma, ng, ns, gm.value)
+
+    def block_energy(self, phi) -> np.ndarray:
+        ph = np.ascontiguousarray(phi, dtype=np.float64)
+        E = np.zeros(self.nblk)
+        lib().orc_block_energy(C.byref(self.m), _p(ph), _p(E))
+        return E
+
+    def total_energy(self, phi) -> float:
+        ph = np.ascontiguousarray(phi, dtype=np.float64)
+        return lib().orc_total_energy(C.byref(self.m), _p(ph))
+
+    def update_site(self, phi: np.ndarray, mask, i: int, T: float, t: int, tag: int, r: int):
+        """Update site i of phi (float64, modified in place); returns the diagnostics."""
+        assert phi.dtype == np.float64 and phi.flags.c_contiguous
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        d = Diag()
+        lib().orc_update_site(C.byref(self.m), _p(phi), _p(mk), i, T, t, tag, r, C.byref(d))
+        return d
+
+    def halfstep(self, phi: np.ndarray, mask, colour: int, T_blk, active=None, t: int = 1,
+                 tag: int = 0, r: int = 0, diag: bool = False):
+        """In-place half-step on phi (float64 C-contiguous). Returns diag array or None."""
+        assert phi.dtype == np.float64 and phi.flags.c_contiguous
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.ascontiguousarray(T_blk, dtype=np.float64)
+        act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+        dg = np.zeros(phi.size, dtype=DIAG_DTYPE) if diag else None
+        if dg is not None:
+            dg["phi_or"] = np.nan
+        lib().orc_halfstep(C.byref(self.m), _p(phi), _p(mk), colour, _p(T),
+                           None if act is None else _p(act), t, tag, r,
+                           None if dg is None else _p(dg))
+        return dg
+
+    def init_block_mean(self, phi, mask, st: BlockStats) -> np.ndarray:
+        out = np.ascontiguousarray(phi, dtype=np.float64).copy()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        lib().orc_init_block_mean(C.byref(self.m), _p(out), _p(mk), _p(st.mean_angle),
+                                  _p(st.n_sample), st.global_mean)
+        return out
+
+    def init_random(self, phi, mask, r: int) -> np.ndarray:
+        out = np.ascontiguousarray(phi, dtype=np.float64).copy()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        lib().orc_init_random(C.byref(self.m), _p(out), _p(mk), r)
+        return out
+
+    def stop_init(self, E0, st: BlockStats):
+        n = self.nblk
+        sigma = np.zeros(n, np.int8); active = np.zeros(n, np.uint8); stop = np.zeros(n, np.int32)
+        E0 = np.ascontiguousarray(E0, dtype=np.float64)
+        lib().orc_stop_init(C.byref(self.m), _p(E0), _p(st.Es), _p(st.Nsp), _p(st.Nb),
+                            _p(st.n_gap), _p(sigma), _p(active), _p(stop))
+        return sigma, active, stop
+
+    def stop_update(self, t, n_max, E, st: BlockStats, sigma, active, stop) -> int:
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        return lib().orc_stop_update(C.byref(self.m), t, n_max, _p(E), _p(st.Es), _p(st.Nsp),
+                                     _p(st.Nb), _p(sigma), _p(active), _p(stop))
+
+    def simulate_one(self, phi0, mask, T_blk, st: BlockStats, n_max: int, r: int,
+                     trace: bool = False):
+        phi = np.ascontiguousarray(phi0, dtype=np.float64).copy()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.ascontiguousarray(T_blk, dtype=np.float64)
+        stop = np.zeros(self.nblk, np.int32)
+        tr = np.full((n_max + 1, self.nblk), np.nan) if trace else None
+        n = lib().orc_simulate_one(C.byref(self.m), _p(phi), _p(mk), _p(T), _p(st.Es),
+                                   _p(st.Nsp), _p(st.Nb), _p(st.n_gap), n_max, r, _p(stop),
+                                   None if tr is None else _p(tr))
+        return phi, stop, n, tr
+
+    def calibrate(self, phi_init, mask, st: BlockStats, n_eq=25, n_meas=20, n_bisect=24,
+                  chains=1, T_lo=1e-4, T_hi=2.0, trace=False):
+        ph = np.ascontiguousarray(phi_init, dtype=np.float64)
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.zeros(self.nblk)
+        tr = np.zeros((n_bisect, self.nblk)) if trace else None
+        lib().orc_calibrate(C.byref(self.m), _p(ph), _p(mk), _p(st.Es), _p(st.Nsp), _p(st.Nb),
+                            n_eq, n_meas, n_bisect, chains, T_lo, T_hi, _p(T),
+                            None if tr is None else _p(tr))
+        return (T, tr) if trace else T
+
+    @staticmethod
+    def median_targeted(T, Nsp) -> float:
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        Nsp = np.ascontiguousarray(Nsp, dtype=np.int64)
+        return lib().orc_median_targeted(T.size, _p(T), _p(Nsp))
+
+    @staticmethod
+    def scores(pred, truth, mask):
+        p = np.ascontiguousarray(pred, dtype=np.float32).ravel()
+        t = np.ascontiguousarray(truth, dtype=np.float32).ravel()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8).ravel()
+        a, r = C.c_double(), C.c_double()
+        lib().orc_scores(p.size, _p(p), _p(t), _p(mk), C.byref(a), C.byref(r))
+        return a.value, r.value
+
+
+@dataclass
+class GapfillResult:
+    pred: np.ndarray
+    T: np.ndarray
+    stop_sweeps: np.ndarray      # [R, nblk]
+    sweeps: np.ndarray           # [R]
+    mean_phi: np.ndarray
+    zmin: float
+    zmax: float
+    stats: BlockStats
+    gap_updates: int
+
+
+def gapfill(values, mask, lb: int, R: int, seed: int = 0, slice_id: int = 0, q: float = 0.5,
+            J: float = 1.0, n_max: int = 200, n_eq: int = 25, n_meas: int = 20,
+            n_bisect: int = 24, chains: int = 1, T_lo: float = 1e-4, T_hi: float = 2.0,
+            T_blk=None, overrelax: bool = True, threads: int = 0,
+            r0: int = 0) -> GapfillResult:
+    """The whole method on the CPU: Sec. 2.1 transform, Eq. 2 per block,
+    per-block T by energy matching (Sec. 2.2.2; skipped when T_blk is given),
+    R local-equilibrium realizations from the block-mean start (Sec. 3.3.3,
+    Sec. 3.4), their mean and the back-transform (Sec. 2.1, Sec. 3.2)."""
+    values = np.asarray(values, dtype=np.float32)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    H, W = mask.shape
+    o = Oracle(H, W, lb, q=q, J=J, seed=seed, slice_id=slice_id, overrelax=overrelax,
+               threads=threads)
+    phi, zmin, zmax, deg = o.transform(values, mask)
+    st = o.block_stats(phi, mask)
+    phi0 = o.init_block_mean(phi, mask, st)
+    if T_blk is None:
+        T = o.calibrate(phi0, mask, st, n_eq, n_meas, n_bisect, chains, T_lo, T_hi)
+    else:
+        T = np.asarray(T_blk, dtype=np.float64)
+    acc = np.zeros((H, W))
+    stops = np.zeros((R, o.nblk), np.int32)
+    sweeps = np.zeros(R, np.int32)
+    updates = 0
+    for k in range(R):
+        ph, stop, n, _ = o.simulate_one(phi0, mask, T, st, n_max, r0 + k)
+        acc += ph
+        stops[k] = stop
+        sweeps[k] = n
+        updates += int(np.sum(stop.astype(np.int64) * st.n_gap))
+    mean_phi = acc / R if R > 0 else phi0
+    pred = o.backtransform(mean_phi, mask, values, zmin, zmax)
+    return GapfillResult(pred, T, stops, sweeps, mean_phi, zmin, zmax, st, updates)

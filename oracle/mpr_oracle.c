@@ -1,0 +1,507 @@
+/*
+ * CPU oracle for SV-MPR gap filling (Lach & Zukovic, arXiv 2212.01317).
+ *
+ * TEST INFRASTRUCTURE ONLY: a plain, slow FP64 restatement of the method that
+ * the CUDA library is checked against. Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it. It shares no code with the CUDA
+ * library; the two meet only in the seeded inputs they are given.
+ *
+ * Every function follows the paper's definitions in the paper's order, one
+ * site or one bond at a time. Where the paper is silent the documented
+ * readings are:
+ *   - open (free) boundaries, 4-neighbour bonds, J = 1, q = 1/2 by default;
+ *   - a site owns its right and down bonds and a bond belongs to the block
+ *     of its owner (Sec. 2.2.2 "bond with two of its neighbors");
+ *   - e_s,b = E_s,b / N_SP,b over owned sample-sample bonds (Eq. 2 read per
+ *     bond, so both sides of the energy match are per-bond averages);
+ *   - Metropolis with an independent uniform proposal on [0, 2pi], accept iff
+ *     dE <= 0 or u1 < exp(-dE/T), followed by a restricted over-relaxation
+ *     reflection about the local field direction, kept only when it lands in
+ *     [0, 2pi];
+ *   - random numbers from Philox4x32-10 with key (seed_lo, seed_hi ^ slice)
+ *     and counter (site, sweep | tag << 16, realization >> 1, 0); realization
+ *     r uses words 2(r&1) (proposal) and 2(r&1)+1 (acceptance);
+ *   - local-equilibrium stop: a block stops at the first sweep t >= 1 at which
+ *     its specific energy has reached its sample energy from the side it
+ *     started on (Sec. 3.4 defers the exact test to the earlier MPR-GPU work);
+ *   - calibration by per-block bisection on T, each iteration re-initialised.
+ */
+#include "mpr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define TWO_PI 6.283185307179586476925286766559
+
+/* ---------------------------------------------------------------- model -- */
+
+void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, double J,
+                    uint64_t seed, uint32_t slice) {
+    memset(m, 0, sizeof(*m));
+    m->H = H;
+    m->W = W;
+    m->lb = lb;
+    m->nbx = (W + lb - 1) / lb;
+    m->nby = (H + lb - 1) / lb;
+    m->nblk = m->nbx * m->nby;
+    m->q = q;
+    m->J = J;
+    m->key0 = (uint32_t)(seed & 0xffffffffu);
+    m->key1 = (uint32_t)(seed >> 32) ^ slice;
+    m->overrelax = 1;
+    m->K = 0;
+    m->threads = 0;
+}
+
+static int block_of(const orc_model* m, int y, int x) { return (y / m->lb) * m->nbx + x / m->lb; }
+
+/* ----------------------------------------------------------------- Philox -- */
+/* Philox4x32-10 as defined by Salmon, Moraes, Dror & Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 products
+ * with the round multipliers, the key advanced by the Weyl constants between
+ * rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint64_t MA = 0xD2511F53u, MB = 0xCD9E8D57u;
+    const uint32_t WA = 0x9E3779B9u, WB = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t pa = MA * (uint64_t)c0;
+        uint64_t pb = MB * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)pb;
+        uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)pa;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += WA;
+        k1 += WB;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Top 24 bits with the lowest forced to 1, times 2^-24: an odd multiple of
+ * 2^-24 in (0,1), exactly representable in FP32 and FP64. */
+double orc_u01(uint32_t x) { return (double)((x >> 8) | 1u) * (1.0 / 16777216.0); }
+
+void orc_site_uniforms(const orc_model* m, int64_t i, uint32_t t, uint32_t tag, uint32_t r,
+                       double* u0, double* u1) {
+    uint32_t ctr[4] = {(uint32_t)i, t | (tag << 16), r >> 1, 0u};
+    uint32_t key[2] = {m->key0, m->key1};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    int o = (int)(r & 1u) * 2;
+    *u0 = orc_u01(w[o]);
+    *u1 = orc_u01(w[o + 1]);
+}
+
+/* -------------------------------------------------------------- transform -- */
+/* Sec. 2.1: the data are mapped linearly onto spin angles in [0, 2pi]; the
+ * extremes are taken over the samples (the only values known). */
+int orc_transform(int64_t n, const float* values, const uint8_t* mask, double* zmin,
+                  double* zmax, double* phi) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask[i]) continue;
+        double v = (double)values[i];
+        if (v < lo) lo = v;
+        if (v > hi) hi = v;
+    }
+    *zmin = lo;
+    *zmax = hi;
+    int degenerate = !(hi > lo);
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask[i]) { phi[i] = 0.0; continue; }
+        phi[i] = degenerate ? 0.0 : TWO_PI * ((double)values[i] - lo) / (hi - lo);
+    }
+    return degenerate;
+}
+
+/* Sec. 2.1 / Sec. 3.2: prediction = back-transformed conditional mean; samples copied. */
+void orc_backtransform(int64_t n, const double* mean_phi, const uint8_t* mask,
+                       const float* values, double zmin, double zmax, float* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        if (!mask[i]) { out[i] = values[i]; continue; }
+        out[i] = (float)(zmin + (zmax - zmin) * mean_phi[i] / TWO_PI);
+    }
+}
+
+/* ----------------------------------------------------------------- energy -- */
+static double bond_energy(const orc_model* m, double a, double b) {
+    return -m->J * cos(m->q * (a - b));
+}
+
+/* Eq. 2 applied per block: sample-sample bonds owned by the block, their count,
+ * and every owned bond (N_b). Also the block's sample mean angle (Sec. 3.3.3). */
+void orc_block_stats(const orc_model* m, const double* phi, const uint8_t* mask,
+                     double* Es, int64_t* Nsp, int64_t* Nb, double* mean_angle,
+                     int64_t* n_gap, int64_t* n_sample, double* global_mean) {
+    const int H = m->H, W = m->W;
+    double gsum = 0.0;
+    int64_t gcnt = 0;
+    for (int b = 0; b < m->nblk; ++b) {
+        Es[b] = 0.0; Nsp[b] = 0; Nb[b] = 0; mean_angle[b] = 0.0; n_gap[b] = 0; n_sample[b] = 0;
+    }
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            int b = block_of(m, y, x);
+            if (mask[i]) {
+                n_gap[b] += 1;
+            } else {
+                n_sample[b] += 1;
+                mean_angle[b] += phi[i];
+                gsum += phi[i];
+                gcnt += 1;
+            }
+            /* right bond */
+            if (x + 1 < W) {
+                Nb[b] += 1;
+                if (!mask[i] && !mask[i + 1]) {
+                    Es[b] += bond_energy(m, phi[i], phi[i + 1]);
+                    Nsp[b] += 1;
+                }
+            }
+            /* down bond */
+            if (y + 1 < H) {
+                Nb[b] += 1;
+                if (!mask[i] && !mask[i + W]) {
+                    Es[b] += bond_energy(m, phi[i], phi[i + W]);
+                    Nsp[b] += 1;
+                }
+            }
+        }
+    }
+    for (int b = 0; b < m->nblk; ++b)
+        if (n_sample[b] > 0) mean_angle[b] /= (double)n_sample[b];
+    *global_mean = gcnt > 0 ? gsum / (double)gcnt : 0.0;
+}
+
+void orc_block_energy(const orc_model* m, const double* phi, double* E) {
+    const int H = m->H, W = m->W, lb = m->lb;
+    int nthreads = m->threads;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+#endif
+    for (int b = 0; b < m->nblk; ++b) {
+        int by = b / m->nbx, bx = b % m->nbx;
+        double s = 0.0;
+        for (int y = by * lb; y < (by + 1) * lb && y < H; ++y) {
+            for (int x = bx * lb; x < (bx + 1) * lb && x < W; ++x) {
+                int64_t i = (int64_t)y * W + x;
+                if (x + 1 < W) s += bond_energy(m, phi[i], phi[i + 1]);
+                if (y + 1 < H) s += bond_energy(m, phi[i], phi[i + W]);
+            }
+        }
+        E[b] = s;
+    }
+}
+
+double orc_total_energy(const orc_model* m, const double* phi) {
+    double s = 0.0;
+    for (int y = 0; y < m->H; ++y)
+        for (int x = 0; x < m->W; ++x) {
+            int64_t i = (int64_t)y * m->W + x;
+            if (x + 1 < m->W) s += bond_energy(m, phi[i], phi[i + 1]);
+            if (y + 1 < m->H) s += bond_energy(m, phi[i], phi[i + m->W]);
+        }
+    return s;
+}
+
+/* ----------------------------------------------------------------- update -- */
+/* One conditional MC update of gap site i (Sec. 2.1: only prediction sites move;
+ * samples are fixed), at the temperature of its block (Sec. 2.2.2). */
+void orc_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64_t i,
+                     double T, uint32_t t, uint32_t tag, uint32_t r, orc_diag* d) {
+    (void)mask;
+    const int W = m->W, H = m->H;
+    const int y = (int)(i / W), x = (int)(i % W);
+    int64_t nb[4];
+    int nn = 0;
+    if (x > 0) nb[nn++] = i - 1;
+    if (x + 1 < W) nb[nn++] = i + 1;
+    if (y > 0) nb[nn++] = i - W;
+    if (y + 1 < H) nb[nn++] = i + W;
+
+    double u0, u1;
+    orc_site_uniforms(m, i, t, tag, r, &u0, &u1);
+
+    const double phi_old = phi[i];
+    double phi_prop;
+    if (m->K > 0) {
+        int k = (int)floor((double)m->K * u0);
+        if (k >= m->K) k = m->K - 1;
+        phi_prop = TWO_PI * (double)k / (double)m->K;
+    } else {
+        phi_prop = TWO_PI * u0;
+    }
+
+    /* dE = H(after) - H(before), Eq. 1 restricted to the bonds of site i. */
+    double dE = 0.0;
+    for (int k = 0; k < nn; ++k) {
+        double pj = phi[nb[k]];
+        dE += -m->J * cos(m->q * (phi_prop - pj)) + m->J * cos(m->q * (phi_old - pj));
+    }
+    const double theta = -T * log(u1);
+    int accepted = (dE <= 0.0) || (u1 < exp(-dE / T));
+    double phi_new = accepted ? phi_prop : phi_old;
+
+    /* Over-relaxation: reflect q*phi about the direction psi of the local
+     * field sum_j (cos q phi_j, sin q phi_j); the site energy
+     * -J (C cos q phi + S sin q phi) is unchanged. Kept only inside [0, 2pi]. */
+    double phi_or = NAN, R = 0.0;
+    int or_applied = 0;
+    if (m->overrelax && m->K == 0) {
+        double C = 0.0, S = 0.0;
+        for (int k = 0; k < nn; ++k) {
+            C += cos(m->q * phi[nb[k]]);
+            S += sin(m->q * phi[nb[k]]);
+        }
+        R = sqrt(C * C + S * S);
+        if (C != 0.0 || S != 0.0) {
+            double psi = atan2(S, C);
+            phi_or = (2.0 * psi - m->q * phi_new) / m->q;
+            if (phi_or >= 0.0 && phi_or <= TWO_PI) {
+                phi_new = phi_or;
+                or_applied = 1;
+            }
+        }
+    }
+    phi[i] = phi_new;
+    if (d) {
+        d->dE = dE;
+        d->theta = theta;
+        d->phi_or = phi_or;
+        d->R = R;
+        d->phi_old = phi_old;
+        d->phi_prop = phi_prop;
+        d->accepted = accepted;
+        d->or_applied = or_applied;
+    }
+}
+
+/* Sec. 2.2.2 single checkerboard: the sites of one sub-grid have all their
+ * neighbours on the other, so one colour is updated at a time (here in raster
+ * order; any order gives the same result). */
+void orc_halfstep(const orc_model* m, double* phi, const uint8_t* mask, int colour,
+                  const double* T_blk, const uint8_t* active, uint32_t t, uint32_t tag,
+                  uint32_t r, orc_diag* diag) {
+    const int H = m->H, W = m->W;
+    int nthreads = m->threads;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+#endif
+    for (int y = 0; y < H; ++y) {
+        for (int x = (y + colour) & 1; x < W; x += 2) {
+            int64_t i = (int64_t)y * W + x;
+            if (!mask[i]) continue;
+            int b = block_of(m, y, x);
+            if (active && !active[b]) continue;
+            orc_update_site(m, phi, mask, i, T_blk[b], t, tag, r, diag ? &diag[i] : NULL);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------- init -- */
+void orc_init_block_mean(const orc_model* m, double* phi, const uint8_t* mask,
+                         const double* mean_angle, const int64_t* n_sample, double global_mean) {
+    for (int y = 0; y < m->H; ++y)
+        for (int x = 0; x < m->W; ++x) {
+            int64_t i = (int64_t)y * m->W + x;
+            if (!mask[i]) continue;
+            int b = block_of(m, y, x);
+            phi[i] = n_sample[b] > 0 ? mean_angle[b] : global_mean;
+        }
+}
+
+void orc_init_random(const orc_model* m, double* phi, const uint8_t* mask, uint32_t r) {
+    for (int64_t i = 0; i < (int64_t)m->H * m->W; ++i) {
+        if (!mask[i]) continue;
+        double u0, u1;
+        orc_site_uniforms(m, i, 0u, 0xFFFFu, r, &u0, &u1);
+        phi[i] = TWO_PI * u0;
+    }
+}
+
+/* ------------------------------------------------------------------- stop -- */
+/* t = 0 bookkeeping: a block without gap sites has nothing to simulate and is
+ * stopped; sigma_b records from which side e_b starts relative to e_s,b. */
+void orc_stop_init(const orc_model* m, const double* E0, const double* Es, const int64_t* Nsp,
+                   const int64_t* Nb, const int64_t* n_gap, int8_t* sigma, uint8_t* active,
+                   int32_t* stop_sweep) {
+    int targeted_active = 0;
+    for (int b = 0; b < m->nblk; ++b) {
+        sigma[b] = 0;
+        active[b] = n_gap[b] > 0;
+        stop_sweep[b] = active[b] ? -1 : 0;
+        if (Nsp[b] > 0) {
+            double es = Es[b] / (double)Nsp[b];
+            double e0 = E0[b] / (double)Nb[b];
+            sigma[b] = (int8_t)((es > e0) - (es < e0));
+            if (active[b]) targeted_active = 1;
+        }
+    }
+    if (!targeted_active)
+        for (int b = 0; b < m->nblk; ++b)
+            if (active[b]) { active[b] = 0; stop_sweep[b] = 0; }
+}
+
+/* After sweep t: a targeted block stops once sigma_b (e_b(t) - e_s,b) >= 0; a
+ * block without sample bonds stops when no targeted block is left running;
+ * every block stops at t = n_max. Returns the number of blocks still active. */
+int orc_stop_update(const orc_model* m, int32_t t, int32_t n_max, const double* E,
+                    const double* Es, const int64_t* Nsp, const int64_t* Nb, const int8_t* sigma,
+                    uint8_t* active, int32_t* stop_sweep) {
+    int targeted_active = 0;
+    for (int b = 0; b < m->nblk; ++b) {
+        if (!active[b] || Nsp[b] == 0) continue;
+        double es = Es[b] / (double)Nsp[b];
+        double e = E[b] / (double)Nb[b];
+        if ((double)sigma[b] * (e - es) >= 0.0) {
+            active[b] = 0;
+            stop_sweep[b] = t;
+        } else {
+            targeted_active = 1;
+        }
+    }
+    int left = 0;
+    for (int b = 0; b < m->nblk; ++b) {
+        if (!active[b]) continue;
+        if ((Nsp[b] == 0 && !targeted_active) || t >= n_max) {
+            active[b] = 0;
+            stop_sweep[b] = t;
+        } else {
+            left += 1;
+        }
+    }
+    return left;
+}
+
+int orc_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const double* T_blk,
+                     const double* Es, const int64_t* Nsp, const int64_t* Nb,
+                     const int64_t* n_gap, int32_t n_max, uint32_t r, int32_t* stop_sweep,
+                     double* e_trace) {
+    const int nblk = m->nblk;
+    double* E = (double*)malloc(sizeof(double) * nblk);
+    int8_t* sigma = (int8_t*)malloc(nblk);
+    uint8_t* active = (uint8_t*)malloc(nblk);
+    orc_block_energy(m, phi, E);
+    if (e_trace)
+        for (int b = 0; b < nblk; ++b) e_trace[b] = Nb[b] > 0 ? E[b] / (double)Nb[b] : 0.0;
+    orc_stop_init(m, E, Es, Nsp, Nb, n_gap, sigma, active, stop_sweep);
+    int left = 0;
+    for (int b = 0; b < nblk; ++b) left += active[b];
+    int t = 0;
+    while (left > 0 && t < n_max) {
+        t += 1;
+        orc_halfstep(m, phi, mask, 0, T_blk, active, (uint32_t)t, 0u, r, NULL);
+        orc_halfstep(m, phi, mask, 1, T_blk, active, (uint32_t)t, 0u, r, NULL);
+        orc_block_energy(m, phi, E);
+        if (e_trace)
+            for (int b = 0; b < nblk; ++b)
+                e_trace[(int64_t)t * nblk + b] = Nb[b] > 0 ? E[b] / (double)Nb[b] : 0.0;
+        left = orc_stop_update(m, t, n_max, E, Es, Nsp, Nb, sigma, active, stop_sweep);
+    }
+    free(E);
+    free(sigma);
+    free(active);
+    return t;
+}
+
+/* ------------------------------------------------------------ calibration -- */
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Median of the targeted blocks' temperatures: the middle element for an odd
+ * count, the mean of the two middle elements for an even count. */
+double orc_median_targeted(int32_t nblk, const double* T, const int64_t* Nsp) {
+    double* v = (double*)malloc(sizeof(double) * (nblk > 0 ? nblk : 1));
+    int n = 0;
+    for (int b = 0; b < nblk; ++b)
+        if (Nsp[b] > 0) v[n++] = T[b];
+    double med = 0.0;
+    if (n > 0) {
+        qsort(v, (size_t)n, sizeof(double), cmp_double);
+        med = (n & 1) ? v[n / 2] : 0.5 * (v[n / 2 - 1] + v[n / 2]);
+    }
+    free(v);
+    return med;
+}
+
+/* Sec. 2.1 estimates T by matching the simulated specific energy with e_s;
+ * Sec. 2.2.2 does this per block. Each bisection iteration k: every targeted
+ * block takes the midpoint of its bracket, blocks without sample bonds take
+ * the median of those midpoints; the initialised state is equilibrated for
+ * n_eq sweeps and e_b is averaged over n_meas further sweeps (and over the
+ * chains); then the bracket half on the wrong side of e_s,b is dropped
+ * (<e_b> increases with T). Random numbers use tag 1 + k. */
+void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* mask,
+                   const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                   int32_t n_meas, int32_t n_bisect, int32_t chains, double T_lo, double T_hi,
+                   double* T_out, double* ebar_trace) {
+    const int nblk = m->nblk;
+    const int64_t n = (int64_t)m->H * m->W;
+    double* lo = (double*)malloc(sizeof(double) * nblk);
+    double* hi = (double*)malloc(sizeof(double) * nblk);
+    double* T = (double*)malloc(sizeof(double) * nblk);
+    double* ebar = (double*)malloc(sizeof(double) * nblk);
+    double* E = (double*)malloc(sizeof(double) * nblk);
+    double* phi = (double*)malloc(sizeof(double) * n);
+    for (int b = 0; b < nblk; ++b) { lo[b] = T_lo; hi[b] = T_hi; }
+    for (int k = 0; k < n_bisect; ++k) {
+        for (int b = 0; b < nblk; ++b) T[b] = 0.5 * (lo[b] + hi[b]);
+        double med = orc_median_targeted(nblk, T, Nsp);
+        for (int b = 0; b < nblk; ++b) {
+            if (Nsp[b] == 0) T[b] = med;
+            ebar[b] = 0.0;
+        }
+        for (int c = 0; c < chains; ++c) {
+            memcpy(phi, phi_init, sizeof(double) * n);
+            for (int s = 1; s <= n_eq + n_meas; ++s) {
+                orc_halfstep(m, phi, mask, 0, T, NULL, (uint32_t)s, (uint32_t)(1 + k), (uint32_t)c, NULL);
+                orc_halfstep(m, phi, mask, 1, T, NULL, (uint32_t)s, (uint32_t)(1 + k), (uint32_t)c, NULL);
+                if (s > n_eq) {
+                    orc_block_energy(m, phi, E);
+                    for (int b = 0; b < nblk; ++b)
+                        if (Nb[b] > 0) ebar[b] += E[b] / (double)Nb[b];
+                }
+            }
+        }
+        for (int b = 0; b < nblk; ++b) {
+            ebar[b] /= (double)n_meas * (double)chains;
+            if (ebar_trace) ebar_trace[(int64_t)k * nblk + b] = ebar[b];
+            if (Nsp[b] == 0) continue;
+            double es = Es[b] / (double)Nsp[b];
+            if (ebar[b] < es) lo[b] = T[b]; else hi[b] = T[b];
+        }
+    }
+    for (int b = 0; b < nblk; ++b) T_out[b] = 0.5 * (lo[b] + hi[b]);
+    double med = orc_median_targeted(nblk, T_out, Nsp);
+    for (int b = 0; b < nblk; ++b)
+        if (Nsp[b] == 0) T_out[b] = med;
+    free(lo); free(hi); free(T); free(ebar); free(E); free(phi);
+}
+
+/* ----------------------------------------------------------------- scores -- */
+/* Eqs. 3-4: AAE and RASE over the P prediction sites. */
+void orc_scores(int64_t n, const float* pred, const float* truth, const uint8_t* mask,
+                double* aae, double* rase) {
+    double sa = 0.0, s2 = 0.0;
+    int64_t P = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!mask[i]) continue;
+        double e = (double)truth[i] - (double)pred[i];
+        sa += fabs(e);
+        s2 += e * e;
+        P += 1;
+    }
+    *aae = P ? sa / (double)P : 0.0;
+    *rase = P ? sqrt(s2 / (double)P) : 0.0;
+}

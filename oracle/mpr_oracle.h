@@ -1,0 +1,117 @@
+/*
+ * CPU oracle for SV-MPR gap filling (Lach & Zukovic, arXiv 2212.01317).
+ *
+ * TEST INFRASTRUCTURE ONLY. This is a plain, slow, FP64 restatement of the
+ * method used to check the CUDA library. Only the test-suite, the smoke check
+ * and the benchmark's CPU-baseline leg may load it; the product path never
+ * does. It shares no code with the CUDA library.
+ *
+ * Layout: angles phi are full-grid, row-major double arrays [H*W] per
+ * realization; mask is uint8 [H*W] with 1 = gap (prediction site, G_P) and
+ * 0 = sample (G_S). Blocks are lb x lb squares, b = (y/lb)*nbx + x/lb.
+ */
+#ifndef MPR_ORACLE_H
+#define MPR_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t H, W, lb;        /* grid and block side l_b */
+    int32_t nbx, nby, nblk;  /* filled by orc_model_init */
+    double q, J;             /* Eq. 1 parameters */
+    uint32_t key0, key1;     /* Philox key: (seed_lo, seed_hi ^ slice) */
+    int32_t overrelax;       /* 1: Metropolis followed by over-relaxation */
+    int32_t K;               /* 0: continuous angles; K>0: K discrete levels, OR off */
+    int32_t threads;         /* OpenMP threads (<=0: library default) */
+} orc_model;
+
+void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, double J,
+                    uint64_t seed, uint32_t slice);
+
+/* Philox4x32-10 (Salmon et al., SC'11) and the (0,1) uniform used by the chain. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_u01(uint32_t x);
+/* The two uniforms (u0 proposal, u1 acceptance) of site i, sweep t, tag, realization r. */
+void orc_site_uniforms(const orc_model* m, int64_t i, uint32_t t, uint32_t tag, uint32_t r,
+                       double* u0, double* u1);
+
+/* Sec. 2.1: linear map of sample values onto [0, 2pi]; returns 1 if z_max == z_min. */
+int orc_transform(int64_t n, const float* values, const uint8_t* mask, double* zmin,
+                  double* zmax, double* phi);
+void orc_backtransform(int64_t n, const double* mean_phi, const uint8_t* mask,
+                       const float* values, double zmin, double zmax, float* out);
+
+/* Eq. 2 per block with owned-bond counting (Sec. 2.2.2). */
+void orc_block_stats(const orc_model* m, const double* phi, const uint8_t* mask,
+                     double* Es, int64_t* Nsp, int64_t* Nb, double* mean_angle,
+                     int64_t* n_gap, int64_t* n_sample, double* global_mean);
+/* Eq. 1 restricted to the bonds owned by each block. */
+void orc_block_energy(const orc_model* m, const double* phi, double* E);
+/* Eq. 1 over the whole grid. */
+double orc_total_energy(const orc_model* m, const double* phi);
+
+/* Per-site diagnostics of one update (margins of the floating-point decisions). */
+typedef struct {
+    double dE, theta;   /* Metropolis: accept iff dE < theta (theta = -T ln u1) */
+    double phi_or;      /* over-relaxed candidate (NaN when skipped) */
+    double R;           /* |C + iS| of the neighbour field (OR conditioning) */
+    double phi_old, phi_prop;
+    int32_t accepted, or_applied;
+} orc_diag;
+
+/* Metropolis (+ OR) update of gap site i at temperature T, in place. */
+void orc_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64_t i,
+                     double T, uint32_t t, uint32_t tag, uint32_t r, orc_diag* d);
+/* One checkerboard half-step (Sec. 2.2.2): all gap sites of `colour` whose block
+ * is active. T_blk[nblk]; active[nblk] (NULL = all active); diag[H*W] or NULL. */
+void orc_halfstep(const orc_model* m, double* phi, const uint8_t* mask, int colour,
+                  const double* T_blk, const uint8_t* active, uint32_t t, uint32_t tag,
+                  uint32_t r, orc_diag* diag);
+
+/* Sec. 3.3.3 initialisation: gaps <- block sample mean (fallback: global mean). */
+void orc_init_block_mean(const orc_model* m, double* phi, const uint8_t* mask,
+                         const double* mean_angle, const int64_t* n_sample, double global_mean);
+/* Plain-MPR random initialisation: gaps <- 2*pi*u from the reserved tag 0xFFFF. */
+void orc_init_random(const orc_model* m, double* phi, const uint8_t* mask, uint32_t r);
+
+/* Local-equilibrium simulation of one realization with per-block stop (Sec. 3.4).
+ * phi holds the initial state on entry and the final state on exit.
+ * stop_sweep[nblk] receives each block's stop sweep. e_trace (nullable) receives
+ * e_b(t) for t = 0..n_max as [(n_max+1) * nblk] (unused entries untouched).
+ * Returns the number of sweeps run. */
+int orc_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const double* T_blk,
+                     const double* Es, const int64_t* Nsp, const int64_t* Nb,
+                     const int64_t* n_gap, int32_t n_max, uint32_t r, int32_t* stop_sweep,
+                     double* e_trace);
+
+/* Stop bookkeeping shared by orc_simulate_one and step-wise callers:
+ * decide stops after sweep t given block energies E[nblk]. */
+void orc_stop_init(const orc_model* m, const double* E0, const double* Es, const int64_t* Nsp,
+                   const int64_t* Nb, const int64_t* n_gap, int8_t* sigma, uint8_t* active,
+                   int32_t* stop_sweep);
+int orc_stop_update(const orc_model* m, int32_t t, int32_t n_max, const double* E,
+                    const double* Es, const int64_t* Nsp, const int64_t* Nb, const int8_t* sigma,
+                    uint8_t* active, int32_t* stop_sweep);
+
+/* Block-temperature calibration by bisection (Sec. 2.1 energy matching applied
+ * per block as in Sec. 2.2.2). phi_init holds the initialised state (copied for
+ * every chain of every iteration). T_out[nblk]. ebar_trace (nullable) gets the
+ * per-iteration measured energies [n_bisect * nblk]. */
+void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* mask,
+                   const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                   int32_t n_meas, int32_t n_bisect, int32_t chains, double T_lo, double T_hi,
+                   double* T_out, double* ebar_trace);
+/* Median of the temperatures of targeted blocks (Sec. 2.2.2 fallback). */
+double orc_median_targeted(int32_t nblk, const double* T, const int64_t* Nsp);
+
+/* Sec. 3.2, Eqs. 3-4 over the gap sites. */
+void orc_scores(int64_t n, const float* pred, const float* truth, const uint8_t* mask,
+                double* aae, double* rase);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,194 @@
+"""Seeded synthetic inputs shaped like the remote-sensing grids of Lach & Zukovic
+(arXiv 2212.01317, Sec. 3.1, Table 1): Gaussian random fields with exponential
+covariance (stationary and with a correlation length that drifts across the
+grid), optional nugget and lognormal marginal, thinned by uniformly random or
+cloud-like (union of discs) gap masks (Sec. 3.2 thins the data at random).
+
+This module produces values and masks only. It holds none of the method's
+arithmetic (no transform, no energy, no sampling of the MPR chain), so both the
+CUDA path and the CPU oracle can consume its output.
+
+Recipe (each generator is a pure function of its arguments and seed):
+  * GRF: spectral synthesis on a periodic torus of side max(L, 8*xi_max).
+    C(r) = exp(-r/xi) with periodic distance, S = Re FFT(C) clipped at 0,
+    field = Re IFFT(sqrt(S) * FFT(w)), w ~ N(0,1) white noise, cropped to HxW
+    and standardised to zero mean / unit variance.
+  * Non-stationary GRF: the same w filtered at 8 log-spaced xi_k; column x
+    blends the two bracketing fields (linear weight in log xi) at
+    xi(x) = xi_min + (xi_max - xi_min) * x / (W-1); re-standardised.
+  * Random mask: exactly round(p*H*W) gap sites from a seeded permutation.
+  * Disc mask: discs of uniform radius [r_min, r_max] and uniform centre are
+    added one at a time until the gap fraction reaches the target.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "grf", "grf_nonstationary", "mask_random", "mask_discs", "Workload",
+    "workload", "WORKLOADS",
+]
+
+
+def _torus_spectrum(n: int, xi: float) -> np.ndarray:
+    d = np.arange(n, dtype=np.float64)
+    d = np.minimum(d, n - d)
+    r = np.sqrt(d[:, None] ** 2 + d[None, :] ** 2)
+    c = np.exp(-r / float(xi))
+    s = np.fft.rfft2(c).real
+    np.maximum(s, 0.0, out=s)
+    return s
+
+
+def _filtered(wf: np.ndarray, n: int, xi: float) -> np.ndarray:
+    s = _torus_spectrum(n, xi)
+    return np.fft.irfft2(np.sqrt(s) * wf, s=(n, n))
+
+
+def _standardise(f: np.ndarray) -> np.ndarray:
+    f = f - f.mean()
+    sd = f.std()
+    return f / sd if sd > 0 else f
+
+
+def grf(h: int, w: int, xi: float, seed: int) -> np.ndarray:
+    """Stationary zero-mean unit-variance GRF with exponential covariance (float64)."""
+    n = int(max(h, w, math.ceil(8 * xi)))
+    rng = np.random.default_rng(seed)
+    wn = rng.standard_normal((n, n))
+    f = _filtered(np.fft.rfft2(wn), n, xi)[:h, :w]
+    return _standardise(f)
+
+
+def grf_nonstationary(h: int, w: int, xi_min: float, xi_max: float, seed: int,
+                      n_levels: int = 8) -> np.ndarray:
+    """GRF whose correlation length grows linearly from xi_min (x=0) to xi_max (x=W-1)."""
+    n = int(max(h, w, math.ceil(8 * xi_max)))
+    rng = np.random.default_rng(seed)
+    wn = rng.standard_normal((n, n))
+    wf = np.fft.rfft2(wn)
+    lx = np.linspace(math.log(xi_min), math.log(xi_max), n_levels)
+    xis = np.exp(lx)
+    x = np.arange(w, dtype=np.float64)
+    xi_x = xi_min + (xi_max - xi_min) * x / max(w - 1, 1)
+    lxi = np.log(xi_x)
+    k = np.clip(np.searchsorted(lx, lxi, side="right") - 1, 0, n_levels - 2)
+    a = np.clip((lxi - lx[k]) / (lx[k + 1] - lx[k]), 0.0, 1.0)
+    out = np.zeros((h, w), dtype=np.float64)
+    for lev in range(n_levels):
+        wt = np.where(k == lev, 1.0 - a, 0.0) + np.where(k + 1 == lev, a, 0.0)
+        if not np.any(wt):
+            continue
+        f = _standardise(_filtered(wf, n, xis[lev])[:h, :w])
+        out += f * wt[None, :]
+    return _standardise(out)
+
+
+def mask_random(h: int, w: int, p: float, seed: int) -> np.ndarray:
+    """uint8 mask (1 = gap) with exactly round(p*h*w) gaps."""
+    n = h * w
+    k = int(round(p * n))
+    rng = np.random.default_rng(seed)
+    m = np.zeros(n, dtype=np.uint8)
+    m[rng.permutation(n)[:k]] = 1
+    return m.reshape(h, w)
+
+
+def mask_discs(h: int, w: int, frac: float, seed: int, r_min: float = 5.0,
+               r_max: float = 60.0) -> np.ndarray:
+    """uint8 mask (1 = gap): union of random discs until the gap fraction >= frac."""
+    rng = np.random.default_rng(seed)
+    m = np.zeros((h, w), dtype=np.uint8)
+    target = frac * h * w
+    covered = 0
+    while covered < target:
+        r = rng.uniform(r_min, r_max)
+        cy = rng.uniform(0, h)
+        cx = rng.uniform(0, w)
+        y0, y1 = max(0, int(cy - r)), min(h, int(cy + r) + 1)
+        x0, x1 = max(0, int(cx - r)), min(w, int(cx + r) + 1)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        yy = np.arange(y0, y1)[:, None] + 0.5
+        xx = np.arange(x0, x1)[None, :] + 0.5
+        inside = (yy - cy) ** 2 + (xx - cx) ** 2 <= r * r
+        sub = m[y0:y1, x0:x1]
+        covered += int(np.count_nonzero(inside & (sub == 0)))
+        sub[inside] = 1
+    return m
+
+
+@dataclass
+class Workload:
+    """One synthetic gap-filling problem: truth field, gap mask and run parameters."""
+    name: str
+    truth: np.ndarray          # float32 [H, W]
+    mask: np.ndarray           # uint8 [H, W], 1 = gap
+    block: int                 # l_b
+    realizations: int
+    storage: str = "f32"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def values(self) -> np.ndarray:
+        """Values handed to the library: truth at data sites, NaN at gaps."""
+        v = self.truth.copy()
+        v[self.mask != 0] = np.nan
+        return v
+
+    @property
+    def shape(self):
+        return self.truth.shape
+
+    @property
+    def n_gap(self) -> int:
+        return int(np.count_nonzero(self.mask))
+
+
+def _wl_field128(seed: int = 0) -> Workload:
+    z = grf(128, 128, 8.0, seed).astype(np.float32)
+    m = mask_random(128, 128, 0.33, seed + 1)
+    return Workload("field128_xi8_p33_lb8_R10", z, m, 8, 10,
+                    meta={"H": 128, "W": 128, "xi": 8, "p": 0.33})
+
+
+def _wl_field1024(seed: int = 0) -> Workload:
+    g = grf_nonstationary(1024, 1024, 4.0, 32.0, seed)
+    rng = np.random.default_rng(seed + 7)
+    z = (g + rng.normal(0.0, 0.1, g.shape)).astype(np.float32)
+    m = mask_random(1024, 1024, 0.5, seed + 1)
+    return Workload("field1024_xi4-32_nug0.1_p50_lb16_R100", z, m, 16, 100,
+                    meta={"H": 1024, "W": 1024, "xi": [4, 32], "p": 0.5, "nugget": 0.1})
+
+
+def _wl_field4096(seed: int = 0) -> Workload:
+    g = grf_nonstationary(4096, 4096, 4.0, 64.0, seed)
+    z = np.exp(0.5 * g).astype(np.float32)
+    m = mask_discs(4096, 4096, 0.6, seed + 1)
+    return Workload("field4096_xi4-64_lognormal_disc60_lb32", z, m, 32, 10, storage="bf16",
+                    meta={"H": 4096, "W": 4096, "xi": [4, 64], "p": float(m.mean())})
+
+
+WORKLOADS = {
+    "field128": _wl_field128,
+    "field1024": _wl_field1024,
+    "field4096": _wl_field4096,
+}
+
+
+def workload(name: str, seed: int = 0) -> Workload:
+    return WORKLOADS[name](seed)
+
+
+def small_problem(h: int, w: int, p: float, seed: int, xi: float = 6.0,
+                  kind: str = "random") -> tuple[np.ndarray, np.ndarray]:
+    """(truth float32 [h,w], mask uint8 [h,w]) for tests at arbitrary small sizes."""
+    z = grf(h, w, xi, seed).astype(np.float32)
+    if kind == "random":
+        m = mask_random(h, w, p, seed + 1)
+    else:
+        m = mask_discs(h, w, p, seed + 1, r_min=1.5, r_max=max(2.0, min(h, w) / 6))
+    return z, m
