@@ -1,0 +1,387 @@
+"""Benchmark of the SV-MPR hot path on GB300 (one JSON line on rank 0).
+
+A step is one pass of the whole method over one synthetic field: create
+(Sec. 2.1 transform, Eq. 2 per block), per-block temperature calibration,
+R local-equilibrium realizations with per-block stop, and the back-transformed
+mean. Default workload: a 1024 x 1024 non-stationary Gaussian random field
+(correlation length 4 -> 32 cells left to right, N(0, 0.1^2) nugget), 50 %
+gaps at random, 16 x 16 temperature blocks, 100 realizations, FP32.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Metric: gap-site updates/s (Metropolis + over-relaxation site updates of the
+calibration and of the realizations, per second of step time); the line also
+carries gap-filled Mpix/s. Under torchrun every rank fills its own field
+(independent slices, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gap-site updates/s"
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="field1024")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def bytes_per_gap_update(s_bytes: float, p: float) -> float:
+    """Algorithmic HBM bytes per gap-site update of one field: per sweep the
+    two half-steps read the other colour once (s*HW), read and write the
+    gap sites (2*s*p*HW) and read the gap mask (HW/8 bytes); divided by the
+    p*HW updates of the sweep."""
+    return (s_bytes * (1.0 + 2.0 * p) + 0.125) / p
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower() in ("active", "1")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ reference --
+def run_reference(args, world, rank):
+    """The oracle (FP64 C, all host cores) on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2212_01317_gb300 import synth
+    oracle.build()
+    wl = synth.workload(args.workload)
+    H, W = wl.shape
+    lb = wl.block
+    cores = len(os.sched_getaffinity(0))
+    o = oracle.Oracle(H, W, lb, seed=2024, threads=cores)
+    phi, zmin, zmax, _ = o.transform(wl.truth, wl.mask)
+    st = o.block_stats(phi, wl.mask)
+    phi0 = o.init_block_mean(phi, wl.mask, st)
+    T = np.full(o.nblk, 0.1)
+
+    def step(r):
+        t0 = time.perf_counter()
+        _, stop, _, _ = o.simulate_one(phi0, wl.mask, T, st, 200, r)
+        dt = time.perf_counter() - t0
+        return int(np.sum(stop.astype(np.int64) * st.n_gap)), dt
+
+    for r in range(args.warmup):
+        step(r)
+    ups, secs = 0, 0.0
+    for r in range(args.steps):
+        u, dt = step(args.warmup + r)
+        ups += u
+        secs += dt
+    val = ups / secs
+    sample = (f"oracle simulate of one realization per step on {wl.name} at uniform T=0.1 "
+              f"(calibration not run), {cores} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "H": H, "W": W, "block": lb,
+                       "realizations": wl.realizations},
+            "cpu_baseline": {"value": val, "unit": "updates/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- our arm --
+def cpu_baseline(wl, T_gpu, seconds):
+    import oracle
+    oracle.build()
+    H, W = wl.shape
+    cores = len(os.sched_getaffinity(0))
+    o = oracle.Oracle(H, W, wl.block, seed=2024, threads=cores)
+    phi, *_ = o.transform(wl.truth, wl.mask)
+    st = o.block_stats(phi, wl.mask)
+    phi0 = o.init_block_mean(phi, wl.mask, st)
+    T = np.asarray(T_gpu, dtype=np.float64)
+    ups, secs, r = 0, 0.0, 0
+    while secs < seconds or r == 0:
+        t0 = time.perf_counter()
+        _, stop, _, _ = o.simulate_one(phi0, wl.mask, T, st, 200, r)
+        secs += time.perf_counter() - t0
+        ups += int(np.sum(stop.astype(np.int64) * st.n_gap))
+        r += 1
+    return {"value": ups / secs, "unit": "updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{r} realization(s) of {wl.name} at the GPU-calibrated block T, "
+                      f"simulate only, {secs:.1f} s on {cores} threads"}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2212_01317_gb300 import mpr, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mpr.load()
+    wl = synth.workload(args.workload, seed=0)
+    H, W = wl.shape
+    n = H * W
+    P = wl.n_gap
+    p = P / n
+    R = wl.realizations
+    stream = torch.cuda.current_stream(dev)
+    vals_h = np.where(wl.mask != 0, np.nan, wl.truth).astype(np.float32)
+    values_d = torch.from_numpy(vals_h).to(dev)
+    mask_d = torch.from_numpy(wl.mask).to(dev)
+    out_d = torch.empty((H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def options(profile):
+        return mpr.mpr_default_options(seed=2024 + 7919 * rank, slice_id=rank, profile=profile,
+                                       cuda_stream=stream.cuda_stream)
+
+    def step(values, mask, out, profile=1):
+        ctx = mpr.mpr_create(H, W, wl.block, mask, values, options(profile))
+        try:
+            mpr.mpr_calibrate(ctx, None)
+            mpr.mpr_simulate(ctx, R)
+            mpr.mpr_predict(ctx, out)
+            info = mpr.mpr_get_info(ctx)
+            prof = mpr.mpr_get_profile(ctx)
+        finally:
+            mpr.mpr_destroy(ctx)
+        return info, prof
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(values_d, mask_d, out_d)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, updates, cal_updates, launches = [], 0, 0, 0
+    sim_ms = cal_ms = 0.0
+    sim_launch = cal_launch = sim_updates = 0
+    for k in range(args.steps):
+        flush.zero_()                              # L2 flush between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info, prof = step(values_d, mask_d, out_d)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        updates += info.gap_updates + info.cal_gap_updates
+        sim_updates += info.gap_updates
+        cal_updates += info.cal_gap_updates
+        launches += prof.kernel_launches
+        sim_ms += prof.sim_halfstep_ms
+        cal_ms += prof.cal_halfstep_ms
+        sim_launch += prof.sim_halfstep_launches
+        cal_launch += prof.cal_halfstep_launches
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([float(updates)], device=dev, dtype=torch.float64)
+        dist.all_reduce(u)
+        updates_all = float(u.item())
+    else:
+        updates_all = float(updates)
+    value = updates_all / (total_ms / 1e3)
+    mpix = world * P * args.steps / (total_ms / 1e3) / 1e6
+
+    # End to end through the C-ABI with pinned host buffers: the H2D copy of
+    # the step's inputs and the D2H copy of its predictions are timed.
+    e2e = None
+    if not args.no_e2e:
+        vals_pin = torch.from_numpy(vals_h).pin_memory()
+        mask_pin = torch.from_numpy(wl.mask).pin_memory()
+        out_pin = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        step(vals_pin, mask_pin, out_pin, profile=0)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ups = 0
+        for k in range(args.steps):
+            info, _ = step(vals_pin, mask_pin, out_pin, profile=0)
+            ups += info.gap_updates + info.cal_gap_updates
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * ups / dt, "unit": "updates/s",
+               "h2d_bytes_per_step": int(vals_h.nbytes + wl.mask.nbytes),
+               "d2h_bytes_per_step": int(out_pin.numel() * 4),
+               "gap_filled_mpix_s": world * P * args.steps / dt / 1e6}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peaks()
+    bpu = bytes_per_gap_update(4.0, p)
+    sim_gbs = sim_updates * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+    cal_gbs = cal_updates * bpu / (cal_ms / 1e3) / 1e9 if cal_ms > 0 else None
+    # Dominant kernel by summed device time.
+    dom = "sim" if sim_ms >= cal_ms else "cal"
+    achieved = sim_gbs if dom == "sim" else cal_gbs
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(f"k_halfstep_{dom}_{wl.name}")
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+        "kernel": f"k_halfstep ({'realizations' if dom == 'sim' else 'calibration'})",
+        "peak_kind": peak_kind,
+        "bytes_per_gap_update": bpu,
+        "avg_launch_us": 1e3 * (sim_ms / sim_launch if dom == "sim" else cal_ms / max(cal_launch, 1)),
+        "sim_halfstep": {"ms": sim_ms / args.steps, "launches": sim_launch // args.steps,
+                         "gbs": sim_gbs,
+                         "updates_per_s": sim_updates / (sim_ms / 1e3) if sim_ms else None},
+        "cal_halfstep": {"ms": cal_ms / args.steps, "launches": cal_launch // args.steps,
+                         "gbs": cal_gbs,
+                         "updates_per_s": cal_updates / (cal_ms / 1e3) if cal_ms else None},
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "H": H, "W": W, "block": wl.block, "gap_fraction": p,
+                   "realizations": R, "storage": "f32", "l2": "flushed between timed steps",
+                   "parallelism": f"replicas{world}"},
+        "gap_filled_mpix_s": mpix,
+        "updates_per_step": {"calibration": cal_updates // args.steps,
+                             "realizations": sim_updates // args.steps},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu:
+        ctx = mpr.mpr_create(H, W, wl.block, mask_d, values_d, options(0))
+        T = np.zeros(mpr.mpr_get_info(ctx).nblk, np.float32)
+        mpr.mpr_calibrate(ctx, T)
+        mpr.mpr_destroy(ctx)
+        line["cpu_baseline"] = cpu_baseline(wl, T, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

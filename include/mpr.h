@@ -1,0 +1,208 @@
+/*
+ * libmpr — SV-MPR gap filling on one GB300 (sm_103a).
+ *
+ * Spatially variable modified-planar-rotator gap filling of Lach & Zukovic,
+ * "Fast gap-filling of massive data by local-equilibrium conditional
+ * simulations on GPU" (arXiv 2212.01317): block-specific temperatures
+ * (Sec. 2.2.2, "BST"), checkerboard conditional Monte Carlo of Eq. 1 over the
+ * gap sites only, a per-block stop at local equilibrium, and the conditional
+ * mean back-transformed to the data scale (Sec. 2.1, Sec. 3.2).
+ *
+ * Conventions for every entry point:
+ *   - Grids are row-major H x W; site (y,x) has linear index y*W + x and
+ *     checkerboard colour (x + y) & 1. Blocks are l_b x l_b squares, block
+ *     id b = (y / l_b) * nbx + x / l_b with nbx = ceil(W / l_b); edge blocks
+ *     may be partial.
+ *   - mask[i] != 0 marks a gap (prediction site); mask[i] == 0 a sample.
+ *   - Pointer arguments may be host or device memory (detected with
+ *     cudaPointerGetAttributes); device pointers must be on the context's
+ *     device. Inputs are copied; the caller keeps ownership of every buffer it
+ *     passes. Outputs are written into caller-allocated buffers of the stated
+ *     size.
+ *   - All work is issued on the context's CUDA stream (mpr_options.cuda_stream,
+ *     NULL = the legacy default stream). Calls that return host-visible data
+ *     synchronise that stream before returning.
+ *   - No call throws; each returns an mpr_status and records a message that
+ *     mpr_last_error() returns until the next call on the same context.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef MPR_H
+#define MPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPR_ABI_VERSION 1
+
+typedef struct mpr_ctx mpr_ctx; /* opaque; owns every device buffer it uses */
+
+typedef enum {
+    MPR_OK = 0,
+    MPR_EINVAL = 1,      /* bad argument: sizes, pointers, option values */
+    MPR_ENOMEM = 2,      /* device or host allocation failed */
+    MPR_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    MPR_ENOSAMPLES = 4,  /* no nearest-neighbour sample pair anywhere: Eq. 2 undefined */
+    MPR_ETIMEOUT = 5,    /* a bounded device-side wait gave up (reported, not hung) */
+    MPR_ESTATE = 6       /* call out of order (e.g. predict before simulate) */
+} mpr_status;
+
+typedef enum { MPR_STORE_F32 = 0, MPR_STORE_BF16 = 1, MPR_STORE_F16 = 2 } mpr_storage;
+typedef enum { MPR_INIT_BLOCK_MEAN = 0, MPR_INIT_RANDOM = 1 } mpr_init;
+
+typedef struct {
+    int32_t height, width; /* H, W >= 1, each <= 32768 */
+    int32_t block;         /* l_b >= 1 (Sec. 2.2.2 block side) */
+} mpr_grid;
+
+typedef struct {
+    double q;            /* Eq. 1 modification parameter, 0 < q <= 1/2 (default 0.5) */
+    double J;            /* Eq. 1 coupling, J > 0 (default 1) */
+    uint64_t seed;       /* Philox key (seed_lo, seed_hi ^ slice_id) */
+    uint32_t slice_id;   /* distinguishes random streams of independent fields */
+    int32_t n_max;       /* sweep cap per realization (default 200), <= 65535 */
+    int32_t n_eq;        /* calibration: equilibration sweeps per iteration (25) */
+    int32_t n_meas;      /* calibration: measured sweeps per iteration (20) */
+    int32_t n_bisect;    /* calibration: bisection iterations (24), <= 65534 */
+    int32_t cal_chains;  /* calibration: independent chains averaged (1) */
+    float t_lo, t_hi;    /* calibration bracket (1e-4, 2) */
+    int32_t overrelax;   /* 1: Metropolis then over-relaxation per site (default 1) */
+    int32_t init;        /* mpr_init (default MPR_INIT_BLOCK_MEAN, Sec. 3.3.3) */
+    int32_t storage;     /* mpr_storage for the gap angles (default F32) */
+    int32_t group;       /* realizations interleaved per lane group: 0 = auto, 1, 8, 32 */
+    int32_t profile;     /* 1: time every sweep-kernel launch with CUDA events (default 0) */
+    void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
+} mpr_options;
+
+typedef struct {
+    int64_t kernel_launches;        /* kernels this context launched so far */
+    int64_t sim_halfstep_launches;  /* half-step launches made by simulate */
+    int64_t cal_halfstep_launches;  /* half-step launches made by calibrate */
+    double sim_halfstep_ms;         /* summed device time of those launches (profile = 1) */
+    double cal_halfstep_ms;
+} mpr_profile;
+
+typedef struct {
+    int32_t height, width, block, nbx, nby, nblk;
+    int64_t n_gap;              /* |G_P| */
+    int64_t n_gap_colour[2];    /* gap sites per checkerboard colour */
+    double zmin, zmax;          /* Sec. 2.1 transform range (over samples) */
+    int32_t degenerate;         /* 1 if zmax == zmin: predictions are the constant */
+    int32_t calibrated;         /* temperatures set (calibrated or given) */
+    int64_t realizations;       /* realizations accumulated into the mean so far */
+    int32_t batch;              /* realizations in the current step-wise batch */
+    int32_t group;              /* lane-group width in use */
+    int64_t gap_updates;        /* Metropolis+OR site updates run by simulate so far */
+    int64_t cal_gap_updates;    /* site updates run by calibrate so far */
+    int64_t device_bytes;       /* device memory held by the context */
+} mpr_info;
+
+/* Fills *opt with the defaults listed above. */
+void mpr_default_options(mpr_options* opt);
+
+/* Sec. 2.1 transform and Eq. 2 per block (Sec. 2.2.2).
+ * mask: H*W uint8 (host or device), != 0 = gap. values: H*W float (host or
+ * device), read at sample sites only (gap entries may hold anything, NaN
+ * included). Computes z_min/z_max over the samples, the angle of every
+ * sample, each block's sample energy E_s,b over the sample-sample bonds it
+ * owns (a site owns its right and down bond), N_SP,b, N_b and the block's
+ * sample mean angle, and builds the gap-site lists. opt may be NULL
+ * (defaults). On success *out receives a new context.
+ * Errors: EINVAL (sizes, NULL pointers, options), ENOMEM, ECUDA,
+ * ENOSAMPLES (no sample pair on the grid and at least one gap site). */
+mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask, const float* values,
+                      const mpr_options* opt, mpr_ctx** out);
+
+/* Releases every resource of ctx (NULL is a no-op). */
+void mpr_destroy(mpr_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); valid until the next call. */
+const char* mpr_last_error(const mpr_ctx* ctx);
+const char* mpr_status_string(mpr_status s);
+
+mpr_status mpr_get_info(const mpr_ctx* ctx, mpr_info* info);
+
+/* Launch counts and, with mpr_options.profile = 1, the device time of the
+ * half-step kernel measured with CUDA events on the context's stream around
+ * each launch. Synchronises the stream. */
+mpr_status mpr_get_profile(mpr_ctx* ctx, mpr_profile* out);
+
+/* Per-block temperatures by energy matching (Sec. 2.1, applied per block in
+ * Sec. 2.2.2): bisection on T_b in [t_lo, t_hi]; every iteration re-initialises
+ * the gap sites, runs n_eq + n_meas sweeps of cal_chains chains at the current
+ * midpoints and keeps the half of each bracket on the side of e_s,b. Blocks
+ * without sample bonds take the median of the other blocks' temperatures.
+ * block_T_out: NULL or nblk floats (host or device), row-major blocks.
+ * Errors: EINVAL, ECUDA. A degenerate field (z_max == z_min) skips the
+ * iterations and sets every T_b to t_lo. */
+mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out);
+
+/* Sets the block temperatures directly (nblk floats > 0, host or device). */
+mpr_status mpr_set_temperatures(mpr_ctx* ctx, const float* block_T);
+mpr_status mpr_get_temperatures(mpr_ctx* ctx, float* block_T_out);
+
+/* Runs n_realizations more local-equilibrium conditional simulations
+ * (Sec. 2.2.2 block temperatures, Sec. 3.3.3 block-mean start, Sec. 3.4 stop)
+ * and adds their final states to the running mean. Realization indices
+ * continue from earlier calls, so calling it twice with R equals one call
+ * with 2R. Errors: ESTATE (no temperatures yet), EINVAL (n < 1), ENOMEM, ECUDA. */
+mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n_realizations);
+
+/* Conditional mean back-transformed (Sec. 2.1, Sec. 3.2): out[H*W] (host or
+ * device) receives the predictions at gap sites and the input values at
+ * sample sites, bit for bit. truth: NULL or H*W values; when given,
+ * aae_rase[2] (host) receives AAE and RASE over the gap sites (Eqs. 3-4).
+ * Errors: ESTATE (no realization accumulated), EINVAL, ECUDA. */
+mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae_rase);
+
+/* ---- block statistics (Eq. 2 per block), host or device outputs, each nblk long;
+ *      any pointer may be NULL. ---- */
+mpr_status mpr_get_block_stats(mpr_ctx* ctx, double* Es, int32_t* Nsp, int32_t* Nb,
+                               float* mean_angle, int32_t* n_gap);
+
+/* ---- step-wise simulation: the pieces mpr_simulate is made of ----
+ * mpr_sim_begin: allocates a batch of n realizations (indices continue from
+ *   the accumulated count), initialises their gap sites, computes e_b(0) and
+ *   the t = 0 stops. mpr_sim_sweep: runs up to n_sweeps sweeps (colour 0 then
+ *   colour 1 half-step, block energies, stop decisions) and writes the number
+ *   of (block, realization) pairs still running to *n_active (may be NULL).
+ *   mpr_sim_end: adds the batch's states to the running mean. */
+mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n_realizations);
+mpr_status mpr_sim_sweep(mpr_ctx* ctx, int32_t n_sweeps, int64_t* n_active);
+mpr_status mpr_sim_end(mpr_ctx* ctx);
+
+/* One checkerboard half-step (Sec. 2.2.2) of every realization of the batch:
+ * Metropolis (+ over-relaxation) on the gap sites of `colour` whose block is
+ * running, with the random-number tag `tag` (0 = simulation, 1 + k =
+ * calibration iteration k) and sweep index t. No energies, no stop test. */
+mpr_status mpr_halfstep(mpr_ctx* ctx, int32_t colour, int32_t t, int32_t tag);
+
+/* Angles of realization r of the batch as a full H*W float grid (host or
+ * device); sample sites carry their transformed angle. set_state reads gap
+ * sites only. */
+mpr_status mpr_get_state(mpr_ctx* ctx, int32_t r, float* angles);
+mpr_status mpr_set_state(mpr_ctx* ctx, int32_t r, const float* angles);
+
+/* Stop bookkeeping of the batch, [batch][nblk] row-major (host or device):
+ * stop sweep (-1 = running) and running flag (1 = running). Either may be NULL.
+ * set_running overwrites the running flags (1 byte per entry). */
+mpr_status mpr_get_stop(mpr_ctx* ctx, int32_t* stop_sweep, uint8_t* running);
+mpr_status mpr_set_running(mpr_ctx* ctx, const uint8_t* running);
+
+/* Specific energies e_b = E_b / N_b that the stop test last used, [batch][nblk]
+ * doubles (host or device): E_b summed by the sweep kernels (FP32 bond terms,
+ * FP64 block sums) at t = 0 (mpr_sim_begin) and after every sweep in which the
+ * block was running; entries of stopped blocks keep their last value. */
+mpr_status mpr_get_block_e(mpr_ctx* ctx, double* e);
+
+/* Block energies E_b (Eq. 1 over the bonds each block owns) of realization r
+ * of the batch, recomputed from scratch in FP64; nblk doubles (host or device). */
+mpr_status mpr_block_energy(mpr_ctx* ctx, int32_t r, double* E);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPR_H */

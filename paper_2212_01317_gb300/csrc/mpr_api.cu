@@ -1,0 +1,900 @@
+// C-ABI of libmpr (include/mpr.h): context lifetime, device memory, and the
+// order of kernel launches for create / calibrate / simulate / predict.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mpr.h"
+#include "mpr_internal.h"
+#include "mpr_launch.h"
+
+using namespace mpr;
+
+struct mpr_ctx {
+    mpr_options opt{};
+    Geom g{};
+    Model m{};
+    Rng rng{};
+    cudaStream_t s = nullptr;
+    int device = 0, n_sm = 152;
+    std::string err;
+
+    double zmin = 0, zmax = 0;
+    int degenerate = 0;
+    int64_t n_gap[2] = {0, 0};
+    int calibrated = 0;
+
+    std::vector<void*> owned;  // every device allocation, freed at destroy
+    int64_t device_bytes = 0;
+
+    // field
+    float* values = nullptr;
+    uint8_t* mask = nullptr;
+    float* dang = nullptr;
+    float2* dcs = nullptr;
+    uint2* list[2] = {nullptr, nullptr};
+    int32_t* start[2] = {nullptr, nullptr};
+    double* Es = nullptr;
+    int32_t *Nsp = nullptr, *Nb = nullptr, *nsamp = nullptr, *ngap_c[2] = {nullptr, nullptr},
+            *ngap = nullptr;
+    double* ssum = nullptr;
+    float* init_angle = nullptr;
+    float *T = nullptr, *beta = nullptr, *lo = nullptr, *hi = nullptr;
+    double* ebar = nullptr;
+    double* sum = nullptr;  // [2][H][Wh] running sums of gap angles
+    float* out_buf = nullptr;
+    float* truth_buf = nullptr;
+    double* err_buf = nullptr;
+    unsigned long long* counters = nullptr;      // [0] running pairs, [1] site updates
+    unsigned long long* h_counters = nullptr;    // pinned mirror
+    uint32_t* mm = nullptr;
+
+    // batch (step-wise simulation or calibration chains)
+    int G = 1, groups = 0, Rp = 0, R = 0, r_off = 0;
+    uint32_t r_even = 0;
+    int t = 0;
+    int batch_open = 0;
+    float* ang = nullptr;
+    size_t ang_cap = 0;
+    double* eacc = nullptr;
+    uint8_t* running = nullptr;
+    int32_t* stop = nullptr;
+    int8_t* sigma = nullptr;
+    double* e_last = nullptr;
+    int32_t* tcount = nullptr;
+    size_t blk_cap = 0, lane_cap = 0;
+
+    int64_t realizations = 0;
+    int64_t gap_updates = 0, cal_updates = 0;
+
+    // instrumentation
+    int64_t launches = 0;                        // kernels launched by this context
+    std::vector<cudaEvent_t> ev_pool;            // recycled events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_sim, ev_cal;  // pending pairs
+    double sim_halfstep_ms = 0.0, cal_halfstep_ms = 0.0;
+    int64_t sim_halfstep_launches = 0, cal_halfstep_launches = 0;
+};
+
+namespace {
+
+mpr_status fail(mpr_ctx* c, mpr_status st, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MPR_ENOMEM : MPR_ECUDA,        \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,     \
+                        __LINE__);                                                            \
+    } while (0)
+
+#define CKL()                                                                                 \
+    do {                                                                                      \
+        ++ctx->launches;                                                                      \
+        cudaError_t e_ = cudaPeekAtLastError();                                               \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, MPR_ECUDA, "kernel launch failed: %s (%s:%d)",                   \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                          \
+    } while (0)
+
+#define TRY(expr)                                    \
+    do {                                             \
+        mpr_status st_ = (expr);                     \
+        if (st_ != MPR_OK) return st_;               \
+    } while (0)
+
+template <class T>
+mpr_status dalloc(mpr_ctx* ctx, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, MPR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    ctx->owned.push_back(q);
+    ctx->device_bytes += (int64_t)(count * sizeof(T));
+    *p = static_cast<T*>(q);
+    return MPR_OK;
+}
+
+void dfree(mpr_ctx* ctx, void* p) {
+    if (!p) return;
+    auto it = std::find(ctx->owned.begin(), ctx->owned.end(), p);
+    if (it != ctx->owned.end()) ctx->owned.erase(it);
+    cudaFree(p);
+}
+
+int pick_group(int lanes, int requested) {
+    if (requested == 1 || requested == 8 || requested == 32) return requested;
+    if (lanes <= 1) return 1;
+    const int p8 = (lanes + 7) / 8 * 8, p32 = (lanes + 31) / 32 * 32;
+    return p32 <= p8 ? 32 : 8;
+}
+
+mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
+    if (!(o.q > 0.0 && o.q <= 0.5)) return fail(ctx, MPR_EINVAL, "q must be in (0, 1/2]");
+    if (!(o.J > 0.0)) return fail(ctx, MPR_EINVAL, "J must be > 0");
+    if (o.n_max < 1 || o.n_max > 65535) return fail(ctx, MPR_EINVAL, "n_max must be in [1, 65535]");
+    if (o.n_eq < 0 || o.n_meas < 1 || o.n_eq + o.n_meas > 65535)
+        return fail(ctx, MPR_EINVAL, "n_eq >= 0, n_meas >= 1, n_eq + n_meas <= 65535");
+    if (o.n_bisect < 0 || o.n_bisect > 65534) return fail(ctx, MPR_EINVAL, "n_bisect in [0, 65534]");
+    if (o.cal_chains < 1 || o.cal_chains > 4096) return fail(ctx, MPR_EINVAL, "cal_chains in [1, 4096]");
+    if (!(o.t_lo > 0.0f && o.t_hi > o.t_lo)) return fail(ctx, MPR_EINVAL, "need 0 < t_lo < t_hi");
+    if (o.storage != MPR_STORE_F32)
+        return fail(ctx, MPR_EINVAL, "storage %d not supported by this build", o.storage);
+    if (o.group != 0 && o.group != 1 && o.group != 8 && o.group != 32)
+        return fail(ctx, MPR_EINVAL, "group must be 0, 1, 8 or 32");
+    if (o.init != MPR_INIT_BLOCK_MEAN && o.init != MPR_INIT_RANDOM)
+        return fail(ctx, MPR_EINVAL, "unknown init mode");
+    return MPR_OK;
+}
+
+// Copies n bytes from a host or device pointer into device memory on the stream.
+mpr_status copy_in(mpr_ctx* ctx, void* dst, const void* src, size_t n) {
+    CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, ctx->s));
+    return MPR_OK;
+}
+
+mpr_status copy_out(mpr_ctx* ctx, void* dst, const void* src, size_t n) {
+    CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return MPR_OK;
+}
+
+// Per-batch buffers sized for `lanes` realization lanes.
+mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group) {
+    const Geom& g = ctx->g;
+    const int G = pick_group(lanes, requested_group);
+    const int groups = (lanes + G - 1) / G;
+    const int Rp = groups * G;
+    const size_t ang_need = (size_t)groups * 2 * g.H * g.Wh * G;
+    if (ang_need > ctx->ang_cap) {
+        dfree(ctx, ctx->ang);
+        ctx->ang = nullptr;
+        ctx->ang_cap = 0;
+        TRY(dalloc(ctx, &ctx->ang, ang_need));
+        ctx->ang_cap = ang_need;
+    }
+    const size_t blk_need = (size_t)g.nblk * Rp;
+    if (blk_need > ctx->blk_cap) {
+        for (void* p : {(void*)ctx->eacc, (void*)ctx->running, (void*)ctx->stop, (void*)ctx->sigma,
+                        (void*)ctx->e_last})
+            dfree(ctx, p);
+        ctx->eacc = nullptr; ctx->running = nullptr; ctx->stop = nullptr; ctx->sigma = nullptr;
+        ctx->e_last = nullptr;
+        ctx->blk_cap = 0;
+        TRY(dalloc(ctx, &ctx->eacc, blk_need));
+        TRY(dalloc(ctx, &ctx->e_last, blk_need));
+        TRY(dalloc(ctx, &ctx->running, blk_need));
+        TRY(dalloc(ctx, &ctx->stop, blk_need));
+        TRY(dalloc(ctx, &ctx->sigma, blk_need));
+        ctx->blk_cap = blk_need;
+    }
+    if ((size_t)Rp > ctx->lane_cap) {
+        dfree(ctx, ctx->tcount);
+        ctx->tcount = nullptr;
+        ctx->lane_cap = 0;
+        TRY(dalloc(ctx, &ctx->tcount, (size_t)Rp));
+        ctx->lane_cap = Rp;
+    }
+    ctx->G = G;
+    ctx->groups = groups;
+    ctx->Rp = Rp;
+    CK(cudaMemsetAsync(ctx->eacc, 0, blk_need * sizeof(double), ctx->s));
+    return MPR_OK;
+}
+
+SweepArgs sweep_args(mpr_ctx* ctx, int colour, uint32_t t, uint32_t tag, int update, int energy,
+                     bool use_running) {
+    SweepArgs a{};
+    a.g = ctx->g;
+    a.m = ctx->m;
+    a.rng = ctx->rng;
+    a.colour = colour;
+    a.list = ctx->list[colour];
+    a.start = ctx->start[colour];
+    a.ang = ctx->ang;
+    a.dcs = ctx->dcs;
+    a.beta = ctx->beta;
+    a.running = use_running ? ctx->running : nullptr;
+    a.eacc = ctx->eacc;
+    a.R = ctx->R;
+    a.Rp = ctx->Rp;
+    a.groups = ctx->groups;
+    a.r_base = ctx->r_even;
+    a.t = t;
+    a.tag = tag;
+    a.update = update;
+    a.energy = energy;
+    return a;
+}
+
+cudaEvent_t get_event(mpr_ctx* ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Launches one half-step; with profiling on, brackets it with events on the
+// context's stream (summed when the stream is next synchronised).
+mpr_status halfstep_launch(mpr_ctx* ctx, const SweepArgs& a, bool sim) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->opt.profile) {
+        e0 = get_event(ctx);
+        e1 = get_event(ctx);
+        if (e0) cudaEventRecord(e0, ctx->s);
+    }
+    launch_halfstep(a, ctx->G, ctx->n_sm, ctx->s);
+    CKL();
+    if (e0 && e1) {
+        cudaEventRecord(e1, ctx->s);
+        (sim ? ctx->ev_sim : ctx->ev_cal).emplace_back(e0, e1);
+    }
+    if (sim) ++ctx->sim_halfstep_launches; else ++ctx->cal_halfstep_launches;
+    return MPR_OK;
+}
+
+// After a stream synchronisation: fold the recorded pairs into the totals.
+void collect_events(mpr_ctx* ctx) {
+    for (int which = 0; which < 2; ++which) {
+        auto& v = which ? ctx->ev_cal : ctx->ev_sim;
+        double& acc = which ? ctx->cal_halfstep_ms : ctx->sim_halfstep_ms;
+        for (auto& pr : v) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) acc += ms;
+            else cudaGetLastError();
+            ctx->ev_pool.push_back(pr.first);
+            ctx->ev_pool.push_back(pr.second);
+        }
+        v.clear();
+    }
+}
+
+mpr_status init_batch_state(mpr_ctx* ctx) {
+    const int random = ctx->opt.init == MPR_INIT_RANDOM;
+    for (int c = 0; c < 2; ++c) {
+        launch_init(ctx->g, ctx->list[c], ctx->n_gap[c], c, ctx->init_angle, ctx->ang, ctx->G,
+                    ctx->Rp, random, ctx->rng, ctx->r_even, ctx->s);
+        CKL();
+    }
+    return MPR_OK;
+}
+
+__global__ void k_fill_valid(uint8_t* running, int64_t n, int Rp, int r_off, int R) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t % Rp);
+        running[t] = (r >= r_off && r < r_off + R) ? 1 : 0;
+    }
+}
+
+mpr_status sweep_once(mpr_ctx* ctx) {
+    ctx->t += 1;
+    const uint32_t t = (uint32_t)ctx->t;
+    for (int c = 0; c < 2; ++c) TRY(halfstep_launch(ctx, sweep_args(ctx, c, t, 0u, 1, 1, true), true));
+    launch_stop_targeted(ctx->g.nblk, ctx->Rp, ctx->t, ctx->Es, ctx->Nsp, ctx->Nb, ctx->eacc,
+                         ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
+    CKL();
+    launch_stop_rest(ctx->g.nblk, ctx->Rp, ctx->t, ctx->opt.n_max, ctx->Nsp, ctx->running,
+                     ctx->stop, ctx->tcount, &ctx->counters[0], ctx->s);
+    CKL();
+    return MPR_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ public --
+extern "C" {
+
+void mpr_default_options(mpr_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->q = 0.5;
+    o->J = 1.0;
+    o->seed = 0;
+    o->slice_id = 0;
+    o->n_max = 200;
+    o->n_eq = 25;
+    o->n_meas = 20;
+    o->n_bisect = 24;
+    o->cal_chains = 1;
+    o->t_lo = 1e-4f;
+    o->t_hi = 2.0f;
+    o->overrelax = 1;
+    o->init = MPR_INIT_BLOCK_MEAN;
+    o->storage = MPR_STORE_F32;
+    o->group = 0;
+    o->profile = 0;
+    o->cuda_stream = nullptr;
+}
+
+const char* mpr_status_string(mpr_status s) {
+    switch (s) {
+        case MPR_OK: return "ok";
+        case MPR_EINVAL: return "invalid argument";
+        case MPR_ENOMEM: return "out of memory";
+        case MPR_ECUDA: return "CUDA error";
+        case MPR_ENOSAMPLES: return "no sample pair";
+        case MPR_ETIMEOUT: return "device wait timed out";
+        case MPR_ESTATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* mpr_last_error(const mpr_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+void mpr_destroy(mpr_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->s);
+    for (auto& pr : ctx->ev_sim) ctx->ev_pool.insert(ctx->ev_pool.end(), {pr.first, pr.second});
+    for (auto& pr : ctx->ev_cal) ctx->ev_pool.insert(ctx->ev_pool.end(), {pr.first, pr.second});
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (void* p : ctx->owned) cudaFree(p);
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    delete ctx;
+}
+
+mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float* values_in,
+                      const mpr_options* opt_in, mpr_ctx** out) {
+    if (!out) return MPR_EINVAL;
+    *out = nullptr;
+    if (!grid || !mask_in || !values_in) return MPR_EINVAL;
+    mpr_ctx* ctx = new (std::nothrow) mpr_ctx();
+    if (!ctx) return MPR_ENOMEM;
+    auto bail = [&](mpr_status st) {
+        // Keep the context only for its error message when the caller asked
+        // for nothing else; otherwise release it.
+        mpr_destroy(ctx);
+        return st;
+    };
+    if (opt_in) ctx->opt = *opt_in; else mpr_default_options(&ctx->opt);
+    if (check_opts(ctx, ctx->opt) != MPR_OK) return bail(MPR_EINVAL);
+    const int H = grid->height, W = grid->width, lb = grid->block;
+    if (H < 1 || W < 1 || H > MAX_SIDE || W > MAX_SIDE || lb < 1) return bail(MPR_EINVAL);
+    Geom& g = ctx->g;
+    g.H = H;
+    g.W = W;
+    g.Wh = (W + 1) / 2;
+    g.lb = lb;
+    g.nbx = (W + lb - 1) / lb;
+    g.nby = (H + lb - 1) / lb;
+    if ((int64_t)g.nbx * g.nby > MAX_BLOCKS) return bail(MPR_EINVAL);
+    g.nblk = g.nbx * g.nby;
+    ctx->m.q = (float)ctx->opt.q;
+    ctx->m.J = (float)ctx->opt.J;
+    ctx->m.inv_q = (float)(1.0 / ctx->opt.q);
+    ctx->m.overrelax = ctx->opt.overrelax ? 1 : 0;
+    ctx->rng.key0 = (uint32_t)(ctx->opt.seed & 0xffffffffu);
+    ctx->rng.key1 = (uint32_t)(ctx->opt.seed >> 32) ^ ctx->opt.slice_id;
+    ctx->s = (cudaStream_t)ctx->opt.cuda_stream;
+
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(MPR_ECUDA);
+    cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (ctx->n_sm < 1) ctx->n_sm = 1;
+
+    const int64_t n = (int64_t)H * W;
+    const size_t plane = (size_t)H * g.Wh;
+    mpr_status st;
+#define ST(x) do { st = (x); if (st != MPR_OK) return bail(st); } while (0)
+    ST(dalloc(ctx, &ctx->values, n));
+    ST(dalloc(ctx, &ctx->mask, n));
+    ST(dalloc(ctx, &ctx->dang, 2 * plane));
+    ST(dalloc(ctx, &ctx->dcs, 2 * plane));
+    ST(dalloc(ctx, &ctx->sum, 2 * plane));
+    ST(dalloc(ctx, &ctx->Es, g.nblk));
+    ST(dalloc(ctx, &ctx->Nsp, g.nblk));
+    ST(dalloc(ctx, &ctx->Nb, g.nblk));
+    ST(dalloc(ctx, &ctx->nsamp, g.nblk));
+    ST(dalloc(ctx, &ctx->ngap_c[0], g.nblk));
+    ST(dalloc(ctx, &ctx->ngap_c[1], g.nblk));
+    ST(dalloc(ctx, &ctx->ngap, g.nblk));
+    ST(dalloc(ctx, &ctx->ssum, g.nblk));
+    ST(dalloc(ctx, &ctx->init_angle, g.nblk));
+    ST(dalloc(ctx, &ctx->T, g.nblk));
+    ST(dalloc(ctx, &ctx->beta, g.nblk));
+    ST(dalloc(ctx, &ctx->lo, g.nblk));
+    ST(dalloc(ctx, &ctx->hi, g.nblk));
+    ST(dalloc(ctx, &ctx->ebar, g.nblk));
+    ST(dalloc(ctx, &ctx->start[0], g.nblk + 1));
+    ST(dalloc(ctx, &ctx->start[1], g.nblk + 1));
+    ST(dalloc(ctx, &ctx->counters, 4));
+    ST(dalloc(ctx, &ctx->mm, 2));
+    ST(dalloc(ctx, &ctx->err_buf, 2));
+    if (cudaMallocHost(&ctx->h_counters, 4 * sizeof(unsigned long long)) != cudaSuccess)
+        return bail(MPR_ENOMEM);
+
+    if (copy_in(ctx, ctx->values, values_in, n * sizeof(float)) != MPR_OK) return bail(MPR_ECUDA);
+    if (copy_in(ctx, ctx->mask, mask_in, n) != MPR_OK) return bail(MPR_ECUDA);
+    // z_min / z_max over the samples.
+    {
+        uint32_t mm_init[2] = {0xffffffffu, 0u};
+        if (cudaMemcpyAsync(ctx->mm, mm_init, sizeof(mm_init), cudaMemcpyHostToDevice, ctx->s) !=
+            cudaSuccess)
+            return bail(MPR_ECUDA);
+        launch_minmax(ctx->values, ctx->mask, n, ctx->mm, ctx->s);
+        ++ctx->launches;
+        uint32_t hmm[2];
+        if (cudaMemcpyAsync(hmm, ctx->mm, sizeof(hmm), cudaMemcpyDeviceToHost, ctx->s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(ctx->s) != cudaSuccess)
+            return bail(MPR_ECUDA);
+        if (hmm[0] == 0xffffffffu) {
+            // no sample at all
+            ctx->zmin = ctx->zmax = 0.0;
+            ctx->degenerate = 1;
+        } else {
+            ctx->zmin = (double)ord2f(hmm[0]);
+            ctx->zmax = (double)ord2f(hmm[1]);
+            ctx->degenerate = !(ctx->zmax > ctx->zmin);
+        }
+    }
+    launch_layout(g, ctx->values, ctx->mask, ctx->zmin, ctx->zmax, ctx->degenerate, ctx->m.q,
+                  ctx->dang, ctx->dcs, ctx->s);
+    launch_block_stats(g, ctx->values, ctx->mask, ctx->zmin, ctx->zmax, ctx->degenerate,
+                       ctx->opt.q, ctx->opt.J, ctx->Es, ctx->Nsp, ctx->Nb, ctx->ssum, ctx->nsamp,
+                       ctx->ngap_c[0], ctx->ngap_c[1], ctx->s);
+    launch_scan(ctx->ngap_c[0], g.nblk, ctx->start[0], ctx->s);
+    launch_scan(ctx->ngap_c[1], g.nblk, ctx->start[1], ctx->s);
+    ctx->launches += 4;
+    if (cudaPeekAtLastError() != cudaSuccess) return bail(MPR_ECUDA);
+
+    // Host-side bookkeeping: list sizes, initial angles, sample-pair check.
+    std::vector<int32_t> s0(g.nblk + 1), s1(g.nblk + 1), nsp(g.nblk), nsm(g.nblk), ng0(g.nblk),
+        ng1(g.nblk);
+    std::vector<double> ssum(g.nblk);
+    if (cudaMemcpyAsync(s0.data(), ctx->start[0], s0.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaMemcpyAsync(s1.data(), ctx->start[1], s1.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaMemcpyAsync(nsp.data(), ctx->Nsp, nsp.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaMemcpyAsync(nsm.data(), ctx->nsamp, nsm.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaMemcpyAsync(ng0.data(), ctx->ngap_c[0], ng0.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaMemcpyAsync(ng1.data(), ctx->ngap_c[1], ng1.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaMemcpyAsync(ssum.data(), ctx->ssum, ssum.size() * 8, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaStreamSynchronize(ctx->s))
+        return bail(MPR_ECUDA);
+    ctx->n_gap[0] = s0[g.nblk];
+    ctx->n_gap[1] = s1[g.nblk];
+    int64_t pairs = 0, samples = 0;
+    double gsum = 0.0;
+    std::vector<float> init(g.nblk);
+    std::vector<int32_t> ng(g.nblk);
+    for (int b = 0; b < g.nblk; ++b) {
+        pairs += nsp[b];
+        samples += nsm[b];
+        gsum += ssum[b];
+        ng[b] = ng0[b] + ng1[b];
+    }
+    const double gmean = samples ? gsum / (double)samples : 0.0;
+    for (int b = 0; b < g.nblk; ++b)
+        init[b] = (float)(nsm[b] > 0 ? ssum[b] / (double)nsm[b] : gmean);
+    if (pairs == 0 && ctx->n_gap[0] + ctx->n_gap[1] > 0) {
+        mpr_destroy(ctx);
+        return MPR_ENOSAMPLES;
+    }
+    ST(dalloc(ctx, &ctx->list[0], ctx->n_gap[0]));
+    ST(dalloc(ctx, &ctx->list[1], ctx->n_gap[1]));
+    if (cudaMemcpyAsync(ctx->init_angle, init.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s) ||
+        cudaMemcpyAsync(ctx->ngap, ng.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s))
+        return bail(MPR_ECUDA);
+    launch_build_lists(g, ctx->mask, ctx->start[0], ctx->start[1], ctx->list[0], ctx->list[1],
+                       ctx->s);
+    ++ctx->launches;
+    if (cudaMemsetAsync(ctx->sum, 0, 2 * plane * sizeof(double), ctx->s) ||
+        cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), ctx->s) ||
+        cudaPeekAtLastError() || cudaStreamSynchronize(ctx->s))
+        return bail(MPR_ECUDA);
+#undef ST
+    *out = ctx;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_info(const mpr_ctx* ctx, mpr_info* info) {
+    if (!ctx || !info) return MPR_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->height = ctx->g.H;
+    info->width = ctx->g.W;
+    info->block = ctx->g.lb;
+    info->nbx = ctx->g.nbx;
+    info->nby = ctx->g.nby;
+    info->nblk = ctx->g.nblk;
+    info->n_gap = ctx->n_gap[0] + ctx->n_gap[1];
+    info->n_gap_colour[0] = ctx->n_gap[0];
+    info->n_gap_colour[1] = ctx->n_gap[1];
+    info->zmin = ctx->zmin;
+    info->zmax = ctx->zmax;
+    info->degenerate = ctx->degenerate;
+    info->calibrated = ctx->calibrated;
+    info->realizations = ctx->realizations;
+    info->batch = ctx->batch_open ? ctx->R : 0;
+    info->group = ctx->G;
+    info->gap_updates = ctx->gap_updates;
+    info->cal_gap_updates = ctx->cal_updates;
+    info->device_bytes = ctx->device_bytes;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_profile(mpr_ctx* ctx, mpr_profile* p) {
+    if (!ctx || !p) return MPR_EINVAL;
+    ctx->err.clear();
+    CK(cudaStreamSynchronize(ctx->s));
+    collect_events(ctx);
+    std::memset(p, 0, sizeof(*p));
+    p->kernel_launches = ctx->launches;
+    p->sim_halfstep_launches = ctx->sim_halfstep_launches;
+    p->cal_halfstep_launches = ctx->cal_halfstep_launches;
+    p->sim_halfstep_ms = ctx->sim_halfstep_ms;
+    p->cal_halfstep_ms = ctx->cal_halfstep_ms;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_block_stats(mpr_ctx* ctx, double* Es, int32_t* Nsp, int32_t* Nb,
+                               float* mean_angle, int32_t* n_gap) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    const size_t nb = ctx->g.nblk;
+    if (Es) TRY(copy_out(ctx, Es, ctx->Es, nb * 8));
+    if (Nsp) TRY(copy_out(ctx, Nsp, ctx->Nsp, nb * 4));
+    if (Nb) TRY(copy_out(ctx, Nb, ctx->Nb, nb * 4));
+    if (mean_angle) TRY(copy_out(ctx, mean_angle, ctx->init_angle, nb * 4));
+    if (n_gap) TRY(copy_out(ctx, n_gap, ctx->ngap, nb * 4));
+    return MPR_OK;
+}
+
+mpr_status mpr_set_temperatures(mpr_ctx* ctx, const float* T) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!T) return fail(ctx, MPR_EINVAL, "T is NULL");
+    std::vector<float> h(ctx->g.nblk), bt(ctx->g.nblk);
+    CK(cudaMemcpyAsync(h.data(), T, h.size() * 4, cudaMemcpyDefault, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (int b = 0; b < ctx->g.nblk; ++b) {
+        if (!(h[b] > 0.0f) || !std::isfinite(h[b]))
+            return fail(ctx, MPR_EINVAL, "temperature of block %d is not a positive number", b);
+        bt[b] = 1.0f / h[b];
+    }
+    CK(cudaMemcpyAsync(ctx->T, h.data(), h.size() * 4, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(ctx->beta, bt.data(), bt.size() * 4, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->calibrated = 1;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_temperatures(mpr_ctx* ctx, float* T) {
+    if (!ctx || !T) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->calibrated) return fail(ctx, MPR_ESTATE, "no temperatures yet");
+    return copy_out(ctx, T, ctx->T, (size_t)ctx->g.nblk * 4);
+}
+
+mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    const Geom& g = ctx->g;
+    const mpr_options& o = ctx->opt;
+    ctx->batch_open = 0;
+    if (ctx->degenerate) {
+        std::vector<float> h(g.nblk, o.t_lo);
+        CK(cudaMemcpyAsync(ctx->T, h.data(), h.size() * 4, cudaMemcpyHostToDevice, ctx->s));
+        for (auto& v : h) v = 1.0f / o.t_lo;
+        CK(cudaMemcpyAsync(ctx->beta, h.data(), h.size() * 4, cudaMemcpyHostToDevice, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        ctx->calibrated = 1;
+        if (block_T_out) return copy_out(ctx, block_T_out, ctx->T, (size_t)g.nblk * 4);
+        return MPR_OK;
+    }
+    const int chains = o.cal_chains;
+    TRY(ensure_batch(ctx, chains, o.group));
+    ctx->R = chains;
+    ctx->r_off = 0;
+    ctx->r_even = 0;
+    launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->s);
+    CKL();
+    const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);
+    for (int k = 0; k < o.n_bisect; ++k) {
+        launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->s);
+        launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+        CKL();
+        TRY(init_batch_state(ctx));
+        const uint32_t tag = (uint32_t)(1 + k);
+        for (int sw = 1; sw <= o.n_eq + o.n_meas; ++sw) {
+            const int measure = sw > o.n_eq;
+            for (int c = 0; c < 2; ++c)
+                TRY(halfstep_launch(ctx, sweep_args(ctx, c, (uint32_t)sw, tag, 1, measure, false),
+                                    false));
+            if (measure) {
+                launch_cal_measure(g.nblk, ctx->Rp, chains, ctx->Es, ctx->Nb, ctx->eacc,
+                                   ctx->ebar, ctx->s);
+                CKL();
+            }
+        }
+        launch_cal_update(g.nblk, inv_count, ctx->Es, ctx->Nsp, ctx->T, ctx->lo, ctx->hi,
+                          ctx->ebar, nullptr, ctx->s);
+        CKL();
+    }
+    launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->s);
+    launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+    CKL();
+    ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains *
+                        (ctx->n_gap[0] + ctx->n_gap[1]);
+    ctx->calibrated = 1;
+    if (block_T_out) TRY(copy_out(ctx, block_T_out, ctx->T, (size_t)g.nblk * 4));
+    CK(cudaStreamSynchronize(ctx->s));
+    collect_events(ctx);
+    return MPR_OK;
+}
+
+mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (n < 1) return fail(ctx, MPR_EINVAL, "n_realizations must be >= 1");
+    if (!ctx->calibrated) return fail(ctx, MPR_ESTATE, "calibrate or set temperatures first");
+    const int64_t r_base = ctx->realizations;
+    if (r_base + n > (int64_t)0x1FFFFFFFF) return fail(ctx, MPR_EINVAL, "realization index overflow");
+    ctx->r_off = (int)(r_base & 1);
+    ctx->r_even = (uint32_t)(r_base - ctx->r_off);
+    TRY(ensure_batch(ctx, n + ctx->r_off, ctx->opt.group));
+    ctx->R = n;
+    ctx->t = 0;
+    const int64_t nbr = (int64_t)ctx->g.nblk * ctx->Rp;
+    k_fill_valid<<<(int)std::min<int64_t>((nbr + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
+        ctx->running, nbr, ctx->Rp, ctx->r_off, ctx->R);
+    CKL();
+    TRY(init_batch_state(ctx));
+    CK(cudaMemsetAsync(ctx->tcount, 0, ctx->Rp * sizeof(int32_t), ctx->s));
+    // E_b(0): bond energies of the initial state (no moves).
+    for (int c = 0; c < 2; ++c) {
+        launch_halfstep(sweep_args(ctx, c, 0u, 0u, 0, 1, true), ctx->G, ctx->n_sm, ctx->s);
+        CKL();
+    }
+    launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->R, ctx->r_off, ctx->Es, ctx->Nsp, ctx->Nb, ctx->ngap,
+                     ctx->eacc, ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last,
+                     ctx->s);
+    CKL();
+    CK(cudaMemsetAsync(&ctx->counters[0], 0, sizeof(unsigned long long), ctx->s));
+    launch_stop_rest(ctx->g.nblk, ctx->Rp, 0, ctx->opt.n_max, ctx->Nsp, ctx->running, ctx->stop,
+                     ctx->tcount, &ctx->counters[0], ctx->s);
+    CKL();
+    ctx->batch_open = 1;
+    return MPR_OK;
+}
+
+mpr_status mpr_sim_sweep(mpr_ctx* ctx, int32_t n_sweeps, int64_t* n_active) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch (mpr_sim_begin)");
+    for (int i = 0; i < n_sweeps && ctx->t < ctx->opt.n_max; ++i) {
+        CK(cudaMemsetAsync(&ctx->counters[0], 0, sizeof(unsigned long long), ctx->s));
+        TRY(sweep_once(ctx));
+    }
+    if (n_active) {
+        CK(cudaMemcpyAsync(ctx->h_counters, ctx->counters, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        *n_active = (int64_t)ctx->h_counters[0];
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_sim_end(mpr_ctx* ctx) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch (mpr_sim_begin)");
+    for (int c = 0; c < 2; ++c) {
+        launch_accumulate(ctx->g, ctx->list[c], ctx->n_gap[c], c, ctx->ang, ctx->G, ctx->groups,
+                          ctx->r_off, ctx->R, ctx->sum, ctx->s);
+        CKL();
+    }
+    CK(cudaMemsetAsync(&ctx->counters[1], 0, sizeof(unsigned long long), ctx->s));
+    launch_count_updates(ctx->g.nblk, ctx->Rp, ctx->stop, ctx->ngap, &ctx->counters[1], ctx->s);
+    CKL();
+    CK(cudaMemcpyAsync(ctx->h_counters + 1, ctx->counters + 1, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    collect_events(ctx);
+    ctx->gap_updates += (int64_t)ctx->h_counters[1];
+    ctx->realizations += ctx->R;
+    ctx->batch_open = 0;
+    return MPR_OK;
+}
+
+mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
+    if (!ctx) return MPR_EINVAL;
+    TRY(mpr_sim_begin(ctx, n));
+    const int chunk = 8;
+    while (ctx->t < ctx->opt.n_max) {
+        int64_t left = 0;
+        TRY(mpr_sim_sweep(ctx, chunk, &left));
+        if (left == 0) break;
+    }
+    return mpr_sim_end(ctx);
+}
+
+mpr_status mpr_halfstep(mpr_ctx* ctx, int32_t colour, int32_t t, int32_t tag) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch (mpr_sim_begin)");
+    if (colour != 0 && colour != 1) return fail(ctx, MPR_EINVAL, "colour must be 0 or 1");
+    if (t < 0 || t > 65535 || tag < 0 || tag > 65535)
+        return fail(ctx, MPR_EINVAL, "t and tag must be in [0, 65535]");
+    launch_halfstep(sweep_args(ctx, colour, (uint32_t)t, (uint32_t)tag, 1, 0, true), ctx->G,
+                    ctx->n_sm, ctx->s);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->s));
+    return MPR_OK;
+}
+
+mpr_status mpr_get_state(mpr_ctx* ctx, int32_t r, float* angles) {
+    if (!ctx || !angles) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch");
+    if (r < 0 || r >= ctx->R) return fail(ctx, MPR_EINVAL, "r out of range");
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
+    if (!ctx->out_buf) TRY(dalloc(ctx, &ctx->out_buf, n));
+    launch_get_state(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->G, r + ctx->r_off, ctx->out_buf,
+                     ctx->s);
+    CKL();
+    return copy_out(ctx, angles, ctx->out_buf, n * 4);
+}
+
+mpr_status mpr_set_state(mpr_ctx* ctx, int32_t r, const float* angles) {
+    if (!ctx || !angles) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch");
+    if (r < 0 || r >= ctx->R) return fail(ctx, MPR_EINVAL, "r out of range");
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
+    if (!ctx->truth_buf) TRY(dalloc(ctx, &ctx->truth_buf, n));
+    TRY(copy_in(ctx, ctx->truth_buf, angles, n * 4));
+    launch_set_state(ctx->g, ctx->mask, ctx->ang, ctx->G, r + ctx->r_off, ctx->truth_buf, ctx->s);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->s));
+    return MPR_OK;
+}
+
+mpr_status mpr_get_stop(mpr_ctx* ctx, int32_t* stop_sweep, uint8_t* running) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch");
+    const int nb = ctx->g.nblk;
+    std::vector<int32_t> hs((size_t)nb * ctx->Rp);
+    std::vector<uint8_t> hr((size_t)nb * ctx->Rp);
+    CK(cudaMemcpyAsync(hs.data(), ctx->stop, hs.size() * 4, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(hr.data(), ctx->running, hr.size(), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    std::vector<int32_t> os((size_t)ctx->R * nb);
+    std::vector<uint8_t> orr((size_t)ctx->R * nb);
+    for (int r = 0; r < ctx->R; ++r)
+        for (int b = 0; b < nb; ++b) {
+            os[(size_t)r * nb + b] = hs[(size_t)b * ctx->Rp + r + ctx->r_off];
+            orr[(size_t)r * nb + b] = hr[(size_t)b * ctx->Rp + r + ctx->r_off];
+        }
+    if (stop_sweep)
+        CK(cudaMemcpyAsync(stop_sweep, os.data(), os.size() * 4, cudaMemcpyDefault, ctx->s));
+    if (running) CK(cudaMemcpyAsync(running, orr.data(), orr.size(), cudaMemcpyDefault, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return MPR_OK;
+}
+
+mpr_status mpr_get_block_e(mpr_ctx* ctx, double* e) {
+    if (!ctx || !e) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch");
+    const int nb = ctx->g.nblk;
+    std::vector<double> h((size_t)nb * ctx->Rp), o((size_t)ctx->R * nb);
+    CK(cudaMemcpyAsync(h.data(), ctx->e_last, h.size() * 8, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (int r = 0; r < ctx->R; ++r)
+        for (int b = 0; b < nb; ++b) o[(size_t)r * nb + b] = h[(size_t)b * ctx->Rp + r + ctx->r_off];
+    CK(cudaMemcpyAsync(e, o.data(), o.size() * 8, cudaMemcpyDefault, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return MPR_OK;
+}
+
+mpr_status mpr_set_running(mpr_ctx* ctx, const uint8_t* running) {
+    if (!ctx || !running) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch");
+    const int nb = ctx->g.nblk;
+    std::vector<uint8_t> in((size_t)ctx->R * nb), hr((size_t)nb * ctx->Rp, 0);
+    CK(cudaMemcpyAsync(in.data(), running, in.size(), cudaMemcpyDefault, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (int r = 0; r < ctx->R; ++r)
+        for (int b = 0; b < nb; ++b)
+            hr[(size_t)b * ctx->Rp + r + ctx->r_off] = in[(size_t)r * nb + b] ? 1 : 0;
+    CK(cudaMemcpyAsync(ctx->running, hr.data(), hr.size(), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return MPR_OK;
+}
+
+mpr_status mpr_block_energy(mpr_ctx* ctx, int32_t r, double* E) {
+    if (!ctx || !E) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch");
+    if (r < 0 || r >= ctx->R) return fail(ctx, MPR_EINVAL, "r out of range");
+    double* d = nullptr;
+    TRY(dalloc(ctx, &d, ctx->g.nblk));
+    launch_block_energy(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->G, r + ctx->r_off, ctx->opt.q,
+                        ctx->opt.J, d, ctx->s);
+    mpr_status st = MPR_OK;
+    if (cudaPeekAtLastError() != cudaSuccess) st = fail(ctx, MPR_ECUDA, "block energy launch failed");
+    if (st == MPR_OK) st = copy_out(ctx, E, d, (size_t)ctx->g.nblk * 8);
+    dfree(ctx, d);
+    ctx->device_bytes -= (int64_t)ctx->g.nblk * 8;
+    return st;
+}
+
+mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae_rase) {
+    if (!ctx || !out) return MPR_EINVAL;
+    ctx->err.clear();
+    const int64_t total_gap = ctx->n_gap[0] + ctx->n_gap[1];
+    if (ctx->realizations == 0 && total_gap > 0)
+        return fail(ctx, MPR_ESTATE, "no realization accumulated (mpr_simulate)");
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
+    if (!ctx->out_buf) TRY(dalloc(ctx, &ctx->out_buf, n));
+    const float* tr = nullptr;
+    if (truth) {
+        if (!ctx->truth_buf) TRY(dalloc(ctx, &ctx->truth_buf, n));
+        TRY(copy_in(ctx, ctx->truth_buf, truth, n * 4));
+        tr = ctx->truth_buf;
+        CK(cudaMemsetAsync(ctx->err_buf, 0, 2 * sizeof(double), ctx->s));
+    }
+    const double inv_r = ctx->realizations > 0 ? 1.0 / (double)ctx->realizations : 0.0;
+    launch_predict(ctx->g, ctx->values, ctx->mask, ctx->sum, inv_r, ctx->zmin, ctx->zmax,
+                   ctx->out_buf, tr, ctx->err_buf, ctx->s);
+    CKL();
+    TRY(copy_out(ctx, out, ctx->out_buf, n * 4));
+    if (truth && aae_rase) {
+        double h[2];
+        TRY(copy_out(ctx, h, ctx->err_buf, sizeof(h)));
+        aae_rase[0] = total_gap ? h[0] / (double)total_gap : 0.0;
+        aae_rase[1] = total_gap ? std::sqrt(h[1] / (double)total_gap) : 0.0;
+    }
+    return MPR_OK;
+}
+
+}  // extern "C"

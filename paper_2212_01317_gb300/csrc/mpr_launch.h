@@ -1,0 +1,63 @@
+// Host-side launchers of the kernels in mpr_kernels.cu (stream-ordered, no sync).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mpr_internal.h"
+
+namespace mpr {
+
+float ord2f(uint32_t u);
+
+void launch_minmax(const float* values, const uint8_t* mask, int64_t n, uint32_t* mm,
+                   cudaStream_t s);
+void launch_layout(const Geom& g, const float* values, const uint8_t* mask, double zmin,
+                   double zmax, int degenerate, float q, float* dang, float2* dcs, cudaStream_t s);
+void launch_block_stats(const Geom& g, const float* values, const uint8_t* mask, double zmin,
+                        double zmax, int degenerate, double q, double J, double* Es, int32_t* Nsp,
+                        int32_t* Nb, double* ssum, int32_t* nsamp, int32_t* ngap0, int32_t* ngap1,
+                        cudaStream_t s);
+void launch_scan(const int32_t* cnt, int n, int32_t* out, cudaStream_t s);
+void launch_build_lists(const Geom& g, const uint8_t* mask, const int32_t* start0,
+                        const int32_t* start1, uint2* list0, uint2* list1, cudaStream_t s);
+void launch_init(const Geom& g, const uint2* list, int64_t n_list, int colour,
+                 const float* init_angle, float* ang, int G, int Rp, int random, Rng rng,
+                 uint32_t r_even, cudaStream_t s);
+void launch_halfstep(const SweepArgs& a, int G, int n_sm, cudaStream_t s);
+void launch_stop_init(int nblk, int Rp, int R, int r_off, const double* Es, const int32_t* Nsp,
+                      const int32_t* Nb, const int32_t* ngap, double* eacc, int8_t* sigma,
+                      uint8_t* running, int32_t* stop, int32_t* tcount, double* e_last,
+                      cudaStream_t s);
+void launch_stop_targeted(int nblk, int Rp, int t, const double* Es, const int32_t* Nsp,
+                          const int32_t* Nb, double* eacc, const int8_t* sigma, uint8_t* running,
+                          int32_t* stop, int32_t* tcount, double* e_last, cudaStream_t s);
+void launch_stop_rest(int nblk, int Rp, int t, int n_max, const int32_t* Nsp, uint8_t* running,
+                      int32_t* stop, const int32_t* tcount, unsigned long long* n_running,
+                      cudaStream_t s);
+void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
+                          unsigned long long* total, cudaStream_t s);
+void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,
+                     cudaStream_t s);
+void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T,
+                    cudaStream_t s);
+void launch_cal_fill(int nblk, const int32_t* Nsp, float* T, float* beta, cudaStream_t s);
+void launch_cal_measure(int nblk, int Rp, int chains, const double* Es, const int32_t* Nb,
+                        double* eacc, double* ebar, cudaStream_t s);
+void launch_cal_update(int nblk, double inv_count, const double* Es, const int32_t* Nsp,
+                       const float* T, float* lo, float* hi, double* ebar, double* trace,
+                       cudaStream_t s);
+void launch_accumulate(const Geom& g, const uint2* list, int64_t n_list, int colour,
+                       const float* ang, int G, int groups, int r_off, int R, double* sum,
+                       cudaStream_t s);
+void launch_predict(const Geom& g, const float* values, const uint8_t* mask, const double* sum,
+                    double inv_r, double zmin, double zmax, float* out, const float* truth,
+                    double* err, cudaStream_t s);
+void launch_get_state(const Geom& g, const uint8_t* mask, const float* dang, const float* ang,
+                      int G, int r, float* out, cudaStream_t s);
+void launch_set_state(const Geom& g, const uint8_t* mask, float* ang, int G, int r,
+                      const float* in, cudaStream_t s);
+void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, const float* ang,
+                         int G, int r, double q, double J, double* E, cudaStream_t s);
+
+}  // namespace mpr

@@ -1,0 +1,336 @@
+"""Thin ctypes binding of libmpr (include/mpr.h), same names as the C-ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); device
+tensors are passed as device pointers. The library must be built for sm_103a
+(``paper_2212_01317_gb300.build``); without it, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MPR_OK, MPR_EINVAL, MPR_ENOMEM, MPR_ECUDA, MPR_ENOSAMPLES, MPR_ETIMEOUT, MPR_ESTATE = range(7)
+MPR_STORE_F32, MPR_STORE_BF16, MPR_STORE_F16 = 0, 1, 2
+MPR_INIT_BLOCK_MEAN, MPR_INIT_RANDOM = 0, 1
+
+EXPORTS = [
+    "mpr_default_options", "mpr_create", "mpr_destroy", "mpr_last_error", "mpr_status_string",
+    "mpr_get_info", "mpr_calibrate", "mpr_set_temperatures", "mpr_get_temperatures",
+    "mpr_simulate", "mpr_predict", "mpr_get_block_stats", "mpr_sim_begin", "mpr_sim_sweep",
+    "mpr_sim_end", "mpr_halfstep", "mpr_get_state", "mpr_set_state", "mpr_get_stop",
+    "mpr_set_running", "mpr_block_energy", "mpr_get_block_e", "mpr_get_profile",
+]
+
+
+class mpr_grid(C.Structure):
+    _fields_ = [("height", C.c_int32), ("width", C.c_int32), ("block", C.c_int32)]
+
+
+class mpr_options(C.Structure):
+    _fields_ = [("q", C.c_double), ("J", C.c_double), ("seed", C.c_uint64),
+                ("slice_id", C.c_uint32), ("n_max", C.c_int32), ("n_eq", C.c_int32),
+                ("n_meas", C.c_int32), ("n_bisect", C.c_int32), ("cal_chains", C.c_int32),
+                ("t_lo", C.c_float), ("t_hi", C.c_float), ("overrelax", C.c_int32),
+                ("init", C.c_int32), ("storage", C.c_int32), ("group", C.c_int32),
+                ("profile", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class mpr_profile(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("sim_halfstep_launches", C.c_int64),
+                ("cal_halfstep_launches", C.c_int64), ("sim_halfstep_ms", C.c_double),
+                ("cal_halfstep_ms", C.c_double)]
+
+
+class mpr_info(C.Structure):
+    _fields_ = [("height", C.c_int32), ("width", C.c_int32), ("block", C.c_int32),
+                ("nbx", C.c_int32), ("nby", C.c_int32), ("nblk", C.c_int32),
+                ("n_gap", C.c_int64), ("n_gap_colour", C.c_int64 * 2),
+                ("zmin", C.c_double), ("zmax", C.c_double), ("degenerate", C.c_int32),
+                ("calibrated", C.c_int32), ("realizations", C.c_int64), ("batch", C.c_int32),
+                ("group", C.c_int32), ("gap_updates", C.c_int64),
+                ("cal_gap_updates", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class MprError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS_NAMES = {0: "MPR_OK", 1: "MPR_EINVAL", 2: "MPR_ENOMEM", 3: "MPR_ECUDA",
+                 4: "MPR_ENOSAMPLES", 5: "MPR_ETIMEOUT", 6: "MPR_ESTATE"}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads libmpr.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.LIB
+        if not _build.up_to_date():
+            _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libmpr.so not found at {path}; build it with "
+                          "paper_2212_01317_gb300.build.build()")
+    L = C.CDLL(path)
+    P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    st = C.c_int
+    sig = {
+        "mpr_default_options": (None, [C.POINTER(mpr_options)]),
+        "mpr_create": (st, [C.POINTER(mpr_grid), P, P, C.POINTER(mpr_options), C.POINTER(P)]),
+        "mpr_destroy": (None, [P]),
+        "mpr_last_error": (C.c_char_p, [P]),
+        "mpr_status_string": (C.c_char_p, [st]),
+        "mpr_get_info": (st, [P, C.POINTER(mpr_info)]),
+        "mpr_calibrate": (st, [P, P]),
+        "mpr_set_temperatures": (st, [P, P]),
+        "mpr_get_temperatures": (st, [P, P]),
+        "mpr_simulate": (st, [P, i32]),
+        "mpr_predict": (st, [P, P, P, P]),
+        "mpr_get_block_stats": (st, [P, P, P, P, P, P]),
+        "mpr_sim_begin": (st, [P, i32]),
+        "mpr_sim_sweep": (st, [P, i32, C.POINTER(i64)]),
+        "mpr_sim_end": (st, [P]),
+        "mpr_halfstep": (st, [P, i32, i32, i32]),
+        "mpr_get_state": (st, [P, i32, P]),
+        "mpr_set_state": (st, [P, i32, P]),
+        "mpr_get_stop": (st, [P, P, P]),
+        "mpr_set_running": (st, [P, P]),
+        "mpr_block_energy": (st, [P, i32, P]),
+        "mpr_get_block_e": (st, [P, P]),
+        "mpr_get_profile": (st, [P, C.POINTER(mpr_profile)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (host or device), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous, "arrays must be C-contiguous"
+        return C.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return C.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(ctx, status: int):
+    if status != MPR_OK:
+        msg = load().mpr_last_error(ctx).decode() if ctx else ""
+        raise MprError(status, msg or load().mpr_status_string(status).decode())
+
+
+def mpr_default_options(**kw) -> mpr_options:
+    o = mpr_options()
+    load().mpr_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def mpr_create(height: int, width: int, block: int, mask, values, options: mpr_options | None = None):
+    g = mpr_grid(height, width, block)
+    out = C.c_void_p()
+    st = load().mpr_create(C.byref(g), _ptr(mask), _ptr(values),
+                           None if options is None else C.byref(options), C.byref(out))
+    if st != MPR_OK:
+        raise MprError(st, load().mpr_status_string(st).decode())
+    return out
+
+
+def mpr_destroy(ctx):
+    load().mpr_destroy(ctx)
+
+
+def mpr_get_info(ctx) -> mpr_info:
+    info = mpr_info()
+    _check(ctx, load().mpr_get_info(ctx, C.byref(info)))
+    return info
+
+
+def mpr_calibrate(ctx, block_T_out=None):
+    _check(ctx, load().mpr_calibrate(ctx, _ptr(block_T_out)))
+
+
+def mpr_set_temperatures(ctx, T):
+    _check(ctx, load().mpr_set_temperatures(ctx, _ptr(T)))
+
+
+def mpr_get_temperatures(ctx, out):
+    _check(ctx, load().mpr_get_temperatures(ctx, _ptr(out)))
+
+
+def mpr_simulate(ctx, n_realizations: int):
+    _check(ctx, load().mpr_simulate(ctx, int(n_realizations)))
+
+
+def mpr_predict(ctx, out, truth=None, aae_rase=None):
+    _check(ctx, load().mpr_predict(ctx, _ptr(out), _ptr(truth), _ptr(aae_rase)))
+
+
+def mpr_get_block_stats(ctx, Es=None, Nsp=None, Nb=None, mean_angle=None, n_gap=None):
+    _check(ctx, load().mpr_get_block_stats(ctx, _ptr(Es), _ptr(Nsp), _ptr(Nb), _ptr(mean_angle),
+                                           _ptr(n_gap)))
+
+
+def mpr_sim_begin(ctx, n_realizations: int):
+    _check(ctx, load().mpr_sim_begin(ctx, int(n_realizations)))
+
+
+def mpr_sim_sweep(ctx, n_sweeps: int) -> int:
+    left = C.c_int64()
+    _check(ctx, load().mpr_sim_sweep(ctx, int(n_sweeps), C.byref(left)))
+    return left.value
+
+
+def mpr_sim_end(ctx):
+    _check(ctx, load().mpr_sim_end(ctx))
+
+
+def mpr_halfstep(ctx, colour: int, t: int, tag: int = 0):
+    _check(ctx, load().mpr_halfstep(ctx, colour, t, tag))
+
+
+def mpr_get_state(ctx, r: int, out):
+    _check(ctx, load().mpr_get_state(ctx, r, _ptr(out)))
+
+
+def mpr_set_state(ctx, r: int, angles):
+    _check(ctx, load().mpr_set_state(ctx, r, _ptr(angles)))
+
+
+def mpr_get_stop(ctx, stop_sweep=None, running=None):
+    _check(ctx, load().mpr_get_stop(ctx, _ptr(stop_sweep), _ptr(running)))
+
+
+def mpr_set_running(ctx, running):
+    _check(ctx, load().mpr_set_running(ctx, _ptr(running)))
+
+
+def mpr_block_energy(ctx, r: int, out):
+    _check(ctx, load().mpr_block_energy(ctx, r, _ptr(out)))
+
+
+def mpr_get_profile(ctx) -> mpr_profile:
+    p = mpr_profile()
+    _check(ctx, load().mpr_get_profile(ctx, C.byref(p)))
+    return p
+
+
+def mpr_get_block_e(ctx, out):
+    _check(ctx, load().mpr_get_block_e(ctx, _ptr(out)))
+
+
+class GapFiller:
+    """Owns one mpr context; numpy in, numpy out (marshalling only)."""
+
+    def __init__(self, values, mask, block: int, **options):
+        values = np.ascontiguousarray(values, dtype=np.float32)
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        self.H, self.W = mask.shape
+        self.opt = mpr_default_options(**options)
+        self.ctx = mpr_create(self.H, self.W, block, mask, values, self.opt)
+        self.info = mpr_get_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mpr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nblk(self) -> int:
+        return self.info.nblk
+
+    def refresh(self) -> mpr_info:
+        self.info = mpr_get_info(self.ctx)
+        return self.info
+
+    def calibrate(self) -> np.ndarray:
+        T = np.zeros(self.nblk, np.float32)
+        mpr_calibrate(self.ctx, T)
+        return T
+
+    def set_temperatures(self, T):
+        mpr_set_temperatures(self.ctx, np.ascontiguousarray(T, dtype=np.float32))
+
+    def simulate(self, n: int):
+        mpr_simulate(self.ctx, n)
+
+    def predict(self, truth=None):
+        out = np.zeros((self.H, self.W), np.float32)
+        if truth is None:
+            mpr_predict(self.ctx, out)
+            return out, None
+        err = np.zeros(2, np.float64)
+        mpr_predict(self.ctx, out, np.ascontiguousarray(truth, dtype=np.float32), err)
+        return out, (float(err[0]), float(err[1]))
+
+    def block_stats(self):
+        n = self.nblk
+        Es, Nsp, Nb = np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.int32)
+        ma, ng = np.zeros(n, np.float32), np.zeros(n, np.int32)
+        mpr_get_block_stats(self.ctx, Es, Nsp, Nb, ma, ng)
+        return Es, Nsp, Nb, ma, ng
+
+    # step-wise access
+    def sim_begin(self, n: int):
+        mpr_sim_begin(self.ctx, n)
+
+    def sim_sweep(self, n: int = 1) -> int:
+        return mpr_sim_sweep(self.ctx, n)
+
+    def sim_end(self):
+        mpr_sim_end(self.ctx)
+
+    def halfstep(self, colour: int, t: int, tag: int = 0):
+        mpr_halfstep(self.ctx, colour, t, tag)
+
+    def get_state(self, r: int) -> np.ndarray:
+        out = np.zeros((self.H, self.W), np.float32)
+        mpr_get_state(self.ctx, r, out)
+        return out
+
+    def set_state(self, r: int, angles):
+        mpr_set_state(self.ctx, r, np.ascontiguousarray(angles, dtype=np.float32))
+
+    def get_stop(self, R: int):
+        stop = np.zeros((R, self.nblk), np.int32)
+        run = np.zeros((R, self.nblk), np.uint8)
+        mpr_get_stop(self.ctx, stop, run)
+        return stop, run
+
+    def set_running(self, running):
+        mpr_set_running(self.ctx, np.ascontiguousarray(running, dtype=np.uint8))
+
+    def block_e(self, R: int) -> np.ndarray:
+        e = np.zeros((R, self.nblk))
+        mpr_get_block_e(self.ctx, e)
+        return e
+
+    def block_energy(self, r: int) -> np.ndarray:
+        E = np.zeros(self.nblk)
+        mpr_block_energy(self.ctx, r, E)
+        return E
