@@ -72,7 +72,7 @@ typedef struct {
     int32_t overrelax;   /* 1: Metropolis then over-relaxation per site (default 1) */
     int32_t init;        /* mpr_init (default MPR_INIT_BLOCK_MEAN, Sec. 3.3.3) */
     int32_t storage;     /* mpr_storage for the gap angles (default F32) */
-    int32_t group;       /* realizations interleaved per lane group: 0 = auto, 1, 8, 32 */
+    int32_t group;       /* realizations interleaved per site: 0 = auto, 2 or 8 */
     int32_t profile;     /* 1: time every sweep-kernel launch with CUDA events (default 0) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mpr.h"
+#include "mpr.h"
 #include "mpr_internal.h"
 #include "mpr_launch.h"
 
@@ -22,6 +22,7 @@ struct mpr_ctx {
     Model m{};
     Rng rng{};
     cudaStream_t s = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only to record graphs
     int device = 0, n_sm = 152;
     std::string err;
 
@@ -40,7 +41,10 @@ struct mpr_ctx {
     float2* dcs = nullptr;
     uint2* list[2] = {nullptr, nullptr};
     int32_t* start[2] = {nullptr, nullptr};
+    int32_t* split[2] = {nullptr, nullptr};
     double* Es = nullptr;
+    double* es = nullptr;   // E_s,b / N_SP,b
+    double* inb = nullptr;  // 1 / N_b
     int32_t *Nsp = nullptr, *Nb = nullptr, *nsamp = nullptr, *ngap_c[2] = {nullptr, nullptr},
             *ngap = nullptr;
     double* ssum = nullptr;
@@ -62,13 +66,19 @@ struct mpr_ctx {
     int batch_open = 0;
     float* ang = nullptr;
     size_t ang_cap = 0;
-    double* eacc = nullptr;
+    float* eacc = nullptr;
+    double* ecur = nullptr;      // [nblk][Rp] current E_b of every (block, realization)
     uint8_t* running = nullptr;
     int32_t* stop = nullptr;
     int8_t* sigma = nullptr;
     double* e_last = nullptr;
     int32_t* tcount = nullptr;
-    size_t blk_cap = 0, lane_cap = 0;
+    uint32_t* work = nullptr;    // [nblk * groups] worklist of running items
+    size_t blk_cap = 0, lane_cap = 0, work_cap = 0;
+    Control* ctl = nullptr;      // device loop state
+    Control* h_ctl = nullptr;    // pinned mirror
+    int grid_sweep[2] = {0, 0};  // persistent grid of k_sweep<2>, k_sweep<8>
+    bool energy_dirty = false;
 
     int64_t realizations = 0;
     int64_t gap_updates = 0, cal_updates = 0;
@@ -143,11 +153,11 @@ void dfree(mpr_ctx* ctx, void* p) {
     cudaFree(p);
 }
 
+// Lane-group width: 2 (one realization pair per group) for up to two lanes
+// or when asked, else 8 (four pairs per group).
 int pick_group(int lanes, int requested) {
-    if (requested == 1 || requested == 8 || requested == 32) return requested;
-    if (lanes <= 1) return 1;
-    const int p8 = (lanes + 7) / 8 * 8, p32 = (lanes + 31) / 32 * 32;
-    return p32 <= p8 ? 32 : 8;
+    if (requested == 2 || requested == 8) return requested;
+    return lanes <= 2 ? 2 : 8;
 }
 
 mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
@@ -161,8 +171,8 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (!(o.t_lo > 0.0f && o.t_hi > o.t_lo)) return fail(ctx, MPR_EINVAL, "need 0 < t_lo < t_hi");
     if (o.storage != MPR_STORE_F32)
         return fail(ctx, MPR_EINVAL, "storage %d not supported by this build", o.storage);
-    if (o.group != 0 && o.group != 1 && o.group != 8 && o.group != 32)
-        return fail(ctx, MPR_EINVAL, "group must be 0, 1, 8 or 32");
+    if (o.group != 0 && o.group != 2 && o.group != 8)
+        return fail(ctx, MPR_EINVAL, "group must be 0, 2 or 8");
     if (o.init != MPR_INIT_BLOCK_MEAN && o.init != MPR_INIT_RANDOM)
         return fail(ctx, MPR_EINVAL, "unknown init mode");
     return MPR_OK;
@@ -197,12 +207,13 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group) {
     const size_t blk_need = (size_t)g.nblk * Rp;
     if (blk_need > ctx->blk_cap) {
         for (void* p : {(void*)ctx->eacc, (void*)ctx->running, (void*)ctx->stop, (void*)ctx->sigma,
-                        (void*)ctx->e_last})
+                        (void*)ctx->e_last, (void*)ctx->ecur})
             dfree(ctx, p);
         ctx->eacc = nullptr; ctx->running = nullptr; ctx->stop = nullptr; ctx->sigma = nullptr;
-        ctx->e_last = nullptr;
+        ctx->e_last = nullptr; ctx->ecur = nullptr;
         ctx->blk_cap = 0;
         TRY(dalloc(ctx, &ctx->eacc, blk_need));
+        TRY(dalloc(ctx, &ctx->ecur, blk_need));
         TRY(dalloc(ctx, &ctx->e_last, blk_need));
         TRY(dalloc(ctx, &ctx->running, blk_need));
         TRY(dalloc(ctx, &ctx->stop, blk_need));
@@ -216,15 +227,23 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group) {
         TRY(dalloc(ctx, &ctx->tcount, (size_t)Rp));
         ctx->lane_cap = Rp;
     }
+    const size_t work_need = (size_t)g.nblk * groups;
+    if (work_need > ctx->work_cap) {
+        dfree(ctx, ctx->work);
+        ctx->work = nullptr;
+        ctx->work_cap = 0;
+        TRY(dalloc(ctx, &ctx->work, work_need));
+        ctx->work_cap = work_need;
+    }
     ctx->G = G;
     ctx->groups = groups;
     ctx->Rp = Rp;
-    CK(cudaMemsetAsync(ctx->eacc, 0, blk_need * sizeof(double), ctx->s));
+    CK(cudaMemsetAsync(ctx->eacc, 0, blk_need * sizeof(float), ctx->s));
+    CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(Control), ctx->s));
     return MPR_OK;
 }
 
-SweepArgs sweep_args(mpr_ctx* ctx, int colour, uint32_t t, uint32_t tag, int update, int energy,
-                     bool use_running) {
+SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
     SweepArgs a{};
     a.g = ctx->g;
     a.m = ctx->m;
@@ -232,21 +251,24 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, uint32_t t, uint32_t tag, int upd
     a.colour = colour;
     a.list = ctx->list[colour];
     a.start = ctx->start[colour];
+    a.split = ctx->split[colour];
     a.ang = ctx->ang;
     a.dcs = ctx->dcs;
     a.beta = ctx->beta;
-    a.running = use_running ? ctx->running : nullptr;
+    a.running = simulate ? ctx->running : nullptr;
     a.eacc = ctx->eacc;
+    a.ecur = ctx->ecur;
+    a.work = simulate ? ctx->work : nullptr;
+    a.ctl = ctx->ctl;
     a.R = ctx->R;
     a.Rp = ctx->Rp;
     a.groups = ctx->groups;
     a.r_base = ctx->r_even;
-    a.t = t;
-    a.tag = tag;
-    a.update = update;
-    a.energy = energy;
+    a.energy = 1;
     return a;
 }
+
+int sweep_grid(mpr_ctx* ctx) { return ctx->grid_sweep[ctx->G == 2 ? 0 : 1]; }
 
 cudaEvent_t get_event(mpr_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -271,13 +293,30 @@ mpr_status halfstep_launch(mpr_ctx* ctx, const SweepArgs& a, bool sim) {
         e1 = get_event(ctx);
         if (e0) cudaEventRecord(e0, ctx->s);
     }
-    launch_halfstep(a, ctx->G, ctx->n_sm, ctx->s);
+    launch_sweep(a, ctx->G, sweep_grid(ctx), false, ctx->s);
+    CKL();
+    launch_sweep(a, ctx->G, sweep_grid(ctx), true, ctx->s);
     CKL();
     if (e0 && e1) {
         cudaEventRecord(e1, ctx->s);
         (sim ? ctx->ev_sim : ctx->ev_cal).emplace_back(e0, e1);
     }
     if (sim) ++ctx->sim_halfstep_launches; else ++ctx->cal_halfstep_launches;
+    return MPR_OK;
+}
+
+// E_b of the batch's current state from scratch, into ecur: E_s,b plus every
+// bond that touches a gap site (every lane of every block: the pass ignores
+// the running flags). Clears eacc.
+mpr_status energy_pass(mpr_ctx* ctx) {
+    launch_ecur_reset(ctx->g.nblk, ctx->Rp, ctx->Es, ctx->ecur, ctx->eacc, ctx->s);
+    CKL();
+    for (int c = 0; c < 2; ++c) {
+        SweepArgs a = sweep_args(ctx, c, false);
+        a.R = ctx->Rp;
+        launch_energy(a, ctx->G, sweep_grid(ctx), ctx->s);
+        CKL();
+    }
     return MPR_OK;
 }
 
@@ -307,6 +346,25 @@ mpr_status init_batch_state(mpr_ctx* ctx) {
     return MPR_OK;
 }
 
+// After the running flags were overwritten: per-realization counts of running
+// targeted blocks and the worklist of items with a running lane.
+__global__ void k_rebuild(int nblk, int groups, int G, int Rp, const int32_t* Nsp,
+                          const uint8_t* running, int32_t* tcount, Control* ctl, uint32_t* work) {
+    const int64_t n = (int64_t)nblk * groups;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(it / groups), grp = (int)(it % groups);
+        bool any = false;
+        for (int g = 0; g < G; ++g) {
+            const int r = grp * G + g;
+            if (!running[(size_t)b * Rp + r]) continue;
+            any = true;
+            if (Nsp[b] > 0) atomicAdd(&tcount[r], 1);
+        }
+        if (any) work[atomicAdd(&ctl->n_work_next, 1u)] = (uint32_t)it;
+    }
+}
+
 __global__ void k_fill_valid(uint8_t* running, int64_t n, int Rp, int r_off, int R) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -315,17 +373,136 @@ __global__ void k_fill_valid(uint8_t* running, int64_t n, int Rp, int r_off, int
     }
 }
 
+// One sweep of the batch: colour 0, colour 1, block energies, stop tests,
+// next worklist. Everything the kernels need comes from device memory.
 mpr_status sweep_once(mpr_ctx* ctx) {
-    ctx->t += 1;
-    const uint32_t t = (uint32_t)ctx->t;
-    for (int c = 0; c < 2; ++c) TRY(halfstep_launch(ctx, sweep_args(ctx, c, t, 0u, 1, 1, true), true));
-    launch_stop_targeted(ctx->g.nblk, ctx->Rp, ctx->t, ctx->Es, ctx->Nsp, ctx->Nb, ctx->eacc,
+    const Geom& g = ctx->g;
+    launch_tick(ctx->ctl, ctx->s);
+    CKL();
+    for (int c = 0; c < 2; ++c) TRY(halfstep_launch(ctx, sweep_args(ctx, c, true), true));
+    launch_stop_targeted(g.nblk, ctx->Rp, ctx->ctl, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
                          ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
-    launch_stop_rest(ctx->g.nblk, ctx->Rp, ctx->t, ctx->opt.n_max, ctx->Nsp, ctx->running,
-                     ctx->stop, ctx->tcount, &ctx->counters[0], ctx->s);
+    launch_stop_rest(g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->ctl, ctx->Nsp,
+                     ctx->running, ctx->stop, ctx->tcount, ctx->work, ctx->s);
+    CKL();
+    ctx->t += 1;
+    return MPR_OK;
+}
+
+// E_b of every (block, realization) recomputed from the state (after the
+// state was overwritten through the API).
+mpr_status refresh_energies(mpr_ctx* ctx) {
+    TRY(energy_pass(ctx));
+    ctx->energy_dirty = false;
+    return MPR_OK;
+}
+
+// One bisection iteration k (Sec. 2.1 energy matching per block): midpoints
+// and median fallback, fresh start, E_b from scratch, n_eq + n_meas sweeps
+// with the energies of the last n_meas summed, bisection step. With cond != 0
+// the last kernel also sets the graph's loop condition.
+mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphConditionalHandle cond) {
+    const Geom& g = ctx->g;
+    const mpr_options& o = ctx->opt;
+    launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+    CKL();
+    launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+    CKL();
+    TRY(init_batch_state(ctx));
+    TRY(energy_pass(ctx));
+    for (int sw = 1; sw <= o.n_eq + o.n_meas; ++sw) {
+        launch_tick(ctx->ctl, ctx->s);
+        CKL();
+        for (int c = 0; c < 2; ++c) {
+            launch_sweep(sweep_args(ctx, c, false), ctx->G, sweep_grid(ctx), false, ctx->s);
+            CKL();
+            launch_sweep(sweep_args(ctx, c, false), ctx->G, sweep_grid(ctx), true, ctx->s);
+            CKL();
+            ++ctx->cal_halfstep_launches;
+        }
+        launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, ctx->ctl, ctx->inb, ctx->eacc,
+                        ctx->ecur, ctx->ebar, ctx->s);
+        CKL();
+    }
+    launch_cal_update(g.nblk, inv_count, ctx->es, ctx->Nsp, ctx->T, ctx->lo, ctx->hi, ctx->ebar,
+                      ctx->ctl, o.n_bisect, cond, ctx->s);
     CKL();
     return MPR_OK;
+}
+
+// All n_bisect iterations as one CUDA graph: a device-side WHILE loop whose
+// body is one iteration (captured once); k_cal_update ends it. One launch, no
+// host round trip per iteration.
+mpr_status calibration_graph(mpr_ctx* ctx, double inv_count) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    mpr_status st = MPR_OK;
+    cudaGraphConditionalHandle cond = 0;
+    cudaGraphNodeParams p = {};
+    cudaGraphNode_t node = nullptr;
+    cudaGraph_t body = nullptr, captured = nullptr;
+    const int64_t launches0 = ctx->launches, hs0 = ctx->cal_halfstep_launches;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) goto cuda_fail;
+    if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        goto cuda_fail;
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) != cudaSuccess) goto cuda_fail;
+    body = p.conditional.phGraph_out[0];
+    // Record on the private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); launch on the caller's stream.
+    if (cudaStreamBeginCaptureToGraph(ctx->cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        goto cuda_fail;
+    {
+        cudaStream_t user = ctx->s;
+        ctx->s = ctx->cap;
+        st = calibration_iteration(ctx, inv_count, cond);
+        ctx->s = user;
+    }
+    if (cudaStreamEndCapture(ctx->cap, &captured) != cudaSuccess && st == MPR_OK) goto cuda_fail;
+    if (st != MPR_OK) goto done;
+    // The body ran once at capture time only as a recording; the loop runs
+    // it n_bisect times.
+    {
+        const int64_t per_iter_launches = ctx->launches - launches0;
+        const int64_t per_iter_hs = ctx->cal_halfstep_launches - hs0;
+        ctx->launches = launches0 + per_iter_launches * ctx->opt.n_bisect;
+        ctx->cal_halfstep_launches = hs0 + per_iter_hs * ctx->opt.n_bisect;
+    }
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) goto cuda_fail;
+    if (ctx->opt.profile) {
+        e0 = get_event(ctx);
+        e1 = get_event(ctx);
+        if (e0) cudaEventRecord(e0, ctx->s);
+    }
+    if (cudaGraphLaunch(exec, ctx->s) != cudaSuccess) goto cuda_fail;
+    if (e0 && e1) {
+        cudaEventRecord(e1, ctx->s);
+        ctx->ev_cal.emplace_back(e0, e1);
+    }
+    goto done;
+cuda_fail: {
+        cudaError_t e = cudaGetLastError();
+        st = fail(ctx, MPR_ECUDA, "calibration graph: %s", cudaGetErrorString(e));
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(ctx->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(ctx->cap, &tmp);
+            if (tmp && tmp != body) cudaGraphDestroy(tmp);
+        }
+    }
+done:
+    if (exec) {
+        cudaStreamSynchronize(ctx->s);
+        cudaGraphExecDestroy(exec);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return st;
 }
 
 }  // namespace
@@ -376,8 +553,10 @@ void mpr_destroy(mpr_ctx* ctx) {
     for (auto& pr : ctx->ev_sim) ctx->ev_pool.insert(ctx->ev_pool.end(), {pr.first, pr.second});
     for (auto& pr : ctx->ev_cal) ctx->ev_pool.insert(ctx->ev_pool.end(), {pr.first, pr.second});
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     for (void* p : ctx->owned) cudaFree(p);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     delete ctx;
 }
 
@@ -416,6 +595,8 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     ctx->s = (cudaStream_t)ctx->opt.cuda_stream;
 
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(MPR_ECUDA);
+    if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(MPR_ECUDA);
     cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
     if (ctx->n_sm < 1) ctx->n_sm = 1;
 
@@ -429,6 +610,8 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     ST(dalloc(ctx, &ctx->dcs, 2 * plane));
     ST(dalloc(ctx, &ctx->sum, 2 * plane));
     ST(dalloc(ctx, &ctx->Es, g.nblk));
+    ST(dalloc(ctx, &ctx->es, g.nblk));
+    ST(dalloc(ctx, &ctx->inb, g.nblk));
     ST(dalloc(ctx, &ctx->Nsp, g.nblk));
     ST(dalloc(ctx, &ctx->Nb, g.nblk));
     ST(dalloc(ctx, &ctx->nsamp, g.nblk));
@@ -444,11 +627,17 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     ST(dalloc(ctx, &ctx->ebar, g.nblk));
     ST(dalloc(ctx, &ctx->start[0], g.nblk + 1));
     ST(dalloc(ctx, &ctx->start[1], g.nblk + 1));
+    ST(dalloc(ctx, &ctx->split[0], g.nblk));
+    ST(dalloc(ctx, &ctx->split[1], g.nblk));
     ST(dalloc(ctx, &ctx->counters, 4));
     ST(dalloc(ctx, &ctx->mm, 2));
     ST(dalloc(ctx, &ctx->err_buf, 2));
-    if (cudaMallocHost(&ctx->h_counters, 4 * sizeof(unsigned long long)) != cudaSuccess)
+    ST(dalloc(ctx, &ctx->ctl, 1));
+    if (cudaMallocHost(&ctx->h_counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ctl, sizeof(Control)) != cudaSuccess)
         return bail(MPR_ENOMEM);
+    ctx->grid_sweep[0] = ctx->n_sm * sweep_blocks_per_sm(2);
+    ctx->grid_sweep[1] = ctx->n_sm * sweep_blocks_per_sm(8);
 
     if (copy_in(ctx, ctx->values, values_in, n * sizeof(float)) != MPR_OK) return bail(MPR_ECUDA);
     if (copy_in(ctx, ctx->mask, mask_in, n) != MPR_OK) return bail(MPR_ECUDA);
@@ -487,8 +676,8 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
 
     // Host-side bookkeeping: list sizes, initial angles, sample-pair check.
     std::vector<int32_t> s0(g.nblk + 1), s1(g.nblk + 1), nsp(g.nblk), nsm(g.nblk), ng0(g.nblk),
-        ng1(g.nblk);
-    std::vector<double> ssum(g.nblk);
+        ng1(g.nblk), nbv(g.nblk);
+    std::vector<double> ssum(g.nblk), esv(g.nblk);
     if (cudaMemcpyAsync(s0.data(), ctx->start[0], s0.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
         cudaMemcpyAsync(s1.data(), ctx->start[1], s1.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
         cudaMemcpyAsync(nsp.data(), ctx->Nsp, nsp.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
@@ -496,6 +685,8 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
         cudaMemcpyAsync(ng0.data(), ctx->ngap_c[0], ng0.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
         cudaMemcpyAsync(ng1.data(), ctx->ngap_c[1], ng1.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
         cudaMemcpyAsync(ssum.data(), ctx->ssum, ssum.size() * 8, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaMemcpyAsync(esv.data(), ctx->Es, esv.size() * 8, cudaMemcpyDeviceToHost, ctx->s) ||
+        cudaMemcpyAsync(nbv.data(), ctx->Nb, nbv.size() * 4, cudaMemcpyDeviceToHost, ctx->s) ||
         cudaStreamSynchronize(ctx->s))
         return bail(MPR_ECUDA);
     ctx->n_gap[0] = s0[g.nblk];
@@ -513,6 +704,11 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     const double gmean = samples ? gsum / (double)samples : 0.0;
     for (int b = 0; b < g.nblk; ++b)
         init[b] = (float)(nsm[b] > 0 ? ssum[b] / (double)nsm[b] : gmean);
+    std::vector<double> es_h(g.nblk), inb_h(g.nblk);
+    for (int b = 0; b < g.nblk; ++b) {
+        es_h[b] = nsp[b] > 0 ? esv[b] / (double)nsp[b] : 0.0;
+        inb_h[b] = nbv[b] > 0 ? 1.0 / (double)nbv[b] : 0.0;
+    }
     if (pairs == 0 && ctx->n_gap[0] + ctx->n_gap[1] > 0) {
         mpr_destroy(ctx);
         return MPR_ENOSAMPLES;
@@ -520,12 +716,15 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     ST(dalloc(ctx, &ctx->list[0], ctx->n_gap[0]));
     ST(dalloc(ctx, &ctx->list[1], ctx->n_gap[1]));
     if (cudaMemcpyAsync(ctx->init_angle, init.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s) ||
+        cudaMemcpyAsync(ctx->es, es_h.data(), g.nblk * 8, cudaMemcpyHostToDevice, ctx->s) ||
+        cudaMemcpyAsync(ctx->inb, inb_h.data(), g.nblk * 8, cudaMemcpyHostToDevice, ctx->s) ||
         cudaMemcpyAsync(ctx->ngap, ng.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s))
         return bail(MPR_ECUDA);
     launch_build_lists(g, ctx->mask, ctx->start[0], ctx->start[1], ctx->list[0], ctx->list[1],
-                       ctx->s);
+                       ctx->split[0], ctx->split[1], ctx->s);
     ++ctx->launches;
     if (cudaMemsetAsync(ctx->sum, 0, 2 * plane * sizeof(double), ctx->s) ||
+        cudaMemsetAsync(ctx->ctl, 0, sizeof(Control), ctx->s) ||
         cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), ctx->s) ||
         cudaPeekAtLastError() || cudaStreamSynchronize(ctx->s))
         return bail(MPR_ECUDA);
@@ -629,35 +828,18 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
         return MPR_OK;
     }
     const int chains = o.cal_chains;
-    TRY(ensure_batch(ctx, chains, o.group));
-    ctx->R = chains;
     ctx->r_off = 0;
     ctx->r_even = 0;
-    launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->s);
+    TRY(ensure_batch(ctx, chains, o.group));
+    ctx->R = chains;
+    launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->ctl, ctx->s);
     CKL();
     const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);
-    for (int k = 0; k < o.n_bisect; ++k) {
-        launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->s);
-        launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
-        CKL();
-        TRY(init_batch_state(ctx));
-        const uint32_t tag = (uint32_t)(1 + k);
-        for (int sw = 1; sw <= o.n_eq + o.n_meas; ++sw) {
-            const int measure = sw > o.n_eq;
-            for (int c = 0; c < 2; ++c)
-                TRY(halfstep_launch(ctx, sweep_args(ctx, c, (uint32_t)sw, tag, 1, measure, false),
-                                    false));
-            if (measure) {
-                launch_cal_measure(g.nblk, ctx->Rp, chains, ctx->Es, ctx->Nb, ctx->eacc,
-                                   ctx->ebar, ctx->s);
-                CKL();
-            }
-        }
-        launch_cal_update(g.nblk, inv_count, ctx->Es, ctx->Nsp, ctx->T, ctx->lo, ctx->hi,
-                          ctx->ebar, nullptr, ctx->s);
-        CKL();
-    }
-    launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->s);
+    launch_fill_samples(g, ctx->mask, ctx->dang, ctx->ang, ctx->G, ctx->groups, ctx->s);
+    CKL();
+    if (o.n_bisect > 0) TRY(calibration_graph(ctx, inv_count));
+    launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+    CKL();
     launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
     CKL();
     ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains *
@@ -685,21 +867,20 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     k_fill_valid<<<(int)std::min<int64_t>((nbr + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
         ctx->running, nbr, ctx->Rp, ctx->r_off, ctx->R);
     CKL();
+    launch_fill_samples(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->G, ctx->groups, ctx->s);
+    CKL();
     TRY(init_batch_state(ctx));
     CK(cudaMemsetAsync(ctx->tcount, 0, ctx->Rp * sizeof(int32_t), ctx->s));
-    // E_b(0): bond energies of the initial state (no moves).
-    for (int c = 0; c < 2; ++c) {
-        launch_halfstep(sweep_args(ctx, c, 0u, 0u, 0, 1, true), ctx->G, ctx->n_sm, ctx->s);
-        CKL();
-    }
-    launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->R, ctx->r_off, ctx->Es, ctx->Nsp, ctx->Nb, ctx->ngap,
-                     ctx->eacc, ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last,
-                     ctx->s);
+    // E_b(0): bond energies of the initial state (no moves), t = 0 stops,
+    // worklist of the first sweep.
+    TRY(energy_pass(ctx));
+    launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->es, ctx->inb, ctx->Nsp, ctx->ngap, ctx->ecur,
+                     ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
-    CK(cudaMemsetAsync(&ctx->counters[0], 0, sizeof(unsigned long long), ctx->s));
-    launch_stop_rest(ctx->g.nblk, ctx->Rp, 0, ctx->opt.n_max, ctx->Nsp, ctx->running, ctx->stop,
-                     ctx->tcount, &ctx->counters[0], ctx->s);
+    launch_stop_rest(ctx->g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->ctl, ctx->Nsp,
+                     ctx->running, ctx->stop, ctx->tcount, ctx->work, ctx->s);
     CKL();
+    ctx->energy_dirty = false;
     ctx->batch_open = 1;
     return MPR_OK;
 }
@@ -708,15 +889,12 @@ mpr_status mpr_sim_sweep(mpr_ctx* ctx, int32_t n_sweeps, int64_t* n_active) {
     if (!ctx) return MPR_EINVAL;
     ctx->err.clear();
     if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch (mpr_sim_begin)");
-    for (int i = 0; i < n_sweeps && ctx->t < ctx->opt.n_max; ++i) {
-        CK(cudaMemsetAsync(&ctx->counters[0], 0, sizeof(unsigned long long), ctx->s));
-        TRY(sweep_once(ctx));
-    }
+    if (ctx->energy_dirty) TRY(refresh_energies(ctx));
+    for (int i = 0; i < n_sweeps && ctx->t < ctx->opt.n_max; ++i) TRY(sweep_once(ctx));
     if (n_active) {
-        CK(cudaMemcpyAsync(ctx->h_counters, ctx->counters, sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, ctx->s));
         CK(cudaStreamSynchronize(ctx->s));
-        *n_active = (int64_t)ctx->h_counters[0];
+        *n_active = (int64_t)ctx->h_ctl->n_running;
     }
     return MPR_OK;
 }
@@ -746,12 +924,37 @@ mpr_status mpr_sim_end(mpr_ctx* ctx) {
 mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
     if (!ctx) return MPR_EINVAL;
     TRY(mpr_sim_begin(ctx, n));
+    // Sweeps are queued in chunks; after each chunk the running count is
+    // copied to pinned memory. The host checks the count of the chunk before
+    // the one it just queued, so the GPU never waits for the host. Sweeps
+    // queued after everything stopped find an empty worklist.
     const int chunk = 8;
+    unsigned long long* flag = ctx->h_counters + 2;   // two pinned slots
+    cudaEvent_t ev[2] = {get_event(ctx), get_event(ctx)};
+    if (!ev[0] || !ev[1]) return fail(ctx, MPR_ECUDA, "cudaEventCreate failed");
+    int c = 0;
+    mpr_status st = MPR_OK;
     while (ctx->t < ctx->opt.n_max) {
-        int64_t left = 0;
-        TRY(mpr_sim_sweep(ctx, chunk, &left));
-        if (left == 0) break;
+        for (int i = 0; i < chunk && ctx->t < ctx->opt.n_max && st == MPR_OK; ++i) st = sweep_once(ctx);
+        if (st != MPR_OK) break;
+        if (cudaMemcpyAsync(flag + (c & 1), &ctx->ctl->n_running, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, ctx->s) != cudaSuccess ||
+            cudaEventRecord(ev[c & 1], ctx->s) != cudaSuccess) {
+            st = fail(ctx, MPR_ECUDA, "simulate: copy of the running count failed");
+            break;
+        }
+        if (c >= 1) {
+            if (cudaEventSynchronize(ev[(c - 1) & 1]) != cudaSuccess) {
+                st = fail(ctx, MPR_ECUDA, "simulate: event synchronisation failed");
+                break;
+            }
+            if (flag[(c - 1) & 1] == 0) break;
+        }
+        ++c;
     }
+    ctx->ev_pool.push_back(ev[0]);
+    ctx->ev_pool.push_back(ev[1]);
+    if (st != MPR_OK) return st;
     return mpr_sim_end(ctx);
 }
 
@@ -762,10 +965,24 @@ mpr_status mpr_halfstep(mpr_ctx* ctx, int32_t colour, int32_t t, int32_t tag) {
     if (colour != 0 && colour != 1) return fail(ctx, MPR_EINVAL, "colour must be 0 or 1");
     if (t < 0 || t > 65535 || tag < 0 || tag > 65535)
         return fail(ctx, MPR_EINVAL, "t and tag must be in [0, 65535]");
-    launch_halfstep(sweep_args(ctx, colour, (uint32_t)t, (uint32_t)tag, 1, 0, true), ctx->G,
-                    ctx->n_sm, ctx->s);
+    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    Control saved = *ctx->h_ctl;
+    ctx->h_ctl->t = (uint32_t)t;
+    ctx->h_ctl->tag = (uint32_t)tag;
+    CK(cudaMemcpyAsync(ctx->ctl, ctx->h_ctl, sizeof(Control), cudaMemcpyHostToDevice, ctx->s));
+    SweepArgs a = sweep_args(ctx, colour, true);
+    a.work = nullptr;       // every item; the running flags decide
+    a.energy = 0;
+    launch_sweep(a, ctx->G, sweep_grid(ctx), false, ctx->s);
+    CKL();
+    launch_sweep(a, ctx->G, sweep_grid(ctx), true, ctx->s);
     CKL();
     CK(cudaStreamSynchronize(ctx->s));
+    *ctx->h_ctl = saved;
+    CK(cudaMemcpyAsync(ctx->ctl, ctx->h_ctl, sizeof(Control), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->energy_dirty = true;
     return MPR_OK;
 }
 
@@ -793,6 +1010,7 @@ mpr_status mpr_set_state(mpr_ctx* ctx, int32_t r, const float* angles) {
     launch_set_state(ctx->g, ctx->mask, ctx->ang, ctx->G, r + ctx->r_off, ctx->truth_buf, ctx->s);
     CKL();
     CK(cudaStreamSynchronize(ctx->s));
+    ctx->energy_dirty = true;
     return MPR_OK;
 }
 
@@ -847,6 +1065,12 @@ mpr_status mpr_set_running(mpr_ctx* ctx, const uint8_t* running) {
         for (int b = 0; b < nb; ++b)
             hr[(size_t)b * ctx->Rp + r + ctx->r_off] = in[(size_t)r * nb + b] ? 1 : 0;
     CK(cudaMemcpyAsync(ctx->running, hr.data(), hr.size(), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemsetAsync(ctx->tcount, 0, ctx->Rp * sizeof(int32_t), ctx->s));
+    CK(cudaMemsetAsync(&ctx->ctl->n_work_next, 0, sizeof(uint32_t), ctx->s));
+    const int64_t items = (int64_t)nb * ctx->groups;
+    k_rebuild<<<(int)std::min<int64_t>((items + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
+        nb, ctx->groups, ctx->G, ctx->Rp, ctx->Nsp, ctx->running, ctx->tcount, ctx->ctl, ctx->work);
+    CKL();
     CK(cudaStreamSynchronize(ctx->s));
     return MPR_OK;
 }

@@ -15,14 +15,12 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
                                               uint32_t k0, uint32_t k1, uint32_t out[4]) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo_a = 0xD2511F53u * c0;
-        const uint32_t hi_a = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo_b = 0xCD9E8D57u * c2;
-        const uint32_t hi_b = __umulhi(0xCD9E8D57u, c2);
-        c0 = hi_b ^ c1 ^ k0;
-        c1 = lo_b;
-        c2 = hi_a ^ c3 ^ k1;
-        c3 = lo_a;
+        const uint64_t pa = (uint64_t)0xD2511F53u * c0;
+        const uint64_t pb = (uint64_t)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(pb >> 32) ^ c1 ^ k0;
+        c1 = (uint32_t)pb;
+        c2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+        c3 = (uint32_t)pa;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -32,14 +30,42 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     out[3] = c3;
 }
 
-// Odd multiple of 2^-24 in (0,1): exact in FP32, identical to the oracle's value.
+// (((x >> 8) | 1) * 2^-24): an odd multiple of 2^-24 in (0,1), exact in FP32
+// and equal to the oracle's value. Built from the bits: 1 + (x >> 9) * 2^-23
+// is a float with mantissa x >> 9; subtracting 1 is exact (Sterbenz) and
+// adding 2^-24 lands on the representable (2 (x >> 9) + 1) * 2^-24.
 __device__ __forceinline__ float u01(uint32_t x) {
-    return __uint2float_rz((x >> 8) | 1u) * 5.9604644775390625e-08f;
+    return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 5.9604644775390625e-08f;
 }
 
-// Result of one site update: new angle and (cos, sin) of q times it.
+// psi = atan2(S, C) for S >= 0, psi in [0, pi]: atan(t) = t P(t^2) on
+// t = min/max of (|C|, S) in [0, 1], then the octant is restored. P is a
+// degree-7 near-minimax fit (gen_atan_poly.py; |error| < 7e-8 on [0, 1]).
+__device__ __forceinline__ float atan2_upper(float S, float C) {
+    const float ax = fabsf(C);
+    const float mn = fminf(ax, S), mx = fmaxf(ax, S);
+    const float t = __fdividef(mn, mx);
+    const float z = t * t;
+    float p = -4.054566845e-03f;
+    p = fmaf(p, z, 2.186295763e-02f);
+    p = fmaf(p, z, -5.591232702e-02f);
+    p = fmaf(p, z, 9.642197192e-02f);
+    p = fmaf(p, z, -1.390862912e-01f);
+    p = fmaf(p, z, 1.994656622e-01f);
+    p = fmaf(p, z, -3.332985938e-01f);
+    p = fmaf(p, z, 9.999993443e-01f);
+    float a = t * p;
+    a = (S > ax) ? (1.57079632679489662f - a) : a;
+    return (C < 0.0f) ? (3.14159265358979324f - a) : a;
+}
+
+// Outcome of one site update.
 struct SiteNew {
-    float phi, c, s;
+    float phi;      // new angle
+    float dE;       // energy change of the Metropolis move (0 when rejected)
+    float co, so;   // cos, sin of q * old angle
+    float ca, sa;   // cos, sin of q * angle after the Metropolis move
+    bool refl;      // over-relaxation applied
 };
 
 // Metropolis with an independent uniform proposal on [0, 2pi] at inverse
@@ -47,36 +73,44 @@ struct SiteNew {
 // reflection of q*phi about psi = atan2(S, C), kept when it lands in
 // [0, 2pi]. (C, S) is the neighbour field sum_j (cos q phi_j, sin q phi_j);
 // the site energy is -J (C cos q phi + S sin q phi), so
-// dE = J [(C co + S so) - (C cp + S sp)].
+// dE = J [(C co + S so) - (C cp + S sp)]; the reflection conserves it.
 __device__ __forceinline__ SiteNew site_update(float phi, float C, float S, float u0, float u1,
                                                float beta, const Model& m) {
-    float so, co, sp, cp;
-    __sincosf(m.q * phi, &so, &co);
-    const float php = kTwoPi * u0;
-    __sincosf(m.q * php, &sp, &cp);
-    const float dE = m.J * ((C * co + S * so) - (C * cp + S * sp));
-    const bool acc = (dE <= 0.0f) || (u1 < __expf(-dE * beta));
     SiteNew n;
+    __sincosf(m.q * phi, &n.so, &n.co);
+    const float php = kTwoPi * u0;
+    float sp, cp;
+    __sincosf(m.q * php, &sp, &cp);
+    const float dE = m.J * ((C * n.co + S * n.so) - (C * cp + S * sp));
+    const bool acc = (dE <= 0.0f) || (u1 < __expf(-dE * beta));
     n.phi = acc ? php : phi;
-    n.c = acc ? cp : co;
-    n.s = acc ? sp : so;
-    if (m.overrelax && (C != 0.0f || S != 0.0f)) {
-        const float psi = atan2f(S, C);
-        const float por = (2.0f * psi - m.q * n.phi) * m.inv_q;
-        if (por >= 0.0f && por <= kTwoPi) {
-            // cos/sin of 2 psi from (C, S): no transcendental needed.
-            const float r2 = C * C + S * S;
-            const float ir2 = __fdividef(1.0f, r2);
-            const float c2 = (C * C - S * S) * ir2;
-            const float s2 = 2.0f * C * S * ir2;
-            const float nc = c2 * n.c + s2 * n.s;
-            const float ns = s2 * n.c - c2 * n.s;
-            n.phi = por;
-            n.c = nc;
-            n.s = ns;
-        }
-    }
+    n.dE = acc ? dE : 0.0f;
+    n.ca = acc ? cp : n.co;
+    n.sa = acc ? sp : n.so;
+    // Over-relaxation, without branches. The reflected angle (2 psi - q phi)/q
+    // is >= 0 only if psi >= 0, i.e. S >= 0, so psi is taken from (|S|, C) and
+    // the move is kept only when S >= 0 and the angle lies in [0, 2pi]
+    // (C = S = 0 gives NaN and fails the test).
+    const float psi = atan2_upper(fabsf(S), C);
+    const float por = (2.0f * psi - m.q * n.phi) * m.inv_q;
+    n.refl = m.overrelax && S >= 0.0f && por >= 0.0f && por <= kTwoPi;
+    n.phi = n.refl ? por : n.phi;
     return n;
+}
+
+// cos / sin of q times the final angle: after a reflection,
+// q phi'' = 2 psi - q phi_a with cos 2psi = (C^2 - S^2)/R^2, sin 2psi = 2CS/R^2.
+__device__ __forceinline__ void final_cs(const SiteNew& n, float C, float S, float& c, float& s) {
+    if (n.refl) {
+        const float ir2 = __fdividef(1.0f, C * C + S * S);
+        const float c2 = (C * C - S * S) * ir2;
+        const float s2 = 2.0f * C * S * ir2;
+        c = c2 * n.ca + s2 * n.sa;
+        s = s2 * n.ca - c2 * n.sa;
+    } else {
+        c = n.ca;
+        s = n.sa;
+    }
 }
 
 }  // namespace mpr

@@ -9,8 +9,8 @@
 //   ang    [groups][2][H][Wh][G]  gap angles of the batch: realization
 //                             r = group * G + lane lives in lane r % G of group
 //                             r / G; sample entries are never read or written
-//   eacc   [nblk][Rp] double  per-sweep sums of the bond energies that involve a
-//                             gap site, owned by each block (Rp = groups * G)
+//   eacc   [nblk][Rp] float   per-sweep energy change of each block (Rp = groups * G)
+//   ecur   [nblk][Rp] double  current block energy E_b
 //   running[nblk][Rp] uint8   1 while block b of realization r still sweeps
 // Wh = ceil(W/2); site (y,x) of colour c = (x+y)&1 sits at half index x >> 1.
 #pragma once
@@ -48,7 +48,21 @@ struct Model {
     int overrelax;
 };
 
-// One half-step over the gap sites of one colour, all realizations of a batch.
+// Device-resident loop state of a batch. Kernels read the sweep index, the
+// random-stream tag and the worklist size from here, so a captured CUDA
+// graph replays sweeps without new launch parameters.
+struct Control {
+    uint32_t t;                  // sweep index of the sweep in progress
+    uint32_t tag;                // random-stream tag (0 realizations, 1 + k calibration)
+    uint32_t k;                  // calibration iteration
+    uint32_t n_work;             // items in the worklist read by this sweep
+    uint32_t n_work_next;        // items appended by the stop test for the next sweep
+    uint32_t energy_dirty;       // state was overwritten: energies must be recomputed
+    unsigned long long n_running;  // running (block, realization) pairs after the last stop test
+};
+
+// One half-step over the gap sites of one colour, for every running
+// (block, lane group) item.
 struct SweepArgs {
     Geom g;
     Model m;
@@ -56,16 +70,18 @@ struct SweepArgs {
     int colour;
     const uint2* list;        // gap entries of this colour
     const int32_t* start;     // [nblk + 1]
-    float* ang;               // batch state (float storage)
+    const int32_t* split;     // [nblk] end of each block's edge entries
+    float* ang;               // batch state [groups][2][H][Wh][G]
     const float2* dcs;        // [2][H][Wh]
     const float* beta;        // [nblk] 1 / T_b
-    const uint8_t* running;   // [nblk][Rp] or nullptr (= every block runs)
-    double* eacc;             // [nblk][Rp]
-    int R, Rp, groups;        // realizations in the batch, padded count, lane groups
-    uint32_t r_base;          // global index of batch realization 0 (random stream)
-    uint32_t t, tag;          // sweep index and stream tag
-    int update;               // 0: bond energies only, no move
-    int energy;               // accumulate bond energies into eacc
+    const uint8_t* running;   // [nblk][Rp] or nullptr (= every lane r < R runs)
+    float* eacc;              // [nblk][Rp] energy change of this sweep (moves)
+    double* ecur;             // [nblk][Rp] E_b (the energy pass adds into it)
+    const uint32_t* work;     // worklist of items b * groups + group, or nullptr = all items
+    const Control* ctl;
+    int R, Rp, groups;        // realizations in the batch, padded lanes, lane groups
+    uint32_t r_base;          // global index of lane 0 (even)
+    int energy;               // 1: accumulate energy increments of the moves
 };
 
 }  // namespace mpr

@@ -177,11 +177,15 @@ __global__ void k_scan_counts(const int32_t* __restrict__ cnt, int n, int32_t* _
     if (t == 1023) out[n] = (int32_t)part[1023];
 }
 
-// One warp per block: write the gap entries of both colours in row-major
-// order into the block's list segments (ballot-based stable compaction).
+// One warp per block: write the gap entries of both colours into the block's
+// list segments, ballot-compacted: first the sites whose left or up bond
+// belongs to a neighbouring block (block edge), then the others, each group
+// in row-major order. Keeping the edge sites together lets most warps of the
+// sweep skip the per-bond energy split.
 __global__ void k_build_lists(Geom g, const uint8_t* __restrict__ mask,
                               const int32_t* __restrict__ start0, const int32_t* __restrict__ start1,
-                              uint2* __restrict__ list0, uint2* __restrict__ list1) {
+                              uint2* __restrict__ list0, uint2* __restrict__ list1,
+                              int32_t* __restrict__ split0, int32_t* __restrict__ split1) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= g.nblk) return;
@@ -191,35 +195,42 @@ __global__ void k_build_lists(Geom g, const uint8_t* __restrict__ mask,
     const int y1 = min(g.H, y0 + g.lb), x1 = min(g.W, x0 + g.lb);
     const int bw = x1 - x0, nsite = (y1 - y0) * bw;
     int o0 = start0[b], o1 = start1[b];
-    for (int j0 = 0; j0 < nsite; j0 += 32) {
-        const int j = j0 + lane;
-        bool gap = false;
-        int y = 0, x = 0, c = 0;
-        if (j < nsite) {
-            y = y0 + j / bw;
-            x = x0 + j % bw;
-            gap = mask[(int64_t)y * g.W + x] != 0;
-            c = (x + y) & 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int j0 = 0; j0 < nsite; j0 += 32) {
+            const int j = j0 + lane;
+            bool take = false;
+            int y = 0, x = 0, c = 0;
+            if (j < nsite) {
+                y = y0 + j / bw;
+                x = x0 + j % bw;
+                const bool edge = (x > 0 && x == x0) || (y > 0 && y == y0);
+                take = mask[(int64_t)y * g.W + x] != 0 && edge == (pass == 0);
+                c = (x + y) & 1;
+            }
+            const unsigned m0 = __ballot_sync(0xffffffffu, take && c == 0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, take && c == 1);
+            if (take) {
+                const int64_t i = (int64_t)y * g.W + x;
+                uint32_t f = 0;
+                if (x > 0) { f |= NB_L; if (mask[i - 1]) f |= GAP_L; }
+                if (x + 1 < g.W) { f |= NB_R; if (mask[i + 1]) f |= GAP_R; }
+                if (y > 0) { f |= NB_U; if (mask[i - g.W]) f |= GAP_U; }
+                if (y + 1 < g.H) { f |= NB_D; if (mask[i + g.W]) f |= GAP_D; }
+                if (x > 0 && x == x0) f |= EDGE_L;
+                if (y > 0 && y == y0) f |= EDGE_U;
+                const uint2 e = make_uint2(((uint32_t)y << 16) | (uint32_t)x,
+                                           ((uint32_t)b << META_SHIFT) | f);
+                const unsigned below = (1u << lane) - 1u;
+                if (c == 0) list0[o0 + __popc(m0 & below)] = e;
+                else list1[o1 + __popc(m1 & below)] = e;
+            }
+            o0 += __popc(m0);
+            o1 += __popc(m1);
         }
-        const unsigned m0 = __ballot_sync(0xffffffffu, gap && c == 0);
-        const unsigned m1 = __ballot_sync(0xffffffffu, gap && c == 1);
-        if (gap) {
-            const int64_t i = (int64_t)y * g.W + x;
-            uint32_t f = 0;
-            if (x > 0) { f |= NB_L; if (mask[i - 1]) f |= GAP_L; }
-            if (x + 1 < g.W) { f |= NB_R; if (mask[i + 1]) f |= GAP_R; }
-            if (y > 0) { f |= NB_U; if (mask[i - g.W]) f |= GAP_U; }
-            if (y + 1 < g.H) { f |= NB_D; if (mask[i + g.W]) f |= GAP_D; }
-            if (x > 0 && x % g.lb == 0) f |= EDGE_L;
-            if (y > 0 && y % g.lb == 0) f |= EDGE_U;
-            const uint2 e = make_uint2(((uint32_t)y << 16) | (uint32_t)x,
-                                       ((uint32_t)b << META_SHIFT) | f);
-            const unsigned below = (1u << lane) - 1u;
-            if (c == 0) list0[o0 + __popc(m0 & below)] = e;
-            else list1[o1 + __popc(m1 & below)] = e;
+        if (pass == 0 && lane == 0) {
+            split0[b] = o0;   // end of the block's edge entries
+            split1[b] = o1;
         }
-        o0 += __popc(m0);
-        o1 += __popc(m1);
     }
 }
 
@@ -252,190 +263,385 @@ __global__ void k_init(Geom g, const uint2* __restrict__ list, int64_t n_list, i
     }
 }
 
-// ----------------------------------------------------------------- sweep --
-// One checkerboard half-step. A warp owns one (block, lane-group) work item
-// and walks the block's list of gap sites of the colour; lane = slot * G +
-// realization lane. With G >= 2 each lane pair (realizations 2m, 2m+1)
-// shares Philox blocks: the even lane draws for site A, the odd lane for
-// site B, and the two swap the halves they do not own.
-//
-// Bond energies for the stop test are summed here. A bond always joins a
-// colour-0 and a colour-1 site; the colour-1 half-step adds every bond of its
-// gap sites (their colour-0 partners are final for the sweep); the colour-0
-// half-step adds the bonds of its gap sites to sample neighbours (those
-// partners never move). Bonds between two samples are the constant E_s,b.
-// A bond is owned by the block of its left / upper site.
-template <int G>
-__global__ void __launch_bounds__(256) k_halfstep(SweepArgs a) {
-    constexpr int S = 32 / G;                 // list slots per warp pass
-    constexpr int PER = (G >= 2) ? 2 : 1;     // entries per slot per pass
-    const int lane = threadIdx.x & 31;
-    const int gl = lane % G;
-    const int slot = lane / G;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    const int n_items = a.g.nblk * a.groups;
-    const int c = a.colour, co = c ^ 1;
-    const size_t plane = (size_t)a.g.H * a.g.Wh;
-    const uint32_t ctr1 = a.t | (a.tag << 16);
-
-    for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_items;
-         item += warps) {
-        const int b = item / a.groups;
-        const int grp = item - b * a.groups;
-        const int e0 = a.start[b], e1 = a.start[b + 1];
-        if (e0 == e1) continue;
-        const int rl = grp * G + gl;                     // lane realization in the batch
-        bool run_own = true, run_l = false, run_u = false;
-        if (a.running) {
-            run_own = a.running[(size_t)b * a.Rp + rl] != 0;
-            if (a.energy) {
-                const int bx = b % a.g.nbx;
-                run_l = bx > 0 && a.running[(size_t)(b - 1) * a.Rp + rl] != 0;
-                run_u = b >= a.g.nbx && a.running[(size_t)(b - a.g.nbx) * a.Rp + rl] != 0;
-            }
-        } else {
-            run_own = rl < a.R;
-            run_l = run_own && a.energy && (b % a.g.nbx) > 0;
-            run_u = run_own && a.energy && b >= a.g.nbx;
-        }
-        if (!__any_sync(0xffffffffu, run_own || run_l || run_u)) continue;
-        const bool move = a.update && run_own;
-        float* own = a.ang + (size_t)(grp * 2 + c) * plane * G;
-        const float* oth = a.ang + (size_t)(grp * 2 + co) * plane * G;
-        const float2* dco = a.dcs + (size_t)co * plane;
-        const float beta = a.beta[b];
-        const uint32_t rg = a.r_base + (uint32_t)rl;   // global realization index
-        double d_own = 0.0;
-        float f_own = 0.0f, f_l = 0.0f, f_u = 0.0f;
-        int fold = 0;
-
-        for (int base = e0; base < e1; base += S * PER) {
-            uint2 ent[PER];
-            bool val[PER];
-#pragma unroll
-            for (int p = 0; p < PER; ++p) {
-                const int e = base + slot * PER + p;
-                val[p] = e < e1;
-                ent[p] = val[p] ? a.list[e] : make_uint2(0u, 0u);
-            }
-            // Random numbers: words (2(r&1), 2(r&1)+1) of the block for
-            // counter (site, t | tag << 16, r >> 1, 0).
-            float u0[PER], u1[PER];
-            if (a.update) {
-                if constexpr (G >= 2) {
-                    const bool odd = (gl & 1) != 0;
-                    const uint2 mine = odd ? ent[1] : ent[0];
-                    const uint32_t site = (mine.x >> 16) * (uint32_t)a.g.W + (mine.x & 0xffffu);
-                    uint32_t w[4];
-                    philox4x32_10(site, ctr1, rg >> 1, 0u, a.rng.key0, a.rng.key1, w);
-                    const uint32_t sx = odd ? w[0] : w[2];
-                    const uint32_t sy = odd ? w[1] : w[3];
-                    const uint32_t rx = __shfl_xor_sync(0xffffffffu, sx, 1);
-                    const uint32_t ry = __shfl_xor_sync(0xffffffffu, sy, 1);
-                    // even: A = (w0, w1) own, B = (rx, ry); odd: A = (rx, ry), B = (w2, w3)
-                    u0[0] = u01(odd ? rx : w[0]);
-                    u1[0] = u01(odd ? ry : w[1]);
-                    u0[1] = u01(odd ? w[2] : rx);
-                    u1[1] = u01(odd ? w[3] : ry);
-                } else {
-                    const uint32_t site = (ent[0].x >> 16) * (uint32_t)a.g.W + (ent[0].x & 0xffffu);
-                    uint32_t w[4];
-                    philox4x32_10(site, ctr1, rg >> 1, 0u, a.rng.key0, a.rng.key1, w);
-                    const int o = (rg & 1u) * 2;
-                    u0[0] = u01(o ? w[2] : w[0]);
-                    u1[0] = u01(o ? w[3] : w[1]);
-                }
-            }
-#pragma unroll
-            for (int p = 0; p < PER; ++p) {
-                if (!val[p]) continue;
-                const int y = ent[p].x >> 16, x = ent[p].x & 0xffff;
-                const uint32_t f = ent[p].y;
-                const size_t hs = (size_t)y * a.g.Wh + (x >> 1);
-                // Neighbour field and, per neighbour, (cos, sin) of q*phi_j.
-                float nc[4], ns[4];
-                const int ny[4] = {y, y, y - 1, y + 1};
-                const int nx[4] = {x - 1, x + 1, x, x};
-#pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    nc[d] = 0.0f;
-                    ns[d] = 0.0f;
-                    if (f & (NB_L << d)) {
-                        const size_t hn = (size_t)ny[d] * a.g.Wh + (nx[d] >> 1);
-                        if (f & (GAP_L << d)) {
-                            const float pj = oth[hn * G + gl];
-                            __sincosf(a.m.q * pj, &ns[d], &nc[d]);
-                        } else {
-                            const float2 cs = __ldg(&dco[hn]);
-                            nc[d] = cs.x;
-                            ns[d] = cs.y;
-                        }
-                    }
-                }
-                const float C = (nc[0] + nc[1]) + (nc[2] + nc[3]);
-                const float Sg = (ns[0] + ns[1]) + (ns[2] + ns[3]);
-                const float phi = own[hs * G + gl];
-                float cn, sn;
-                if (move) {
-                    const SiteNew n = site_update(phi, C, Sg, u0[p], u1[p], beta, a.m);
-                    own[hs * G + gl] = n.phi;
-                    cn = n.c;
-                    sn = n.s;
-                } else {
-                    __sincosf(a.m.q * phi, &sn, &cn);
-                }
-                if (a.energy) {
-                    // colour 1: every bond; colour 0: bonds to sample neighbours.
-                    const uint32_t take = (c == 1) ? 0xFu : (~(f >> 4) & 0xFu);
-                    float eb[4];
-#pragma unroll
-                    for (int d = 0; d < 4; ++d)
-                        eb[d] = ((f & (NB_L << d)) && (take & (1u << d)))
-                                    ? -a.m.J * (cn * nc[d] + sn * ns[d])
-                                    : 0.0f;
-                    // right and down are always owned by b; left / up by b only
-                    // inside the block.
-                    f_own += eb[1] + eb[3];
-                    if (f & EDGE_L) f_l += eb[0]; else f_own += eb[0];
-                    if (f & EDGE_U) f_u += eb[2]; else f_own += eb[2];
-                }
-            }
-            if (a.energy && ++fold == 8) {
-                d_own += (double)f_own;
-                f_own = 0.0f;
-                fold = 0;
-            }
-        }
-        if (a.energy) {
-            d_own += (double)f_own;
-            double d_l = (double)f_l, d_u = (double)f_u;
-            // Sum over the slots that share a realization lane.
-#pragma unroll
-            for (int d = G; d < 32; d <<= 1) {
-                d_own += __shfl_xor_sync(0xffffffffu, d_own, d);
-                d_l += __shfl_xor_sync(0xffffffffu, d_l, d);
-                d_u += __shfl_xor_sync(0xffffffffu, d_u, d);
-            }
-            if (slot == 0 && rl < a.Rp) {
-                if (run_own) atomicAdd(&a.eacc[(size_t)b * a.Rp + rl], d_own);
-                if (run_l && d_l != 0.0) atomicAdd(&a.eacc[(size_t)(b - 1) * a.Rp + rl], d_l);
-                if (run_u && d_u != 0.0)
-                    atomicAdd(&a.eacc[(size_t)(b - a.g.nbx) * a.Rp + rl], d_u);
-            }
-        }
+// Sample angles copied into every lane of the batch state, so that a
+// neighbour read is the same load whether the neighbour is a gap or a sample.
+__global__ void k_fill_samples(Geom g, const uint8_t* __restrict__ mask,
+                               const float* __restrict__ dang, float* __restrict__ ang, int G,
+                               int groups) {
+    const int64_t n = (int64_t)g.H * g.W;
+    const size_t plane = (size_t)g.H * g.Wh;
+    const int64_t total = n * groups;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t % n;
+        const int grp = (int)(t / n);
+        if (mask[i]) continue;
+        const int y = (int)(i / g.W), x = (int)(i % g.W);
+        const int c = (x + y) & 1;
+        const size_t hs = (size_t)y * g.Wh + (x >> 1);
+        const float v = dang[(size_t)c * plane + hs];
+        float* dst = ang + ((size_t)(grp * 2 + c) * plane + hs) * G;
+        for (int l = 0; l < G; ++l) dst[l] = v;
     }
 }
 
-template __global__ void k_halfstep<1>(SweepArgs);
-template __global__ void k_halfstep<8>(SweepArgs);
-template __global__ void k_halfstep<32>(SweepArgs);
+// ----------------------------------------------------------------- sweep --
+// One checkerboard half-step (Sec. 2.2.2) over the running (block, lane
+// group) items of a batch. The state interleaves G realizations per site; a
+// CTA of four warps takes one item, warp w handles the realization pair
+// (group * G + 2q, + 1), q = w mod G/2, and its 32 lanes walk the block's
+// list of gap sites 32 at a time (warps sharing a pair split the list). Each
+// lane updates its site in both realizations of the pair from one Philox
+// block: words 0, 1 for the even realization, 2, 3 for the odd one.
+//
+// Block energies are kept incrementally: a Metropolis move changes the
+// energy of the site's four bonds by dE and the reflection conserves it, so a
+// site whose bonds all belong to its own block adds dE there. A site on the
+// left or top edge of its block splits the change bond by bond, because its
+// left / up bond belongs to the neighbouring block (a bond is owned by the
+// block of its left / upper site). Frozen sites never move, so stopped
+// (block, realization) pairs cost nothing.
+namespace {
+
+__device__ __forceinline__ void add_energy(const SiteNew& n, uint32_t f, float C, float S,
+                                           const float* nc, const float* ns, float J, float& ao,
+                                           float& al, float& au) {
+    if (!(f & (EDGE_L | EDGE_U))) {
+        ao += n.dE;
+        return;
+    }
+    float cn, sn;
+    final_cs(n, C, S, cn, sn);
+    const float dc = cn - n.co, ds = sn - n.so;
+    const float dl = -J * (dc * nc[0] + ds * ns[0]);
+    const float dr = -J * (dc * nc[1] + ds * ns[1]);
+    const float du = -J * (dc * nc[2] + ds * ns[2]);
+    const float dd = -J * (dc * nc[3] + ds * ns[3]);
+    ao += dr + dd;
+    if (f & EDGE_L) al += dl; else ao += dl;
+    if (f & EDGE_U) au += du; else ao += du;
+}
+
+// Interior sites: only the block's own change.
+__device__ __forceinline__ void flush_own(const SweepArgs& a, int b, int rl, float ao0, float ao1) {
+    if (!__any_sync(0xffffffffu, ao0 != 0.0f || ao1 != 0.0f)) return;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
+        ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
+    }
+    if ((threadIdx.x & 31) != 0) return;
+    float* ea = a.eacc + (size_t)b * a.Rp + rl;
+    if (ao0 != 0.0f) atomicAdd(ea, ao0);
+    if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
+}
+
+// The same for the from-scratch energies, in FP64 into the block energies.
+__device__ __forceinline__ void flush_energy64(const SweepArgs& a, int b, int rl, double ao0,
+                                               double ao1, double al0, double al1, double au0,
+                                               double au1) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
+        ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
+        al0 += __shfl_xor_sync(0xffffffffu, al0, s);
+        al1 += __shfl_xor_sync(0xffffffffu, al1, s);
+        au0 += __shfl_xor_sync(0xffffffffu, au0, s);
+        au1 += __shfl_xor_sync(0xffffffffu, au1, s);
+    }
+    if ((threadIdx.x & 31) != 0) return;
+    double* ea = a.ecur + (size_t)b * a.Rp + rl;
+    if (ao0 != 0.0) atomicAdd(ea, ao0);
+    if (ao1 != 0.0) atomicAdd(ea + 1, ao1);
+    if (al0 != 0.0) atomicAdd(ea - a.Rp, al0);
+    if (al1 != 0.0) atomicAdd(ea - a.Rp + 1, al1);
+    const size_t up = (size_t)a.g.nbx * a.Rp;
+    if (au0 != 0.0) atomicAdd(ea - up, au0);
+    if (au1 != 0.0) atomicAdd(ea - up + 1, au1);
+}
+
+// (cos, sin) of q * phi_j of the four neighbours in both realizations. The
+// state holds sample angles too, so every neighbour is one 8-byte load and a
+// sin/cos pair per realization; a neighbour outside the grid is masked out.
+__device__ __forceinline__ void neighbour_field(const SweepArgs& a, const float2* __restrict__ oth,
+                                                int NP, uint32_t hs, int x, uint32_t f, float* nc0,
+                                                float* ns0, float* nc1, float* ns1) {
+    const uint32_t o = (uint32_t)(x & 1);
+    const uint32_t hn[4] = {hs + o - 1u, hs + o, hs - (uint32_t)a.g.Wh, hs + (uint32_t)a.g.Wh};
+    float2 v[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const bool ex = (f & (NB_L << d)) != 0;
+        v[d] = ex ? oth[(size_t)hn[d] * NP] : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const float m = (f & (NB_L << d)) ? 1.0f : 0.0f;
+        float s0, c0, s1, c1;
+        __sincosf(a.m.q * v[d].x, &s0, &c0);
+        __sincosf(a.m.q * v[d].y, &s1, &c1);
+        nc0[d] = m * c0;
+        ns0[d] = m * s0;
+        nc1[d] = m * c1;
+        ns1[d] = m * s1;
+    }
+}
+
+}  // namespace
+
+// Interior sites of each block (the segment after its edge entries): every
+// bond of the site belongs to the block, so the block's energy changes by the
+// Metropolis dE (the reflection conserves it).
+template <int G>
+__global__ void __launch_bounds__(128) k_sweep(SweepArgs a) {
+    constexpr int NP = G / 2;        // realization pairs per lane group
+    constexpr int CW = 4 / NP;       // warps sharing one pair
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp % NP, cw = warp / NP;
+    const uint32_t ctr1 = a.ctl->t | (a.ctl->tag << 16);
+    const int n_items = a.work ? (int)a.ctl->n_work : a.g.nblk * a.groups;
+    const size_t plane = (size_t)a.g.H * a.g.Wh;
+    const int c = a.colour, co = c ^ 1;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int item = a.work ? (int)a.work[it] : it;
+        const int b = item / a.groups, grp = item - b * a.groups;
+        const int e0 = a.split[b], e1 = a.start[b + 1];
+        if (e0 >= e1) continue;
+        const int rl = grp * G + 2 * q;
+        bool run0, run1;
+        if (a.running) {
+            run0 = a.running[(size_t)b * a.Rp + rl] != 0;
+            run1 = a.running[(size_t)b * a.Rp + rl + 1] != 0;
+        } else {
+            run0 = rl < a.R;
+            run1 = rl + 1 < a.R;
+        }
+        if (!(run0 || run1)) continue;
+        float2* own = reinterpret_cast<float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
+        const float2* oth =
+            reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
+        const float beta = a.beta[b];
+        const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
+        float ao0 = 0.f, ao1 = 0.f;
+        for (int e = e0 + cw * 32 + lane; e < e1; e += CW * 32) {
+            const uint2 en = a.list[e];
+            const int y = en.x >> 16, x = en.x & 0xffff;
+            const uint32_t f = en.y;
+            const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
+            uint32_t w[4];
+            philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)x, ctr1, rpair, 0u,
+                          a.rng.key0, a.rng.key1, w);
+            const float2 ph = own[(size_t)hs * NP];
+            float nc0[4], ns0[4], nc1[4], ns1[4];
+            neighbour_field(a, oth, NP, hs, x, f, nc0, ns0, nc1, ns1);
+            const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
+            const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
+            const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
+            const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
+            float2 out = ph;
+            if (run0) {
+                const SiteNew n = site_update(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
+                out.x = n.phi;
+                ao0 += n.dE;
+            }
+            if (run1) {
+                const SiteNew n = site_update(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
+                out.y = n.phi;
+                ao1 += n.dE;
+            }
+            own[(size_t)hs * NP] = out;
+        }
+        if (a.energy) flush_own(a, b, rl, ao0, ao1);
+    }
+}
+
+// Edge sites of each block (left / top edge: the left / up bond belongs to
+// the neighbouring block, so the energy change is split bond by bond). A
+// block has few of them, so one warp takes a whole (block, lane group) item:
+// lane = entry slot * (G/2) + pair, i.e. 32/(G/2) entries times all pairs per
+// pass, and one site's G realizations are read as one contiguous chunk.
+template <int G>
+__global__ void __launch_bounds__(128) k_sweep_edge(SweepArgs a) {
+    constexpr int NP = G / 2;
+    constexpr int EPI = 32 / NP;     // entries per warp pass
+    const int lane = threadIdx.x & 31;
+    const int q = lane % NP, el = lane / NP;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
+    const uint32_t ctr1 = a.ctl->t | (a.ctl->tag << 16);
+    const int n_items = a.work ? (int)a.ctl->n_work : a.g.nblk * a.groups;
+    const size_t plane = (size_t)a.g.H * a.g.Wh;
+    const int c = a.colour, co = c ^ 1;
+    for (int it = blockIdx.x * wpb + (threadIdx.x >> 5); it < n_items; it += nwarps) {
+        const int item = a.work ? (int)a.work[it] : it;
+        const int b = item / a.groups, grp = item - b * a.groups;
+        const int e0 = a.start[b], e1 = a.split[b];
+        if (e0 >= e1) continue;
+        const int rl = grp * G + 2 * q;
+        bool run0, run1;
+        if (a.running) {
+            run0 = a.running[(size_t)b * a.Rp + rl] != 0;
+            run1 = a.running[(size_t)b * a.Rp + rl + 1] != 0;
+        } else {
+            run0 = rl < a.R;
+            run1 = rl + 1 < a.R;
+        }
+        if (!__any_sync(0xffffffffu, run0 || run1)) continue;
+        float2* own = reinterpret_cast<float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
+        const float2* oth =
+            reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
+        const float beta = a.beta[b];
+        const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
+        float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
+        for (int base = e0; base < e1; base += EPI) {
+            const int e = base + el;
+            if (e >= e1 || !(run0 || run1)) continue;
+            const uint2 en = a.list[e];
+            const int y = en.x >> 16, x = en.x & 0xffff;
+            const uint32_t f = en.y;
+            const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
+            uint32_t w[4];
+            philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)x, ctr1, rpair, 0u,
+                          a.rng.key0, a.rng.key1, w);
+            const float2 ph = own[(size_t)hs * NP];
+            float nc0[4], ns0[4], nc1[4], ns1[4];
+            neighbour_field(a, oth, NP, hs, x, f, nc0, ns0, nc1, ns1);
+            const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
+            const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
+            const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
+            const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
+            float2 out = ph;
+            if (run0) {
+                const SiteNew n = site_update(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
+                out.x = n.phi;
+                add_energy(n, f, C0, S0, nc0, ns0, a.m.J, ao0, al0, au0);
+            }
+            if (run1) {
+                const SiteNew n = site_update(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
+                out.y = n.phi;
+                add_energy(n, f, C1, S1, nc1, ns1, a.m.J, ao1, al1, au1);
+            }
+            own[(size_t)hs * NP] = out;
+        }
+        if (!a.energy) continue;
+        // Sum over the entry slots of each pair, then the slot-0 lane of each
+        // pair adds to the blocks.
+#pragma unroll
+        for (int s = NP; s < 32; s <<= 1) {
+            ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
+            ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
+            al0 += __shfl_xor_sync(0xffffffffu, al0, s);
+            al1 += __shfl_xor_sync(0xffffffffu, al1, s);
+            au0 += __shfl_xor_sync(0xffffffffu, au0, s);
+            au1 += __shfl_xor_sync(0xffffffffu, au1, s);
+        }
+        if (el != 0) continue;
+        float* ea = a.eacc + (size_t)b * a.Rp + rl;
+        if (ao0 != 0.0f) atomicAdd(ea, ao0);
+        if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
+        if (al0 != 0.0f) atomicAdd(ea - a.Rp, al0);
+        if (al1 != 0.0f) atomicAdd(ea - a.Rp + 1, al1);
+        const size_t up = (size_t)a.g.nbx * a.Rp;
+        if (au0 != 0.0f) atomicAdd(ea - up, au0);
+        if (au1 != 0.0f) atomicAdd(ea - up + 1, au1);
+    }
+}
+
+// Energies from scratch (no move): every bond that touches a gap site, once.
+// A bond always joins a colour-0 and a colour-1 site; colour 1 adds every
+// bond of its gap sites, colour 0 the bonds of its gap sites to samples.
+// Bonds between two samples are the constant E_s,b.
+template <int G>
+__global__ void __launch_bounds__(128) k_energy(SweepArgs a) {
+    constexpr int NP = G / 2;
+    constexpr int CW = 4 / NP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp % NP, cw = warp / NP;
+    const int n_items = a.g.nblk * a.groups;
+    const size_t plane = (size_t)a.g.H * a.g.Wh;
+    const int c = a.colour, co = c ^ 1;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int b = it / a.groups, grp = it - b * a.groups;
+        const int rl = grp * G + 2 * q;
+        bool run0, run1;
+        if (a.running) {
+            run0 = a.running[(size_t)b * a.Rp + rl] != 0;
+            run1 = a.running[(size_t)b * a.Rp + rl + 1] != 0;
+        } else {
+            run0 = rl < a.R;
+            run1 = rl + 1 < a.R;
+        }
+        if (!(run0 || run1)) continue;
+        const int e0 = a.start[b], e1 = a.start[b + 1];
+        const float2* own =
+            reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
+        const float2* oth =
+            reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
+        double ao0 = 0.0, ao1 = 0.0, al0 = 0.0, al1 = 0.0, au0 = 0.0, au1 = 0.0;
+        for (int e = e0 + cw * 32 + lane; e < e1; e += CW * 32) {
+            const uint2 en = a.list[e];
+            const int y = en.x >> 16, x = en.x & 0xffff;
+            const uint32_t f = en.y;
+            const size_t hs = (size_t)y * a.g.Wh + (x >> 1);
+            const float2 ph = own[hs * NP];
+            float nc0[4], ns0[4], nc1[4], ns1[4];
+            neighbour_field(a, oth, NP, (uint32_t)hs, x, f, nc0, ns0, nc1, ns1);
+            float s0, c0, s1, c1;
+            __sincosf(a.m.q * ph.x, &s0, &c0);
+            __sincosf(a.m.q * ph.y, &s1, &c1);
+            const uint32_t take = (c == 1) ? 0xFu : (~(f >> 4) & 0xFu);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                if (!((f & (NB_L << d)) && (take & (1u << d)))) continue;
+                const float b0 = -a.m.J * (c0 * nc0[d] + s0 * ns0[d]);
+                const float b1 = -a.m.J * (c1 * nc1[d] + s1 * ns1[d]);
+                if (d == 0 && (f & EDGE_L)) { al0 += b0; al1 += b1; }
+                else if (d == 2 && (f & EDGE_U)) { au0 += b0; au1 += b1; }
+                else { ao0 += b0; ao1 += b1; }
+            }
+        }
+        flush_energy64(a, b, rl, ao0, ao1, al0, al1, au0, au1);
+    }
+}
+
+template __global__ void k_sweep<2>(SweepArgs);
+template __global__ void k_sweep<8>(SweepArgs);
+template __global__ void k_sweep_edge<2>(SweepArgs);
+template __global__ void k_sweep_edge<8>(SweepArgs);
+template __global__ void k_energy<2>(SweepArgs);
+template __global__ void k_energy<8>(SweepArgs);
+
+// Advances the sweep index and hands the worklist built by the last stop
+// test to the sweep that starts.
+__global__ void k_tick(Control* ctl) {
+    ctl->t += 1;
+    ctl->n_work = ctl->n_work_next;
+    ctl->n_work_next = 0;
+    ctl->n_running = 0;
+}
 
 // ------------------------------------------------------------------ stop --
-// t = 0: E_b(0) = E_s,b + eacc, sigma = sign(e_s,b - e_b(0)), blocks without
-// gap sites stop at 0; counts the running targeted blocks per realization.
-__global__ void k_stop_init(int nblk, int Rp, int R, int r_off, const double* __restrict__ Es,
-                            const int32_t* __restrict__ Nsp, const int32_t* __restrict__ Nb,
-                            const int32_t* __restrict__ ngap, double* __restrict__ eacc,
+// es[b] = E_s,b / N_SP,b (0 without sample bonds) and inb[b] = 1 / N_b (0 for
+// a block that owns no bond) are computed once at create, in FP64.
+
+// E_b <- E_s,b for every (block, lane): the constant sample-sample part; the
+// energy pass then adds the bonds that touch a gap site.
+__global__ void k_ecur_reset(int nblk, int Rp, const double* __restrict__ Es,
+                             double* __restrict__ ecur, float* __restrict__ eacc) {
+    const int64_t n = (int64_t)nblk * Rp;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        ecur[t] = Es[t / Rp];
+        eacc[t] = 0.0f;
+    }
+}
+
+// t = 0: sigma = sign(e_s,b - e_b(0)), blocks without gap sites stop at 0;
+// counts the running targeted blocks of every realization. `running` holds 1
+// for the batch's lanes on entry.
+__global__ void k_stop_init(int nblk, int Rp, const double* __restrict__ es,
+                            const double* __restrict__ inb, const int32_t* __restrict__ Nsp,
+                            const int32_t* __restrict__ ngap, const double* __restrict__ ecur,
                             int8_t* __restrict__ sigma, uint8_t* __restrict__ running,
                             int32_t* __restrict__ stop, int32_t* __restrict__ tcount,
                             double* __restrict__ e_last) {
@@ -443,43 +649,43 @@ __global__ void k_stop_init(int nblk, int Rp, int R, int r_off, const double* __
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(t / Rp), r = (int)(t % Rp);
-        const bool valid = r >= r_off && r < r_off + R;
-        const double E0 = Es[b] + eacc[t];
-        eacc[t] = 0.0;
-        e_last[t] = Nb[b] > 0 ? E0 / (double)Nb[b] : 0.0;
+        const bool valid = running[t] != 0;
+        const double e0 = ecur[t] * inb[b];
+        e_last[t] = e0;
         int8_t sg = 0;
-        if (Nsp[b] > 0 && Nb[b] > 0) {
-            const double es = Es[b] / (double)Nsp[b];
-            const double e0 = E0 / (double)Nb[b];
-            sg = (int8_t)((es > e0) - (es < e0));
-        }
+        if (Nsp[b] > 0 && inb[b] > 0.0) sg = (int8_t)((es[b] > e0) - (es[b] < e0));
         sigma[t] = sg;
         const bool run = valid && ngap[b] > 0;
         running[t] = run;
-        stop[t] = valid ? (run ? -1 : 0) : 0;
+        stop[t] = run ? -1 : 0;
         if (run && Nsp[b] > 0) atomicAdd(&tcount[r], 1);
     }
 }
 
-// After sweep t, targeted blocks: stop once sigma (e_b(t) - e_s,b) >= 0.
-// e_last keeps e_b(t) of every running (block, realization) for inspection.
-__global__ void k_stop_targeted(int nblk, int Rp, int t_sweep, const double* __restrict__ Es,
-                                const int32_t* __restrict__ Nsp, const int32_t* __restrict__ Nb,
-                                double* __restrict__ eacc, const int8_t* __restrict__ sigma,
+// After sweep t: E_b += the sweep's change; targeted blocks stop once
+// sigma (e_b(t) - e_s,b) >= 0. e_last keeps e_b(t) for inspection.
+__global__ void k_stop_targeted(int nblk, int Rp, const Control* __restrict__ ctl,
+                                const double* __restrict__ es, const double* __restrict__ inb,
+                                const int32_t* __restrict__ Nsp, float* __restrict__ eacc,
+                                double* __restrict__ ecur, const int8_t* __restrict__ sigma,
                                 uint8_t* __restrict__ running, int32_t* __restrict__ stop,
                                 int32_t* __restrict__ tcount, double* __restrict__ e_last) {
     const int64_t n = (int64_t)nblk * Rp;
+    const int t_sweep = (int)ctl->t;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(t / Rp), r = (int)(t % Rp);
-        const double acc = eacc[t];
-        eacc[t] = 0.0;
+        const float acc = eacc[t];
+        if (acc != 0.0f) eacc[t] = 0.0f;
         if (!running[t]) continue;
-        const double e = Nb[b] > 0 ? (Es[b] + acc) / (double)Nb[b] : 0.0;
+        const int b = (int)(t / Rp), r = (int)(t % Rp);
+        const double E = ecur[t] + (double)acc;
+        ecur[t] = E;
+        const double e = E * inb[b];
         e_last[t] = e;
         if (Nsp[b] == 0) continue;
-        const double es = Es[b] / (double)Nsp[b];
-        if ((double)sigma[t] * (e - es) >= 0.0) {
+        const int sg = sigma[t];
+        const bool reached = sg > 0 ? (e >= es[b]) : (sg < 0 ? (e <= es[b]) : true);
+        if (reached) {
             running[t] = 0;
             stop[t] = t_sweep;
             atomicSub(&tcount[r], 1);
@@ -488,26 +694,35 @@ __global__ void k_stop_targeted(int nblk, int Rp, int t_sweep, const double* __r
 }
 
 // Blocks without sample bonds stop when no targeted block of their
-// realization runs; every block stops at n_max. Counts what still runs.
-__global__ void k_stop_rest(int nblk, int Rp, int t_sweep, int n_max,
-                            const int32_t* __restrict__ Nsp, uint8_t* __restrict__ running,
-                            int32_t* __restrict__ stop, const int32_t* __restrict__ tcount,
-                            unsigned long long* __restrict__ n_running) {
-    const int64_t n = (int64_t)nblk * Rp;
+// realization runs; every block stops at n_max. One thread per (block, lane
+// group) item: items with a running lane go on the next sweep's worklist.
+__global__ void k_stop_rest(int nblk, int groups, int G, int Rp, int n_max,
+                            Control* __restrict__ ctl, const int32_t* __restrict__ Nsp,
+                            uint8_t* __restrict__ running, int32_t* __restrict__ stop,
+                            const int32_t* __restrict__ tcount, uint32_t* __restrict__ work) {
+    const int64_t n = (int64_t)nblk * groups;
+    const int t_sweep = (int)ctl->t;
     unsigned cnt = 0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (!running[t]) continue;
-        const int b = (int)(t / Rp), r = (int)(t % Rp);
-        if ((Nsp[b] == 0 && tcount[r] == 0) || t_sweep >= n_max) {
-            running[t] = 0;
-            stop[t] = t_sweep;
-        } else {
-            ++cnt;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(it / groups), grp = (int)(it % groups);
+        bool any = false;
+        for (int g = 0; g < G; ++g) {
+            const int r = grp * G + g;
+            const size_t k = (size_t)b * Rp + r;
+            if (!running[k]) continue;
+            if ((Nsp[b] == 0 && tcount[r] == 0) || t_sweep >= n_max) {
+                running[k] = 0;
+                stop[k] = t_sweep;
+            } else {
+                ++cnt;
+                any = true;
+            }
         }
+        if (any) work[atomicAdd(&ctl->n_work_next, 1u)] = (uint32_t)it;
     }
     for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n_running, (unsigned long long)cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&ctl->n_running, (unsigned long long)cnt);
 }
 
 // Site updates run by the batch: sum over (b, r) of stop sweep x gap sites.
@@ -527,19 +742,25 @@ __global__ void k_count_updates(int nblk, int Rp, const int32_t* __restrict__ st
 
 // ----------------------------------------------------------- calibration --
 __global__ void k_cal_init(int nblk, float t_lo, float t_hi, float* __restrict__ lo,
-                           float* __restrict__ hi, double* __restrict__ ebar) {
+                           float* __restrict__ hi, double* __restrict__ ebar, Control* ctl) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
         lo[b] = t_lo;
         hi[b] = t_hi;
         ebar[b] = 0.0;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->k = 0;
 }
 
-// Targeted blocks take their bracket midpoint; others are set by k_cal_fill.
+// Targeted blocks take their bracket midpoint (others: k_cal_fill); starts
+// iteration ctl->k: random-stream tag 1 + k, sweep counter 0.
 __global__ void k_cal_mid(int nblk, const int32_t* __restrict__ Nsp, const float* __restrict__ lo,
-                          const float* __restrict__ hi, float* __restrict__ T) {
+                          const float* __restrict__ hi, float* __restrict__ T, Control* ctl) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x)
         T[b] = Nsp[b] > 0 ? 0.5f * (lo[b] + hi[b]) : 0.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->tag = 1u + ctl->k;
+        ctl->t = 0;
+    }
 }
 
 // Median of the targeted blocks' T by a single-CTA radix select on the
@@ -586,10 +807,10 @@ __global__ void k_cal_fill(int nblk, const int32_t* __restrict__ Nsp, float* __r
     const uint32_t n = s_n;
     float med = 0.0f;
     if (n > 0) {
-        const float a = __uint_as_float(select_kth(T, Nsp, nblk, (n - 1) / 2, hist, &s_digit, &s_k));
-        const float b = (n & 1) ? a
-                                : __uint_as_float(select_kth(T, Nsp, nblk, n / 2, hist, &s_digit, &s_k));
-        med = 0.5f * (a + b);
+        const float lo = __uint_as_float(select_kth(T, Nsp, nblk, (n - 1) / 2, hist, &s_digit, &s_k));
+        const float hi = (n & 1) ? lo
+                                 : __uint_as_float(select_kth(T, Nsp, nblk, n / 2, hist, &s_digit, &s_k));
+        med = 0.5f * (lo + hi);
     }
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         float tb = T[b];
@@ -601,33 +822,43 @@ __global__ void k_cal_fill(int nblk, const int32_t* __restrict__ Nsp, float* __r
     }
 }
 
-// After a measured sweep: e_b summed over the chains of the batch.
-__global__ void k_cal_measure(int nblk, int Rp, int chains, const double* __restrict__ Es,
-                              const int32_t* __restrict__ Nb, double* __restrict__ eacc,
-                              double* __restrict__ ebar) {
+// After calibration sweep t: fold the sweep's change into E_b; past n_eq
+// sweeps add e_b of every chain to the running sum.
+__global__ void k_cal_step(int nblk, int Rp, int chains, int n_eq, const Control* __restrict__ ctl,
+                           const double* __restrict__ inb, float* __restrict__ eacc,
+                           double* __restrict__ ecur, double* __restrict__ ebar) {
+    const bool measure = (int)ctl->t > n_eq;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int r = 0; r < chains; ++r) {
-            const double acc = eacc[(size_t)b * Rp + r];
-            eacc[(size_t)b * Rp + r] = 0.0;
-            if (Nb[b] > 0) s += (Es[b] + acc) / (double)Nb[b];
+            const size_t k = (size_t)b * Rp + r;
+            const double E = ecur[k] + (double)eacc[k];
+            ecur[k] = E;
+            eacc[k] = 0.0f;
+            s += E * inb[b];
         }
-        ebar[b] += s;
+        if (measure) ebar[b] += s;
     }
 }
 
 // Bisection step: <e_b> increases with T, so keep the half containing e_s,b.
-__global__ void k_cal_update(int nblk, double inv_count, const double* __restrict__ Es,
+// Inside the calibration graph, one thread also decides whether the loop over
+// iterations goes on (cond != 0: graph conditional handle of the loop).
+__global__ void k_cal_update(int nblk, double inv_count, const double* __restrict__ es,
                              const int32_t* __restrict__ Nsp, const float* __restrict__ T,
                              float* __restrict__ lo, float* __restrict__ hi,
-                             double* __restrict__ ebar, double* __restrict__ trace) {
+                             double* __restrict__ ebar, Control* ctl, int n_bisect,
+                             cudaGraphConditionalHandle cond) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
         const double e = ebar[b] * inv_count;
         ebar[b] = 0.0;
-        if (trace) trace[b] = e;
         if (Nsp[b] <= 0) continue;
-        const double es = Es[b] / (double)Nsp[b];
-        if (e < es) lo[b] = T[b]; else hi[b] = T[b];
+        if (e < es[b]) lo[b] = T[b]; else hi[b] = T[b];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t k = ctl->k + 1;
+        ctl->k = k;
+        if (cond) cudaGraphSetConditional(cond, k < (uint32_t)n_bisect ? 1u : 0u);
     }
 }
 
@@ -783,10 +1014,11 @@ void launch_scan(const int32_t* cnt, int n, int32_t* out, cudaStream_t s) {
 }
 
 void launch_build_lists(const Geom& g, const uint8_t* mask, const int32_t* start0,
-                        const int32_t* start1, uint2* list0, uint2* list1, cudaStream_t s) {
+                        const int32_t* start1, uint2* list0, uint2* list1, int32_t* split0,
+                        int32_t* split1, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((int64_t)g.nblk * 32 + threads - 1) / threads);
-    k_build_lists<<<blocks, threads, 0, s>>>(g, mask, start0, start1, list0, list1);
+    k_build_lists<<<blocks, threads, 0, s>>>(g, mask, start0, start1, list0, list1, split0, split1);
 }
 
 void launch_init(const Geom& g, const uint2* list, int64_t n_list, int colour,
@@ -797,38 +1029,61 @@ void launch_init(const Geom& g, const uint2* list, int64_t n_list, int colour,
                                                      Rp, random, rng, r_even);
 }
 
-void launch_halfstep(const SweepArgs& a, int G, int n_sm, cudaStream_t s) {
-    const int threads = 256;
-    const int64_t items = (int64_t)a.g.nblk * a.groups;
-    const int64_t want = (items + 7) / 8;
-    const int blocks = (int)(want < (int64_t)n_sm * 8 ? want : (int64_t)n_sm * 8);
-    switch (G) {
-        case 1: k_halfstep<1><<<blocks, threads, 0, s>>>(a); break;
-        case 8: k_halfstep<8><<<blocks, threads, 0, s>>>(a); break;
-        default: k_halfstep<32><<<blocks, threads, 0, s>>>(a); break;
+void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, float* ang, int G,
+                         int groups, cudaStream_t s) {
+    k_fill_samples<<<grid_for((int64_t)g.H * g.W * groups, 256), 256, 0, s>>>(g, mask, dang, ang, G,
+                                                                             groups);
+}
+
+void launch_sweep(const SweepArgs& a, int G, int grid, bool edge, cudaStream_t s) {
+    if (G == 2) {
+        if (edge) k_sweep_edge<2><<<grid, 128, 0, s>>>(a);
+        else k_sweep<2><<<grid, 128, 0, s>>>(a);
+    } else {
+        if (edge) k_sweep_edge<8><<<grid, 128, 0, s>>>(a);
+        else k_sweep<8><<<grid, 128, 0, s>>>(a);
     }
 }
 
-void launch_stop_init(int nblk, int Rp, int R, int r_off, const double* Es, const int32_t* Nsp,
-                      const int32_t* Nb, const int32_t* ngap, double* eacc, int8_t* sigma,
-                      uint8_t* running, int32_t* stop, int32_t* tcount, double* e_last,
-                      cudaStream_t s) {
+void launch_energy(const SweepArgs& a, int G, int grid, cudaStream_t s) {
+    if (G == 2) k_energy<2><<<grid, 128, 0, s>>>(a);
+    else k_energy<8><<<grid, 128, 0, s>>>(a);
+}
+
+int sweep_blocks_per_sm(int G) {
+    int n = 0;
+    if (G == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8>, 128, 0);
+    return n > 0 ? n : 1;
+}
+
+void launch_tick(Control* ctl, cudaStream_t s) { k_tick<<<1, 1, 0, s>>>(ctl); }
+
+void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
+                       cudaStream_t s) {
+    k_ecur_reset<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, Es, ecur, eacc);
+}
+
+void launch_stop_init(int nblk, int Rp, const double* es, const double* inb, const int32_t* Nsp,
+                      const int32_t* ngap, const double* ecur, int8_t* sigma, uint8_t* running,
+                      int32_t* stop, int32_t* tcount, double* e_last, cudaStream_t s) {
     k_stop_init<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(
-        nblk, Rp, R, r_off, Es, Nsp, Nb, ngap, eacc, sigma, running, stop, tcount, e_last);
+        nblk, Rp, es, inb, Nsp, ngap, ecur, sigma, running, stop, tcount, e_last);
 }
 
-void launch_stop_targeted(int nblk, int Rp, int t, const double* Es, const int32_t* Nsp,
-                          const int32_t* Nb, double* eacc, const int8_t* sigma, uint8_t* running,
-                          int32_t* stop, int32_t* tcount, double* e_last, cudaStream_t s) {
+void launch_stop_targeted(int nblk, int Rp, const Control* ctl, const double* es,
+                          const double* inb, const int32_t* Nsp, float* eacc, double* ecur,
+                          const int8_t* sigma, uint8_t* running, int32_t* stop, int32_t* tcount,
+                          double* e_last, cudaStream_t s) {
     k_stop_targeted<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(
-        nblk, Rp, t, Es, Nsp, Nb, eacc, sigma, running, stop, tcount, e_last);
+        nblk, Rp, ctl, es, inb, Nsp, eacc, ecur, sigma, running, stop, tcount, e_last);
 }
 
-void launch_stop_rest(int nblk, int Rp, int t, int n_max, const int32_t* Nsp, uint8_t* running,
-                      int32_t* stop, const int32_t* tcount, unsigned long long* n_running,
-                      cudaStream_t s) {
-    k_stop_rest<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, t, n_max, Nsp,
-                                                                  running, stop, tcount, n_running);
+void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, Control* ctl,
+                      const int32_t* Nsp, uint8_t* running, int32_t* stop, const int32_t* tcount,
+                      uint32_t* work, cudaStream_t s) {
+    k_stop_rest<<<grid_for((int64_t)nblk * groups, 256), 256, 0, s>>>(
+        nblk, groups, G, Rp, n_max, ctl, Nsp, running, stop, tcount, work);
 }
 
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
@@ -837,29 +1092,30 @@ void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* 
 }
 
 void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,
-                     cudaStream_t s) {
-    k_cal_init<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, t_lo, t_hi, lo, hi, ebar);
+                     Control* ctl, cudaStream_t s) {
+    k_cal_init<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, t_lo, t_hi, lo, hi, ebar, ctl);
 }
 
 void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T,
-                    cudaStream_t s) {
-    k_cal_mid<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Nsp, lo, hi, T);
+                    Control* ctl, cudaStream_t s) {
+    k_cal_mid<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Nsp, lo, hi, T, ctl);
 }
 
 void launch_cal_fill(int nblk, const int32_t* Nsp, float* T, float* beta, cudaStream_t s) {
     k_cal_fill<<<1, 1024, 0, s>>>(nblk, Nsp, T, beta);
 }
 
-void launch_cal_measure(int nblk, int Rp, int chains, const double* Es, const int32_t* Nb,
-                        double* eacc, double* ebar, cudaStream_t s) {
-    k_cal_measure<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Rp, chains, Es, Nb, eacc, ebar);
+void launch_cal_step(int nblk, int Rp, int chains, int n_eq, const Control* ctl,
+                     const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s) {
+    k_cal_step<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Rp, chains, n_eq, ctl, inb, eacc, ecur,
+                                                  ebar);
 }
 
-void launch_cal_update(int nblk, double inv_count, const double* Es, const int32_t* Nsp,
-                       const float* T, float* lo, float* hi, double* ebar, double* trace,
-                       cudaStream_t s) {
-    k_cal_update<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, inv_count, Es, Nsp, T, lo, hi, ebar,
-                                                    trace);
+void launch_cal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,
+                       const float* T, float* lo, float* hi, double* ebar, Control* ctl,
+                       int n_bisect, cudaGraphConditionalHandle cond, cudaStream_t s) {
+    k_cal_update<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, inv_count, es, Nsp, T, lo, hi, ebar,
+                                                    ctl, n_bisect, cond);
 }
 
 void launch_accumulate(const Geom& g, const uint2* list, int64_t n_list, int colour,

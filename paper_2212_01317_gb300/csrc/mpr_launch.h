@@ -20,33 +20,41 @@ void launch_block_stats(const Geom& g, const float* values, const uint8_t* mask,
                         cudaStream_t s);
 void launch_scan(const int32_t* cnt, int n, int32_t* out, cudaStream_t s);
 void launch_build_lists(const Geom& g, const uint8_t* mask, const int32_t* start0,
-                        const int32_t* start1, uint2* list0, uint2* list1, cudaStream_t s);
+                        const int32_t* start1, uint2* list0, uint2* list1, int32_t* split0,
+                        int32_t* split1, cudaStream_t s);
 void launch_init(const Geom& g, const uint2* list, int64_t n_list, int colour,
                  const float* init_angle, float* ang, int G, int Rp, int random, Rng rng,
                  uint32_t r_even, cudaStream_t s);
-void launch_halfstep(const SweepArgs& a, int G, int n_sm, cudaStream_t s);
-void launch_stop_init(int nblk, int Rp, int R, int r_off, const double* Es, const int32_t* Nsp,
-                      const int32_t* Nb, const int32_t* ngap, double* eacc, int8_t* sigma,
-                      uint8_t* running, int32_t* stop, int32_t* tcount, double* e_last,
-                      cudaStream_t s);
-void launch_stop_targeted(int nblk, int Rp, int t, const double* Es, const int32_t* Nsp,
-                          const int32_t* Nb, double* eacc, const int8_t* sigma, uint8_t* running,
-                          int32_t* stop, int32_t* tcount, double* e_last, cudaStream_t s);
-void launch_stop_rest(int nblk, int Rp, int t, int n_max, const int32_t* Nsp, uint8_t* running,
-                      int32_t* stop, const int32_t* tcount, unsigned long long* n_running,
-                      cudaStream_t s);
+void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, float* ang, int G,
+                         int groups, cudaStream_t s);
+void launch_sweep(const SweepArgs& a, int G, int grid, bool edge, cudaStream_t s);
+void launch_energy(const SweepArgs& a, int G, int grid, cudaStream_t s);
+int sweep_blocks_per_sm(int G);
+void launch_tick(Control* ctl, cudaStream_t s);
+void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
+                       cudaStream_t s);
+void launch_stop_init(int nblk, int Rp, const double* es, const double* inb, const int32_t* Nsp,
+                      const int32_t* ngap, const double* ecur, int8_t* sigma, uint8_t* running,
+                      int32_t* stop, int32_t* tcount, double* e_last, cudaStream_t s);
+void launch_stop_targeted(int nblk, int Rp, const Control* ctl, const double* es,
+                          const double* inb, const int32_t* Nsp, float* eacc, double* ecur,
+                          const int8_t* sigma, uint8_t* running, int32_t* stop, int32_t* tcount,
+                          double* e_last, cudaStream_t s);
+void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, Control* ctl,
+                      const int32_t* Nsp, uint8_t* running, int32_t* stop, const int32_t* tcount,
+                      uint32_t* work, cudaStream_t s);
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
                           unsigned long long* total, cudaStream_t s);
 void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,
-                     cudaStream_t s);
+                     Control* ctl, cudaStream_t s);
 void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T,
-                    cudaStream_t s);
+                    Control* ctl, cudaStream_t s);
 void launch_cal_fill(int nblk, const int32_t* Nsp, float* T, float* beta, cudaStream_t s);
-void launch_cal_measure(int nblk, int Rp, int chains, const double* Es, const int32_t* Nb,
-                        double* eacc, double* ebar, cudaStream_t s);
-void launch_cal_update(int nblk, double inv_count, const double* Es, const int32_t* Nsp,
-                       const float* T, float* lo, float* hi, double* ebar, double* trace,
-                       cudaStream_t s);
+void launch_cal_step(int nblk, int Rp, int chains, int n_eq, const Control* ctl,
+                     const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s);
+void launch_cal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,
+                       const float* T, float* lo, float* hi, double* ebar, Control* ctl,
+                       int n_bisect, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_accumulate(const Geom& g, const uint2* list, int64_t n_list, int colour,
                        const float* ang, int G, int groups, int r_off, int R, double* sum,
                        cudaStream_t s);

@@ -3,7 +3,7 @@
 Every check feeds both sides the same inputs and the same Philox draws:
   * block statistics of Eq. 2 per block (Sec. 2.2.2);
   * one checkerboard half-step, element by element, every gap site, for each
-    lane-group width (1, 8, 32) and with running / stopped blocks;
+    lane-group width (2, 8) and with running / stopped blocks;
   * whole sweeps with the fused block energies and the stop decisions
     (Sec. 3.4), half-step by half-step with re-synchronisation;
   * calibration (bisection per block) and the full predict pipeline;
@@ -84,7 +84,7 @@ def _random_state(gf, m, rng, R):
     return states
 
 
-@pytest.mark.parametrize("group,R", [(1, 1), (8, 12), (32, 40), (8, 3)])
+@pytest.mark.parametrize("group,R", [(2, 1), (2, 5), (8, 12), (8, 40), (8, 3)])
 @pytest.mark.parametrize("colour", [0, 1])
 def test_halfstep_lockstep(group, R, colour):
     H, W, lb = 45, 38, 8
@@ -124,7 +124,7 @@ def test_halfstep_is_independent_of_group_width():
     H, W, lb, R = 33, 29, 5, 10
     z, m = problem(H, W, 0.5, seed=21)
     outs = []
-    for group in (8, 32):
+    for group in (2, 8):
         gf = make(z, m, lb, seed=99, group=group)
         gf.set_temperatures(np.full(gf.nblk, 0.3, np.float32))
         gf.sim_begin(R)
@@ -214,8 +214,8 @@ def _lockstep_sweeps(group, R, H=48, W=40, lb=8, p=0.5, seed=5, n_sweeps=30, kin
     return checked, flips, stop_checked
 
 
-@pytest.mark.parametrize("group,R,kind", [(1, 1, "random"), (8, 6, "random"), (32, 33, "disc"),
-                                          (8, 9, "disc")])
+@pytest.mark.parametrize("group,R,kind", [(2, 1, "random"), (2, 6, "random"), (8, 6, "random"),
+                                          (8, 33, "disc"), (8, 9, "disc")])
 def test_sweeps_energy_and_stop_lockstep(group, R, kind):
     checked, flips, stop_checked = _lockstep_sweeps(group, R, kind=kind, p=0.6 if kind == "disc" else 0.5)
     assert checked > 0 and stop_checked > 0
@@ -256,7 +256,7 @@ def test_calibrate_median_fallback_for_blocks_without_pairs():
 
 
 # -------------------------------------------------------------- pipeline --
-@pytest.mark.parametrize("group", [8, 32])
+@pytest.mark.parametrize("group", [2, 8])
 def test_pipeline_matches_oracle_given_T(group):
     H, W, lb, R = 40, 48, 8, 6
     z, m = problem(H, W, 0.5, seed=31)
@@ -338,7 +338,7 @@ def test_full_size_workload_sampled_sites():
     R = wl.realizations
     gf.sim_begin(R)
     info = gf.refresh()
-    assert info.group in (8, 32)
+    assert info.group == 8
     picks = [0, 1, 57, R - 1]
     pre = {r: gf.get_state(r) for r in picks}
     gf.sim_sweep(1)
