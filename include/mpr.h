@@ -202,6 +202,35 @@ mpr_status mpr_get_block_e(mpr_ctx* ctx, double* e);
  * of the batch, recomputed from scratch in FP64; nblk doubles (host or device). */
 mpr_status mpr_block_energy(mpr_ctx* ctx, int32_t r, double* E);
 
+/* ---- block statistics without allocation ----
+ * The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate device memory at the time they call: a service that
+ * reserves all device memory up front for its own pool, code on a
+ * latency-critical path that cannot pay for the device-wide synchronisation
+ * cudaFree performs, or code running under memory pressure that must not fail
+ * on an allocation. It computes what mpr_create computes for the block
+ * statistics of one field (Sec. 2.1 range, Eq. 2 per block) but allocates
+ * nothing: it works in a fixed scratch array of about 1.25 MiB that the
+ * library keeps on every device that loads it, until the process exits.
+ *   mask, values: H*W device arrays (as mpr_create); Es, Nsp, Nb, mean_angle,
+ *   n_gap: nblk device arrays (as mpr_get_block_stats); zrange: 2 device
+ *   doubles (z_min, z_max; both 0 without samples). Host pointers are
+ *   rejected.
+ *   The grid may have at most MPR_NOALLOC_MAX_BLOCKS blocks; larger grids
+ *   return MPR_EINVAL without touching the outputs.
+ *   Work is queued on cuda_stream (NULL = default stream) and not awaited.
+ *   The first call on a device looks up the scratch array's device address;
+ *   make that first call before any stream capture.
+ *   All calls share the one scratch array: calls that may overlap on the GPU
+ *   (different streams, or different host threads) race and must be
+ *   serialised by the caller.
+ * Errors: EINVAL (sizes, parameters, NULL or host pointers), ECUDA. */
+#define MPR_NOALLOC_MAX_BLOCKS 65536
+mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_t* mask, const float* values,
+                                   double q, double J, double* Es, int32_t* Nsp, int32_t* Nb,
+                                   float* mean_angle, int32_t* n_gap, double* zrange,
+                                   void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,238 @@
+// Block statistics (Sec. 2.1 transform range, Eq. 2 per block) of a field in
+// device memory, computed without allocating any memory.
+//
+// Some callers cannot allocate device memory when they call us: a service
+// that reserves all device memory at start-up and hands it to its own pool,
+// code on a latency-critical path that must not pay for cudaFree's implicit
+// device-wide synchronisation, or code that runs while the process is short
+// of memory and must not fail for that reason. mpr_create allocates its
+// context; this entry point instead works in a fixed scratch array that the
+// library holds on every device that loads it, and writes only into buffers
+// the caller passes.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "mpr.h"
+#include "mpr_internal.h"
+#include "mpr_launch.h"
+
+using namespace mpr;
+
+namespace {
+
+constexpr int kMaxBlocks = MPR_NOALLOC_MAX_BLOCKS;
+constexpr size_t kHeader = 256;
+constexpr size_t kScratchBytes = kHeader + (size_t)kMaxBlocks * (sizeof(double) + 3 * sizeof(int32_t));
+
+// The scratch array: [0, 8) z-range in order-preserving uint32 form,
+// [256, ...) per-block sample sums (double), sample counts and gap counts per
+// colour (int32). Every call overwrites what it reads; nothing survives a call
+// in a form the next one depends on.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+struct Scratch {
+    uint32_t* mm;
+    double* ssum;
+    int32_t* nsamp;
+    int32_t* ng0;
+    int32_t* ng1;
+};
+
+Scratch carve(unsigned char* base) {
+    Scratch s;
+    s.mm = reinterpret_cast<uint32_t*>(base);
+    s.ssum = reinterpret_cast<double*>(base + kHeader);
+    s.nsamp = reinterpret_cast<int32_t*>(base + kHeader + (size_t)kMaxBlocks * sizeof(double));
+    s.ng0 = s.nsamp + kMaxBlocks;
+    s.ng1 = s.ng0 + kMaxBlocks;
+    return s;
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char* g_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device; looked up once
+// per device (the host-side symbol is only a stand-in, not a device address).
+cudaError_t scratch_address(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        g_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_addr[dev];
+    return cudaSuccess;
+}
+
+__device__ __forceinline__ float ord_to_float(uint32_t u) {
+    const uint32_t v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    return __uint_as_float(v);
+}
+
+// The min/max reduction accumulates into the scratch; start it from the
+// identity of min and max.
+__global__ void k_na_reset(uint32_t* mm) {
+    mm[0] = 0xffffffffu;
+    mm[1] = 0u;
+}
+
+// z_min / z_max as doubles (both 0 when there is no sample).
+__global__ void k_na_range(const uint32_t* __restrict__ mm, double* __restrict__ zrange) {
+    if (mm[0] == 0xffffffffu) {
+        zrange[0] = 0.0;
+        zrange[1] = 0.0;
+    } else {
+        zrange[0] = (double)ord_to_float(mm[0]);
+        zrange[1] = (double)ord_to_float(mm[1]);
+    }
+}
+
+// Eq. 2 per block with the range read from device memory: one warp per block,
+// owned bonds (right and down), FP64 sums.
+__global__ void k_na_block_stats(Geom g, const float* __restrict__ values,
+                                 const uint8_t* __restrict__ mask, const double* __restrict__ zrange,
+                                 double q, double J, double* __restrict__ Es,
+                                 int32_t* __restrict__ Nsp, int32_t* __restrict__ Nb, Scratch sc) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= g.nblk) return;
+    const double zmin = zrange[0], zmax = zrange[1];
+    const bool degenerate = !(zmax > zmin);
+    const int by = warp / g.nbx, bx = warp % g.nbx;
+    const int y0 = by * g.lb, x0 = bx * g.lb;
+    const int y1 = min(g.H, y0 + g.lb), x1 = min(g.W, x0 + g.lb);
+    const int bw = x1 - x0, nsite = (y1 - y0) * bw;
+    const double scale = degenerate ? 0.0 : 6.283185307179586476925 / (zmax - zmin);
+    double es = 0.0, sm = 0.0;
+    int nsp = 0, nb = 0, ns = 0, g0 = 0, g1 = 0;
+    for (int j = lane; j < nsite; j += 32) {
+        const int y = y0 + j / bw, x = x0 + j % bw;
+        const int64_t i = (int64_t)y * g.W + x;
+        const bool gap = mask[i] != 0;
+        const double pi = gap ? 0.0 : ((double)values[i] - zmin) * scale;
+        if (gap) {
+            if (((x + y) & 1) == 0) ++g0; else ++g1;
+        } else {
+            sm += pi;
+            ++ns;
+        }
+        if (x + 1 < g.W) {
+            ++nb;
+            if (!gap && !mask[i + 1]) {
+                es += -J * cos(q * (pi - ((double)values[i + 1] - zmin) * scale));
+                ++nsp;
+            }
+        }
+        if (y + 1 < g.H) {
+            ++nb;
+            if (!gap && !mask[i + g.W]) {
+                es += -J * cos(q * (pi - ((double)values[i + g.W] - zmin) * scale));
+                ++nsp;
+            }
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        es += __shfl_xor_sync(0xffffffffu, es, d);
+        sm += __shfl_xor_sync(0xffffffffu, sm, d);
+        nsp += __shfl_xor_sync(0xffffffffu, nsp, d);
+        nb += __shfl_xor_sync(0xffffffffu, nb, d);
+        ns += __shfl_xor_sync(0xffffffffu, ns, d);
+        g0 += __shfl_xor_sync(0xffffffffu, g0, d);
+        g1 += __shfl_xor_sync(0xffffffffu, g1, d);
+    }
+    if (lane == 0) {
+        Es[warp] = es;
+        Nsp[warp] = nsp;
+        Nb[warp] = nb;
+        sc.ssum[warp] = sm;
+        sc.nsamp[warp] = ns;
+        sc.ng0[warp] = g0;
+        sc.ng1[warp] = g1;
+    }
+}
+
+// One CTA: global sample mean (fallback of blocks without samples, Sec. 3.3.3),
+// then each block's mean sample angle and gap count.
+__global__ void k_na_finalize(int nblk, Scratch sc, float* __restrict__ mean_angle,
+                              int32_t* __restrict__ n_gap) {
+    __shared__ double s_sum[256];
+    __shared__ long long s_cnt[256];
+    double sum = 0.0;
+    long long cnt = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        sum += sc.ssum[b];
+        cnt += sc.nsamp[b];
+    }
+    s_sum[threadIdx.x] = sum;
+    s_cnt[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s_sum[threadIdx.x] += s_sum[threadIdx.x + w];
+            s_cnt[threadIdx.x] += s_cnt[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    const double gmean = s_cnt[0] > 0 ? s_sum[0] / (double)s_cnt[0] : 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const int ns = sc.nsamp[b];
+        mean_angle[b] = (float)(ns > 0 ? sc.ssum[b] / (double)ns : gmean);
+        n_gap[b] = sc.ng0[b] + sc.ng1[b];
+    }
+}
+
+bool on_device(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_t* mask,
+                                              const float* values, double q, double J,
+                                              double* Es, int32_t* Nsp, int32_t* Nb,
+                                              float* mean_angle, int32_t* n_gap, double* zrange,
+                                              void* cuda_stream) {
+    if (!grid || !mask || !values || !Es || !Nsp || !Nb || !mean_angle || !n_gap || !zrange)
+        return MPR_EINVAL;
+    const int H = grid->height, W = grid->width, lb = grid->block;
+    if (H < 1 || W < 1 || H > MAX_SIDE || W > MAX_SIDE || lb < 1) return MPR_EINVAL;
+    if (!(q > 0.0 && q <= 0.5) || !(J > 0.0)) return MPR_EINVAL;
+    Geom g;
+    g.H = H;
+    g.W = W;
+    g.Wh = (W + 1) / 2;
+    g.lb = lb;
+    g.nbx = (W + lb - 1) / lb;
+    g.nby = (H + lb - 1) / lb;
+    if ((int64_t)g.nbx * g.nby > kMaxBlocks) return MPR_EINVAL;  // beyond the scratch array
+    g.nblk = g.nbx * g.nby;
+    const void* ptrs[] = {mask, values, Es, Nsp, Nb, mean_angle, n_gap, zrange};
+    for (const void* p : ptrs)
+        if (!on_device(p)) return MPR_EINVAL;
+    unsigned char* base = nullptr;
+    if (scratch_address(&base) != cudaSuccess) return MPR_ECUDA;
+    const Scratch sc = carve(base);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t n = (int64_t)H * W;
+    k_na_reset<<<1, 1, 0, s>>>(sc.mm);
+    launch_minmax(values, mask, n, sc.mm, s);
+    k_na_range<<<1, 1, 0, s>>>(sc.mm, zrange);
+    const int threads = 256;
+    const int blocks = (int)(((int64_t)g.nblk * 32 + threads - 1) / threads);
+    k_na_block_stats<<<blocks, threads, 0, s>>>(g, values, mask, zrange, q, J, Es, Nsp, Nb, sc);
+    k_na_finalize<<<1, 256, 0, s>>>(g.nblk, sc, mean_angle, n_gap);
+    return cudaPeekAtLastError() == cudaSuccess ? MPR_OK : MPR_ECUDA;
+}

@@ -24,7 +24,9 @@ EXPORTS = [
     "mpr_simulate", "mpr_predict", "mpr_get_block_stats", "mpr_sim_begin", "mpr_sim_sweep",
     "mpr_sim_end", "mpr_halfstep", "mpr_get_state", "mpr_set_state", "mpr_get_stop",
     "mpr_set_running", "mpr_block_energy", "mpr_get_block_e", "mpr_get_profile",
+    "mpr_block_stats_noalloc",
 ]
+MPR_NOALLOC_MAX_BLOCKS = 65536
 
 
 class mpr_grid(C.Structure):
@@ -107,6 +109,8 @@ def load(path: str | None = None):
         "mpr_block_energy": (st, [P, i32, P]),
         "mpr_get_block_e": (st, [P, P]),
         "mpr_get_profile": (st, [P, C.POINTER(mpr_profile)]),
+        "mpr_block_stats_noalloc": (st, [C.POINTER(mpr_grid), P, P, C.c_double, C.c_double, P, P,
+                                         P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -236,6 +240,16 @@ def mpr_get_profile(ctx) -> mpr_profile:
 
 def mpr_get_block_e(ctx, out):
     _check(ctx, load().mpr_get_block_e(ctx, _ptr(out)))
+
+
+def mpr_block_stats_noalloc(height: int, width: int, block: int, mask, values, Es, Nsp, Nb,
+                            mean_angle, n_gap, zrange, q: float = 0.5, J: float = 1.0,
+                            cuda_stream=None) -> int:
+    """Block statistics without allocation; every array a CUDA tensor. Returns the status."""
+    g = mpr_grid(height, width, block)
+    return load().mpr_block_stats_noalloc(C.byref(g), _ptr(mask), _ptr(values), q, J, _ptr(Es),
+                                          _ptr(Nsp), _ptr(Nb), _ptr(mean_angle), _ptr(n_gap),
+                                          _ptr(zrange), cuda_stream)
 
 
 class GapFiller:
