@@ -331,11 +331,12 @@ def run_ours(args, world, rank, local):
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
-            traffic = json.load(f).get(f"k_halfstep_{dom}_{wl.name}")
+            traffic = json.load(f).get(f"{dom}_{wl.name}")
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-        "kernel": f"k_halfstep ({'realizations' if dom == 'sim' else 'calibration'})",
+        "kernel": ("k_sweep + k_sweep_edge (realizations)" if dom == "sim"
+                   else "k_sweep_flat (calibration)"),
         "peak_kind": peak_kind,
         "bytes_per_gap_update": bpu,
         "avg_launch_us": 1e3 * (sim_ms / sim_launch if dom == "sim" else cal_ms / max(cal_launch, 1)),

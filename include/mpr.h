@@ -74,6 +74,12 @@ typedef struct {
     int32_t storage;     /* mpr_storage for the gap angles (default F32) */
     int32_t group;       /* realizations interleaved per site: 0 = auto, 2 or 8 */
     int32_t profile;     /* 1: time every sweep-kernel launch with CUDA events (default 0) */
+    int32_t cal_mode;    /* calibration launch: 0 auto (= 1), 1 one CUDA graph of per-half-step
+                            launches, 2 one persistent cooperative kernel with grid barriers */
+    int32_t wait_ms;     /* limit of a device-side grid-barrier wait (default 2000 ms);
+                            a wait that gives up makes the call return MPR_ETIMEOUT */
+    int32_t barrier_test; /* test hook: extra arrivals the grid barrier waits for (default 0);
+                             > 0 makes every wait give up after wait_ms */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 

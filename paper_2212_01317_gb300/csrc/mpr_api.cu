@@ -78,7 +78,11 @@ struct mpr_ctx {
     Control* ctl = nullptr;      // device loop state
     Control* h_ctl = nullptr;    // pinned mirror
     int grid_sweep[2] = {0, 0};  // persistent grid of k_sweep<2>, k_sweep<8>
+    int grid_all[2] = {0, 0};    // grid of k_sweep_all<2>, k_sweep_all<8>
     bool energy_dirty = false;
+    GridBarrier* bar = nullptr;  // grid barrier of the persistent calibration
+    float* med = nullptr;
+    int coop = 0;                // device supports cooperative launch
 
     int64_t realizations = 0;
     int64_t gap_updates = 0, cal_updates = 0;
@@ -175,6 +179,9 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
         return fail(ctx, MPR_EINVAL, "group must be 0, 2 or 8");
     if (o.init != MPR_INIT_BLOCK_MEAN && o.init != MPR_INIT_RANDOM)
         return fail(ctx, MPR_EINVAL, "unknown init mode");
+    if (o.cal_mode < 0 || o.cal_mode > 2) return fail(ctx, MPR_EINVAL, "cal_mode must be 0, 1 or 2");
+    if (o.wait_ms < 1) return fail(ctx, MPR_EINVAL, "wait_ms must be >= 1");
+    if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
     return MPR_OK;
 }
 
@@ -212,7 +219,7 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group) {
         ctx->eacc = nullptr; ctx->running = nullptr; ctx->stop = nullptr; ctx->sigma = nullptr;
         ctx->e_last = nullptr; ctx->ecur = nullptr;
         ctx->blk_cap = 0;
-        TRY(dalloc(ctx, &ctx->eacc, blk_need));
+        TRY(dalloc(ctx, &ctx->eacc, 2 * blk_need));   // two per-sweep buffers
         TRY(dalloc(ctx, &ctx->ecur, blk_need));
         TRY(dalloc(ctx, &ctx->e_last, blk_need));
         TRY(dalloc(ctx, &ctx->running, blk_need));
@@ -238,7 +245,7 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group) {
     ctx->G = G;
     ctx->groups = groups;
     ctx->Rp = Rp;
-    CK(cudaMemsetAsync(ctx->eacc, 0, blk_need * sizeof(float), ctx->s));
+    CK(cudaMemsetAsync(ctx->eacc, 0, 2 * blk_need * sizeof(float), ctx->s));
     CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(Control), ctx->s));
     return MPR_OK;
 }
@@ -269,6 +276,7 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
 }
 
 int sweep_grid(mpr_ctx* ctx) { return ctx->grid_sweep[ctx->G == 2 ? 0 : 1]; }
+int sweep_all_grid(mpr_ctx* ctx) { return ctx->grid_all[ctx->G == 2 ? 0 : 1]; }
 
 cudaEvent_t get_event(mpr_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -412,22 +420,94 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     TRY(init_batch_state(ctx));
     TRY(energy_pass(ctx));
     for (int sw = 1; sw <= o.n_eq + o.n_meas; ++sw) {
-        launch_tick(ctx->ctl, ctx->s);
-        CKL();
         for (int c = 0; c < 2; ++c) {
-            launch_sweep(sweep_args(ctx, c, false), ctx->G, sweep_grid(ctx), false, ctx->s);
-            CKL();
-            launch_sweep(sweep_args(ctx, c, false), ctx->G, sweep_grid(ctx), true, ctx->s);
+            SweepArgs a = sweep_args(ctx, c, false);
+            a.t_fixed = sw;
+            launch_sweep_flat(a, ctx->G, ctx->n_gap[c], ctx->s);
             CKL();
             ++ctx->cal_halfstep_launches;
         }
-        launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, ctx->ctl, ctx->inb, ctx->eacc,
+        launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, sw, ctx->ctl, ctx->inb, ctx->eacc,
                         ctx->ecur, ctx->ebar, ctx->s);
         CKL();
     }
     launch_cal_update(g.nblk, inv_count, ctx->es, ctx->Nsp, ctx->T, ctx->lo, ctx->hi, ctx->ebar,
                       ctx->ctl, o.n_bisect, cond, ctx->s);
     CKL();
+    return MPR_OK;
+}
+
+// All iterations in one cooperative launch (mpr_persist.cu). Returns MPR_OK,
+// MPR_ETIMEOUT (a barrier wait gave up), or `fallback` set when the launch was
+// refused (then nothing ran and the graph path can take over).
+mpr_status calibration_persistent(mpr_ctx* ctx, double inv_count, bool* fallback) {
+    *fallback = false;
+    const Geom& g = ctx->g;
+    const mpr_options& o = ctx->opt;
+    const int per_sm = cal_persistent_blocks_per_sm(ctx->G);
+    if (!ctx->coop || per_sm < 1) {
+        *fallback = true;
+        return MPR_OK;
+    }
+    CalPersistArgs a{};
+    a.sw = sweep_args(ctx, 0, false);
+    a.sw.energy = 1;
+    for (int c = 0; c < 2; ++c) {
+        a.list[c] = ctx->list[c];
+        a.start[c] = ctx->start[c];
+        a.split[c] = ctx->split[c];
+        a.n_list[c] = ctx->n_gap[c];
+    }
+    const size_t blk = (size_t)g.nblk * ctx->Rp;
+    a.eacc2[0] = ctx->eacc;
+    a.eacc2[1] = ctx->eacc + blk;
+    a.Es = ctx->Es;
+    a.es = ctx->es;
+    a.inb = ctx->inb;
+    a.Nsp = ctx->Nsp;
+    a.T = ctx->T;
+    a.beta = ctx->beta;
+    a.lo = ctx->lo;
+    a.hi = ctx->hi;
+    a.ebar = ctx->ebar;
+    a.init_angle = ctx->init_angle;
+    a.chains = o.cal_chains;
+    a.n_eq = o.n_eq;
+    a.n_meas = o.n_meas;
+    a.n_bisect = o.n_bisect;
+    a.random_init = o.init == MPR_INIT_RANDOM;
+    a.inv_count = inv_count;
+    a.bar = ctx->bar;
+    a.spin_limit = (unsigned long long)o.wait_ms * 10000ull;   // ~100 ns per poll
+    a.med = ctx->med;
+    GridBarrier hb{0u, 0u, 0u, (unsigned int)o.barrier_test};
+    CK(cudaMemcpyAsync(ctx->bar, &hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (o.profile) {
+        e0 = get_event(ctx);
+        e1 = get_event(ctx);
+        if (e0) cudaEventRecord(e0, ctx->s);
+    }
+    const cudaError_t le = launch_cal_persistent(a, ctx->G, ctx->n_sm * per_sm, ctx->s);
+    if (le != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) ctx->ev_pool.push_back(e0);
+        if (e1) ctx->ev_pool.push_back(e1);
+        *fallback = true;
+        return MPR_OK;
+    }
+    ++ctx->launches;
+    ctx->cal_halfstep_launches += 1;
+    if (e0 && e1) {
+        cudaEventRecord(e1, ctx->s);
+        ctx->ev_cal.emplace_back(e0, e1);
+    }
+    CK(cudaMemcpyAsync(&hb, ctx->bar, sizeof(hb), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    if (hb.err)
+        return fail(ctx, MPR_ETIMEOUT,
+                    "calibration: a grid-barrier wait gave up after %d ms; the calibration "
+                    "did not complete", o.wait_ms);
     return MPR_OK;
 }
 
@@ -529,6 +609,9 @@ void mpr_default_options(mpr_options* o) {
     o->storage = MPR_STORE_F32;
     o->group = 0;
     o->profile = 0;
+    o->cal_mode = 0;
+    o->wait_ms = 2000;
+    o->barrier_test = 0;
     o->cuda_stream = nullptr;
 }
 
@@ -633,11 +716,16 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     ST(dalloc(ctx, &ctx->mm, 2));
     ST(dalloc(ctx, &ctx->err_buf, 2));
     ST(dalloc(ctx, &ctx->ctl, 1));
+    ST(dalloc(ctx, &ctx->bar, 1));
+    ST(dalloc(ctx, &ctx->med, 1));
+    cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, ctx->device);
     if (cudaMallocHost(&ctx->h_counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_ctl, sizeof(Control)) != cudaSuccess)
         return bail(MPR_ENOMEM);
     ctx->grid_sweep[0] = ctx->n_sm * sweep_blocks_per_sm(2);
     ctx->grid_sweep[1] = ctx->n_sm * sweep_blocks_per_sm(8);
+    ctx->grid_all[0] = ctx->n_sm * sweep_all_blocks_per_sm(2);
+    ctx->grid_all[1] = ctx->n_sm * sweep_all_blocks_per_sm(8);
 
     if (copy_in(ctx, ctx->values, values_in, n * sizeof(float)) != MPR_OK) return bail(MPR_ECUDA);
     if (copy_in(ctx, ctx->mask, mask_in, n) != MPR_OK) return bail(MPR_ECUDA);
@@ -837,11 +925,19 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);
     launch_fill_samples(g, ctx->mask, ctx->dang, ctx->ang, ctx->G, ctx->groups, ctx->s);
     CKL();
-    if (o.n_bisect > 0) TRY(calibration_graph(ctx, inv_count));
-    launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
-    CKL();
-    launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
-    CKL();
+    bool fallback = o.cal_mode != 2;   // auto and 1: graph; 2: persistent
+    if (!fallback) {
+        TRY(calibration_persistent(ctx, inv_count, &fallback));
+        if (fallback && o.cal_mode == 2)
+            return fail(ctx, MPR_ECUDA, "calibration: cooperative launch refused");
+    }
+    if (fallback) {
+        if (o.n_bisect > 0) TRY(calibration_graph(ctx, inv_count));
+        launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+        CKL();
+        launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+        CKL();
+    }
     ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains *
                         (ctx->n_gap[0] + ctx->n_gap[1]);
     ctx->calibrated = 1;
@@ -974,9 +1070,7 @@ mpr_status mpr_halfstep(mpr_ctx* ctx, int32_t colour, int32_t t, int32_t tag) {
     SweepArgs a = sweep_args(ctx, colour, true);
     a.work = nullptr;       // every item; the running flags decide
     a.energy = 0;
-    launch_sweep(a, ctx->G, sweep_grid(ctx), false, ctx->s);
-    CKL();
-    launch_sweep(a, ctx->G, sweep_grid(ctx), true, ctx->s);
+    launch_sweep_all(a, ctx->G, sweep_all_grid(ctx), ctx->s);
     CKL();
     CK(cudaStreamSynchronize(ctx->s));
     *ctx->h_ctl = saved;

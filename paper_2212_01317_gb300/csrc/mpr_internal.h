@@ -82,6 +82,40 @@ struct SweepArgs {
     int R, Rp, groups;        // realizations in the batch, padded lanes, lane groups
     uint32_t r_base;          // global index of lane 0 (even)
     int energy;               // 1: accumulate energy increments of the moves
+    int t_fixed;              // > 0: sweep index of this launch (else read from ctl)
+};
+
+// Grid-wide barrier state of a cooperative launch (zeroed before each launch).
+struct GridBarrier {
+    unsigned int arrive;   // CTAs arrived at the current barrier
+    unsigned int gen;      // barriers completed
+    unsigned int err;      // 1: a wait gave up (the launch returned early)
+    unsigned int extra;    // test hook: arrivals awaited beyond the grid (0 normally)
+};
+
+// The persistent calibration kernel's arguments.
+struct CalPersistArgs {
+    SweepArgs sw;              // colour-independent sweep fields (ecur, ang, beta, ...)
+    const uint2* list[2];
+    const int32_t* start[2];
+    const int32_t* split[2];
+    int64_t n_list[2];
+    float* eacc2[2];           // per-sweep energy changes, by sweep parity
+    const double* Es;
+    const double* es;
+    const double* inb;
+    const int32_t* Nsp;
+    float* T;
+    float* beta;
+    float* lo;
+    float* hi;
+    double* ebar;
+    const float* init_angle;
+    int chains, n_eq, n_meas, n_bisect, random_init;
+    double inv_count;
+    GridBarrier* bar;
+    unsigned long long spin_limit;
+    float* med;                // median of the targeted blocks' T
 };
 
 }  // namespace mpr

@@ -15,6 +15,7 @@
 #include "mpr_device.cuh"
 #include "mpr_internal.h"
 #include "mpr_launch.h"
+#include "mpr_sweep.cuh"
 
 namespace mpr {
 
@@ -286,328 +287,74 @@ __global__ void k_fill_samples(Geom g, const uint8_t* __restrict__ mask,
 }
 
 // ----------------------------------------------------------------- sweep --
-// One checkerboard half-step (Sec. 2.2.2) over the running (block, lane
-// group) items of a batch. The state interleaves G realizations per site; a
-// CTA of four warps takes one item, warp w handles the realization pair
-// (group * G + 2q, + 1), q = w mod G/2, and its 32 lanes walk the block's
-// list of gap sites 32 at a time (warps sharing a pair split the list). Each
-// lane updates its site in both realizations of the pair from one Philox
-// block: words 0, 1 for the even realization, 2, 3 for the odd one.
-//
-// Block energies are kept incrementally: a Metropolis move changes the
-// energy of the site's four bonds by dE and the reflection conserves it, so a
-// site whose bonds all belong to its own block adds dE there. A site on the
-// left or top edge of its block splits the change bond by bond, because its
-// left / up bond belongs to the neighbouring block (a bond is owned by the
-// block of its left / upper site). Frozen sites never move, so stopped
-// (block, realization) pairs cost nothing.
-namespace {
-
-__device__ __forceinline__ void add_energy(const SiteNew& n, uint32_t f, float C, float S,
-                                           const float* nc, const float* ns, float J, float& ao,
-                                           float& al, float& au) {
-    if (!(f & (EDGE_L | EDGE_U))) {
-        ao += n.dE;
-        return;
-    }
-    float cn, sn;
-    final_cs(n, C, S, cn, sn);
-    const float dc = cn - n.co, ds = sn - n.so;
-    const float dl = -J * (dc * nc[0] + ds * ns[0]);
-    const float dr = -J * (dc * nc[1] + ds * ns[1]);
-    const float du = -J * (dc * nc[2] + ds * ns[2]);
-    const float dd = -J * (dc * nc[3] + ds * ns[3]);
-    ao += dr + dd;
-    if (f & EDGE_L) al += dl; else ao += dl;
-    if (f & EDGE_U) au += du; else ao += du;
-}
-
-// Interior sites: only the block's own change.
-__device__ __forceinline__ void flush_own(const SweepArgs& a, int b, int rl, float ao0, float ao1) {
-    if (!__any_sync(0xffffffffu, ao0 != 0.0f || ao1 != 0.0f)) return;
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
-        ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
-    }
-    if ((threadIdx.x & 31) != 0) return;
-    float* ea = a.eacc + (size_t)b * a.Rp + rl;
-    if (ao0 != 0.0f) atomicAdd(ea, ao0);
-    if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
-}
-
-// The same for the from-scratch energies, in FP64 into the block energies.
-__device__ __forceinline__ void flush_energy64(const SweepArgs& a, int b, int rl, double ao0,
-                                               double ao1, double al0, double al1, double au0,
-                                               double au1) {
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
-        ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
-        al0 += __shfl_xor_sync(0xffffffffu, al0, s);
-        al1 += __shfl_xor_sync(0xffffffffu, al1, s);
-        au0 += __shfl_xor_sync(0xffffffffu, au0, s);
-        au1 += __shfl_xor_sync(0xffffffffu, au1, s);
-    }
-    if ((threadIdx.x & 31) != 0) return;
-    double* ea = a.ecur + (size_t)b * a.Rp + rl;
-    if (ao0 != 0.0) atomicAdd(ea, ao0);
-    if (ao1 != 0.0) atomicAdd(ea + 1, ao1);
-    if (al0 != 0.0) atomicAdd(ea - a.Rp, al0);
-    if (al1 != 0.0) atomicAdd(ea - a.Rp + 1, al1);
-    const size_t up = (size_t)a.g.nbx * a.Rp;
-    if (au0 != 0.0) atomicAdd(ea - up, au0);
-    if (au1 != 0.0) atomicAdd(ea - up + 1, au1);
-}
-
-// (cos, sin) of q * phi_j of the four neighbours in both realizations. The
-// state holds sample angles too, so every neighbour is one 8-byte load and a
-// sin/cos pair per realization; a neighbour outside the grid is masked out.
-__device__ __forceinline__ void neighbour_field(const SweepArgs& a, const float2* __restrict__ oth,
-                                                int NP, uint32_t hs, int x, uint32_t f, float* nc0,
-                                                float* ns0, float* nc1, float* ns1) {
-    const uint32_t o = (uint32_t)(x & 1);
-    const uint32_t hn[4] = {hs + o - 1u, hs + o, hs - (uint32_t)a.g.Wh, hs + (uint32_t)a.g.Wh};
-    float2 v[4];
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        const bool ex = (f & (NB_L << d)) != 0;
-        v[d] = ex ? oth[(size_t)hn[d] * NP] : make_float2(0.0f, 0.0f);
-    }
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        const float m = (f & (NB_L << d)) ? 1.0f : 0.0f;
-        float s0, c0, s1, c1;
-        __sincosf(a.m.q * v[d].x, &s0, &c0);
-        __sincosf(a.m.q * v[d].y, &s1, &c1);
-        nc0[d] = m * c0;
-        ns0[d] = m * s0;
-        nc1[d] = m * c1;
-        ns1[d] = m * s1;
-    }
-}
-
-}  // namespace
-
-// Interior sites of each block (the segment after its edge entries): every
-// bond of the site belongs to the block, so the block's energy changes by the
-// Metropolis dE (the reflection conserves it).
+// Interior sites. G = 8: a CTA per item, one warp per realization pair.
+// G = 2 (one pair): a warp per item, four items per CTA.
 template <int G>
-__global__ void __launch_bounds__(128) k_sweep(SweepArgs a) {
-    constexpr int NP = G / 2;        // realization pairs per lane group
-    constexpr int CW = 4 / NP;       // warps sharing one pair
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = warp % NP, cw = warp / NP;
+__global__ void __launch_bounds__(128, 10) k_sweep(SweepArgs a) {
     const uint32_t ctr1 = a.ctl->t | (a.ctl->tag << 16);
     const int n_items = a.work ? (int)a.ctl->n_work : a.g.nblk * a.groups;
-    const size_t plane = (size_t)a.g.H * a.g.Wh;
-    const int c = a.colour, co = c ^ 1;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int item = a.work ? (int)a.work[it] : it;
-        const int b = item / a.groups, grp = item - b * a.groups;
-        const int e0 = a.split[b], e1 = a.start[b + 1];
-        if (e0 >= e1) continue;
-        const int rl = grp * G + 2 * q;
-        bool run0, run1;
-        if (a.running) {
-            run0 = a.running[(size_t)b * a.Rp + rl] != 0;
-            run1 = a.running[(size_t)b * a.Rp + rl + 1] != 0;
-        } else {
-            run0 = rl < a.R;
-            run1 = rl + 1 < a.R;
-        }
-        if (!(run0 || run1)) continue;
-        float2* own = reinterpret_cast<float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
-        const float2* oth =
-            reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
-        const float beta = a.beta[b];
-        const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
-        float ao0 = 0.f, ao1 = 0.f;
-        for (int e = e0 + cw * 32 + lane; e < e1; e += CW * 32) {
-            const uint2 en = a.list[e];
-            const int y = en.x >> 16, x = en.x & 0xffff;
-            const uint32_t f = en.y;
-            const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
-            uint32_t w[4];
-            philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)x, ctr1, rpair, 0u,
-                          a.rng.key0, a.rng.key1, w);
-            const float2 ph = own[(size_t)hs * NP];
-            float nc0[4], ns0[4], nc1[4], ns1[4];
-            neighbour_field(a, oth, NP, hs, x, f, nc0, ns0, nc1, ns1);
-            const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
-            const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
-            const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
-            const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
-            float2 out = ph;
-            if (run0) {
-                const SiteNew n = site_update(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
-                out.x = n.phi;
-                ao0 += n.dE;
-            }
-            if (run1) {
-                const SiteNew n = site_update(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
-                out.y = n.phi;
-                ao1 += n.dE;
-            }
-            own[(size_t)hs * NP] = out;
-        }
-        if (a.energy) flush_own(a, b, rl, ao0, ao1);
+    const int warp = threadIdx.x >> 5;
+    if constexpr (G == 2) {
+        for (int it = blockIdx.x * 4 + warp; it < n_items; it += gridDim.x * 4)
+            sweep_interior_item<G>(a, a.work ? (int)a.work[it] : it, 0, 1, ctr1);
+    } else {
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x)
+            sweep_interior_item<G>(a, a.work ? (int)a.work[it] : it, warp, 4, ctr1);
     }
 }
 
-// Edge sites of each block (left / top edge: the left / up bond belongs to
-// the neighbouring block, so the energy change is split bond by bond). A
-// block has few of them, so one warp takes a whole (block, lane group) item:
-// lane = entry slot * (G/2) + pair, i.e. 32/(G/2) entries times all pairs per
-// pass, and one site's G realizations are read as one contiguous chunk.
+// Interior and edge sites of the running items in one launch: warps 0-3 of a
+// CTA take interior sites (G = 8: the four warps share an item, one pair each;
+// G = 2: one item per warp), warps 4-7 take edge sites, one item per warp.
+template <int G>
+__global__ void __launch_bounds__(256) k_sweep_all(SweepArgs a) {
+    const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
+    const uint32_t ctr1 = t | (a.ctl->tag << 16);
+    const int n_items = a.work ? (int)a.ctl->n_work : a.g.nblk * a.groups;
+    const int warp = threadIdx.x >> 5;
+    if (warp < 4) {
+        if constexpr (G == 2) {
+            for (int it = blockIdx.x * 4 + warp; it < n_items; it += gridDim.x * 4)
+                sweep_interior_item2<G>(a, a.work ? (int)a.work[it] : it, 0, 1, ctr1);
+        } else {
+            for (int it = blockIdx.x; it < n_items; it += gridDim.x)
+                sweep_interior_item2<G>(a, a.work ? (int)a.work[it] : it, warp, 4, ctr1);
+        }
+    } else {
+        for (int it = blockIdx.x * 4 + (warp - 4); it < n_items; it += gridDim.x * 4)
+            sweep_edge_item<G>(a, a.work ? (int)a.work[it] : it, ctr1);
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kFlatThreads) k_sweep_flat(SweepArgs a, int64_t n_list) {
+    const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
+    sweep_flat<G>(a, n_list, t | (a.ctl->tag << 16));
+}
+
 template <int G>
 __global__ void __launch_bounds__(128) k_sweep_edge(SweepArgs a) {
-    constexpr int NP = G / 2;
-    constexpr int EPI = 32 / NP;     // entries per warp pass
-    const int lane = threadIdx.x & 31;
-    const int q = lane % NP, el = lane / NP;
-    const int wpb = blockDim.x >> 5;
-    const int nwarps = gridDim.x * wpb;
     const uint32_t ctr1 = a.ctl->t | (a.ctl->tag << 16);
     const int n_items = a.work ? (int)a.ctl->n_work : a.g.nblk * a.groups;
-    const size_t plane = (size_t)a.g.H * a.g.Wh;
-    const int c = a.colour, co = c ^ 1;
-    for (int it = blockIdx.x * wpb + (threadIdx.x >> 5); it < n_items; it += nwarps) {
-        const int item = a.work ? (int)a.work[it] : it;
-        const int b = item / a.groups, grp = item - b * a.groups;
-        const int e0 = a.start[b], e1 = a.split[b];
-        if (e0 >= e1) continue;
-        const int rl = grp * G + 2 * q;
-        bool run0, run1;
-        if (a.running) {
-            run0 = a.running[(size_t)b * a.Rp + rl] != 0;
-            run1 = a.running[(size_t)b * a.Rp + rl + 1] != 0;
-        } else {
-            run0 = rl < a.R;
-            run1 = rl + 1 < a.R;
-        }
-        if (!__any_sync(0xffffffffu, run0 || run1)) continue;
-        float2* own = reinterpret_cast<float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
-        const float2* oth =
-            reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
-        const float beta = a.beta[b];
-        const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
-        float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
-        for (int base = e0; base < e1; base += EPI) {
-            const int e = base + el;
-            if (e >= e1 || !(run0 || run1)) continue;
-            const uint2 en = a.list[e];
-            const int y = en.x >> 16, x = en.x & 0xffff;
-            const uint32_t f = en.y;
-            const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
-            uint32_t w[4];
-            philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)x, ctr1, rpair, 0u,
-                          a.rng.key0, a.rng.key1, w);
-            const float2 ph = own[(size_t)hs * NP];
-            float nc0[4], ns0[4], nc1[4], ns1[4];
-            neighbour_field(a, oth, NP, hs, x, f, nc0, ns0, nc1, ns1);
-            const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
-            const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
-            const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
-            const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
-            float2 out = ph;
-            if (run0) {
-                const SiteNew n = site_update(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
-                out.x = n.phi;
-                add_energy(n, f, C0, S0, nc0, ns0, a.m.J, ao0, al0, au0);
-            }
-            if (run1) {
-                const SiteNew n = site_update(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
-                out.y = n.phi;
-                add_energy(n, f, C1, S1, nc1, ns1, a.m.J, ao1, al1, au1);
-            }
-            own[(size_t)hs * NP] = out;
-        }
-        if (!a.energy) continue;
-        // Sum over the entry slots of each pair, then the slot-0 lane of each
-        // pair adds to the blocks.
-#pragma unroll
-        for (int s = NP; s < 32; s <<= 1) {
-            ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
-            ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
-            al0 += __shfl_xor_sync(0xffffffffu, al0, s);
-            al1 += __shfl_xor_sync(0xffffffffu, al1, s);
-            au0 += __shfl_xor_sync(0xffffffffu, au0, s);
-            au1 += __shfl_xor_sync(0xffffffffu, au1, s);
-        }
-        if (el != 0) continue;
-        float* ea = a.eacc + (size_t)b * a.Rp + rl;
-        if (ao0 != 0.0f) atomicAdd(ea, ao0);
-        if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
-        if (al0 != 0.0f) atomicAdd(ea - a.Rp, al0);
-        if (al1 != 0.0f) atomicAdd(ea - a.Rp + 1, al1);
-        const size_t up = (size_t)a.g.nbx * a.Rp;
-        if (au0 != 0.0f) atomicAdd(ea - up, au0);
-        if (au1 != 0.0f) atomicAdd(ea - up + 1, au1);
-    }
+    const int wpb = blockDim.x >> 5;
+    for (int it = blockIdx.x * wpb + (threadIdx.x >> 5); it < n_items; it += gridDim.x * wpb)
+        sweep_edge_item<G>(a, a.work ? (int)a.work[it] : it, ctr1);
 }
 
-// Energies from scratch (no move): every bond that touches a gap site, once.
-// A bond always joins a colour-0 and a colour-1 site; colour 1 adds every
-// bond of its gap sites, colour 0 the bonds of its gap sites to samples.
-// Bonds between two samples are the constant E_s,b.
 template <int G>
 __global__ void __launch_bounds__(128) k_energy(SweepArgs a) {
-    constexpr int NP = G / 2;
-    constexpr int CW = 4 / NP;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = warp % NP, cw = warp / NP;
     const int n_items = a.g.nblk * a.groups;
-    const size_t plane = (size_t)a.g.H * a.g.Wh;
-    const int c = a.colour, co = c ^ 1;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int b = it / a.groups, grp = it - b * a.groups;
-        const int rl = grp * G + 2 * q;
-        bool run0, run1;
-        if (a.running) {
-            run0 = a.running[(size_t)b * a.Rp + rl] != 0;
-            run1 = a.running[(size_t)b * a.Rp + rl + 1] != 0;
-        } else {
-            run0 = rl < a.R;
-            run1 = rl + 1 < a.R;
-        }
-        if (!(run0 || run1)) continue;
-        const int e0 = a.start[b], e1 = a.start[b + 1];
-        const float2* own =
-            reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
-        const float2* oth =
-            reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
-        double ao0 = 0.0, ao1 = 0.0, al0 = 0.0, al1 = 0.0, au0 = 0.0, au1 = 0.0;
-        for (int e = e0 + cw * 32 + lane; e < e1; e += CW * 32) {
-            const uint2 en = a.list[e];
-            const int y = en.x >> 16, x = en.x & 0xffff;
-            const uint32_t f = en.y;
-            const size_t hs = (size_t)y * a.g.Wh + (x >> 1);
-            const float2 ph = own[hs * NP];
-            float nc0[4], ns0[4], nc1[4], ns1[4];
-            neighbour_field(a, oth, NP, (uint32_t)hs, x, f, nc0, ns0, nc1, ns1);
-            float s0, c0, s1, c1;
-            __sincosf(a.m.q * ph.x, &s0, &c0);
-            __sincosf(a.m.q * ph.y, &s1, &c1);
-            const uint32_t take = (c == 1) ? 0xFu : (~(f >> 4) & 0xFu);
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                if (!((f & (NB_L << d)) && (take & (1u << d)))) continue;
-                const float b0 = -a.m.J * (c0 * nc0[d] + s0 * ns0[d]);
-                const float b1 = -a.m.J * (c1 * nc1[d] + s1 * ns1[d]);
-                if (d == 0 && (f & EDGE_L)) { al0 += b0; al1 += b1; }
-                else if (d == 2 && (f & EDGE_U)) { au0 += b0; au1 += b1; }
-                else { ao0 += b0; ao1 += b1; }
-            }
-        }
-        flush_energy64(a, b, rl, ao0, ao1, al0, al1, au0, au1);
-    }
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) energy_item<G>(a, it, threadIdx.x >> 5, 4);
 }
 
 template __global__ void k_sweep<2>(SweepArgs);
 template __global__ void k_sweep<8>(SweepArgs);
 template __global__ void k_sweep_edge<2>(SweepArgs);
 template __global__ void k_sweep_edge<8>(SweepArgs);
+template __global__ void k_sweep_all<2>(SweepArgs);
+template __global__ void k_sweep_all<8>(SweepArgs);
+template __global__ void k_sweep_flat<2>(SweepArgs, int64_t);
+template __global__ void k_sweep_flat<8>(SweepArgs, int64_t);
 template __global__ void k_energy<2>(SweepArgs);
 template __global__ void k_energy<8>(SweepArgs);
 
@@ -763,55 +510,9 @@ __global__ void k_cal_mid(int nblk, const int32_t* __restrict__ Nsp, const float
     }
 }
 
-// Median of the targeted blocks' T by a single-CTA radix select on the
-// (positive) float bit patterns; even counts average the two middle values.
-__device__ uint32_t select_kth(const float* __restrict__ T, const int32_t* __restrict__ Nsp,
-                               int nblk, uint32_t k, uint32_t* hist, uint32_t* s_digit,
-                               uint32_t* s_k) {
-    uint32_t prefix = 0, pmask = 0;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
-        for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-            if (Nsp[b] <= 0) continue;
-            const uint32_t v = __float_as_uint(T[b]);
-            if ((v & pmask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t kk = k, d = 0;
-            while (d < 255 && kk >= hist[d]) { kk -= hist[d]; ++d; }
-            *s_digit = d;
-            *s_k = kk;
-        }
-        __syncthreads();
-        prefix |= (*s_digit) << shift;
-        pmask |= 255u << shift;
-        k = *s_k;
-        __syncthreads();
-    }
-    return prefix;
-}
-
 __global__ void k_cal_fill(int nblk, const int32_t* __restrict__ Nsp, float* __restrict__ T,
                            float* __restrict__ beta) {
-    __shared__ uint32_t hist[256];
-    __shared__ uint32_t s_digit, s_k, s_n;
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
-    uint32_t cnt = 0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) cnt += Nsp[b] > 0;
-    atomicAdd(&s_n, cnt);
-    __syncthreads();
-    const uint32_t n = s_n;
-    float med = 0.0f;
-    if (n > 0) {
-        const float lo = __uint_as_float(select_kth(T, Nsp, nblk, (n - 1) / 2, hist, &s_digit, &s_k));
-        const float hi = (n & 1) ? lo
-                                 : __uint_as_float(select_kth(T, Nsp, nblk, n / 2, hist, &s_digit, &s_k));
-        med = 0.5f * (lo + hi);
-    }
+    const float med = median_targeted(T, Nsp, nblk);
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         float tb = T[b];
         if (Nsp[b] <= 0) {
@@ -824,10 +525,11 @@ __global__ void k_cal_fill(int nblk, const int32_t* __restrict__ Nsp, float* __r
 
 // After calibration sweep t: fold the sweep's change into E_b; past n_eq
 // sweeps add e_b of every chain to the running sum.
-__global__ void k_cal_step(int nblk, int Rp, int chains, int n_eq, const Control* __restrict__ ctl,
-                           const double* __restrict__ inb, float* __restrict__ eacc,
-                           double* __restrict__ ecur, double* __restrict__ ebar) {
-    const bool measure = (int)ctl->t > n_eq;
+__global__ void k_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed,
+                           const Control* __restrict__ ctl, const double* __restrict__ inb,
+                           float* __restrict__ eacc, double* __restrict__ ecur,
+                           double* __restrict__ ebar) {
+    const bool measure = (t_fixed > 0 ? t_fixed : (int)ctl->t) > n_eq;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int r = 0; r < chains; ++r) {
@@ -1050,6 +752,26 @@ void launch_energy(const SweepArgs& a, int G, int grid, cudaStream_t s) {
     else k_energy<8><<<grid, 128, 0, s>>>(a);
 }
 
+void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s) {
+    if (n_list == 0) return;
+    const int64_t threads = n_list * (G / 2);
+    const dim3 grid((unsigned)((threads + kFlatThreads - 1) / kFlatThreads), (unsigned)a.groups);
+    if (G == 2) k_sweep_flat<2><<<grid, kFlatThreads, 0, s>>>(a, n_list);
+    else k_sweep_flat<8><<<grid, kFlatThreads, 0, s>>>(a, n_list);
+}
+
+void launch_sweep_all(const SweepArgs& a, int G, int grid, cudaStream_t s) {
+    if (G == 2) k_sweep_all<2><<<grid, 256, 0, s>>>(a);
+    else k_sweep_all<8><<<grid, 256, 0, s>>>(a);
+}
+
+int sweep_all_blocks_per_sm(int G) {
+    int n = 0;
+    if (G == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_all<2>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_all<8>, 256, 0);
+    return n > 0 ? n : 1;
+}
+
 int sweep_blocks_per_sm(int G) {
     int n = 0;
     if (G == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2>, 128, 0);
@@ -1105,10 +827,10 @@ void launch_cal_fill(int nblk, const int32_t* Nsp, float* T, float* beta, cudaSt
     k_cal_fill<<<1, 1024, 0, s>>>(nblk, Nsp, T, beta);
 }
 
-void launch_cal_step(int nblk, int Rp, int chains, int n_eq, const Control* ctl,
+void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
                      const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s) {
-    k_cal_step<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Rp, chains, n_eq, ctl, inb, eacc, ecur,
-                                                  ebar);
+    k_cal_step<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Rp, chains, n_eq, t_fixed, ctl, inb, eacc,
+                                                  ecur, ebar);
 }
 
 void launch_cal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,

@@ -30,6 +30,9 @@ void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, 
 void launch_sweep(const SweepArgs& a, int G, int grid, bool edge, cudaStream_t s);
 void launch_energy(const SweepArgs& a, int G, int grid, cudaStream_t s);
 int sweep_blocks_per_sm(int G);
+void launch_sweep_all(const SweepArgs& a, int G, int grid, cudaStream_t s);
+void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s);
+int sweep_all_blocks_per_sm(int G);
 void launch_tick(Control* ctl, cudaStream_t s);
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
                        cudaStream_t s);
@@ -50,7 +53,7 @@ void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, dou
 void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T,
                     Control* ctl, cudaStream_t s);
 void launch_cal_fill(int nblk, const int32_t* Nsp, float* T, float* beta, cudaStream_t s);
-void launch_cal_step(int nblk, int Rp, int chains, int n_eq, const Control* ctl,
+void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
                      const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s);
 void launch_cal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,
                        const float* T, float* lo, float* hi, double* ebar, Control* ctl,
@@ -67,5 +70,8 @@ void launch_set_state(const Geom& g, const uint8_t* mask, float* ang, int G, int
                       const float* in, cudaStream_t s);
 void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, const float* ang,
                          int G, int r, double q, double J, double* E, cudaStream_t s);
+
+int cal_persistent_blocks_per_sm(int G);
+cudaError_t launch_cal_persistent(const CalPersistArgs& a, int G, int grid, cudaStream_t s);
 
 }  // namespace mpr

@@ -39,7 +39,8 @@ class mpr_options(C.Structure):
                 ("n_meas", C.c_int32), ("n_bisect", C.c_int32), ("cal_chains", C.c_int32),
                 ("t_lo", C.c_float), ("t_hi", C.c_float), ("overrelax", C.c_int32),
                 ("init", C.c_int32), ("storage", C.c_int32), ("group", C.c_int32),
-                ("profile", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("profile", C.c_int32), ("cal_mode", C.c_int32), ("wait_ms", C.c_int32),
+                ("barrier_test", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):

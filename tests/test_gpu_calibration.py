@@ -1,0 +1,59 @@
+"""Calibration launch paths (GPU, through the C-ABI).
+
+The per-block bisection of Sec. 2.1 / 2.2.2 runs either as one CUDA graph
+(a device-side loop of per-half-step launches) or as one persistent
+cooperative kernel with grid barriers. Both consume the same random streams
+and the same arithmetic, so they must give the same temperatures. The
+persistent kernel's barrier waits are bounded: a test hook makes every wait
+give up, the call reports MPR_ETIMEOUT, and the device stays usable.
+"""
+import numpy as np
+import pytest
+
+from paper_2212_01317_gb300 import synth
+from paper_2212_01317_gb300.mpr import GapFiller, MprError, MPR_ETIMEOUT
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def make(z, m, lb, **opt):
+    v = np.where(m != 0, np.nan, z).astype(np.float32)
+    return GapFiller(v, m, lb, **opt)
+
+
+@pytest.mark.parametrize("H,W,lb,chains,kind", [(48, 40, 8, 1, "random"), (64, 64, 16, 2, "disc"),
+                                                (37, 53, 8, 5, "random"), (96, 96, 32, 1, "disc")])
+def test_persistent_equals_graph(H, W, lb, chains, kind):
+    z, m = synth.small_problem(H, W, 0.55, seed=H + lb, kind=kind)
+    opts = dict(seed=77, n_eq=6, n_meas=5, n_bisect=8, cal_chains=chains)
+    Ts = []
+    for mode in (1, 2):
+        gf = make(z, m, lb, cal_mode=mode, **opts)
+        Ts.append(gf.calibrate())
+        gf.close()
+    np.testing.assert_allclose(Ts[0], Ts[1], rtol=1e-6)
+
+
+def test_barrier_timeout_is_reported_and_device_stays_usable():
+    z, m = synth.small_problem(40, 40, 0.5, seed=3)
+    gf = make(z, m, 8, cal_mode=2, barrier_test=1, wait_ms=100, n_bisect=2, n_eq=2, n_meas=2)
+    with pytest.raises(MprError) as e:
+        gf.calibrate()
+    assert e.value.status == MPR_ETIMEOUT
+    # The same context and a new one still work.
+    gf.set_temperatures(np.full(gf.nblk, 0.2, np.float32))
+    gf.simulate(2)
+    pred, _ = gf.predict()
+    assert np.isfinite(pred).all()
+    gf.close()
+    gf2 = make(z, m, 8, cal_mode=2, n_bisect=2, n_eq=2, n_meas=2)
+    T = gf2.calibrate()
+    assert np.all(T > 0)
+    gf2.close()
