@@ -12,7 +12,9 @@ gaps at random, 16 x 16 temperature blocks, 100 realizations, FP32.
 Metric: gap-site updates/s (Metropolis + over-relaxation site updates of the
 calibration and of the realizations, per second of step time); the line also
 carries gap-filled Mpix/s. Under torchrun every rank fills its own field
-(independent slices, no collective on the data path): weak scaling.
+(independent slices, no collective on the data path): weak scaling; with
+--shard realizations the ranks share one field's realizations instead and
+add their per-site sums with one all-reduce (strong scaling).
 """
 from __future__ import annotations
 
@@ -44,6 +46,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--shard", default="fields", choices=["fields", "realizations"],
+                    help="fields: every rank its own field (weak scaling, no collective); "
+                         "realizations: ranks share one field's realizations (strong scaling, "
+                         "one all-reduce of the per-site sums)")
     return ap.parse_args()
 
 
@@ -199,7 +205,7 @@ def cpu_baseline(wl, T_gpu, seconds):
 
 def run_ours(args, world, rank, local):
     import torch
-    from paper_2212_01317_gb300 import mpr, synth
+    from paper_2212_01317_gb300 import mpr, replicas, synth
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -220,15 +226,26 @@ def run_ours(args, world, rank, local):
     out_d = torch.empty((H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    shard = args.shard if world > 1 else "fields"
+    seed, slice_id = replicas.rank_seed(2024, rank, shard)
+    acc_d = torch.empty((H, W), dtype=torch.float64, device=dev)
+    T_d = None
+
     def options(profile):
-        return mpr.mpr_default_options(seed=2024 + 7919 * rank, slice_id=rank, profile=profile,
+        return mpr.mpr_default_options(seed=seed, slice_id=slice_id, profile=profile,
                                        cuda_stream=stream.cuda_stream)
 
     def step(values, mask, out, profile=1):
+        nonlocal T_d
         ctx = mpr.mpr_create(H, W, wl.block, mask, values, options(profile))
         try:
-            mpr.mpr_calibrate(ctx, None)
-            mpr.mpr_simulate(ctx, R)
+            if shard == "fields":
+                mpr.mpr_calibrate(ctx, None)
+                mpr.mpr_simulate(ctx, R)
+            else:
+                if T_d is None:
+                    T_d = torch.empty(mpr.mpr_get_info(ctx).nblk, dtype=torch.float32, device=dev)
+                replicas.fill_shared_field(ctx, R, world, rank, acc_d, T_d)
             mpr.mpr_predict(ctx, out)
             info = mpr.mpr_get_info(ctx)
             prof = mpr.mpr_get_profile(ctx)
@@ -274,18 +291,11 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = float(np.sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(updates)], device=dev, dtype=torch.float64)
-        dist.all_reduce(u)
-        updates_all = float(u.item())
-    else:
-        updates_all = float(updates)
+    total_ms = replicas.max_over_ranks(total_ms, dev)
+    updates_all = replicas.sum_over_ranks(updates, dev)
     value = updates_all / (total_ms / 1e3)
-    mpix = world * P * args.steps / (total_ms / 1e3) / 1e6
+    fields = world if shard == "fields" else 1          # distinct fields filled per step
+    mpix = fields * P * args.steps / (total_ms / 1e3) / 1e6
 
     # End to end through the C-ABI with pinned host buffers: the H2D copy of
     # the step's inputs and the D2H copy of its predictions are timed.
@@ -303,16 +313,12 @@ def run_ours(args, world, rank, local):
             info, _ = step(vals_pin, mask_pin, out_pin, profile=0)
             ups += info.gap_updates + info.cal_gap_updates
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * ups / dt, "unit": "updates/s",
+        dt = replicas.max_over_ranks(time.perf_counter() - t0, dev)
+        ups = replicas.sum_over_ranks(ups, dev)
+        e2e = {"value": ups / dt, "unit": "updates/s",
                "h2d_bytes_per_step": int(vals_h.nbytes + wl.mask.nbytes),
                "d2h_bytes_per_step": int(out_pin.numel() * 4),
-               "gap_filled_mpix_s": world * P * args.steps / dt / 1e6}
+               "gap_filled_mpix_s": fields * P * args.steps / dt / 1e6}
 
     if rank != 0:
         if world > 1:
@@ -350,11 +356,13 @@ def run_ours(args, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak" if shard == "fields" else "strong",
+        "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "H": H, "W": W, "block": wl.block, "gap_fraction": p,
                    "realizations": R, "storage": "f32", "l2": "flushed between timed steps",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": (f"replicas{world}" if shard == "fields"
+                                   else f"realizations{world}")},
         "gap_filled_mpix_s": mpix,
         "updates_per_step": {"calibration": cal_updates // args.steps,
                              "realizations": sim_updates // args.steps},

@@ -164,6 +164,26 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n_realizations);
  * Errors: ESTATE (no realization accumulated), EINVAL, ECUDA. */
 mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae_rase);
 
+/* ---- realizations split across processes ----
+ * The realizations of one field are independent chains (Sec. 2.1) that
+ * differ only in their random numbers, which are keyed by the realization
+ * index. A job can therefore give each process a disjoint range of indices
+ * and add up the per-site sums of the final states; the mean of the sum
+ * equals the mean a single process would have accumulated over all ranges.
+ * mpr_set_realization_base: the next realization run gets index r_first
+ *   (>= 0); later realizations continue from it. Only between batches.
+ *   Errors: ESTATE (a batch is open), EINVAL.
+ * mpr_get_accumulator: sum_out[H*W] (host or device, row-major) receives
+ *   sum_r phi_r at every gap site (transformed scale, radians) and 0 at
+ *   sample sites; *n_realizations (may be NULL) the count accumulated.
+ * mpr_set_accumulator: replaces the sums and the count (n_realizations >= 0)
+ *   with the caller's, e.g. the element-wise sum over processes; sample
+ *   entries are ignored. mpr_predict then divides by n_realizations.
+ *   Errors: ESTATE (a batch is open), EINVAL, ECUDA. */
+mpr_status mpr_set_realization_base(mpr_ctx* ctx, int64_t r_first);
+mpr_status mpr_get_accumulator(mpr_ctx* ctx, double* sum_out, int64_t* n_realizations);
+mpr_status mpr_set_accumulator(mpr_ctx* ctx, const double* sum_in, int64_t n_realizations);
+
 /* ---- block statistics (Eq. 2 per block), host or device outputs, each nblk long;
  *      any pointer may be NULL. ---- */
 mpr_status mpr_get_block_stats(mpr_ctx* ctx, double* Es, int32_t* Nsp, int32_t* Nb,

@@ -84,7 +84,8 @@ struct mpr_ctx {
     float* med = nullptr;
     int coop = 0;                // device supports cooperative launch
 
-    int64_t realizations = 0;
+    int64_t realizations = 0;   // accumulated into sum
+    int64_t r_next = 0;         // index of the next realization
     int64_t gap_updates = 0, cal_updates = 0;
 
     // instrumentation
@@ -952,7 +953,7 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     ctx->err.clear();
     if (n < 1) return fail(ctx, MPR_EINVAL, "n_realizations must be >= 1");
     if (!ctx->calibrated) return fail(ctx, MPR_ESTATE, "calibrate or set temperatures first");
-    const int64_t r_base = ctx->realizations;
+    const int64_t r_base = ctx->r_next;
     if (r_base + n > (int64_t)0x1FFFFFFFF) return fail(ctx, MPR_EINVAL, "realization index overflow");
     ctx->r_off = (int)(r_base & 1);
     ctx->r_even = (uint32_t)(r_base - ctx->r_off);
@@ -1013,6 +1014,7 @@ mpr_status mpr_sim_end(mpr_ctx* ctx) {
     collect_events(ctx);
     ctx->gap_updates += (int64_t)ctx->h_counters[1];
     ctx->realizations += ctx->R;
+    ctx->r_next += ctx->R;
     ctx->batch_open = 0;
     return MPR_OK;
 }
@@ -1183,6 +1185,52 @@ mpr_status mpr_block_energy(mpr_ctx* ctx, int32_t r, double* E) {
     if (st == MPR_OK) st = copy_out(ctx, E, d, (size_t)ctx->g.nblk * 8);
     dfree(ctx, d);
     ctx->device_bytes -= (int64_t)ctx->g.nblk * 8;
+    return st;
+}
+
+mpr_status mpr_set_realization_base(mpr_ctx* ctx, int64_t r_first) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
+    if (r_first < 0 || r_first > (int64_t)0x1FFFFFFFF)
+        return fail(ctx, MPR_EINVAL, "r_first out of range");
+    ctx->r_next = r_first;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_accumulator(mpr_ctx* ctx, double* sum_out, int64_t* n_realizations) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
+    if (n_realizations) *n_realizations = ctx->realizations;
+    if (!sum_out) return MPR_OK;
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, n * sizeof(double), ctx->s));
+    launch_sum_to_grid(ctx->g, ctx->mask, ctx->sum, tmp, ctx->s);
+    mpr_status st = cudaGetLastError() == cudaSuccess ? copy_out(ctx, sum_out, tmp, n * 8)
+                                                      : fail(ctx, MPR_ECUDA, "k_sum_to_grid");
+    cudaFreeAsync(tmp, ctx->s);
+    CK(cudaStreamSynchronize(ctx->s));
+    return st;
+}
+
+mpr_status mpr_set_accumulator(mpr_ctx* ctx, const double* sum_in, int64_t n_realizations) {
+    if (!ctx || !sum_in) return MPR_EINVAL;
+    ctx->err.clear();
+    if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
+    if (n_realizations < 0) return fail(ctx, MPR_EINVAL, "n_realizations must be >= 0");
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, n * sizeof(double), ctx->s));
+    mpr_status st = copy_in(ctx, tmp, sum_in, n * 8);
+    if (st == MPR_OK) {
+        launch_grid_to_sum(ctx->g, ctx->mask, tmp, ctx->sum, ctx->s);
+        if (cudaGetLastError() != cudaSuccess) st = fail(ctx, MPR_ECUDA, "k_grid_to_sum");
+    }
+    cudaFreeAsync(tmp, ctx->s);
+    CK(cudaStreamSynchronize(ctx->s));
+    if (st == MPR_OK) ctx->realizations = n_realizations;
     return st;
 }
 

@@ -584,6 +584,31 @@ __global__ void k_accumulate(Geom g, const uint2* __restrict__ list, int64_t n_l
     }
 }
 
+// Half-lattice accumulator <-> row-major grid (gap sites only; 0 at samples).
+__global__ void k_sum_to_grid(Geom g, const uint8_t* __restrict__ mask,
+                              const double* __restrict__ sum, double* __restrict__ out) {
+    const int64_t n = (int64_t)g.H * g.W;
+    const size_t plane = (size_t)g.H * g.Wh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / g.W), x = (int)(i % g.W);
+        const int c = (x + y) & 1;
+        out[i] = mask[i] ? sum[(size_t)c * plane + (size_t)y * g.Wh + (x >> 1)] : 0.0;
+    }
+}
+
+__global__ void k_grid_to_sum(Geom g, const uint8_t* __restrict__ mask,
+                              const double* __restrict__ in, double* __restrict__ sum) {
+    const int64_t n = (int64_t)g.H * g.W;
+    const size_t plane = (size_t)g.H * g.Wh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / g.W), x = (int)(i % g.W);
+        const int c = (x + y) & 1;
+        sum[(size_t)c * plane + (size_t)y * g.Wh + (x >> 1)] = mask[i] ? in[i] : 0.0;
+    }
+}
+
 // Sec. 2.1 back-transform of the conditional mean; samples copied bit for bit.
 __global__ void k_predict(Geom g, const float* __restrict__ values,
                           const uint8_t* __restrict__ mask, const double* __restrict__ sum,
@@ -846,6 +871,16 @@ void launch_accumulate(const Geom& g, const uint2* list, int64_t n_list, int col
     if (n_list == 0) return;
     k_accumulate<<<grid_for(n_list, 256), 256, 0, s>>>(g, list, n_list, colour, ang, G, groups,
                                                       r_off, R, sum);
+}
+
+void launch_sum_to_grid(const Geom& g, const uint8_t* mask, const double* sum, double* out,
+                        cudaStream_t s) {
+    k_sum_to_grid<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, mask, sum, out);
+}
+
+void launch_grid_to_sum(const Geom& g, const uint8_t* mask, const double* in, double* sum,
+                        cudaStream_t s) {
+    k_grid_to_sum<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, mask, in, sum);
 }
 
 void launch_predict(const Geom& g, const float* values, const uint8_t* mask, const double* sum,

@@ -61,6 +61,10 @@ void launch_cal_update(int nblk, double inv_count, const double* es, const int32
 void launch_accumulate(const Geom& g, const uint2* list, int64_t n_list, int colour,
                        const float* ang, int G, int groups, int r_off, int R, double* sum,
                        cudaStream_t s);
+void launch_sum_to_grid(const Geom& g, const uint8_t* mask, const double* sum, double* out,
+                        cudaStream_t s);
+void launch_grid_to_sum(const Geom& g, const uint8_t* mask, const double* in, double* sum,
+                        cudaStream_t s);
 void launch_predict(const Geom& g, const float* values, const uint8_t* mask, const double* sum,
                     double inv_r, double zmin, double zmax, float* out, const float* truth,
                     double* err, cudaStream_t s);

@@ -24,7 +24,8 @@ EXPORTS = [
     "mpr_simulate", "mpr_predict", "mpr_get_block_stats", "mpr_sim_begin", "mpr_sim_sweep",
     "mpr_sim_end", "mpr_halfstep", "mpr_get_state", "mpr_set_state", "mpr_get_stop",
     "mpr_set_running", "mpr_block_energy", "mpr_get_block_e", "mpr_get_profile",
-    "mpr_block_stats_noalloc",
+    "mpr_block_stats_noalloc", "mpr_set_realization_base", "mpr_get_accumulator",
+    "mpr_set_accumulator",
 ]
 MPR_NOALLOC_MAX_BLOCKS = 65536
 
@@ -112,6 +113,9 @@ def load(path: str | None = None):
         "mpr_get_profile": (st, [P, C.POINTER(mpr_profile)]),
         "mpr_block_stats_noalloc": (st, [C.POINTER(mpr_grid), P, P, C.c_double, C.c_double, P, P,
                                          P, P, P, P, P]),
+        "mpr_set_realization_base": (st, [P, i64]),
+        "mpr_get_accumulator": (st, [P, P, C.POINTER(i64)]),
+        "mpr_set_accumulator": (st, [P, P, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -241,6 +245,20 @@ def mpr_get_profile(ctx) -> mpr_profile:
 
 def mpr_get_block_e(ctx, out):
     _check(ctx, load().mpr_get_block_e(ctx, _ptr(out)))
+
+
+def mpr_set_realization_base(ctx, r_first: int):
+    _check(ctx, load().mpr_set_realization_base(ctx, int(r_first)))
+
+
+def mpr_get_accumulator(ctx, sum_out=None) -> int:
+    n = C.c_int64()
+    _check(ctx, load().mpr_get_accumulator(ctx, _ptr(sum_out), C.byref(n)))
+    return n.value
+
+
+def mpr_set_accumulator(ctx, sum_in, n_realizations: int):
+    _check(ctx, load().mpr_set_accumulator(ctx, _ptr(sum_in), int(n_realizations)))
 
 
 def mpr_block_stats_noalloc(height: int, width: int, block: int, mask, values, Es, Nsp, Nb,
