@@ -30,6 +30,7 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 sys.path.insert(0, ROOT)
 
 METRIC = "gap-site updates/s"
@@ -46,6 +47,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="element type of the realizations' angles (arithmetic stays FP32)")
+    ap.add_argument("--cal-mode", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="calibration launch form (3: every kernel from the host, for profilers)")
     ap.add_argument("--shard", default="fields", choices=["fields", "realizations"],
                     help="fields: every rank its own field (weak scaling, no collective); "
                          "realizations: ranks share one field's realizations (strong scaling, "
@@ -233,6 +238,7 @@ def run_ours(args, world, rank, local):
 
     def options(profile):
         return mpr.mpr_default_options(seed=seed, slice_id=slice_id, profile=profile,
+                                       storage=STORAGE[args.storage], cal_mode=args.cal_mode,
                                        cuda_stream=stream.cuda_stream)
 
     def step(values, mask, out, profile=1):
@@ -327,7 +333,7 @@ def run_ours(args, world, rank, local):
         return
 
     peak, peak_kind = measured_peaks()
-    bpu = bytes_per_gap_update(4.0, p)
+    bpu = bytes_per_gap_update(4.0 if args.storage == "f32" else 2.0, p)
     sim_gbs = sim_updates * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
     cal_gbs = cal_updates * bpu / (cal_ms / 1e3) / 1e9 if cal_ms > 0 else None
     # Dominant kernel by summed device time.
@@ -341,8 +347,9 @@ def run_ours(args, world, rank, local):
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-        "kernel": ("k_sweep + k_sweep_edge (realizations)" if dom == "sim"
-                   else "k_sweep_flat (calibration)"),
+        "kernel": ("k_sweep (realizations)" if dom == "sim"
+                   else ("k_sweep_flat (calibration)" if args.cal_mode == 3
+                         else "calibration graph (k_sweep_flat + bookkeeping)")),
         "peak_kind": peak_kind,
         "bytes_per_gap_update": bpu,
         "avg_launch_us": 1e3 * (sim_ms / sim_launch if dom == "sim" else cal_ms / max(cal_launch, 1)),
@@ -360,7 +367,8 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "H": H, "W": W, "block": wl.block, "gap_fraction": p,
-                   "realizations": R, "storage": "f32", "l2": "flushed between timed steps",
+                   "realizations": R, "storage": args.storage, "cal_mode": args.cal_mode,
+                   "l2": "flushed between timed steps",
                    "parallelism": (f"replicas{world}" if shard == "fields"
                                    else f"realizations{world}")},
         "gap_filled_mpix_s": mpix,

@@ -71,11 +71,18 @@ typedef struct {
     float t_lo, t_hi;    /* calibration bracket (1e-4, 2) */
     int32_t overrelax;   /* 1: Metropolis then over-relaxation per site (default 1) */
     int32_t init;        /* mpr_init (default MPR_INIT_BLOCK_MEAN, Sec. 3.3.3) */
-    int32_t storage;     /* mpr_storage for the gap angles (default F32) */
+    int32_t storage;     /* mpr_storage of the realizations' gap angles (default F32).
+                            BF16 / F16 halve the state; arithmetic stays FP32 and the
+                            block energies FP64; proposals and reflections are rounded
+                            to the stored type before their energy is taken, so the
+                            incremental block energies stay exact for the stored state.
+                            Sample angles and the calibration chains stay FP32. */
     int32_t group;       /* realizations interleaved per site: 0 = auto, 2 or 8 */
     int32_t profile;     /* 1: time every sweep-kernel launch with CUDA events (default 0) */
     int32_t cal_mode;    /* calibration launch: 0 auto (= 1), 1 one CUDA graph of per-half-step
-                            launches, 2 one persistent cooperative kernel with grid barriers */
+                            launches, 2 one persistent cooperative kernel with grid barriers,
+                            3 every kernel launched from the host (profilers see each one;
+                            with profile = 1 every half-step is timed) */
     int32_t wait_ms;     /* limit of a device-side grid-barrier wait (default 2000 ms);
                             a wait that gives up makes the call return MPR_ETIMEOUT */
     int32_t barrier_test; /* test hook: extra arrivals the grid barrier waits for (default 0);
@@ -88,7 +95,8 @@ typedef struct {
     int64_t sim_halfstep_launches;  /* half-step launches made by simulate */
     int64_t cal_halfstep_launches;  /* half-step launches made by calibrate */
     double sim_halfstep_ms;         /* summed device time of those launches (profile = 1) */
-    double cal_halfstep_ms;
+    double cal_halfstep_ms;         /* cal_mode 1: time of the whole calibration graph;
+                                       cal_mode 3: summed time of the half-step launches */
 } mpr_profile;
 
 typedef struct {

@@ -38,7 +38,6 @@ struct mpr_ctx {
     float* values = nullptr;
     uint8_t* mask = nullptr;
     float* dang = nullptr;
-    float2* dcs = nullptr;
     uint2* list[2] = {nullptr, nullptr};
     int32_t* start[2] = {nullptr, nullptr};
     int32_t* split[2] = {nullptr, nullptr};
@@ -64,8 +63,9 @@ struct mpr_ctx {
     uint32_t r_even = 0;
     int t = 0;
     int batch_open = 0;
-    float* ang = nullptr;
-    size_t ang_cap = 0;
+    int storage = 0;             // element type of the batch state (an mpr_storage)
+    void* ang = nullptr;
+    size_t ang_cap = 0;          // bytes
     float* eacc = nullptr;
     double* ecur = nullptr;      // [nblk][Rp] current E_b of every (block, realization)
     uint8_t* running = nullptr;
@@ -73,12 +73,13 @@ struct mpr_ctx {
     int8_t* sigma = nullptr;
     double* e_last = nullptr;
     int32_t* tcount = nullptr;
-    uint32_t* work = nullptr;    // [nblk * groups] worklist of running items
+    uint32_t* work = nullptr;    // [2][nblk * groups] worklists of running items, by sweep parity
+    uint32_t work_stride = 0;
     size_t blk_cap = 0, lane_cap = 0, work_cap = 0;
     Control* ctl = nullptr;      // device loop state
     Control* h_ctl = nullptr;    // pinned mirror
-    int grid_sweep[2] = {0, 0};  // persistent grid of k_sweep<2>, k_sweep<8>
-    int grid_all[2] = {0, 0};    // grid of k_sweep_all<2>, k_sweep_all<8>
+    int grid_cache[2][3][2] = {};  // full grid of k_sweep by (G = 2 / 8, storage, wide)
+    unsigned long long bound = ~0ull;  // upper bound of the running pairs (from the last read)
     bool energy_dirty = false;
     GridBarrier* bar = nullptr;  // grid barrier of the persistent calibration
     float* med = nullptr;
@@ -174,13 +175,13 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.n_bisect < 0 || o.n_bisect > 65534) return fail(ctx, MPR_EINVAL, "n_bisect in [0, 65534]");
     if (o.cal_chains < 1 || o.cal_chains > 4096) return fail(ctx, MPR_EINVAL, "cal_chains in [1, 4096]");
     if (!(o.t_lo > 0.0f && o.t_hi > o.t_lo)) return fail(ctx, MPR_EINVAL, "need 0 < t_lo < t_hi");
-    if (o.storage != MPR_STORE_F32)
-        return fail(ctx, MPR_EINVAL, "storage %d not supported by this build", o.storage);
+    if (o.storage != MPR_STORE_F32 && o.storage != MPR_STORE_BF16 && o.storage != MPR_STORE_F16)
+        return fail(ctx, MPR_EINVAL, "unknown storage %d", o.storage);
     if (o.group != 0 && o.group != 2 && o.group != 8)
         return fail(ctx, MPR_EINVAL, "group must be 0, 2 or 8");
     if (o.init != MPR_INIT_BLOCK_MEAN && o.init != MPR_INIT_RANDOM)
         return fail(ctx, MPR_EINVAL, "unknown init mode");
-    if (o.cal_mode < 0 || o.cal_mode > 2) return fail(ctx, MPR_EINVAL, "cal_mode must be 0, 1 or 2");
+    if (o.cal_mode < 0 || o.cal_mode > 3) return fail(ctx, MPR_EINVAL, "cal_mode must be 0 ... 3");
     if (o.wait_ms < 1) return fail(ctx, MPR_EINVAL, "wait_ms must be >= 1");
     if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
     return MPR_OK;
@@ -198,18 +199,23 @@ mpr_status copy_out(mpr_ctx* ctx, void* dst, const void* src, size_t n) {
     return MPR_OK;
 }
 
-// Per-batch buffers sized for `lanes` realization lanes.
-mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group) {
+size_t storage_bytes(int storage) { return storage == MPR_STORE_F32 ? 4 : 2; }
+
+// Per-batch buffers sized for `lanes` realization lanes, state elements of
+// type `storage`.
+mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group, int storage) {
     const Geom& g = ctx->g;
     const int G = pick_group(lanes, requested_group);
     const int groups = (lanes + G - 1) / G;
     const int Rp = groups * G;
-    const size_t ang_need = (size_t)groups * 2 * g.H * g.Wh * G;
+    const size_t ang_need = (size_t)groups * 2 * g.H * g.Wh * G * storage_bytes(storage);
     if (ang_need > ctx->ang_cap) {
         dfree(ctx, ctx->ang);
         ctx->ang = nullptr;
         ctx->ang_cap = 0;
-        TRY(dalloc(ctx, &ctx->ang, ang_need));
+        uint8_t* p = nullptr;
+        TRY(dalloc(ctx, &p, ang_need));
+        ctx->ang = p;
         ctx->ang_cap = ang_need;
     }
     const size_t blk_need = (size_t)g.nblk * Rp;
@@ -240,9 +246,12 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group) {
         dfree(ctx, ctx->work);
         ctx->work = nullptr;
         ctx->work_cap = 0;
-        TRY(dalloc(ctx, &ctx->work, work_need));
+        TRY(dalloc(ctx, &ctx->work, 2 * work_need));
         ctx->work_cap = work_need;
     }
+    ctx->work_stride = (uint32_t)work_need;
+    ctx->storage = storage;
+    ctx->bound = ~0ull;
     ctx->G = G;
     ctx->groups = groups;
     ctx->Rp = Rp;
@@ -261,12 +270,13 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
     a.start = ctx->start[colour];
     a.split = ctx->split[colour];
     a.ang = ctx->ang;
-    a.dcs = ctx->dcs;
+    a.dang = ctx->dang;
     a.beta = ctx->beta;
     a.running = simulate ? ctx->running : nullptr;
     a.eacc = ctx->eacc;
     a.ecur = ctx->ecur;
     a.work = simulate ? ctx->work : nullptr;
+    a.work_stride = ctx->work_stride;
     a.ctl = ctx->ctl;
     a.R = ctx->R;
     a.Rp = ctx->Rp;
@@ -276,8 +286,25 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
     return a;
 }
 
-int sweep_grid(mpr_ctx* ctx) { return ctx->grid_sweep[ctx->G == 2 ? 0 : 1]; }
-int sweep_all_grid(mpr_ctx* ctx) { return ctx->grid_all[ctx->G == 2 ? 0 : 1]; }
+// Few items left (the realizations' tail): the wide form, and a grid no
+// larger than the running pairs can fill.
+bool sweep_wide(mpr_ctx* ctx) { return ctx->bound < (unsigned long long)ctx->n_sm * 4; }
+
+int sweep_grid(mpr_ctx* ctx, bool wide) {
+    int& full = ctx->grid_cache[ctx->G == 2 ? 0 : 1][ctx->storage][wide ? 1 : 0];
+    if (full == 0) full = ctx->n_sm * sweep_blocks_per_sm(ctx->G, ctx->storage, wide);
+    const unsigned long long ipc = (unsigned long long)sweep_items_per_cta(ctx->G, wide);
+    const unsigned long long need = (ctx->bound + ipc - 1) / ipc;
+    return (int)std::max<unsigned long long>(1, std::min<unsigned long long>(full, need));
+}
+
+// Grid of the stop kernels: a thread per (item, lane) or per item, capped.
+int stop_grid(mpr_ctx* ctx, int64_t per_item) {
+    const int64_t items = std::min<int64_t>((int64_t)ctx->g.nblk * ctx->groups,
+                                            (int64_t)std::min<unsigned long long>(ctx->bound, 1ull << 40));
+    const int64_t n = std::max<int64_t>(1, items * per_item);
+    return (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->n_sm * 16);
+}
 
 cudaEvent_t get_event(mpr_ctx* ctx) {
     if (!ctx->ev_pool.empty()) {
@@ -302,9 +329,8 @@ mpr_status halfstep_launch(mpr_ctx* ctx, const SweepArgs& a, bool sim) {
         e1 = get_event(ctx);
         if (e0) cudaEventRecord(e0, ctx->s);
     }
-    launch_sweep(a, ctx->G, sweep_grid(ctx), false, ctx->s);
-    CKL();
-    launch_sweep(a, ctx->G, sweep_grid(ctx), true, ctx->s);
+    const bool wide = sweep_wide(ctx);
+    launch_sweep(a, ctx->G, ctx->storage, wide, sweep_grid(ctx, wide), ctx->s);
     CKL();
     if (e0 && e1) {
         cudaEventRecord(e1, ctx->s);
@@ -323,7 +349,7 @@ mpr_status energy_pass(mpr_ctx* ctx) {
     for (int c = 0; c < 2; ++c) {
         SweepArgs a = sweep_args(ctx, c, false);
         a.R = ctx->Rp;
-        launch_energy(a, ctx->G, sweep_grid(ctx), ctx->s);
+        launch_energy(a, ctx->G, ctx->storage, ctx->n_sm * 8, ctx->s);
         CKL();
     }
     return MPR_OK;
@@ -348,8 +374,8 @@ void collect_events(mpr_ctx* ctx) {
 mpr_status init_batch_state(mpr_ctx* ctx) {
     const int random = ctx->opt.init == MPR_INIT_RANDOM;
     for (int c = 0; c < 2; ++c) {
-        launch_init(ctx->g, ctx->list[c], ctx->n_gap[c], c, ctx->init_angle, ctx->ang, ctx->G,
-                    ctx->Rp, random, ctx->rng, ctx->r_even, ctx->s);
+        launch_init(ctx->g, ctx->list[c], ctx->n_gap[c], c, ctx->init_angle, ctx->ang,
+                    ctx->storage, ctx->G, ctx->Rp, random, ctx->rng, ctx->r_even, ctx->s);
         CKL();
     }
     return MPR_OK;
@@ -358,8 +384,11 @@ mpr_status init_batch_state(mpr_ctx* ctx) {
 // After the running flags were overwritten: per-realization counts of running
 // targeted blocks and the worklist of items with a running lane.
 __global__ void k_rebuild(int nblk, int groups, int G, int Rp, const int32_t* Nsp,
-                          const uint8_t* running, int32_t* tcount, Control* ctl, uint32_t* work) {
+                          const uint8_t* running, int32_t* tcount, Control* ctl, uint32_t* work_all,
+                          uint32_t work_stride) {
     const int64_t n = (int64_t)nblk * groups;
+    const uint32_t par = ctl->t & 1u;
+    uint32_t* work = work_all + (size_t)par * work_stride;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n;
          it += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(it / groups), grp = (int)(it % groups);
@@ -370,7 +399,7 @@ __global__ void k_rebuild(int nblk, int groups, int G, int Rp, const int32_t* Ns
             any = true;
             if (Nsp[b] > 0) atomicAdd(&tcount[r], 1);
         }
-        if (any) work[atomicAdd(&ctl->n_work_next, 1u)] = (uint32_t)it;
+        if (any) work[atomicAdd(&ctl->n_work[par], 1u)] = (uint32_t)it;
     }
 }
 
@@ -386,14 +415,14 @@ __global__ void k_fill_valid(uint8_t* running, int64_t n, int Rp, int r_off, int
 // next worklist. Everything the kernels need comes from device memory.
 mpr_status sweep_once(mpr_ctx* ctx) {
     const Geom& g = ctx->g;
-    launch_tick(ctx->ctl, ctx->s);
-    CKL();
     for (int c = 0; c < 2; ++c) TRY(halfstep_launch(ctx, sweep_args(ctx, c, true), true));
-    launch_stop_targeted(g.nblk, ctx->Rp, ctx->ctl, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
+    launch_stop_targeted(ctx->G, ctx->groups, ctx->Rp, stop_grid(ctx, ctx->G), ctx->ctl, ctx->work,
+                         ctx->work_stride, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
                          ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
-    launch_stop_rest(g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->ctl, ctx->Nsp,
-                     ctx->running, ctx->stop, ctx->tcount, ctx->work, ctx->s);
+    launch_stop_rest(g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, stop_grid(ctx, 1),
+                     ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp, ctx->running,
+                     ctx->stop, ctx->tcount, ctx->s);
     CKL();
     ctx->t += 1;
     return MPR_OK;
@@ -411,7 +440,8 @@ mpr_status refresh_energies(mpr_ctx* ctx) {
 // and median fallback, fresh start, E_b from scratch, n_eq + n_meas sweeps
 // with the energies of the last n_meas summed, bisection step. With cond != 0
 // the last kernel also sets the graph's loop condition.
-mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphConditionalHandle cond) {
+mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphConditionalHandle cond,
+                                 bool timed) {
     const Geom& g = ctx->g;
     const mpr_options& o = ctx->opt;
     launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
@@ -424,8 +454,18 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
         for (int c = 0; c < 2; ++c) {
             SweepArgs a = sweep_args(ctx, c, false);
             a.t_fixed = sw;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (timed && ctx->opt.profile) {
+                e0 = get_event(ctx);
+                e1 = get_event(ctx);
+                if (e0) cudaEventRecord(e0, ctx->s);
+            }
             launch_sweep_flat(a, ctx->G, ctx->n_gap[c], ctx->s);
             CKL();
+            if (e0 && e1) {
+                cudaEventRecord(e1, ctx->s);
+                ctx->ev_cal.emplace_back(e0, e1);
+            }
             ++ctx->cal_halfstep_launches;
         }
         launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, sw, ctx->ctl, ctx->inb, ctx->eacc,
@@ -542,7 +582,7 @@ mpr_status calibration_graph(mpr_ctx* ctx, double inv_count) {
     {
         cudaStream_t user = ctx->s;
         ctx->s = ctx->cap;
-        st = calibration_iteration(ctx, inv_count, cond);
+        st = calibration_iteration(ctx, inv_count, cond, false);
         ctx->s = user;
     }
     if (cudaStreamEndCapture(ctx->cap, &captured) != cudaSuccess && st == MPR_OK) goto cuda_fail;
@@ -691,7 +731,6 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     ST(dalloc(ctx, &ctx->values, n));
     ST(dalloc(ctx, &ctx->mask, n));
     ST(dalloc(ctx, &ctx->dang, 2 * plane));
-    ST(dalloc(ctx, &ctx->dcs, 2 * plane));
     ST(dalloc(ctx, &ctx->sum, 2 * plane));
     ST(dalloc(ctx, &ctx->Es, g.nblk));
     ST(dalloc(ctx, &ctx->es, g.nblk));
@@ -723,10 +762,6 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     if (cudaMallocHost(&ctx->h_counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_ctl, sizeof(Control)) != cudaSuccess)
         return bail(MPR_ENOMEM);
-    ctx->grid_sweep[0] = ctx->n_sm * sweep_blocks_per_sm(2);
-    ctx->grid_sweep[1] = ctx->n_sm * sweep_blocks_per_sm(8);
-    ctx->grid_all[0] = ctx->n_sm * sweep_all_blocks_per_sm(2);
-    ctx->grid_all[1] = ctx->n_sm * sweep_all_blocks_per_sm(8);
 
     if (copy_in(ctx, ctx->values, values_in, n * sizeof(float)) != MPR_OK) return bail(MPR_ECUDA);
     if (copy_in(ctx, ctx->mask, mask_in, n) != MPR_OK) return bail(MPR_ECUDA);
@@ -753,8 +788,8 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
             ctx->degenerate = !(ctx->zmax > ctx->zmin);
         }
     }
-    launch_layout(g, ctx->values, ctx->mask, ctx->zmin, ctx->zmax, ctx->degenerate, ctx->m.q,
-                  ctx->dang, ctx->dcs, ctx->s);
+    launch_layout(g, ctx->values, ctx->mask, ctx->zmin, ctx->zmax, ctx->degenerate, ctx->dang,
+                  ctx->s);
     launch_block_stats(g, ctx->values, ctx->mask, ctx->zmin, ctx->zmax, ctx->degenerate,
                        ctx->opt.q, ctx->opt.J, ctx->Es, ctx->Nsp, ctx->Nb, ctx->ssum, ctx->nsamp,
                        ctx->ngap_c[0], ctx->ngap_c[1], ctx->s);
@@ -919,21 +954,27 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     const int chains = o.cal_chains;
     ctx->r_off = 0;
     ctx->r_even = 0;
-    TRY(ensure_batch(ctx, chains, o.group));
+    TRY(ensure_batch(ctx, chains, o.group, MPR_STORE_F32));
     ctx->R = chains;
     launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->ctl, ctx->s);
     CKL();
     const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);
-    launch_fill_samples(g, ctx->mask, ctx->dang, ctx->ang, ctx->G, ctx->groups, ctx->s);
+    launch_fill_samples(g, ctx->mask, ctx->dang, ctx->ang, MPR_STORE_F32, ctx->G, ctx->groups,
+                        ctx->s);
     CKL();
-    bool fallback = o.cal_mode != 2;   // auto and 1: graph; 2: persistent
+    // auto and 1: graph; 2: persistent; 3: a launch per kernel from the host.
+    bool fallback = o.cal_mode != 2;
     if (!fallback) {
         TRY(calibration_persistent(ctx, inv_count, &fallback));
         if (fallback && o.cal_mode == 2)
             return fail(ctx, MPR_ECUDA, "calibration: cooperative launch refused");
     }
     if (fallback) {
-        if (o.n_bisect > 0) TRY(calibration_graph(ctx, inv_count));
+        if (o.n_bisect > 0 && o.cal_mode == 3) {
+            for (int k = 0; k < o.n_bisect; ++k) TRY(calibration_iteration(ctx, inv_count, 0, true));
+        } else if (o.n_bisect > 0) {
+            TRY(calibration_graph(ctx, inv_count));
+        }
         launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
         CKL();
         launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
@@ -957,14 +998,15 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     if (r_base + n > (int64_t)0x1FFFFFFFF) return fail(ctx, MPR_EINVAL, "realization index overflow");
     ctx->r_off = (int)(r_base & 1);
     ctx->r_even = (uint32_t)(r_base - ctx->r_off);
-    TRY(ensure_batch(ctx, n + ctx->r_off, ctx->opt.group));
+    TRY(ensure_batch(ctx, n + ctx->r_off, ctx->opt.group, ctx->opt.storage));
     ctx->R = n;
     ctx->t = 0;
     const int64_t nbr = (int64_t)ctx->g.nblk * ctx->Rp;
     k_fill_valid<<<(int)std::min<int64_t>((nbr + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
         ctx->running, nbr, ctx->Rp, ctx->r_off, ctx->R);
     CKL();
-    launch_fill_samples(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->G, ctx->groups, ctx->s);
+    launch_fill_samples(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->storage, ctx->G, ctx->groups,
+                        ctx->s);
     CKL();
     TRY(init_batch_state(ctx));
     CK(cudaMemsetAsync(ctx->tcount, 0, ctx->Rp * sizeof(int32_t), ctx->s));
@@ -974,8 +1016,9 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->es, ctx->inb, ctx->Nsp, ctx->ngap, ctx->ecur,
                      ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
-    launch_stop_rest(ctx->g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->ctl, ctx->Nsp,
-                     ctx->running, ctx->stop, ctx->tcount, ctx->work, ctx->s);
+    launch_stop_rest(ctx->g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, stop_grid(ctx, 1),
+                     ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp, ctx->running,
+                     ctx->stop, ctx->tcount, ctx->s);
     CKL();
     ctx->energy_dirty = false;
     ctx->batch_open = 1;
@@ -1001,7 +1044,8 @@ mpr_status mpr_sim_end(mpr_ctx* ctx) {
     ctx->err.clear();
     if (!ctx->batch_open) return fail(ctx, MPR_ESTATE, "no open batch (mpr_sim_begin)");
     for (int c = 0; c < 2; ++c) {
-        launch_accumulate(ctx->g, ctx->list[c], ctx->n_gap[c], c, ctx->ang, ctx->G, ctx->groups,
+        launch_accumulate(ctx->g, ctx->list[c], ctx->n_gap[c], c, ctx->ang, ctx->storage, ctx->G,
+                          ctx->groups,
                           ctx->r_off, ctx->R, ctx->sum, ctx->s);
         CKL();
     }
@@ -1046,7 +1090,10 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
                 st = fail(ctx, MPR_ECUDA, "simulate: event synchronisation failed");
                 break;
             }
-            if (flag[(c - 1) & 1] == 0) break;
+            // The running count never grows, so the count read here bounds
+            // the work of every sweep queued from now on.
+            ctx->bound = flag[(c - 1) & 1];
+            if (ctx->bound == 0) break;
         }
         ++c;
     }
@@ -1072,7 +1119,10 @@ mpr_status mpr_halfstep(mpr_ctx* ctx, int32_t colour, int32_t t, int32_t tag) {
     SweepArgs a = sweep_args(ctx, colour, true);
     a.work = nullptr;       // every item; the running flags decide
     a.energy = 0;
-    launch_sweep_all(a, ctx->G, sweep_all_grid(ctx), ctx->s);
+    const unsigned long long bound = ctx->bound;
+    ctx->bound = ~0ull;
+    launch_sweep(a, ctx->G, ctx->storage, false, sweep_grid(ctx, false), ctx->s);
+    ctx->bound = bound;
     CKL();
     CK(cudaStreamSynchronize(ctx->s));
     *ctx->h_ctl = saved;
@@ -1089,8 +1139,8 @@ mpr_status mpr_get_state(mpr_ctx* ctx, int32_t r, float* angles) {
     if (r < 0 || r >= ctx->R) return fail(ctx, MPR_EINVAL, "r out of range");
     const size_t n = (size_t)ctx->g.H * ctx->g.W;
     if (!ctx->out_buf) TRY(dalloc(ctx, &ctx->out_buf, n));
-    launch_get_state(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->G, r + ctx->r_off, ctx->out_buf,
-                     ctx->s);
+    launch_get_state(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->storage, ctx->G, r + ctx->r_off,
+                     ctx->out_buf, ctx->s);
     CKL();
     return copy_out(ctx, angles, ctx->out_buf, n * 4);
 }
@@ -1103,7 +1153,8 @@ mpr_status mpr_set_state(mpr_ctx* ctx, int32_t r, const float* angles) {
     const size_t n = (size_t)ctx->g.H * ctx->g.W;
     if (!ctx->truth_buf) TRY(dalloc(ctx, &ctx->truth_buf, n));
     TRY(copy_in(ctx, ctx->truth_buf, angles, n * 4));
-    launch_set_state(ctx->g, ctx->mask, ctx->ang, ctx->G, r + ctx->r_off, ctx->truth_buf, ctx->s);
+    launch_set_state(ctx->g, ctx->mask, ctx->ang, ctx->storage, ctx->G, r + ctx->r_off,
+                     ctx->truth_buf, ctx->s);
     CKL();
     CK(cudaStreamSynchronize(ctx->s));
     ctx->energy_dirty = true;
@@ -1162,10 +1213,15 @@ mpr_status mpr_set_running(mpr_ctx* ctx, const uint8_t* running) {
             hr[(size_t)b * ctx->Rp + r + ctx->r_off] = in[(size_t)r * nb + b] ? 1 : 0;
     CK(cudaMemcpyAsync(ctx->running, hr.data(), hr.size(), cudaMemcpyHostToDevice, ctx->s));
     CK(cudaMemsetAsync(ctx->tcount, 0, ctx->Rp * sizeof(int32_t), ctx->s));
-    CK(cudaMemsetAsync(&ctx->ctl->n_work_next, 0, sizeof(uint32_t), ctx->s));
+    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    const uint32_t par = ctx->h_ctl->t & 1u;
+    CK(cudaMemsetAsync(&ctx->ctl->n_work[par], 0, sizeof(uint32_t), ctx->s));
     const int64_t items = (int64_t)nb * ctx->groups;
     k_rebuild<<<(int)std::min<int64_t>((items + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
-        nb, ctx->groups, ctx->G, ctx->Rp, ctx->Nsp, ctx->running, ctx->tcount, ctx->ctl, ctx->work);
+        nb, ctx->groups, ctx->G, ctx->Rp, ctx->Nsp, ctx->running, ctx->tcount, ctx->ctl, ctx->work,
+        ctx->work_stride);
+    ctx->bound = ~0ull;
     CKL();
     CK(cudaStreamSynchronize(ctx->s));
     return MPR_OK;
@@ -1178,8 +1234,8 @@ mpr_status mpr_block_energy(mpr_ctx* ctx, int32_t r, double* E) {
     if (r < 0 || r >= ctx->R) return fail(ctx, MPR_EINVAL, "r out of range");
     double* d = nullptr;
     TRY(dalloc(ctx, &d, ctx->g.nblk));
-    launch_block_energy(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->G, r + ctx->r_off, ctx->opt.q,
-                        ctx->opt.J, d, ctx->s);
+    launch_block_energy(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->storage, ctx->G,
+                        r + ctx->r_off, ctx->opt.q, ctx->opt.J, d, ctx->s);
     mpr_status st = MPR_OK;
     if (cudaPeekAtLastError() != cudaSuccess) st = fail(ctx, MPR_ECUDA, "block energy launch failed");
     if (st == MPR_OK) st = copy_out(ctx, E, d, (size_t)ctx->g.nblk * 8);

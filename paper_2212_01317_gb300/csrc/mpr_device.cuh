@@ -68,36 +68,6 @@ struct SiteNew {
     bool refl;      // over-relaxation applied
 };
 
-// Metropolis with an independent uniform proposal on [0, 2pi] at inverse
-// temperature beta, then (optionally) the restricted over-relaxation
-// reflection of q*phi about psi = atan2(S, C), kept when it lands in
-// [0, 2pi]. (C, S) is the neighbour field sum_j (cos q phi_j, sin q phi_j);
-// the site energy is -J (C cos q phi + S sin q phi), so
-// dE = J [(C co + S so) - (C cp + S sp)]; the reflection conserves it.
-__device__ __forceinline__ SiteNew site_update(float phi, float C, float S, float u0, float u1,
-                                               float beta, const Model& m) {
-    SiteNew n;
-    __sincosf(m.q * phi, &n.so, &n.co);
-    const float php = kTwoPi * u0;
-    float sp, cp;
-    __sincosf(m.q * php, &sp, &cp);
-    const float dE = m.J * ((C * n.co + S * n.so) - (C * cp + S * sp));
-    const bool acc = (dE <= 0.0f) || (u1 < __expf(-dE * beta));
-    n.phi = acc ? php : phi;
-    n.dE = acc ? dE : 0.0f;
-    n.ca = acc ? cp : n.co;
-    n.sa = acc ? sp : n.so;
-    // Over-relaxation, without branches. The reflected angle (2 psi - q phi)/q
-    // is >= 0 only if psi >= 0, i.e. S >= 0, so psi is taken from (|S|, C) and
-    // the move is kept only when S >= 0 and the angle lies in [0, 2pi]
-    // (C = S = 0 gives NaN and fails the test).
-    const float psi = atan2_upper(fabsf(S), C);
-    const float por = (2.0f * psi - m.q * n.phi) * m.inv_q;
-    n.refl = m.overrelax && S >= 0.0f && por >= 0.0f && por <= kTwoPi;
-    n.phi = n.refl ? por : n.phi;
-    return n;
-}
-
 // cos / sin of q times the final angle: after a reflection,
 // q phi'' = 2 psi - q phi_a with cos 2psi = (C^2 - S^2)/R^2, sin 2psi = 2CS/R^2.
 __device__ __forceinline__ void final_cs(const SiteNew& n, float C, float S, float& c, float& s) {

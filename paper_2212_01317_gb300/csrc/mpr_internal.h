@@ -2,13 +2,14 @@
 //
 // Device memory of one context (one field):
 //   dang   [2][H][Wh] float   sample angles per checkerboard colour (0 at gaps)
-//   dcs    [2][H][Wh] float2  (cos q*phi, sin q*phi) of sample sites
 //   list_c [n_gap_c]  uint2   gap sites of colour c, block-major, row-major
 //                             within a block: .x = y << 16 | x, .y = b << 10 | flags
 //   start_c[nblk+1]   int32   list_c segment of every block
-//   ang    [groups][2][H][Wh][G]  gap angles of the batch: realization
-//                             r = group * G + lane lives in lane r % G of group
-//                             r / G; sample entries are never read or written
+//   ang    [groups][2][H][Wh][G]  angles of the batch (FP32, FP16 or BF16):
+//                             realization r = group * G + lane lives in lane
+//                             r % G of group r / G; the FP32 form also holds
+//                             the sample angles there, the 16-bit forms read
+//                             samples from dang only
 //   eacc   [nblk][Rp] float   per-sweep energy change of each block (Rp = groups * G)
 //   ecur   [nblk][Rp] double  current block energy E_b
 //   running[nblk][Rp] uint8   1 while block b of realization r still sweeps
@@ -49,16 +50,19 @@ struct Model {
 };
 
 // Device-resident loop state of a batch. Kernels read the sweep index, the
-// random-stream tag and the worklist size from here, so a captured CUDA
-// graph replays sweeps without new launch parameters.
+// random-stream tag and the worklist size from here, so sweeps need no new
+// launch parameters. The worklist is double-buffered by sweep parity: sweep t
+// reads list t & 1, and its stop test writes list (t + 1) & 1.
 struct Control {
     uint32_t t;                  // sweep index of the sweep in progress
     uint32_t tag;                // random-stream tag (0 realizations, 1 + k calibration)
     uint32_t k;                  // calibration iteration
-    uint32_t n_work;             // items in the worklist read by this sweep
-    uint32_t n_work_next;        // items appended by the stop test for the next sweep
+    uint32_t n_work[2];          // worklist sizes by sweep parity
     uint32_t energy_dirty;       // state was overwritten: energies must be recomputed
-    unsigned long long n_running;  // running (block, realization) pairs after the last stop test
+    uint32_t ticket;             // CTAs of the closing stop kernel that have finished
+    uint32_t pad;
+    unsigned long long n_running;      // running (block, realization) pairs after the last stop test
+    unsigned long long n_running_acc;  // the same, being counted by the stop test in progress
 };
 
 // One half-step over the gap sites of one colour, for every running
@@ -71,13 +75,14 @@ struct SweepArgs {
     const uint2* list;        // gap entries of this colour
     const int32_t* start;     // [nblk + 1]
     const int32_t* split;     // [nblk] end of each block's edge entries
-    float* ang;               // batch state [groups][2][H][Wh][G]
-    const float2* dcs;        // [2][H][Wh]
+    void* ang;                // batch state [groups][2][H][Wh][G] (FP32, FP16 or BF16)
+    const float* dang;        // [2][H][Wh] FP32 sample angles (0 at gaps)
     const float* beta;        // [nblk] 1 / T_b
     const uint8_t* running;   // [nblk][Rp] or nullptr (= every lane r < R runs)
     float* eacc;              // [nblk][Rp] energy change of this sweep (moves)
     double* ecur;             // [nblk][Rp] E_b (the energy pass adds into it)
-    const uint32_t* work;     // worklist of items b * groups + group, or nullptr = all items
+    const uint32_t* work;     // two worklists of items b * groups + group, or nullptr = all items
+    uint32_t work_stride;     // elements per worklist
     const Control* ctl;
     int R, Rp, groups;        // realizations in the batch, padded lanes, lane groups
     uint32_t r_base;          // global index of lane 0 (even)

@@ -62,10 +62,9 @@ __global__ void k_minmax(const float* __restrict__ values, const uint8_t* __rest
     }
 }
 
-// Sample angles and their (cos, sin) of q*phi, per checkerboard colour.
+// Sample angles per checkerboard colour (Sec. 2.1 transform).
 __global__ void k_layout(Geom g, const float* __restrict__ values, const uint8_t* __restrict__ mask,
-                         double zmin, double zmax, int degenerate, float q,
-                         float* __restrict__ dang, float2* __restrict__ dcs) {
+                         double zmin, double zmax, int degenerate, float* __restrict__ dang) {
     const int64_t n = (int64_t)g.H * g.W;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -74,17 +73,12 @@ __global__ void k_layout(Geom g, const float* __restrict__ values, const uint8_t
         const size_t h = hidx(g, c, y, x);
         if (mask[i]) {
             dang[h] = 0.0f;
-            dcs[h] = make_float2(0.0f, 0.0f);
             continue;
         }
         const double phi = degenerate ? 0.0
                                       : 6.283185307179586476925 * ((double)values[i] - zmin) /
                                             (zmax - zmin);
-        const float pf = (float)phi;
-        dang[h] = pf;
-        double s, co;
-        sincos((double)q * phi, &s, &co);
-        dcs[h] = make_float2((float)co, (float)s);
+        dang[h] = (float)phi;
     }
 }
 
@@ -239,8 +233,9 @@ __global__ void k_build_lists(Geom g, const uint8_t* __restrict__ mask,
 // Sec. 3.3.3: every gap site starts from the sample mean angle of its block
 // (global sample mean when the block has no sample); random start (plain
 // MPR) draws 2*pi*u from the reserved tag 0xFFFF.
+template <typename S>
 __global__ void k_init(Geom g, const uint2* __restrict__ list, int64_t n_list, int colour,
-                       const float* __restrict__ init_angle, float* __restrict__ ang, int G,
+                       const float* __restrict__ init_angle, S* __restrict__ ang, int G,
                        int Rp, int random, Rng rng, uint32_t r_even) {
     const int64_t total = n_list * Rp;
     const size_t plane = (size_t)g.H * g.Wh;
@@ -260,7 +255,8 @@ __global__ void k_init(Geom g, const uint2* __restrict__ list, int64_t n_list, i
             v = kTwoPi * u01(w[(gr & 1u) * 2u]);
         }
         const int grp = r / G, lane = r % G;
-        ang[(((size_t)(grp * 2 + colour) * plane) + (size_t)y * g.Wh + (x >> 1)) * G + lane] = v;
+        Store<S>::store1(
+            ang + (((size_t)(grp * 2 + colour) * plane) + (size_t)y * g.Wh + (x >> 1)) * G + lane, v);
     }
 }
 
@@ -287,43 +283,23 @@ __global__ void k_fill_samples(Geom g, const uint8_t* __restrict__ mask,
 }
 
 // ----------------------------------------------------------------- sweep --
-// Interior sites. G = 8: a CTA per item, one warp per realization pair.
-// G = 2 (one pair): a warp per item, four items per CTA.
-template <int G>
-__global__ void __launch_bounds__(128, 10) k_sweep(SweepArgs a) {
-    const uint32_t ctr1 = a.ctl->t | (a.ctl->tag << 16);
-    const int n_items = a.work ? (int)a.ctl->n_work : a.g.nblk * a.groups;
-    const int warp = threadIdx.x >> 5;
-    if constexpr (G == 2) {
-        for (int it = blockIdx.x * 4 + warp; it < n_items; it += gridDim.x * 4)
-            sweep_interior_item<G>(a, a.work ? (int)a.work[it] : it, 0, 1, ctr1);
-    } else {
-        for (int it = blockIdx.x; it < n_items; it += gridDim.x)
-            sweep_interior_item<G>(a, a.work ? (int)a.work[it] : it, warp, 4, ctr1);
-    }
-}
-
-// Interior and edge sites of the running items in one launch: warps 0-3 of a
-// CTA take interior sites (G = 8: the four warps share an item, one pair each;
-// G = 2: one item per warp), warps 4-7 take edge sites, one item per warp.
-template <int G>
-__global__ void __launch_bounds__(256) k_sweep_all(SweepArgs a) {
+// One half-step of the batch over the worklist of running items (or every
+// item). WPI warps per item, THREADS / (32 WPI) items per CTA:
+//   G = 8 (four realization pairs): WPI = 4, a CTA of 128 per item; the tail
+//     form WPI = 16 (512 threads) gives every pair four warps, so the few
+//     items left at the end of a batch finish in one pass over their entries.
+//   G = 2 (one pair): WPI = 1, four items per CTA; tail form WPI = 4.
+template <int G, typename S, int WPI, int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 8 : 2) k_sweep(SweepArgs a) {
     const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
     const uint32_t ctr1 = t | (a.ctl->tag << 16);
-    const int n_items = a.work ? (int)a.ctl->n_work : a.g.nblk * a.groups;
+    const uint32_t* work = a.work ? a.work + (size_t)(t & 1u) * a.work_stride : nullptr;
+    const int n_items = work ? (int)a.ctl->n_work[t & 1u] : a.g.nblk * a.groups;
+    constexpr int IPC = THREADS / 32 / WPI;
     const int warp = threadIdx.x >> 5;
-    if (warp < 4) {
-        if constexpr (G == 2) {
-            for (int it = blockIdx.x * 4 + warp; it < n_items; it += gridDim.x * 4)
-                sweep_interior_item2<G>(a, a.work ? (int)a.work[it] : it, 0, 1, ctr1);
-        } else {
-            for (int it = blockIdx.x; it < n_items; it += gridDim.x)
-                sweep_interior_item2<G>(a, a.work ? (int)a.work[it] : it, warp, 4, ctr1);
-        }
-    } else {
-        for (int it = blockIdx.x * 4 + (warp - 4); it < n_items; it += gridDim.x * 4)
-            sweep_edge_item<G>(a, a.work ? (int)a.work[it] : it, ctr1);
-    }
+    const int slot = warp / WPI, wi = warp % WPI;
+    for (int it = blockIdx.x * IPC + slot; it < n_items; it += gridDim.x * IPC)
+        sweep_item<G, S>(a, work ? (int)work[it] : it, wi, WPI, ctr1);
 }
 
 template <int G>
@@ -332,40 +308,15 @@ __global__ void __launch_bounds__(kFlatThreads) k_sweep_flat(SweepArgs a, int64_
     sweep_flat<G>(a, n_list, t | (a.ctl->tag << 16));
 }
 
-template <int G>
-__global__ void __launch_bounds__(128) k_sweep_edge(SweepArgs a) {
-    const uint32_t ctr1 = a.ctl->t | (a.ctl->tag << 16);
-    const int n_items = a.work ? (int)a.ctl->n_work : a.g.nblk * a.groups;
-    const int wpb = blockDim.x >> 5;
-    for (int it = blockIdx.x * wpb + (threadIdx.x >> 5); it < n_items; it += gridDim.x * wpb)
-        sweep_edge_item<G>(a, a.work ? (int)a.work[it] : it, ctr1);
-}
-
-template <int G>
+template <int G, typename S>
 __global__ void __launch_bounds__(128) k_energy(SweepArgs a) {
     const int n_items = a.g.nblk * a.groups;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) energy_item<G>(a, it, threadIdx.x >> 5, 4);
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x)
+        energy_item<G, S>(a, it, threadIdx.x >> 5, 4);
 }
 
-template __global__ void k_sweep<2>(SweepArgs);
-template __global__ void k_sweep<8>(SweepArgs);
-template __global__ void k_sweep_edge<2>(SweepArgs);
-template __global__ void k_sweep_edge<8>(SweepArgs);
-template __global__ void k_sweep_all<2>(SweepArgs);
-template __global__ void k_sweep_all<8>(SweepArgs);
 template __global__ void k_sweep_flat<2>(SweepArgs, int64_t);
 template __global__ void k_sweep_flat<8>(SweepArgs, int64_t);
-template __global__ void k_energy<2>(SweepArgs);
-template __global__ void k_energy<8>(SweepArgs);
-
-// Advances the sweep index and hands the worklist built by the last stop
-// test to the sweep that starts.
-__global__ void k_tick(Control* ctl) {
-    ctl->t += 1;
-    ctl->n_work = ctl->n_work_next;
-    ctl->n_work_next = 0;
-    ctl->n_running = 0;
-}
 
 // ------------------------------------------------------------------ stop --
 // es[b] = E_s,b / N_SP,b (0 without sample bonds) and inb[b] = 1 / N_b (0 for
@@ -409,67 +360,102 @@ __global__ void k_stop_init(int nblk, int Rp, const double* __restrict__ es,
     }
 }
 
-// After sweep t: E_b += the sweep's change; targeted blocks stop once
-// sigma (e_b(t) - e_s,b) >= 0. e_last keeps e_b(t) for inspection.
-__global__ void k_stop_targeted(int nblk, int Rp, const Control* __restrict__ ctl,
+// The stop test after sweep t, over the items of the sweep's worklist (every
+// running (block, realization) pair belongs to one of them), in two kernels:
+// the second needs the final per-realization count of running targeted
+// blocks, which the first completes.
+//
+// k_stop_targeted: E_b += the sweep's change (eacc, then cleared);
+// e_b = E_b / N_b; a targeted block stops once sigma (e_b(t) - e_s,b) >= 0.
+// One thread per (item, lane).
+__global__ void k_stop_targeted(int G, int groups, int Rp, Control* __restrict__ ctl,
+                                const uint32_t* __restrict__ work, uint32_t work_stride,
                                 const double* __restrict__ es, const double* __restrict__ inb,
                                 const int32_t* __restrict__ Nsp, float* __restrict__ eacc,
                                 double* __restrict__ ecur, const int8_t* __restrict__ sigma,
                                 uint8_t* __restrict__ running, int32_t* __restrict__ stop,
                                 int32_t* __restrict__ tcount, double* __restrict__ e_last) {
-    const int64_t n = (int64_t)nblk * Rp;
-    const int t_sweep = (int)ctl->t;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const float acc = eacc[t];
-        if (acc != 0.0f) eacc[t] = 0.0f;
-        if (!running[t]) continue;
-        const int b = (int)(t / Rp), r = (int)(t % Rp);
-        const double E = ecur[t] + (double)acc;
-        ecur[t] = E;
+    const uint32_t t_sweep = ctl->t;
+    const uint32_t* w = work + (size_t)(t_sweep & 1u) * work_stride;
+    const int64_t n = (int64_t)ctl->n_work[t_sweep & 1u] * G;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t item = w[i / G];
+        const int b = (int)(item / (uint32_t)groups);
+        const int r = (int)(item % (uint32_t)groups) * G + (int)(i % G);
+        const size_t k = (size_t)b * Rp + r;
+        if (!running[k]) continue;
+        const double E = ecur[k] + (double)eacc[k];
+        eacc[k] = 0.0f;
+        ecur[k] = E;
         const double e = E * inb[b];
-        e_last[t] = e;
+        e_last[k] = e;
         if (Nsp[b] == 0) continue;
-        const int sg = sigma[t];
+        const int sg = sigma[k];
         const bool reached = sg > 0 ? (e >= es[b]) : (sg < 0 ? (e <= es[b]) : true);
         if (reached) {
-            running[t] = 0;
-            stop[t] = t_sweep;
+            running[k] = 0;
+            stop[k] = (int32_t)t_sweep;
             atomicSub(&tcount[r], 1);
         }
     }
 }
 
-// Blocks without sample bonds stop when no targeted block of their
-// realization runs; every block stops at n_max. One thread per (block, lane
-// group) item: items with a running lane go on the next sweep's worklist.
+// k_stop_rest: blocks without sample bonds stop when no targeted block of
+// their realization runs; everything stops at n_max. Items with a lane still
+// running go on the next sweep's worklist. One thread per item of the
+// worklist (`work` == nullptr: every item, as at t = 0). The CTA that
+// finishes last closes the sweep: t + 1, the next worklist's size, the
+// running count, and a cleared counter for the list after it.
 __global__ void k_stop_rest(int nblk, int groups, int G, int Rp, int n_max,
-                            Control* __restrict__ ctl, const int32_t* __restrict__ Nsp,
-                            uint8_t* __restrict__ running, int32_t* __restrict__ stop,
-                            const int32_t* __restrict__ tcount, uint32_t* __restrict__ work) {
-    const int64_t n = (int64_t)nblk * groups;
-    const int t_sweep = (int)ctl->t;
+                            Control* __restrict__ ctl, const uint32_t* __restrict__ work,
+                            uint32_t* __restrict__ work_all, uint32_t work_stride,
+                            const int32_t* __restrict__ Nsp, uint8_t* __restrict__ running,
+                            int32_t* __restrict__ stop, const int32_t* __restrict__ tcount) {
+    const uint32_t t_sweep = ctl->t;
+    const uint32_t par = t_sweep & 1u, nxt = par ^ 1u;
+    const uint32_t* w = work ? work + (size_t)par * work_stride : nullptr;
+    uint32_t* out = work_all + (size_t)nxt * work_stride;
+    const int64_t n = w ? (int64_t)ctl->n_work[par] : (int64_t)nblk * groups;
     unsigned cnt = 0;
-    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n;
-         it += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(it / groups), grp = (int)(it % groups);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t item = w ? w[i] : (uint32_t)i;
+        const int b = (int)(item / (uint32_t)groups), grp = (int)(item % (uint32_t)groups);
         bool any = false;
         for (int g = 0; g < G; ++g) {
             const int r = grp * G + g;
             const size_t k = (size_t)b * Rp + r;
             if (!running[k]) continue;
-            if ((Nsp[b] == 0 && tcount[r] == 0) || t_sweep >= n_max) {
+            if ((Nsp[b] == 0 && tcount[r] == 0) || (int)t_sweep >= n_max) {
                 running[k] = 0;
-                stop[k] = t_sweep;
+                stop[k] = (int32_t)t_sweep;
             } else {
                 ++cnt;
                 any = true;
             }
         }
-        if (any) work[atomicAdd(&ctl->n_work_next, 1u)] = (uint32_t)it;
+        if (any) out[atomicAdd(&ctl->n_work[nxt], 1u)] = item;
     }
     for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&ctl->n_running, (unsigned long long)cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&ctl->n_running_acc, (unsigned long long)cnt);
+    // Last CTA out closes the sweep (every other CTA's atomics are visible to
+    // it after its ticket: each CTA fences before taking one).
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        ctl->n_running = atomicExch(&ctl->n_running_acc, 0ull);
+        ctl->n_work[par] = 0;
+        ctl->ticket = 0;
+        ctl->t = t_sweep + 1;
+        __threadfence();
+    }
 }
 
 // Site updates run by the batch: sum over (b, r) of stop sweep x gap sites.
@@ -566,8 +552,9 @@ __global__ void k_cal_update(int nblk, double inv_count, const double* __restric
 
 // --------------------------------------------------------------- predict --
 // Adds the batch's final angles of every gap site to the running sums.
+template <typename S>
 __global__ void k_accumulate(Geom g, const uint2* __restrict__ list, int64_t n_list, int colour,
-                             const float* __restrict__ ang, int G, int groups, int r_off, int R,
+                             const S* __restrict__ ang, int G, int groups, int r_off, int R,
                              double* __restrict__ sum) {
     const size_t plane = (size_t)g.H * g.Wh;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_list;
@@ -578,7 +565,7 @@ __global__ void k_accumulate(Geom g, const uint2* __restrict__ list, int64_t n_l
         double s = 0.0;
         for (int r = r_off; r < r_off + R; ++r) {
             const int grp = r / G, lane = r % G;
-            s += (double)ang[((size_t)(grp * 2 + colour) * plane + hs) * G + lane];
+            s += (double)Store<S>::load1(ang + ((size_t)(grp * 2 + colour) * plane + hs) * G + lane);
         }
         sum[(size_t)colour * plane + hs] += s;
     }
@@ -645,8 +632,9 @@ __global__ void k_predict(Geom g, const float* __restrict__ values,
 }
 
 // ------------------------------------------------------- state access --
+template <typename S>
 __global__ void k_get_state(Geom g, const uint8_t* __restrict__ mask, const float* __restrict__ dang,
-                            const float* __restrict__ ang, int G, int r, float* __restrict__ out) {
+                            const S* __restrict__ ang, int G, int r, float* __restrict__ out) {
     const int64_t n = (int64_t)g.H * g.W;
     const size_t plane = (size_t)g.H * g.Wh;
     const int grp = r / G, lane = r % G;
@@ -655,12 +643,13 @@ __global__ void k_get_state(Geom g, const uint8_t* __restrict__ mask, const floa
         const int y = (int)(i / g.W), x = (int)(i % g.W);
         const int c = (x + y) & 1;
         const size_t hs = (size_t)y * g.Wh + (x >> 1);
-        out[i] = mask[i] ? ang[((size_t)(grp * 2 + c) * plane + hs) * G + lane]
+        out[i] = mask[i] ? Store<S>::load1(ang + ((size_t)(grp * 2 + c) * plane + hs) * G + lane)
                          : dang[(size_t)c * plane + hs];
     }
 }
 
-__global__ void k_set_state(Geom g, const uint8_t* __restrict__ mask, float* __restrict__ ang,
+template <typename S>
+__global__ void k_set_state(Geom g, const uint8_t* __restrict__ mask, S* __restrict__ ang,
                             int G, int r, const float* __restrict__ in) {
     const int64_t n = (int64_t)g.H * g.W;
     const size_t plane = (size_t)g.H * g.Wh;
@@ -671,13 +660,14 @@ __global__ void k_set_state(Geom g, const uint8_t* __restrict__ mask, float* __r
         const int y = (int)(i / g.W), x = (int)(i % g.W);
         const int c = (x + y) & 1;
         const size_t hs = (size_t)y * g.Wh + (x >> 1);
-        ang[((size_t)(grp * 2 + c) * plane + hs) * G + lane] = in[i];
+        Store<S>::store1(ang + ((size_t)(grp * 2 + c) * plane + hs) * G + lane, in[i]);
     }
 }
 
 // E_b from scratch in FP64 (one warp per block): Eq. 1 over the owned bonds.
+template <typename S>
 __global__ void k_block_energy(Geom g, const uint8_t* __restrict__ mask,
-                               const float* __restrict__ dang, const float* __restrict__ ang, int G,
+                               const float* __restrict__ dang, const S* __restrict__ ang, int G,
                                int r, double q, double J, double* __restrict__ E) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -687,8 +677,9 @@ __global__ void k_block_energy(Geom g, const uint8_t* __restrict__ mask,
     auto angle = [&](int y, int x) -> double {
         const int c = (x + y) & 1;
         const size_t hs = (size_t)y * g.Wh + (x >> 1);
-        return mask[(int64_t)y * g.W + x] ? (double)ang[((size_t)(grp * 2 + c) * plane + hs) * G + ln]
-                                          : (double)dang[(size_t)c * plane + hs];
+        return mask[(int64_t)y * g.W + x]
+                   ? (double)Store<S>::load1(ang + ((size_t)(grp * 2 + c) * plane + hs) * G + ln)
+                   : (double)dang[(size_t)c * plane + hs];
     };
     const int by = warp / g.nbx, bx = warp % g.nbx;
     const int y0 = by * g.lb, x0 = bx * g.lb;
@@ -721,9 +712,9 @@ void launch_minmax(const float* values, const uint8_t* mask, int64_t n, uint32_t
 }
 
 void launch_layout(const Geom& g, const float* values, const uint8_t* mask, double zmin,
-                   double zmax, int degenerate, float q, float* dang, float2* dcs, cudaStream_t s) {
+                   double zmax, int degenerate, float* dang, cudaStream_t s) {
     k_layout<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, values, mask, zmin, zmax,
-                                                              degenerate, q, dang, dcs);
+                                                              degenerate, dang);
 }
 
 void launch_block_stats(const Geom& g, const float* values, const uint8_t* mask, double zmin,
@@ -748,33 +739,85 @@ void launch_build_lists(const Geom& g, const uint8_t* mask, const int32_t* start
     k_build_lists<<<blocks, threads, 0, s>>>(g, mask, start0, start1, list0, list1, split0, split1);
 }
 
+namespace {
+template <typename S> struct Tag { using type = S; };
+// Calls f(Tag<S>) with the state element type of `storage` (an mpr_storage).
+template <typename F> void with_storage(int storage, F&& f) {
+    if (storage == 1) f(Tag<__nv_bfloat16>{});
+    else if (storage == 2) f(Tag<__half>{});
+    else f(Tag<float>{});
+}
+}  // namespace
+
 void launch_init(const Geom& g, const uint2* list, int64_t n_list, int colour,
-                 const float* init_angle, float* ang, int G, int Rp, int random, Rng rng,
-                 uint32_t r_even, cudaStream_t s) {
+                 const float* init_angle, void* ang, int storage, int G, int Rp, int random,
+                 Rng rng, uint32_t r_even, cudaStream_t s) {
     if (n_list == 0) return;
-    k_init<<<grid_for(n_list * Rp, 256), 256, 0, s>>>(g, list, n_list, colour, init_angle, ang, G,
-                                                     Rp, random, rng, r_even);
+    with_storage(storage, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k_init<S><<<grid_for(n_list * Rp, 256), 256, 0, s>>>(
+            g, list, n_list, colour, init_angle, static_cast<S*>(ang), G, Rp, random, rng, r_even);
+    });
 }
 
-void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, float* ang, int G,
-                         int groups, cudaStream_t s) {
-    k_fill_samples<<<grid_for((int64_t)g.H * g.W * groups, 256), 256, 0, s>>>(g, mask, dang, ang, G,
-                                                                             groups);
+void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, void* ang,
+                         int storage, int G, int groups, cudaStream_t s) {
+    if (storage != 0) return;        // the 16-bit forms read samples from dang
+    k_fill_samples<<<grid_for((int64_t)g.H * g.W * groups, 256), 256, 0, s>>>(
+        g, mask, dang, static_cast<float*>(ang), G, groups);
 }
 
-void launch_sweep(const SweepArgs& a, int G, int grid, bool edge, cudaStream_t s) {
-    if (G == 2) {
-        if (edge) k_sweep_edge<2><<<grid, 128, 0, s>>>(a);
-        else k_sweep<2><<<grid, 128, 0, s>>>(a);
+namespace {
+template <int G, typename S>
+void sweep_dispatch(const SweepArgs& a, bool wide, int grid, cudaStream_t s) {
+    if constexpr (G == 2) {
+        if (wide) k_sweep<2, S, 4, 128><<<grid, 128, 0, s>>>(a);
+        else k_sweep<2, S, 1, 128><<<grid, 128, 0, s>>>(a);
     } else {
-        if (edge) k_sweep_edge<8><<<grid, 128, 0, s>>>(a);
-        else k_sweep<8><<<grid, 128, 0, s>>>(a);
+        if (wide) k_sweep<8, S, 16, 512><<<grid, 512, 0, s>>>(a);
+        else k_sweep<8, S, 4, 128><<<grid, 128, 0, s>>>(a);
     }
 }
 
-void launch_energy(const SweepArgs& a, int G, int grid, cudaStream_t s) {
-    if (G == 2) k_energy<2><<<grid, 128, 0, s>>>(a);
-    else k_energy<8><<<grid, 128, 0, s>>>(a);
+template <int G, typename S>
+int sweep_occupancy(bool wide) {
+    int n = 0;
+    if constexpr (G == 2) {
+        if (wide) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 4, 128>, 128, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 1, 128>, 128, 0);
+    } else {
+        if (wide) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 16, 512>, 512, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 4, 128>, 128, 0);
+    }
+    return n > 0 ? n : 1;
+}
+}  // namespace
+
+void launch_sweep(const SweepArgs& a, int G, int storage, bool wide, int grid, cudaStream_t s) {
+    with_storage(storage, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        if (G == 2) sweep_dispatch<2, S>(a, wide, grid, s);
+        else sweep_dispatch<8, S>(a, wide, grid, s);
+    });
+}
+
+int sweep_blocks_per_sm(int G, int storage, bool wide) {
+    int n = 1;
+    with_storage(storage, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        n = G == 2 ? sweep_occupancy<2, S>(wide) : sweep_occupancy<8, S>(wide);
+    });
+    return n;
+}
+
+int sweep_items_per_cta(int G, bool wide) { return (G == 2 && !wide) ? 4 : 1; }
+
+void launch_energy(const SweepArgs& a, int G, int storage, int grid, cudaStream_t s) {
+    with_storage(storage, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        if (G == 2) k_energy<2, S><<<grid, 128, 0, s>>>(a);
+        else k_energy<8, S><<<grid, 128, 0, s>>>(a);
+    });
 }
 
 void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s) {
@@ -784,27 +827,6 @@ void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s
     if (G == 2) k_sweep_flat<2><<<grid, kFlatThreads, 0, s>>>(a, n_list);
     else k_sweep_flat<8><<<grid, kFlatThreads, 0, s>>>(a, n_list);
 }
-
-void launch_sweep_all(const SweepArgs& a, int G, int grid, cudaStream_t s) {
-    if (G == 2) k_sweep_all<2><<<grid, 256, 0, s>>>(a);
-    else k_sweep_all<8><<<grid, 256, 0, s>>>(a);
-}
-
-int sweep_all_blocks_per_sm(int G) {
-    int n = 0;
-    if (G == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_all<2>, 256, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_all<8>, 256, 0);
-    return n > 0 ? n : 1;
-}
-
-int sweep_blocks_per_sm(int G) {
-    int n = 0;
-    if (G == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8>, 128, 0);
-    return n > 0 ? n : 1;
-}
-
-void launch_tick(Control* ctl, cudaStream_t s) { k_tick<<<1, 1, 0, s>>>(ctl); }
 
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
                        cudaStream_t s) {
@@ -818,19 +840,21 @@ void launch_stop_init(int nblk, int Rp, const double* es, const double* inb, con
         nblk, Rp, es, inb, Nsp, ngap, ecur, sigma, running, stop, tcount, e_last);
 }
 
-void launch_stop_targeted(int nblk, int Rp, const Control* ctl, const double* es,
+void launch_stop_targeted(int G, int groups, int Rp, int grid, Control* ctl,
+                          const uint32_t* work, uint32_t work_stride, const double* es,
                           const double* inb, const int32_t* Nsp, float* eacc, double* ecur,
                           const int8_t* sigma, uint8_t* running, int32_t* stop, int32_t* tcount,
                           double* e_last, cudaStream_t s) {
-    k_stop_targeted<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(
-        nblk, Rp, ctl, es, inb, Nsp, eacc, ecur, sigma, running, stop, tcount, e_last);
+    k_stop_targeted<<<grid, 256, 0, s>>>(G, groups, Rp, ctl, work, work_stride, es, inb, Nsp, eacc,
+                                         ecur, sigma, running, stop, tcount, e_last);
 }
 
-void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, Control* ctl,
+void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, int grid, Control* ctl,
+                      const uint32_t* work, uint32_t* work_all, uint32_t work_stride,
                       const int32_t* Nsp, uint8_t* running, int32_t* stop, const int32_t* tcount,
-                      uint32_t* work, cudaStream_t s) {
-    k_stop_rest<<<grid_for((int64_t)nblk * groups, 256), 256, 0, s>>>(
-        nblk, groups, G, Rp, n_max, ctl, Nsp, running, stop, tcount, work);
+                      cudaStream_t s) {
+    k_stop_rest<<<grid, 256, 0, s>>>(nblk, groups, G, Rp, n_max, ctl, work, work_all, work_stride,
+                                     Nsp, running, stop, tcount);
 }
 
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
@@ -866,11 +890,14 @@ void launch_cal_update(int nblk, double inv_count, const double* es, const int32
 }
 
 void launch_accumulate(const Geom& g, const uint2* list, int64_t n_list, int colour,
-                       const float* ang, int G, int groups, int r_off, int R, double* sum,
-                       cudaStream_t s) {
+                       const void* ang, int storage, int G, int groups, int r_off, int R,
+                       double* sum, cudaStream_t s) {
     if (n_list == 0) return;
-    k_accumulate<<<grid_for(n_list, 256), 256, 0, s>>>(g, list, n_list, colour, ang, G, groups,
-                                                      r_off, R, sum);
+    with_storage(storage, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k_accumulate<S><<<grid_for(n_list, 256), 256, 0, s>>>(
+            g, list, n_list, colour, static_cast<const S*>(ang), G, groups, r_off, R, sum);
+    });
 }
 
 void launch_sum_to_grid(const Geom& g, const uint8_t* mask, const double* sum, double* out,
@@ -890,21 +917,34 @@ void launch_predict(const Geom& g, const float* values, const uint8_t* mask, con
                                                                zmax, out, truth, err);
 }
 
-void launch_get_state(const Geom& g, const uint8_t* mask, const float* dang, const float* ang,
-                      int G, int r, float* out, cudaStream_t s) {
-    k_get_state<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, mask, dang, ang, G, r, out);
+void launch_get_state(const Geom& g, const uint8_t* mask, const float* dang, const void* ang,
+                      int storage, int G, int r, float* out, cudaStream_t s) {
+    with_storage(storage, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k_get_state<S><<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(
+            g, mask, dang, static_cast<const S*>(ang), G, r, out);
+    });
 }
 
-void launch_set_state(const Geom& g, const uint8_t* mask, float* ang, int G, int r,
+void launch_set_state(const Geom& g, const uint8_t* mask, void* ang, int storage, int G, int r,
                       const float* in, cudaStream_t s) {
-    k_set_state<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, mask, ang, G, r, in);
+    with_storage(storage, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k_set_state<S><<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(
+            g, mask, static_cast<S*>(ang), G, r, in);
+    });
 }
 
-void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, const float* ang,
-                         int G, int r, double q, double J, double* E, cudaStream_t s) {
+void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, const void* ang,
+                         int storage, int G, int r, double q, double J, double* E,
+                         cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((int64_t)g.nblk * 32 + threads - 1) / threads);
-    k_block_energy<<<blocks, threads, 0, s>>>(g, mask, dang, ang, G, r, q, J, E);
+    with_storage(storage, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k_block_energy<S><<<blocks, threads, 0, s>>>(g, mask, dang, static_cast<const S*>(ang), G,
+                                                     r, q, J, E);
+    });
 }
 
 }  // namespace mpr

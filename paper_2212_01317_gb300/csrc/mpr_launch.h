@@ -13,7 +13,7 @@ float ord2f(uint32_t u);
 void launch_minmax(const float* values, const uint8_t* mask, int64_t n, uint32_t* mm,
                    cudaStream_t s);
 void launch_layout(const Geom& g, const float* values, const uint8_t* mask, double zmin,
-                   double zmax, int degenerate, float q, float* dang, float2* dcs, cudaStream_t s);
+                   double zmax, int degenerate, float* dang, cudaStream_t s);
 void launch_block_stats(const Geom& g, const float* values, const uint8_t* mask, double zmin,
                         double zmax, int degenerate, double q, double J, double* Es, int32_t* Nsp,
                         int32_t* Nb, double* ssum, int32_t* nsamp, int32_t* ngap0, int32_t* ngap1,
@@ -22,30 +22,35 @@ void launch_scan(const int32_t* cnt, int n, int32_t* out, cudaStream_t s);
 void launch_build_lists(const Geom& g, const uint8_t* mask, const int32_t* start0,
                         const int32_t* start1, uint2* list0, uint2* list1, int32_t* split0,
                         int32_t* split1, cudaStream_t s);
+// `storage` is an mpr_storage value (0 FP32, 1 BF16, 2 FP16): the element
+// type of the batch state `ang`.
 void launch_init(const Geom& g, const uint2* list, int64_t n_list, int colour,
-                 const float* init_angle, float* ang, int G, int Rp, int random, Rng rng,
-                 uint32_t r_even, cudaStream_t s);
-void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, float* ang, int G,
-                         int groups, cudaStream_t s);
-void launch_sweep(const SweepArgs& a, int G, int grid, bool edge, cudaStream_t s);
-void launch_energy(const SweepArgs& a, int G, int grid, cudaStream_t s);
-int sweep_blocks_per_sm(int G);
-void launch_sweep_all(const SweepArgs& a, int G, int grid, cudaStream_t s);
+                 const float* init_angle, void* ang, int storage, int G, int Rp, int random,
+                 Rng rng, uint32_t r_even, cudaStream_t s);
+void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, void* ang,
+                         int storage, int G, int groups, cudaStream_t s);
+// wide: the tail form with more warps per item (few items left).
+void launch_sweep(const SweepArgs& a, int G, int storage, bool wide, int grid, cudaStream_t s);
+int sweep_blocks_per_sm(int G, int storage, bool wide);
+int sweep_items_per_cta(int G, bool wide);
+void launch_energy(const SweepArgs& a, int G, int storage, int grid, cudaStream_t s);
 void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s);
-int sweep_all_blocks_per_sm(int G);
-void launch_tick(Control* ctl, cudaStream_t s);
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
                        cudaStream_t s);
 void launch_stop_init(int nblk, int Rp, const double* es, const double* inb, const int32_t* Nsp,
                       const int32_t* ngap, const double* ecur, int8_t* sigma, uint8_t* running,
                       int32_t* stop, int32_t* tcount, double* e_last, cudaStream_t s);
-void launch_stop_targeted(int nblk, int Rp, const Control* ctl, const double* es,
+void launch_stop_targeted(int G, int groups, int Rp, int grid, Control* ctl,
+                          const uint32_t* work, uint32_t work_stride, const double* es,
                           const double* inb, const int32_t* Nsp, float* eacc, double* ecur,
                           const int8_t* sigma, uint8_t* running, int32_t* stop, int32_t* tcount,
                           double* e_last, cudaStream_t s);
-void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, Control* ctl,
+// work == nullptr: every item (t = 0). Writes the next sweep's worklist into
+// work_all and advances ctl->t.
+void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, int grid, Control* ctl,
+                      const uint32_t* work, uint32_t* work_all, uint32_t work_stride,
                       const int32_t* Nsp, uint8_t* running, int32_t* stop, const int32_t* tcount,
-                      uint32_t* work, cudaStream_t s);
+                      cudaStream_t s);
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
                           unsigned long long* total, cudaStream_t s);
 void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,
@@ -59,8 +64,8 @@ void launch_cal_update(int nblk, double inv_count, const double* es, const int32
                        const float* T, float* lo, float* hi, double* ebar, Control* ctl,
                        int n_bisect, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_accumulate(const Geom& g, const uint2* list, int64_t n_list, int colour,
-                       const float* ang, int G, int groups, int r_off, int R, double* sum,
-                       cudaStream_t s);
+                       const void* ang, int storage, int G, int groups, int r_off, int R,
+                       double* sum, cudaStream_t s);
 void launch_sum_to_grid(const Geom& g, const uint8_t* mask, const double* sum, double* out,
                         cudaStream_t s);
 void launch_grid_to_sum(const Geom& g, const uint8_t* mask, const double* in, double* sum,
@@ -68,12 +73,13 @@ void launch_grid_to_sum(const Geom& g, const uint8_t* mask, const double* in, do
 void launch_predict(const Geom& g, const float* values, const uint8_t* mask, const double* sum,
                     double inv_r, double zmin, double zmax, float* out, const float* truth,
                     double* err, cudaStream_t s);
-void launch_get_state(const Geom& g, const uint8_t* mask, const float* dang, const float* ang,
-                      int G, int r, float* out, cudaStream_t s);
-void launch_set_state(const Geom& g, const uint8_t* mask, float* ang, int G, int r,
+void launch_get_state(const Geom& g, const uint8_t* mask, const float* dang, const void* ang,
+                      int storage, int G, int r, float* out, cudaStream_t s);
+void launch_set_state(const Geom& g, const uint8_t* mask, void* ang, int storage, int G, int r,
                       const float* in, cudaStream_t s);
-void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, const float* ang,
-                         int G, int r, double q, double J, double* E, cudaStream_t s);
+void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, const void* ang,
+                         int storage, int G, int r, double q, double J, double* E,
+                         cudaStream_t s);
 
 int cal_persistent_blocks_per_sm(int G);
 cudaError_t launch_cal_persistent(const CalPersistArgs& a, int G, int grid, cudaStream_t s);

@@ -97,8 +97,7 @@ __device__ __forceinline__ void fold_sweep(const CalPersistArgs& a, int sweep, i
 }  // namespace
 
 // One CTA of 512 threads (16 warps) per SM. Items are taken by groups of four
-// warps (energy pass; interior sites with G = 8) or by single warps (edge
-// sites; interior sites with G = 2).
+// warps (energy pass; sweeps with G = 8) or by single warps (sweeps with G = 2).
 template <int G>
 __global__ void __launch_bounds__(512, 1) k_cal_persistent(CalPersistArgs a) {
     unsigned int gen = 0;
@@ -152,8 +151,8 @@ __global__ void __launch_bounds__(512, 1) k_cal_persistent(CalPersistArgs a) {
                     v = kTwoPi * u01(w[(r & 1) * 2]);
                 }
                 const int grp = r / G, lane = r % G;
-                a.sw.ang[((size_t)(grp * 2 + c) * plane + (size_t)y * a.sw.g.Wh + (x >> 1)) * G +
-                         lane] = v;
+                static_cast<float*>(a.sw.ang)[((size_t)(grp * 2 + c) * plane +
+                                               (size_t)y * a.sw.g.Wh + (x >> 1)) * G + lane] = v;
             }
         }
         for (int64_t t = tid; t < (int64_t)nblk * Rp; t += nthr) {
@@ -165,7 +164,7 @@ __global__ void __launch_bounds__(512, 1) k_cal_persistent(CalPersistArgs a) {
         // E_b of the start state from scratch.
         for (int c = 0; c < 2; ++c) {
             const SweepArgs s = colour_args(a, c);
-            for (int it = gquad; it < n_items; it += nquads) energy_item<G>(s, it, warp & 3, 4);
+            for (int it = gquad; it < n_items; it += nquads) energy_item<G, float>(s, it, warp & 3, 4);
         }
         if (!grid_sync(a.bar, gen, lim)) return;
         // n_eq + n_meas sweeps; the change of sweep t is folded into E_b while
@@ -177,12 +176,11 @@ __global__ void __launch_bounds__(512, 1) k_cal_persistent(CalPersistArgs a) {
                 s.eacc = a.eacc2[sweep & 1];
                 if constexpr (G == 2) {
                     for (int it = gwarp; it < n_items; it += nwarps)
-                        sweep_interior_item<G>(s, it, 0, 1, ctr1);
+                        sweep_item<G, float>(s, it, 0, 1, ctr1);
                 } else {
                     for (int it = gquad; it < n_items; it += nquads)
-                        sweep_interior_item<G>(s, it, warp & 3, 4, ctr1);
+                        sweep_item<G, float>(s, it, warp & 3, 4, ctr1);
                 }
-                for (int it = gwarp; it < n_items; it += nwarps) sweep_edge_item<G>(s, it, ctr1);
                 if (c == 0 && sweep > 1) fold_sweep(a, sweep - 1, tid, nthr);
                 if (!grid_sync(a.bar, gen, lim)) return;
             }

@@ -7,14 +7,16 @@
 // lane updates its site in both realizations of one realization pair, from
 // one Philox block: words 0, 1 for the even realization, 2, 3 for the odd.
 //
-// Block energies are kept incrementally: a Metropolis move changes the energy
-// of the site's four bonds by dE and the reflection conserves it, so a site
-// whose bonds all belong to its own block adds dE there. A site on the left or
-// top edge of its block splits the change bond by bond, because its left / up
-// bond belongs to the neighbouring block (a bond is owned by the block of its
-// left / upper site). Frozen sites never move, so stopped (block, realization)
-// pairs cost nothing.
+// Block energies are kept incrementally. A move changes the energy of the
+// site's four bonds by dE, and the reflection conserves it (up to the
+// rounding of the stored angle, which the 16-bit forms account for), so the
+// site's block gains dE. A site on the left or top edge of its block hands
+// the change of its left / up bond to the neighbouring block that owns it (a
+// bond is owned by the block of its left / upper site). Frozen sites never
+// move, so stopped (block, realization) pairs cost nothing.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -24,6 +26,102 @@
 
 namespace mpr {
 
+// Element type of the batch state: a realization pair is two adjacent
+// elements, loaded and stored as one 8-byte (FP32) or 4-byte (FP16 / BF16)
+// access; arithmetic is FP32 throughout. The sample angles the method
+// conditions on are never rounded: the 16-bit forms read them from the FP32
+// per-field table instead of the state.
+template <typename S> struct Store;
+
+template <> struct Store<float> {
+    static constexpr bool kExact = true;
+    __device__ static float2 load2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+    __device__ static void store2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+    __device__ static float load1(const float* p) { return *p; }
+    __device__ static void store1(float* p, float v) { *p = v; }
+    __device__ static float round(float v) { return v; }
+};
+
+template <> struct Store<__half> {
+    static constexpr bool kExact = false;
+    __device__ static float2 load2(const __half* p) {
+        return __half22float2(*reinterpret_cast<const __half2*>(p));
+    }
+    __device__ static void store2(__half* p, float2 v) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.x, v.y);
+    }
+    __device__ static float load1(const __half* p) { return __half2float(*p); }
+    __device__ static void store1(__half* p, float v) { *p = __float2half_rn(v); }
+    __device__ static float round(float v) { return __half2float(__float2half_rn(v)); }
+};
+
+template <> struct Store<__nv_bfloat16> {
+    static constexpr bool kExact = false;
+    __device__ static float2 load2(const __nv_bfloat16* p) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    __device__ static void store2(__nv_bfloat16* p, float2 v) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.x, v.y);
+    }
+    __device__ static float load1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static void store1(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+};
+
+// Site update with the state's rounding applied: the proposal is rounded
+// before its energy is taken, so the Metropolis test judges the angle that
+// is stored; the reflected angle is rounded too, and for the 16-bit forms
+// dE becomes the exact change from the old to the stored final angle, with
+// (ca, sa) the final angle's cos / sin and refl cleared.
+template <typename S>
+__device__ __forceinline__ SiteNew site_update(float phi, float C, float Sn, float u0, float u1,
+                                               float beta, const Model& m) {
+    SiteNew n;
+    __sincosf(m.q * phi, &n.so, &n.co);
+    const float php = Store<S>::round(kTwoPi * u0);
+    float sp, cp;
+    __sincosf(m.q * php, &sp, &cp);
+    const float dE = m.J * ((C * n.co + Sn * n.so) - (C * cp + Sn * sp));
+    const bool acc = (dE <= 0.0f) || (u1 < __expf(-dE * beta));
+    n.phi = acc ? php : phi;
+    n.dE = acc ? dE : 0.0f;
+    n.ca = acc ? cp : n.co;
+    n.sa = acc ? sp : n.so;
+    // Over-relaxation, without branches. The reflected angle (2 psi - q phi)/q
+    // is >= 0 only if psi >= 0, i.e. S >= 0, so psi is taken from (|S|, C) and
+    // the move is kept only when S >= 0 and the angle lies in [0, 2pi]
+    // (C = S = 0 gives NaN and fails the test).
+    const float psi = atan2_upper(fabsf(Sn), C);
+    const float por = (2.0f * psi - m.q * n.phi) * m.inv_q;
+    n.refl = m.overrelax && Sn >= 0.0f && por >= 0.0f && por <= kTwoPi;
+    n.phi = n.refl ? Store<S>::round(por) : n.phi;
+    if constexpr (!Store<S>::kExact) {
+        float sf, cf;
+        __sincosf(m.q * n.phi, &sf, &cf);
+        n.ca = cf;
+        n.sa = sf;
+        n.refl = false;
+        n.dE = m.J * ((C * n.co + Sn * n.so) - (C * cf + Sn * sf));
+    }
+    return n;
+}
+
+// Interior sites: warp sum of a block's change, FP32 atomics into eacc (the
+// stop test folds eacc into the FP64 block energy once per sweep).
+__device__ __forceinline__ void flush_pair(float* ea, float v0, float v1) {
+    if (!__any_sync(0xffffffffu, v0 != 0.0f || v1 != 0.0f)) return;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, s);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, s);
+    }
+    if ((threadIdx.x & 31) != 0) return;
+    if (v0 != 0.0f) atomicAdd(ea, v0);
+    if (v1 != 0.0f) atomicAdd(ea + 1, v1);
+}
+
+// Bond-by-bond split of a move at a block edge (used by the flat kernel,
+// which keeps all four neighbours' (cos, sin)).
 __device__ __forceinline__ void add_energy(const SiteNew& n, uint32_t f, float C, float S,
                                            const float* nc, const float* ns, float J, float& ao,
                                            float& al, float& au) {
@@ -35,67 +133,45 @@ __device__ __forceinline__ void add_energy(const SiteNew& n, uint32_t f, float C
     final_cs(n, C, S, cn, sn);
     const float dc = cn - n.co, ds = sn - n.so;
     const float dl = -J * (dc * nc[0] + ds * ns[0]);
-    const float dr = -J * (dc * nc[1] + ds * ns[1]);
     const float du = -J * (dc * nc[2] + ds * ns[2]);
-    const float dd = -J * (dc * nc[3] + ds * ns[3]);
-    ao += dr + dd;
-    if (f & EDGE_L) al += dl; else ao += dl;
-    if (f & EDGE_U) au += du; else ao += du;
+    ao += n.dE;
+    if (f & EDGE_L) { ao -= dl; al += dl; }
+    if (f & EDGE_U) { ao -= du; au += du; }
 }
 
-// Interior sites: warp sum of the block's own change, FP32 atomics into eacc
-// (the stop test folds eacc into the FP64 block energy once per sweep).
-__device__ __forceinline__ void flush_own(const SweepArgs& a, int b, int rl, float ao0, float ao1) {
-    if (!__any_sync(0xffffffffu, ao0 != 0.0f || ao1 != 0.0f)) return;
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
-        ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
-    }
-    if ((threadIdx.x & 31) != 0) return;
-    float* ea = a.eacc + (size_t)b * a.Rp + rl;
-    if (ao0 != 0.0f) atomicAdd(ea, ao0);
-    if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
-}
-
-// From-scratch energies: FP64 warp sums added to the block energies.
-__device__ __forceinline__ void flush_energy64(const SweepArgs& a, int b, int rl, double ao0,
-                                               double ao1, double al0, double al1, double au0,
-                                               double au1) {
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
-        ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
-        al0 += __shfl_xor_sync(0xffffffffu, al0, s);
-        al1 += __shfl_xor_sync(0xffffffffu, al1, s);
-        au0 += __shfl_xor_sync(0xffffffffu, au0, s);
-        au1 += __shfl_xor_sync(0xffffffffu, au1, s);
-    }
-    if ((threadIdx.x & 31) != 0) return;
-    double* ea = a.ecur + (size_t)b * a.Rp + rl;
-    if (ao0 != 0.0) atomicAdd(ea, ao0);
-    if (ao1 != 0.0) atomicAdd(ea + 1, ao1);
-    if (al0 != 0.0) atomicAdd(ea - a.Rp, al0);
-    if (al1 != 0.0) atomicAdd(ea - a.Rp + 1, al1);
-    const size_t up = (size_t)a.g.nbx * a.Rp;
-    if (au0 != 0.0) atomicAdd(ea - up, au0);
-    if (au1 != 0.0) atomicAdd(ea - up + 1, au1);
-}
-
-// (cos, sin) of q * phi_j of the four neighbours in both realizations. The
-// state holds sample angles too, so every neighbour is one 8-byte load and a
-// sin/cos pair per realization; a neighbour outside the grid is masked out.
-__device__ __forceinline__ void neighbour_field(const SweepArgs& a, const float2* __restrict__ oth,
-                                                int NP, uint32_t hs, int x, uint32_t f, float* nc0,
-                                                float* ns0, float* nc1, float* ns1) {
+// Angles of the four neighbours of a site in both realizations of the pair.
+// FP32 state: every neighbour is one 8-byte state load (the state holds the
+// sample angles too). 16-bit state: a gap neighbour is read from the state,
+// a sample neighbour from the FP32 per-field table `dang`, both loads
+// predicated on the flags. A neighbour outside the grid reads as 0 and is
+// masked out by the caller.
+template <typename S>
+__device__ __forceinline__ void neighbour_angles(const SweepArgs& a, const S* __restrict__ oth,
+                                                 int G, uint32_t hs, int x, uint32_t f,
+                                                 float2 v[4]) {
     const uint32_t o = (uint32_t)(x & 1);
     const uint32_t hn[4] = {hs + o - 1u, hs + o, hs - (uint32_t)a.g.Wh, hs + (uint32_t)a.g.Wh};
-    float2 v[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         const bool ex = (f & (NB_L << d)) != 0;
-        v[d] = ex ? oth[(size_t)hn[d] * NP] : make_float2(0.0f, 0.0f);
+        if constexpr (Store<S>::kExact) {
+            v[d] = ex ? Store<S>::load2(oth + (size_t)hn[d] * G) : make_float2(0.0f, 0.0f);
+        } else {
+            const bool gap = (f & (GAP_L << d)) != 0;
+            const float* dn = a.dang + (size_t)(a.colour ^ 1) * a.g.H * a.g.Wh;
+            const float sv = (ex && !gap) ? dn[hn[d]] : 0.0f;
+            v[d] = (ex && gap) ? Store<S>::load2(oth + (size_t)hn[d] * G) : make_float2(sv, sv);
+        }
     }
+}
+
+// (cos, sin) of q * phi_j of the four neighbours, masked by existence.
+template <typename S>
+__device__ __forceinline__ void neighbour_field(const SweepArgs& a, const S* __restrict__ oth,
+                                                int G, uint32_t hs, int x, uint32_t f, float* nc0,
+                                                float* ns0, float* nc1, float* ns1) {
+    float2 v[4];
+    neighbour_angles<S>(a, oth, G, hs, x, f, v);
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         const float m = (f & (NB_L << d)) ? 1.0f : 0.0f;
@@ -112,216 +188,79 @@ __device__ __forceinline__ void neighbour_field(const SweepArgs& a, const float2
 __device__ __forceinline__ void pair_running(const SweepArgs& a, int b, int rl, bool& run0,
                                              bool& run1) {
     if (a.running) {
-        run0 = a.running[(size_t)b * a.Rp + rl] != 0;
-        run1 = a.running[(size_t)b * a.Rp + rl + 1] != 0;
+        const uchar2 r2 = *reinterpret_cast<const uchar2*>(a.running + (size_t)b * a.Rp + rl);
+        run0 = r2.x != 0;
+        run1 = r2.y != 0;
     } else {
         run0 = rl < a.R;
         run1 = rl + 1 < a.R;
     }
 }
 
-// Interior sites of one item (the segment after the block's edge entries):
-// every bond of such a site belongs to the block, so the block's energy
-// changes by the Metropolis dE. wpi warps share the item (wi = this warp's
-// index among them): warp wi handles realization pair q = wi mod G/2, and
-// warps of the same pair split the entries 32 at a time.
-template <int G>
-__device__ __forceinline__ void sweep_interior_item(const SweepArgs& a, int item, int wi, int wpi,
-                                                    uint32_t ctr1) {
+// All gap sites of colour c in one item. wpi warps share the item (wi = this
+// warp's index among them): warp wi handles realization pair q = wi mod G/2,
+// and the wpi / (G/2) warps of a pair split the entries 32 at a time. The
+// next entry of a lane is loaded while the current one is updated. The
+// block's list puts its edge entries first, so the branch that splits an
+// edge move bond by bond diverges in the first 32 entries only.
+template <int G, typename S>
+__device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi, int wpi,
+                                           uint32_t ctr1) {
     constexpr int NP = G / 2;
     const int lane = threadIdx.x & 31;
     const int q = wi % NP, cw = wi / NP, CW = wpi / NP;
     const size_t plane = (size_t)a.g.H * a.g.Wh;
     const int c = a.colour, co = c ^ 1;
     const int b = item / a.groups, grp = item - b * a.groups;
-    const int e0 = a.split[b], e1 = a.start[b + 1];
+    const int e0 = a.start[b], e1 = a.start[b + 1];
     if (e0 >= e1) return;
     const int rl = grp * G + 2 * q;
     bool run0, run1;
     pair_running(a, b, rl, run0, run1);
     if (!(run0 || run1)) return;
-    float2* own = reinterpret_cast<float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
-    const float2* oth =
-        reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
+    S* own = static_cast<S*>(a.ang) + (size_t)(grp * 2 + c) * plane * G + 2 * q;
+    const S* oth = static_cast<const S*>(a.ang) + (size_t)(grp * 2 + co) * plane * G + 2 * q;
     const float beta = a.beta[b];
-    const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
-    float ao0 = 0.f, ao1 = 0.f;
-    for (int e = e0 + cw * 32 + lane; e < e1; e += CW * 32) {
-        const uint2 en = a.list[e];
-        const int y = en.x >> 16, x = en.x & 0xffff;
-        const uint32_t f = en.y;
-        const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
-        uint32_t w[4];
-        philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)x, ctr1, rpair, 0u, a.rng.key0,
-                      a.rng.key1, w);
-        const float2 ph = own[(size_t)hs * NP];
-        float nc0[4], ns0[4], nc1[4], ns1[4];
-        neighbour_field(a, oth, NP, hs, x, f, nc0, ns0, nc1, ns1);
-        const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
-        const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
-        const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
-        const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
-        float2 out = ph;
-        if (run0) {
-            const SiteNew n = site_update(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
-            out.x = n.phi;
-            ao0 += n.dE;
-        }
-        if (run1) {
-            const SiteNew n = site_update(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
-            out.y = n.phi;
-            ao1 += n.dE;
-        }
-        own[(size_t)hs * NP] = out;
-    }
-    if (a.energy) flush_own(a, b, rl, ao0, ao1);
-}
-
-// Interior sites of one item with two list entries per lane in flight: the
-// two entries' loads and arithmetic are independent, and both realizations
-// of the pair are computed without branches (a stopped one keeps its angle),
-// so the compiler can overlap the two memory round trips.
-template <int G>
-__device__ __forceinline__ void sweep_interior_item2(const SweepArgs& a, int item, int wi, int wpi,
-                                                     uint32_t ctr1) {
-    constexpr int NP = G / 2;
-    const int lane = threadIdx.x & 31;
-    const int q = wi % NP, cw = wi / NP, CW = wpi / NP;
-    const size_t plane = (size_t)a.g.H * a.g.Wh;
-    const int c = a.colour, co = c ^ 1;
-    const int b = item / a.groups, grp = item - b * a.groups;
-    const int e0 = a.split[b], e1 = a.start[b + 1];
-    if (e0 >= e1) return;
-    const int rl = grp * G + 2 * q;
-    bool run0, run1;
-    pair_running(a, b, rl, run0, run1);
-    if (!(run0 || run1)) return;
-    float2* own = reinterpret_cast<float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
-    const float2* oth =
-        reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
-    const float beta = a.beta[b];
-    const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
-    float ao0 = 0.f, ao1 = 0.f;
-    for (int base = e0 + cw * 64 + lane; base < e1; base += CW * 64) {
-        uint2 en[2];
-        bool val[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int e = base + 32 * j;
-            val[j] = e < e1;
-            en[j] = val[j] ? a.list[e] : make_uint2(0u, 0u);
-        }
-        uint32_t hs[2], w[2][4];
-        int xs[2];
-        float2 ph[2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int y = en[j].x >> 16;
-            xs[j] = en[j].x & 0xffff;
-            hs[j] = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(xs[j] >> 1);
-            ph[j] = val[j] ? own[(size_t)hs[j] * NP] : make_float2(0.0f, 0.0f);
-            philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)xs[j], ctr1, rpair, 0u,
-                          a.rng.key0, a.rng.key1, w[j]);
-        }
-        float nc0[2][4], ns0[2][4], nc1[2][4], ns1[2][4];
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-            neighbour_field(a, oth, NP, hs[j], xs[j], val[j] ? en[j].y : 0u, nc0[j], ns0[j], nc1[j],
-                            ns1[j]);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const float C0 = (nc0[j][0] + nc0[j][1]) + (nc0[j][2] + nc0[j][3]);
-            const float S0 = (ns0[j][0] + ns0[j][1]) + (ns0[j][2] + ns0[j][3]);
-            const float C1 = (nc1[j][0] + nc1[j][1]) + (nc1[j][2] + nc1[j][3]);
-            const float S1 = (ns1[j][0] + ns1[j][1]) + (ns1[j][2] + ns1[j][3]);
-            const SiteNew n0 = site_update(ph[j].x, C0, S0, u01(w[j][0]), u01(w[j][1]), beta, a.m);
-            const SiteNew n1 = site_update(ph[j].y, C1, S1, u01(w[j][2]), u01(w[j][3]), beta, a.m);
-            const bool m0 = run0 && val[j], m1 = run1 && val[j];
-            ao0 += m0 ? n0.dE : 0.0f;
-            ao1 += m1 ? n1.dE : 0.0f;
-            if (val[j])
-                own[(size_t)hs[j] * NP] = make_float2(m0 ? n0.phi : ph[j].x, m1 ? n1.phi : ph[j].y);
-        }
-    }
-    if (a.energy) flush_own(a, b, rl, ao0, ao1);
-}
-
-// Edge sites of one item (left / top edge of the block). A block has few of
-// them, so one warp takes the whole item: lane = entry slot * (G/2) + pair,
-// i.e. 32/(G/2) entries times all pairs per pass, and one site's G
-// realizations are read as one contiguous chunk.
-template <int G>
-__device__ __forceinline__ void sweep_edge_item(const SweepArgs& a, int item, uint32_t ctr1) {
-    constexpr int NP = G / 2;
-    constexpr int EPI = 32 / NP;
-    const int lane = threadIdx.x & 31;
-    const int q = lane % NP, el = lane / NP;
-    const size_t plane = (size_t)a.g.H * a.g.Wh;
-    const int c = a.colour, co = c ^ 1;
-    const int b = item / a.groups, grp = item - b * a.groups;
-    const int e0 = a.start[b], e1 = a.split[b];
-    if (e0 >= e1) return;
-    const int rl = grp * G + 2 * q;
-    bool run0, run1;
-    pair_running(a, b, rl, run0, run1);
-    if (!__any_sync(0xffffffffu, run0 || run1)) return;
-    float2* own = reinterpret_cast<float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
-    const float2* oth =
-        reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
-    const float beta = a.beta[b];
+    const float J = a.m.J;
     const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
     float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
-    for (int base = e0; base < e1; base += EPI) {
-        const int e = base + el;
-        if (e >= e1 || !(run0 || run1)) continue;
-        const uint2 en = a.list[e];
+    const int step = CW * 32;
+    int e = e0 + cw * 32 + lane;
+    uint2 nx = e < e1 ? a.list[e] : make_uint2(0u, 0u);
+    for (; e < e1; e += step) {
+        const uint2 en = nx;
+        if (e + step < e1) nx = a.list[e + step];
         const int y = en.x >> 16, x = en.x & 0xffff;
         const uint32_t f = en.y;
         const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
         uint32_t w[4];
         philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)x, ctr1, rpair, 0u, a.rng.key0,
                       a.rng.key1, w);
-        const float2 ph = own[(size_t)hs * NP];
+        const float2 ph = Store<S>::load2(own + (size_t)hs * G);
         float nc0[4], ns0[4], nc1[4], ns1[4];
-        neighbour_field(a, oth, NP, hs, x, f, nc0, ns0, nc1, ns1);
+        neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
         const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
         const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
         const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
         const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
         float2 out = ph;
         if (run0) {
-            const SiteNew n = site_update(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
+            const SiteNew n = site_update<S>(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
             out.x = n.phi;
-            add_energy(n, f, C0, S0, nc0, ns0, a.m.J, ao0, al0, au0);
+            add_energy(n, f, C0, S0, nc0, ns0, J, ao0, al0, au0);
         }
         if (run1) {
-            const SiteNew n = site_update(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
+            const SiteNew n = site_update<S>(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
             out.y = n.phi;
-            add_energy(n, f, C1, S1, nc1, ns1, a.m.J, ao1, al1, au1);
+            add_energy(n, f, C1, S1, nc1, ns1, J, ao1, al1, au1);
         }
-        own[(size_t)hs * NP] = out;
+        Store<S>::store2(own + (size_t)hs * G, out);
     }
     if (!a.energy) return;
-    // Sum over the entry slots of each pair; the slot-0 lane of each pair adds
-    // to the blocks.
-#pragma unroll
-    for (int s = NP; s < 32; s <<= 1) {
-        ao0 += __shfl_xor_sync(0xffffffffu, ao0, s);
-        ao1 += __shfl_xor_sync(0xffffffffu, ao1, s);
-        al0 += __shfl_xor_sync(0xffffffffu, al0, s);
-        al1 += __shfl_xor_sync(0xffffffffu, al1, s);
-        au0 += __shfl_xor_sync(0xffffffffu, au0, s);
-        au1 += __shfl_xor_sync(0xffffffffu, au1, s);
-    }
-    if (el != 0) return;
     float* ea = a.eacc + (size_t)b * a.Rp + rl;
-    if (ao0 != 0.0f) atomicAdd(ea, ao0);
-    if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
-    if (al0 != 0.0f) atomicAdd(ea - a.Rp, al0);
-    if (al1 != 0.0f) atomicAdd(ea - a.Rp + 1, al1);
-    const size_t up = (size_t)a.g.nbx * a.Rp;
-    if (au0 != 0.0f) atomicAdd(ea - up, au0);
-    if (au1 != 0.0f) atomicAdd(ea - up + 1, au1);
+    flush_pair(ea, ao0, ao1);
+    flush_pair(ea - a.Rp, al0, al1);
+    flush_pair(ea - (size_t)a.g.nbx * a.Rp, au0, au1);
 }
 
 // One half-step over the whole list of one colour, flat: one thread per
@@ -356,9 +295,9 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
         bool run0, run1;
         pair_running(a, b, rl, run0, run1);
         if (run0 || run1) {
-            float2* own = reinterpret_cast<float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
+            float2* own = reinterpret_cast<float2*>(static_cast<float*>(a.ang) + (size_t)(grp * 2 + c) * plane * G) + q;
             const float2* oth =
-                reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
+                reinterpret_cast<const float2*>(static_cast<const float*>(a.ang) + (size_t)(grp * 2 + co) * plane * G) + q;
             const int y = en.x >> 16, x = en.x & 0xffff;
             const uint32_t f = en.y;
             const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
@@ -367,7 +306,8 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
                           (a.r_base + (uint32_t)rl) >> 1, 0u, a.rng.key0, a.rng.key1, w);
             const float2 ph = own[(size_t)hs * NP];
             float nc0[4], ns0[4], nc1[4], ns1[4];
-            neighbour_field(a, oth, NP, hs, x, f, nc0, ns0, nc1, ns1);
+            neighbour_field<float>(a, reinterpret_cast<const float*>(oth), G, hs, x, f, nc0, ns0,
+                                   nc1, ns1);
             const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
             const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
             const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
@@ -376,12 +316,12 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
             float2 out = ph;
             float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
             if (run0) {
-                const SiteNew n = site_update(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
+                const SiteNew n = site_update<float>(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
                 out.x = n.phi;
                 add_energy(n, f, C0, S0, nc0, ns0, a.m.J, ao0, al0, au0);
             }
             if (run1) {
-                const SiteNew n = site_update(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
+                const SiteNew n = site_update<float>(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
                 out.y = n.phi;
                 add_energy(n, f, C1, S1, nc1, ns1, a.m.J, ao1, al1, au1);
             }
@@ -415,12 +355,12 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
     }
 }
 
-// Energies from scratch (no move) of one item: every bond that touches a gap
-// site, once. A bond always joins a colour-0 and a colour-1 site; colour 1
-// adds every bond of its gap sites, colour 0 the bonds of its gap sites to
-// samples. Bonds between two samples are the constant E_s,b. Every lane of
-// the item is counted (the pass ignores the running flags).
-template <int G>
+// Energies from scratch (no move) of one item: the bonds that touch a gap
+// site of this colour and belong to no gap site of the other colour (colour
+// 1 counts all bonds of its gap sites, colour 0 only those to sample
+// neighbours). Each lane sums its few bonds in FP32; the warp sums and the
+// block totals are FP64.
+template <int G, typename S>
 __device__ __forceinline__ void energy_item(const SweepArgs& a, int item, int wi, int wpi) {
     constexpr int NP = G / 2;
     const int lane = threadIdx.x & 31;
@@ -430,19 +370,17 @@ __device__ __forceinline__ void energy_item(const SweepArgs& a, int item, int wi
     const int b = item / a.groups, grp = item - b * a.groups;
     const int rl = grp * G + 2 * q;
     const int e0 = a.start[b], e1 = a.start[b + 1];
-    const float2* own =
-        reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + c) * plane * G) + q;
-    const float2* oth =
-        reinterpret_cast<const float2*>(a.ang + (size_t)(grp * 2 + co) * plane * G) + q;
-    double ao0 = 0.0, ao1 = 0.0, al0 = 0.0, al1 = 0.0, au0 = 0.0, au1 = 0.0;
+    const S* own = static_cast<const S*>(a.ang) + (size_t)(grp * 2 + c) * plane * G + 2 * q;
+    const S* oth = static_cast<const S*>(a.ang) + (size_t)(grp * 2 + co) * plane * G + 2 * q;
+    float o0 = 0.f, o1 = 0.f, l0 = 0.f, l1 = 0.f, u0 = 0.f, u1 = 0.f;
     for (int e = e0 + cw * 32 + lane; e < e1; e += CW * 32) {
         const uint2 en = a.list[e];
         const int y = en.x >> 16, x = en.x & 0xffff;
         const uint32_t f = en.y;
         const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
-        const float2 ph = own[(size_t)hs * NP];
+        const float2 ph = Store<S>::load2(own + (size_t)hs * G);
         float nc0[4], ns0[4], nc1[4], ns1[4];
-        neighbour_field(a, oth, NP, hs, x, f, nc0, ns0, nc1, ns1);
+        neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
         float s0, c0, s1, c1;
         __sincosf(a.m.q * ph.x, &s0, &c0);
         __sincosf(a.m.q * ph.y, &s1, &c1);
@@ -452,12 +390,25 @@ __device__ __forceinline__ void energy_item(const SweepArgs& a, int item, int wi
             if (!((f & (NB_L << d)) && (take & (1u << d)))) continue;
             const float b0 = -a.m.J * (c0 * nc0[d] + s0 * ns0[d]);
             const float b1 = -a.m.J * (c1 * nc1[d] + s1 * ns1[d]);
-            if (d == 0 && (f & EDGE_L)) { al0 += b0; al1 += b1; }
-            else if (d == 2 && (f & EDGE_U)) { au0 += b0; au1 += b1; }
-            else { ao0 += b0; ao1 += b1; }
+            if (d == 0 && (f & EDGE_L)) { l0 += b0; l1 += b1; }
+            else if (d == 2 && (f & EDGE_U)) { u0 += b0; u1 += b1; }
+            else { o0 += b0; o1 += b1; }
         }
     }
-    flush_energy64(a, b, rl, ao0, ao1, al0, al1, au0, au1);
+    double v[6] = {o0, o1, l0, l1, u0, u1};
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
+    if (lane != 0) return;
+    double* ea = a.ecur + (size_t)b * a.Rp + rl;
+    const size_t up = (size_t)a.g.nbx * a.Rp;
+    if (v[0] != 0.0) atomicAdd(ea, v[0]);
+    if (v[1] != 0.0) atomicAdd(ea + 1, v[1]);
+    if (v[2] != 0.0) atomicAdd(ea - a.Rp, v[2]);
+    if (v[3] != 0.0) atomicAdd(ea - a.Rp + 1, v[3]);
+    if (v[4] != 0.0) atomicAdd(ea - up, v[4]);
+    if (v[5] != 0.0) atomicAdd(ea - up + 1, v[5]);
 }
 
 // Median of the targeted blocks' T by a radix select over the (positive)
