@@ -45,7 +45,8 @@ class Model(C.Structure):
                 ("nbx", C.c_int32), ("nby", C.c_int32), ("nblk", C.c_int32),
                 ("q", C.c_double), ("J", C.c_double),
                 ("key0", C.c_uint32), ("key1", C.c_uint32),
-                ("overrelax", C.c_int32), ("K", C.c_int32), ("threads", C.c_int32)]
+                ("overrelax", C.c_int32), ("K", C.c_int32), ("threads", C.c_int32),
+                ("T_site", C.c_void_p)]
 
 
 class Diag(C.Structure):
@@ -90,6 +91,7 @@ def lib():
             "orc_calibrate": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, f64, f64, P, P]),
             "orc_median_targeted": (f64, [i32, P, P]),
             "orc_scores": (None, [i64, P, P, P, P, P]),
+            "orc_sst_temperatures": (None, [MP, P, i32, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -202,6 +204,23 @@ class Oracle:
         ph = np.ascontiguousarray(phi, dtype=np.float64)
         return lib().orc_total_energy(C.byref(self.m), _p(ph))
 
+    def sst_temperatures(self, T_blk, r_s: int, n_s: int) -> np.ndarray:
+        """Sec. 2.2.3 site temperatures from the block temperatures."""
+        T = np.ascontiguousarray(T_blk, dtype=np.float64)
+        out = np.zeros((self.H, self.W))
+        lib().orc_sst_temperatures(C.byref(self.m), _p(T), int(r_s), int(n_s), _p(out))
+        return out
+
+    def use_site_temperatures(self, T_site):
+        """Updates take T from T_site[H, W] (SST) instead of the block's T; None
+        restores the block temperatures (BST). The array is kept alive here."""
+        if T_site is None:
+            self._T_site = None
+            self.m.T_site = None
+            return
+        self._T_site = np.ascontiguousarray(T_site, dtype=np.float64).reshape(self.H, self.W)
+        self.m.T_site = self._T_site.ctypes.data
+
     def update_site(self, phi: np.ndarray, mask, i: int, T: float, t: int, tag: int, r: int):
         """Update site i of phi (float64, modified in place); returns the diagnostics."""
         assert phi.dtype == np.float64 and phi.flags.c_contiguous
@@ -307,11 +326,13 @@ def gapfill(values, mask, lb: int, R: int, seed: int = 0, slice_id: int = 0, q: 
             J: float = 1.0, n_max: int = 200, n_eq: int = 25, n_meas: int = 20,
             n_bisect: int = 24, chains: int = 1, T_lo: float = 1e-4, T_hi: float = 2.0,
             T_blk=None, overrelax: bool = True, threads: int = 0,
-            r0: int = 0) -> GapfillResult:
+            r0: int = 0, sst=None) -> GapfillResult:
     """The whole method on the CPU: Sec. 2.1 transform, Eq. 2 per block,
     per-block T by energy matching (Sec. 2.2.2; skipped when T_blk is given),
     R local-equilibrium realizations from the block-mean start (Sec. 3.3.3,
-    Sec. 3.4), their mean and the back-transform (Sec. 2.1, Sec. 3.2)."""
+    Sec. 3.4), their mean and the back-transform (Sec. 2.1, Sec. 3.2).
+    sst = (r_s, n_s): the realizations run at the smoothed site temperatures
+    of Sec. 2.2.3 instead of the block temperatures."""
     values = np.asarray(values, dtype=np.float32)
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     H, W = mask.shape
@@ -324,6 +345,8 @@ def gapfill(values, mask, lb: int, R: int, seed: int = 0, slice_id: int = 0, q: 
         T = o.calibrate(phi0, mask, st, n_eq, n_meas, n_bisect, chains, T_lo, T_hi)
     else:
         T = np.asarray(T_blk, dtype=np.float64)
+    if sst is not None:
+        o.use_site_temperatures(o.sst_temperatures(T, sst[0], sst[1]))
     acc = np.zeros((H, W))
     stops = np.zeros((R, o.nblk), np.int32)
     sweeps = np.zeros(R, np.int32)

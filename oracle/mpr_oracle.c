@@ -55,6 +55,7 @@ void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, do
     m->overrelax = 1;
     m->K = 0;
     m->threads = 0;
+    m->T_site = NULL;
 }
 
 static int block_of(const orc_model* m, int y, int x) { return (y / m->lb) * m->nbx + x / m->lb; }
@@ -287,6 +288,36 @@ void orc_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64
 /* Sec. 2.2.2 single checkerboard: the sites of one sub-grid have all their
  * neighbours on the other, so one colour is updated at a time (here in raster
  * order; any order gives the same result). */
+/* Sec. 2.2.3: smoothing of the block temperatures into site temperatures,
+ * written out as the plain window mean (no separable or running-sum form). */
+void orc_sst_temperatures(const orc_model* m, const double* T_blk, int32_t r_s, int32_t n_s,
+                          double* T_site) {
+    const int H = m->H, W = m->W;
+    const int64_t n = (int64_t)H * W;
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) T_site[(int64_t)y * W + x] = T_blk[block_of(m, y, x)];
+    const double inv = 1.0 / ((double)(2 * r_s + 1) * (double)(2 * r_s + 1));
+    for (int pass = 0; pass < n_s; ++pass) {
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                double s = 0.0;
+                for (int dy = -r_s; dy <= r_s; ++dy) {
+                    int yy = y + dy;
+                    yy = yy < 0 ? 0 : (yy >= H ? H - 1 : yy);
+                    for (int dx = -r_s; dx <= r_s; ++dx) {
+                        int xx = x + dx;
+                        xx = xx < 0 ? 0 : (xx >= W ? W - 1 : xx);
+                        s += T_site[(int64_t)yy * W + xx];
+                    }
+                }
+                tmp[(int64_t)y * W + x] = s * inv;
+            }
+        for (int64_t i = 0; i < n; ++i) T_site[i] = tmp[i];
+    }
+    free(tmp);
+}
+
 void orc_halfstep(const orc_model* m, double* phi, const uint8_t* mask, int colour,
                   const double* T_blk, const uint8_t* active, uint32_t t, uint32_t tag,
                   uint32_t r, orc_diag* diag) {
@@ -302,7 +333,8 @@ void orc_halfstep(const orc_model* m, double* phi, const uint8_t* mask, int colo
             if (!mask[i]) continue;
             int b = block_of(m, y, x);
             if (active && !active[b]) continue;
-            orc_update_site(m, phi, mask, i, T_blk[b], t, tag, r, diag ? &diag[i] : NULL);
+            const double T = m->T_site ? m->T_site[i] : T_blk[b];
+            orc_update_site(m, phi, mask, i, T, t, tag, r, diag ? &diag[i] : NULL);
         }
     }
 }

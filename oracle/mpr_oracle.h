@@ -26,6 +26,8 @@ typedef struct {
     int32_t overrelax;       /* 1: Metropolis followed by over-relaxation */
     int32_t K;               /* 0: continuous angles; K>0: K discrete levels, OR off */
     int32_t threads;         /* OpenMP threads (<=0: library default) */
+    const double* T_site;    /* NULL: block temperatures (BST); else H*W site
+                                temperatures (SST, Sec. 2.2.3) used by the updates */
 } orc_model;
 
 void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, double J,
@@ -61,6 +63,13 @@ typedef struct {
     double phi_old, phi_prop;
     int32_t accepted, or_applied;
 } orc_diag;
+
+/* SST site temperatures (Sec. 2.2.3): every site starts from its block's T,
+ * then n_s times every site's T is replaced by the mean over the square of
+ * side 2 r_s + 1 centred on it, with coordinates clamped to the grid.
+ * T_blk[nblk] -> T_site[H*W]. */
+void orc_sst_temperatures(const orc_model* m, const double* T_blk, int32_t r_s, int32_t n_s,
+                          double* T_site);
 
 /* Metropolis (+ OR) update of gap site i at temperature T, in place. */
 void orc_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64_t i,

@@ -1,0 +1,119 @@
+"""The 16-bit state forms (BF16 / FP16 storage of the realizations' angles,
+FP32 arithmetic, FP64 block energies), through the C-ABI.
+
+What must hold exactly, whatever the storage:
+  * the incremental block energies equal the energies recomputed in FP64
+    from the stored state (the kernels round every proposal and reflection
+    to the stored type before taking its energy, and account the reflection's
+    rounding);
+  * stored gap angles are values of the storage type, in [0, 2pi];
+  * sample sites keep their FP32 angle bit for bit.
+What is stated, not exact: the error of the predictions against the FP64
+oracle (same random streams; a rounded proposal can flip a decision, so the
+chains separate), checked at equal AAE within the Monte Carlo spread.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_01317_gb300 import synth
+from paper_2212_01317_gb300.mpr import GapFiller
+
+from parity import TWO_PI
+
+pytestmark = pytest.mark.gpu
+STORE = {"f32": 0, "bf16": 1, "f16": 2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def make(z, m, lb, **opt):
+    v = np.where(m != 0, np.nan, z).astype(np.float32)
+    return GapFiller(v, m, lb, **opt)
+
+
+def representable(x: np.ndarray, storage: str) -> bool:
+    x = np.asarray(x, np.float32)
+    if storage == "f32":
+        return True
+    if storage == "f16":
+        return np.array_equal(x.astype(np.float16).astype(np.float32), x)
+    return bool(np.all((x.view(np.uint32) & 0xFFFF) == 0))
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("group,R", [(2, 1), (8, 6)])
+def test_incremental_energy_equals_recomputed(storage, group, R):
+    z, m = synth.small_problem(48, 40, 0.55, seed=13)
+    gf = make(z, m, 8, seed=3, storage=STORE[storage], group=group, n_max=200)
+    rng = np.random.default_rng(1)
+    gf.set_temperatures(rng.uniform(0.03, 0.3, gf.nblk).astype(np.float32))
+    gf.sim_begin(R)
+    Es, Nsp, Nb, _, _ = gf.block_stats()
+    for _ in range(3):
+        gf.sim_sweep(4)
+        e = gf.block_e(R)
+        _, run = gf.get_stop(R)
+        for r in range(R):
+            E = gf.block_energy(r)
+            ok = (run[r] == 1) & (Nb > 0)
+            np.testing.assert_allclose(e[r][ok], E[ok] / Nb[ok], rtol=0, atol=5e-6)
+    for r in range(R):
+        s = gf.get_state(r)
+        g = m != 0
+        assert representable(s[g], storage)
+        assert s[g].min() >= 0.0 and s[g].max() <= TWO_PI
+    gf.sim_end()
+    gf.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_samples_stay_exact(storage):
+    z, m = synth.small_problem(33, 47, 0.4, seed=2, kind="disc")
+    ref = make(z, m, 8, seed=3)
+    ref.set_temperatures(np.full(ref.nblk, 0.1, np.float32))
+    ref.sim_begin(2)
+    base = ref.get_state(0)
+    ref.sim_end()
+    ref.close()
+    gf = make(z, m, 8, seed=3, storage=STORE[storage])
+    gf.set_temperatures(np.full(gf.nblk, 0.1, np.float32))
+    gf.sim_begin(3)
+    gf.sim_sweep(5)
+    for r in range(3):
+        s = gf.get_state(r)
+        assert np.array_equal(s[m == 0].view(np.uint32), base[m == 0].view(np.uint32))
+    gf.sim_end()
+    gf.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_prediction_error_against_fp64_oracle(storage, record_property):
+    """Equal AAE within the spread over seeds; the mean absolute difference
+    of the predictions from the FP64 oracle's is recorded."""
+    H, W, lb, R = 48, 48, 8, 8
+    z, m = synth.small_problem(H, W, 0.5, seed=61, xi=6.0)
+    T = np.full((H // lb) * (W // lb), 0.08, np.float32)
+    d_aae, diffs = [], []
+    for s in range(6):
+        gf = make(z, m, lb, seed=500 + s, n_max=60, storage=STORE[storage])
+        gf.set_temperatures(T)
+        gf.simulate(R)
+        pred, (aae, _) = gf.predict(truth=z)
+        gf.close()
+        ref = oracle.gapfill(z, m, lb, R=R, seed=500 + s, T_blk=T.astype(np.float64), n_max=60)
+        a_ref = oracle.Oracle.scores(ref.pred, z, m)[0]
+        d_aae.append(aae - a_ref)
+        g = m != 0
+        diffs.append(np.abs(pred[g] - ref.pred[g]).mean() / (z.max() - z.min()))
+    d = np.array(d_aae)
+    se = max(d.std(ddof=1) / np.sqrt(len(d)), 1e-12)
+    record_property("mean_abs_pred_diff_over_range", float(np.mean(diffs)))
+    record_property("aae_diff_mean", float(d.mean()))
+    assert abs(d.mean()) <= 3 * se + 0.005 * abs(a_ref)
+    assert np.mean(diffs) < 0.05
