@@ -339,11 +339,16 @@ def run_ours(args, world, rank, local):
     # Dominant kernel by summed device time.
     dom = "sim" if sim_ms >= cal_ms else "cal"
     achieved = sim_gbs if dom == "sim" else cal_gbs
+    # DRAM bytes per launch of the dominant kernel: the ncu-measured bytes per
+    # gap-site update (profiles/traffic.json, taken on this workload) times the
+    # average updates per launch of this run.
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
+    if os.path.exists(tpath) and dom == "sim" and args.storage == "f32" and sim_launch:
         with open(tpath) as f:
-            traffic = json.load(f).get(f"{dom}_{wl.name}")
+            rec = json.load(f).get(f"sim_{wl.name}")
+        if rec:
+            traffic = rec["bytes_per_update"] * sim_updates / sim_launch
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "traffic": traffic,

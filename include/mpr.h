@@ -158,6 +158,25 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out);
 mpr_status mpr_set_temperatures(mpr_ctx* ctx, const float* block_T);
 mpr_status mpr_get_temperatures(mpr_ctx* ctx, float* block_T_out);
 
+/* ---- site-specific temperatures (SST, Sec. 2.2.3) ----
+ * mpr_smooth_temperatures: every site starts from its block's temperature
+ *   (after mpr_calibrate or mpr_set_temperatures), then n_s times every
+ *   site's T is replaced by the mean over the square of side 2 r_s + 1
+ *   centred on it, coordinates clamped to the grid (sums in FP64, stored as
+ *   FP32). Realizations run after this use the site temperatures in their
+ *   Metropolis tests; the stop test is unchanged (block energies against
+ *   e_s,b). T_site_out: NULL or H*W floats (host or device), row-major.
+ *   0 <= r_s <= 4096, 0 <= n_s <= 1000.
+ * mpr_set_site_temperatures: H*W positive floats (host or device), or NULL
+ *   to return to the block temperatures. mpr_calibrate and
+ *   mpr_set_temperatures also return to the block temperatures.
+ * mpr_get_site_temperatures: H*W floats.
+ * Errors: ESTATE (no block temperatures yet, a batch is open, or no site
+ * temperatures to get), EINVAL, ECUDA. */
+mpr_status mpr_smooth_temperatures(mpr_ctx* ctx, int32_t r_s, int32_t n_s, float* T_site_out);
+mpr_status mpr_set_site_temperatures(mpr_ctx* ctx, const float* T_site);
+mpr_status mpr_get_site_temperatures(mpr_ctx* ctx, float* T_site);
+
 /* Runs n_realizations more local-equilibrium conditional simulations
  * (Sec. 2.2.2 block temperatures, Sec. 3.3.3 block-mean start, Sec. 3.4 stop)
  * and adds their final states to the running mean. Realization indices

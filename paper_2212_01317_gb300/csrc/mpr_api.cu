@@ -49,6 +49,9 @@ struct mpr_ctx {
     double* ssum = nullptr;
     float* init_angle = nullptr;
     float *T = nullptr, *beta = nullptr, *lo = nullptr, *hi = nullptr;
+    float* T_site = nullptr;     // [H*W] site temperatures (SST), allocated on first use
+    float* beta_site = nullptr;  // [H*W] 1 / T_site
+    int sst = 0;                 // 1: realizations use the site temperatures
     double* ebar = nullptr;
     double* sum = nullptr;  // [2][H][Wh] running sums of gap angles
     float* out_buf = nullptr;
@@ -272,6 +275,7 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
     a.ang = ctx->ang;
     a.dang = ctx->dang;
     a.beta = ctx->beta;
+    a.beta_site = (simulate && ctx->sst) ? ctx->beta_site : nullptr;
     a.running = simulate ? ctx->running : nullptr;
     a.eacc = ctx->eacc;
     a.ecur = ctx->ecur;
@@ -925,6 +929,7 @@ mpr_status mpr_set_temperatures(mpr_ctx* ctx, const float* T) {
     CK(cudaMemcpyAsync(ctx->beta, bt.data(), bt.size() * 4, cudaMemcpyHostToDevice, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     ctx->calibrated = 1;
+    ctx->sst = 0;
     return MPR_OK;
 }
 
@@ -983,6 +988,7 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains *
                         (ctx->n_gap[0] + ctx->n_gap[1]);
     ctx->calibrated = 1;
+    ctx->sst = 0;
     if (block_T_out) TRY(copy_out(ctx, block_T_out, ctx->T, (size_t)g.nblk * 4));
     CK(cudaStreamSynchronize(ctx->s));
     collect_events(ctx);
@@ -1242,6 +1248,68 @@ mpr_status mpr_block_energy(mpr_ctx* ctx, int32_t r, double* E) {
     dfree(ctx, d);
     ctx->device_bytes -= (int64_t)ctx->g.nblk * 8;
     return st;
+}
+
+mpr_status ensure_site_buffers(mpr_ctx* ctx) {
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
+    if (!ctx->T_site) TRY(dalloc(ctx, &ctx->T_site, n));
+    if (!ctx->beta_site) TRY(dalloc(ctx, &ctx->beta_site, n));
+    return MPR_OK;
+}
+
+mpr_status mpr_smooth_temperatures(mpr_ctx* ctx, int32_t r_s, int32_t n_s, float* T_site_out) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->calibrated) return fail(ctx, MPR_ESTATE, "calibrate or set temperatures first");
+    if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
+    if (r_s < 0 || r_s > 4096 || n_s < 0 || n_s > 1000)
+        return fail(ctx, MPR_EINVAL, "need 0 <= r_s <= 4096 and 0 <= n_s <= 1000");
+    TRY(ensure_site_buffers(ctx));
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
+    double *Ts = nullptr, *tmp = nullptr;
+    CK(cudaMallocAsync((void**)&Ts, n * sizeof(double), ctx->s));
+    CK(cudaMallocAsync((void**)&tmp, n * sizeof(double), ctx->s));
+    launch_sst(ctx->g, ctx->T, r_s, n_s, Ts, tmp, ctx->T_site, ctx->beta_site, ctx->s);
+    ctx->launches += 2 + 2 * n_s;
+    const cudaError_t e = cudaPeekAtLastError();
+    cudaFreeAsync(Ts, ctx->s);
+    cudaFreeAsync(tmp, ctx->s);
+    if (e != cudaSuccess) return fail(ctx, MPR_ECUDA, "smoothing: %s", cudaGetErrorString(e));
+    ctx->sst = 1;
+    if (T_site_out) return copy_out(ctx, T_site_out, ctx->T_site, n * 4);
+    CK(cudaStreamSynchronize(ctx->s));
+    return MPR_OK;
+}
+
+mpr_status mpr_set_site_temperatures(mpr_ctx* ctx, const float* T_site) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
+    if (!T_site) {
+        ctx->sst = 0;
+        return MPR_OK;
+    }
+    if (!ctx->calibrated) return fail(ctx, MPR_ESTATE, "calibrate or set temperatures first");
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
+    std::vector<float> h(n);
+    CK(cudaMemcpyAsync(h.data(), T_site, n * 4, cudaMemcpyDefault, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (float v : h)
+        if (!(v > 0.0f) || !std::isfinite(v)) return fail(ctx, MPR_EINVAL, "site temperatures must be > 0");
+    TRY(ensure_site_buffers(ctx));
+    CK(cudaMemcpyAsync(ctx->T_site, h.data(), n * 4, cudaMemcpyHostToDevice, ctx->s));
+    launch_site_beta((int64_t)n, ctx->T_site, ctx->beta_site, ctx->s);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->sst = 1;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_site_temperatures(mpr_ctx* ctx, float* T_site) {
+    if (!ctx || !T_site) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->sst) return fail(ctx, MPR_ESTATE, "no site temperatures");
+    return copy_out(ctx, T_site, ctx->T_site, (size_t)ctx->g.H * ctx->g.W * 4);
 }
 
 mpr_status mpr_set_realization_base(mpr_ctx* ctx, int64_t r_first) {

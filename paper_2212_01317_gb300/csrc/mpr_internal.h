@@ -78,6 +78,7 @@ struct SweepArgs {
     void* ang;                // batch state [groups][2][H][Wh][G] (FP32, FP16 or BF16)
     const float* dang;        // [2][H][Wh] FP32 sample angles (0 at gaps)
     const float* beta;        // [nblk] 1 / T_b
+    const float* beta_site;   // [H*W] 1 / T_i (site temperatures, Sec. 2.2.3) or nullptr
     const uint8_t* running;   // [nblk][Rp] or nullptr (= every lane r < R runs)
     float* eacc;              // [nblk][Rp] energy change of this sweep (moves)
     double* ecur;             // [nblk][Rp] E_b (the energy pass adds into it)

@@ -696,6 +696,55 @@ __global__ void k_block_energy(Geom g, const uint8_t* __restrict__ mask,
     if (lane == 0) E[warp] = s;
 }
 
+// ------------------------------------------------------------------- sst --
+// Sec. 2.2.3: site temperatures start from the block temperatures and are
+// replaced n_s times by the mean over the square of radius r around every
+// site (coordinates clamped to the grid). The square mean is the row mean
+// of the column means, so a pass is a row pass then a column pass; both sum
+// their window directly in FP64.
+__global__ void k_sst_expand(Geom g, const float* __restrict__ T_blk, double* __restrict__ Ts) {
+    const int64_t n = (int64_t)g.H * g.W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / g.W), x = (int)(i % g.W);
+        Ts[i] = (double)T_blk[(y / g.lb) * g.nbx + x / g.lb];
+    }
+}
+
+__global__ void k_sst_box(Geom g, const double* __restrict__ in, double* __restrict__ out, int r,
+                          int along_x) {
+    const int64_t n = (int64_t)g.H * g.W;
+    const double inv = 1.0 / (double)(2 * r + 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / g.W), x = (int)(i % g.W);
+        double s = 0.0;
+        if (along_x) {
+            const double* row = in + (int64_t)y * g.W;
+            for (int d = -r; d <= r; ++d) s += row[min(max(x + d, 0), g.W - 1)];
+        } else {
+            for (int d = -r; d <= r; ++d) s += in[(int64_t)min(max(y + d, 0), g.H - 1) * g.W + x];
+        }
+        out[i] = s * inv;
+    }
+}
+
+__global__ void k_site_beta(int64_t n, const float* __restrict__ Tf, float* __restrict__ beta) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        beta[i] = 1.0f / Tf[i];
+}
+
+__global__ void k_sst_beta(int64_t n, const double* __restrict__ Ts, float* __restrict__ Tf,
+                           float* __restrict__ beta) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float t = (float)Ts[i];
+        Tf[i] = t;
+        beta[i] = 1.0f / t;
+    }
+}
+
 // ---------------------------------------------------------- launchers --
 namespace {
 inline int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
@@ -945,6 +994,22 @@ void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, 
         k_block_energy<S><<<blocks, threads, 0, s>>>(g, mask, dang, static_cast<const S*>(ang), G,
                                                      r, q, J, E);
     });
+}
+
+void launch_sst(const Geom& g, const float* T_blk, int r, int n_s, double* Ts, double* tmp,
+                float* Tf, float* beta, cudaStream_t s) {
+    const int64_t n = (int64_t)g.H * g.W;
+    const int grid = grid_for(n, 256);
+    k_sst_expand<<<grid, 256, 0, s>>>(g, T_blk, Ts);
+    for (int k = 0; k < n_s; ++k) {
+        k_sst_box<<<grid, 256, 0, s>>>(g, Ts, tmp, r, 1);
+        k_sst_box<<<grid, 256, 0, s>>>(g, tmp, Ts, r, 0);
+    }
+    k_sst_beta<<<grid, 256, 0, s>>>(n, Ts, Tf, beta);
+}
+
+void launch_site_beta(int64_t n, const float* Tf, float* beta, cudaStream_t s) {
+    k_site_beta<<<grid_for(n, 256), 256, 0, s>>>(n, Tf, beta);
 }
 
 }  // namespace mpr

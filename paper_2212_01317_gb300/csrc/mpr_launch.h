@@ -81,6 +81,12 @@ void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, 
                          int storage, int G, int r, double q, double J, double* E,
                          cudaStream_t s);
 
+// Sec. 2.2.3 site temperatures: Ts (FP64, H*W) smoothed from T_blk, then
+// Tf = (float)Ts and beta = 1 / Tf; tmp is H*W doubles of scratch.
+void launch_sst(const Geom& g, const float* T_blk, int r, int n_s, double* Ts, double* tmp,
+                float* Tf, float* beta, cudaStream_t s);
+void launch_site_beta(int64_t n, const float* Tf, float* beta, cudaStream_t s);
+
 int cal_persistent_blocks_per_sm(int G);
 cudaError_t launch_cal_persistent(const CalPersistArgs& a, int G, int grid, cudaStream_t s);
 

@@ -243,14 +243,15 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
         const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
         const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
         const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
+        const float bt = a.beta_site ? a.beta_site[(size_t)y * a.g.W + x] : beta;
         float2 out = ph;
         if (run0) {
-            const SiteNew n = site_update<S>(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
+            const SiteNew n = site_update<S>(ph.x, C0, S0, u01(w[0]), u01(w[1]), bt, a.m);
             out.x = n.phi;
             add_energy(n, f, C0, S0, nc0, ns0, J, ao0, al0, au0);
         }
         if (run1) {
-            const SiteNew n = site_update<S>(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
+            const SiteNew n = site_update<S>(ph.y, C1, S1, u01(w[2]), u01(w[3]), bt, a.m);
             out.y = n.phi;
             add_energy(n, f, C1, S1, nc1, ns1, J, ao1, al1, au1);
         }

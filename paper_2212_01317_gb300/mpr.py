@@ -25,7 +25,8 @@ EXPORTS = [
     "mpr_sim_end", "mpr_halfstep", "mpr_get_state", "mpr_set_state", "mpr_get_stop",
     "mpr_set_running", "mpr_block_energy", "mpr_get_block_e", "mpr_get_profile",
     "mpr_block_stats_noalloc", "mpr_set_realization_base", "mpr_get_accumulator",
-    "mpr_set_accumulator",
+    "mpr_set_accumulator", "mpr_smooth_temperatures", "mpr_set_site_temperatures",
+    "mpr_get_site_temperatures",
 ]
 MPR_NOALLOC_MAX_BLOCKS = 65536
 
@@ -116,6 +117,9 @@ def load(path: str | None = None):
         "mpr_set_realization_base": (st, [P, i64]),
         "mpr_get_accumulator": (st, [P, P, C.POINTER(i64)]),
         "mpr_set_accumulator": (st, [P, P, i64]),
+        "mpr_smooth_temperatures": (st, [P, i32, i32, P]),
+        "mpr_set_site_temperatures": (st, [P, P]),
+        "mpr_get_site_temperatures": (st, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -247,6 +251,18 @@ def mpr_get_block_e(ctx, out):
     _check(ctx, load().mpr_get_block_e(ctx, _ptr(out)))
 
 
+def mpr_smooth_temperatures(ctx, r_s: int, n_s: int, T_site_out=None):
+    _check(ctx, load().mpr_smooth_temperatures(ctx, int(r_s), int(n_s), _ptr(T_site_out)))
+
+
+def mpr_set_site_temperatures(ctx, T_site=None):
+    _check(ctx, load().mpr_set_site_temperatures(ctx, _ptr(T_site)))
+
+
+def mpr_get_site_temperatures(ctx, out):
+    _check(ctx, load().mpr_get_site_temperatures(ctx, _ptr(out)))
+
+
 def mpr_set_realization_base(ctx, r_first: int):
     _check(ctx, load().mpr_set_realization_base(ctx, int(r_first)))
 
@@ -327,6 +343,15 @@ class GapFiller:
         ma, ng = np.zeros(n, np.float32), np.zeros(n, np.int32)
         mpr_get_block_stats(self.ctx, Es, Nsp, Nb, ma, ng)
         return Es, Nsp, Nb, ma, ng
+
+    def smooth_temperatures(self, r_s: int, n_s: int) -> np.ndarray:
+        out = np.zeros((self.H, self.W), np.float32)
+        mpr_smooth_temperatures(self.ctx, r_s, n_s, out)
+        return out
+
+    def set_site_temperatures(self, T_site):
+        mpr_set_site_temperatures(
+            self.ctx, None if T_site is None else np.ascontiguousarray(T_site, dtype=np.float32))
 
     # step-wise access
     def sim_begin(self, n: int):

@@ -1,0 +1,130 @@
+"""Site-specific temperatures (SST, Sec. 2.2.3) on the GPU against the oracle.
+
+  * the smoothed site temperatures, element by element;
+  * one half-step at site temperatures, element by element (decisions within
+    rounding of their threshold may flip, as for the block temperatures);
+  * the full pipeline given block temperatures and (r_s, n_s).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_01317_gb300 import synth
+from paper_2212_01317_gb300.mpr import GapFiller, MprError
+
+from parity import TWO_PI, checkerboard, compare_site_updates
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def make(z, m, lb, **opt):
+    v = np.where(m != 0, np.nan, z).astype(np.float32)
+    return GapFiller(v, m, lb, **opt)
+
+
+@pytest.mark.parametrize("H,W,lb,r_s,n_s", [(40, 56, 8, 8, 5), (37, 29, 5, 2, 3), (64, 64, 16, 16, 5),
+                                            (17, 90, 32, 1, 1), (20, 20, 4, 0, 2), (33, 33, 8, 40, 2)])
+def test_site_temperatures_match_oracle(H, W, lb, r_s, n_s):
+    z, m = synth.small_problem(H, W, 0.5, seed=H * W)
+    gf = make(z, m, lb)
+    rng = np.random.default_rng(H)
+    T = rng.uniform(0.02, 1.5, gf.nblk).astype(np.float32)
+    gf.set_temperatures(T)
+    ts = gf.smooth_temperatures(r_s, n_s)
+    o = oracle.Oracle(H, W, lb)
+    want = o.sst_temperatures(T.astype(np.float64), r_s, n_s).astype(np.float32)
+    np.testing.assert_allclose(ts, want, rtol=2e-7, atol=0)
+    got = np.zeros_like(ts)
+    from paper_2212_01317_gb300 import mpr
+    mpr.mpr_get_site_temperatures(gf.ctx, got)
+    np.testing.assert_array_equal(got, ts)
+    gf.close()
+
+
+@pytest.mark.parametrize("group,R", [(2, 1), (8, 12)])
+@pytest.mark.parametrize("colour", [0, 1])
+def test_halfstep_at_site_temperatures(group, R, colour):
+    H, W, lb = 45, 38, 8
+    z, m = synth.small_problem(H, W, 0.55, seed=9 + colour)
+    gf = make(z, m, lb, seed=0x5151, group=group)
+    o = oracle.Oracle(H, W, lb, seed=0x5151)
+    rng = np.random.default_rng(3)
+    T = rng.uniform(0.02, 1.2, gf.nblk).astype(np.float32)
+    gf.set_temperatures(T)
+    ts = rng.uniform(0.02, 1.2, (H, W)).astype(np.float32)
+    gf.set_site_temperatures(ts)
+    o.use_site_temperatures(ts.astype(np.float64))
+    gf.sim_begin(R)
+    pre = []
+    for r in range(R):
+        s = gf.get_state(r)
+        s[m != 0] = rng.uniform(0, TWO_PI, int((m != 0).sum())).astype(np.float32)
+        gf.set_state(r, s)
+        pre.append(s)
+    gf.halfstep(colour, 11, 0)
+    cb = checkerboard(H, W)
+    total = flips = 0
+    for r in range(R):
+        post = gf.get_state(r)
+        ph = pre[r].astype(np.float64)
+        diag = o.halfstep(ph, m, colour, T.astype(np.float64), None, t=11, tag=0, r=r,
+                          diag=True).reshape(H, W)
+        may = (m != 0) & (cb == colour)
+        n, f, bad, msg = compare_site_updates(post, ph, pre[r], diag, may)
+        assert bad == 0, f"r={r}: {msg}"
+        total += n
+        flips += f
+    assert flips <= max(2, total // 2000)
+    gf.sim_end()
+    gf.close()
+
+
+@pytest.mark.parametrize("group", [2, 8])
+def test_pipeline_matches_oracle_with_sst(group):
+    H, W, lb, R = 40, 48, 8, 6
+    z, m = synth.small_problem(H, W, 0.5, seed=31)
+    rng = np.random.default_rng(2)
+    T = rng.uniform(0.02, 0.4, (H // lb) * (W // lb)).astype(np.float32)
+    gf = make(z, m, lb, seed=77, group=group, n_max=60)
+    gf.set_temperatures(T)
+    gf.smooth_temperatures(4, 5)
+    gf.simulate(R)
+    pred, (aae, rase) = gf.predict(truth=z)
+    ref = oracle.gapfill(z, m, lb, R=R, seed=77, T_blk=T.astype(np.float64), n_max=60,
+                         sst=(4, 5))
+    a_ref, r_ref = oracle.Oracle.scores(ref.pred, z, m)
+    g = m != 0
+    scale = gf.info.zmax - gf.info.zmin
+    close = np.abs(pred - ref.pred) <= 1e-4 * scale
+    if close[g].all():
+        assert abs(aae - a_ref) <= 1e-4 * a_ref and abs(rase - r_ref) <= 1e-4 * r_ref
+    else:
+        assert close[g].mean() > 0.9
+        assert abs(aae - a_ref) <= 0.05 * a_ref
+    gf.close()
+
+
+def test_sst_state_rules():
+    z, m = synth.small_problem(20, 20, 0.5, seed=1)
+    gf = make(z, m, 4)
+    with pytest.raises(MprError):
+        gf.smooth_temperatures(1, 1)               # no block temperatures yet
+    gf.set_temperatures(np.full(gf.nblk, 0.1, np.float32))
+    with pytest.raises(MprError):
+        gf.smooth_temperatures(-1, 1)
+    with pytest.raises(MprError):
+        gf.set_site_temperatures(np.zeros((20, 20), np.float32))
+    ts = gf.smooth_temperatures(2, 2)
+    np.testing.assert_allclose(ts, 0.1, rtol=1e-6)
+    gf.set_temperatures(np.full(gf.nblk, 0.2, np.float32))   # back to block temperatures
+    from paper_2212_01317_gb300 import mpr
+    with pytest.raises(MprError):
+        mpr.mpr_get_site_temperatures(gf.ctx, np.zeros((20, 20), np.float32))
+    gf.close()
