@@ -92,6 +92,9 @@ def lib():
             "orc_median_targeted": (f64, [i32, P, P]),
             "orc_scores": (None, [i64, P, P, P, P, P]),
             "orc_sst_temperatures": (None, [MP, P, i32, i32, P]),
+            "orc_energy_moments": (None, [MP, P, P, P, i32, i32, i32, u32, P, P, P, P, P]),
+            "orc_calibrate_newton": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, f64, f64, f64,
+                                            P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -291,6 +294,31 @@ class Oracle:
         lib().orc_calibrate(C.byref(self.m), _p(ph), _p(mk), _p(st.Es), _p(st.Nsp), _p(st.Nb),
                             n_eq, n_meas, n_bisect, chains, T_lo, T_hi, _p(T),
                             None if tr is None else _p(tr))
+        return (T, tr) if trace else T
+
+    def energy_moments(self, phi_chains, mask, T_blk, n_eq: int, n_meas: int, tag: int,
+                       st: BlockStats):
+        """Moments of the block energies over the chains' measured sweeps; the
+        chains' states phi_chains[chains, H, W] advance in place. Returns
+        (mean_e, var_E, cov_right, cov_down), each nblk long."""
+        assert phi_chains.dtype == np.float64 and phi_chains.flags.c_contiguous
+        chains = phi_chains.shape[0]
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.ascontiguousarray(T_blk, dtype=np.float64)
+        out = [np.zeros(self.nblk) for _ in range(4)]
+        lib().orc_energy_moments(C.byref(self.m), _p(phi_chains), _p(mk), _p(T), n_eq, n_meas,
+                                 chains, tag, _p(st.Nb), *[_p(a) for a in out])
+        return tuple(out)
+
+    def calibrate_newton(self, phi_init, mask, st: BlockStats, n_eq=25, n_meas=20, n_newton=6,
+                         chains=1, T_lo=1e-4, T_hi=2.0, T0=0.1, trace=False):
+        ph = np.ascontiguousarray(phi_init, dtype=np.float64)
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.zeros(self.nblk)
+        tr = np.zeros((n_newton, self.nblk)) if trace else None
+        lib().orc_calibrate_newton(C.byref(self.m), _p(ph), _p(mk), _p(st.Es), _p(st.Nsp),
+                                   _p(st.Nb), n_eq, n_meas, n_newton, chains, T_lo, T_hi, T0,
+                                   _p(T), None if tr is None else _p(tr))
         return (T, tr) if trace else T
 
     @staticmethod

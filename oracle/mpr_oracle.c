@@ -522,6 +522,81 @@ void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* ma
 }
 
 /* ----------------------------------------------------------------- scores -- */
+/* --------------------------------------------- moments and Newton (f1) -- */
+
+void orc_energy_moments(const orc_model* m, double* phi, const uint8_t* mask, const double* T,
+                        int32_t n_eq, int32_t n_meas, int32_t chains, uint32_t tag,
+                        const int64_t* Nb, double* mean_e, double* var_E, double* cov_r,
+                        double* cov_d) {
+    const int nblk = m->nblk, nbx = m->nbx;
+    const int64_t n = (int64_t)m->H * m->W;
+    double* E = (double*)malloc(sizeof(double) * nblk);
+    double* s1 = (double*)calloc((size_t)nblk, sizeof(double));
+    double* s2 = (double*)calloc((size_t)nblk, sizeof(double));
+    double* sr = (double*)calloc((size_t)nblk, sizeof(double));
+    double* sd = (double*)calloc((size_t)nblk, sizeof(double));
+    for (int c = 0; c < chains; ++c) {
+        double* ph = phi + (int64_t)c * n;
+        for (int s = 1; s <= n_eq + n_meas; ++s) {
+            orc_halfstep(m, ph, mask, 0, T, NULL, (uint32_t)s, tag, (uint32_t)c, NULL);
+            orc_halfstep(m, ph, mask, 1, T, NULL, (uint32_t)s, tag, (uint32_t)c, NULL);
+            if (s <= n_eq) continue;
+            orc_block_energy(m, ph, E);
+            for (int b = 0; b < nblk; ++b) {
+                s1[b] += E[b];
+                s2[b] += E[b] * E[b];
+                if (b % nbx != nbx - 1) sr[b] += E[b] * E[b + 1];
+                if (b + nbx < nblk) sd[b] += E[b] * E[b + nbx];
+            }
+        }
+    }
+    const double inv = 1.0 / ((double)n_meas * (double)chains);
+    for (int b = 0; b < nblk; ++b) {
+        const double m1 = s1[b] * inv;
+        if (mean_e) mean_e[b] = Nb[b] > 0 ? m1 / (double)Nb[b] : 0.0;
+        if (var_E) var_E[b] = s2[b] * inv - m1 * m1;
+        if (cov_r) cov_r[b] = (b % nbx != nbx - 1) ? sr[b] * inv - m1 * s1[b + 1] * inv : 0.0;
+        if (cov_d) cov_d[b] = (b + nbx < nblk) ? sd[b] * inv - m1 * s1[b + nbx] * inv : 0.0;
+    }
+    free(E); free(s1); free(s2); free(sr); free(sd);
+}
+
+void orc_calibrate_newton(const orc_model* m, const double* phi_init, const uint8_t* mask,
+                          const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                          int32_t n_meas, int32_t n_newton, int32_t chains, double T_lo,
+                          double T_hi, double T0, double* T_out, double* trace) {
+    const int nblk = m->nblk;
+    const int64_t n = (int64_t)m->H * m->W;
+    double* lo = (double*)malloc(sizeof(double) * nblk);
+    double* hi = (double*)malloc(sizeof(double) * nblk);
+    double* T = (double*)malloc(sizeof(double) * nblk);
+    double* y = (double*)malloc(sizeof(double) * nblk);
+    double* v = (double*)malloc(sizeof(double) * nblk);
+    double* phi = (double*)malloc(sizeof(double) * n * (size_t)chains);
+    for (int c = 0; c < chains; ++c) memcpy(phi + (int64_t)c * n, phi_init, sizeof(double) * n);
+    for (int b = 0; b < nblk; ++b) { lo[b] = T_lo; hi[b] = T_hi; T[b] = T0; }
+    for (int k = 0; k < n_newton; ++k) {
+        const double med = orc_median_targeted(nblk, T, Nsp);
+        for (int b = 0; b < nblk; ++b)
+            if (Nsp[b] == 0) T[b] = med;
+        if (trace) memcpy(trace + (int64_t)k * nblk, T, sizeof(double) * nblk);
+        orc_energy_moments(m, phi, mask, T, n_eq, n_meas, chains, (uint32_t)(1 + k), Nb, y, v,
+                           NULL, NULL);
+        for (int b = 0; b < nblk; ++b) {
+            if (Nsp[b] == 0) continue;
+            const double es = Es[b] / (double)Nsp[b];
+            if (y[b] < es) lo[b] = T[b]; else hi[b] = T[b];
+            const double beta = 1.0 / T[b];
+            const double bn = v[b] > 0.0 ? beta + (y[b] - es) * (double)Nb[b] / v[b] : 0.0;
+            const double tn = bn > 0.0 ? 1.0 / bn : 0.0;
+            T[b] = (tn > lo[b] && tn < hi[b]) ? tn : 0.5 * (lo[b] + hi[b]);
+        }
+    }
+    const double med = orc_median_targeted(nblk, T, Nsp);
+    for (int b = 0; b < nblk; ++b) T_out[b] = Nsp[b] == 0 ? med : T[b];
+    free(lo); free(hi); free(T); free(y); free(v); free(phi);
+}
+
 /* Eqs. 3-4: AAE and RASE over the P prediction sites. */
 void orc_scores(int64_t n, const float* pred, const float* truth, const uint8_t* mask,
                 double* aae, double* rase) {

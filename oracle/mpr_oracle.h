@@ -113,6 +113,37 @@ void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* ma
                    const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
                    int32_t n_meas, int32_t n_bisect, int32_t chains, double T_lo, double T_hi,
                    double* T_out, double* ebar_trace);
+/* Energy moments of the calibration chains at block temperatures T[nblk]
+ * (the energy matching of Sec. 2.1 / 2.2.2, with the fluctuation identity
+ * for its derivative): chain c (c < chains) of phi[c][H*W] runs sweeps
+ * s = 1 .. n_eq + n_meas with random-stream tag `tag` and realization index
+ * c; after each of the last n_meas sweeps, E_b (Eq. 1 over the bonds block b
+ * owns, FP64 from scratch) enters the sums. Out (each nblk, any may be NULL):
+ * mean_e[b] = <E_b> / N_b (0 if N_b = 0), var_E[b] = <E_b^2> - <E_b>^2,
+ * cov_r[b] = <E_b E_{b+1}> - <E_b><E_{b+1}> (block to the right; 0 on the last
+ * block column), cov_d[b] = the same with the block below (0 on the last row).
+ * Averages run over the n_meas sweeps and the chains. phi is updated in place. */
+void orc_energy_moments(const orc_model* m, double* phi, const uint8_t* mask, const double* T,
+                        int32_t n_eq, int32_t n_meas, int32_t chains, uint32_t tag,
+                        const int64_t* Nb, double* mean_e, double* var_E, double* cov_r,
+                        double* cov_d);
+
+/* Per-block temperatures by safeguarded Newton steps on the energy match:
+ * iteration k (k < n_newton) gives untargeted blocks the median of the
+ * targeted T, runs the chains (fresh from phi_init at k = 0, continued after)
+ * with tag 1 + k, and from y_b = <E_b>/N_b and d y_b / d beta_b = -Var(E_b)/N_b
+ * (fluctuation identity) moves every targeted block to
+ *   beta_b + (y_b - e_s,b) N_b / Var(E_b),
+ * unless Var(E_b) = 0 or the step leaves the block's bracket (T_lo, T_hi),
+ * which shrinks on every iteration to the side of e_s,b as in bisection; then
+ * T_b is the bracket's midpoint. Starts at T0. T_out: final temperatures,
+ * untargeted blocks at the median. trace (NULL or n_newton * nblk): the T_b
+ * each iteration ran at. */
+void orc_calibrate_newton(const orc_model* m, const double* phi_init, const uint8_t* mask,
+                          const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                          int32_t n_meas, int32_t n_newton, int32_t chains, double T_lo,
+                          double T_hi, double T0, double* T_out, double* trace);
+
 /* Median of the temperatures of targeted blocks (Sec. 2.2.2 fallback). */
 double orc_median_targeted(int32_t nblk, const double* T, const int64_t* Nsp);
 
