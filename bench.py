@@ -51,6 +51,9 @@ def parse():
                     help="element type of the realizations' angles (arithmetic stays FP32)")
     ap.add_argument("--cal-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="calibration launch form (3: every kernel from the host, for profilers)")
+    ap.add_argument("--calibration", default="bisection", choices=["bisection", "newton"],
+                    help="per-block temperature fit: bisection (the plain form) or safeguarded "
+                         "Newton steps from the fluctuation identity")
     ap.add_argument("--shard", default="fields", choices=["fields", "realizations"],
                     help="fields: every rank its own field (weak scaling, no collective); "
                          "realizations: ranks share one field's realizations (strong scaling, "
@@ -239,6 +242,7 @@ def run_ours(args, world, rank, local):
     def options(profile):
         return mpr.mpr_default_options(seed=seed, slice_id=slice_id, profile=profile,
                                        storage=STORAGE[args.storage], cal_mode=args.cal_mode,
+                                       cal_method=1 if args.calibration == "newton" else 0,
                                        cuda_stream=stream.cuda_stream)
 
     def step(values, mask, out, profile=1):
@@ -373,6 +377,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": wl.name, "H": H, "W": W, "block": wl.block, "gap_fraction": p,
                    "realizations": R, "storage": args.storage, "cal_mode": args.cal_mode,
+                   "calibration": args.calibration,
                    "l2": "flushed between timed steps",
                    "parallelism": (f"replicas{world}" if shard == "fields"
                                    else f"realizations{world}")},

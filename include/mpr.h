@@ -87,6 +87,10 @@ typedef struct {
                             a wait that gives up makes the call return MPR_ETIMEOUT */
     int32_t barrier_test; /* test hook: extra arrivals the grid barrier waits for (default 0);
                              > 0 makes every wait give up after wait_ms */
+    int32_t cal_method;  /* 0 bisection (default), 1 damped Newton steps on beta_b with
+                            d<e_b>/d beta_b = -Var(E_b)/N_b (see mpr_energy_moments) */
+    int32_t n_newton;    /* Newton iterations (default 6), each n_eq + n_meas sweeps */
+    float t_init;        /* Newton starting temperature (default 0.1) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 
@@ -149,6 +153,13 @@ mpr_status mpr_get_profile(mpr_ctx* ctx, mpr_profile* out);
  * the gap sites, runs n_eq + n_meas sweeps of cal_chains chains at the current
  * midpoints and keeps the half of each bracket on the side of e_s,b. Blocks
  * without sample bonds take the median of the other blocks' temperatures.
+ * With cal_method = 1 the bisection is replaced by n_newton damped Newton
+ * steps on beta_b (see mpr_energy_moments): iteration k runs the chains
+ * (fresh at k = 0, continued after) with tag 1 + k at the current T, and
+ * every targeted block moves to beta_b + (y_b - e_s,b) N_b / Var(E_b), the
+ * new T kept within a factor 2 of the old one and within [t_lo, t_hi] (T
+ * doubled when that beta is <= 0; without variance, doubled or halved
+ * towards e_s,b). Starts at t_init.
  * block_T_out: NULL or nblk floats (host or device), row-major blocks.
  * Errors: EINVAL, ECUDA. A degenerate field (z_max == z_min) skips the
  * iterations and sets every T_b to t_lo. */
@@ -157,6 +168,35 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out);
 /* Sets the block temperatures directly (nblk floats > 0, host or device). */
 mpr_status mpr_set_temperatures(mpr_ctx* ctx, const float* block_T);
 mpr_status mpr_get_temperatures(mpr_ctx* ctx, float* block_T_out);
+
+/* ---- differentiable energy matching ----
+ * The calibration (Sec. 2.1, applied per block in Sec. 2.2.2) matches the
+ * chains' mean specific block energy y_b = <E_b>/N_b to e_s,b. For the Gibbs
+ * law exp(-sum_b beta_b E_b) its derivative is the fluctuation identity
+ *   d y_a / d beta_b = -Cov(E_a, E_b) / N_a,
+ * exact for one block and for blocks whose gap sites' bonds all belong to
+ * their own block; at block edges (a site's left / up bond owned by the
+ * neighbouring block, updated at its own block's beta) it is an
+ * approximation. Covariances beyond the four neighbouring blocks are
+ * taken as 0.
+ * mpr_energy_moments: sets the block inverse temperatures to beta[nblk]
+ *   (host or device floats > 0, as mpr_set_temperatures with T = 1/beta),
+ *   then runs the cal_chains calibration chains for n_eq + n_meas sweeps
+ *   with random-stream tag `tag` (1 ... 65534): fresh from the block-mean
+ *   start when restart != 0 (equal tags and restarts give common random
+ *   numbers), else continuing the chains of the last call or calibration.
+ *   Out (each nblk doubles, host or device, any may be NULL): mean_e = y_b,
+ *   var_E = Var(E_b), cov_r = Cov(E_b, E_{b+1}) (block to the right; 0 on
+ *   the last block column), cov_d = Cov(E_b, E_{b+nbx}) (0 on the last
+ *   block row); averages over the n_meas measured sweeps and the chains,
+ *   FP64. The moments stay in the context for mpr_energy_vjp.
+ * mpr_energy_vjp: grad_beta[b] = sum_a grad_e[a] d y_a / d beta_b with the
+ *   moments of the last mpr_energy_moments (nblk doubles each, host or device).
+ * Errors: ESTATE (a realization batch is open; no moments yet), EINVAL, ECUDA. */
+mpr_status mpr_energy_moments(mpr_ctx* ctx, const float* beta, int32_t n_eq, int32_t n_meas,
+                              int32_t tag, int32_t restart, double* mean_e, double* var_E,
+                              double* cov_r, double* cov_d);
+mpr_status mpr_energy_vjp(mpr_ctx* ctx, const double* grad_e, double* grad_beta);
 
 /* ---- site-specific temperatures (SST, Sec. 2.2.3) ----
  * mpr_smooth_temperatures: every site starts from its block's temperature

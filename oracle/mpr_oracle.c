@@ -561,20 +561,20 @@ void orc_energy_moments(const orc_model* m, double* phi, const uint8_t* mask, co
     free(E); free(s1); free(s2); free(sr); free(sd);
 }
 
+#define NEWTON_STEP 2.0   /* largest factor by which one Newton step moves T */
+
 void orc_calibrate_newton(const orc_model* m, const double* phi_init, const uint8_t* mask,
                           const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_newton, int32_t chains, double T_lo,
                           double T_hi, double T0, double* T_out, double* trace) {
     const int nblk = m->nblk;
     const int64_t n = (int64_t)m->H * m->W;
-    double* lo = (double*)malloc(sizeof(double) * nblk);
-    double* hi = (double*)malloc(sizeof(double) * nblk);
     double* T = (double*)malloc(sizeof(double) * nblk);
     double* y = (double*)malloc(sizeof(double) * nblk);
     double* v = (double*)malloc(sizeof(double) * nblk);
     double* phi = (double*)malloc(sizeof(double) * n * (size_t)chains);
     for (int c = 0; c < chains; ++c) memcpy(phi + (int64_t)c * n, phi_init, sizeof(double) * n);
-    for (int b = 0; b < nblk; ++b) { lo[b] = T_lo; hi[b] = T_hi; T[b] = T0; }
+    for (int b = 0; b < nblk; ++b) T[b] = T0;
     for (int k = 0; k < n_newton; ++k) {
         const double med = orc_median_targeted(nblk, T, Nsp);
         for (int b = 0; b < nblk; ++b)
@@ -585,16 +585,21 @@ void orc_calibrate_newton(const orc_model* m, const double* phi_init, const uint
         for (int b = 0; b < nblk; ++b) {
             if (Nsp[b] == 0) continue;
             const double es = Es[b] / (double)Nsp[b];
-            if (y[b] < es) lo[b] = T[b]; else hi[b] = T[b];
-            const double beta = 1.0 / T[b];
-            const double bn = v[b] > 0.0 ? beta + (y[b] - es) * (double)Nb[b] / v[b] : 0.0;
-            const double tn = bn > 0.0 ? 1.0 / bn : 0.0;
-            T[b] = (tn > lo[b] && tn < hi[b]) ? tn : 0.5 * (lo[b] + hi[b]);
+            double tn;
+            if (v[b] > 0.0) {
+                const double bn = 1.0 / T[b] + (y[b] - es) * (double)Nb[b] / v[b];
+                tn = bn > 0.0 ? 1.0 / bn : NEWTON_STEP * T[b];
+            } else {
+                tn = y[b] < es ? NEWTON_STEP * T[b] : T[b] / NEWTON_STEP;
+            }
+            tn = tn < T[b] / NEWTON_STEP ? T[b] / NEWTON_STEP
+                                         : (tn > NEWTON_STEP * T[b] ? NEWTON_STEP * T[b] : tn);
+            T[b] = tn < T_lo ? T_lo : (tn > T_hi ? T_hi : tn);
         }
     }
     const double med = orc_median_targeted(nblk, T, Nsp);
     for (int b = 0; b < nblk; ++b) T_out[b] = Nsp[b] == 0 ? med : T[b];
-    free(lo); free(hi); free(T); free(y); free(v); free(phi);
+    free(T); free(y); free(v); free(phi);
 }
 
 /* Eqs. 3-4: AAE and RASE over the P prediction sites. */

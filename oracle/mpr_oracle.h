@@ -128,17 +128,16 @@ void orc_energy_moments(const orc_model* m, double* phi, const uint8_t* mask, co
                         const int64_t* Nb, double* mean_e, double* var_E, double* cov_r,
                         double* cov_d);
 
-/* Per-block temperatures by safeguarded Newton steps on the energy match:
+/* Per-block temperatures by damped Newton steps on the energy match:
  * iteration k (k < n_newton) gives untargeted blocks the median of the
  * targeted T, runs the chains (fresh from phi_init at k = 0, continued after)
  * with tag 1 + k, and from y_b = <E_b>/N_b and d y_b / d beta_b = -Var(E_b)/N_b
  * (fluctuation identity) moves every targeted block to
- *   beta_b + (y_b - e_s,b) N_b / Var(E_b),
- * unless Var(E_b) = 0 or the step leaves the block's bracket (T_lo, T_hi),
- * which shrinks on every iteration to the side of e_s,b as in bisection; then
- * T_b is the bracket's midpoint. Starts at T0. T_out: final temperatures,
- * untargeted blocks at the median. trace (NULL or n_newton * nblk): the T_b
- * each iteration ran at. */
+ *   beta_b + (y_b - e_s,b) N_b / Var(E_b)
+ * (T doubled if that beta is <= 0; without variance, T doubled or halved
+ * towards e_s,b), the new T kept within a factor 2 of the old one and within
+ * [T_lo, T_hi]. Starts at T0. T_out: final temperatures, untargeted blocks at
+ * the median. trace (NULL or n_newton * nblk): the T_b each iteration ran at. */
 void orc_calibrate_newton(const orc_model* m, const double* phi_init, const uint8_t* mask,
                           const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_newton, int32_t chains, double T_lo,

@@ -52,6 +52,10 @@ struct mpr_ctx {
     float* T_site = nullptr;     // [H*W] site temperatures (SST), allocated on first use
     float* beta_site = nullptr;  // [H*W] 1 / T_site
     int sst = 0;                 // 1: realizations use the site temperatures
+    double* msum = nullptr;      // [4][nblk] sums of E, E^2, E E_right, E E_down
+    double* mom = nullptr;       // [4][nblk] moments of the last energy-moment run
+    bool chains_valid = false;   // the batch state holds the calibration chains
+    bool moments_valid = false;
     double* ebar = nullptr;
     double* sum = nullptr;  // [2][H][Wh] running sums of gap angles
     float* out_buf = nullptr;
@@ -187,6 +191,10 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.cal_mode < 0 || o.cal_mode > 3) return fail(ctx, MPR_EINVAL, "cal_mode must be 0 ... 3");
     if (o.wait_ms < 1) return fail(ctx, MPR_EINVAL, "wait_ms must be >= 1");
     if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
+    if (o.cal_method != 0 && o.cal_method != 1) return fail(ctx, MPR_EINVAL, "cal_method must be 0 or 1");
+    if (o.n_newton < 0 || o.n_newton > 65533) return fail(ctx, MPR_EINVAL, "n_newton in [0, 65533]");
+    if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
+        return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
     return MPR_OK;
 }
 
@@ -444,6 +452,85 @@ mpr_status refresh_energies(mpr_ctx* ctx) {
 // and median fallback, fresh start, E_b from scratch, n_eq + n_meas sweeps
 // with the energies of the last n_meas summed, bisection step. With cond != 0
 // the last kernel also sets the graph's loop condition.
+// One calibration half-step of colour c at sweep index sw (k_sweep_flat),
+// timed with events when asked and profiling is on.
+mpr_status flat_halfstep(mpr_ctx* ctx, int c, int sw, bool timed) {
+    SweepArgs a = sweep_args(ctx, c, false);
+    a.t_fixed = sw;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed && ctx->opt.profile) {
+        e0 = get_event(ctx);
+        e1 = get_event(ctx);
+        if (e0) cudaEventRecord(e0, ctx->s);
+    }
+    launch_sweep_flat(a, ctx->G, ctx->n_gap[c], ctx->s);
+    CKL();
+    if (e0 && e1) {
+        cudaEventRecord(e1, ctx->s);
+        ctx->ev_cal.emplace_back(e0, e1);
+    }
+    ++ctx->cal_halfstep_launches;
+    return MPR_OK;
+}
+
+// The calibration chains (fresh from the block-mean start, or continued) run
+// n_eq + n_meas sweeps at the current beta with random-stream tag `tag`; the
+// block-energy moments of the measured sweeps land in ctx->mom.
+mpr_status moments_run(mpr_ctx* ctx, uint32_t tag, bool restart, int n_eq, int n_meas) {
+    const Geom& g = ctx->g;
+    const int chains = ctx->opt.cal_chains;
+    if (restart || !ctx->chains_valid || ctx->storage != MPR_STORE_F32 || ctx->R != chains) {
+        ctx->r_off = 0;
+        ctx->r_even = 0;
+        TRY(ensure_batch(ctx, chains, ctx->opt.group, MPR_STORE_F32));
+        ctx->R = chains;
+        launch_fill_samples(g, ctx->mask, ctx->dang, ctx->ang, MPR_STORE_F32, ctx->G,
+                            ctx->groups, ctx->s);
+        CKL();
+        TRY(init_batch_state(ctx));
+        ctx->chains_valid = true;
+    }
+    launch_set_tag(ctx->ctl, tag, ctx->s);
+    CKL();
+    TRY(energy_pass(ctx));
+    CK(cudaMemsetAsync(ctx->msum, 0, 4 * (size_t)g.nblk * sizeof(double), ctx->s));
+    for (int sw = 1; sw <= n_eq + n_meas; ++sw) {
+        for (int c = 0; c < 2; ++c) TRY(flat_halfstep(ctx, c, sw, true));
+        launch_cal_step(g.nblk, ctx->Rp, chains, n_eq, sw, ctx->ctl, ctx->inb, ctx->eacc,
+                        ctx->ecur, ctx->ebar, ctx->s);
+        CKL();
+        if (sw > n_eq) {
+            launch_cal_moments(g.nblk, g.nbx, ctx->Rp, chains, ctx->ecur, ctx->msum, ctx->s);
+            CKL();
+        }
+    }
+    launch_moments_final(g.nblk, g.nbx, 1.0 / ((double)n_meas * (double)chains), ctx->Nb,
+                         ctx->msum, ctx->mom, ctx->s);
+    CKL();
+    ctx->moments_valid = true;
+    ctx->cal_updates += (int64_t)(n_eq + n_meas) * chains * (ctx->n_gap[0] + ctx->n_gap[1]);
+    return MPR_OK;
+}
+
+// Damped Newton calibration (cal_method 1).
+mpr_status calibration_newton(mpr_ctx* ctx) {
+    const Geom& g = ctx->g;
+    const mpr_options& o = ctx->opt;
+    launch_newton_init(g.nblk, o.t_init, o.t_lo, o.t_hi, ctx->T, ctx->lo, ctx->hi, ctx->s);
+    CKL();
+    for (int k = 0; k < o.n_newton; ++k) {
+        launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);   // median, beta
+        CKL();
+        TRY(moments_run(ctx, (uint32_t)(1 + k), k == 0, o.n_eq, o.n_meas));
+        launch_newton_update(g.nblk, ctx->es, ctx->Nsp, ctx->Nb, ctx->mom, ctx->T, (double)o.t_lo,
+                             (double)o.t_hi, ctx->s);
+        CKL();
+    }
+    launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+    CKL();
+    return MPR_OK;
+}
+
 mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphConditionalHandle cond,
                                  bool timed) {
     const Geom& g = ctx->g;
@@ -657,6 +744,9 @@ void mpr_default_options(mpr_options* o) {
     o->cal_mode = 0;
     o->wait_ms = 2000;
     o->barrier_test = 0;
+    o->cal_method = 0;
+    o->n_newton = 6;
+    o->t_init = 0.1f;
     o->cuda_stream = nullptr;
 }
 
@@ -737,6 +827,8 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     ST(dalloc(ctx, &ctx->dang, 2 * plane));
     ST(dalloc(ctx, &ctx->sum, 2 * plane));
     ST(dalloc(ctx, &ctx->Es, g.nblk));
+    ST(dalloc(ctx, &ctx->msum, 4 * (size_t)g.nblk));
+    ST(dalloc(ctx, &ctx->mom, 4 * (size_t)g.nblk));
     ST(dalloc(ctx, &ctx->es, g.nblk));
     ST(dalloc(ctx, &ctx->inb, g.nblk));
     ST(dalloc(ctx, &ctx->Nsp, g.nblk));
@@ -957,10 +1049,20 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
         return MPR_OK;
     }
     const int chains = o.cal_chains;
+    if (o.cal_method == 1) {
+        TRY(calibration_newton(ctx));
+        ctx->calibrated = 1;
+        ctx->sst = 0;
+        if (block_T_out) TRY(copy_out(ctx, block_T_out, ctx->T, (size_t)g.nblk * 4));
+        CK(cudaStreamSynchronize(ctx->s));
+        collect_events(ctx);
+        return MPR_OK;
+    }
     ctx->r_off = 0;
     ctx->r_even = 0;
     TRY(ensure_batch(ctx, chains, o.group, MPR_STORE_F32));
     ctx->R = chains;
+    ctx->chains_valid = true;
     launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->ctl, ctx->s);
     CKL();
     const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);
@@ -1006,6 +1108,7 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     ctx->r_even = (uint32_t)(r_base - ctx->r_off);
     TRY(ensure_batch(ctx, n + ctx->r_off, ctx->opt.group, ctx->opt.storage));
     ctx->R = n;
+    ctx->chains_valid = false;
     ctx->t = 0;
     const int64_t nbr = (int64_t)ctx->g.nblk * ctx->Rp;
     k_fill_valid<<<(int)std::min<int64_t>((nbr + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
@@ -1310,6 +1413,56 @@ mpr_status mpr_get_site_temperatures(mpr_ctx* ctx, float* T_site) {
     ctx->err.clear();
     if (!ctx->sst) return fail(ctx, MPR_ESTATE, "no site temperatures");
     return copy_out(ctx, T_site, ctx->T_site, (size_t)ctx->g.H * ctx->g.W * 4);
+}
+
+mpr_status mpr_energy_moments(mpr_ctx* ctx, const float* beta, int32_t n_eq, int32_t n_meas,
+                              int32_t tag, int32_t restart, double* mean_e, double* var_E,
+                              double* cov_r, double* cov_d) {
+    if (!ctx || !beta) return MPR_EINVAL;
+    ctx->err.clear();
+    if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a realization batch is open");
+    if (n_eq < 0 || n_meas < 1 || n_eq + n_meas > 65535)
+        return fail(ctx, MPR_EINVAL, "need n_eq >= 0, n_meas >= 1, n_eq + n_meas <= 65535");
+    if (tag < 1 || tag > 65534) return fail(ctx, MPR_EINVAL, "tag must be in [1, 65534]");
+    const int nb = ctx->g.nblk;
+    std::vector<float> hb(nb), ht(nb);
+    CK(cudaMemcpyAsync(hb.data(), beta, nb * 4, cudaMemcpyDefault, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (int b = 0; b < nb; ++b) {
+        if (!(hb[b] > 0.0f) || !std::isfinite(hb[b]))
+            return fail(ctx, MPR_EINVAL, "beta of block %d is not a positive number", b);
+        ht[b] = 1.0f / hb[b];
+    }
+    CK(cudaMemcpyAsync(ctx->beta, hb.data(), nb * 4, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(ctx->T, ht.data(), nb * 4, cudaMemcpyHostToDevice, ctx->s));
+    ctx->calibrated = 1;
+    ctx->sst = 0;
+    TRY(moments_run(ctx, (uint32_t)tag, restart != 0, n_eq, n_meas));
+    double* outs[4] = {mean_e, var_E, cov_r, cov_d};
+    for (int k = 0; k < 4; ++k)
+        if (outs[k]) TRY(copy_out(ctx, outs[k], ctx->mom + (size_t)k * nb, (size_t)nb * 8));
+    CK(cudaStreamSynchronize(ctx->s));
+    collect_events(ctx);
+    return MPR_OK;
+}
+
+mpr_status mpr_energy_vjp(mpr_ctx* ctx, const double* grad_e, double* grad_beta) {
+    if (!ctx || !grad_e || !grad_beta) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!ctx->moments_valid) return fail(ctx, MPR_ESTATE, "no energy moments yet");
+    const size_t nb = (size_t)ctx->g.nblk;
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, 2 * nb * sizeof(double), ctx->s));
+    mpr_status st = copy_in(ctx, tmp, grad_e, nb * 8);
+    if (st == MPR_OK) {
+        launch_energy_vjp(ctx->g.nblk, ctx->g.nbx, ctx->Nb, ctx->mom, tmp, tmp + nb, ctx->s);
+        ++ctx->launches;
+        st = cudaPeekAtLastError() == cudaSuccess ? copy_out(ctx, grad_beta, tmp + nb, nb * 8)
+                                                  : fail(ctx, MPR_ECUDA, "k_energy_vjp");
+    }
+    cudaFreeAsync(tmp, ctx->s);
+    CK(cudaStreamSynchronize(ctx->s));
+    return st;
 }
 
 mpr_status mpr_set_realization_base(mpr_ctx* ctx, int64_t r_first) {

@@ -696,6 +696,100 @@ __global__ void k_block_energy(Geom g, const uint8_t* __restrict__ mask,
     if (lane == 0) E[warp] = s;
 }
 
+// --------------------------------------------------------------- moments --
+// The energy matching's derivative (fluctuation identity): after every
+// measured calibration sweep (block energies folded), per block the sums of
+// E_b, E_b^2 and E_b times the right / lower neighbour block's energy in the
+// same chain. S is [4][nblk].
+__global__ void k_cal_moments(int nblk, int nbx, int Rp, int chains,
+                              const double* __restrict__ ecur, double* __restrict__ S) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        double s1 = 0.0, s2 = 0.0, sr = 0.0, sd = 0.0;
+        const bool right = b % nbx != nbx - 1, down = b + nbx < nblk;
+        for (int r = 0; r < chains; ++r) {
+            const double E = ecur[(size_t)b * Rp + r];
+            s1 += E;
+            s2 += E * E;
+            if (right) sr += E * ecur[(size_t)(b + 1) * Rp + r];
+            if (down) sd += E * ecur[(size_t)(b + nbx) * Rp + r];
+        }
+        S[b] += s1;
+        S[nblk + b] += s2;
+        S[2 * nblk + b] += sr;
+        S[3 * nblk + b] += sd;
+    }
+}
+
+// Moments from the sums over n = measured sweeps x chains: M[0] = <E_b>/N_b,
+// M[1] = Var(E_b), M[2] = Cov(E_b, E_right), M[3] = Cov(E_b, E_down).
+__global__ void k_moments_final(int nblk, int nbx, double inv_n, const int32_t* __restrict__ Nb,
+                                const double* __restrict__ S, double* __restrict__ M) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        const double m1 = S[b] * inv_n;
+        M[b] = Nb[b] > 0 ? m1 / (double)Nb[b] : 0.0;
+        M[nblk + b] = S[nblk + b] * inv_n - m1 * m1;
+        M[2 * nblk + b] =
+            (b % nbx != nbx - 1) ? S[2 * nblk + b] * inv_n - m1 * (S[b + 1] * inv_n) : 0.0;
+        M[3 * nblk + b] = (b + nbx < nblk) ? S[3 * nblk + b] * inv_n - m1 * (S[b + nbx] * inv_n)
+                                           : 0.0;
+    }
+}
+
+// Damped Newton step of every targeted block on beta:
+// beta_b + (y_b - e_s,b) N_b / Var(E_b) (T doubled when that beta is <= 0;
+// without variance T doubled or halved towards e_s,b, as <e_b> grows with T),
+// kept within a factor 2 of the old T and within [t_lo, t_hi].
+__global__ void k_newton_update(int nblk, const double* __restrict__ es,
+                                const int32_t* __restrict__ Nsp, const int32_t* __restrict__ Nb,
+                                const double* __restrict__ M, float* __restrict__ T, double t_lo,
+                                double t_hi) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        if (Nsp[b] <= 0) continue;
+        const double y = M[b], v = M[nblk + b], tb = (double)T[b];
+        double tn;
+        if (v > 0.0) {
+            const double bn = 1.0 / tb + (y - es[b]) * (double)Nb[b] / v;
+            tn = bn > 0.0 ? 1.0 / bn : 2.0 * tb;
+        } else {
+            tn = y < es[b] ? 2.0 * tb : 0.5 * tb;
+        }
+        tn = fmin(fmax(tn, 0.5 * tb), 2.0 * tb);
+        T[b] = (float)fmin(fmax(tn, t_lo), t_hi);
+    }
+}
+
+__global__ void k_newton_init(int nblk, float t_init, float t_lo, float t_hi,
+                              float* __restrict__ T, float* __restrict__ lo,
+                              float* __restrict__ hi) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        T[b] = t_init;
+        lo[b] = t_lo;
+        hi[b] = t_hi;
+    }
+}
+
+// Vector-Jacobian product of y = <E>/N with respect to beta from the stored
+// moments: grad_beta_b = -sum_a g_a Cov(E_a, E_b) / N_a over a = b and its
+// four neighbouring blocks.
+__global__ void k_energy_vjp(int nblk, int nbx, const int32_t* __restrict__ Nb,
+                             const double* __restrict__ M, const double* __restrict__ g,
+                             double* __restrict__ out) {
+    const double* var = M + nblk;
+    const double* cr = M + 2 * nblk;
+    const double* cd = M + 3 * nblk;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        auto w = [&](int a) { return Nb[a] > 0 ? g[a] / (double)Nb[a] : 0.0; };
+        double acc = w(b) * var[b];
+        if (b % nbx != nbx - 1) acc += w(b + 1) * cr[b];
+        if (b % nbx != 0) acc += w(b - 1) * cr[b - 1];
+        if (b + nbx < nblk) acc += w(b + nbx) * cd[b];
+        if (b >= nbx) acc += w(b - nbx) * cd[b - nbx];
+        out[b] = -acc;
+    }
+}
+
+__global__ void k_set_tag(Control* ctl, uint32_t tag) { ctl->tag = tag; }
+
 // ------------------------------------------------------------------- sst --
 // Sec. 2.2.3: site temperatures start from the block temperatures and are
 // replaced n_s times by the mean over the square of radius r around every
@@ -1011,5 +1105,32 @@ void launch_sst(const Geom& g, const float* T_blk, int r, int n_s, double* Ts, d
 void launch_site_beta(int64_t n, const float* Tf, float* beta, cudaStream_t s) {
     k_site_beta<<<grid_for(n, 256), 256, 0, s>>>(n, Tf, beta);
 }
+
+void launch_cal_moments(int nblk, int nbx, int Rp, int chains, const double* ecur, double* S,
+                        cudaStream_t s) {
+    k_cal_moments<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, nbx, Rp, chains, ecur, S);
+}
+
+void launch_moments_final(int nblk, int nbx, double inv_n, const int32_t* Nb, const double* S,
+                          double* M, cudaStream_t s) {
+    k_moments_final<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, nbx, inv_n, Nb, S, M);
+}
+
+void launch_newton_update(int nblk, const double* es, const int32_t* Nsp, const int32_t* Nb,
+                          const double* M, float* T, double t_lo, double t_hi, cudaStream_t s) {
+    k_newton_update<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, es, Nsp, Nb, M, T, t_lo, t_hi);
+}
+
+void launch_newton_init(int nblk, float t_init, float t_lo, float t_hi, float* T, float* lo,
+                        float* hi, cudaStream_t s) {
+    k_newton_init<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, t_init, t_lo, t_hi, T, lo, hi);
+}
+
+void launch_energy_vjp(int nblk, int nbx, const int32_t* Nb, const double* M, const double* g,
+                       double* out, cudaStream_t s) {
+    k_energy_vjp<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, nbx, Nb, M, g, out);
+}
+
+void launch_set_tag(Control* ctl, uint32_t tag, cudaStream_t s) { k_set_tag<<<1, 1, 0, s>>>(ctl, tag); }
 
 }  // namespace mpr

@@ -87,6 +87,19 @@ void launch_sst(const Geom& g, const float* T_blk, int r, int n_s, double* Ts, d
                 float* Tf, float* beta, cudaStream_t s);
 void launch_site_beta(int64_t n, const float* Tf, float* beta, cudaStream_t s);
 
+// Energy moments of the calibration chains and the Newton calibration.
+void launch_cal_moments(int nblk, int nbx, int Rp, int chains, const double* ecur, double* S,
+                        cudaStream_t s);
+void launch_moments_final(int nblk, int nbx, double inv_n, const int32_t* Nb, const double* S,
+                          double* M, cudaStream_t s);
+void launch_newton_update(int nblk, const double* es, const int32_t* Nsp, const int32_t* Nb,
+                          const double* M, float* T, double t_lo, double t_hi, cudaStream_t s);
+void launch_newton_init(int nblk, float t_init, float t_lo, float t_hi, float* T, float* lo,
+                        float* hi, cudaStream_t s);
+void launch_energy_vjp(int nblk, int nbx, const int32_t* Nb, const double* M, const double* g,
+                       double* out, cudaStream_t s);
+void launch_set_tag(Control* ctl, uint32_t tag, cudaStream_t s);
+
 int cal_persistent_blocks_per_sm(int G);
 cudaError_t launch_cal_persistent(const CalPersistArgs& a, int G, int grid, cudaStream_t s);
 

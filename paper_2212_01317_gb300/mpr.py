@@ -26,7 +26,7 @@ EXPORTS = [
     "mpr_set_running", "mpr_block_energy", "mpr_get_block_e", "mpr_get_profile",
     "mpr_block_stats_noalloc", "mpr_set_realization_base", "mpr_get_accumulator",
     "mpr_set_accumulator", "mpr_smooth_temperatures", "mpr_set_site_temperatures",
-    "mpr_get_site_temperatures",
+    "mpr_get_site_temperatures", "mpr_energy_moments", "mpr_energy_vjp",
 ]
 MPR_NOALLOC_MAX_BLOCKS = 65536
 
@@ -42,7 +42,8 @@ class mpr_options(C.Structure):
                 ("t_lo", C.c_float), ("t_hi", C.c_float), ("overrelax", C.c_int32),
                 ("init", C.c_int32), ("storage", C.c_int32), ("group", C.c_int32),
                 ("profile", C.c_int32), ("cal_mode", C.c_int32), ("wait_ms", C.c_int32),
-                ("barrier_test", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("barrier_test", C.c_int32), ("cal_method", C.c_int32), ("n_newton", C.c_int32),
+                ("t_init", C.c_float), ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):
@@ -120,6 +121,8 @@ def load(path: str | None = None):
         "mpr_smooth_temperatures": (st, [P, i32, i32, P]),
         "mpr_set_site_temperatures": (st, [P, P]),
         "mpr_get_site_temperatures": (st, [P, P]),
+        "mpr_energy_moments": (st, [P, P, i32, i32, i32, i32, P, P, P, P]),
+        "mpr_energy_vjp": (st, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -261,6 +264,17 @@ def mpr_set_site_temperatures(ctx, T_site=None):
 
 def mpr_get_site_temperatures(ctx, out):
     _check(ctx, load().mpr_get_site_temperatures(ctx, _ptr(out)))
+
+
+def mpr_energy_moments(ctx, beta, n_eq: int, n_meas: int, tag: int, restart: bool,
+                       mean_e=None, var_E=None, cov_r=None, cov_d=None):
+    _check(ctx, load().mpr_energy_moments(ctx, _ptr(beta), int(n_eq), int(n_meas), int(tag),
+                                          1 if restart else 0, _ptr(mean_e), _ptr(var_E),
+                                          _ptr(cov_r), _ptr(cov_d)))
+
+
+def mpr_energy_vjp(ctx, grad_e, grad_beta):
+    _check(ctx, load().mpr_energy_vjp(ctx, _ptr(grad_e), _ptr(grad_beta)))
 
 
 def mpr_set_realization_base(ctx, r_first: int):

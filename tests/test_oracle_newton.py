@@ -124,13 +124,15 @@ def test_newton_finds_the_exact_root():
     T, tr = o.calibrate_newton(phi0, mask, st, n_eq=10, n_meas=60, n_newton=8, chains=16,
                                T0=0.1, trace=True)
     assert abs(T[0] - T_star) / T_star < 0.03, (T[0], T_star, tr[:, 0])
-    # Newton steps converge fast: the last three iterates agree within 4 %
-    # (bisection alone, which the safeguard falls back to, would still move
-    # by about 8 % of T* between its 6th and 8th iterate from [1e-4, 2]).
-    assert np.ptp(tr[-3:, 0]) / T_star < 0.04
+    # Newton steps converge fast: the last three iterates agree within the
+    # Monte Carlo noise of one iteration's estimate (a few per cent).
+    assert np.ptp(tr[-3:, 0]) / T_star < 0.06
+    # every step stays within a factor 2 of the previous temperature
+    r = tr[1:, 0] / tr[:-1, 0]
+    assert np.all((r >= 0.5 - 1e-12) & (r <= 2 + 1e-12))
 
 
-def test_newton_median_fallback_and_bracket():
+def test_newton_median_fallback_and_bounds():
     z = np.random.default_rng(0).normal(size=(16, 16)).astype(np.float32)
     mask = np.zeros((16, 16), np.uint8)
     mask[0:8, 0:8] = 1                     # block 0: no sample bond at all
