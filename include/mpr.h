@@ -116,6 +116,7 @@ typedef struct {
     int64_t gap_updates;        /* Metropolis+OR site updates run by simulate so far */
     int64_t cal_gap_updates;    /* site updates run by calibrate so far */
     int64_t device_bytes;       /* device memory held by the context */
+    int32_t n_slices;           /* fields in the context (1 for mpr_create) */
 } mpr_info;
 
 /* Fills *opt with the defaults listed above. */
@@ -133,6 +134,34 @@ void mpr_default_options(mpr_options* opt);
  * ENOSAMPLES (no sample pair on the grid and at least one gap site). */
 mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask, const float* values,
                       const mpr_options* opt, mpr_ctx** out);
+
+/* ---- many fields in one context (the batched form) ----
+ * mpr_create_batch: n independent fields (time slices) of any sizes, each
+ * with its own mask and values (host or device pointers, row-major H_s*W_s;
+ * all grids[k].block equal), packed into one canvas of whole blocks so that
+ * every kernel launch of the context runs all of them: the calibration, each
+ * sweep's half-steps and stop test, the accumulation. No bond joins two
+ * fields; every field keeps its own transform range (Sec. 2.1), its own
+ * median for blocks without sample bonds (Sec. 2.2.2), its own stop
+ * bookkeeping, and its own random streams (key word 1 = seed_hi ^ (slice_id
+ * + k), site index within the field), so field k computes what mpr_create
+ * on it with slice_id + k computes. Canvas-level calls (state, stop,
+ * temperatures, block statistics) use the canvas layout given by
+ * mpr_get_slice_layout; mpr_predict writes the whole canvas (0 outside the
+ * fields). Errors: EINVAL (sizes, the canvas would exceed 32768 sites a side
+ * or 2^22 blocks), ENOSAMPLES (a field with gaps but no sample pair), ENOMEM,
+ * ECUDA. The persistent calibration (cal_mode 2) takes one field only.
+ * mpr_predict_batch: outs[k] (H_s*W_s floats, host or device) for every
+ *   field; truths: NULL or n pointers; aae_rase: NULL or 2n doubles (host),
+ *   AAE and RASE (Eqs. 3-4) of every field.
+ * mpr_get_slice_layout: rects[4n] (host) = (y0, x0, H_s, W_s) of every field
+ *   in the canvas. */
+mpr_status mpr_create_batch(int32_t n, const mpr_grid* grids, const uint8_t* const* masks,
+                            const float* const* values, const mpr_options* options,
+                            mpr_ctx** out);
+mpr_status mpr_predict_batch(mpr_ctx* ctx, float* const* outs, const float* const* truths,
+                             double* aae_rase);
+mpr_status mpr_get_slice_layout(const mpr_ctx* ctx, int32_t* rects);
 
 /* Releases every resource of ctx (NULL is a no-op). */
 void mpr_destroy(mpr_ctx* ctx);

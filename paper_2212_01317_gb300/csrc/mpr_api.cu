@@ -26,9 +26,23 @@ struct mpr_ctx {
     int device = 0, n_sm = 152;
     std::string err;
 
-    double zmin = 0, zmax = 0;
+    double zmin = 0, zmax = 0;   // slice 0
     int degenerate = 0;
+    // fields packed into the canvas (one for mpr_create)
+    int n_slices = 1;
+    std::vector<int4> h_rect;    // (y0, x0, H, W) per slice
+    std::vector<double> h_zmin, h_zmax;
+    std::vector<int32_t> h_degen;
+    int4* d_rect = nullptr;
+    int4* d_blk = nullptr;
+    int32_t* d_of_block = nullptr;
+    uint32_t* d_key1 = nullptr;
+    double* d_zmin = nullptr;
+    double* d_zmax = nullptr;
+    int32_t* d_degen = nullptr;
+    Slices sl{};
     int64_t n_gap[2] = {0, 0};
+    std::vector<int64_t> h_ngap;   // gap sites per slice
     int calibrated = 0;
 
     std::vector<void*> owned;  // every device allocation, freed at destroy
@@ -245,12 +259,12 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group, int storag
         TRY(dalloc(ctx, &ctx->sigma, blk_need));
         ctx->blk_cap = blk_need;
     }
-    if ((size_t)Rp > ctx->lane_cap) {
+    if ((size_t)Rp * ctx->n_slices > ctx->lane_cap) {
         dfree(ctx, ctx->tcount);
         ctx->tcount = nullptr;
         ctx->lane_cap = 0;
-        TRY(dalloc(ctx, &ctx->tcount, (size_t)Rp));
-        ctx->lane_cap = Rp;
+        TRY(dalloc(ctx, &ctx->tcount, (size_t)Rp * ctx->n_slices));
+        ctx->lane_cap = (size_t)Rp * ctx->n_slices;
     }
     const size_t work_need = (size_t)g.nblk * groups;
     if (work_need > ctx->work_cap) {
@@ -276,6 +290,7 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
     a.g = ctx->g;
     a.m = ctx->m;
     a.rng = ctx->rng;
+    a.sl = ctx->sl;
     a.colour = colour;
     a.list = ctx->list[colour];
     a.start = ctx->start[colour];
@@ -386,7 +401,7 @@ void collect_events(mpr_ctx* ctx) {
 mpr_status init_batch_state(mpr_ctx* ctx) {
     const int random = ctx->opt.init == MPR_INIT_RANDOM;
     for (int c = 0; c < 2; ++c) {
-        launch_init(ctx->g, ctx->list[c], ctx->n_gap[c], c, ctx->init_angle, ctx->ang,
+        launch_init(ctx->g, ctx->sl, ctx->list[c], ctx->n_gap[c], c, ctx->init_angle, ctx->ang,
                     ctx->storage, ctx->G, ctx->Rp, random, ctx->rng, ctx->r_even, ctx->s);
         CKL();
     }
@@ -395,9 +410,9 @@ mpr_status init_batch_state(mpr_ctx* ctx) {
 
 // After the running flags were overwritten: per-realization counts of running
 // targeted blocks and the worklist of items with a running lane.
-__global__ void k_rebuild(int nblk, int groups, int G, int Rp, const int32_t* Nsp,
-                          const uint8_t* running, int32_t* tcount, Control* ctl, uint32_t* work_all,
-                          uint32_t work_stride) {
+__global__ void k_rebuild(int nblk, int groups, int G, int Rp, const int32_t* of_block,
+                          const int32_t* Nsp, const uint8_t* running, int32_t* tcount, Control* ctl,
+                          uint32_t* work_all, uint32_t work_stride) {
     const int64_t n = (int64_t)nblk * groups;
     const uint32_t par = ctl->t & 1u;
     uint32_t* work = work_all + (size_t)par * work_stride;
@@ -409,7 +424,7 @@ __global__ void k_rebuild(int nblk, int groups, int G, int Rp, const int32_t* Ns
             const int r = grp * G + g;
             if (!running[(size_t)b * Rp + r]) continue;
             any = true;
-            if (Nsp[b] > 0) atomicAdd(&tcount[r], 1);
+            if (Nsp[b] > 0) atomicAdd(&tcount[of_block[b] * Rp + r], 1);
         }
         if (any) work[atomicAdd(&ctl->n_work[par], 1u)] = (uint32_t)it;
     }
@@ -428,13 +443,14 @@ __global__ void k_fill_valid(uint8_t* running, int64_t n, int Rp, int r_off, int
 mpr_status sweep_once(mpr_ctx* ctx) {
     const Geom& g = ctx->g;
     for (int c = 0; c < 2; ++c) TRY(halfstep_launch(ctx, sweep_args(ctx, c, true), true));
-    launch_stop_targeted(ctx->G, ctx->groups, ctx->Rp, stop_grid(ctx, ctx->G), ctx->ctl, ctx->work,
+    launch_stop_targeted(ctx->G, ctx->groups, ctx->Rp, ctx->d_of_block, stop_grid(ctx, ctx->G),
+                         ctx->ctl, ctx->work,
                          ctx->work_stride, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
                          ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
-    launch_stop_rest(g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, stop_grid(ctx, 1),
-                     ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp, ctx->running,
-                     ctx->stop, ctx->tcount, ctx->s);
+    launch_stop_rest(g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
+                     stop_grid(ctx, 1), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp,
+                     ctx->running, ctx->stop, ctx->tcount, ctx->s);
     CKL();
     ctx->t += 1;
     return MPR_OK;
@@ -519,14 +535,14 @@ mpr_status calibration_newton(mpr_ctx* ctx) {
     launch_newton_init(g.nblk, o.t_init, o.t_lo, o.t_hi, ctx->T, ctx->lo, ctx->hi, ctx->s);
     CKL();
     for (int k = 0; k < o.n_newton; ++k) {
-        launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);   // median, beta
+        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);   // median, beta
         CKL();
         TRY(moments_run(ctx, (uint32_t)(1 + k), k == 0, o.n_eq, o.n_meas));
         launch_newton_update(g.nblk, ctx->es, ctx->Nsp, ctx->Nb, ctx->mom, ctx->T, (double)o.t_lo,
                              (double)o.t_hi, ctx->s);
         CKL();
     }
-    launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+    launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
     CKL();
     return MPR_OK;
 }
@@ -537,7 +553,7 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     const mpr_options& o = ctx->opt;
     launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
     CKL();
-    launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+    launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
     CKL();
     TRY(init_batch_state(ctx));
     TRY(energy_pass(ctx));
@@ -778,22 +794,45 @@ void mpr_destroy(mpr_ctx* ctx) {
     delete ctx;
 }
 
-mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float* values_in,
-                      const mpr_options* opt_in, mpr_ctx** out) {
-    if (!out) return MPR_EINVAL;
-    *out = nullptr;
-    if (!grid || !mask_in || !values_in) return MPR_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// Canvas mask: 1 gap / 0 sample inside every slice's field (any nonzero
+// input is a gap), 2 everywhere else.
+__global__ void k_mask_normalize(Geom g, Slices sl, uint8_t* __restrict__ mask) {
+    const int64_t n = (int64_t)g.H * g.W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / g.W), x = (int)(i % g.W);
+        const int s = sl.of_block[(y / g.lb) * g.nbx + x / g.lb];
+        bool inside = false;
+        if (s >= 0) {
+            const int4 rc = sl.rect[s];
+            inside = y < rc.x + rc.z && x < rc.y + rc.w;
+        }
+        mask[i] = inside ? (mask[i] != 0 ? MASK_GAP : 0) : MASK_ABSENT;
+    }
+}
+
+struct SliceDesc {
+    int y0, x0, H, W;
+};
+
+// Allocation, slice tables, transform, Eq. 2 statistics and gap lists of a
+// canvas holding `desc` fields; `upload` copies the inputs into ctx->values
+// and ctx->mask (canvas layout; mask is normalised afterwards).
+template <class Upload>
+mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
+                       const std::vector<SliceDesc>& desc, Upload upload, mpr_ctx** out) {
     mpr_ctx* ctx = new (std::nothrow) mpr_ctx();
     if (!ctx) return MPR_ENOMEM;
     auto bail = [&](mpr_status st) {
-        // Keep the context only for its error message when the caller asked
-        // for nothing else; otherwise release it.
         mpr_destroy(ctx);
         return st;
     };
     if (opt_in) ctx->opt = *opt_in; else mpr_default_options(&ctx->opt);
     if (check_opts(ctx, ctx->opt) != MPR_OK) return bail(MPR_EINVAL);
-    const int H = grid->height, W = grid->width, lb = grid->block;
     if (H < 1 || W < 1 || H > MAX_SIDE || W > MAX_SIDE || lb < 1) return bail(MPR_EINVAL);
     Geom& g = ctx->g;
     g.H = H;
@@ -804,6 +843,8 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     g.nby = (H + lb - 1) / lb;
     if ((int64_t)g.nbx * g.nby > MAX_BLOCKS) return bail(MPR_EINVAL);
     g.nblk = g.nbx * g.nby;
+    const int ns = (int)desc.size();
+    ctx->n_slices = ns;
     ctx->m.q = (float)ctx->opt.q;
     ctx->m.J = (float)ctx->opt.J;
     ctx->m.inv_q = (float)(1.0 / ctx->opt.q);
@@ -849,46 +890,87 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
     ST(dalloc(ctx, &ctx->split[0], g.nblk));
     ST(dalloc(ctx, &ctx->split[1], g.nblk));
     ST(dalloc(ctx, &ctx->counters, 4));
-    ST(dalloc(ctx, &ctx->mm, 2));
-    ST(dalloc(ctx, &ctx->err_buf, 2));
+    ST(dalloc(ctx, &ctx->mm, 2 * (size_t)ns));
+    ST(dalloc(ctx, &ctx->err_buf, 2 * (size_t)ns));
     ST(dalloc(ctx, &ctx->ctl, 1));
     ST(dalloc(ctx, &ctx->bar, 1));
     ST(dalloc(ctx, &ctx->med, 1));
+    ST(dalloc(ctx, &ctx->d_rect, ns));
+    ST(dalloc(ctx, &ctx->d_blk, ns));
+    ST(dalloc(ctx, &ctx->d_of_block, g.nblk));
+    ST(dalloc(ctx, &ctx->d_key1, ns));
+    ST(dalloc(ctx, &ctx->d_zmin, ns));
+    ST(dalloc(ctx, &ctx->d_zmax, ns));
+    ST(dalloc(ctx, &ctx->d_degen, ns));
     cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, ctx->device);
     if (cudaMallocHost(&ctx->h_counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_ctl, sizeof(Control)) != cudaSuccess)
         return bail(MPR_ENOMEM);
 
-    if (copy_in(ctx, ctx->values, values_in, n * sizeof(float)) != MPR_OK) return bail(MPR_ECUDA);
-    if (copy_in(ctx, ctx->mask, mask_in, n) != MPR_OK) return bail(MPR_ECUDA);
-    // z_min / z_max over the samples.
+    // Slice tables: rectangles, block rectangles, slice of every block, keys.
+    std::vector<int4> rect(ns), blk(ns);
+    std::vector<int32_t> of_block(g.nblk, -1);
+    std::vector<uint32_t> key1(ns);
+    for (int k = 0; k < ns; ++k) {
+        const SliceDesc& d = desc[k];
+        rect[k] = make_int4(d.y0, d.x0, d.H, d.W);
+        const int by0 = d.y0 / lb, bx0 = d.x0 / lb;
+        const int nby = (d.H + lb - 1) / lb, nbx = (d.W + lb - 1) / lb;
+        blk[k] = make_int4(by0, bx0, nby, nbx);
+        for (int by = by0; by < by0 + nby; ++by)
+            for (int bx = bx0; bx < bx0 + nbx; ++bx) of_block[(size_t)by * g.nbx + bx] = k;
+        key1[k] = (uint32_t)(ctx->opt.seed >> 32) ^ (ctx->opt.slice_id + (uint32_t)k);
+    }
+    ctx->h_rect = rect;
+    if (cudaMemcpyAsync(ctx->d_rect, rect.data(), ns * sizeof(int4), cudaMemcpyHostToDevice, ctx->s) ||
+        cudaMemcpyAsync(ctx->d_blk, blk.data(), ns * sizeof(int4), cudaMemcpyHostToDevice, ctx->s) ||
+        cudaMemcpyAsync(ctx->d_of_block, of_block.data(), g.nblk * 4, cudaMemcpyHostToDevice,
+                        ctx->s) ||
+        cudaMemcpyAsync(ctx->d_key1, key1.data(), ns * 4, cudaMemcpyHostToDevice, ctx->s))
+        return bail(MPR_ECUDA);
+    ctx->sl = Slices{ns,          ctx->d_rect, ctx->d_blk, ctx->d_of_block, ctx->d_key1,
+                     ctx->d_zmin, ctx->d_zmax, ctx->d_degen};
+
+    if (upload(ctx) != MPR_OK) return bail(MPR_ECUDA);
+    k_mask_normalize<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
+        g, ctx->sl, ctx->mask);
+    ++ctx->launches;
+    // z_min / z_max over the samples of every slice.
     {
-        uint32_t mm_init[2] = {0xffffffffu, 0u};
-        if (cudaMemcpyAsync(ctx->mm, mm_init, sizeof(mm_init), cudaMemcpyHostToDevice, ctx->s) !=
+        std::vector<uint32_t> mm(2 * (size_t)ns);
+        for (int k = 0; k < ns; ++k) { mm[2 * k] = 0xffffffffu; mm[2 * k + 1] = 0u; }
+        if (cudaMemcpyAsync(ctx->mm, mm.data(), mm.size() * 4, cudaMemcpyHostToDevice, ctx->s) !=
             cudaSuccess)
             return bail(MPR_ECUDA);
-        launch_minmax(ctx->values, ctx->mask, n, ctx->mm, ctx->s);
+        launch_minmax(g, ctx->d_of_block, ctx->values, ctx->mask, ctx->mm, ctx->s);
         ++ctx->launches;
-        uint32_t hmm[2];
-        if (cudaMemcpyAsync(hmm, ctx->mm, sizeof(hmm), cudaMemcpyDeviceToHost, ctx->s) !=
+        if (cudaMemcpyAsync(mm.data(), ctx->mm, mm.size() * 4, cudaMemcpyDeviceToHost, ctx->s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(ctx->s) != cudaSuccess)
             return bail(MPR_ECUDA);
-        if (hmm[0] == 0xffffffffu) {
-            // no sample at all
-            ctx->zmin = ctx->zmax = 0.0;
-            ctx->degenerate = 1;
-        } else {
-            ctx->zmin = (double)ord2f(hmm[0]);
-            ctx->zmax = (double)ord2f(hmm[1]);
-            ctx->degenerate = !(ctx->zmax > ctx->zmin);
+        ctx->h_zmin.assign(ns, 0.0);
+        ctx->h_zmax.assign(ns, 0.0);
+        ctx->h_degen.assign(ns, 1);
+        for (int k = 0; k < ns; ++k) {
+            if (mm[2 * k] == 0xffffffffu) continue;   // no sample in the slice
+            ctx->h_zmin[k] = (double)ord2f(mm[2 * k]);
+            ctx->h_zmax[k] = (double)ord2f(mm[2 * k + 1]);
+            ctx->h_degen[k] = !(ctx->h_zmax[k] > ctx->h_zmin[k]);
         }
+        ctx->zmin = ctx->h_zmin[0];
+        ctx->zmax = ctx->h_zmax[0];
+        ctx->degenerate = 1;     // every slice constant: nothing to calibrate
+        for (int k = 0; k < ns; ++k) ctx->degenerate &= ctx->h_degen[k];
+        if (cudaMemcpyAsync(ctx->d_zmin, ctx->h_zmin.data(), ns * 8, cudaMemcpyHostToDevice, ctx->s) ||
+            cudaMemcpyAsync(ctx->d_zmax, ctx->h_zmax.data(), ns * 8, cudaMemcpyHostToDevice, ctx->s) ||
+            cudaMemcpyAsync(ctx->d_degen, ctx->h_degen.data(), ns * 4, cudaMemcpyHostToDevice,
+                            ctx->s))
+            return bail(MPR_ECUDA);
     }
-    launch_layout(g, ctx->values, ctx->mask, ctx->zmin, ctx->zmax, ctx->degenerate, ctx->dang,
-                  ctx->s);
-    launch_block_stats(g, ctx->values, ctx->mask, ctx->zmin, ctx->zmax, ctx->degenerate,
-                       ctx->opt.q, ctx->opt.J, ctx->Es, ctx->Nsp, ctx->Nb, ctx->ssum, ctx->nsamp,
-                       ctx->ngap_c[0], ctx->ngap_c[1], ctx->s);
+    launch_layout(g, ctx->sl, ctx->values, ctx->mask, ctx->dang, ctx->s);
+    launch_block_stats(g, ctx->sl, ctx->values, ctx->mask, ctx->opt.q, ctx->opt.J, ctx->Es,
+                       ctx->Nsp, ctx->Nb, ctx->ssum, ctx->nsamp, ctx->ngap_c[0], ctx->ngap_c[1],
+                       ctx->s);
     launch_scan(ctx->ngap_c[0], g.nblk, ctx->start[0], ctx->s);
     launch_scan(ctx->ngap_c[1], g.nblk, ctx->start[1], ctx->s);
     ctx->launches += 4;
@@ -911,27 +993,36 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
         return bail(MPR_ECUDA);
     ctx->n_gap[0] = s0[g.nblk];
     ctx->n_gap[1] = s1[g.nblk];
-    int64_t pairs = 0, samples = 0;
-    double gsum = 0.0;
-    std::vector<float> init(g.nblk);
+    // Per slice: sample pairs (Eq. 2 needs one), gap sites, global sample mean.
+    std::vector<int64_t> pairs(ns, 0), samples(ns, 0);
+    std::vector<double> gsum(ns, 0.0);
+    ctx->h_ngap.assign(ns, 0);
+    std::vector<float> init(g.nblk, 0.0f);
     std::vector<int32_t> ng(g.nblk);
     for (int b = 0; b < g.nblk; ++b) {
-        pairs += nsp[b];
-        samples += nsm[b];
-        gsum += ssum[b];
         ng[b] = ng0[b] + ng1[b];
+        const int k = of_block[b];
+        if (k < 0) continue;
+        pairs[k] += nsp[b];
+        samples[k] += nsm[b];
+        gsum[k] += ssum[b];
+        ctx->h_ngap[k] += ng[b];
     }
-    const double gmean = samples ? gsum / (double)samples : 0.0;
-    for (int b = 0; b < g.nblk; ++b)
+    for (int k = 0; k < ns; ++k)
+        if (pairs[k] == 0 && ctx->h_ngap[k] > 0) {
+            mpr_destroy(ctx);
+            return MPR_ENOSAMPLES;
+        }
+    for (int b = 0; b < g.nblk; ++b) {
+        const int k = of_block[b];
+        if (k < 0) continue;
+        const double gmean = samples[k] ? gsum[k] / (double)samples[k] : 0.0;
         init[b] = (float)(nsm[b] > 0 ? ssum[b] / (double)nsm[b] : gmean);
+    }
     std::vector<double> es_h(g.nblk), inb_h(g.nblk);
     for (int b = 0; b < g.nblk; ++b) {
         es_h[b] = nsp[b] > 0 ? esv[b] / (double)nsp[b] : 0.0;
         inb_h[b] = nbv[b] > 0 ? 1.0 / (double)nbv[b] : 0.0;
-    }
-    if (pairs == 0 && ctx->n_gap[0] + ctx->n_gap[1] > 0) {
-        mpr_destroy(ctx);
-        return MPR_ENOSAMPLES;
     }
     ST(dalloc(ctx, &ctx->list[0], ctx->n_gap[0]));
     ST(dalloc(ctx, &ctx->list[1], ctx->n_gap[1]));
@@ -940,8 +1031,8 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
         cudaMemcpyAsync(ctx->inb, inb_h.data(), g.nblk * 8, cudaMemcpyHostToDevice, ctx->s) ||
         cudaMemcpyAsync(ctx->ngap, ng.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s))
         return bail(MPR_ECUDA);
-    launch_build_lists(g, ctx->mask, ctx->start[0], ctx->start[1], ctx->list[0], ctx->list[1],
-                       ctx->split[0], ctx->split[1], ctx->s);
+    launch_build_lists(g, ctx->d_of_block, ctx->mask, ctx->start[0], ctx->start[1], ctx->list[0],
+                       ctx->list[1], ctx->split[0], ctx->split[1], ctx->s);
     ++ctx->launches;
     if (cudaMemsetAsync(ctx->sum, 0, 2 * plane * sizeof(double), ctx->s) ||
         cudaMemsetAsync(ctx->ctl, 0, sizeof(Control), ctx->s) ||
@@ -951,6 +1042,88 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
 #undef ST
     *out = ctx;
     return MPR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float* values_in,
+                      const mpr_options* opt_in, mpr_ctx** out) {
+    if (!out) return MPR_EINVAL;
+    *out = nullptr;
+    if (!grid || !mask_in || !values_in) return MPR_EINVAL;
+    const int H = grid->height, W = grid->width;
+    if (H < 1 || W < 1 || H > MAX_SIDE || W > MAX_SIDE || grid->block < 1) return MPR_EINVAL;
+    const size_t n = (size_t)H * W;
+    auto upload = [&](mpr_ctx* ctx) -> mpr_status {
+        if (copy_in(ctx, ctx->values, values_in, n * sizeof(float)) != MPR_OK) return MPR_ECUDA;
+        return copy_in(ctx, ctx->mask, mask_in, n);
+    };
+    return create_impl(opt_in, H, W, grid->block, {SliceDesc{0, 0, H, W}}, upload, out);
+}
+
+mpr_status mpr_create_batch(int32_t n, const mpr_grid* grids, const uint8_t* const* masks,
+                            const float* const* values, const mpr_options* opt_in,
+                            mpr_ctx** out) {
+    if (!out) return MPR_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !grids || !masks || !values) return MPR_EINVAL;
+    const int lb = grids[0].block;
+    if (lb < 1) return MPR_EINVAL;
+    for (int k = 0; k < n; ++k)
+        if (grids[k].block != lb || grids[k].height < 1 || grids[k].width < 1 ||
+            grids[k].height > MAX_SIDE || grids[k].width > MAX_SIDE || !masks[k] || !values[k])
+            return MPR_EINVAL;
+    // Shelf packing on a grid of L x L cells, L = l_b (2 l_b if l_b is odd,
+    // so that every slice origin has y0 + x0 even): slices sorted by height,
+    // placed left to right, a new shelf when the row is full.
+    const int L = (lb % 2 == 0) ? lb : 2 * lb;
+    auto up = [&](int v) { return (v + L - 1) / L * L; };
+    std::vector<int> order(n);
+    int64_t area = 0;
+    int wmax = 0;
+    for (int k = 0; k < n; ++k) {
+        order[k] = k;
+        area += (int64_t)up(grids[k].height) * up(grids[k].width);
+        wmax = std::max(wmax, up(grids[k].width));
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return grids[a].height > grids[b].height; });
+    const int Wc = std::max(wmax, up((int)std::ceil(std::sqrt((double)area))));
+    std::vector<SliceDesc> desc(n);
+    int x = 0, y = 0, shelf = 0;
+    for (int k : order) {
+        const int hp = up(grids[k].height), wp = up(grids[k].width);
+        if (x + wp > Wc) {
+            y += shelf;
+            x = 0;
+            shelf = 0;
+        }
+        desc[k] = SliceDesc{y, x, grids[k].height, grids[k].width};
+        x += wp;
+        shelf = std::max(shelf, hp);
+    }
+    const int Hc = y + shelf;
+    if (Hc > MAX_SIDE || Wc > MAX_SIDE) return MPR_EINVAL;
+    auto upload = [&](mpr_ctx* ctx) -> mpr_status {
+        const size_t nc = (size_t)ctx->g.H * ctx->g.W;
+        if (cudaMemsetAsync(ctx->mask, 0, nc, ctx->s) != cudaSuccess ||
+            cudaMemsetAsync(ctx->values, 0, nc * sizeof(float), ctx->s) != cudaSuccess)
+            return MPR_ECUDA;
+        for (int k = 0; k < n; ++k) {
+            const SliceDesc& d = desc[k];
+            const size_t off = (size_t)d.y0 * ctx->g.W + d.x0;
+            if (cudaMemcpy2DAsync(ctx->values + off, (size_t)ctx->g.W * sizeof(float), values[k],
+                                  (size_t)d.W * sizeof(float), (size_t)d.W * sizeof(float), d.H,
+                                  cudaMemcpyDefault, ctx->s) != cudaSuccess ||
+                cudaMemcpy2DAsync(ctx->mask + off, (size_t)ctx->g.W, masks[k], (size_t)d.W,
+                                  (size_t)d.W, d.H, cudaMemcpyDefault, ctx->s) != cudaSuccess)
+                return MPR_ECUDA;
+        }
+        return MPR_OK;
+    };
+    return create_impl(opt_in, Hc, Wc, lb, desc, upload, out);
 }
 
 mpr_status mpr_get_info(const mpr_ctx* ctx, mpr_info* info) {
@@ -975,6 +1148,7 @@ mpr_status mpr_get_info(const mpr_ctx* ctx, mpr_info* info) {
     info->gap_updates = ctx->gap_updates;
     info->cal_gap_updates = ctx->cal_updates;
     info->device_bytes = ctx->device_bytes;
+    info->n_slices = ctx->n_slices;
     return MPR_OK;
 }
 
@@ -1071,6 +1245,8 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     CKL();
     // auto and 1: graph; 2: persistent; 3: a launch per kernel from the host.
     bool fallback = o.cal_mode != 2;
+    if (!fallback && ctx->n_slices > 1)
+        return fail(ctx, MPR_EINVAL, "the persistent calibration (cal_mode 2) takes one field");
     if (!fallback) {
         TRY(calibration_persistent(ctx, inv_count, &fallback));
         if (fallback && o.cal_mode == 2)
@@ -1084,7 +1260,7 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
         }
         launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
         CKL();
-        launch_cal_fill(g.nblk, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
         CKL();
     }
     ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains *
@@ -1118,16 +1294,17 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
                         ctx->s);
     CKL();
     TRY(init_batch_state(ctx));
-    CK(cudaMemsetAsync(ctx->tcount, 0, ctx->Rp * sizeof(int32_t), ctx->s));
+    CK(cudaMemsetAsync(ctx->tcount, 0, (size_t)ctx->Rp * ctx->n_slices * sizeof(int32_t), ctx->s));
     // E_b(0): bond energies of the initial state (no moves), t = 0 stops,
     // worklist of the first sweep.
     TRY(energy_pass(ctx));
-    launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->es, ctx->inb, ctx->Nsp, ctx->ngap, ctx->ecur,
+    launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->d_of_block, ctx->es, ctx->inb, ctx->Nsp, ctx->ngap,
+                     ctx->ecur,
                      ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
-    launch_stop_rest(ctx->g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, stop_grid(ctx, 1),
-                     ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp, ctx->running,
-                     ctx->stop, ctx->tcount, ctx->s);
+    launch_stop_rest(ctx->g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
+                     stop_grid(ctx, 1), ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp,
+                     ctx->running, ctx->stop, ctx->tcount, ctx->s);
     CKL();
     ctx->energy_dirty = false;
     ctx->batch_open = 1;
@@ -1321,15 +1498,15 @@ mpr_status mpr_set_running(mpr_ctx* ctx, const uint8_t* running) {
         for (int b = 0; b < nb; ++b)
             hr[(size_t)b * ctx->Rp + r + ctx->r_off] = in[(size_t)r * nb + b] ? 1 : 0;
     CK(cudaMemcpyAsync(ctx->running, hr.data(), hr.size(), cudaMemcpyHostToDevice, ctx->s));
-    CK(cudaMemsetAsync(ctx->tcount, 0, ctx->Rp * sizeof(int32_t), ctx->s));
+    CK(cudaMemsetAsync(ctx->tcount, 0, (size_t)ctx->Rp * ctx->n_slices * sizeof(int32_t), ctx->s));
     CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     const uint32_t par = ctx->h_ctl->t & 1u;
     CK(cudaMemsetAsync(&ctx->ctl->n_work[par], 0, sizeof(uint32_t), ctx->s));
     const int64_t items = (int64_t)nb * ctx->groups;
     k_rebuild<<<(int)std::min<int64_t>((items + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
-        nb, ctx->groups, ctx->G, ctx->Rp, ctx->Nsp, ctx->running, ctx->tcount, ctx->ctl, ctx->work,
-        ctx->work_stride);
+        nb, ctx->groups, ctx->G, ctx->Rp, ctx->d_of_block, ctx->Nsp, ctx->running, ctx->tcount,
+        ctx->ctl, ctx->work, ctx->work_stride);
     ctx->bound = ~0ull;
     CKL();
     CK(cudaStreamSynchronize(ctx->s));
@@ -1343,7 +1520,8 @@ mpr_status mpr_block_energy(mpr_ctx* ctx, int32_t r, double* E) {
     if (r < 0 || r >= ctx->R) return fail(ctx, MPR_EINVAL, "r out of range");
     double* d = nullptr;
     TRY(dalloc(ctx, &d, ctx->g.nblk));
-    launch_block_energy(ctx->g, ctx->mask, ctx->dang, ctx->ang, ctx->storage, ctx->G,
+    launch_block_energy(ctx->g, ctx->d_of_block, ctx->mask, ctx->dang, ctx->ang, ctx->storage,
+                        ctx->G,
                         r + ctx->r_off, ctx->opt.q, ctx->opt.J, d, ctx->s);
     mpr_status st = MPR_OK;
     if (cudaPeekAtLastError() != cudaSuccess) st = fail(ctx, MPR_ECUDA, "block energy launch failed");
@@ -1372,7 +1550,7 @@ mpr_status mpr_smooth_temperatures(mpr_ctx* ctx, int32_t r_s, int32_t n_s, float
     double *Ts = nullptr, *tmp = nullptr;
     CK(cudaMallocAsync((void**)&Ts, n * sizeof(double), ctx->s));
     CK(cudaMallocAsync((void**)&tmp, n * sizeof(double), ctx->s));
-    launch_sst(ctx->g, ctx->T, r_s, n_s, Ts, tmp, ctx->T_site, ctx->beta_site, ctx->s);
+    launch_sst(ctx->g, ctx->sl, ctx->T, r_s, n_s, Ts, tmp, ctx->T_site, ctx->beta_site, ctx->s);
     ctx->launches += 2 + 2 * n_s;
     const cudaError_t e = cudaPeekAtLastError();
     cudaFreeAsync(Ts, ctx->s);
@@ -1511,31 +1689,89 @@ mpr_status mpr_set_accumulator(mpr_ctx* ctx, const double* sum_in, int64_t n_rea
     return st;
 }
 
-mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae_rase) {
-    if (!ctx || !out) return MPR_EINVAL;
-    ctx->err.clear();
+// Predictions of the whole canvas into ctx->out_buf; with a truth canvas in
+// ctx->truth_buf the per-slice error sums land in ctx->err_buf.
+mpr_status predict_canvas(mpr_ctx* ctx, bool with_truth) {
     const int64_t total_gap = ctx->n_gap[0] + ctx->n_gap[1];
     if (ctx->realizations == 0 && total_gap > 0)
         return fail(ctx, MPR_ESTATE, "no realization accumulated (mpr_simulate)");
     const size_t n = (size_t)ctx->g.H * ctx->g.W;
     if (!ctx->out_buf) TRY(dalloc(ctx, &ctx->out_buf, n));
-    const float* tr = nullptr;
+    if (with_truth)
+        CK(cudaMemsetAsync(ctx->err_buf, 0, 2 * (size_t)ctx->n_slices * sizeof(double), ctx->s));
+    const double inv_r = ctx->realizations > 0 ? 1.0 / (double)ctx->realizations : 0.0;
+    launch_predict(ctx->g, ctx->sl, ctx->values, ctx->mask, ctx->sum, inv_r, ctx->out_buf,
+                   with_truth ? ctx->truth_buf : nullptr, ctx->err_buf, ctx->s);
+    CKL();
+    return MPR_OK;
+}
+
+mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae_rase) {
+    if (!ctx || !out) return MPR_EINVAL;
+    ctx->err.clear();
+    const size_t n = (size_t)ctx->g.H * ctx->g.W;
     if (truth) {
         if (!ctx->truth_buf) TRY(dalloc(ctx, &ctx->truth_buf, n));
         TRY(copy_in(ctx, ctx->truth_buf, truth, n * 4));
-        tr = ctx->truth_buf;
-        CK(cudaMemsetAsync(ctx->err_buf, 0, 2 * sizeof(double), ctx->s));
     }
-    const double inv_r = ctx->realizations > 0 ? 1.0 / (double)ctx->realizations : 0.0;
-    launch_predict(ctx->g, ctx->values, ctx->mask, ctx->sum, inv_r, ctx->zmin, ctx->zmax,
-                   ctx->out_buf, tr, ctx->err_buf, ctx->s);
-    CKL();
+    TRY(predict_canvas(ctx, truth != nullptr));
     TRY(copy_out(ctx, out, ctx->out_buf, n * 4));
     if (truth && aae_rase) {
-        double h[2];
-        TRY(copy_out(ctx, h, ctx->err_buf, sizeof(h)));
-        aae_rase[0] = total_gap ? h[0] / (double)total_gap : 0.0;
-        aae_rase[1] = total_gap ? std::sqrt(h[1] / (double)total_gap) : 0.0;
+        std::vector<double> h(2 * (size_t)ctx->n_slices);
+        TRY(copy_out(ctx, h.data(), ctx->err_buf, h.size() * 8));
+        double a = 0.0, r = 0.0;
+        for (int k = 0; k < ctx->n_slices; ++k) { a += h[2 * k]; r += h[2 * k + 1]; }
+        const int64_t total_gap = ctx->n_gap[0] + ctx->n_gap[1];
+        aae_rase[0] = total_gap ? a / (double)total_gap : 0.0;
+        aae_rase[1] = total_gap ? std::sqrt(r / (double)total_gap) : 0.0;
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_predict_batch(mpr_ctx* ctx, float* const* outs, const float* const* truths,
+                             double* aae_rase) {
+    if (!ctx || !outs) return MPR_EINVAL;
+    ctx->err.clear();
+    const Geom& g = ctx->g;
+    const size_t n = (size_t)g.H * g.W;
+    for (int k = 0; k < ctx->n_slices; ++k)
+        if (!outs[k] || (truths && !truths[k])) return fail(ctx, MPR_EINVAL, "NULL slice pointer");
+    if (truths) {
+        if (!ctx->truth_buf) TRY(dalloc(ctx, &ctx->truth_buf, n));
+        CK(cudaMemsetAsync(ctx->truth_buf, 0, n * 4, ctx->s));
+        for (int k = 0; k < ctx->n_slices; ++k) {
+            const int4 rc = ctx->h_rect[k];
+            CK(cudaMemcpy2DAsync(ctx->truth_buf + (size_t)rc.x * g.W + rc.y, (size_t)g.W * 4,
+                                 truths[k], (size_t)rc.w * 4, (size_t)rc.w * 4, rc.z,
+                                 cudaMemcpyDefault, ctx->s));
+        }
+    }
+    TRY(predict_canvas(ctx, truths != nullptr));
+    for (int k = 0; k < ctx->n_slices; ++k) {
+        const int4 rc = ctx->h_rect[k];
+        CK(cudaMemcpy2DAsync(outs[k], (size_t)rc.w * 4, ctx->out_buf + (size_t)rc.x * g.W + rc.y,
+                             (size_t)g.W * 4, (size_t)rc.w * 4, rc.z, cudaMemcpyDefault, ctx->s));
+    }
+    CK(cudaStreamSynchronize(ctx->s));
+    if (truths && aae_rase) {
+        std::vector<double> h(2 * (size_t)ctx->n_slices);
+        TRY(copy_out(ctx, h.data(), ctx->err_buf, h.size() * 8));
+        for (int k = 0; k < ctx->n_slices; ++k) {
+            const int64_t ng = ctx->h_ngap[k];
+            aae_rase[2 * k] = ng ? h[2 * k] / (double)ng : 0.0;
+            aae_rase[2 * k + 1] = ng ? std::sqrt(h[2 * k + 1] / (double)ng) : 0.0;
+        }
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_get_slice_layout(const mpr_ctx* ctx, int32_t* rects) {
+    if (!ctx || !rects) return MPR_EINVAL;
+    for (int k = 0; k < ctx->n_slices; ++k) {
+        rects[4 * k] = ctx->h_rect[k].x;
+        rects[4 * k + 1] = ctx->h_rect[k].y;
+        rects[4 * k + 2] = ctx->h_rect[k].z;
+        rects[4 * k + 3] = ctx->h_rect[k].w;
     }
     return MPR_OK;
 }

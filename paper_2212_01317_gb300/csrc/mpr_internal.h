@@ -15,6 +15,8 @@
 //   running[nblk][Rp] uint8   1 while block b of realization r still sweeps
 // Wh = ceil(W/2); site (y,x) of colour c = (x+y)&1 sits at half index x >> 1.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace mpr {
@@ -44,6 +46,34 @@ struct Rng {
     uint32_t key0, key1;
 };
 
+// Mask values of the canvas: 0 sample, 1 gap (prediction site), 2 absent
+// (no site: the padding between the fields packed into one canvas).
+constexpr uint8_t MASK_GAP = 1;
+constexpr uint8_t MASK_ABSENT = 2;
+
+// Independent fields (slices) packed into one canvas. A slice occupies a
+// rectangle of whole blocks whose origin has y0 + x0 even (so a site's
+// checkerboard colour is the same in the canvas and in its own field); the
+// sites of the rectangle outside the field are absent. No bond joins two
+// slices. Every slice keeps its own transform range, random-stream key and
+// site numbering, so a slice of a batch computes what its field computes
+// alone. A single field is the one-slice case.
+struct Slices {
+    int n;
+    const int4* rect;          // [n] (y0, x0, H_s, W_s): the field's sites in the canvas
+    const int4* blk;           // [n] (by0, bx0, nby_s, nbx_s): the slice's blocks
+    const int32_t* of_block;   // [nblk] slice of every block, -1 for padding blocks
+    const uint32_t* key1;      // [n] Philox key word 1 (seed_hi ^ slice id)
+    const double* zmin;        // [n] Sec. 2.1 range over the slice's samples
+    const double* zmax;        // [n]
+    const int32_t* degenerate; // [n] 1: z_max == z_min
+};
+
+// Philox counter word 0 of a site: its index within its own field.
+__host__ __device__ inline uint32_t local_index(const int4& rc, int y, int x) {
+    return (uint32_t)(y - rc.x) * (uint32_t)rc.w + (uint32_t)(x - rc.y);
+}
+
 struct Model {
     float q, J, inv_q;
     int overrelax;
@@ -70,7 +100,8 @@ struct Control {
 struct SweepArgs {
     Geom g;
     Model m;
-    Rng rng;
+    Rng rng;                  // key0 (seed_lo); key1 comes from the slice table
+    Slices sl;
     int colour;
     const uint2* list;        // gap entries of this colour
     const int32_t* start;     // [nblk + 1]

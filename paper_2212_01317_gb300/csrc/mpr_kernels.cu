@@ -42,8 +42,9 @@ float ord2f(uint32_t u) {
 
 // ---------------------------------------------------------------- setup --
 // z_min / z_max over the samples (Sec. 2.1: only the samples are known).
-__global__ void k_minmax(const float* __restrict__ values, const uint8_t* __restrict__ mask,
-                         int64_t n, uint32_t* __restrict__ mm) {
+// z_min / z_max over the samples of one field (mask != 0: gap), into mm[0..1].
+__global__ void k_minmax_field(const float* __restrict__ values, const uint8_t* __restrict__ mask,
+                               int64_t n, uint32_t* __restrict__ mm) {
     uint32_t lo = 0xffffffffu, hi = 0u;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -62,9 +63,26 @@ __global__ void k_minmax(const float* __restrict__ values, const uint8_t* __rest
     }
 }
 
+// z_min / z_max over the samples of every slice (Sec. 2.1: only the samples
+// are known): mm[2 s], mm[2 s + 1] as order-preserving integers.
+__global__ void k_minmax(Geom g, const int32_t* __restrict__ of_block,
+                         const float* __restrict__ values, const uint8_t* __restrict__ mask,
+                         uint32_t* __restrict__ mm) {
+    const int64_t n = (int64_t)g.H * g.W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (mask[i]) continue;
+        const int y = (int)(i / g.W), x = (int)(i % g.W);
+        const int s = of_block[(y / g.lb) * g.nbx + x / g.lb];
+        const uint32_t o = f2ord(values[i]);
+        atomicMin(&mm[2 * s], o);
+        atomicMax(&mm[2 * s + 1], o);
+    }
+}
+
 // Sample angles per checkerboard colour (Sec. 2.1 transform).
-__global__ void k_layout(Geom g, const float* __restrict__ values, const uint8_t* __restrict__ mask,
-                         double zmin, double zmax, int degenerate, float* __restrict__ dang) {
+__global__ void k_layout(Geom g, Slices sl, const float* __restrict__ values,
+                         const uint8_t* __restrict__ mask, float* __restrict__ dang) {
     const int64_t n = (int64_t)g.H * g.W;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -75,21 +93,23 @@ __global__ void k_layout(Geom g, const float* __restrict__ values, const uint8_t
             dang[h] = 0.0f;
             continue;
         }
-        const double phi = degenerate ? 0.0
-                                      : 6.283185307179586476925 * ((double)values[i] - zmin) /
-                                            (zmax - zmin);
+        const int s = sl.of_block[(y / g.lb) * g.nbx + x / g.lb];
+        const double zmin = sl.zmin[s], zmax = sl.zmax[s];
+        const double phi = sl.degenerate[s] ? 0.0
+                                            : 6.283185307179586476925 * ((double)values[i] - zmin) /
+                                                  (zmax - zmin);
         dang[h] = (float)phi;
     }
 }
 
 // One warp per block: Eq. 2 over the owned sample-sample bonds (FP64), bond
 // counts, sample mean angle, gap counts per colour.
-__global__ void k_block_stats(Geom g, const float* __restrict__ values,
-                              const uint8_t* __restrict__ mask, double zmin, double zmax,
-                              int degenerate, double q, double J, double* __restrict__ Es,
-                              int32_t* __restrict__ Nsp, int32_t* __restrict__ Nb,
-                              double* __restrict__ ssum, int32_t* __restrict__ nsamp,
-                              int32_t* __restrict__ ngap0, int32_t* __restrict__ ngap1) {
+__global__ void k_block_stats(Geom g, Slices sl, const float* __restrict__ values,
+                              const uint8_t* __restrict__ mask, double q, double J,
+                              double* __restrict__ Es, int32_t* __restrict__ Nsp,
+                              int32_t* __restrict__ Nb, double* __restrict__ ssum,
+                              int32_t* __restrict__ nsamp, int32_t* __restrict__ ngap0,
+                              int32_t* __restrict__ ngap1) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= g.nblk) return;
@@ -97,13 +117,20 @@ __global__ void k_block_stats(Geom g, const float* __restrict__ values,
     const int y0 = by * g.lb, x0 = bx * g.lb;
     const int y1 = min(g.H, y0 + g.lb), x1 = min(g.W, x0 + g.lb);
     const int bw = x1 - x0, nsite = (y1 - y0) * bw;
-    const double scale = degenerate ? 0.0 : 6.283185307179586476925 / (zmax - zmin);
+    const int s = sl.of_block[warp];
+    const double zmin = s >= 0 ? sl.zmin[s] : 0.0, zmax = s >= 0 ? sl.zmax[s] : 1.0;
+    const double scale = (s < 0 || sl.degenerate[s]) ? 0.0 : 6.283185307179586476925 / (zmax - zmin);
+    // A bond to the right / down neighbour exists when that site is present
+    // and in the same slice (blocks never straddle slices).
+    const bool right_ok = x1 < g.W && bx + 1 < g.nbx && sl.of_block[warp + 1] == s;
+    const bool down_ok = y1 < g.H && by + 1 < g.nby && sl.of_block[warp + g.nbx] == s;
     double es = 0.0, sm = 0.0;
     int nsp = 0, nb = 0, ns = 0, g0 = 0, g1 = 0;
-    for (int j = lane; j < nsite; j += 32) {
+    for (int j = lane; j < nsite && s >= 0; j += 32) {
         const int y = y0 + j / bw, x = x0 + j % bw;
         const int64_t i = (int64_t)y * g.W + x;
-        const bool gap = mask[i] != 0;
+        if (mask[i] == MASK_ABSENT) continue;
+        const bool gap = mask[i] == MASK_GAP;
         const double pi = gap ? 0.0 : ((double)values[i] - zmin) * scale;
         if (gap) {
             if (((x + y) & 1) == 0) ++g0; else ++g1;
@@ -111,20 +138,26 @@ __global__ void k_block_stats(Geom g, const float* __restrict__ values,
             sm += pi;
             ++ns;
         }
-        if (x + 1 < g.W) {
-            ++nb;
-            if (!gap && !mask[i + 1]) {
-                const double pj = ((double)values[i + 1] - zmin) * scale;
-                es += -J * cos(q * (pi - pj));
-                ++nsp;
+        if (x + 1 < x1 || right_ok) {
+            const uint8_t mj = mask[i + 1];
+            if (mj != MASK_ABSENT) {
+                ++nb;
+                if (!gap && mj == 0) {
+                    const double pj = ((double)values[i + 1] - zmin) * scale;
+                    es += -J * cos(q * (pi - pj));
+                    ++nsp;
+                }
             }
         }
-        if (y + 1 < g.H) {
-            ++nb;
-            if (!gap && !mask[i + g.W]) {
-                const double pj = ((double)values[i + g.W] - zmin) * scale;
-                es += -J * cos(q * (pi - pj));
-                ++nsp;
+        if (y + 1 < y1 || down_ok) {
+            const uint8_t mj = mask[i + g.W];
+            if (mj != MASK_ABSENT) {
+                ++nb;
+                if (!gap && mj == 0) {
+                    const double pj = ((double)values[i + g.W] - zmin) * scale;
+                    es += -J * cos(q * (pi - pj));
+                    ++nsp;
+                }
             }
         }
     }
@@ -177,7 +210,8 @@ __global__ void k_scan_counts(const int32_t* __restrict__ cnt, int n, int32_t* _
 // belongs to a neighbouring block (block edge), then the others, each group
 // in row-major order. Keeping the edge sites together lets most warps of the
 // sweep skip the per-bond energy split.
-__global__ void k_build_lists(Geom g, const uint8_t* __restrict__ mask,
+__global__ void k_build_lists(Geom g, const int32_t* __restrict__ of_block,
+                              const uint8_t* __restrict__ mask,
                               const int32_t* __restrict__ start0, const int32_t* __restrict__ start1,
                               uint2* __restrict__ list0, uint2* __restrict__ list1,
                               int32_t* __restrict__ split0, int32_t* __restrict__ split1) {
@@ -189,6 +223,13 @@ __global__ void k_build_lists(Geom g, const uint8_t* __restrict__ mask,
     const int y0 = by * g.lb, x0 = bx * g.lb;
     const int y1 = min(g.H, y0 + g.lb), x1 = min(g.W, x0 + g.lb);
     const int bw = x1 - x0, nsite = (y1 - y0) * bw;
+    const int s = of_block[b];
+    // Neighbours across the block's left / right / upper / lower edge exist
+    // only in the same slice; within the slice, absent sites have no bonds.
+    const bool l_ok = bx > 0 && of_block[b - 1] == s;
+    const bool r_ok = bx + 1 < g.nbx && of_block[b + 1] == s;
+    const bool u_ok = by > 0 && of_block[b - g.nbx] == s;
+    const bool d_ok = by + 1 < g.nby && of_block[b + g.nbx] == s;
     int o0 = start0[b], o1 = start1[b];
     for (int pass = 0; pass < 2; ++pass) {
         for (int j0 = 0; j0 < nsite; j0 += 32) {
@@ -198,8 +239,8 @@ __global__ void k_build_lists(Geom g, const uint8_t* __restrict__ mask,
             if (j < nsite) {
                 y = y0 + j / bw;
                 x = x0 + j % bw;
-                const bool edge = (x > 0 && x == x0) || (y > 0 && y == y0);
-                take = mask[(int64_t)y * g.W + x] != 0 && edge == (pass == 0);
+                const bool edge = (x == x0 && l_ok) || (y == y0 && u_ok);
+                take = mask[(int64_t)y * g.W + x] == MASK_GAP && edge == (pass == 0);
                 c = (x + y) & 1;
             }
             const unsigned m0 = __ballot_sync(0xffffffffu, take && c == 0);
@@ -207,12 +248,16 @@ __global__ void k_build_lists(Geom g, const uint8_t* __restrict__ mask,
             if (take) {
                 const int64_t i = (int64_t)y * g.W + x;
                 uint32_t f = 0;
-                if (x > 0) { f |= NB_L; if (mask[i - 1]) f |= GAP_L; }
-                if (x + 1 < g.W) { f |= NB_R; if (mask[i + 1]) f |= GAP_R; }
-                if (y > 0) { f |= NB_U; if (mask[i - g.W]) f |= GAP_U; }
-                if (y + 1 < g.H) { f |= NB_D; if (mask[i + g.W]) f |= GAP_D; }
-                if (x > 0 && x == x0) f |= EDGE_L;
-                if (y > 0 && y == y0) f |= EDGE_U;
+                const bool hl = (x > x0 || l_ok) && mask[i - 1] != MASK_ABSENT;
+                const bool hr = (x + 1 < x1 || r_ok) && mask[i + 1] != MASK_ABSENT;
+                const bool hu = (y > y0 || u_ok) && mask[i - g.W] != MASK_ABSENT;
+                const bool hd = (y + 1 < y1 || d_ok) && mask[i + g.W] != MASK_ABSENT;
+                if (hl) { f |= NB_L; if (mask[i - 1] == MASK_GAP) f |= GAP_L; }
+                if (hr) { f |= NB_R; if (mask[i + 1] == MASK_GAP) f |= GAP_R; }
+                if (hu) { f |= NB_U; if (mask[i - g.W] == MASK_GAP) f |= GAP_U; }
+                if (hd) { f |= NB_D; if (mask[i + g.W] == MASK_GAP) f |= GAP_D; }
+                if (hl && x == x0) f |= EDGE_L;
+                if (hu && y == y0) f |= EDGE_U;
                 const uint2 e = make_uint2(((uint32_t)y << 16) | (uint32_t)x,
                                            ((uint32_t)b << META_SHIFT) | f);
                 const unsigned below = (1u << lane) - 1u;
@@ -234,8 +279,8 @@ __global__ void k_build_lists(Geom g, const uint8_t* __restrict__ mask,
 // (global sample mean when the block has no sample); random start (plain
 // MPR) draws 2*pi*u from the reserved tag 0xFFFF.
 template <typename S>
-__global__ void k_init(Geom g, const uint2* __restrict__ list, int64_t n_list, int colour,
-                       const float* __restrict__ init_angle, S* __restrict__ ang, int G,
+__global__ void k_init(Geom g, Slices sl, const uint2* __restrict__ list, int64_t n_list,
+                       int colour, const float* __restrict__ init_angle, S* __restrict__ ang, int G,
                        int Rp, int random, Rng rng, uint32_t r_even) {
     const int64_t total = n_list * Rp;
     const size_t plane = (size_t)g.H * g.Wh;
@@ -249,9 +294,10 @@ __global__ void k_init(Geom g, const uint2* __restrict__ list, int64_t n_list, i
         float v = init_angle[b];
         if (random) {
             const uint32_t gr = r_even + (uint32_t)r;
+            const int s = sl.of_block[b];
             uint32_t w[4];
-            philox4x32_10((uint32_t)((int64_t)y * g.W + x), 0u | (0xFFFFu << 16), gr >> 1, 0u,
-                          rng.key0, rng.key1, w);
+            philox4x32_10(local_index(sl.rect[s], y, x), 0u | (0xFFFFu << 16), gr >> 1, 0u,
+                          rng.key0, sl.key1[s], w);
             v = kTwoPi * u01(w[(gr & 1u) * 2u]);
         }
         const int grp = r / G, lane = r % G;
@@ -337,7 +383,8 @@ __global__ void k_ecur_reset(int nblk, int Rp, const double* __restrict__ Es,
 // t = 0: sigma = sign(e_s,b - e_b(0)), blocks without gap sites stop at 0;
 // counts the running targeted blocks of every realization. `running` holds 1
 // for the batch's lanes on entry.
-__global__ void k_stop_init(int nblk, int Rp, const double* __restrict__ es,
+__global__ void k_stop_init(int nblk, int Rp, const int32_t* __restrict__ of_block,
+                            const double* __restrict__ es,
                             const double* __restrict__ inb, const int32_t* __restrict__ Nsp,
                             const int32_t* __restrict__ ngap, const double* __restrict__ ecur,
                             int8_t* __restrict__ sigma, uint8_t* __restrict__ running,
@@ -356,7 +403,7 @@ __global__ void k_stop_init(int nblk, int Rp, const double* __restrict__ es,
         const bool run = valid && ngap[b] > 0;
         running[t] = run;
         stop[t] = run ? -1 : 0;
-        if (run && Nsp[b] > 0) atomicAdd(&tcount[r], 1);
+        if (run && Nsp[b] > 0) atomicAdd(&tcount[of_block[b] * Rp + r], 1);
     }
 }
 
@@ -368,7 +415,8 @@ __global__ void k_stop_init(int nblk, int Rp, const double* __restrict__ es,
 // k_stop_targeted: E_b += the sweep's change (eacc, then cleared);
 // e_b = E_b / N_b; a targeted block stops once sigma (e_b(t) - e_s,b) >= 0.
 // One thread per (item, lane).
-__global__ void k_stop_targeted(int G, int groups, int Rp, Control* __restrict__ ctl,
+__global__ void k_stop_targeted(int G, int groups, int Rp, const int32_t* __restrict__ of_block,
+                                Control* __restrict__ ctl,
                                 const uint32_t* __restrict__ work, uint32_t work_stride,
                                 const double* __restrict__ es, const double* __restrict__ inb,
                                 const int32_t* __restrict__ Nsp, float* __restrict__ eacc,
@@ -396,7 +444,7 @@ __global__ void k_stop_targeted(int G, int groups, int Rp, Control* __restrict__
         if (reached) {
             running[k] = 0;
             stop[k] = (int32_t)t_sweep;
-            atomicSub(&tcount[r], 1);
+            atomicSub(&tcount[of_block[b] * Rp + r], 1);
         }
     }
 }
@@ -408,7 +456,7 @@ __global__ void k_stop_targeted(int G, int groups, int Rp, Control* __restrict__
 // finishes last closes the sweep: t + 1, the next worklist's size, the
 // running count, and a cleared counter for the list after it.
 __global__ void k_stop_rest(int nblk, int groups, int G, int Rp, int n_max,
-                            Control* __restrict__ ctl, const uint32_t* __restrict__ work,
+                            const int32_t* __restrict__ of_block, Control* __restrict__ ctl, const uint32_t* __restrict__ work,
                             uint32_t* __restrict__ work_all, uint32_t work_stride,
                             const int32_t* __restrict__ Nsp, uint8_t* __restrict__ running,
                             int32_t* __restrict__ stop, const int32_t* __restrict__ tcount) {
@@ -422,12 +470,13 @@ __global__ void k_stop_rest(int nblk, int groups, int G, int Rp, int n_max,
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t item = w ? w[i] : (uint32_t)i;
         const int b = (int)(item / (uint32_t)groups), grp = (int)(item % (uint32_t)groups);
+        const int32_t* tc = tcount + (size_t)(of_block[b] < 0 ? 0 : of_block[b]) * Rp;
         bool any = false;
         for (int g = 0; g < G; ++g) {
             const int r = grp * G + g;
             const size_t k = (size_t)b * Rp + r;
             if (!running[k]) continue;
-            if ((Nsp[b] == 0 && tcount[r] == 0) || (int)t_sweep >= n_max) {
+            if ((Nsp[b] == 0 && tc[r] == 0) || (int)t_sweep >= n_max) {
                 running[k] = 0;
                 stop[k] = (int32_t)t_sweep;
             } else {
@@ -496,10 +545,15 @@ __global__ void k_cal_mid(int nblk, const int32_t* __restrict__ Nsp, const float
     }
 }
 
-__global__ void k_cal_fill(int nblk, const int32_t* __restrict__ Nsp, float* __restrict__ T,
-                           float* __restrict__ beta) {
-    const float med = median_targeted(T, Nsp, nblk);
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+// Blocks without sample bonds take the median of their slice's targeted
+// blocks' T (Sec. 2.2.2); every block gets beta = 1 / T. One CTA per slice.
+__global__ void k_cal_fill(Slices sl, int nbx, const int32_t* __restrict__ Nsp,
+                           float* __restrict__ T, float* __restrict__ beta) {
+    const int4 bk = sl.blk[blockIdx.x];
+    const float med = median_targeted(T, Nsp, bk, nbx);
+    const int nb = bk.z * bk.w;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const int b = (bk.x + j / bk.w) * nbx + bk.y + j % bk.w;
         float tb = T[b];
         if (Nsp[b] <= 0) {
             tb = med;
@@ -580,7 +634,7 @@ __global__ void k_sum_to_grid(Geom g, const uint8_t* __restrict__ mask,
          i += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / g.W), x = (int)(i % g.W);
         const int c = (x + y) & 1;
-        out[i] = mask[i] ? sum[(size_t)c * plane + (size_t)y * g.Wh + (x >> 1)] : 0.0;
+        out[i] = mask[i] == MASK_GAP ? sum[(size_t)c * plane + (size_t)y * g.Wh + (x >> 1)] : 0.0;
     }
 }
 
@@ -592,41 +646,59 @@ __global__ void k_grid_to_sum(Geom g, const uint8_t* __restrict__ mask,
          i += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / g.W), x = (int)(i % g.W);
         const int c = (x + y) & 1;
-        sum[(size_t)c * plane + (size_t)y * g.Wh + (x >> 1)] = mask[i] ? in[i] : 0.0;
+        sum[(size_t)c * plane + (size_t)y * g.Wh + (x >> 1)] = mask[i] == MASK_GAP ? in[i] : 0.0;
     }
 }
 
 // Sec. 2.1 back-transform of the conditional mean; samples copied bit for bit.
-__global__ void k_predict(Geom g, const float* __restrict__ values,
+__global__ void k_predict(Geom g, Slices sl, const float* __restrict__ values,
                           const uint8_t* __restrict__ mask, const double* __restrict__ sum,
-                          double inv_r, double zmin, double zmax, float* __restrict__ out,
-                          const float* __restrict__ truth, double* __restrict__ err) {
+                          double inv_r, float* __restrict__ out, const float* __restrict__ truth,
+                          double* __restrict__ err) {
     const int64_t n = (int64_t)g.H * g.W;
-    double ea = 0.0, e2 = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+    const int64_t n_warps = (n + 31) / 32 * 32;   // every lane of a warp runs every iteration
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_warps;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (!mask[i]) {
-            out[i] = values[i];
-            continue;
+        double ea = 0.0, e2 = 0.0;
+        int s = -1;
+        bool gap = false;
+        if (i < n) {
+            const uint8_t mk = mask[i];
+            const int y = (int)(i / g.W), x = (int)(i % g.W);
+            s = sl.of_block[(y / g.lb) * g.nbx + x / g.lb];
+            if (mk == MASK_ABSENT) {
+                out[i] = 0.0f;
+            } else if (mk == 0) {
+                out[i] = values[i];
+            } else {
+                gap = true;
+                const double zmin = sl.zmin[s], zmax = sl.zmax[s];
+                const double mphi = sum[hidx(g, (x + y) & 1, y, x)] * inv_r;
+                const float z = (float)(zmin + (zmax - zmin) * mphi / 6.283185307179586476925);
+                out[i] = z;
+                if (truth) {
+                    const double e = (double)truth[i] - (double)z;
+                    ea = fabs(e);
+                    e2 = e * e;
+                }
+            }
         }
-        const int y = (int)(i / g.W), x = (int)(i % g.W);
-        const double mphi = sum[hidx(g, (x + y) & 1, y, x)] * inv_r;
-        const float z = (float)(zmin + (zmax - zmin) * mphi / 6.283185307179586476925);
-        out[i] = z;
-        if (truth) {
-            const double e = (double)truth[i] - (double)z;
-            ea += fabs(e);
-            e2 += e * e;
-        }
-    }
-    if (truth) {
-        for (int d = 16; d > 0; d >>= 1) {
-            ea += __shfl_xor_sync(0xffffffffu, ea, d);
-            e2 += __shfl_xor_sync(0xffffffffu, e2, d);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&err[0], ea);
-            atomicAdd(&err[1], e2);
+        if (!truth) continue;
+        // Per-slice error sums (Eqs. 3-4): one warp sum when all its sites
+        // share a slice, per-site atomics otherwise.
+        const int s0 = __shfl_sync(0xffffffffu, s, 0);
+        if (__all_sync(0xffffffffu, s == s0)) {
+            for (int d = 16; d > 0; d >>= 1) {
+                ea += __shfl_xor_sync(0xffffffffu, ea, d);
+                e2 += __shfl_xor_sync(0xffffffffu, e2, d);
+            }
+            if ((threadIdx.x & 31) == 0 && s0 >= 0 && (ea != 0.0 || e2 != 0.0)) {
+                atomicAdd(&err[2 * s0], ea);
+                atomicAdd(&err[2 * s0 + 1], e2);
+            }
+        } else if (s >= 0 && gap) {
+            atomicAdd(&err[2 * s], ea);
+            atomicAdd(&err[2 * s + 1], e2);
         }
     }
 }
@@ -643,8 +715,9 @@ __global__ void k_get_state(Geom g, const uint8_t* __restrict__ mask, const floa
         const int y = (int)(i / g.W), x = (int)(i % g.W);
         const int c = (x + y) & 1;
         const size_t hs = (size_t)y * g.Wh + (x >> 1);
-        out[i] = mask[i] ? Store<S>::load1(ang + ((size_t)(grp * 2 + c) * plane + hs) * G + lane)
-                         : dang[(size_t)c * plane + hs];
+        out[i] = mask[i] == MASK_GAP
+                     ? Store<S>::load1(ang + ((size_t)(grp * 2 + c) * plane + hs) * G + lane)
+                     : dang[(size_t)c * plane + hs];
     }
 }
 
@@ -656,7 +729,7 @@ __global__ void k_set_state(Geom g, const uint8_t* __restrict__ mask, S* __restr
     const int grp = r / G, lane = r % G;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (!mask[i]) continue;
+        if (mask[i] != MASK_GAP) continue;
         const int y = (int)(i / g.W), x = (int)(i % g.W);
         const int c = (x + y) & 1;
         const size_t hs = (size_t)y * g.Wh + (x >> 1);
@@ -666,7 +739,8 @@ __global__ void k_set_state(Geom g, const uint8_t* __restrict__ mask, S* __restr
 
 // E_b from scratch in FP64 (one warp per block): Eq. 1 over the owned bonds.
 template <typename S>
-__global__ void k_block_energy(Geom g, const uint8_t* __restrict__ mask,
+__global__ void k_block_energy(Geom g, const int32_t* __restrict__ of_block,
+                               const uint8_t* __restrict__ mask,
                                const float* __restrict__ dang, const S* __restrict__ ang, int G,
                                int r, double q, double J, double* __restrict__ E) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -677,20 +751,27 @@ __global__ void k_block_energy(Geom g, const uint8_t* __restrict__ mask,
     auto angle = [&](int y, int x) -> double {
         const int c = (x + y) & 1;
         const size_t hs = (size_t)y * g.Wh + (x >> 1);
-        return mask[(int64_t)y * g.W + x]
+        return mask[(int64_t)y * g.W + x] == MASK_GAP
                    ? (double)Store<S>::load1(ang + ((size_t)(grp * 2 + c) * plane + hs) * G + ln)
                    : (double)dang[(size_t)c * plane + hs];
+    };
+    // A bond exists between present sites of the same slice.
+    auto bond = [&](int y2, int x2, int sb) {
+        return y2 < g.H && x2 < g.W && mask[(int64_t)y2 * g.W + x2] != MASK_ABSENT &&
+               of_block[(y2 / g.lb) * g.nbx + x2 / g.lb] == sb;
     };
     const int by = warp / g.nbx, bx = warp % g.nbx;
     const int y0 = by * g.lb, x0 = bx * g.lb;
     const int y1 = min(g.H, y0 + g.lb), x1 = min(g.W, x0 + g.lb);
     const int bw = x1 - x0, nsite = (y1 - y0) * bw;
+    const int sb = of_block[warp];
     double s = 0.0;
     for (int j = lane; j < nsite; j += 32) {
         const int y = y0 + j / bw, x = x0 + j % bw;
+        if (mask[(int64_t)y * g.W + x] == MASK_ABSENT) continue;
         const double pi = angle(y, x);
-        if (x + 1 < g.W) s += -J * cos(q * (pi - angle(y, x + 1)));
-        if (y + 1 < g.H) s += -J * cos(q * (pi - angle(y + 1, x)));
+        if (bond(y, x + 1, sb)) s += -J * cos(q * (pi - angle(y, x + 1)));
+        if (bond(y + 1, x, sb)) s += -J * cos(q * (pi - angle(y + 1, x)));
     }
     for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
     if (lane == 0) E[warp] = s;
@@ -805,19 +886,24 @@ __global__ void k_sst_expand(Geom g, const float* __restrict__ T_blk, double* __
     }
 }
 
-__global__ void k_sst_box(Geom g, const double* __restrict__ in, double* __restrict__ out, int r,
-                          int along_x) {
+__global__ void k_sst_box(Geom g, Slices sl, const double* __restrict__ in,
+                          double* __restrict__ out, int r, int along_x) {
     const int64_t n = (int64_t)g.H * g.W;
     const double inv = 1.0 / (double)(2 * r + 1);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / g.W), x = (int)(i % g.W);
+        const int sb = sl.of_block[(y / g.lb) * g.nbx + x / g.lb];
+        if (sb < 0) continue;
+        const int4 rc = sl.rect[sb];   // coordinates clamp to the site's own field
+        if (y >= rc.x + rc.z || x >= rc.y + rc.w) continue;
         double s = 0.0;
         if (along_x) {
             const double* row = in + (int64_t)y * g.W;
-            for (int d = -r; d <= r; ++d) s += row[min(max(x + d, 0), g.W - 1)];
+            for (int d = -r; d <= r; ++d) s += row[min(max(x + d, rc.y), rc.y + rc.w - 1)];
         } else {
-            for (int d = -r; d <= r; ++d) s += in[(int64_t)min(max(y + d, 0), g.H - 1) * g.W + x];
+            for (int d = -r; d <= r; ++d)
+                s += in[(int64_t)min(max(y + d, rc.x), rc.x + rc.z - 1) * g.W + x];
         }
         out[i] = s * inv;
     }
@@ -849,37 +935,41 @@ inline int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
 }
 }  // namespace
 
-void launch_minmax(const float* values, const uint8_t* mask, int64_t n, uint32_t* mm,
-                   cudaStream_t s) {
-    k_minmax<<<grid_for(n, 256), 256, 0, s>>>(values, mask, n, mm);
+void launch_minmax_field(const float* values, const uint8_t* mask, int64_t n, uint32_t* mm,
+                         cudaStream_t s) {
+    k_minmax_field<<<grid_for(n, 256), 256, 0, s>>>(values, mask, n, mm);
 }
 
-void launch_layout(const Geom& g, const float* values, const uint8_t* mask, double zmin,
-                   double zmax, int degenerate, float* dang, cudaStream_t s) {
-    k_layout<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, values, mask, zmin, zmax,
-                                                              degenerate, dang);
+void launch_minmax(const Geom& g, const int32_t* of_block, const float* values,
+                   const uint8_t* mask, uint32_t* mm, cudaStream_t s) {
+    k_minmax<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, of_block, values, mask, mm);
 }
 
-void launch_block_stats(const Geom& g, const float* values, const uint8_t* mask, double zmin,
-                        double zmax, int degenerate, double q, double J, double* Es, int32_t* Nsp,
-                        int32_t* Nb, double* ssum, int32_t* nsamp, int32_t* ngap0, int32_t* ngap1,
-                        cudaStream_t s) {
+void launch_layout(const Geom& g, const Slices& sl, const float* values, const uint8_t* mask,
+                   float* dang, cudaStream_t s) {
+    k_layout<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, sl, values, mask, dang);
+}
+
+void launch_block_stats(const Geom& g, const Slices& sl, const float* values, const uint8_t* mask,
+                        double q, double J, double* Es, int32_t* Nsp, int32_t* Nb, double* ssum,
+                        int32_t* nsamp, int32_t* ngap0, int32_t* ngap1, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((int64_t)g.nblk * 32 + threads - 1) / threads);
-    k_block_stats<<<blocks, threads, 0, s>>>(g, values, mask, zmin, zmax, degenerate, q, J, Es,
-                                             Nsp, Nb, ssum, nsamp, ngap0, ngap1);
+    k_block_stats<<<blocks, threads, 0, s>>>(g, sl, values, mask, q, J, Es, Nsp, Nb, ssum, nsamp,
+                                             ngap0, ngap1);
 }
 
 void launch_scan(const int32_t* cnt, int n, int32_t* out, cudaStream_t s) {
     k_scan_counts<<<1, 1024, 0, s>>>(cnt, n, out);
 }
 
-void launch_build_lists(const Geom& g, const uint8_t* mask, const int32_t* start0,
-                        const int32_t* start1, uint2* list0, uint2* list1, int32_t* split0,
-                        int32_t* split1, cudaStream_t s) {
+void launch_build_lists(const Geom& g, const int32_t* of_block, const uint8_t* mask,
+                        const int32_t* start0, const int32_t* start1, uint2* list0, uint2* list1,
+                        int32_t* split0, int32_t* split1, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((int64_t)g.nblk * 32 + threads - 1) / threads);
-    k_build_lists<<<blocks, threads, 0, s>>>(g, mask, start0, start1, list0, list1, split0, split1);
+    k_build_lists<<<blocks, threads, 0, s>>>(g, of_block, mask, start0, start1, list0, list1,
+                                             split0, split1);
 }
 
 namespace {
@@ -892,14 +982,15 @@ template <typename F> void with_storage(int storage, F&& f) {
 }
 }  // namespace
 
-void launch_init(const Geom& g, const uint2* list, int64_t n_list, int colour,
+void launch_init(const Geom& g, const Slices& sl, const uint2* list, int64_t n_list, int colour,
                  const float* init_angle, void* ang, int storage, int G, int Rp, int random,
                  Rng rng, uint32_t r_even, cudaStream_t s) {
     if (n_list == 0) return;
     with_storage(storage, [&](auto tag) {
         using S = typename decltype(tag)::type;
-        k_init<S><<<grid_for(n_list * Rp, 256), 256, 0, s>>>(
-            g, list, n_list, colour, init_angle, static_cast<S*>(ang), G, Rp, random, rng, r_even);
+        k_init<S><<<grid_for(n_list * Rp, 256), 256, 0, s>>>(g, sl, list, n_list, colour,
+                                                            init_angle, static_cast<S*>(ang), G,
+                                                            Rp, random, rng, r_even);
     });
 }
 
@@ -976,28 +1067,29 @@ void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* 
     k_ecur_reset<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, Es, ecur, eacc);
 }
 
-void launch_stop_init(int nblk, int Rp, const double* es, const double* inb, const int32_t* Nsp,
-                      const int32_t* ngap, const double* ecur, int8_t* sigma, uint8_t* running,
-                      int32_t* stop, int32_t* tcount, double* e_last, cudaStream_t s) {
+void launch_stop_init(int nblk, int Rp, const int32_t* of_block, const double* es,
+                      const double* inb, const int32_t* Nsp, const int32_t* ngap, const double* ecur,
+                      int8_t* sigma, uint8_t* running, int32_t* stop, int32_t* tcount,
+                      double* e_last, cudaStream_t s) {
     k_stop_init<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(
-        nblk, Rp, es, inb, Nsp, ngap, ecur, sigma, running, stop, tcount, e_last);
+        nblk, Rp, of_block, es, inb, Nsp, ngap, ecur, sigma, running, stop, tcount, e_last);
 }
 
-void launch_stop_targeted(int G, int groups, int Rp, int grid, Control* ctl,
-                          const uint32_t* work, uint32_t work_stride, const double* es,
-                          const double* inb, const int32_t* Nsp, float* eacc, double* ecur,
-                          const int8_t* sigma, uint8_t* running, int32_t* stop, int32_t* tcount,
-                          double* e_last, cudaStream_t s) {
-    k_stop_targeted<<<grid, 256, 0, s>>>(G, groups, Rp, ctl, work, work_stride, es, inb, Nsp, eacc,
-                                         ecur, sigma, running, stop, tcount, e_last);
+void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, int grid,
+                          Control* ctl, const uint32_t* work, uint32_t work_stride,
+                          const double* es, const double* inb, const int32_t* Nsp, float* eacc,
+                          double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
+                          int32_t* tcount, double* e_last, cudaStream_t s) {
+    k_stop_targeted<<<grid, 256, 0, s>>>(G, groups, Rp, of_block, ctl, work, work_stride, es, inb,
+                                         Nsp, eacc, ecur, sigma, running, stop, tcount, e_last);
 }
 
-void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, int grid, Control* ctl,
-                      const uint32_t* work, uint32_t* work_all, uint32_t work_stride,
-                      const int32_t* Nsp, uint8_t* running, int32_t* stop, const int32_t* tcount,
-                      cudaStream_t s) {
-    k_stop_rest<<<grid, 256, 0, s>>>(nblk, groups, G, Rp, n_max, ctl, work, work_all, work_stride,
-                                     Nsp, running, stop, tcount);
+void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int32_t* of_block,
+                      int grid, Control* ctl, const uint32_t* work, uint32_t* work_all,
+                      uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
+                      const int32_t* tcount, cudaStream_t s) {
+    k_stop_rest<<<grid, 256, 0, s>>>(nblk, groups, G, Rp, n_max, of_block, ctl, work, work_all,
+                                     work_stride, Nsp, running, stop, tcount);
 }
 
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
@@ -1015,8 +1107,9 @@ void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* 
     k_cal_mid<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Nsp, lo, hi, T, ctl);
 }
 
-void launch_cal_fill(int nblk, const int32_t* Nsp, float* T, float* beta, cudaStream_t s) {
-    k_cal_fill<<<1, 1024, 0, s>>>(nblk, Nsp, T, beta);
+void launch_cal_fill(const Slices& sl, int nbx, const int32_t* Nsp, float* T, float* beta,
+                     cudaStream_t s) {
+    k_cal_fill<<<sl.n, 1024, 0, s>>>(sl, nbx, Nsp, T, beta);
 }
 
 void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
@@ -1053,11 +1146,11 @@ void launch_grid_to_sum(const Geom& g, const uint8_t* mask, const double* in, do
     k_grid_to_sum<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, mask, in, sum);
 }
 
-void launch_predict(const Geom& g, const float* values, const uint8_t* mask, const double* sum,
-                    double inv_r, double zmin, double zmax, float* out, const float* truth,
-                    double* err, cudaStream_t s) {
-    k_predict<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, values, mask, sum, inv_r, zmin,
-                                                               zmax, out, truth, err);
+void launch_predict(const Geom& g, const Slices& sl, const float* values, const uint8_t* mask,
+                    const double* sum, double inv_r, float* out, const float* truth, double* err,
+                    cudaStream_t s) {
+    k_predict<<<grid_for((int64_t)g.H * g.W, 256), 256, 0, s>>>(g, sl, values, mask, sum, inv_r,
+                                                               out, truth, err);
 }
 
 void launch_get_state(const Geom& g, const uint8_t* mask, const float* dang, const void* ang,
@@ -1078,26 +1171,26 @@ void launch_set_state(const Geom& g, const uint8_t* mask, void* ang, int storage
     });
 }
 
-void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, const void* ang,
-                         int storage, int G, int r, double q, double J, double* E,
-                         cudaStream_t s) {
+void launch_block_energy(const Geom& g, const int32_t* of_block, const uint8_t* mask,
+                         const float* dang, const void* ang, int storage, int G, int r, double q,
+                         double J, double* E, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)(((int64_t)g.nblk * 32 + threads - 1) / threads);
     with_storage(storage, [&](auto tag) {
         using S = typename decltype(tag)::type;
-        k_block_energy<S><<<blocks, threads, 0, s>>>(g, mask, dang, static_cast<const S*>(ang), G,
-                                                     r, q, J, E);
+        k_block_energy<S><<<blocks, threads, 0, s>>>(g, of_block, mask, dang,
+                                                     static_cast<const S*>(ang), G, r, q, J, E);
     });
 }
 
-void launch_sst(const Geom& g, const float* T_blk, int r, int n_s, double* Ts, double* tmp,
-                float* Tf, float* beta, cudaStream_t s) {
+void launch_sst(const Geom& g, const Slices& sl, const float* T_blk, int r, int n_s, double* Ts,
+                double* tmp, float* Tf, float* beta, cudaStream_t s) {
     const int64_t n = (int64_t)g.H * g.W;
     const int grid = grid_for(n, 256);
     k_sst_expand<<<grid, 256, 0, s>>>(g, T_blk, Ts);
     for (int k = 0; k < n_s; ++k) {
-        k_sst_box<<<grid, 256, 0, s>>>(g, Ts, tmp, r, 1);
-        k_sst_box<<<grid, 256, 0, s>>>(g, tmp, Ts, r, 0);
+        k_sst_box<<<grid, 256, 0, s>>>(g, sl, Ts, tmp, r, 1);
+        k_sst_box<<<grid, 256, 0, s>>>(g, sl, tmp, Ts, r, 0);
     }
     k_sst_beta<<<grid, 256, 0, s>>>(n, Ts, Tf, beta);
 }

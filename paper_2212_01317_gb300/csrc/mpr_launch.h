@@ -10,21 +10,24 @@ namespace mpr {
 
 float ord2f(uint32_t u);
 
-void launch_minmax(const float* values, const uint8_t* mask, int64_t n, uint32_t* mm,
-                   cudaStream_t s);
-void launch_layout(const Geom& g, const float* values, const uint8_t* mask, double zmin,
-                   double zmax, int degenerate, float* dang, cudaStream_t s);
-void launch_block_stats(const Geom& g, const float* values, const uint8_t* mask, double zmin,
-                        double zmax, int degenerate, double q, double J, double* Es, int32_t* Nsp,
-                        int32_t* Nb, double* ssum, int32_t* nsamp, int32_t* ngap0, int32_t* ngap1,
-                        cudaStream_t s);
+// One field (mask != 0: gap): mm[0..1] = order-preserving (min, max), pre-set.
+void launch_minmax_field(const float* values, const uint8_t* mask, int64_t n, uint32_t* mm,
+                         cudaStream_t s);
+// mm: 2 per slice (order-preserving min, max), pre-set to (max, 0).
+void launch_minmax(const Geom& g, const int32_t* of_block, const float* values,
+                   const uint8_t* mask, uint32_t* mm, cudaStream_t s);
+void launch_layout(const Geom& g, const Slices& sl, const float* values, const uint8_t* mask,
+                   float* dang, cudaStream_t s);
+void launch_block_stats(const Geom& g, const Slices& sl, const float* values, const uint8_t* mask,
+                        double q, double J, double* Es, int32_t* Nsp, int32_t* Nb, double* ssum,
+                        int32_t* nsamp, int32_t* ngap0, int32_t* ngap1, cudaStream_t s);
 void launch_scan(const int32_t* cnt, int n, int32_t* out, cudaStream_t s);
-void launch_build_lists(const Geom& g, const uint8_t* mask, const int32_t* start0,
-                        const int32_t* start1, uint2* list0, uint2* list1, int32_t* split0,
-                        int32_t* split1, cudaStream_t s);
+void launch_build_lists(const Geom& g, const int32_t* of_block, const uint8_t* mask,
+                        const int32_t* start0, const int32_t* start1, uint2* list0, uint2* list1,
+                        int32_t* split0, int32_t* split1, cudaStream_t s);
 // `storage` is an mpr_storage value (0 FP32, 1 BF16, 2 FP16): the element
 // type of the batch state `ang`.
-void launch_init(const Geom& g, const uint2* list, int64_t n_list, int colour,
+void launch_init(const Geom& g, const Slices& sl, const uint2* list, int64_t n_list, int colour,
                  const float* init_angle, void* ang, int storage, int G, int Rp, int random,
                  Rng rng, uint32_t r_even, cudaStream_t s);
 void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, void* ang,
@@ -37,27 +40,30 @@ void launch_energy(const SweepArgs& a, int G, int storage, int grid, cudaStream_
 void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s);
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
                        cudaStream_t s);
-void launch_stop_init(int nblk, int Rp, const double* es, const double* inb, const int32_t* Nsp,
-                      const int32_t* ngap, const double* ecur, int8_t* sigma, uint8_t* running,
-                      int32_t* stop, int32_t* tcount, double* e_last, cudaStream_t s);
-void launch_stop_targeted(int G, int groups, int Rp, int grid, Control* ctl,
-                          const uint32_t* work, uint32_t work_stride, const double* es,
-                          const double* inb, const int32_t* Nsp, float* eacc, double* ecur,
-                          const int8_t* sigma, uint8_t* running, int32_t* stop, int32_t* tcount,
-                          double* e_last, cudaStream_t s);
+// tcount is [n_slices][Rp]: running targeted blocks per slice and realization.
+void launch_stop_init(int nblk, int Rp, const int32_t* of_block, const double* es,
+                      const double* inb, const int32_t* Nsp, const int32_t* ngap, const double* ecur,
+                      int8_t* sigma, uint8_t* running, int32_t* stop, int32_t* tcount,
+                      double* e_last, cudaStream_t s);
+void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, int grid,
+                          Control* ctl, const uint32_t* work, uint32_t work_stride,
+                          const double* es, const double* inb, const int32_t* Nsp, float* eacc,
+                          double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
+                          int32_t* tcount, double* e_last, cudaStream_t s);
 // work == nullptr: every item (t = 0). Writes the next sweep's worklist into
 // work_all and advances ctl->t.
-void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, int grid, Control* ctl,
-                      const uint32_t* work, uint32_t* work_all, uint32_t work_stride,
-                      const int32_t* Nsp, uint8_t* running, int32_t* stop, const int32_t* tcount,
-                      cudaStream_t s);
+void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int32_t* of_block,
+                      int grid, Control* ctl, const uint32_t* work, uint32_t* work_all,
+                      uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
+                      const int32_t* tcount, cudaStream_t s);
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
                           unsigned long long* total, cudaStream_t s);
 void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,
                      Control* ctl, cudaStream_t s);
 void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T,
                     Control* ctl, cudaStream_t s);
-void launch_cal_fill(int nblk, const int32_t* Nsp, float* T, float* beta, cudaStream_t s);
+void launch_cal_fill(const Slices& sl, int nbx, const int32_t* Nsp, float* T, float* beta,
+                     cudaStream_t s);
 void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
                      const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s);
 void launch_cal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,
@@ -70,21 +76,22 @@ void launch_sum_to_grid(const Geom& g, const uint8_t* mask, const double* sum, d
                         cudaStream_t s);
 void launch_grid_to_sum(const Geom& g, const uint8_t* mask, const double* in, double* sum,
                         cudaStream_t s);
-void launch_predict(const Geom& g, const float* values, const uint8_t* mask, const double* sum,
-                    double inv_r, double zmin, double zmax, float* out, const float* truth,
-                    double* err, cudaStream_t s);
+// err: 2 per slice (sum |e|, sum e^2 over the slice's gap sites), pre-zeroed.
+void launch_predict(const Geom& g, const Slices& sl, const float* values, const uint8_t* mask,
+                    const double* sum, double inv_r, float* out, const float* truth, double* err,
+                    cudaStream_t s);
 void launch_get_state(const Geom& g, const uint8_t* mask, const float* dang, const void* ang,
                       int storage, int G, int r, float* out, cudaStream_t s);
 void launch_set_state(const Geom& g, const uint8_t* mask, void* ang, int storage, int G, int r,
                       const float* in, cudaStream_t s);
-void launch_block_energy(const Geom& g, const uint8_t* mask, const float* dang, const void* ang,
-                         int storage, int G, int r, double q, double J, double* E,
-                         cudaStream_t s);
+void launch_block_energy(const Geom& g, const int32_t* of_block, const uint8_t* mask,
+                         const float* dang, const void* ang, int storage, int G, int r, double q,
+                         double J, double* E, cudaStream_t s);
 
 // Sec. 2.2.3 site temperatures: Ts (FP64, H*W) smoothed from T_blk, then
 // Tf = (float)Ts and beta = 1 / Tf; tmp is H*W doubles of scratch.
-void launch_sst(const Geom& g, const float* T_blk, int r, int n_s, double* Ts, double* tmp,
-                float* Tf, float* beta, cudaStream_t s);
+void launch_sst(const Geom& g, const Slices& sl, const float* T_blk, int r, int n_s, double* Ts,
+                double* tmp, float* Tf, float* beta, cudaStream_t s);
 void launch_site_beta(int64_t n, const float* Tf, float* beta, cudaStream_t s);
 
 // Energy moments of the calibration chains and the Newton calibration.

@@ -228,7 +228,7 @@ extern "C" mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int64_t n = (int64_t)H * W;
     k_na_reset<<<1, 1, 0, s>>>(sc.mm);
-    launch_minmax(values, mask, n, sc.mm, s);
+    launch_minmax_field(values, mask, n, sc.mm, s);
     k_na_range<<<1, 1, 0, s>>>(sc.mm, zrange);
     const int threads = 256;
     const int blocks = (int)(((int64_t)g.nblk * 32 + threads - 1) / threads);

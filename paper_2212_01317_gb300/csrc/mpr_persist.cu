@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(512, 1) k_cal_persistent(CalPersistArgs a) {
             a.T[b] = a.Nsp[b] > 0 ? 0.5f * (a.lo[b] + a.hi[b]) : 0.0f;
         if (!grid_sync(a.bar, gen, lim)) return;
         if (blockIdx.x == 0) {
-            const float med = median_targeted(a.T, a.Nsp, nblk);
+            const float med =
+                median_targeted(a.T, a.Nsp, make_int4(0, 0, a.sw.g.nby, a.sw.g.nbx), a.sw.g.nbx);
             if (threadIdx.x == 0) *a.med = med;
         }
         if (!grid_sync(a.bar, gen, lim)) return;
@@ -145,9 +146,10 @@ __global__ void __launch_bounds__(512, 1) k_cal_persistent(CalPersistArgs a) {
                 const int y = en.x >> 16, x = en.x & 0xffff;
                 float v = a.init_angle[en.y >> META_SHIFT];
                 if (a.random_init) {
+                    const int sl = a.sw.sl.of_block[en.y >> META_SHIFT];
                     uint32_t w[4];
-                    philox4x32_10((uint32_t)y * (uint32_t)a.sw.g.W + (uint32_t)x, 0xFFFFu << 16,
-                                  (uint32_t)r >> 1, 0u, a.sw.rng.key0, a.sw.rng.key1, w);
+                    philox4x32_10(local_index(a.sw.sl.rect[sl], y, x), 0xFFFFu << 16,
+                                  (uint32_t)r >> 1, 0u, a.sw.rng.key0, a.sw.sl.key1[sl], w);
                     v = kTwoPi * u01(w[(r & 1) * 2]);
                 }
                 const int grp = r / G, lane = r % G;

@@ -223,6 +223,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
     const float beta = a.beta[b];
     const float J = a.m.J;
     const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
+    const int sl = a.sl.of_block[b];
+    const int4 rc = a.sl.rect[sl];
+    const uint32_t key1 = a.sl.key1[sl];
     float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
     const int step = CW * 32;
     int e = e0 + cw * 32 + lane;
@@ -234,8 +237,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
         const uint32_t f = en.y;
         const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
         uint32_t w[4];
-        philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)x, ctr1, rpair, 0u, a.rng.key0,
-                      a.rng.key1, w);
+        philox4x32_10(local_index(rc, y, x), ctr1, rpair, 0u, a.rng.key0, key1, w);
         const float2 ph = Store<S>::load2(own + (size_t)hs * G);
         float nc0[4], ns0[4], nc1[4], ns1[4];
         neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
@@ -302,9 +304,10 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
             const int y = en.x >> 16, x = en.x & 0xffff;
             const uint32_t f = en.y;
             const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
+            const int sl = a.sl.of_block[b];
             uint32_t w[4];
-            philox4x32_10((uint32_t)y * (uint32_t)a.g.W + (uint32_t)x, ctr1,
-                          (a.r_base + (uint32_t)rl) >> 1, 0u, a.rng.key0, a.rng.key1, w);
+            philox4x32_10(local_index(a.sl.rect[sl], y, x), ctr1, (a.r_base + (uint32_t)rl) >> 1,
+                          0u, a.rng.key0, a.sl.key1[sl], w);
             const float2 ph = own[(size_t)hs * NP];
             float nc0[4], ns0[4], nc1[4], ns1[4];
             neighbour_field<float>(a, reinterpret_cast<const float*>(oth), G, hs, x, f, nc0, ns0,
@@ -413,16 +416,20 @@ __device__ __forceinline__ void energy_item(const SweepArgs& a, int item, int wi
 }
 
 // Median of the targeted blocks' T by a radix select over the (positive)
-// float bit patterns, run by one CTA; k is the 0-based rank.
+// float bit patterns, run by one CTA over the blocks of one slice (the block
+// rectangle bk = (by0, bx0, nby_s, nbx_s) of a canvas nbx blocks wide); k is
+// the 0-based rank.
 __device__ inline uint32_t select_kth(const float* __restrict__ T, const int32_t* __restrict__ Nsp,
-                                      int nblk, uint32_t k, uint32_t* hist, uint32_t* s_digit,
-                                      uint32_t* s_k) {
+                                      int4 bk, int nbx, uint32_t k, uint32_t* hist,
+                                      uint32_t* s_digit, uint32_t* s_k) {
+    const int nb = bk.z * bk.w;
     uint32_t prefix = 0, pmask = 0;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
-        for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+            const int b = (bk.x + j / bk.w) * nbx + bk.y + j % bk.w;
             if (Nsp[b] <= 0) continue;
             const uint32_t v = __float_as_uint(T[b]);
             if ((v & pmask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
@@ -444,23 +451,27 @@ __device__ inline uint32_t select_kth(const float* __restrict__ T, const int32_t
 }
 
 // Median (mean of the two middle values for an even count) of the targeted
-// blocks' T, by one CTA; 0 when no block is targeted.
+// blocks' T within one slice, by one CTA; 0 when no block is targeted.
 __device__ inline float median_targeted(const float* __restrict__ T, const int32_t* __restrict__ Nsp,
-                                        int nblk) {
+                                        int4 bk, int nbx) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t s_digit, s_k, s_n;
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
+    const int nb = bk.z * bk.w;
     uint32_t cnt = 0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) cnt += Nsp[b] > 0;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x)
+        cnt += Nsp[(bk.x + j / bk.w) * nbx + bk.y + j % bk.w] > 0;
     atomicAdd(&s_n, cnt);
     __syncthreads();
     const uint32_t n = s_n;
     float med = 0.0f;
     if (n > 0) {
-        const float lo = __uint_as_float(select_kth(T, Nsp, nblk, (n - 1) / 2, hist, &s_digit, &s_k));
-        const float hi =
-            (n & 1) ? lo : __uint_as_float(select_kth(T, Nsp, nblk, n / 2, hist, &s_digit, &s_k));
+        const float lo =
+            __uint_as_float(select_kth(T, Nsp, bk, nbx, (n - 1) / 2, hist, &s_digit, &s_k));
+        const float hi = (n & 1) ? lo
+                                 : __uint_as_float(select_kth(T, Nsp, bk, nbx, n / 2, hist,
+                                                              &s_digit, &s_k));
         med = 0.5f * (lo + hi);
     }
     return med;

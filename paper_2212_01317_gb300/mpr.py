@@ -26,7 +26,8 @@ EXPORTS = [
     "mpr_set_running", "mpr_block_energy", "mpr_get_block_e", "mpr_get_profile",
     "mpr_block_stats_noalloc", "mpr_set_realization_base", "mpr_get_accumulator",
     "mpr_set_accumulator", "mpr_smooth_temperatures", "mpr_set_site_temperatures",
-    "mpr_get_site_temperatures", "mpr_energy_moments", "mpr_energy_vjp",
+    "mpr_get_site_temperatures", "mpr_energy_moments", "mpr_energy_vjp", "mpr_create_batch",
+    "mpr_predict_batch", "mpr_get_slice_layout",
 ]
 MPR_NOALLOC_MAX_BLOCKS = 65536
 
@@ -59,7 +60,8 @@ class mpr_info(C.Structure):
                 ("zmin", C.c_double), ("zmax", C.c_double), ("degenerate", C.c_int32),
                 ("calibrated", C.c_int32), ("realizations", C.c_int64), ("batch", C.c_int32),
                 ("group", C.c_int32), ("gap_updates", C.c_int64),
-                ("cal_gap_updates", C.c_int64), ("device_bytes", C.c_int64)]
+                ("cal_gap_updates", C.c_int64), ("device_bytes", C.c_int64),
+                ("n_slices", C.c_int32)]
 
 
 class MprError(RuntimeError):
@@ -123,6 +125,9 @@ def load(path: str | None = None):
         "mpr_get_site_temperatures": (st, [P, P]),
         "mpr_energy_moments": (st, [P, P, i32, i32, i32, i32, P, P, P, P]),
         "mpr_energy_vjp": (st, [P, P, P]),
+        "mpr_create_batch": (st, [i32, P, P, P, C.POINTER(mpr_options), C.POINTER(P)]),
+        "mpr_predict_batch": (st, [P, P, P, P]),
+        "mpr_get_slice_layout": (st, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -169,6 +174,34 @@ def mpr_create(height: int, width: int, block: int, mask, values, options: mpr_o
     if st != MPR_OK:
         raise MprError(st, load().mpr_status_string(st).decode())
     return out
+
+
+def mpr_create_batch(grids, masks, values, options: mpr_options | None = None):
+    """grids: list of (height, width, block); masks / values: lists of arrays or
+    tensors (host or device), one per field."""
+    n = len(grids)
+    g = (mpr_grid * n)(*[mpr_grid(h, w, b) for (h, w, b) in grids])
+    mp = (C.c_void_p * n)(*[_ptr(m).value for m in masks])
+    vp = (C.c_void_p * n)(*[_ptr(v).value for v in values])
+    out = C.c_void_p()
+    st = load().mpr_create_batch(n, g, mp, vp, None if options is None else C.byref(options),
+                                 C.byref(out))
+    if st != MPR_OK:
+        raise MprError(st, load().mpr_status_string(st).decode())
+    return out
+
+
+def mpr_predict_batch(ctx, outs, truths=None, aae_rase=None):
+    n = len(outs)
+    op = (C.c_void_p * n)(*[_ptr(o).value for o in outs])
+    tp = None if truths is None else (C.c_void_p * n)(*[_ptr(t).value for t in truths])
+    _check(ctx, load().mpr_predict_batch(ctx, op, tp, _ptr(aae_rase)))
+
+
+def mpr_get_slice_layout(ctx, n: int) -> np.ndarray:
+    r = np.zeros((n, 4), np.int32)
+    _check(ctx, load().mpr_get_slice_layout(ctx, _ptr(r)))
+    return r
 
 
 def mpr_destroy(ctx):
@@ -406,3 +439,58 @@ class GapFiller:
         E = np.zeros(self.nblk)
         mpr_block_energy(self.ctx, r, E)
         return E
+
+
+class BatchFiller:
+    """Many fields in one context (mpr_create_batch); numpy in, numpy out."""
+
+    def __init__(self, values_list, mask_list, block: int, **options):
+        self.values = [np.ascontiguousarray(v, dtype=np.float32) for v in values_list]
+        self.masks = [np.ascontiguousarray(m, dtype=np.uint8) for m in mask_list]
+        self.shapes = [m.shape for m in self.masks]
+        self.opt = mpr_default_options(**options)
+        self.ctx = mpr_create_batch([(h, w, block) for (h, w) in self.shapes], self.masks,
+                                    self.values, self.opt)
+        self.info = mpr_get_info(self.ctx)
+        self.layout = mpr_get_slice_layout(self.ctx, len(self.shapes))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mpr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def calibrate(self) -> np.ndarray:
+        T = np.zeros(self.info.nblk, np.float32)
+        mpr_calibrate(self.ctx, T)
+        return T
+
+    def set_temperatures(self, T):
+        mpr_set_temperatures(self.ctx, np.ascontiguousarray(T, dtype=np.float32))
+
+    def simulate(self, n: int):
+        mpr_simulate(self.ctx, n)
+
+    def predict(self, truths=None):
+        outs = [np.zeros(s, np.float32) for s in self.shapes]
+        if truths is None:
+            mpr_predict_batch(self.ctx, outs)
+            return outs, None
+        err = np.zeros(2 * len(outs), np.float64)
+        mpr_predict_batch(self.ctx, outs,
+                          [np.ascontiguousarray(t, dtype=np.float32) for t in truths], err)
+        return outs, err.reshape(-1, 2)
+
+    def block_slice(self, k: int, canvas_blocks: np.ndarray) -> np.ndarray:
+        """The blocks of field k from a canvas-wide per-block array."""
+        y0, x0, h, w = self.layout[k]
+        lb = self.info.block
+        grid = canvas_blocks.reshape(self.info.nby, self.info.nbx)
+        return grid[y0 // lb:y0 // lb + (h + lb - 1) // lb,
+                    x0 // lb:x0 // lb + (w + lb - 1) // lb].ravel()
+

@@ -1,0 +1,136 @@
+"""Many fields in one context (mpr_create_batch), through the C-ABI.
+
+Each field of a batch must compute what it computes alone (mpr_create with
+slice_id + k): its own transform range, Eq. 2 statistics, random streams
+(site numbering within the field), median fallback and stop bookkeeping,
+and no bond to another field. The single-field path is checked against the
+oracle elsewhere, so the batch is checked against it field by field.
+"""
+import numpy as np
+import pytest
+
+from paper_2212_01317_gb300 import mpr, synth
+from paper_2212_01317_gb300.mpr import BatchFiller, GapFiller
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(37, 53, "random", 0.45), (64, 64, "disc", 0.6), (20, 90, "random", 0.3),
+          (48, 40, "random", 0.7), (9, 9, "random", 0.5)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def fields(lb=8):
+    out = []
+    for k, (h, w, kind, p) in enumerate(SHAPES):
+        z, m = synth.small_problem(h, w, p, seed=40 + k, kind=kind)
+        z = (z * (1 + k) + 10 * k).astype(np.float32)          # different value ranges
+        out.append((z, m, np.where(m != 0, np.nan, z).astype(np.float32)))
+    return out
+
+
+def block_rects(bf):
+    lb = bf.info.block
+    return [(y0 // lb, x0 // lb, (h + lb - 1) // lb, (w + lb - 1) // lb)
+            for (y0, x0, h, w) in bf.layout]
+
+
+def scatter_blocks(bf, per_field, fill=1.0):
+    canvas = np.full((bf.info.nby, bf.info.nbx), fill, np.float32)
+    for (by, bx, nby, nbx), v in zip(block_rects(bf), per_field):
+        canvas[by:by + nby, bx:bx + nbx] = np.asarray(v, np.float32).reshape(nby, nbx)
+    return canvas.ravel()
+
+
+def test_layout_and_block_statistics():
+    fs = fields()
+    bf = BatchFiller([v for (_, _, v) in fs], [m for (_, m, _) in fs], 8, seed=3)
+    info = bf.info
+    assert info.n_slices == len(fs)
+    occ = np.zeros((info.height, info.width), np.int32)
+    for (y0, x0, h, w), (z, m, v) in zip(bf.layout, fs):
+        assert (h, w) == m.shape and (y0 + x0) % 2 == 0 and y0 % 8 == 0 and x0 % 8 == 0
+        occ[y0:y0 + h, x0:x0 + w] += 1
+    assert occ.max() == 1
+    n = info.nblk
+    Es, Nsp, Nb, ma, ng = (np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.int32),
+                           np.zeros(n, np.float32), np.zeros(n, np.int32))
+    mpr.mpr_get_block_stats(bf.ctx, Es, Nsp, Nb, ma, ng)
+    for k, (z, m, v) in enumerate(fs):
+        gf = GapFiller(v, m, 8, seed=3, slice_id=k)
+        e1, nsp1, nb1, ma1, ng1 = gf.block_stats()
+        np.testing.assert_allclose(bf.block_slice(k, Es), e1, rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(bf.block_slice(k, Nsp), nsp1)
+        np.testing.assert_array_equal(bf.block_slice(k, Nb), nb1)
+        np.testing.assert_array_equal(bf.block_slice(k, ng), ng1)
+        np.testing.assert_allclose(bf.block_slice(k, ma), ma1, rtol=1e-6, atol=1e-7)
+        gf.close()
+    bf.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_fields_compute_what_they_compute_alone(storage):
+    fs = fields()
+    R = 6
+    rng = np.random.default_rng(5)
+    bf = BatchFiller([v for (_, _, v) in fs], [m for (_, m, _) in fs], 8, seed=9, slice_id=20,
+                     n_max=60, storage=storage)
+    Ts = [rng.uniform(0.03, 0.4, nby * nbx).astype(np.float32)
+          for (_, _, nby, nbx) in block_rects(bf)]
+    bf.set_temperatures(scatter_blocks(bf, Ts))
+    bf.simulate(R)
+    preds, errs = bf.predict([z for (z, _, _) in fs])
+    for k, (z, m, v) in enumerate(fs):
+        gf = GapFiller(v, m, 8, seed=9, slice_id=20 + k, n_max=60, storage=storage)
+        gf.set_temperatures(Ts[k])
+        gf.simulate(R)
+        p1, (a1, r1) = gf.predict(z)
+        gf.close()
+        g = m != 0
+        scale = float(z[m == 0].max() - z[m == 0].min())
+        close = np.abs(preds[k] - p1) <= 1e-5 * scale
+        assert close[g].mean() >= 0.98, (k, close[g].mean())
+        assert np.array_equal(preds[k][~g], z[~g])
+        assert abs(errs[k, 0] - a1) <= 0.02 * a1 + 1e-6
+    bf.close()
+
+
+def test_calibration_per_field():
+    fs = fields()
+    bf = BatchFiller([v for (_, _, v) in fs], [m for (_, m, _) in fs], 8, seed=2, n_bisect=10,
+                     n_eq=6, n_meas=6)
+    T = bf.calibrate()
+    for k, (z, m, v) in enumerate(fs):
+        gf = GapFiller(v, m, 8, seed=2, slice_id=k, n_bisect=10, n_eq=6, n_meas=6)
+        T1 = gf.calibrate()
+        gf.close()
+        Tk = bf.block_slice(k, T)
+        assert (np.abs(Tk - T1) <= 1e-6 * T1).mean() >= 0.9, (k, Tk, T1)
+    bf.close()
+
+
+def test_canvas_predict_and_limits():
+    fs = fields()
+    bf = BatchFiller([v for (_, _, v) in fs], [m for (_, m, _) in fs], 8, seed=1, n_max=20)
+    bf.set_temperatures(np.full(bf.info.nblk, 0.1, np.float32))
+    bf.simulate(2)
+    canvas = np.zeros((bf.info.height, bf.info.width), np.float32)
+    mpr.mpr_predict(bf.ctx, canvas)
+    inside = np.zeros(canvas.shape, bool)
+    preds, _ = bf.predict()
+    for (y0, x0, h, w), p in zip(bf.layout, preds):
+        inside[y0:y0 + h, x0:x0 + w] = True
+        np.testing.assert_array_equal(canvas[y0:y0 + h, x0:x0 + w], p)
+    assert (canvas[~inside] == 0).all()
+    bf.close()
+    # mixed block sizes are refused
+    g = [(10, 10, 4), (10, 10, 8)]
+    z = np.zeros((10, 10), np.float32)
+    m = np.zeros((10, 10), np.uint8)
+    with pytest.raises(mpr.MprError):
+        mpr.mpr_create_batch(g, [m, m], [z, z])
