@@ -51,6 +51,9 @@ def parse():
                     help="element type of the realizations' angles (arithmetic stays FP32)")
     ap.add_argument("--cal-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="calibration launch form (3: every kernel from the host, for profilers)")
+    ap.add_argument("--plain-sample", type=int, default=0,
+                    help="batch workloads: also time the plain form (one FP32 context per "
+                         "field) on this many fields")
     ap.add_argument("--calibration", default="bisection", choices=["bisection", "newton"],
                     help="per-block temperature fit: bisection (the plain form) or safeguarded "
                          "Newton steps from the fluctuation identity")
@@ -149,7 +152,14 @@ def run_reference(args, world, rank):
     import oracle
     from paper_2212_01317_gb300 import synth
     oracle.build()
-    wl = synth.workload(args.workload)
+    if args.workload in synth.BATCH_WORKLOADS:
+        # A batch's fields are independent problems: the oracle's rate is taken
+        # on its first field.
+        bw = synth.batch_workload(args.workload)
+        wl = synth.Workload(bw.name + "_field0", bw.truths[0], bw.masks[0], bw.block,
+                            bw.realizations)
+    else:
+        wl = synth.workload(args.workload)
     H, W = wl.shape
     lb = wl.block
     cores = len(os.sched_getaffinity(0))
@@ -401,11 +411,156 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_ours_batch(args, world, rank, local):
+    """Batched form: all fields of a batch workload in one context (one launch
+    per half-step for all of them), against the plain form (one FP32 context
+    per field, one after another) on a sample of the fields."""
+    import torch
+    from paper_2212_01317_gb300 import mpr, replicas, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mpr.load()
+    bw = synth.batch_workload(args.workload, seed=rank)
+    R = bw.realizations
+    stream = torch.cuda.current_stream(dev)
+    vals_h = [np.where(m != 0, np.nan, z).astype(np.float32) for z, m in zip(bw.truths, bw.masks)]
+    vals_d = [torch.from_numpy(v).to(dev) for v in vals_h]
+    masks_d = [torch.from_numpy(m).to(dev) for m in bw.masks]
+    outs_d = [torch.empty(m.shape, dtype=torch.float32, device=dev) for m in bw.masks]
+    grids = [(m.shape[0], m.shape[1], bw.block) for m in bw.masks]
+    storage = args.storage
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def options(profile, st=storage, slice_id=0):
+        return mpr.mpr_default_options(seed=2024 + 7919 * rank, slice_id=slice_id, profile=profile,
+                                       storage=STORAGE[st], cal_mode=args.cal_mode,
+                                       cal_method=1 if args.calibration == "newton" else 0,
+                                       sim_graph=0, cuda_stream=stream.cuda_stream)
+
+    def step(values, masks, outs, profile=1):
+        ctx = mpr.mpr_create_batch(grids, masks, values, options(profile))
+        try:
+            mpr.mpr_calibrate(ctx, None)
+            mpr.mpr_simulate(ctx, R)
+            mpr.mpr_predict_batch(ctx, outs)
+            info = mpr.mpr_get_info(ctx)
+            prof = mpr.mpr_get_profile(ctx)
+        finally:
+            mpr.mpr_destroy(ctx)
+        return info, prof
+
+    for _ in range(args.warmup):
+        step(vals_d, masks_d, outs_d)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, updates, sim_updates, launches, sim_ms, sim_launch = [], 0, 0, 0, 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info, prof = step(vals_d, masks_d, outs_d)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        updates += info.gap_updates + info.cal_gap_updates
+        sim_updates += info.gap_updates
+        launches += prof.kernel_launches
+        sim_ms += prof.sim_halfstep_ms
+        sim_launch += prof.sim_halfstep_launches
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = replicas.max_over_ranks(float(np.sum(step_ms)), dev)
+    updates_all = replicas.sum_over_ranks(updates, dev)
+    P = bw.n_gap
+    value = updates_all / (total_ms / 1e3)
+    mpix = world * P * args.steps / (total_ms / 1e3) / 1e6
+    # Accuracy of the timed form: AAE over all gap sites of the last step.
+    err = sum(float(np.abs(o.cpu().numpy() - z)[m != 0].sum())
+              for o, z, m in zip(outs_d, bw.truths, bw.masks))
+    aae = err / P
+
+    # The plain form on a sample of fields: one FP32 context per field, in turn.
+    plain = None
+    if args.plain_sample > 0 and rank == 0:
+        k = min(args.plain_sample, len(bw.masks))
+        ups, t_plain, gaps, err_p = 0, 0.0, 0, 0.0
+        for j in range(k):
+            H, W = bw.masks[j].shape
+            o1 = torch.empty((H, W), dtype=torch.float32, device=dev)
+            for rep in range(2):                 # first pass warms the allocator and caches
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx = mpr.mpr_create(H, W, bw.block, masks_d[j], vals_d[j],
+                                     options(0, "f32", slice_id=j))
+                mpr.mpr_calibrate(ctx, None)
+                mpr.mpr_simulate(ctx, R)
+                mpr.mpr_predict(ctx, o1)
+                inf = mpr.mpr_get_info(ctx)
+                mpr.mpr_destroy(ctx)
+                e1.record(stream)
+                e1.synchronize()
+            ups += inf.gap_updates + inf.cal_gap_updates
+            t_plain += e0.elapsed_time(e1)
+            gaps += int(np.count_nonzero(bw.masks[j]))
+            err_p += float(np.abs(o1.cpu().numpy() - bw.truths[j])[bw.masks[j] != 0].sum())
+        err_b = sum(float(np.abs(outs_d[j].cpu().numpy() - bw.truths[j])[bw.masks[j] != 0].sum())
+                    for j in range(k))
+        plain = {"value": ups / (t_plain / 1e3), "unit": "updates/s",
+                 "gap_filled_mpix_s": gaps / (t_plain / 1e3) / 1e6, "aae": err_p / gaps,
+                 "aae_batched_same_fields": err_b / gaps,
+                 "sample": f"fields 0..{k - 1} of {len(bw.masks)}, one FP32 context each, "
+                           "calibrate + simulate + predict, one after another"}
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    p_mean = P / bw.n_sites
+    bpu = bytes_per_gap_update(4.0 if storage == "f32" else 2.0, p_mean)
+    achieved = sim_updates * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": bw.name, "fields": len(bw.masks), "sites": bw.n_sites,
+                   "gap_sites": P, "block": bw.block, "realizations": R, "storage": storage,
+                   "form": "batched: every field in one context", "calibration": args.calibration,
+                   "l2": "inputs larger than L2; flushed between timed steps",
+                   "parallelism": f"replicas{world}"},
+        "gap_filled_mpix_s": mpix, "aae": aae,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "k_sweep (realizations)", "peak_kind": peak_kind,
+                     "bytes_per_gap_update": bpu,
+                     "avg_launch_us": 1e3 * sim_ms / sim_launch if sim_launch else None},
+        "clocks": clk, "e2e": None, "plain_form": plain,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    from paper_2212_01317_gb300 import synth
+    if args.workload in synth.BATCH_WORKLOADS:
+        run_ours_batch(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

@@ -91,6 +91,8 @@ typedef struct {
                             d<e_b>/d beta_b = -Var(E_b)/N_b (see mpr_energy_moments) */
     int32_t n_newton;    /* Newton iterations (default 6), each n_eq + n_meas sweeps */
     float t_init;        /* Newton starting temperature (default 0.1) */
+    int32_t sim_graph;   /* 1: mpr_simulate runs its sweep loop as one CUDA graph (a device-side
+                            loop; full grids, no per-launch timing; ignored when profile = 1) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 
@@ -259,6 +261,25 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n_realizations);
  * aae_rase[2] (host) receives AAE and RASE over the gap sites (Eqs. 3-4).
  * Errors: ESTATE (no realization accumulated), EINVAL, ECUDA. */
 mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae_rase);
+
+/* ---- launch-shape autotuning ----
+ * mpr_autotune times the sweep kernel's work decompositions on trial batches
+ * of n_realizations realizations (their first n_sweeps sweeps, every block
+ * running, CUDA events on the context's stream) and keeps the fastest for
+ * the context's later simulations: lane-group width G (2 or 8 realizations
+ * interleaved per site) and the sweep form (four warps per item of G = 8 /
+ * one warp per item of G = 2, or the wide form with four times as many
+ * warps per item). The results do not depend on the choice (the random
+ * streams are keyed by realization, not by lane). The trial batches are
+ * discarded: nothing is accumulated or counted. Needs temperatures; no batch
+ * may be open. out->ms[k]: time of candidate k = (2, normal), (2, wide),
+ * (8, normal), (8, wide). Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+typedef struct {
+    int32_t group;   /* chosen lane-group width */
+    int32_t wide;    /* 1: the wide form for every sweep */
+    float ms[4];     /* timed candidates */
+} mpr_tuning;
+mpr_status mpr_autotune(mpr_ctx* ctx, int32_t n_realizations, int32_t n_sweeps, mpr_tuning* out);
 
 /* ---- realizations split across processes ----
  * The realizations of one field are independent chains (Sec. 2.1) that

@@ -70,6 +70,7 @@ struct mpr_ctx {
     double* mom = nullptr;       // [4][nblk] moments of the last energy-moment run
     bool chains_valid = false;   // the batch state holds the calibration chains
     bool moments_valid = false;
+    cudaGraphConditionalHandle sim_cond = 0;   // set while a sweep loop is being captured
     double* ebar = nullptr;
     double* sum = nullptr;  // [2][H][Wh] running sums of gap angles
     float* out_buf = nullptr;
@@ -101,6 +102,7 @@ struct mpr_ctx {
     Control* h_ctl = nullptr;    // pinned mirror
     int grid_cache[2][3][2] = {};  // full grid of k_sweep by (G = 2 / 8, storage, wide)
     unsigned long long bound = ~0ull;  // upper bound of the running pairs (from the last read)
+    int wide_always = 0;         // autotuned: the wide sweep form for every sweep
     bool energy_dirty = false;
     GridBarrier* bar = nullptr;  // grid barrier of the persistent calibration
     float* med = nullptr;
@@ -315,7 +317,9 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
 
 // Few items left (the realizations' tail): the wide form, and a grid no
 // larger than the running pairs can fill.
-bool sweep_wide(mpr_ctx* ctx) { return ctx->bound < (unsigned long long)ctx->n_sm * 4; }
+bool sweep_wide(mpr_ctx* ctx) {
+    return ctx->wide_always || ctx->bound < (unsigned long long)ctx->n_sm * 4;
+}
 
 int sweep_grid(mpr_ctx* ctx, bool wide) {
     int& full = ctx->grid_cache[ctx->G == 2 ? 0 : 1][ctx->storage][wide ? 1 : 0];
@@ -450,7 +454,7 @@ mpr_status sweep_once(mpr_ctx* ctx) {
     CKL();
     launch_stop_rest(g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
                      stop_grid(ctx, 1), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp,
-                     ctx->running, ctx->stop, ctx->tcount, ctx->s);
+                     ctx->running, ctx->stop, ctx->tcount, ctx->sim_cond, ctx->s);
     CKL();
     ctx->t += 1;
     return MPR_OK;
@@ -763,6 +767,7 @@ void mpr_default_options(mpr_options* o) {
     o->cal_method = 0;
     o->n_newton = 6;
     o->t_init = 0.1f;
+    o->sim_graph = 0;
     o->cuda_stream = nullptr;
 }
 
@@ -928,8 +933,8 @@ mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
                         ctx->s) ||
         cudaMemcpyAsync(ctx->d_key1, key1.data(), ns * 4, cudaMemcpyHostToDevice, ctx->s))
         return bail(MPR_ECUDA);
-    ctx->sl = Slices{ns,          ctx->d_rect, ctx->d_blk, ctx->d_of_block, ctx->d_key1,
-                     ctx->d_zmin, ctx->d_zmax, ctx->d_degen};
+    ctx->sl = Slices{ns,          rect[0],     key1[0],    ctx->d_rect, ctx->d_blk, ctx->d_of_block,
+                     ctx->d_key1, ctx->d_zmin, ctx->d_zmax, ctx->d_degen};
 
     if (upload(ctx) != MPR_OK) return bail(MPR_ECUDA);
     k_mask_normalize<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
@@ -1304,7 +1309,7 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     CKL();
     launch_stop_rest(ctx->g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
                      stop_grid(ctx, 1), ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp,
-                     ctx->running, ctx->stop, ctx->tcount, ctx->s);
+                     ctx->running, ctx->stop, ctx->tcount, 0, ctx->s);
     CKL();
     ctx->energy_dirty = false;
     ctx->batch_open = 1;
@@ -1349,9 +1354,84 @@ mpr_status mpr_sim_end(mpr_ctx* ctx) {
     return MPR_OK;
 }
 
+// The whole sweep loop as one CUDA graph: a conditional WHILE node whose body
+// is one sweep (two half-steps, the two stop kernels); the stop test's last
+// CTA sets the loop condition on the device. Grids are the full ones (the
+// running count is not known when the graph is recorded).
+mpr_status simulate_graph(mpr_ctx* ctx) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    mpr_status st = MPR_OK;
+    cudaGraphConditionalHandle cond = 0;
+    cudaGraphNodeParams p = {};
+    cudaGraphNode_t node = nullptr;
+    cudaGraph_t body = nullptr, captured = nullptr;
+    const int64_t launches0 = ctx->launches;
+    const unsigned long long bound = ctx->bound;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) goto cuda_fail;
+    if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        goto cuda_fail;
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) != cudaSuccess) goto cuda_fail;
+    body = p.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(ctx->cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        goto cuda_fail;
+    {
+        cudaStream_t user = ctx->s;
+        const int profile = ctx->opt.profile;
+        ctx->s = ctx->cap;
+        ctx->sim_cond = cond;
+        ctx->opt.profile = 0;
+        ctx->bound = ~0ull;
+        st = sweep_once(ctx);
+        ctx->opt.profile = profile;
+        ctx->sim_cond = 0;
+        ctx->s = user;
+    }
+    if (cudaStreamEndCapture(ctx->cap, &captured) != cudaSuccess && st == MPR_OK) goto cuda_fail;
+    if (st != MPR_OK) goto done;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) goto cuda_fail;
+    if (cudaGraphLaunch(exec, ctx->s) != cudaSuccess) goto cuda_fail;
+    goto done;
+cuda_fail: {
+        cudaError_t e = cudaGetLastError();
+        st = fail(ctx, MPR_ECUDA, "simulate graph: %s", cudaGetErrorString(e));
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(ctx->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(ctx->cap, &tmp);
+            if (tmp && tmp != body) cudaGraphDestroy(tmp);
+        }
+    }
+done:
+    if (exec) {
+        cudaStreamSynchronize(ctx->s);
+        cudaGraphExecDestroy(exec);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    ctx->bound = bound;
+    if (st == MPR_OK) {
+        // Sweeps done = the device sweep index minus one.
+        CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        const int64_t per_sweep = ctx->launches - launches0;
+        ctx->t = (int)ctx->h_ctl->t - 1;
+        ctx->launches = launches0 + per_sweep * ctx->t;
+    }
+    return st;
+}
+
 mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
     if (!ctx) return MPR_EINVAL;
     TRY(mpr_sim_begin(ctx, n));
+    if (ctx->opt.sim_graph && !ctx->opt.profile) {
+        TRY(simulate_graph(ctx));
+        return mpr_sim_end(ctx);
+    }
     // Sweeps are queued in chunks; after each chunk the running count is
     // copied to pinned memory. The host checks the count of the chunk before
     // the one it just queued, so the GPU never waits for the host. Sweeps
@@ -1641,6 +1721,63 @@ mpr_status mpr_energy_vjp(mpr_ctx* ctx, const double* grad_e, double* grad_beta)
     cudaFreeAsync(tmp, ctx->s);
     CK(cudaStreamSynchronize(ctx->s));
     return st;
+}
+
+mpr_status mpr_autotune(mpr_ctx* ctx, int32_t n_realizations, int32_t n_sweeps,
+                        mpr_tuning* out) {
+    if (!ctx || !out) return MPR_EINVAL;
+    ctx->err.clear();
+    if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
+    if (!ctx->calibrated) return fail(ctx, MPR_ESTATE, "calibrate or set temperatures first");
+    if (n_realizations < 1 || n_sweeps < 1 || n_sweeps > 64)
+        return fail(ctx, MPR_EINVAL, "need n_realizations >= 1 and 1 <= n_sweeps <= 64");
+    std::memset(out, 0, sizeof(*out));
+    const int saved_group = ctx->opt.group, saved_wide = ctx->wide_always;
+    const int saved_profile = ctx->opt.profile;
+    const int64_t saved[4] = {ctx->gap_updates, ctx->launches, ctx->sim_halfstep_launches,
+                              ctx->realizations};
+    const int cand[4][2] = {{2, 0}, {2, 1}, {8, 0}, {8, 1}};
+    float best = 0.0f;
+    int best_k = -1;
+    mpr_status st = MPR_OK;
+    ctx->opt.profile = 0;
+    for (int k = 0; k < 4 && st == MPR_OK; ++k) {
+        ctx->opt.group = cand[k][0];
+        ctx->wide_always = cand[k][1];
+        // A trial batch: the first sweeps (every pair running), timed on the
+        // stream; discarded afterwards (nothing is accumulated or counted).
+        st = mpr_sim_begin(ctx, n_realizations);
+        if (st != MPR_OK) break;
+        cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
+        if (!e0 || !e1) { st = fail(ctx, MPR_ECUDA, "cudaEventCreate failed"); break; }
+        cudaEventRecord(e0, ctx->s);
+        for (int i = 0; i < n_sweeps && st == MPR_OK; ++i) st = sweep_once(ctx);
+        cudaEventRecord(e1, ctx->s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, MPR_ECUDA, "autotune sync");
+        float ms = 0.0f;
+        if (st == MPR_OK) cudaEventElapsedTime(&ms, e0, e1);
+        ctx->ev_pool.push_back(e0);
+        ctx->ev_pool.push_back(e1);
+        ctx->batch_open = 0;
+        out->ms[k] = ms;
+        if (st == MPR_OK && (best_k < 0 || ms < best)) { best = ms; best_k = k; }
+    }
+    ctx->opt.profile = saved_profile;
+    ctx->gap_updates = saved[0];
+    ctx->launches = saved[1];
+    ctx->sim_halfstep_launches = saved[2];
+    ctx->realizations = saved[3];
+    ctx->chains_valid = false;
+    if (st != MPR_OK) {
+        ctx->opt.group = saved_group;
+        ctx->wide_always = saved_wide;
+        return st;
+    }
+    ctx->opt.group = cand[best_k][0];
+    ctx->wide_always = cand[best_k][1];
+    out->group = cand[best_k][0];
+    out->wide = cand[best_k][1];
+    return MPR_OK;
 }
 
 mpr_status mpr_set_realization_base(mpr_ctx* ctx, int64_t r_first) {

@@ -60,6 +60,8 @@ constexpr uint8_t MASK_ABSENT = 2;
 // alone. A single field is the one-slice case.
 struct Slices {
     int n;
+    int4 rect0;                // rect[0] and key1[0], read from the kernel parameters
+    uint32_t key1_0;           // when n == 1 (no table lookups on the hot path)
     const int4* rect;          // [n] (y0, x0, H_s, W_s): the field's sites in the canvas
     const int4* blk;           // [n] (by0, bx0, nby_s, nbx_s): the slice's blocks
     const int32_t* of_block;   // [nblk] slice of every block, -1 for padding blocks
@@ -68,6 +70,17 @@ struct Slices {
     const double* zmax;        // [n]
     const int32_t* degenerate; // [n] 1: z_max == z_min
 };
+
+// Slice s's rectangle and key word (the one-field case without a lookup).
+__device__ __forceinline__ int4 slice_rect(const Slices& sl, int s) {
+    return sl.n == 1 ? sl.rect0 : sl.rect[s];
+}
+__device__ __forceinline__ uint32_t slice_key1(const Slices& sl, int s) {
+    return sl.n == 1 ? sl.key1_0 : sl.key1[s];
+}
+__device__ __forceinline__ int slice_of(const Slices& sl, int b) {
+    return sl.n == 1 ? 0 : sl.of_block[b];
+}
 
 // Philox counter word 0 of a site: its index within its own field.
 __host__ __device__ inline uint32_t local_index(const int4& rc, int y, int x) {

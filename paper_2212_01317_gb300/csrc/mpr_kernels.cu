@@ -456,7 +456,8 @@ __global__ void k_stop_targeted(int G, int groups, int Rp, const int32_t* __rest
 // finishes last closes the sweep: t + 1, the next worklist's size, the
 // running count, and a cleared counter for the list after it.
 __global__ void k_stop_rest(int nblk, int groups, int G, int Rp, int n_max,
-                            const int32_t* __restrict__ of_block, Control* __restrict__ ctl, const uint32_t* __restrict__ work,
+                            const int32_t* __restrict__ of_block, cudaGraphConditionalHandle cond,
+                            Control* __restrict__ ctl, const uint32_t* __restrict__ work,
                             uint32_t* __restrict__ work_all, uint32_t work_stride,
                             const int32_t* __restrict__ Nsp, uint8_t* __restrict__ running,
                             int32_t* __restrict__ stop, const int32_t* __restrict__ tcount) {
@@ -499,11 +500,14 @@ __global__ void k_stop_rest(int nblk, int groups, int G, int Rp, int n_max,
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
-        ctl->n_running = atomicExch(&ctl->n_running_acc, 0ull);
+        const unsigned long long left = atomicExch(&ctl->n_running_acc, 0ull);
+        ctl->n_running = left;
         ctl->n_work[par] = 0;
         ctl->ticket = 0;
         ctl->t = t_sweep + 1;
         __threadfence();
+        // Inside a graph's sweep loop: continue while pairs run and sweeps remain.
+        if (cond) cudaGraphSetConditional(cond, (left > 0 && (int)t_sweep < n_max) ? 1u : 0u);
     }
 }
 
@@ -1087,9 +1091,9 @@ void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, in
 void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int32_t* of_block,
                       int grid, Control* ctl, const uint32_t* work, uint32_t* work_all,
                       uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
-                      const int32_t* tcount, cudaStream_t s) {
-    k_stop_rest<<<grid, 256, 0, s>>>(nblk, groups, G, Rp, n_max, of_block, ctl, work, work_all,
-                                     work_stride, Nsp, running, stop, tcount);
+                      const int32_t* tcount, cudaGraphConditionalHandle cond, cudaStream_t s) {
+    k_stop_rest<<<grid, 256, 0, s>>>(nblk, groups, G, Rp, n_max, of_block, cond, ctl, work,
+                                     work_all, work_stride, Nsp, running, stop, tcount);
 }
 
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,

@@ -55,7 +55,7 @@ void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, in
 void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int32_t* of_block,
                       int grid, Control* ctl, const uint32_t* work, uint32_t* work_all,
                       uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
-                      const int32_t* tcount, cudaStream_t s);
+                      const int32_t* tcount, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
                           unsigned long long* total, cudaStream_t s);
 void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,

@@ -223,9 +223,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
     const float beta = a.beta[b];
     const float J = a.m.J;
     const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
-    const int sl = a.sl.of_block[b];
-    const int4 rc = a.sl.rect[sl];
-    const uint32_t key1 = a.sl.key1[sl];
+    const int sl = slice_of(a.sl, b);
+    const int4 rc = slice_rect(a.sl, sl);
+    const uint32_t key1 = slice_key1(a.sl, sl);
     float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
     const int step = CW * 32;
     int e = e0 + cw * 32 + lane;
@@ -304,10 +304,10 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
             const int y = en.x >> 16, x = en.x & 0xffff;
             const uint32_t f = en.y;
             const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
-            const int sl = a.sl.of_block[b];
+            const int sl = slice_of(a.sl, b);
             uint32_t w[4];
-            philox4x32_10(local_index(a.sl.rect[sl], y, x), ctr1, (a.r_base + (uint32_t)rl) >> 1,
-                          0u, a.rng.key0, a.sl.key1[sl], w);
+            philox4x32_10(local_index(slice_rect(a.sl, sl), y, x), ctr1,
+                          (a.r_base + (uint32_t)rl) >> 1, 0u, a.rng.key0, slice_key1(a.sl, sl), w);
             const float2 ph = own[(size_t)hs * NP];
             float nc0[4], ns0[4], nc1[4], ns1[4];
             neighbour_field<float>(a, reinterpret_cast<const float*>(oth), G, hs, x, f, nc0, ns0,

@@ -27,7 +27,7 @@ EXPORTS = [
     "mpr_block_stats_noalloc", "mpr_set_realization_base", "mpr_get_accumulator",
     "mpr_set_accumulator", "mpr_smooth_temperatures", "mpr_set_site_temperatures",
     "mpr_get_site_temperatures", "mpr_energy_moments", "mpr_energy_vjp", "mpr_create_batch",
-    "mpr_predict_batch", "mpr_get_slice_layout",
+    "mpr_predict_batch", "mpr_get_slice_layout", "mpr_autotune",
 ]
 MPR_NOALLOC_MAX_BLOCKS = 65536
 
@@ -44,13 +44,17 @@ class mpr_options(C.Structure):
                 ("init", C.c_int32), ("storage", C.c_int32), ("group", C.c_int32),
                 ("profile", C.c_int32), ("cal_mode", C.c_int32), ("wait_ms", C.c_int32),
                 ("barrier_test", C.c_int32), ("cal_method", C.c_int32), ("n_newton", C.c_int32),
-                ("t_init", C.c_float), ("cuda_stream", C.c_void_p)]
+                ("t_init", C.c_float), ("sim_graph", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("sim_halfstep_launches", C.c_int64),
                 ("cal_halfstep_launches", C.c_int64), ("sim_halfstep_ms", C.c_double),
                 ("cal_halfstep_ms", C.c_double)]
+
+
+class mpr_tuning(C.Structure):
+    _fields_ = [("group", C.c_int32), ("wide", C.c_int32), ("ms", C.c_float * 4)]
 
 
 class mpr_info(C.Structure):
@@ -128,6 +132,7 @@ def load(path: str | None = None):
         "mpr_create_batch": (st, [i32, P, P, P, C.POINTER(mpr_options), C.POINTER(P)]),
         "mpr_predict_batch": (st, [P, P, P, P]),
         "mpr_get_slice_layout": (st, [P, P]),
+        "mpr_autotune": (st, [P, i32, i32, C.POINTER(mpr_tuning)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -202,6 +207,12 @@ def mpr_get_slice_layout(ctx, n: int) -> np.ndarray:
     r = np.zeros((n, 4), np.int32)
     _check(ctx, load().mpr_get_slice_layout(ctx, _ptr(r)))
     return r
+
+
+def mpr_autotune(ctx, n_realizations: int, n_sweeps: int = 4) -> mpr_tuning:
+    t = mpr_tuning()
+    _check(ctx, load().mpr_autotune(ctx, int(n_realizations), int(n_sweeps), C.byref(t)))
+    return t
 
 
 def mpr_destroy(ctx):

@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "grf", "grf_nonstationary", "mask_random", "mask_discs", "Workload",
-    "workload", "WORKLOADS",
+    "workload", "WORKLOADS", "BatchWorkload", "batch_workload", "BATCH_WORKLOADS",
 ]
 
 
@@ -181,6 +181,56 @@ WORKLOADS = {
 
 def workload(name: str, seed: int = 0) -> Workload:
     return WORKLOADS[name](seed)
+
+
+@dataclass
+class BatchWorkload:
+    """Many independent fields (time slices) filled together."""
+    name: str
+    truths: list               # float32 [H_k, W_k]
+    masks: list                # uint8 [H_k, W_k], 1 = gap
+    block: int
+    realizations: int
+    storage: str = "bf16"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_gap(self) -> int:
+        return int(sum(int(np.count_nonzero(m)) for m in self.masks))
+
+    @property
+    def n_sites(self) -> int:
+        return int(sum(m.size for m in self.masks))
+
+
+def _slices(n: int, seed: int) -> BatchWorkload:
+    """n square slices, side round(exp(U(ln 256, ln 2048))), each its own seeded
+    stationary GRF (xi ~ U(4, 32)), its own gap fraction p ~ U(0.1, 0.9), a
+    uniformly random or disc mask with probability 1/2 each; l_b = 32, R = 50."""
+    rng = np.random.default_rng(seed)
+    truths, masks, sides = [], [], []
+    for k in range(n):
+        L = int(round(math.exp(rng.uniform(math.log(256), math.log(2048)))))
+        xi = float(rng.uniform(4.0, 32.0))
+        p = float(rng.uniform(0.1, 0.9))
+        disc = bool(rng.uniform() < 0.5)
+        s = seed * 1000003 + 17 * k
+        truths.append(grf(L, L, xi, s).astype(np.float32))
+        masks.append(mask_discs(L, L, p, s + 1) if disc else mask_random(L, L, p, s + 1))
+        sides.append(L)
+    return BatchWorkload(f"slices{n}_256-2048_xi4-32_p10-90_lb32_R50", truths, masks, 32, 50,
+                         meta={"slices": n, "sides": [min(sides), max(sides)],
+                               "sites": int(sum(x * x for x in sides))})
+
+
+BATCH_WORKLOADS = {
+    "slices256": lambda seed=0: _slices(256, seed),
+    "slices32": lambda seed=0: _slices(32, seed),
+}
+
+
+def batch_workload(name: str, seed: int = 0) -> BatchWorkload:
+    return BATCH_WORKLOADS[name](seed)
 
 
 def small_problem(h: int, w: int, p: float, seed: int, xi: float = 6.0,

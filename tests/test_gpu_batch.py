@@ -134,3 +134,39 @@ def test_canvas_predict_and_limits():
     m = np.zeros((10, 10), np.uint8)
     with pytest.raises(mpr.MprError):
         mpr.mpr_create_batch(g, [m, m], [z, z])
+
+
+def test_simulate_graph_equals_host_loop():
+    fs = fields()
+    outs = []
+    for graph in (0, 1):
+        bf = BatchFiller([v for (_, _, v) in fs], [m for (_, m, _) in fs], 8, seed=4, n_max=80,
+                         sim_graph=graph)
+        bf.set_temperatures(np.full(bf.info.nblk, 0.08, np.float32))
+        bf.simulate(5)
+        outs.append((bf.predict()[0], mpr.mpr_get_info(bf.ctx).gap_updates))
+        bf.close()
+    for (z, m, v), a, b in zip(fs, outs[0][0], outs[1][0]):
+        scale = float(z[m == 0].max() - z[m == 0].min())
+        assert (np.abs(a - b) <= 1e-5 * scale)[m != 0].mean() >= 0.98
+    assert abs(outs[0][1] - outs[1][1]) <= 0.02 * outs[0][1]
+
+
+def test_autotune_picks_a_candidate_and_keeps_results():
+    z, m = synth.small_problem(96, 80, 0.5, seed=8)
+    v = np.where(m != 0, np.nan, z).astype(np.float32)
+    T = np.full(((96 + 7) // 8) * ((80 + 7) // 8), 0.1, np.float32)
+    preds = []
+    for tune in (False, True):
+        gf = GapFiller(v, m, 8, seed=6, n_max=50)
+        gf.set_temperatures(T)
+        if tune:
+            t = mpr.mpr_autotune(gf.ctx, 12, 3)
+            assert (t.group, t.wide) in {(2, 0), (2, 1), (8, 0), (8, 1)}
+            assert all(x > 0 for x in t.ms)
+            assert gf.refresh().realizations == 0 and gf.info.gap_updates == 0
+        gf.simulate(12)
+        preds.append(gf.predict()[0])
+        gf.close()
+    scale = float(z[m == 0].max() - z[m == 0].min())
+    assert (np.abs(preds[0] - preds[1]) <= 1e-5 * scale)[m != 0].mean() >= 0.98
