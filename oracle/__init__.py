@@ -46,7 +46,7 @@ class Model(C.Structure):
                 ("q", C.c_double), ("J", C.c_double),
                 ("key0", C.c_uint32), ("key1", C.c_uint32),
                 ("overrelax", C.c_int32), ("K", C.c_int32), ("threads", C.c_int32),
-                ("T_site", C.c_void_p)]
+                ("T_site", C.c_void_p), ("D", C.c_int32), ("nbz", C.c_int32)]
 
 
 class Diag(C.Structure):
@@ -92,6 +92,14 @@ def lib():
             "orc_median_targeted": (f64, [i32, P, P]),
             "orc_scores": (None, [i64, P, P, P, P, P]),
             "orc_sst_temperatures": (None, [MP, P, i32, i32, P]),
+            "orc3_model_init": (None, [MP, i32, i32, i32, i32, f64, f64, u64, u32]),
+            "orc3_block_stats": (None, [MP, P, P, P, P, P, P, P, P, P]),
+            "orc3_block_energy": (None, [MP, P, P]),
+            "orc3_update_site": (None, [MP, P, P, i64, f64, u32, u32, u32, P]),
+            "orc3_halfstep": (None, [MP, P, P, C.c_int, P, P, u32, u32, u32, P]),
+            "orc3_init_block_mean": (None, [MP, P, P, P, P, f64]),
+            "orc3_simulate_one": (C.c_int, [MP, P, P, P, P, P, P, P, i32, u32, P, P]),
+            "orc3_calibrate": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, f64, f64, P]),
             "orc_energy_moments": (None, [MP, P, P, P, i32, i32, i32, u32, P, P, P, P, P]),
             "orc_calibrate_newton": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, f64, f64, f64,
                                             P, P]),
@@ -335,6 +343,115 @@ class Oracle:
         a, r = C.c_double(), C.c_double()
         lib().orc_scores(p.size, _p(p), _p(t), _p(mk), C.byref(a), C.byref(r))
         return a.value, r.value
+
+
+class Oracle3:
+    """A D x H x W grid (6-neighbour bonds, cubic blocks); arrays are [D, H, W]."""
+
+    def __init__(self, D: int, H: int, W: int, lb: int, q: float = 0.5, J: float = 1.0,
+                 seed: int = 0, slice_id: int = 0, overrelax: bool = True):
+        self.m = Model()
+        lib().orc3_model_init(C.byref(self.m), D, H, W, lb, q, J, seed & (2**64 - 1), slice_id)
+        self.m.overrelax = 1 if overrelax else 0
+        self.D, self.H, self.W, self.lb = D, H, W, lb
+
+    @property
+    def nblk(self) -> int:
+        return self.m.nblk
+
+    def block_index(self) -> np.ndarray:
+        z, y, x = np.mgrid[0:self.D, 0:self.H, 0:self.W]
+        lb = self.lb
+        return ((z // lb) * self.m.nby + y // lb) * self.m.nbx + x // lb
+
+    def block_stats(self, phi, mask) -> BlockStats:
+        ph = np.ascontiguousarray(phi, dtype=np.float64)
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        n = self.nblk
+        Es = np.zeros(n); Nsp = np.zeros(n, np.int64); Nb = np.zeros(n, np.int64)
+        ma = np.zeros(n); ng = np.zeros(n, np.int64); ns = np.zeros(n, np.int64)
+        gm = C.c_double()
+        lib().orc3_block_stats(C.byref(self.m), _p(ph), _p(mk), _p(Es), _p(Nsp), _p(Nb), _p(ma),
+                               _p(ng), _p(ns), C.byref(gm))
+        return BlockStats(Es, Nsp, Nb, ma, ng, ns, gm.value)
+
+    def block_energy(self, phi) -> np.ndarray:
+        ph = np.ascontiguousarray(phi, dtype=np.float64)
+        E = np.zeros(self.nblk)
+        lib().orc3_block_energy(C.byref(self.m), _p(ph), _p(E))
+        return E
+
+    def update_site(self, phi: np.ndarray, mask, i: int, T: float, t: int, tag: int, r: int):
+        assert phi.dtype == np.float64 and phi.flags.c_contiguous
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        d = Diag()
+        lib().orc3_update_site(C.byref(self.m), _p(phi), _p(mk), i, T, t, tag, r, C.byref(d))
+        return d
+
+    def halfstep(self, phi: np.ndarray, mask, colour: int, T_blk, active=None, t: int = 1,
+                 tag: int = 0, r: int = 0, diag: bool = False):
+        assert phi.dtype == np.float64 and phi.flags.c_contiguous
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.ascontiguousarray(T_blk, dtype=np.float64)
+        act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+        dg = np.zeros(phi.size, dtype=DIAG_DTYPE) if diag else None
+        if dg is not None:
+            dg["phi_or"] = np.nan
+        lib().orc3_halfstep(C.byref(self.m), _p(phi), _p(mk), colour, _p(T),
+                            None if act is None else _p(act), t, tag, r,
+                            None if dg is None else _p(dg))
+        return dg
+
+    def init_block_mean(self, phi, mask, st: BlockStats) -> np.ndarray:
+        ph = np.ascontiguousarray(phi, dtype=np.float64).copy()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        lib().orc3_init_block_mean(C.byref(self.m), _p(ph), _p(mk), _p(st.mean_angle),
+                                   _p(st.n_sample), st.global_mean)
+        return ph
+
+    def simulate_one(self, phi0, mask, T_blk, st: BlockStats, n_max: int, r: int):
+        phi = np.ascontiguousarray(phi0, dtype=np.float64).copy()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.ascontiguousarray(T_blk, dtype=np.float64)
+        stop = np.zeros(self.nblk, np.int32)
+        n = lib().orc3_simulate_one(C.byref(self.m), _p(phi), _p(mk), _p(T), _p(st.Es),
+                                    _p(st.Nsp), _p(st.Nb), _p(st.n_gap), n_max, r, _p(stop), None)
+        return phi, stop, n
+
+    def calibrate(self, phi_init, mask, st: BlockStats, n_eq=25, n_meas=20, n_bisect=24,
+                  chains=1, T_lo=1e-4, T_hi=2.0):
+        ph = np.ascontiguousarray(phi_init, dtype=np.float64)
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.zeros(self.nblk)
+        lib().orc3_calibrate(C.byref(self.m), _p(ph), _p(mk), _p(st.Es), _p(st.Nsp), _p(st.Nb),
+                             n_eq, n_meas, n_bisect, chains, T_lo, T_hi, _p(T))
+        return T
+
+
+def gapfill3(values, mask, lb: int, R: int, seed: int = 0, slice_id: int = 0, n_max: int = 200,
+             n_eq: int = 25, n_meas: int = 20, n_bisect: int = 24, chains: int = 1, T_blk=None):
+    """The method on a D x H x W grid (Sec. 2.1 transform, Eq. 2 per cubic block,
+    calibration, R local-equilibrium realizations, mean, back-transform)."""
+    values = np.asarray(values, dtype=np.float32)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    D, H, W = mask.shape
+    o = Oracle3(D, H, W, lb, seed=seed, slice_id=slice_id)
+    phi, zmin, zmax, _ = Oracle.transform(values.reshape(D * H, W), mask.reshape(D * H, W))
+    phi = phi.reshape(D, H, W)
+    st = o.block_stats(phi, mask)
+    phi0 = o.init_block_mean(phi, mask, st)
+    T = o.calibrate(phi0, mask, st, n_eq, n_meas, n_bisect, chains) if T_blk is None else \
+        np.asarray(T_blk, dtype=np.float64)
+    acc = np.zeros((D, H, W))
+    updates = 0
+    for k in range(R):
+        ph, stop, _ = o.simulate_one(phi0, mask, T, st, n_max, k)
+        acc += ph
+        updates += int(np.sum(stop.astype(np.int64) * st.n_gap))
+    mean_phi = acc / R if R > 0 else phi0
+    pred = Oracle.backtransform(mean_phi.reshape(D * H, W), mask.reshape(D * H, W),
+                                values.reshape(D * H, W), zmin, zmax).reshape(D, H, W)
+    return GapfillResult(pred, T, None, None, mean_phi, zmin, zmax, st, updates)
 
 
 @dataclass

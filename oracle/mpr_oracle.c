@@ -56,6 +56,8 @@ void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, do
     m->K = 0;
     m->threads = 0;
     m->T_site = NULL;
+    m->D = 1;
+    m->nbz = 1;
 }
 
 static int block_of(const orc_model* m, int y, int x) { return (y / m->lb) * m->nbx + x / m->lb; }
@@ -216,18 +218,9 @@ double orc_total_energy(const orc_model* m, const double* phi) {
 /* ----------------------------------------------------------------- update -- */
 /* One conditional MC update of gap site i (Sec. 2.1: only prediction sites move;
  * samples are fixed), at the temperature of its block (Sec. 2.2.2). */
-void orc_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64_t i,
-                     double T, uint32_t t, uint32_t tag, uint32_t r, orc_diag* d) {
-    (void)mask;
-    const int W = m->W, H = m->H;
-    const int y = (int)(i / W), x = (int)(i % W);
-    int64_t nb[4];
-    int nn = 0;
-    if (x > 0) nb[nn++] = i - 1;
-    if (x + 1 < W) nb[nn++] = i + 1;
-    if (y > 0) nb[nn++] = i - W;
-    if (y + 1 < H) nb[nn++] = i + W;
-
+/* Metropolis (+ over-relaxation) update of site i given its neighbours nb[nn]. */
+static void update_core(const orc_model* m, double* phi, int64_t i, const int64_t* nb, int nn,
+                        double T, uint32_t t, uint32_t tag, uint32_t r, orc_diag* d) {
     double u0, u1;
     orc_site_uniforms(m, i, t, tag, r, &u0, &u1);
 
@@ -283,6 +276,20 @@ void orc_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64
         d->accepted = accepted;
         d->or_applied = or_applied;
     }
+}
+
+void orc_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64_t i,
+                     double T, uint32_t t, uint32_t tag, uint32_t r, orc_diag* d) {
+    (void)mask;
+    const int W = m->W, H = m->H;
+    const int y = (int)(i / W), x = (int)(i % W);
+    int64_t nb[4];
+    int nn = 0;
+    if (x > 0) nb[nn++] = i - 1;
+    if (x + 1 < W) nb[nn++] = i + 1;
+    if (y > 0) nb[nn++] = i - W;
+    if (y + 1 < H) nb[nn++] = i + W;
+    update_core(m, phi, i, nb, nn, T, t, tag, r, d);
 }
 
 /* Sec. 2.2.2 single checkerboard: the sites of one sub-grid have all their
@@ -600,6 +607,196 @@ void orc_calibrate_newton(const orc_model* m, const double* phi_init, const uint
     const double med = orc_median_targeted(nblk, T, Nsp);
     for (int b = 0; b < nblk; ++b) T_out[b] = Nsp[b] == 0 ? med : T[b];
     free(T); free(y); free(v); free(phi);
+}
+
+/* ------------------------------------------------------------- 3-D -- */
+
+void orc3_model_init(orc_model* m, int32_t D, int32_t H, int32_t W, int32_t lb, double q,
+                     double J, uint64_t seed, uint32_t slice) {
+    orc_model_init(m, H, W, lb, q, J, seed, slice);
+    m->D = D;
+    m->nbz = (D + lb - 1) / lb;
+    m->nblk = m->nbx * m->nby * m->nbz;
+}
+
+static int block3(const orc_model* m, int z, int y, int x) {
+    return ((z / m->lb) * m->nby + y / m->lb) * m->nbx + x / m->lb;
+}
+
+void orc3_block_stats(const orc_model* m, const double* phi, const uint8_t* mask, double* Es,
+                      int64_t* Nsp, int64_t* Nb, double* mean_angle, int64_t* n_gap,
+                      int64_t* n_sample, double* global_mean) {
+    const int D = m->D, H = m->H, W = m->W;
+    const int64_t HW = (int64_t)H * W;
+    double gsum = 0.0;
+    int64_t gcnt = 0;
+    for (int b = 0; b < m->nblk; ++b) {
+        Es[b] = 0.0; Nsp[b] = 0; Nb[b] = 0; mean_angle[b] = 0.0; n_gap[b] = 0; n_sample[b] = 0;
+    }
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t i = (int64_t)z * HW + (int64_t)y * W + x;
+                const int b = block3(m, z, y, x);
+                if (mask[i]) {
+                    n_gap[b] += 1;
+                } else {
+                    n_sample[b] += 1;
+                    mean_angle[b] += phi[i];
+                    gsum += phi[i];
+                    gcnt += 1;
+                }
+                const int64_t nb[3] = {x + 1 < W ? i + 1 : -1, y + 1 < H ? i + W : -1,
+                                       z + 1 < D ? i + HW : -1};
+                for (int k = 0; k < 3; ++k) {
+                    if (nb[k] < 0) continue;
+                    Nb[b] += 1;
+                    if (!mask[i] && !mask[nb[k]]) {
+                        Es[b] += bond_energy(m, phi[i], phi[nb[k]]);
+                        Nsp[b] += 1;
+                    }
+                }
+            }
+    for (int b = 0; b < m->nblk; ++b)
+        if (n_sample[b] > 0) mean_angle[b] /= (double)n_sample[b];
+    *global_mean = gcnt > 0 ? gsum / (double)gcnt : 0.0;
+}
+
+void orc3_block_energy(const orc_model* m, const double* phi, double* E) {
+    const int D = m->D, H = m->H, W = m->W;
+    const int64_t HW = (int64_t)H * W;
+    for (int b = 0; b < m->nblk; ++b) E[b] = 0.0;
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const int64_t i = (int64_t)z * HW + (int64_t)y * W + x;
+                const int b = block3(m, z, y, x);
+                if (x + 1 < W) E[b] += bond_energy(m, phi[i], phi[i + 1]);
+                if (y + 1 < H) E[b] += bond_energy(m, phi[i], phi[i + W]);
+                if (z + 1 < D) E[b] += bond_energy(m, phi[i], phi[i + HW]);
+            }
+}
+
+void orc3_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64_t i, double T,
+                      uint32_t t, uint32_t tag, uint32_t r, orc_diag* d) {
+    (void)mask;
+    const int D = m->D, H = m->H, W = m->W;
+    const int64_t HW = (int64_t)H * W;
+    const int z = (int)(i / HW), y = (int)((i % HW) / W), x = (int)(i % W);
+    int64_t nb[6];
+    int nn = 0;
+    if (x > 0) nb[nn++] = i - 1;
+    if (x + 1 < W) nb[nn++] = i + 1;
+    if (y > 0) nb[nn++] = i - W;
+    if (y + 1 < H) nb[nn++] = i + W;
+    if (z > 0) nb[nn++] = i - HW;
+    if (z + 1 < D) nb[nn++] = i + HW;
+    update_core(m, phi, i, nb, nn, T, t, tag, r, d);
+}
+
+void orc3_halfstep(const orc_model* m, double* phi, const uint8_t* mask, int colour,
+                   const double* T_blk, const uint8_t* active, uint32_t t, uint32_t tag,
+                   uint32_t r, orc_diag* diag) {
+    const int D = m->D, H = m->H, W = m->W;
+    const int64_t HW = (int64_t)H * W;
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = (y + z + colour) & 1; x < W; x += 2) {
+                const int64_t i = (int64_t)z * HW + (int64_t)y * W + x;
+                if (!mask[i]) continue;
+                const int b = block3(m, z, y, x);
+                if (active && !active[b]) continue;
+                orc3_update_site(m, phi, mask, i, T_blk[b], t, tag, r, diag ? &diag[i] : NULL);
+            }
+}
+
+void orc3_init_block_mean(const orc_model* m, double* phi, const uint8_t* mask,
+                          const double* mean_angle, const int64_t* n_sample, double global_mean) {
+    const int64_t HW = (int64_t)m->H * m->W;
+    for (int z = 0; z < m->D; ++z)
+        for (int y = 0; y < m->H; ++y)
+            for (int x = 0; x < m->W; ++x) {
+                const int64_t i = (int64_t)z * HW + (int64_t)y * m->W + x;
+                if (!mask[i]) continue;
+                const int b = block3(m, z, y, x);
+                phi[i] = n_sample[b] > 0 ? mean_angle[b] : global_mean;
+            }
+}
+
+int orc3_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const double* T_blk,
+                      const double* Es, const int64_t* Nsp, const int64_t* Nb,
+                      const int64_t* n_gap, int32_t n_max, uint32_t r, int32_t* stop_sweep,
+                      double* e_trace) {
+    const int nblk = m->nblk;
+    double* E = (double*)malloc(sizeof(double) * nblk);
+    int8_t* sigma = (int8_t*)malloc(nblk);
+    uint8_t* active = (uint8_t*)malloc(nblk);
+    orc3_block_energy(m, phi, E);
+    if (e_trace)
+        for (int b = 0; b < nblk; ++b) e_trace[b] = Nb[b] > 0 ? E[b] / (double)Nb[b] : 0.0;
+    orc_stop_init(m, E, Es, Nsp, Nb, n_gap, sigma, active, stop_sweep);
+    int left = 0;
+    for (int b = 0; b < nblk; ++b) left += active[b];
+    int t = 0;
+    while (left > 0 && t < n_max) {
+        t += 1;
+        orc3_halfstep(m, phi, mask, 0, T_blk, active, (uint32_t)t, 0u, r, NULL);
+        orc3_halfstep(m, phi, mask, 1, T_blk, active, (uint32_t)t, 0u, r, NULL);
+        orc3_block_energy(m, phi, E);
+        if (e_trace)
+            for (int b = 0; b < nblk; ++b)
+                e_trace[(int64_t)t * nblk + b] = Nb[b] > 0 ? E[b] / (double)Nb[b] : 0.0;
+        left = orc_stop_update(m, t, n_max, E, Es, Nsp, Nb, sigma, active, stop_sweep);
+    }
+    free(E);
+    free(sigma);
+    free(active);
+    return t;
+}
+
+void orc3_calibrate(const orc_model* m, const double* phi_init, const uint8_t* mask,
+                    const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                    int32_t n_meas, int32_t n_bisect, int32_t chains, double T_lo, double T_hi,
+                    double* T_out) {
+    const int nblk = m->nblk;
+    const int64_t n = (int64_t)m->D * m->H * m->W;
+    double* lo = (double*)malloc(sizeof(double) * nblk);
+    double* hi = (double*)malloc(sizeof(double) * nblk);
+    double* T = (double*)malloc(sizeof(double) * nblk);
+    double* ebar = (double*)malloc(sizeof(double) * nblk);
+    double* E = (double*)malloc(sizeof(double) * nblk);
+    double* phi = (double*)malloc(sizeof(double) * n);
+    for (int b = 0; b < nblk; ++b) { lo[b] = T_lo; hi[b] = T_hi; }
+    for (int k = 0; k < n_bisect; ++k) {
+        for (int b = 0; b < nblk; ++b) T[b] = 0.5 * (lo[b] + hi[b]);
+        const double med = orc_median_targeted(nblk, T, Nsp);
+        for (int b = 0; b < nblk; ++b) {
+            if (Nsp[b] == 0) T[b] = med;
+            ebar[b] = 0.0;
+        }
+        for (int c = 0; c < chains; ++c) {
+            memcpy(phi, phi_init, sizeof(double) * n);
+            for (int s = 1; s <= n_eq + n_meas; ++s) {
+                orc3_halfstep(m, phi, mask, 0, T, NULL, (uint32_t)s, (uint32_t)(1 + k), (uint32_t)c, NULL);
+                orc3_halfstep(m, phi, mask, 1, T, NULL, (uint32_t)s, (uint32_t)(1 + k), (uint32_t)c, NULL);
+                if (s <= n_eq) continue;
+                orc3_block_energy(m, phi, E);
+                for (int b = 0; b < nblk; ++b)
+                    if (Nb[b] > 0) ebar[b] += E[b] / (double)Nb[b];
+            }
+        }
+        for (int b = 0; b < nblk; ++b) {
+            ebar[b] /= (double)n_meas * (double)chains;
+            if (Nsp[b] == 0) continue;
+            const double es = Es[b] / (double)Nsp[b];
+            if (ebar[b] < es) lo[b] = T[b]; else hi[b] = T[b];
+        }
+    }
+    for (int b = 0; b < nblk; ++b) T_out[b] = 0.5 * (lo[b] + hi[b]);
+    const double med = orc_median_targeted(nblk, T_out, Nsp);
+    for (int b = 0; b < nblk; ++b)
+        if (Nsp[b] == 0) T_out[b] = med;
+    free(lo); free(hi); free(T); free(ebar); free(E); free(phi);
 }
 
 /* Eqs. 3-4: AAE and RASE over the P prediction sites. */

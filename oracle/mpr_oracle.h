@@ -28,6 +28,7 @@ typedef struct {
     int32_t threads;         /* OpenMP threads (<=0: library default) */
     const double* T_site;    /* NULL: block temperatures (BST); else H*W site
                                 temperatures (SST, Sec. 2.2.3) used by the updates */
+    int32_t D, nbz;          /* 3-D grids (orc3_*): depth and block layers; 1 in 2-D */
 } orc_model;
 
 void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, double J,
@@ -149,6 +150,36 @@ double orc_median_targeted(int32_t nblk, const double* T, const int64_t* Nsp);
 /* Sec. 3.2, Eqs. 3-4 over the gap sites. */
 void orc_scores(int64_t n, const float* pred, const float* truth, const uint8_t* mask,
                 double* aae, double* rase);
+
+/* ---- 3-D grids (space-time extension named in Sec. 4) ----
+ * Sites (z, y, x) of a D x H x W grid, index i = (z H + y) W + x, colour
+ * (x + y + z) mod 2, cubic blocks of side lb numbered ((z/lb) nby + y/lb) nbx
+ * + x/lb. Every site owns its +x, +y and +z bonds (6-neighbour MPR
+ * Hamiltonian, open boundaries). Everything else (random numbers keyed by
+ * the site index, Metropolis + over-relaxation, the stop rule, calibration)
+ * is the 2-D method; D = 1 gives back the 2-D functions' results. Arrays are
+ * D*H*W (sites) or nblk = nbx nby nbz (blocks). */
+void orc3_model_init(orc_model* m, int32_t D, int32_t H, int32_t W, int32_t lb, double q,
+                     double J, uint64_t seed, uint32_t slice);
+void orc3_block_stats(const orc_model* m, const double* phi, const uint8_t* mask, double* Es,
+                      int64_t* Nsp, int64_t* Nb, double* mean_angle, int64_t* n_gap,
+                      int64_t* n_sample, double* global_mean);
+void orc3_block_energy(const orc_model* m, const double* phi, double* E);
+void orc3_update_site(const orc_model* m, double* phi, const uint8_t* mask, int64_t i, double T,
+                      uint32_t t, uint32_t tag, uint32_t r, orc_diag* d);
+void orc3_halfstep(const orc_model* m, double* phi, const uint8_t* mask, int colour,
+                   const double* T_blk, const uint8_t* active, uint32_t t, uint32_t tag,
+                   uint32_t r, orc_diag* diag);
+void orc3_init_block_mean(const orc_model* m, double* phi, const uint8_t* mask,
+                          const double* mean_angle, const int64_t* n_sample, double global_mean);
+int orc3_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const double* T_blk,
+                      const double* Es, const int64_t* Nsp, const int64_t* Nb,
+                      const int64_t* n_gap, int32_t n_max, uint32_t r, int32_t* stop_sweep,
+                      double* e_trace);
+void orc3_calibrate(const orc_model* m, const double* phi_init, const uint8_t* mask,
+                    const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                    int32_t n_meas, int32_t n_bisect, int32_t chains, double T_lo, double T_hi,
+                    double* T_out);
 
 #ifdef __cplusplus
 }
