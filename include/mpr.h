@@ -374,6 +374,53 @@ mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_t* mask, co
                                    float* mean_angle, int32_t* n_gap, double* zrange,
                                    void* cuda_stream);
 
+/* ---- 3-D grids (the space / space-time extension of Sec. 4) ----
+ * A D x H x W grid, site (z, y, x) at index (z H + y) W + x, 6-neighbour
+ * bonds of Eq. 1 with open boundaries, cubic blocks of side `block`
+ * numbered ((z/lb) nby + y/lb) nbx + x/lb; every site owns its +x, +y, +z
+ * bonds; checkerboard colour (x + y + z) mod 2. Everything else is the 2-D
+ * method: Sec. 2.1 transform, Eq. 2 per block, per-block bisection
+ * (calibration options as mpr_options), local-equilibrium realizations
+ * from the block-mean start with the per-block stop (Sec. 3.4), the mean
+ * back-transformed. Random numbers: counter (site index, t | tag << 16,
+ * r / 2, 0), words 2 (r mod 2) and 2 (r mod 2) + 1, key (seed_lo, seed_hi ^
+ * slice_id). FP32 state; the storage, group, cal_mode / cal_method, SST and
+ * sim_graph options do not apply. Realizations of one call carry indices
+ * r_next, r_next + 1, ... with r_next the accumulated count rounded up to
+ * even. Arrays are D*H*W (sites, row-major) or nblk (blocks); pointers
+ * host or device. Errors: as the 2-D calls. */
+typedef struct {
+    int32_t depth, height, width; /* D, H, W >= 1, D*H*W < 2^31 */
+    int32_t block;                /* l_b >= 1 */
+} mpr_grid3;
+
+typedef struct {
+    int32_t depth, height, width, block, nblk;
+    int64_t n_gap;
+    double zmin, zmax;
+    int64_t realizations, gap_updates, cal_gap_updates;
+} mpr3_info;
+
+typedef struct mpr3_ctx mpr3_ctx;
+
+mpr_status mpr3_create(const mpr_grid3* grid, const uint8_t* mask, const float* values,
+                       const mpr_options* options, mpr3_ctx** out);
+void mpr3_destroy(mpr3_ctx* ctx);
+const char* mpr3_last_error(const mpr3_ctx* ctx);
+mpr_status mpr3_get_info(const mpr3_ctx* ctx, mpr3_info* info);
+mpr_status mpr3_get_block_stats(mpr3_ctx* ctx, double* Es, int32_t* Nsp, int32_t* Nb,
+                                float* mean_angle, int32_t* n_gap);
+mpr_status mpr3_calibrate(mpr3_ctx* ctx, float* block_T_out);
+mpr_status mpr3_set_temperatures(mpr3_ctx* ctx, const float* block_T);
+mpr_status mpr3_simulate(mpr3_ctx* ctx, int32_t n_realizations);
+mpr_status mpr3_predict(mpr3_ctx* ctx, float* out, const float* truth, double* aae_rase);
+/* step-wise pieces (as the 2-D ones): a batch, one half-step, state access */
+mpr_status mpr3_sim_begin(mpr3_ctx* ctx, int32_t n_realizations);
+mpr_status mpr3_halfstep(mpr3_ctx* ctx, int32_t colour, int32_t t, int32_t tag);
+mpr_status mpr3_get_state(mpr3_ctx* ctx, int32_t r, float* angles);
+mpr_status mpr3_set_state(mpr3_ctx* ctx, int32_t r, const float* angles);
+mpr_status mpr3_sim_end(mpr3_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

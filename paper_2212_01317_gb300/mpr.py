@@ -28,6 +28,9 @@ EXPORTS = [
     "mpr_set_accumulator", "mpr_smooth_temperatures", "mpr_set_site_temperatures",
     "mpr_get_site_temperatures", "mpr_energy_moments", "mpr_energy_vjp", "mpr_create_batch",
     "mpr_predict_batch", "mpr_get_slice_layout", "mpr_autotune",
+    "mpr3_create", "mpr3_destroy", "mpr3_last_error", "mpr3_get_info", "mpr3_get_block_stats",
+    "mpr3_calibrate", "mpr3_set_temperatures", "mpr3_simulate", "mpr3_predict", "mpr3_sim_begin",
+    "mpr3_halfstep", "mpr3_get_state", "mpr3_set_state", "mpr3_sim_end",
 ]
 MPR_NOALLOC_MAX_BLOCKS = 65536
 
@@ -51,6 +54,18 @@ class mpr_profile(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("sim_halfstep_launches", C.c_int64),
                 ("cal_halfstep_launches", C.c_int64), ("sim_halfstep_ms", C.c_double),
                 ("cal_halfstep_ms", C.c_double)]
+
+
+class mpr_grid3(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("height", C.c_int32), ("width", C.c_int32),
+                ("block", C.c_int32)]
+
+
+class mpr3_info(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("height", C.c_int32), ("width", C.c_int32),
+                ("block", C.c_int32), ("nblk", C.c_int32), ("n_gap", C.c_int64),
+                ("zmin", C.c_double), ("zmax", C.c_double), ("realizations", C.c_int64),
+                ("gap_updates", C.c_int64), ("cal_gap_updates", C.c_int64)]
 
 
 class mpr_tuning(C.Structure):
@@ -133,6 +148,20 @@ def load(path: str | None = None):
         "mpr_predict_batch": (st, [P, P, P, P]),
         "mpr_get_slice_layout": (st, [P, P]),
         "mpr_autotune": (st, [P, i32, i32, C.POINTER(mpr_tuning)]),
+        "mpr3_create": (st, [C.POINTER(mpr_grid3), P, P, C.POINTER(mpr_options), C.POINTER(P)]),
+        "mpr3_destroy": (None, [P]),
+        "mpr3_last_error": (C.c_char_p, [P]),
+        "mpr3_get_info": (st, [P, C.POINTER(mpr3_info)]),
+        "mpr3_get_block_stats": (st, [P, P, P, P, P, P]),
+        "mpr3_calibrate": (st, [P, P]),
+        "mpr3_set_temperatures": (st, [P, P]),
+        "mpr3_simulate": (st, [P, i32]),
+        "mpr3_predict": (st, [P, P, P, P]),
+        "mpr3_sim_begin": (st, [P, i32]),
+        "mpr3_halfstep": (st, [P, i32, i32, i32]),
+        "mpr3_get_state": (st, [P, i32, P]),
+        "mpr3_set_state": (st, [P, i32, P]),
+        "mpr3_sim_end": (st, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -504,4 +533,95 @@ class BatchFiller:
         grid = canvas_blocks.reshape(self.info.nby, self.info.nbx)
         return grid[y0 // lb:y0 // lb + (h + lb - 1) // lb,
                     x0 // lb:x0 // lb + (w + lb - 1) // lb].ravel()
+
+
+def _check3(ctx, status: int):
+    if status != MPR_OK:
+        msg = load().mpr3_last_error(ctx).decode() if ctx else ""
+        raise MprError(status, msg or load().mpr_status_string(status).decode())
+
+
+class GapFiller3:
+    """A D x H x W field (the 3-D extension); numpy in, numpy out."""
+
+    def __init__(self, values, mask, block: int, **options):
+        values = np.ascontiguousarray(values, dtype=np.float32)
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        self.D, self.H, self.W = mask.shape
+        self.opt = mpr_default_options(**options)
+        out = C.c_void_p()
+        g = mpr_grid3(self.D, self.H, self.W, block)
+        st = load().mpr3_create(C.byref(g), _ptr(mask), _ptr(values), C.byref(self.opt),
+                                C.byref(out))
+        if st != MPR_OK:
+            raise MprError(st, load().mpr_status_string(st).decode())
+        self.ctx = out
+        self.info = self.refresh()
+
+    def refresh(self) -> mpr3_info:
+        info = mpr3_info()
+        _check3(self.ctx, load().mpr3_get_info(self.ctx, C.byref(info)))
+        self.info = info
+        return info
+
+    @property
+    def nblk(self) -> int:
+        return self.info.nblk
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().mpr3_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def block_stats(self):
+        n = self.nblk
+        Es, Nsp, Nb = np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.int32)
+        ma, ng = np.zeros(n, np.float32), np.zeros(n, np.int32)
+        _check3(self.ctx, load().mpr3_get_block_stats(self.ctx, _ptr(Es), _ptr(Nsp), _ptr(Nb),
+                                                      _ptr(ma), _ptr(ng)))
+        return Es, Nsp, Nb, ma, ng
+
+    def calibrate(self) -> np.ndarray:
+        T = np.zeros(self.nblk, np.float32)
+        _check3(self.ctx, load().mpr3_calibrate(self.ctx, _ptr(T)))
+        return T
+
+    def set_temperatures(self, T):
+        _check3(self.ctx, load().mpr3_set_temperatures(
+            self.ctx, _ptr(np.ascontiguousarray(T, dtype=np.float32))))
+
+    def simulate(self, n: int):
+        _check3(self.ctx, load().mpr3_simulate(self.ctx, int(n)))
+
+    def predict(self, truth=None):
+        out = np.zeros((self.D, self.H, self.W), np.float32)
+        err = np.zeros(2)
+        tr = None if truth is None else np.ascontiguousarray(truth, dtype=np.float32)
+        _check3(self.ctx, load().mpr3_predict(self.ctx, _ptr(out), _ptr(tr),
+                                              None if tr is None else _ptr(err)))
+        return out, (None if tr is None else (float(err[0]), float(err[1])))
+
+    def sim_begin(self, n: int):
+        _check3(self.ctx, load().mpr3_sim_begin(self.ctx, int(n)))
+
+    def sim_end(self):
+        _check3(self.ctx, load().mpr3_sim_end(self.ctx))
+
+    def halfstep(self, colour: int, t: int, tag: int = 0):
+        _check3(self.ctx, load().mpr3_halfstep(self.ctx, colour, t, tag))
+
+    def get_state(self, r: int) -> np.ndarray:
+        out = np.zeros((self.D, self.H, self.W), np.float32)
+        _check3(self.ctx, load().mpr3_get_state(self.ctx, r, _ptr(out)))
+        return out
+
+    def set_state(self, r: int, angles):
+        _check3(self.ctx, load().mpr3_set_state(
+            self.ctx, r, _ptr(np.ascontiguousarray(angles, dtype=np.float32))))
 

@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "mpr.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mpr_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mpr3?_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_bound_names():
@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
     out = subprocess.run(["nm", "-D", "--defined-only", mpr._build.LIB], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r" T (mpr_\w+)", out))
+    exported = set(re.findall(r" T (mpr3?_\w+)", out))
     assert set(declared_functions()) <= exported
 
 
@@ -46,6 +46,11 @@ def test_struct_layout_matches_c(tmp_path):
 int main(void) {
   printf("mpr_grid %zu\\nmpr_options %zu\\nmpr_info %zu\\n", sizeof(mpr_grid),
          sizeof(mpr_options), sizeof(mpr_info));
+  printf("mpr_grid3 %zu\\nmpr3_info %zu\\nmpr_tuning %zu\\nmpr_profile %zu\\n",
+         sizeof(mpr_grid3), sizeof(mpr3_info), sizeof(mpr_tuning), sizeof(mpr_profile));
+  O(mpr_options, cal_method); O(mpr_options, t_init); O(mpr_options, sim_graph);
+  O(mpr_info, n_slices); O(mpr3_info, n_gap); O(mpr3_info, cal_gap_updates);
+  O(mpr_tuning, ms);
   O(mpr_options, seed); O(mpr_options, slice_id); O(mpr_options, t_lo);
   O(mpr_options, group); O(mpr_options, cuda_stream);
   O(mpr_info, n_gap); O(mpr_info, zmin); O(mpr_info, realizations); O(mpr_info, batch);
@@ -61,6 +66,8 @@ int main(void) {
     assert int(got["mpr_grid"]) == ctypes.sizeof(mpr.mpr_grid)
     assert int(got["mpr_options"]) == ctypes.sizeof(mpr.mpr_options)
     assert int(got["mpr_info"]) == ctypes.sizeof(mpr.mpr_info)
+    for T in ("mpr_grid3", "mpr3_info", "mpr_tuning", "mpr_profile"):
+        assert int(got[T]) == ctypes.sizeof(getattr(mpr, T)), T
     for k, v in got.items():
         if "." in k:
             T, f = k.split(".")

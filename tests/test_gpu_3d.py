@@ -1,0 +1,145 @@
+"""3-D grids on the GPU (mpr3_* calls) against the 3-D oracle.
+
+  * Eq. 2 statistics per cubic block;
+  * one half-step element by element for every gap site of a colour, with
+    the same Philox draws (decisions within rounding of their threshold may
+    flip, as in 2-D);
+  * calibration and the full pipeline;
+  * a grid one layer deep gives the 2-D library's predictions.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_01317_gb300 import synth
+from paper_2212_01317_gb300.mpr import GapFiller, GapFiller3
+
+from parity import TWO_PI, compare_site_updates
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def field3(D, H, W, p, seed):
+    rng = np.random.default_rng(seed)
+    base = np.stack([synth.grf(H, W, 4.0, seed + k) for k in range(D)])
+    z = (base + 0.3 * rng.normal(size=base.shape)).astype(np.float32)
+    m = (rng.uniform(size=(D, H, W)) < p).astype(np.uint8)
+    return z, m
+
+
+def values_of(z, m):
+    return np.where(m != 0, np.nan, z).astype(np.float32)
+
+
+@pytest.mark.parametrize("D,H,W,lb", [(6, 9, 11, 4), (16, 16, 16, 8), (3, 20, 7, 5)])
+def test_block_stats_match_oracle(D, H, W, lb):
+    z, m = field3(D, H, W, 0.45, D * H)
+    gf = GapFiller3(values_of(z, m), m, lb)
+    o = oracle.Oracle3(D, H, W, lb)
+    phi, *_ = oracle.Oracle.transform(z.reshape(D * H, W), m.reshape(D * H, W))
+    st = o.block_stats(phi.reshape(D, H, W), m)
+    Es, Nsp, Nb, ma, ng = gf.block_stats()
+    np.testing.assert_allclose(Es, st.Es, rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(Nsp, st.Nsp)
+    np.testing.assert_array_equal(Nb, st.Nb)
+    np.testing.assert_array_equal(ng, st.n_gap)
+    want = np.where(st.n_sample > 0, st.mean_angle, st.global_mean)
+    np.testing.assert_allclose(ma, want, rtol=1e-6, atol=1e-6)
+    gf.close()
+
+
+@pytest.mark.parametrize("R", [1, 6])
+@pytest.mark.parametrize("colour", [0, 1])
+def test_halfstep_lockstep(R, colour):
+    D, H, W, lb = 7, 10, 12, 4
+    z, m = field3(D, H, W, 0.55, 3 + colour)
+    gf = GapFiller3(values_of(z, m), m, lb, seed=0x3D3D)
+    o = oracle.Oracle3(D, H, W, lb, seed=0x3D3D)
+    rng = np.random.default_rng(5)
+    T = rng.uniform(0.03, 1.0, gf.nblk).astype(np.float32)
+    gf.set_temperatures(T)
+    gf.sim_begin(R)
+    pre = []
+    for r in range(R):
+        s = gf.get_state(r)
+        s[m != 0] = rng.uniform(0, TWO_PI, int((m != 0).sum())).astype(np.float32)
+        gf.set_state(r, s)
+        pre.append(s)
+    gf.halfstep(colour, 13, 2)
+    cz, cy, cx = np.mgrid[0:D, 0:H, 0:W]
+    may = (m != 0) & (((cx + cy + cz) & 1) == colour)
+    total = flips = 0
+    for r in range(R):
+        post = gf.get_state(r)
+        ph = pre[r].astype(np.float64)
+        diag = o.halfstep(ph, m, colour, T.astype(np.float64), t=13, tag=2, r=r,
+                          diag=True).reshape(D, H, W)
+        n, f, bad, msg = compare_site_updates(post, ph, pre[r], diag, may)
+        assert bad == 0, f"r={r}: {msg}"
+        total += n
+        flips += f
+    assert total > 50 * R
+    assert flips <= max(2, total // 2000)
+    gf.sim_end()
+    gf.close()
+
+
+def test_pipeline_matches_oracle_given_T():
+    D, H, W, lb, R = 6, 12, 14, 4, 4
+    z, m = field3(D, H, W, 0.5, 11)
+    rng = np.random.default_rng(2)
+    gf = GapFiller3(values_of(z, m), m, lb, seed=21, n_max=40)
+    T = rng.uniform(0.03, 0.4, gf.nblk).astype(np.float32)
+    gf.set_temperatures(T)
+    gf.simulate(R)
+    pred, (aae, rase) = gf.predict(z)
+    ref = oracle.gapfill3(z, m, lb, R=R, seed=21, n_max=40, T_blk=T.astype(np.float64))
+    g = m != 0
+    scale = float(z[~g].max() - z[~g].min())
+    close = np.abs(pred - ref.pred) <= 1e-4 * scale
+    assert np.array_equal(pred[~g], z[~g])
+    a_ref = np.abs(ref.pred - z)[g].mean()
+    if close[g].all():
+        assert abs(aae - a_ref) <= 1e-4 * a_ref
+        assert gf.refresh().gap_updates == ref.gap_updates
+    else:
+        assert close[g].mean() > 0.9
+        assert abs(aae - a_ref) <= 0.05 * a_ref
+    gf.close()
+
+
+def test_calibration_matches_oracle():
+    D, H, W, lb = 8, 8, 16, 4
+    z, m = field3(D, H, W, 0.45, 17)
+    opts = dict(seed=4, n_bisect=10, n_eq=6, n_meas=6)
+    gf = GapFiller3(values_of(z, m), m, lb, **opts)
+    Tg = gf.calibrate()
+    ref = oracle.gapfill3(z, m, lb, R=0, seed=4, n_bisect=10, n_eq=6, n_meas=6)
+    assert (np.abs(Tg - ref.T) <= 1e-4 * ref.T).mean() >= 0.9
+    gf.close()
+
+
+def test_one_layer_equals_the_2d_library():
+    H, W, lb, R = 40, 36, 8, 5
+    z, m = synth.small_problem(H, W, 0.5, seed=12)
+    v = values_of(z, m)
+    T = np.random.default_rng(0).uniform(0.05, 0.3, (H // lb) * ((W + lb - 1) // lb)).astype(np.float32)
+    g2 = GapFiller(v, m, lb, seed=8, n_max=30)
+    g2.set_temperatures(T)
+    g2.simulate(R)
+    p2, _ = g2.predict()
+    g2.close()
+    g3 = GapFiller3(v[None], m[None], lb, seed=8, n_max=30)
+    g3.set_temperatures(T)
+    g3.simulate(R)
+    p3, _ = g3.predict()
+    g3.close()
+    scale = float(z[m == 0].max() - z[m == 0].min())
+    assert (np.abs(p3[0] - p2) <= 1e-5 * scale)[m != 0].mean() >= 0.98
