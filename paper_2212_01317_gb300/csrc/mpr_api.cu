@@ -380,7 +380,7 @@ mpr_status energy_pass(mpr_ctx* ctx) {
     for (int c = 0; c < 2; ++c) {
         SweepArgs a = sweep_args(ctx, c, false);
         a.R = ctx->Rp;
-        launch_energy(a, ctx->G, ctx->storage, ctx->n_sm * 8, ctx->s);
+        launch_energy(a, ctx->G, ctx->storage, ctx->n_sm, ctx->s);
         CKL();
     }
     return MPR_OK;
@@ -561,17 +561,34 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     CKL();
     TRY(init_batch_state(ctx));
     TRY(energy_pass(ctx));
-    for (int sw = 1; sw <= o.n_eq + o.n_meas; ++sw) {
+    // Sweep sw's changes go to eacc buffer sw & 1; the colour-0 launch of
+    // sweep sw + 1 folds them (extra CTAs), the last sweep's fold runs alone.
+    const size_t blk = (size_t)g.nblk * ctx->Rp;
+    const int n_sw = o.n_eq + o.n_meas;
+    for (int sw = 1; sw <= n_sw; ++sw) {
         for (int c = 0; c < 2; ++c) {
             SweepArgs a = sweep_args(ctx, c, false);
             a.t_fixed = sw;
+            a.eacc = ctx->eacc + (size_t)(sw & 1) * blk;
+            FoldArgs f{};
+            if (c == 0 && sw > 1) {
+                f.ctas = (g.nblk + 255) / 256;
+                f.nblk = g.nblk;
+                f.Rp = ctx->Rp;
+                f.chains = o.cal_chains;
+                f.measure = (sw - 1) > o.n_eq;
+                f.inb = ctx->inb;
+                f.eacc = ctx->eacc + (size_t)((sw - 1) & 1) * blk;
+                f.ecur = ctx->ecur;
+                f.ebar = ctx->ebar;
+            }
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (timed && ctx->opt.profile) {
                 e0 = get_event(ctx);
                 e1 = get_event(ctx);
                 if (e0) cudaEventRecord(e0, ctx->s);
             }
-            launch_sweep_flat(a, ctx->G, ctx->n_gap[c], ctx->s);
+            launch_sweep_flat(a, ctx->G, ctx->n_gap[c], ctx->s, f.ctas ? &f : nullptr);
             CKL();
             if (e0 && e1) {
                 cudaEventRecord(e1, ctx->s);
@@ -579,10 +596,10 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
             }
             ++ctx->cal_halfstep_launches;
         }
-        launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, sw, ctx->ctl, ctx->inb, ctx->eacc,
-                        ctx->ecur, ctx->ebar, ctx->s);
-        CKL();
     }
+    launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, n_sw, ctx->ctl, ctx->inb,
+                    ctx->eacc + (size_t)(n_sw & 1) * blk, ctx->ecur, ctx->ebar, ctx->s);
+    CKL();
     launch_cal_update(g.nblk, inv_count, ctx->es, ctx->Nsp, ctx->T, ctx->lo, ctx->hi, ctx->ebar,
                       ctx->ctl, o.n_bisect, cond, ctx->s);
     CKL();

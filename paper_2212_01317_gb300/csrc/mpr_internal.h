@@ -135,6 +135,17 @@ struct SweepArgs {
     int t_fixed;              // > 0: sweep index of this launch (else read from ctl)
 };
 
+// The calibration's per-sweep fold (E_b += the sweep's change; the measured
+// sweeps' e_b summed), run by extra CTAs of the next half-step's launch.
+struct FoldArgs {
+    int ctas;                 // CTAs of the launch that fold (0: none)
+    int nblk, Rp, chains, measure;
+    const double* inb;        // [nblk] 1 / N_b
+    float* eacc;              // [nblk][Rp] change of the sweep being folded (cleared)
+    double* ecur;             // [nblk][Rp]
+    double* ebar;             // [nblk]
+};
+
 // Grid-wide barrier state of a cooperative launch (zeroed before each launch).
 struct GridBarrier {
     unsigned int arrive;   // CTAs arrived at the current barrier

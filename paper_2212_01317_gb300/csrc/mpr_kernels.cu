@@ -348,8 +348,29 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 8 : 2) k_sweep(Sweep
         sweep_item<G, S>(a, work ? (int)work[it] : it, wi, WPI, ctr1);
 }
 
+// The last f.ctas CTAs (of blockIdx.y = 0) fold the previous sweep's block
+// energies instead: they touch eacc of the other parity and ecur, which the
+// half-step does not.
 template <int G>
-__global__ void __launch_bounds__(kFlatThreads) k_sweep_flat(SweepArgs a, int64_t n_list) {
+__global__ void __launch_bounds__(kFlatThreads) k_sweep_flat(SweepArgs a, int64_t n_list,
+                                                            FoldArgs f) {
+    const int sweep_ctas = (int)gridDim.x - f.ctas;
+    if ((int)blockIdx.x >= sweep_ctas) {
+        if (blockIdx.y != 0) return;
+        for (int b = ((int)blockIdx.x - sweep_ctas) * kFlatThreads + threadIdx.x; b < f.nblk;
+             b += f.ctas * kFlatThreads) {
+            double s = 0.0;
+            for (int r = 0; r < f.chains; ++r) {
+                const size_t k = (size_t)b * f.Rp + r;
+                const double E = f.ecur[k] + (double)f.eacc[k];
+                f.ecur[k] = E;
+                f.eacc[k] = 0.0f;
+                s += E * f.inb[b];
+            }
+            if (f.measure) f.ebar[b] += s;
+        }
+        return;
+    }
     const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
     sweep_flat<G>(a, n_list, t | (a.ctl->tag << 16));
 }
@@ -361,8 +382,8 @@ __global__ void __launch_bounds__(128) k_energy(SweepArgs a) {
         energy_item<G, S>(a, it, threadIdx.x >> 5, 4);
 }
 
-template __global__ void k_sweep_flat<2>(SweepArgs, int64_t);
-template __global__ void k_sweep_flat<8>(SweepArgs, int64_t);
+template __global__ void k_sweep_flat<2>(SweepArgs, int64_t, FoldArgs);
+template __global__ void k_sweep_flat<8>(SweepArgs, int64_t, FoldArgs);
 
 // ------------------------------------------------------------------ stop --
 // es[b] = E_s,b / N_SP,b (0 without sample bonds) and inb[b] = 1 / N_b (0 for
@@ -1050,20 +1071,29 @@ int sweep_blocks_per_sm(int G, int storage, bool wide) {
 
 int sweep_items_per_cta(int G, bool wide) { return (G == 2 && !wide) ? 4 : 1; }
 
-void launch_energy(const SweepArgs& a, int G, int storage, int grid, cudaStream_t s) {
+void launch_energy(const SweepArgs& a, int G, int storage, int n_sm, cudaStream_t s) {
     with_storage(storage, [&](auto tag) {
         using S = typename decltype(tag)::type;
+        // As many CTAs as fit on the GPU at once (the kernel loops over items).
+        int per_sm = 0;
+        if (G == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<2, S>, 128, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy<8, S>, 128, 0);
+        const int grid = n_sm * (per_sm > 0 ? per_sm : 8);
         if (G == 2) k_energy<2, S><<<grid, 128, 0, s>>>(a);
         else k_energy<8, S><<<grid, 128, 0, s>>>(a);
     });
 }
 
-void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s) {
-    if (n_list == 0) return;
+void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s,
+                       const FoldArgs* fold) {
+    FoldArgs f{};
+    if (fold) f = *fold;
+    if (n_list == 0 && f.ctas == 0) return;
     const int64_t threads = n_list * (G / 2);
-    const dim3 grid((unsigned)((threads + kFlatThreads - 1) / kFlatThreads), (unsigned)a.groups);
-    if (G == 2) k_sweep_flat<2><<<grid, kFlatThreads, 0, s>>>(a, n_list);
-    else k_sweep_flat<8><<<grid, kFlatThreads, 0, s>>>(a, n_list);
+    const dim3 grid((unsigned)((threads + kFlatThreads - 1) / kFlatThreads + f.ctas),
+                    (unsigned)a.groups);
+    if (G == 2) k_sweep_flat<2><<<grid, kFlatThreads, 0, s>>>(a, n_list, f);
+    else k_sweep_flat<8><<<grid, kFlatThreads, 0, s>>>(a, n_list, f);
 }
 
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,

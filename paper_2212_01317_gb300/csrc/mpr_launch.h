@@ -36,8 +36,10 @@ void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, 
 void launch_sweep(const SweepArgs& a, int G, int storage, bool wide, int grid, cudaStream_t s);
 int sweep_blocks_per_sm(int G, int storage, bool wide);
 int sweep_items_per_cta(int G, bool wide);
-void launch_energy(const SweepArgs& a, int G, int storage, int grid, cudaStream_t s);
-void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s);
+void launch_energy(const SweepArgs& a, int G, int storage, int n_sm, cudaStream_t s);
+// fold: NULL, or the previous sweep's fold run by extra CTAs of this launch.
+void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s,
+                       const FoldArgs* fold = nullptr);
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
                        cudaStream_t s);
 // tcount is [n_slices][Rp]: running targeted blocks per slice and realization.
