@@ -92,6 +92,8 @@ def lib():
             "orc_median_targeted": (f64, [i32, P, P]),
             "orc_scores": (None, [i64, P, P, P, P, P]),
             "orc_sst_temperatures": (None, [MP, P, i32, i32, P]),
+            "orc_calibrate_points": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, i32, f64, f64,
+                                            P]),
             "orc3_model_init": (None, [MP, i32, i32, i32, i32, f64, f64, u64, u32]),
             "orc3_block_stats": (None, [MP, P, P, P, P, P, P, P, P, P]),
             "orc3_block_energy": (None, [MP, P, P]),
@@ -328,6 +330,16 @@ class Oracle:
                                    _p(st.Nb), n_eq, n_meas, n_newton, chains, T_lo, T_hi, T0,
                                    _p(T), None if tr is None else _p(tr))
         return (T, tr) if trace else T
+
+    def calibrate_points(self, phi_init, mask, st: BlockStats, n_eq=25, n_meas=20, n_iter=16,
+                         chains=1, points=2, T_lo=1e-4, T_hi=2.0):
+        ph = np.ascontiguousarray(phi_init, dtype=np.float64)
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.zeros(self.nblk)
+        lib().orc_calibrate_points(C.byref(self.m), _p(ph), _p(mk), _p(st.Es), _p(st.Nsp),
+                                   _p(st.Nb), n_eq, n_meas, n_iter, chains, points, T_lo, T_hi,
+                                   _p(T))
+        return T
 
     @staticmethod
     def median_targeted(T, Nsp) -> float:

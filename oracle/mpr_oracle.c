@@ -529,6 +529,69 @@ void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* ma
 }
 
 /* ----------------------------------------------------------------- scores -- */
+void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint8_t* mask,
+                          const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                          int32_t n_meas, int32_t n_iter, int32_t chains, int32_t points,
+                          double T_lo, double T_hi, double* T_out) {
+    const int nblk = m->nblk;
+    const int64_t n = (int64_t)m->H * m->W;
+    double* lo = (double*)malloc(sizeof(double) * nblk);
+    double* hi = (double*)malloc(sizeof(double) * nblk);
+    double* T = (double*)malloc(sizeof(double) * nblk * (size_t)points);
+    double* ebar = (double*)malloc(sizeof(double) * nblk * (size_t)points);
+    double* E = (double*)malloc(sizeof(double) * nblk);
+    double* phi = (double*)malloc(sizeof(double) * n);
+    for (int b = 0; b < nblk; ++b) { lo[b] = T_lo; hi[b] = T_hi; }
+    for (int k = 0; k < n_iter; ++k) {
+        for (int p = 0; p < points; ++p) {
+            double* Tp = T + (int64_t)p * nblk;
+            for (int b = 0; b < nblk; ++b)
+                Tp[b] = lo[b] + (double)(p + 1) * (hi[b] - lo[b]) / (double)(points + 1);
+            const double med = orc_median_targeted(nblk, Tp, Nsp);
+            for (int b = 0; b < nblk; ++b) {
+                if (Nsp[b] == 0) Tp[b] = med;
+                ebar[(int64_t)p * nblk + b] = 0.0;
+            }
+        }
+        for (int c = 0; c < chains; ++c)
+            for (int p = 0; p < points; ++p) {
+                const double* Tp = T + (int64_t)p * nblk;
+                const uint32_t r = (uint32_t)(c * points + p);
+                memcpy(phi, phi_init, sizeof(double) * n);
+                for (int s = 1; s <= n_eq + n_meas; ++s) {
+                    orc_halfstep(m, phi, mask, 0, Tp, NULL, (uint32_t)s, (uint32_t)(1 + k), r, NULL);
+                    orc_halfstep(m, phi, mask, 1, Tp, NULL, (uint32_t)s, (uint32_t)(1 + k), r, NULL);
+                    if (s <= n_eq) continue;
+                    orc_block_energy(m, phi, E);
+                    for (int b = 0; b < nblk; ++b)
+                        if (Nb[b] > 0) ebar[(int64_t)p * nblk + b] += E[b] / (double)Nb[b];
+                }
+            }
+        for (int b = 0; b < nblk; ++b) {
+            if (Nsp[b] == 0) continue;
+            const double es = Es[b] / (double)Nsp[b];
+            double nlo = lo[b], nhi = hi[b];
+            for (int p = 0; p < points; ++p) {
+                const double e = ebar[(int64_t)p * nblk + b] / ((double)n_meas * (double)chains);
+                const double tp = T[(int64_t)p * nblk + b];
+                if (e < es) { if (tp > nlo) nlo = tp; }
+                else if (tp < nhi) nhi = tp;
+            }
+            if (nlo > nhi) {   /* the means crossed on noise: keep the points' span */
+                nlo = T[b];
+                nhi = T[(int64_t)(points - 1) * nblk + b];
+            }
+            lo[b] = nlo;
+            hi[b] = nhi;
+        }
+    }
+    for (int b = 0; b < nblk; ++b) T_out[b] = 0.5 * (lo[b] + hi[b]);
+    const double med = orc_median_targeted(nblk, T_out, Nsp);
+    for (int b = 0; b < nblk; ++b)
+        if (Nsp[b] == 0) T_out[b] = med;
+    free(lo); free(hi); free(T); free(ebar); free(E); free(phi);
+}
+
 /* --------------------------------------------- moments and Newton (f1) -- */
 
 void orc_energy_moments(const orc_model* m, double* phi, const uint8_t* mask, const double* T,

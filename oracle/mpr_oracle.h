@@ -114,6 +114,21 @@ void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* ma
                    const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
                    int32_t n_meas, int32_t n_bisect, int32_t chains, double T_lo, double T_hi,
                    double* T_out, double* ebar_trace);
+/* Calibration by k-section (points = 1: the bisection above; points = 2:
+ * trisection): iteration k evaluates every targeted block at the `points`
+ * temperatures splitting its bracket into points + 1 equal parts (untargeted
+ * blocks at the median of the targeted blocks' temperatures of the same
+ * point), with `chains` fresh chains per point (realization index
+ * c * points + p for chain c at point p, tag 1 + k), and keeps the part of
+ * the bracket between the highest point whose mean e_b is below e_s,b and
+ * the lowest point whose mean is not (between the first and last point if
+ * noise makes those cross). T_out: bracket midpoints, untargeted blocks at
+ * the median. */
+void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint8_t* mask,
+                          const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                          int32_t n_meas, int32_t n_iter, int32_t chains, int32_t points,
+                          double T_lo, double T_hi, double* T_out);
+
 /* Energy moments of the calibration chains at block temperatures T[nblk]
  * (the energy matching of Sec. 2.1 / 2.2.2, with the fluctuation identity
  * for its derivative): chain c (c < chains) of phi[c][H*W] runs sweeps

@@ -329,12 +329,14 @@ int sweep_grid(mpr_ctx* ctx, bool wide) {
     return (int)std::max<unsigned long long>(1, std::min<unsigned long long>(full, need));
 }
 
-// Grid of the stop kernels: a thread per (item, lane) or per item, capped.
+// Grid of the stop kernels: a thread per (item, lane) or per item, at most
+// two CTAs per SM (the kernels loop; the closing kernel's CTAs each take one
+// ticket from a single counter, so fewer CTAs wait less on it).
 int stop_grid(mpr_ctx* ctx, int64_t per_item) {
     const int64_t items = std::min<int64_t>((int64_t)ctx->g.nblk * ctx->groups,
                                             (int64_t)std::min<unsigned long long>(ctx->bound, 1ull << 40));
     const int64_t n = std::max<int64_t>(1, items * per_item);
-    return (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->n_sm * 16);
+    return (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->n_sm * 2);
 }
 
 cudaEvent_t get_event(mpr_ctx* ctx) {
@@ -1453,7 +1455,7 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
     // copied to pinned memory. The host checks the count of the chunk before
     // the one it just queued, so the GPU never waits for the host. Sweeps
     // queued after everything stopped find an empty worklist.
-    const int chunk = 8;
+    const int chunk = 4;
     unsigned long long* flag = ctx->h_counters + 2;   // two pinned slots
     cudaEvent_t ev[2] = {get_event(ctx), get_event(ctx)};
     if (!ev[0] || !ev[1]) return fail(ctx, MPR_ECUDA, "cudaEventCreate failed");

@@ -441,3 +441,49 @@ def test_block_mean_init_is_closer_to_equilibrium_than_random():
     e_rnd = np.mean([o.total_energy(o.init_random(phi, mask, r)) / st.Nb.sum()
                      for r in range(4)])
     assert abs(e_blk - es_all) < abs(e_rnd - es_all)
+
+
+def test_one_point_k_section_is_the_bisection():
+    from paper_2212_01317_gb300 import synth
+    z, m = synth.small_problem(20, 24, 0.5, seed=6)
+    o = oracle.Oracle(20, 24, 6, seed=12)
+    phi, *_ = o.transform(z, m)
+    st = o.block_stats(phi, m)
+    phi0 = o.init_block_mean(phi, m, st)
+    a = o.calibrate(phi0, m, st, n_eq=4, n_meas=4, n_bisect=7, chains=2)
+    b = o.calibrate_points(phi0, m, st, n_eq=4, n_meas=4, n_iter=7, chains=2, points=1)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_trisection_matches_exact_energy_matching():
+    # Isolated gaps: <e_b>(T) is exact by quadrature; 16 trisection steps
+    # narrow the bracket below the bisection's 24 steps, and the noisy
+    # estimate lands near the exact root as the bisection's does.
+    rng = np.random.default_rng(12)
+    H, W, lb = 16, 16, 8
+    yy, xx = np.mgrid[0:H, 0:W]
+    z = np.sin(yy / 3.0) + np.cos(xx / 2.5) + rng.normal(0, 0.15 + 0.25 * (xx >= 8), (H, W))
+    mask = (((yy + xx) % 2 == 0) & (rng.uniform(size=(H, W)) < 0.5)).astype(np.uint8)
+    o = oracle.Oracle(H, W, lb, seed=3)
+    phi, *_ = o.transform(z.astype(np.float32), mask)
+    st = o.block_stats(phi, mask)
+    phi0 = o.init_block_mean(phi, mask, st)
+    T3 = o.calibrate_points(phi0, mask, st, n_eq=20, n_meas=40, n_iter=16, chains=8, points=2)
+    T2 = o.calibrate(phi0, mask, st, n_eq=20, n_meas=40, n_bisect=24, chains=8)
+    fn = _isolated_block_energy_fn(phi, mask, lb, o.nbx)
+    lo, hi = np.full(o.nblk, 1e-4), np.full(o.nblk, 2.0)
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        E = fn(mid)
+        e = np.array([E.get(b, 0.0) for b in range(o.nblk)]) / st.Nb
+        lo = np.where(e < st.es, mid, lo)
+        hi = np.where(e < st.es, hi, mid)
+    exact = 0.5 * (lo + hi)
+    # the same bounds as the bisection's pin above, and no worse than it on average
+    assert np.all(np.abs(T3 - exact) < 0.25 * exact + 5e-3), (T3, exact)
+    E_at = fn(T3)
+    for b in range(o.nblk):
+        assert abs(E_at[b] / st.Nb[b] - st.es[b]) < 0.02
+    err3 = np.abs(T3 - exact) / exact
+    err2 = np.abs(T2 - exact) / exact
+    assert err3.mean() < 2 * err2.mean() + 0.02
