@@ -51,6 +51,11 @@ def parse():
                     help="element type of the realizations' angles (arithmetic stays FP32)")
     ap.add_argument("--cal-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="calibration launch form (3: every kernel from the host, for profilers)")
+    ap.add_argument("--cal-points", type=int, default=1, choices=[1, 2],
+                    help="calibration temperatures per block and iteration (1 bisection, "
+                         "2 trisection); --cal-iters sets the iterations")
+    ap.add_argument("--cal-iters", type=int, default=None,
+                    help="calibration iterations (default 24 for bisection, 16 for trisection)")
     ap.add_argument("--plain-sample", type=int, default=0,
                     help="batch workloads: also time the plain form (one FP32 context per "
                          "field) on this many fields")
@@ -69,6 +74,14 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def cal_iters(args) -> int:
+    """Calibration iterations: 24 bisection steps, or 16 trisection steps (a
+    narrower final bracket: 2 / 3^16 < 2 / 2^24)."""
+    if args.cal_iters is not None:
+        return args.cal_iters
+    return 16 if args.cal_points == 2 else 24
 
 
 def bytes_per_gap_update(s_bytes: float, p: float) -> float:
@@ -253,6 +266,7 @@ def run_ours(args, world, rank, local):
         return mpr.mpr_default_options(seed=seed, slice_id=slice_id, profile=profile,
                                        storage=STORAGE[args.storage], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
+                                       cal_points=args.cal_points, n_bisect=cal_iters(args),
                                        cuda_stream=stream.cuda_stream)
 
     def step(values, mask, out, profile=1):
@@ -387,7 +401,8 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": wl.name, "H": H, "W": W, "block": wl.block, "gap_fraction": p,
                    "realizations": R, "storage": args.storage, "cal_mode": args.cal_mode,
-                   "calibration": args.calibration,
+                   "calibration": args.calibration if args.calibration == "newton" else
+                   ("bisection" if args.cal_points == 1 else "trisection") + f" x{cal_iters(args)}",
                    "l2": "flushed between timed steps",
                    "parallelism": (f"replicas{world}" if shard == "fields"
                                    else f"realizations{world}")},
@@ -439,6 +454,7 @@ def run_ours_batch(args, world, rank, local):
         return mpr.mpr_default_options(seed=2024 + 7919 * rank, slice_id=slice_id, profile=profile,
                                        storage=STORAGE[st], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
+                                       cal_points=args.cal_points, n_bisect=cal_iters(args),
                                        sim_graph=0, cuda_stream=stream.cuda_stream)
 
     def step(values, masks, outs, profile=1):

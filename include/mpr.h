@@ -93,6 +93,10 @@ typedef struct {
     float t_init;        /* Newton starting temperature (default 0.1) */
     int32_t sim_graph;   /* 1: mpr_simulate runs its sweep loop as one CUDA graph (a device-side
                             loop; full grids, no per-launch timing; ignored when profile = 1) */
+    int32_t cal_points;  /* temperatures tried per block and calibration iteration: 1 bisection
+                            (default), 2 trisection (the two on the two lanes of a realization
+                            pair; n_bisect iterations shrink each bracket 3x; 16 of them leave
+                            it narrower than 24 bisection steps) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 

@@ -481,10 +481,32 @@ double orc_median_targeted(int32_t nblk, const double* T, const int64_t* Nsp) {
  * n_eq sweeps and e_b is averaged over n_meas further sweeps (and over the
  * chains); then the bracket half on the wrong side of e_s,b is dropped
  * (<e_b> increases with T). Random numbers use tag 1 + k. */
+/* Blocks that calibrate: those with sample bonds (a target e_s,b) and gap
+ * sites (whose temperature the method uses). A block with sample bonds but
+ * no gap site has e_b = e_s,b exactly and nothing to fill; like a block
+ * without sample bonds it takes the median of the calibrating blocks' T and
+ * does not count towards it. Returns Nsp with the others set to 0. */
+static int64_t* calib_targets(const orc_model* m, const uint8_t* mask, const int64_t* Nsp,
+                              int three_d) {
+    int64_t* t = (int64_t*)calloc((size_t)m->nblk, sizeof(int64_t));
+    const int D = three_d ? m->D : 1;
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < m->H; ++y)
+            for (int x = 0; x < m->W; ++x) {
+                const int64_t i = ((int64_t)z * m->H + y) * m->W + x;
+                if (!mask[i]) continue;
+                const int b = ((z / m->lb) * m->nby + y / m->lb) * m->nbx + x / m->lb;
+                t[b] = 1;
+            }
+    for (int b = 0; b < m->nblk; ++b) t[b] = t[b] ? Nsp[b] : 0;
+    return t;
+}
+
 void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* mask,
-                   const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                   const double* Es, const int64_t* Nsp_all, const int64_t* Nb, int32_t n_eq,
                    int32_t n_meas, int32_t n_bisect, int32_t chains, double T_lo, double T_hi,
                    double* T_out, double* ebar_trace) {
+    int64_t* Nsp = calib_targets(m, mask, Nsp_all, 0);
     const int nblk = m->nblk;
     const int64_t n = (int64_t)m->H * m->W;
     double* lo = (double*)malloc(sizeof(double) * nblk);
@@ -526,13 +548,15 @@ void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* ma
     for (int b = 0; b < nblk; ++b)
         if (Nsp[b] == 0) T_out[b] = med;
     free(lo); free(hi); free(T); free(ebar); free(E); free(phi);
+    free(Nsp);
 }
 
 /* ----------------------------------------------------------------- scores -- */
 void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint8_t* mask,
-                          const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                          const double* Es, const int64_t* Nsp_all, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_iter, int32_t chains, int32_t points,
                           double T_lo, double T_hi, double* T_out) {
+    int64_t* Nsp = calib_targets(m, mask, Nsp_all, 0);
     const int nblk = m->nblk;
     const int64_t n = (int64_t)m->H * m->W;
     double* lo = (double*)malloc(sizeof(double) * nblk);
@@ -590,6 +614,7 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
     for (int b = 0; b < nblk; ++b)
         if (Nsp[b] == 0) T_out[b] = med;
     free(lo); free(hi); free(T); free(ebar); free(E); free(phi);
+    free(Nsp);
 }
 
 /* --------------------------------------------- moments and Newton (f1) -- */
@@ -634,9 +659,10 @@ void orc_energy_moments(const orc_model* m, double* phi, const uint8_t* mask, co
 #define NEWTON_STEP 2.0   /* largest factor by which one Newton step moves T */
 
 void orc_calibrate_newton(const orc_model* m, const double* phi_init, const uint8_t* mask,
-                          const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                          const double* Es, const int64_t* Nsp_all, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_newton, int32_t chains, double T_lo,
                           double T_hi, double T0, double* T_out, double* trace) {
+    int64_t* Nsp = calib_targets(m, mask, Nsp_all, 0);
     const int nblk = m->nblk;
     const int64_t n = (int64_t)m->H * m->W;
     double* T = (double*)malloc(sizeof(double) * nblk);
@@ -670,6 +696,7 @@ void orc_calibrate_newton(const orc_model* m, const double* phi_init, const uint
     const double med = orc_median_targeted(nblk, T, Nsp);
     for (int b = 0; b < nblk; ++b) T_out[b] = Nsp[b] == 0 ? med : T[b];
     free(T); free(y); free(v); free(phi);
+    free(Nsp);
 }
 
 /* ------------------------------------------------------------- 3-D -- */
@@ -818,9 +845,10 @@ int orc3_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, cons
 }
 
 void orc3_calibrate(const orc_model* m, const double* phi_init, const uint8_t* mask,
-                    const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
+                    const double* Es, const int64_t* Nsp_all, const int64_t* Nb, int32_t n_eq,
                     int32_t n_meas, int32_t n_bisect, int32_t chains, double T_lo, double T_hi,
                     double* T_out) {
+    int64_t* Nsp = calib_targets(m, mask, Nsp_all, 1);
     const int nblk = m->nblk;
     const int64_t n = (int64_t)m->D * m->H * m->W;
     double* lo = (double*)malloc(sizeof(double) * nblk);
@@ -860,6 +888,7 @@ void orc3_calibrate(const orc_model* m, const double* phi_init, const uint8_t* m
     for (int b = 0; b < nblk; ++b)
         if (Nsp[b] == 0) T_out[b] = med;
     free(lo); free(hi); free(T); free(ebar); free(E); free(phi);
+    free(Nsp);
 }
 
 /* Eqs. 3-4: AAE and RASE over the P prediction sites. */

@@ -463,6 +463,7 @@ struct mpr3_ctx {
     double *Es = nullptr, *es = nullptr, *inb = nullptr, *ssum = nullptr;
     int32_t *Nsp = nullptr, *Nb = nullptr, *nsamp = nullptr, *ngap = nullptr,
             *ngap_c[2] = {nullptr, nullptr}, *zero_slices = nullptr;
+    int32_t* Nsp_cal = nullptr;  // calibrating blocks: sample bonds and gap sites
     float *T = nullptr, *beta = nullptr, *lo = nullptr, *hi = nullptr;
     double* ebar = nullptr;
     double* sum = nullptr;
@@ -703,7 +704,7 @@ mpr_status mpr3_create(const mpr_grid3* grid, const uint8_t* mask_in, const floa
     for (auto* p : {&ctx->Es, &ctx->es, &ctx->inb, &ctx->ssum, &ctx->ebar})
         ST3(alloc3(ctx, p, g.nblk));
     for (auto* p : {&ctx->Nsp, &ctx->Nb, &ctx->nsamp, &ctx->ngap, &ctx->ngap_c[0], &ctx->ngap_c[1],
-                    &ctx->zero_slices})
+                    &ctx->zero_slices, &ctx->Nsp_cal})
         ST3(alloc3(ctx, p, g.nblk));
     for (auto* p : {&ctx->init_angle, &ctx->T, &ctx->beta, &ctx->lo, &ctx->hi})
         ST3(alloc3(ctx, p, g.nblk));
@@ -765,7 +766,9 @@ mpr_status mpr3_create(const mpr_grid3* grid, const uint8_t* mask_in, const floa
     std::vector<float> init(g.nblk);
     std::vector<int32_t> ng(g.nblk);
     std::vector<double> es_h(g.nblk), inb_h(g.nblk);
+    std::vector<int32_t> nsp_cal(g.nblk);
     for (int b = 0; b < g.nblk; ++b) {
+        nsp_cal[b] = (ng0[b] + ng1[b]) > 0 ? nsp[b] : 0;
         pairs += nsp[b];
         samples += nsm[b];
         gsum += ssum[b];
@@ -784,7 +787,8 @@ mpr_status mpr3_create(const mpr_grid3* grid, const uint8_t* mask_in, const floa
     if (cudaMemcpyAsync(ctx->init_angle, init.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s) ||
         cudaMemcpyAsync(ctx->es, es_h.data(), g.nblk * 8, cudaMemcpyHostToDevice, ctx->s) ||
         cudaMemcpyAsync(ctx->inb, inb_h.data(), g.nblk * 8, cudaMemcpyHostToDevice, ctx->s) ||
-        cudaMemcpyAsync(ctx->ngap, ng.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s))
+        cudaMemcpyAsync(ctx->ngap, ng.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s) ||
+        cudaMemcpyAsync(ctx->Nsp_cal, nsp_cal.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s))
         return bail(MPR_ECUDA);
     k3_build_lists<<<bblocks, 256, 0, ctx->s>>>(g, ctx->mask, ctx->start[0], ctx->start[1],
                                                 ctx->list[0], ctx->list[1]);
@@ -846,8 +850,8 @@ mpr_status mpr3_calibrate(mpr3_ctx* ctx, float* T_out) {
         CKL3();
         const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);
         for (int k = 0; k < o.n_bisect; ++k) {
-            launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
-            launch_cal_fill(sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+            launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+            launch_cal_fill(sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
             CKL3();
             TRY3(init3(ctx));
             TRY3(energy3(ctx));
@@ -858,12 +862,12 @@ mpr_status mpr3_calibrate(mpr3_ctx* ctx, float* T_out) {
                                 ctx->ecur, ctx->ebar, ctx->s);
                 CKL3();
             }
-            launch_cal_update(g.nblk, inv_count, ctx->es, ctx->Nsp, ctx->T, ctx->lo, ctx->hi,
+            launch_cal_update(g.nblk, inv_count, ctx->es, ctx->Nsp_cal, ctx->T, ctx->lo, ctx->hi,
                               ctx->ebar, ctx->ctl, o.n_bisect, 0, ctx->s);
             CKL3();
         }
-        launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
-        launch_cal_fill(sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+        launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+        launch_cal_fill(sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
         CKL3();
         ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains *
                             (ctx->n_gap[0] + ctx->n_gap[1]);

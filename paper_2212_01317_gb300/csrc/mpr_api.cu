@@ -60,9 +60,15 @@ struct mpr_ctx {
     double* inb = nullptr;  // 1 / N_b
     int32_t *Nsp = nullptr, *Nb = nullptr, *nsamp = nullptr, *ngap_c[2] = {nullptr, nullptr},
             *ngap = nullptr;
+    // Blocks that calibrate: sample bonds (a target) and gap sites; 0 for the
+    // others, which take the median (a block with sample bonds and no gap
+    // site has e_b = e_s,b exactly and nothing to fill).
+    int32_t* Nsp_cal = nullptr;
     double* ssum = nullptr;
     float* init_angle = nullptr;
     float *T = nullptr, *beta = nullptr, *lo = nullptr, *hi = nullptr;
+    float *T2 = nullptr, *beta2 = nullptr;   // trisection's second point
+    double* ebar2 = nullptr;
     float* T_site = nullptr;     // [H*W] site temperatures (SST), allocated on first use
     float* beta_site = nullptr;  // [H*W] 1 / T_site
     int sst = 0;                 // 1: realizations use the site temperatures
@@ -208,6 +214,7 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.wait_ms < 1) return fail(ctx, MPR_EINVAL, "wait_ms must be >= 1");
     if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
     if (o.cal_method != 0 && o.cal_method != 1) return fail(ctx, MPR_EINVAL, "cal_method must be 0 or 1");
+    if (o.cal_points != 1 && o.cal_points != 2) return fail(ctx, MPR_EINVAL, "cal_points must be 1 or 2");
     if (o.n_newton < 0 || o.n_newton > 65533) return fail(ctx, MPR_EINVAL, "n_newton in [0, 65533]");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
@@ -541,14 +548,14 @@ mpr_status calibration_newton(mpr_ctx* ctx) {
     launch_newton_init(g.nblk, o.t_init, o.t_lo, o.t_hi, ctx->T, ctx->lo, ctx->hi, ctx->s);
     CKL();
     for (int k = 0; k < o.n_newton; ++k) {
-        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);   // median, beta
+        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);   // median, beta
         CKL();
         TRY(moments_run(ctx, (uint32_t)(1 + k), k == 0, o.n_eq, o.n_meas));
-        launch_newton_update(g.nblk, ctx->es, ctx->Nsp, ctx->Nb, ctx->mom, ctx->T, (double)o.t_lo,
+        launch_newton_update(g.nblk, ctx->es, ctx->Nsp_cal, ctx->Nb, ctx->mom, ctx->T, (double)o.t_lo,
                              (double)o.t_hi, ctx->s);
         CKL();
     }
-    launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+    launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
     CKL();
     return MPR_OK;
 }
@@ -557,9 +564,17 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
                                  bool timed) {
     const Geom& g = ctx->g;
     const mpr_options& o = ctx->opt;
-    launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
-    CKL();
-    launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+    const int pts = o.cal_points;
+    if (pts == 2) {
+        launch_kcal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->T2, ctx->ctl, ctx->s);
+        CKL();
+        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T2, ctx->beta2, ctx->s);
+        CKL();
+    } else {
+        launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+        CKL();
+    }
+    launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
     CKL();
     TRY(init_batch_state(ctx));
     TRY(energy_pass(ctx));
@@ -572,12 +587,15 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
             SweepArgs a = sweep_args(ctx, c, false);
             a.t_fixed = sw;
             a.eacc = ctx->eacc + (size_t)(sw & 1) * blk;
+            a.beta_odd = pts == 2 ? ctx->beta2 : nullptr;
             FoldArgs f{};
             if (c == 0 && sw > 1) {
                 f.ctas = (g.nblk + 255) / 256;
                 f.nblk = g.nblk;
                 f.Rp = ctx->Rp;
                 f.chains = o.cal_chains;
+                f.points = pts;
+                f.ebar_odd = ctx->ebar2;
                 f.measure = (sw - 1) > o.n_eq;
                 f.inb = ctx->inb;
                 f.eacc = ctx->eacc + (size_t)((sw - 1) & 1) * blk;
@@ -600,10 +618,15 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
         }
     }
     launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, n_sw, ctx->ctl, ctx->inb,
-                    ctx->eacc + (size_t)(n_sw & 1) * blk, ctx->ecur, ctx->ebar, ctx->s);
+                    ctx->eacc + (size_t)(n_sw & 1) * blk, ctx->ecur, ctx->ebar, ctx->s, pts,
+                    ctx->ebar2);
     CKL();
-    launch_cal_update(g.nblk, inv_count, ctx->es, ctx->Nsp, ctx->T, ctx->lo, ctx->hi, ctx->ebar,
-                      ctx->ctl, o.n_bisect, cond, ctx->s);
+    if (pts == 2)
+        launch_kcal_update(g.nblk, inv_count, ctx->es, ctx->Nsp_cal, ctx->T, ctx->T2, ctx->lo, ctx->hi,
+                           ctx->ebar, ctx->ebar2, ctx->ctl, o.n_bisect, cond, ctx->s);
+    else
+        launch_cal_update(g.nblk, inv_count, ctx->es, ctx->Nsp_cal, ctx->T, ctx->lo, ctx->hi,
+                          ctx->ebar, ctx->ctl, o.n_bisect, cond, ctx->s);
     CKL();
     return MPR_OK;
 }
@@ -635,7 +658,7 @@ mpr_status calibration_persistent(mpr_ctx* ctx, double inv_count, bool* fallback
     a.Es = ctx->Es;
     a.es = ctx->es;
     a.inb = ctx->inb;
-    a.Nsp = ctx->Nsp;
+    a.Nsp = ctx->Nsp_cal;
     a.T = ctx->T;
     a.beta = ctx->beta;
     a.lo = ctx->lo;
@@ -787,6 +810,7 @@ void mpr_default_options(mpr_options* o) {
     o->n_newton = 6;
     o->t_init = 0.1f;
     o->sim_graph = 0;
+    o->cal_points = 1;
     o->cuda_stream = nullptr;
 }
 
@@ -897,6 +921,7 @@ mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
     ST(dalloc(ctx, &ctx->es, g.nblk));
     ST(dalloc(ctx, &ctx->inb, g.nblk));
     ST(dalloc(ctx, &ctx->Nsp, g.nblk));
+    ST(dalloc(ctx, &ctx->Nsp_cal, g.nblk));
     ST(dalloc(ctx, &ctx->Nb, g.nblk));
     ST(dalloc(ctx, &ctx->nsamp, g.nblk));
     ST(dalloc(ctx, &ctx->ngap_c[0], g.nblk));
@@ -909,6 +934,9 @@ mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
     ST(dalloc(ctx, &ctx->lo, g.nblk));
     ST(dalloc(ctx, &ctx->hi, g.nblk));
     ST(dalloc(ctx, &ctx->ebar, g.nblk));
+    ST(dalloc(ctx, &ctx->T2, g.nblk));
+    ST(dalloc(ctx, &ctx->beta2, g.nblk));
+    ST(dalloc(ctx, &ctx->ebar2, g.nblk));
     ST(dalloc(ctx, &ctx->start[0], g.nblk + 1));
     ST(dalloc(ctx, &ctx->start[1], g.nblk + 1));
     ST(dalloc(ctx, &ctx->split[0], g.nblk));
@@ -1044,16 +1072,19 @@ mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
         init[b] = (float)(nsm[b] > 0 ? ssum[b] / (double)nsm[b] : gmean);
     }
     std::vector<double> es_h(g.nblk), inb_h(g.nblk);
+    std::vector<int32_t> nsp_cal(g.nblk);
     for (int b = 0; b < g.nblk; ++b) {
         es_h[b] = nsp[b] > 0 ? esv[b] / (double)nsp[b] : 0.0;
         inb_h[b] = nbv[b] > 0 ? 1.0 / (double)nbv[b] : 0.0;
+        nsp_cal[b] = ng[b] > 0 ? nsp[b] : 0;
     }
     ST(dalloc(ctx, &ctx->list[0], ctx->n_gap[0]));
     ST(dalloc(ctx, &ctx->list[1], ctx->n_gap[1]));
     if (cudaMemcpyAsync(ctx->init_angle, init.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s) ||
         cudaMemcpyAsync(ctx->es, es_h.data(), g.nblk * 8, cudaMemcpyHostToDevice, ctx->s) ||
         cudaMemcpyAsync(ctx->inb, inb_h.data(), g.nblk * 8, cudaMemcpyHostToDevice, ctx->s) ||
-        cudaMemcpyAsync(ctx->ngap, ng.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s))
+        cudaMemcpyAsync(ctx->ngap, ng.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s) ||
+        cudaMemcpyAsync(ctx->Nsp_cal, nsp_cal.data(), g.nblk * 4, cudaMemcpyHostToDevice, ctx->s))
         return bail(MPR_ECUDA);
     launch_build_lists(g, ctx->d_of_block, ctx->mask, ctx->start[0], ctx->start[1], ctx->list[0],
                        ctx->list[1], ctx->split[0], ctx->split[1], ctx->s);
@@ -1258,9 +1289,10 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     }
     ctx->r_off = 0;
     ctx->r_even = 0;
-    TRY(ensure_batch(ctx, chains, o.group, MPR_STORE_F32));
-    ctx->R = chains;
+    TRY(ensure_batch(ctx, chains * o.cal_points, o.group, MPR_STORE_F32));
+    ctx->R = chains * o.cal_points;
     ctx->chains_valid = true;
+    CK(cudaMemsetAsync(ctx->ebar2, 0, (size_t)g.nblk * sizeof(double), ctx->s));
     launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->ctl, ctx->s);
     CKL();
     const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);
@@ -1269,8 +1301,9 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     CKL();
     // auto and 1: graph; 2: persistent; 3: a launch per kernel from the host.
     bool fallback = o.cal_mode != 2;
-    if (!fallback && ctx->n_slices > 1)
-        return fail(ctx, MPR_EINVAL, "the persistent calibration (cal_mode 2) takes one field");
+    if (!fallback && (ctx->n_slices > 1 || o.cal_points != 1))
+        return fail(ctx, MPR_EINVAL,
+                    "the persistent calibration (cal_mode 2) takes one field and bisection");
     if (!fallback) {
         TRY(calibration_persistent(ctx, inv_count, &fallback));
         if (fallback && o.cal_mode == 2)
@@ -1282,12 +1315,12 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
         } else if (o.n_bisect > 0) {
             TRY(calibration_graph(ctx, inv_count));
         }
-        launch_cal_mid(g.nblk, ctx->Nsp, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+        launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
         CKL();
-        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp, ctx->T, ctx->beta, ctx->s);
+        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
         CKL();
     }
-    ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains *
+    ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains * o.cal_points *
                         (ctx->n_gap[0] + ctx->n_gap[1]);
     ctx->calibrated = 1;
     ctx->sst = 0;

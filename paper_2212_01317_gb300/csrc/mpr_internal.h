@@ -123,6 +123,7 @@ struct SweepArgs {
     const float* dang;        // [2][H][Wh] FP32 sample angles (0 at gaps)
     const float* beta;        // [nblk] 1 / T_b
     const float* beta_site;   // [H*W] 1 / T_i (site temperatures, Sec. 2.2.3) or nullptr
+    const float* beta_odd;    // [nblk] 1 / T_b of odd lanes (trisection's second point) or nullptr
     const uint8_t* running;   // [nblk][Rp] or nullptr (= every lane r < R runs)
     float* eacc;              // [nblk][Rp] energy change of this sweep (moves)
     double* ecur;             // [nblk][Rp] E_b (the energy pass adds into it)
@@ -140,10 +141,12 @@ struct SweepArgs {
 struct FoldArgs {
     int ctas;                 // CTAs of the launch that fold (0: none)
     int nblk, Rp, chains, measure;
+    int points;               // 2: even / odd lanes are the trisection's two points
     const double* inb;        // [nblk] 1 / N_b
     float* eacc;              // [nblk][Rp] change of the sweep being folded (cleared)
     double* ecur;             // [nblk][Rp]
-    double* ebar;             // [nblk]
+    double* ebar;             // [nblk] (even lanes when points == 2)
+    double* ebar_odd;         // [nblk] odd lanes (points == 2)
 };
 
 // Grid-wide barrier state of a cooperative launch (zeroed before each launch).

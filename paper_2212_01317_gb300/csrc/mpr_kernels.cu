@@ -359,15 +359,18 @@ __global__ void __launch_bounds__(kFlatThreads) k_sweep_flat(SweepArgs a, int64_
         if (blockIdx.y != 0) return;
         for (int b = ((int)blockIdx.x - sweep_ctas) * kFlatThreads + threadIdx.x; b < f.nblk;
              b += f.ctas * kFlatThreads) {
-            double s = 0.0;
-            for (int r = 0; r < f.chains; ++r) {
+            double s[2] = {0.0, 0.0};
+            for (int r = 0; r < f.chains * f.points; ++r) {
                 const size_t k = (size_t)b * f.Rp + r;
                 const double E = f.ecur[k] + (double)f.eacc[k];
                 f.ecur[k] = E;
                 f.eacc[k] = 0.0f;
-                s += E * f.inb[b];
+                s[f.points == 2 ? (r & 1) : 0] += E * f.inb[b];
             }
-            if (f.measure) f.ebar[b] += s;
+            if (f.measure) {
+                f.ebar[b] += s[0];
+                if (f.points == 2) f.ebar_odd[b] += s[1];
+            }
         }
         return;
     }
@@ -593,18 +596,73 @@ __global__ void k_cal_fill(Slices sl, int nbx, const int32_t* __restrict__ Nsp,
 __global__ void k_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed,
                            const Control* __restrict__ ctl, const double* __restrict__ inb,
                            float* __restrict__ eacc, double* __restrict__ ecur,
-                           double* __restrict__ ebar) {
+                           double* __restrict__ ebar, int points, double* __restrict__ ebar_odd) {
     const bool measure = (t_fixed > 0 ? t_fixed : (int)ctl->t) > n_eq;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int r = 0; r < chains; ++r) {
+        double s[2] = {0.0, 0.0};
+        for (int r = 0; r < chains * points; ++r) {
             const size_t k = (size_t)b * Rp + r;
             const double E = ecur[k] + (double)eacc[k];
             ecur[k] = E;
             eacc[k] = 0.0f;
-            s += E * inb[b];
+            s[points == 2 ? (r & 1) : 0] += E * inb[b];
         }
-        if (measure) ebar[b] += s;
+        if (measure) {
+            ebar[b] += s[0];
+            if (points == 2) ebar_odd[b] += s[1];
+        }
+    }
+}
+
+// Trisection points of every targeted block's bracket (untargeted: 0, the
+// median fills them in).
+__global__ void k_kcal_mid(int nblk, const int32_t* __restrict__ Nsp, const float* __restrict__ lo,
+                           const float* __restrict__ hi, float* __restrict__ T0,
+                           float* __restrict__ T1, Control* ctl) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        const bool t = Nsp[b] > 0;
+        const float w = (hi[b] - lo[b]) / 3.0f;
+        T0[b] = t ? lo[b] + w : 0.0f;
+        T1[b] = t ? lo[b] + 2.0f * w : 0.0f;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->tag = 1u + ctl->k;
+        ctl->t = 0;
+    }
+}
+
+// Trisection step: keep the part of the bracket between the higher point
+// whose mean e_b is below e_s,b and the lower point whose mean is not (the
+// points' span when noise makes those cross).
+__global__ void k_kcal_update(int nblk, double inv_count, const double* __restrict__ es,
+                              const int32_t* __restrict__ Nsp, const float* __restrict__ T0,
+                              const float* __restrict__ T1, float* __restrict__ lo,
+                              float* __restrict__ hi, double* __restrict__ ebar0,
+                              double* __restrict__ ebar1, Control* ctl, int n_iter,
+                              cudaGraphConditionalHandle cond) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        const double e0 = ebar0[b] * inv_count, e1 = ebar1[b] * inv_count;
+        ebar0[b] = 0.0;
+        ebar1[b] = 0.0;
+        if (Nsp[b] <= 0) continue;
+        float nlo = lo[b], nhi = hi[b];
+        const float t[2] = {T0[b], T1[b]};
+        const double e[2] = {e0, e1};
+        for (int p = 0; p < 2; ++p) {
+            if (e[p] < es[b]) { if (t[p] > nlo) nlo = t[p]; }
+            else if (t[p] < nhi) nhi = t[p];
+        }
+        if (nlo > nhi) {
+            nlo = t[0];
+            nhi = t[1];
+        }
+        lo[b] = nlo;
+        hi[b] = nhi;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t k = ctl->k + 1;
+        ctl->k = k;
+        if (cond) cudaGraphSetConditional(cond, k < (uint32_t)n_iter ? 1u : 0u);
     }
 }
 
@@ -1147,9 +1205,23 @@ void launch_cal_fill(const Slices& sl, int nbx, const int32_t* Nsp, float* T, fl
 }
 
 void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
-                     const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s) {
+                     const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s,
+                     int points, double* ebar_odd) {
     k_cal_step<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Rp, chains, n_eq, t_fixed, ctl, inb, eacc,
-                                                  ecur, ebar);
+                                                  ecur, ebar, points, ebar_odd);
+}
+
+void launch_kcal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T0,
+                     float* T1, Control* ctl, cudaStream_t s) {
+    k_kcal_mid<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Nsp, lo, hi, T0, T1, ctl);
+}
+
+void launch_kcal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,
+                        const float* T0, const float* T1, float* lo, float* hi, double* ebar0,
+                        double* ebar1, Control* ctl, int n_iter, cudaGraphConditionalHandle cond,
+                        cudaStream_t s) {
+    k_kcal_update<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, inv_count, es, Nsp, T0, T1, lo, hi,
+                                                     ebar0, ebar1, ctl, n_iter, cond);
 }
 
 void launch_cal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,

@@ -66,8 +66,17 @@ void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* 
                     Control* ctl, cudaStream_t s);
 void launch_cal_fill(const Slices& sl, int nbx, const int32_t* Nsp, float* T, float* beta,
                      cudaStream_t s);
+// points = 2: even lanes' energies go to ebar, odd lanes' to ebar_odd.
 void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
-                     const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s);
+                     const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s,
+                     int points = 1, double* ebar_odd = nullptr);
+// Trisection (two temperatures per block per iteration).
+void launch_kcal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T0,
+                     float* T1, Control* ctl, cudaStream_t s);
+void launch_kcal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,
+                        const float* T0, const float* T1, float* lo, float* hi, double* ebar0,
+                        double* ebar1, Control* ctl, int n_iter, cudaGraphConditionalHandle cond,
+                        cudaStream_t s);
 void launch_cal_update(int nblk, double inv_count, const double* es, const int32_t* Nsp,
                        const float* T, float* lo, float* hi, double* ebar, Control* ctl,
                        int n_bisect, cudaGraphConditionalHandle cond, cudaStream_t s);

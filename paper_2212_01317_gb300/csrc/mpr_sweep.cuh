@@ -317,6 +317,7 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
             const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
             const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
             const float beta = a.beta[b];
+            const float beta1 = a.beta_odd ? a.beta_odd[b] : beta;
             float2 out = ph;
             float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
             if (run0) {
@@ -325,7 +326,7 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
                 add_energy(n, f, C0, S0, nc0, ns0, a.m.J, ao0, al0, au0);
             }
             if (run1) {
-                const SiteNew n = site_update<float>(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta, a.m);
+                const SiteNew n = site_update<float>(ph.y, C1, S1, u01(w[2]), u01(w[3]), beta1, a.m);
                 out.y = n.phi;
                 add_energy(n, f, C1, S1, nc1, ns1, a.m.J, ao1, al1, au1);
             }

@@ -47,7 +47,8 @@ class mpr_options(C.Structure):
                 ("init", C.c_int32), ("storage", C.c_int32), ("group", C.c_int32),
                 ("profile", C.c_int32), ("cal_mode", C.c_int32), ("wait_ms", C.c_int32),
                 ("barrier_test", C.c_int32), ("cal_method", C.c_int32), ("n_newton", C.c_int32),
-                ("t_init", C.c_float), ("sim_graph", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("t_init", C.c_float), ("sim_graph", C.c_int32), ("cal_points", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):
