@@ -169,8 +169,16 @@ mpr_status mpr_predict_batch(mpr_ctx* ctx, float* const* outs, const float* cons
                              double* aae_rase);
 mpr_status mpr_get_slice_layout(const mpr_ctx* ctx, int32_t* rects);
 
-/* Releases every resource of ctx (NULL is a no-op). */
+/* Releases every resource of ctx (NULL is a no-op). Its device memory goes
+ * back to the library's memory pool, where the next context reuses it. */
 void mpr_destroy(mpr_ctx* ctx);
+
+/* Device memory: contexts (2-D and 3-D) allocate from one stream-ordered pool
+ * per device, owned by the library, which keeps freed memory cached so that
+ * creating and destroying a context per field costs no cudaMalloc / cudaFree.
+ * mpr_release_cached_memory returns the cached (unused) part of every pool
+ * to the device; memory of live contexts is not affected. Never fails. */
+void mpr_release_cached_memory(void);
 
 /* Message of the last failed call on ctx ("" if none); valid until the next call. */
 const char* mpr_last_error(const mpr_ctx* ctx);

@@ -27,6 +27,7 @@
 #include "mpr.h"
 #include "mpr_internal.h"
 #include "mpr_launch.h"
+#include "mpr_memory.h"
 #include "mpr_sweep.cuh"
 
 using namespace mpr;
@@ -451,6 +452,7 @@ struct mpr3_ctx {
     Model m{};
     uint32_t key0 = 0, key1 = 0;
     cudaStream_t s = nullptr;
+    int device = 0;
     std::string err;
     std::vector<void*> owned;
     double zmin = 0, zmax = 0;
@@ -524,9 +526,10 @@ template <class T>
 mpr_status alloc3(mpr3_ctx* ctx, T** p, size_t count) {
     *p = nullptr;
     void* q = nullptr;
-    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+    if (pool_alloc(&q, std::max<size_t>(count, 1) * sizeof(T), ctx->device, ctx->s) !=
+        cudaSuccess) {
         cudaGetLastError();
-        return fail3(ctx, MPR_ENOMEM, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+        return fail3(ctx, MPR_ENOMEM, "allocation of %zu bytes failed", count * sizeof(T));
     }
     ctx->owned.push_back(q);
     *p = static_cast<T*>(q);
@@ -537,7 +540,7 @@ void free3(mpr3_ctx* ctx, void* p) {
     if (!p) return;
     auto it = std::find(ctx->owned.begin(), ctx->owned.end(), p);
     if (it != ctx->owned.end()) ctx->owned.erase(it);
-    cudaFree(p);
+    pool_free(p, ctx->s);
 }
 
 Slices slices3(mpr3_ctx* ctx) {
@@ -656,7 +659,8 @@ extern "C" {
 void mpr3_destroy(mpr3_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->s);
-    for (void* p : ctx->owned) cudaFree(p);
+    for (void* p : ctx->owned) pool_free(p, ctx->s);
+    cudaStreamSynchronize(ctx->s);
     delete ctx;
 }
 
@@ -693,6 +697,7 @@ mpr_status mpr3_create(const mpr_grid3* grid, const uint8_t* mask_in, const floa
     ctx->key0 = (uint32_t)(o.seed & 0xffffffffu);
     ctx->key1 = (uint32_t)(o.seed >> 32) ^ o.slice_id;
     ctx->s = (cudaStream_t)o.cuda_stream;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(MPR_ECUDA);
     const int64_t n = (int64_t)D * H * W;
     ctx->n = n;
     mpr_status st;

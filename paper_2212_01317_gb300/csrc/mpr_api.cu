@@ -13,6 +13,7 @@
 #include "mpr.h"
 #include "mpr_internal.h"
 #include "mpr_launch.h"
+#include "mpr_memory.h"
 
 using namespace mpr;
 
@@ -169,10 +170,10 @@ mpr_status dalloc(mpr_ctx* ctx, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    cudaError_t e = pool_alloc(&q, count * sizeof(T), ctx->device, ctx->s);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(ctx, MPR_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+        return fail(ctx, MPR_ENOMEM, "allocation of %zu bytes failed: %s", count * sizeof(T),
                     cudaGetErrorString(e));
     }
     ctx->owned.push_back(q);
@@ -185,7 +186,7 @@ void dfree(mpr_ctx* ctx, void* p) {
     if (!p) return;
     auto it = std::find(ctx->owned.begin(), ctx->owned.end(), p);
     if (it != ctx->owned.end()) ctx->owned.erase(it);
-    cudaFree(p);
+    pool_free(p, ctx->s);
 }
 
 // Lane-group width: 2 (one realization pair per group) for up to two lanes
@@ -360,26 +361,6 @@ cudaEvent_t get_event(mpr_ctx* ctx) {
     return e;
 }
 
-// Launches one half-step; with profiling on, brackets it with events on the
-// context's stream (summed when the stream is next synchronised).
-mpr_status halfstep_launch(mpr_ctx* ctx, const SweepArgs& a, bool sim) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ctx->opt.profile) {
-        e0 = get_event(ctx);
-        e1 = get_event(ctx);
-        if (e0) cudaEventRecord(e0, ctx->s);
-    }
-    const bool wide = sweep_wide(ctx);
-    launch_sweep(a, ctx->G, ctx->storage, wide, sweep_grid(ctx, wide), ctx->s);
-    CKL();
-    if (e0 && e1) {
-        cudaEventRecord(e1, ctx->s);
-        (sim ? ctx->ev_sim : ctx->ev_cal).emplace_back(e0, e1);
-    }
-    if (sim) ++ctx->sim_halfstep_launches; else ++ctx->cal_halfstep_launches;
-    return MPR_OK;
-}
-
 // E_b of the batch's current state from scratch, into ecur: E_s,b plus every
 // bond that touches a gap site (every lane of every block: the pass ignores
 // the running flags). Clears eacc.
@@ -455,7 +436,25 @@ __global__ void k_fill_valid(uint8_t* running, int64_t n, int Rp, int r_off, int
 // next worklist. Everything the kernels need comes from device memory.
 mpr_status sweep_once(mpr_ctx* ctx) {
     const Geom& g = ctx->g;
-    for (int c = 0; c < 2; ++c) TRY(halfstep_launch(ctx, sweep_args(ctx, c, true), true));
+    // With profiling on, one event pair spans the sweep's two half-steps
+    // (launched back to back), so the events do not split them.
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->opt.profile) {
+        e0 = get_event(ctx);
+        e1 = get_event(ctx);
+        if (e0) cudaEventRecord(e0, ctx->s);
+    }
+    for (int c = 0; c < 2; ++c) {
+        const bool wide = sweep_wide(ctx);
+        launch_sweep(sweep_args(ctx, c, true), ctx->G, ctx->storage, wide, sweep_grid(ctx, wide),
+                     ctx->s);
+        CKL();
+        ++ctx->sim_halfstep_launches;
+    }
+    if (e0 && e1) {
+        cudaEventRecord(e1, ctx->s);
+        ctx->ev_sim.emplace_back(e0, e1);
+    }
     launch_stop_targeted(ctx->G, ctx->groups, ctx->Rp, ctx->d_of_block, stop_grid(ctx, ctx->G),
                          ctx->ctl, ctx->work,
                          ctx->work_stride, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
@@ -829,6 +828,8 @@ const char* mpr_status_string(mpr_status s) {
 
 const char* mpr_last_error(const mpr_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
 
+void mpr_release_cached_memory(void) { pool_trim(); }
+
 void mpr_destroy(mpr_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->s);
@@ -836,9 +837,9 @@ void mpr_destroy(mpr_ctx* ctx) {
     for (auto& pr : ctx->ev_cal) ctx->ev_pool.insert(ctx->ev_pool.end(), {pr.first, pr.second});
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
-    for (void* p : ctx->owned) cudaFree(p);
-    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
-    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+    for (void* p : ctx->owned) pool_free(p, ctx->s);
+    cudaStreamSynchronize(ctx->s);
+    pinned_release(ctx->h_counters);   // h_ctl lies in the same slot
     delete ctx;
 }
 
@@ -955,9 +956,14 @@ mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
     ST(dalloc(ctx, &ctx->d_zmax, ns));
     ST(dalloc(ctx, &ctx->d_degen, ns));
     cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, ctx->device);
-    if (cudaMallocHost(&ctx->h_counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_ctl, sizeof(Control)) != cudaSuccess)
-        return bail(MPR_ENOMEM);
+    {
+        // One pinned slot: the four counters, then the Control mirror.
+        static_assert(64 + sizeof(Control) <= kPinnedSlot, "pinned slot too small");
+        uint8_t* slot = static_cast<uint8_t*>(pinned_slot());
+        if (!slot) return bail(MPR_ENOMEM);
+        ctx->h_counters = reinterpret_cast<unsigned long long*>(slot);
+        ctx->h_ctl = reinterpret_cast<Control*>(slot + 64);
+    }
 
     // Slice tables: rectangles, block rectangles, slice of every block, keys.
     std::vector<int4> rect(ns), blk(ns);

@@ -337,6 +337,8 @@ __global__ void k_fill_samples(Geom g, const uint8_t* __restrict__ mask,
 //   G = 2 (one pair): WPI = 1, four items per CTA; tail form WPI = 4.
 template <int G, typename S, int WPI, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 8 : 2) k_sweep(SweepArgs a) {
+    grid_dep_launch();
+    grid_dep_wait();
     const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
     const uint32_t ctr1 = t | (a.ctl->tag << 16);
     const uint32_t* work = a.work ? a.work + (size_t)(t & 1u) * a.work_stride : nullptr;
@@ -354,8 +356,10 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 8 : 2) k_sweep(Sweep
 template <int G>
 __global__ void __launch_bounds__(kFlatThreads) k_sweep_flat(SweepArgs a, int64_t n_list,
                                                             FoldArgs f) {
+    grid_dep_launch();
     const int sweep_ctas = (int)gridDim.x - f.ctas;
     if ((int)blockIdx.x >= sweep_ctas) {
+        grid_dep_wait();
         if (blockIdx.y != 0) return;
         for (int b = ((int)blockIdx.x - sweep_ctas) * kFlatThreads + threadIdx.x; b < f.nblk;
              b += f.ctas * kFlatThreads) {
@@ -447,6 +451,8 @@ __global__ void k_stop_targeted(int G, int groups, int Rp, const int32_t* __rest
                                 double* __restrict__ ecur, const int8_t* __restrict__ sigma,
                                 uint8_t* __restrict__ running, int32_t* __restrict__ stop,
                                 int32_t* __restrict__ tcount, double* __restrict__ e_last) {
+    grid_dep_launch();
+    grid_dep_wait();
     const uint32_t t_sweep = ctl->t;
     const uint32_t* w = work + (size_t)(t_sweep & 1u) * work_stride;
     const int64_t n = (int64_t)ctl->n_work[t_sweep & 1u] * G;
@@ -485,6 +491,8 @@ __global__ void k_stop_rest(int nblk, int groups, int G, int Rp, int n_max,
                             uint32_t* __restrict__ work_all, uint32_t work_stride,
                             const int32_t* __restrict__ Nsp, uint8_t* __restrict__ running,
                             int32_t* __restrict__ stop, const int32_t* __restrict__ tcount) {
+    grid_dep_launch();
+    grid_dep_wait();
     const uint32_t t_sweep = ctl->t;
     const uint32_t par = t_sweep & 1u, nxt = par ^ 1u;
     const uint32_t* w = work ? work + (size_t)par * work_stride : nullptr;
@@ -1056,6 +1064,28 @@ void launch_build_lists(const Geom& g, const int32_t* of_block, const uint8_t* m
 }
 
 namespace {
+// Launch with programmatic dependent launch allowed: the kernel may start
+// while the previous kernel on the stream finishes (every kernel launched
+// this way executes griddepcontrol.wait before reading what its predecessor
+// writes). A refused attribute falls back to a plain launch.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k, args...) != cudaSuccess) {
+        cudaGetLastError();
+        k<<<grid, block, 0, s>>>(args...);
+    }
+}
+
 template <typename S> struct Tag { using type = S; };
 // Calls f(Tag<S>) with the state element type of `storage` (an mpr_storage).
 template <typename F> void with_storage(int storage, F&& f) {
@@ -1088,11 +1118,11 @@ namespace {
 template <int G, typename S>
 void sweep_dispatch(const SweepArgs& a, bool wide, int grid, cudaStream_t s) {
     if constexpr (G == 2) {
-        if (wide) k_sweep<2, S, 4, 128><<<grid, 128, 0, s>>>(a);
-        else k_sweep<2, S, 1, 128><<<grid, 128, 0, s>>>(a);
+        if (wide) launch_pdl(k_sweep<2, S, 4, 128>, grid, 128, s, a);
+        else launch_pdl(k_sweep<2, S, 1, 128>, grid, 128, s, a);
     } else {
-        if (wide) k_sweep<8, S, 16, 512><<<grid, 512, 0, s>>>(a);
-        else k_sweep<8, S, 4, 128><<<grid, 128, 0, s>>>(a);
+        if (wide) launch_pdl(k_sweep<8, S, 16, 512>, grid, 512, s, a);
+        else launch_pdl(k_sweep<8, S, 4, 128>, grid, 128, s, a);
     }
 }
 
@@ -1150,8 +1180,10 @@ void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s
     const int64_t threads = n_list * (G / 2);
     const dim3 grid((unsigned)((threads + kFlatThreads - 1) / kFlatThreads + f.ctas),
                     (unsigned)a.groups);
-    if (G == 2) k_sweep_flat<2><<<grid, kFlatThreads, 0, s>>>(a, n_list, f);
-    else k_sweep_flat<8><<<grid, kFlatThreads, 0, s>>>(a, n_list, f);
+    // Programmatic dependent launch: this half-step's prologue overlaps the
+    // previous launch's tail (the kernel waits before touching its output).
+    if (G == 2) launch_pdl(k_sweep_flat<2>, grid, kFlatThreads, s, a, n_list, f);
+    else launch_pdl(k_sweep_flat<8>, grid, kFlatThreads, s, a, n_list, f);
 }
 
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
@@ -1172,16 +1204,16 @@ void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, in
                           const double* es, const double* inb, const int32_t* Nsp, float* eacc,
                           double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
                           int32_t* tcount, double* e_last, cudaStream_t s) {
-    k_stop_targeted<<<grid, 256, 0, s>>>(G, groups, Rp, of_block, ctl, work, work_stride, es, inb,
-                                         Nsp, eacc, ecur, sigma, running, stop, tcount, e_last);
+    launch_pdl(k_stop_targeted, grid, 256, s, G, groups, Rp, of_block, ctl, work, work_stride, es,
+               inb, Nsp, eacc, ecur, sigma, running, stop, tcount, e_last);
 }
 
 void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int32_t* of_block,
                       int grid, Control* ctl, const uint32_t* work, uint32_t* work_all,
                       uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
                       const int32_t* tcount, cudaGraphConditionalHandle cond, cudaStream_t s) {
-    k_stop_rest<<<grid, 256, 0, s>>>(nblk, groups, G, Rp, n_max, of_block, cond, ctl, work,
-                                     work_all, work_stride, Nsp, running, stop, tcount);
+    launch_pdl(k_stop_rest, grid, 256, s, nblk, groups, G, Rp, n_max, of_block, cond, ctl, work,
+               work_all, work_stride, Nsp, running, stop, tcount);
 }
 
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,

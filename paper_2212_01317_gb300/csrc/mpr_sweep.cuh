@@ -277,6 +277,20 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
 constexpr int kFlatThreads = 256;
 constexpr int kFlatBlocks = 64;     // local blocks summed in shared memory per CTA
 
+// Programmatic dependent launch: a launch may start while the previous
+// kernel on the stream finishes. griddepcontrol.wait blocks until every
+// prerequisite grid has completed and its writes are visible; every thread of
+// such a kernel executes it (so its completion implies its predecessors').
+// launch_dependents lets the next launch begin once every CTA of this one
+// has issued it or exited.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// The list entry, its Philox block and the temperatures do not depend on the
+// previous half-step, so they are taken before the dependency wait and
+// overlap the previous launch's tail.
 template <int G>
 __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, uint32_t ctr1) {
     constexpr int NP = G / 2;
@@ -288,13 +302,29 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
     const int q = (int)(t % NP);
     for (int i = threadIdx.x; i < kFlatBlocks * G; i += kFlatThreads) acc[i] = 0.0f;
     const int b0 = (int)(a.list[t0 / NP].y >> META_SHIFT);
+    const bool live = e < n_list;
+    const int rl = grp * G + 2 * q;
+    uint2 en = make_uint2(0u, 0u);
+    int b = b0;
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    float beta = 0.0f, beta1 = 0.0f;
+    if (live) {
+        en = a.list[e];
+        b = (int)(en.y >> META_SHIFT);
+        const int y = en.x >> 16, x = en.x & 0xffff;
+        const int sl = slice_of(a.sl, b);
+        philox4x32_10(local_index(slice_rect(a.sl, sl), y, x), ctr1,
+                      (a.r_base + (uint32_t)rl) >> 1, 0u, a.rng.key0, slice_key1(a.sl, sl), w);
+        beta = a.beta[b];
+        beta1 = a.beta_odd ? a.beta_odd[b] : beta;
+    }
+    grid_dep_wait();
     __syncthreads();
-    if (e < n_list) {
+    float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
+    uint32_t f = 0;
+    if (live) {
         const size_t plane = (size_t)a.g.H * a.g.Wh;
         const int c = a.colour, co = c ^ 1;
-        const uint2 en = a.list[e];
-        const int b = (int)(en.y >> META_SHIFT);
-        const int rl = grp * G + 2 * q;
         bool run0, run1;
         pair_running(a, b, rl, run0, run1);
         if (run0 || run1) {
@@ -302,12 +332,8 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
             const float2* oth =
                 reinterpret_cast<const float2*>(static_cast<const float*>(a.ang) + (size_t)(grp * 2 + co) * plane * G) + q;
             const int y = en.x >> 16, x = en.x & 0xffff;
-            const uint32_t f = en.y;
+            f = en.y;
             const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
-            const int sl = slice_of(a.sl, b);
-            uint32_t w[4];
-            philox4x32_10(local_index(slice_rect(a.sl, sl), y, x), ctr1,
-                          (a.r_base + (uint32_t)rl) >> 1, 0u, a.rng.key0, slice_key1(a.sl, sl), w);
             const float2 ph = own[(size_t)hs * NP];
             float nc0[4], ns0[4], nc1[4], ns1[4];
             neighbour_field<float>(a, reinterpret_cast<const float*>(oth), G, hs, x, f, nc0, ns0,
@@ -316,10 +342,7 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
             const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
             const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
             const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
-            const float beta = a.beta[b];
-            const float beta1 = a.beta_odd ? a.beta_odd[b] : beta;
             float2 out = ph;
-            float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
             if (run0) {
                 const SiteNew n = site_update<float>(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);
                 out.x = n.phi;
@@ -331,28 +354,50 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
                 add_energy(n, f, C1, S1, nc1, ns1, a.m.J, ao1, al1, au1);
             }
             own[(size_t)hs * NP] = out;
-            if (a.energy) {
-                const int loc = b - b0;
-                if (loc < kFlatBlocks) {
-                    if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * q], ao0);
-                    if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * q + 1], ao1);
-                } else {
-                    float* ea = a.eacc + (size_t)b * a.Rp + rl;
-                    if (ao0 != 0.0f) atomicAdd(ea, ao0);
-                    if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
-                }
-                if (f & (EDGE_L | EDGE_U)) {
-                    float* ea = a.eacc + (size_t)b * a.Rp + rl;
-                    if (al0 != 0.0f) atomicAdd(ea - a.Rp, al0);
-                    if (al1 != 0.0f) atomicAdd(ea - a.Rp + 1, al1);
-                    const size_t up = (size_t)a.g.nbx * a.Rp;
-                    if (au0 != 0.0f) atomicAdd(ea - up, au0);
-                    if (au1 != 0.0f) atomicAdd(ea - up + 1, au1);
-                }
-            }
         }
     }
     if (!a.energy) return;
+    // The block's share: one warp sum per realization lane when the warp's
+    // entries all lie in one block (the usual case: the list is block-major),
+    // else an atomic per lane; shared-memory sums for the CTA's first blocks.
+    const int lane = threadIdx.x & 31;
+    if (__all_sync(0xffffffffu, b == __shfl_sync(0xffffffffu, b, 0))) {
+#pragma unroll
+        for (int d = 16; d >= NP; d >>= 1) {
+            ao0 += __shfl_xor_sync(0xffffffffu, ao0, d);
+            ao1 += __shfl_xor_sync(0xffffffffu, ao1, d);
+        }
+        if (lane < NP) {
+            const int loc = b - b0;
+            if (loc < kFlatBlocks) {
+                if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane], ao0);
+                if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane + 1], ao1);
+            } else {
+                float* ea = a.eacc + (size_t)b * a.Rp + grp * G + 2 * lane;
+                if (ao0 != 0.0f) atomicAdd(ea, ao0);
+                if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
+            }
+        }
+    } else if (live) {
+        const int loc = b - b0;
+        if (loc < kFlatBlocks) {
+            if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * q], ao0);
+            if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * q + 1], ao1);
+        } else {
+            float* ea = a.eacc + (size_t)b * a.Rp + rl;
+            if (ao0 != 0.0f) atomicAdd(ea, ao0);
+            if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
+        }
+    }
+    // Left / up bonds of edge sites belong to the neighbouring blocks.
+    if (f & (EDGE_L | EDGE_U)) {
+        float* ea = a.eacc + (size_t)b * a.Rp + rl;
+        if (al0 != 0.0f) atomicAdd(ea - a.Rp, al0);
+        if (al1 != 0.0f) atomicAdd(ea - a.Rp + 1, al1);
+        const size_t up = (size_t)a.g.nbx * a.Rp;
+        if (au0 != 0.0f) atomicAdd(ea - up, au0);
+        if (au1 != 0.0f) atomicAdd(ea - up + 1, au1);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < kFlatBlocks * G; i += kFlatThreads) {
         const float v = acc[i];

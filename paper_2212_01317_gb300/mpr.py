@@ -27,7 +27,7 @@ EXPORTS = [
     "mpr_block_stats_noalloc", "mpr_set_realization_base", "mpr_get_accumulator",
     "mpr_set_accumulator", "mpr_smooth_temperatures", "mpr_set_site_temperatures",
     "mpr_get_site_temperatures", "mpr_energy_moments", "mpr_energy_vjp", "mpr_create_batch",
-    "mpr_predict_batch", "mpr_get_slice_layout", "mpr_autotune",
+    "mpr_predict_batch", "mpr_get_slice_layout", "mpr_autotune", "mpr_release_cached_memory",
     "mpr3_create", "mpr3_destroy", "mpr3_last_error", "mpr3_get_info", "mpr3_get_block_stats",
     "mpr3_calibrate", "mpr3_set_temperatures", "mpr3_simulate", "mpr3_predict", "mpr3_sim_begin",
     "mpr3_halfstep", "mpr3_get_state", "mpr3_set_state", "mpr3_sim_end",
@@ -115,6 +115,7 @@ def load(path: str | None = None):
         "mpr_default_options": (None, [C.POINTER(mpr_options)]),
         "mpr_create": (st, [C.POINTER(mpr_grid), P, P, C.POINTER(mpr_options), C.POINTER(P)]),
         "mpr_destroy": (None, [P]),
+        "mpr_release_cached_memory": (None, []),
         "mpr_last_error": (C.c_char_p, [P]),
         "mpr_status_string": (C.c_char_p, [st]),
         "mpr_get_info": (st, [P, C.POINTER(mpr_info)]),
@@ -247,6 +248,11 @@ def mpr_autotune(ctx, n_realizations: int, n_sweeps: int = 4) -> mpr_tuning:
 
 def mpr_destroy(ctx):
     load().mpr_destroy(ctx)
+
+
+def mpr_release_cached_memory():
+    """Returns the library's cached (unused) device memory to the device."""
+    load().mpr_release_cached_memory()
 
 
 def mpr_get_info(ctx) -> mpr_info:

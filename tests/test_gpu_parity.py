@@ -444,3 +444,35 @@ def test_device_pointers_through_the_abi():
     np.testing.assert_array_equal(out.cpu().numpy(), pred)
     mpr.mpr_destroy(ctx)
     gf.close()
+
+
+# ------------------------------------------------------------- memory --
+def test_context_memory_is_pooled_and_released():
+    """Contexts allocate from the library's stream-ordered pool: destroying one
+    keeps its memory cached for the next (results unchanged, see every other
+    test, which run on recycled memory), and mpr_release_cached_memory hands
+    the cache back to the device."""
+    import torch
+    from paper_2212_01317_gb300 import mpr
+    z, m = problem(96, 80, 0.5, seed=17)
+    mpr.mpr_release_cached_memory()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    preds = []
+    for _ in range(3):
+        gf = make(z, m, 8, seed=11)
+        gf.set_temperatures(np.full(gf.nblk, 0.2, np.float32))
+        gf.simulate(6)
+        preds.append(gf.predict()[0])
+        gf.close()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    mpr.mpr_release_cached_memory()
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free2 >= free1
+    assert free0 - free2 < 64 << 20
+    # Same seed, same field: the same prediction (up to the order of the FP32
+    # energy atomics, which can only move a stop decision at an exact tie).
+    for p in preds[1:]:
+        assert np.mean(np.abs(p - preds[0])) < 1e-3 * (z.max() - z.min())
