@@ -97,6 +97,12 @@ typedef struct {
                             (default), 2 trisection (the two on the two lanes of a realization
                             pair; n_bisect iterations shrink each bracket 3x; 16 of them leave
                             it narrower than 24 bisection steps) */
+    int32_t sim_tail;    /* running (block, realization) pairs below which mpr_simulate runs the
+                            rest of its sweep loop (half-steps and stop tests, separated by
+                            bounded grid-wide barriers) as one cooperative launch; 0: never
+                            (default: measured slower than the per-launch loop with
+                            programmatic launches; ignored by sim_graph and where cooperative
+                            launch is unavailable) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 

@@ -216,6 +216,7 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
     if (o.cal_method != 0 && o.cal_method != 1) return fail(ctx, MPR_EINVAL, "cal_method must be 0 or 1");
     if (o.cal_points != 1 && o.cal_points != 2) return fail(ctx, MPR_EINVAL, "cal_points must be 1 or 2");
+    if (o.sim_tail < 0) return fail(ctx, MPR_EINVAL, "sim_tail must be >= 0");
     if (o.n_newton < 0 || o.n_newton > 65533) return fail(ctx, MPR_EINVAL, "n_newton in [0, 65533]");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
@@ -810,6 +811,7 @@ void mpr_default_options(mpr_options* o) {
     o->t_init = 0.1f;
     o->sim_graph = 0;
     o->cal_points = 1;
+    o->sim_tail = 0;
     o->cuda_stream = nullptr;
 }
 
@@ -1483,6 +1485,81 @@ done:
     return st;
 }
 
+// The rest of the sweep loop as one cooperative launch (the stop tail, when
+// few pairs still run). *ran is false when the device or the grid does not
+// allow the launch (then nothing ran and the per-launch loop goes on).
+mpr_status simulate_tail(mpr_ctx* ctx, bool* ran) {
+    *ran = false;
+    const int per_sm = ctx->coop ? sim_tail_blocks_per_sm(ctx->G, ctx->storage) : 0;
+    if (per_sm < 1) return MPR_OK;
+    const mpr_options& o = ctx->opt;
+    SimTailArgs a{};
+    a.sw = sweep_args(ctx, 0, true);
+    a.sw.energy = 1;
+    for (int c = 0; c < 2; ++c) {
+        a.list[c] = ctx->list[c];
+        a.start[c] = ctx->start[c];
+        a.split[c] = ctx->split[c];
+    }
+    StopArgs& st = a.st;
+    st.G = ctx->G;
+    st.groups = ctx->groups;
+    st.Rp = ctx->Rp;
+    st.nblk = ctx->g.nblk;
+    st.n_max = o.n_max;
+    st.of_block = ctx->d_of_block;
+    st.es = ctx->es;
+    st.inb = ctx->inb;
+    st.Nsp = ctx->Nsp;
+    st.eacc = ctx->eacc;
+    st.ecur = ctx->ecur;
+    st.sigma = ctx->sigma;
+    st.running = ctx->running;
+    st.stop = ctx->stop;
+    st.tcount = ctx->tcount;
+    st.e_last = ctx->e_last;
+    a.ctl = ctx->ctl;
+    a.work_all = ctx->work;
+    a.bar = ctx->bar;
+    a.spin_limit = (unsigned long long)o.wait_ms * 10000ull;   // ~100 ns per poll
+    GridBarrier hb{0u, 0u, 0u, (unsigned int)o.barrier_test};
+    CK(cudaMemcpyAsync(ctx->bar, &hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (o.profile) {
+        e0 = get_event(ctx);
+        e1 = get_event(ctx);
+        if (e0) cudaEventRecord(e0, ctx->s);
+    }
+    const cudaError_t le = launch_sim_tail(a, ctx->G, ctx->storage, ctx->n_sm * per_sm, ctx->s);
+    if (le != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) ctx->ev_pool.push_back(e0);
+        if (e1) ctx->ev_pool.push_back(e1);
+        return MPR_OK;
+    }
+    *ran = true;
+    ++ctx->launches;
+    if (e0 && e1) {
+        cudaEventRecord(e1, ctx->s);
+        ctx->ev_sim.emplace_back(e0, e1);
+    }
+    CK(cudaMemcpyAsync(&hb, ctx->bar, sizeof(hb), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    if (hb.err)
+        return fail(ctx, MPR_ETIMEOUT,
+                    "simulate: a grid-barrier wait gave up after %d ms; the batch did not "
+                    "complete", o.wait_ms);
+    // Sweeps run by the launch: from the host's count to the device's last.
+    const int t_end = (int)ctx->h_ctl->t - 1;
+    if (t_end > ctx->t) {
+        ctx->sim_halfstep_launches += 2 * (int64_t)(t_end - ctx->t);
+        ctx->t = t_end;
+    }
+    ctx->bound = ctx->h_ctl->n_running;
+    return MPR_OK;
+}
+
 mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
     if (!ctx) return MPR_EINVAL;
     TRY(mpr_sim_begin(ctx, n));
@@ -1500,6 +1577,7 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
     if (!ev[0] || !ev[1]) return fail(ctx, MPR_ECUDA, "cudaEventCreate failed");
     int c = 0;
     mpr_status st = MPR_OK;
+    bool tail = ctx->opt.sim_tail > 0;
     while (ctx->t < ctx->opt.n_max) {
         for (int i = 0; i < chunk && ctx->t < ctx->opt.n_max && st == MPR_OK; ++i) st = sweep_once(ctx);
         if (st != MPR_OK) break;
@@ -1518,6 +1596,13 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
             // the work of every sweep queued from now on.
             ctx->bound = flag[(c - 1) & 1];
             if (ctx->bound == 0) break;
+            // Few pairs left: the rest of the loop as one cooperative launch.
+            if (tail && ctx->bound < (unsigned long long)ctx->opt.sim_tail) {
+                bool ran = false;
+                st = simulate_tail(ctx, &ran);
+                if (st != MPR_OK || ran) break;
+                tail = false;
+            }
         }
         ++c;
     }

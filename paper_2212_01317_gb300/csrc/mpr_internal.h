@@ -136,6 +136,23 @@ struct SweepArgs {
     int t_fixed;              // > 0: sweep index of this launch (else read from ctl)
 };
 
+// Per-(block, realization) bookkeeping of the stop test (Sec. 3.4 reading):
+// the operands of the targeted and the closing parts of a sweep's test.
+struct StopArgs {
+    int G, groups, Rp, nblk, n_max;
+    const int32_t* of_block;  // [nblk] slice of every block
+    const double* es;         // [nblk] e_s,b
+    const double* inb;       // [nblk] 1 / N_b
+    const int32_t* Nsp;       // [nblk] sample bonds (0: not targeted)
+    float* eacc;              // [nblk][Rp] the sweep's change (folded and cleared)
+    double* ecur;             // [nblk][Rp] E_b
+    const int8_t* sigma;      // [nblk][Rp] side of e_s,b at t = 0
+    uint8_t* running;         // [nblk][Rp]
+    int32_t* stop;            // [nblk][Rp] stop sweep
+    int32_t* tcount;          // [n_slices][Rp] running targeted blocks
+    double* e_last;           // [nblk][Rp] e_b after the last test
+};
+
 // The calibration's per-sweep fold (E_b += the sweep's change; the measured
 // sweeps' e_b summed), run by extra CTAs of the next half-step's launch.
 struct FoldArgs {
@@ -155,6 +172,22 @@ struct GridBarrier {
     unsigned int gen;      // barriers completed
     unsigned int err;      // 1: a wait gave up (the launch returned early)
     unsigned int extra;    // test hook: arrivals awaited beyond the grid (0 normally)
+};
+
+// The simulation's stop tail as one cooperative launch: sweeps (two
+// half-steps over the worklist, then the two parts of the stop test) until
+// no pair runs or the sweep index passes n_max, phases separated by grid
+// barriers; the barrier closing a sweep also advances the Control.
+struct SimTailArgs {
+    SweepArgs sw;              // colour-independent sweep fields
+    const uint2* list[2];
+    const int32_t* start[2];
+    const int32_t* split[2];
+    StopArgs st;
+    Control* ctl;
+    uint32_t* work_all;        // the two worklists (sw.work_stride apart)
+    GridBarrier* bar;
+    unsigned long long spin_limit;
 };
 
 // The persistent calibration kernel's arguments.

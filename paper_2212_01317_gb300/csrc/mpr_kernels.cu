@@ -435,90 +435,41 @@ __global__ void k_stop_init(int nblk, int Rp, const int32_t* __restrict__ of_blo
     }
 }
 
-// The stop test after sweep t, over the items of the sweep's worklist (every
-// running (block, realization) pair belongs to one of them), in two kernels:
-// the second needs the final per-realization count of running targeted
-// blocks, which the first completes.
+// The stop test after sweep t in two kernels (stop_targeted_range, then
+// stop_rest_range): the second needs the final per-realization count of
+// running targeted blocks, which the first completes.
 //
-// k_stop_targeted: E_b += the sweep's change (eacc, then cleared);
-// e_b = E_b / N_b; a targeted block stops once sigma (e_b(t) - e_s,b) >= 0.
-// One thread per (item, lane).
-__global__ void k_stop_targeted(int G, int groups, int Rp, const int32_t* __restrict__ of_block,
-                                Control* __restrict__ ctl,
-                                const uint32_t* __restrict__ work, uint32_t work_stride,
-                                const double* __restrict__ es, const double* __restrict__ inb,
-                                const int32_t* __restrict__ Nsp, float* __restrict__ eacc,
-                                double* __restrict__ ecur, const int8_t* __restrict__ sigma,
-                                uint8_t* __restrict__ running, int32_t* __restrict__ stop,
-                                int32_t* __restrict__ tcount, double* __restrict__ e_last) {
+// k_stop_targeted: one thread per (item, lane) of the sweep's worklist.
+__global__ void k_stop_targeted(StopArgs sa, Control* __restrict__ ctl,
+                                const uint32_t* __restrict__ work, uint32_t work_stride) {
     grid_dep_launch();
     grid_dep_wait();
     const uint32_t t_sweep = ctl->t;
     const uint32_t* w = work + (size_t)(t_sweep & 1u) * work_stride;
-    const int64_t n = (int64_t)ctl->n_work[t_sweep & 1u] * G;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t item = w[i / G];
-        const int b = (int)(item / (uint32_t)groups);
-        const int r = (int)(item % (uint32_t)groups) * G + (int)(i % G);
-        const size_t k = (size_t)b * Rp + r;
-        if (!running[k]) continue;
-        const double E = ecur[k] + (double)eacc[k];
-        eacc[k] = 0.0f;
-        ecur[k] = E;
-        const double e = E * inb[b];
-        e_last[k] = e;
-        if (Nsp[b] == 0) continue;
-        const int sg = sigma[k];
-        const bool reached = sg > 0 ? (e >= es[b]) : (sg < 0 ? (e <= es[b]) : true);
-        if (reached) {
-            running[k] = 0;
-            stop[k] = (int32_t)t_sweep;
-            atomicSub(&tcount[of_block[b] * Rp + r], 1);
-        }
-    }
+    const int64_t n = (int64_t)ctl->n_work[t_sweep & 1u] * sa.G;
+    stop_targeted_range(sa, t_sweep, w, n, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                        (int64_t)gridDim.x * blockDim.x);
 }
 
-// k_stop_rest: blocks without sample bonds stop when no targeted block of
-// their realization runs; everything stops at n_max. Items with a lane still
-// running go on the next sweep's worklist. One thread per item of the
-// worklist (`work` == nullptr: every item, as at t = 0). The CTA that
-// finishes last closes the sweep: t + 1, the next worklist's size, the
-// running count, and a cleared counter for the list after it.
-__global__ void k_stop_rest(int nblk, int groups, int G, int Rp, int n_max,
-                            const int32_t* __restrict__ of_block, cudaGraphConditionalHandle cond,
+// k_stop_rest: one thread per item of the worklist (`work` == nullptr: every
+// item, as at t = 0); items with a lane still running go on the next sweep's
+// worklist. The CTA that finishes last closes the sweep: t + 1, the next
+// worklist's size, the running count, and a cleared counter for the list
+// after it.
+__global__ void k_stop_rest(StopArgs sa, cudaGraphConditionalHandle cond,
                             Control* __restrict__ ctl, const uint32_t* __restrict__ work,
-                            uint32_t* __restrict__ work_all, uint32_t work_stride,
-                            const int32_t* __restrict__ Nsp, uint8_t* __restrict__ running,
-                            int32_t* __restrict__ stop, const int32_t* __restrict__ tcount) {
+                            uint32_t* __restrict__ work_all, uint32_t work_stride) {
     grid_dep_launch();
     grid_dep_wait();
     const uint32_t t_sweep = ctl->t;
     const uint32_t par = t_sweep & 1u, nxt = par ^ 1u;
     const uint32_t* w = work ? work + (size_t)par * work_stride : nullptr;
     uint32_t* out = work_all + (size_t)nxt * work_stride;
-    const int64_t n = w ? (int64_t)ctl->n_work[par] : (int64_t)nblk * groups;
-    unsigned cnt = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t item = w ? w[i] : (uint32_t)i;
-        const int b = (int)(item / (uint32_t)groups), grp = (int)(item % (uint32_t)groups);
-        const int32_t* tc = tcount + (size_t)(of_block[b] < 0 ? 0 : of_block[b]) * Rp;
-        bool any = false;
-        for (int g = 0; g < G; ++g) {
-            const int r = grp * G + g;
-            const size_t k = (size_t)b * Rp + r;
-            if (!running[k]) continue;
-            if ((Nsp[b] == 0 && tc[r] == 0) || (int)t_sweep >= n_max) {
-                running[k] = 0;
-                stop[k] = (int32_t)t_sweep;
-            } else {
-                ++cnt;
-                any = true;
-            }
-        }
-        if (any) out[atomicAdd(&ctl->n_work[nxt], 1u)] = item;
-    }
+    const int64_t n = w ? (int64_t)ctl->n_work[par] : (int64_t)sa.nblk * sa.groups;
+    const int n_max = sa.n_max;
+    unsigned cnt = stop_rest_range(sa, t_sweep, w, n, out, &ctl->n_work[nxt],
+                                   blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                                   (int64_t)gridDim.x * blockDim.x);
     for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&ctl->n_running_acc, (unsigned long long)cnt);
     // Last CTA out closes the sweep (every other CTA's atomics are visible to
@@ -1204,16 +1155,40 @@ void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, in
                           const double* es, const double* inb, const int32_t* Nsp, float* eacc,
                           double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
                           int32_t* tcount, double* e_last, cudaStream_t s) {
-    launch_pdl(k_stop_targeted, grid, 256, s, G, groups, Rp, of_block, ctl, work, work_stride, es,
-               inb, Nsp, eacc, ecur, sigma, running, stop, tcount, e_last);
+    StopArgs sa{};
+    sa.G = G;
+    sa.groups = groups;
+    sa.Rp = Rp;
+    sa.of_block = of_block;
+    sa.es = es;
+    sa.inb = inb;
+    sa.Nsp = Nsp;
+    sa.eacc = eacc;
+    sa.ecur = ecur;
+    sa.sigma = sigma;
+    sa.running = running;
+    sa.stop = stop;
+    sa.tcount = tcount;
+    sa.e_last = e_last;
+    launch_pdl(k_stop_targeted, grid, 256, s, sa, ctl, work, work_stride);
 }
 
 void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int32_t* of_block,
                       int grid, Control* ctl, const uint32_t* work, uint32_t* work_all,
                       uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
                       const int32_t* tcount, cudaGraphConditionalHandle cond, cudaStream_t s) {
-    launch_pdl(k_stop_rest, grid, 256, s, nblk, groups, G, Rp, n_max, of_block, cond, ctl, work,
-               work_all, work_stride, Nsp, running, stop, tcount);
+    StopArgs sa{};
+    sa.G = G;
+    sa.groups = groups;
+    sa.Rp = Rp;
+    sa.nblk = nblk;
+    sa.n_max = n_max;
+    sa.of_block = of_block;
+    sa.Nsp = Nsp;
+    sa.running = running;
+    sa.stop = stop;
+    sa.tcount = const_cast<int32_t*>(tcount);
+    launch_pdl(k_stop_rest, grid, 256, s, sa, cond, ctl, work, work_all, work_stride);
 }
 
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,

@@ -118,6 +118,10 @@ void launch_energy_vjp(int nblk, int nbx, const int32_t* Nb, const double* M, co
                        double* out, cudaStream_t s);
 void launch_set_tag(Control* ctl, uint32_t tag, cudaStream_t s);
 
+// The realizations' stop tail as one cooperative launch (mpr_simtail.cu).
+int sim_tail_blocks_per_sm(int G, int storage);
+cudaError_t launch_sim_tail(const SimTailArgs& a, int G, int storage, int grid, cudaStream_t s);
+
 int cal_persistent_blocks_per_sm(int G);
 cudaError_t launch_cal_persistent(const CalPersistArgs& a, int G, int grid, cudaStream_t s);
 

@@ -5,10 +5,8 @@
 // launch and a wave of latency 2 x (n_eq + n_meas) x n_bisect times. Here the
 // phases are separated by a grid-wide barrier instead.
 //
-// The barrier never waits forever: a CTA that has waited `spin_limit` polls
-// sets the error flag and returns, and every CTA that sees the flag returns
-// too; the host then reports MPR_ETIMEOUT. A test hook (`extra`) makes the
-// barrier wait for arrivals that never come, to exercise that path.
+// The phases are separated by grid_sync (mpr_sweep.cuh), which never waits
+// forever: the host then reports MPR_ETIMEOUT.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,53 +17,6 @@
 namespace mpr {
 
 namespace {
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Grid-wide barrier over all CTAs of a cooperative launch. `gen` is the
-// generation this CTA last passed (kept by thread 0). Returns false if the
-// wait gave up here or elsewhere.
-__device__ bool grid_sync(GridBarrier* bar, unsigned int& gen, unsigned long long limit) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = ld_acquire(&bar->err) == 0;
-        if (ok) {
-            const unsigned int target = gen + 1;
-            const unsigned int expect = gridDim.x + bar->extra;
-            __threadfence();
-            const unsigned int arrived = atomicAdd(&bar->arrive, 1u) + 1u;
-            if (arrived == expect) {
-                atomicExch(&bar->arrive, 0u);
-                __threadfence();
-                atomicExch(&bar->gen, target);
-            } else {
-                unsigned long long spins = 0;
-                while (ld_acquire(&bar->gen) != target) {
-                    if (ld_acquire(&bar->err) != 0) {
-                        ok = 0;
-                        break;
-                    }
-                    if (++spins > limit) {
-                        atomicExch(&bar->err, 1u);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(100);
-                }
-            }
-            __threadfence();
-            gen = target;
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 __device__ __forceinline__ SweepArgs colour_args(const CalPersistArgs& a, int c) {
     SweepArgs s = a.sw;

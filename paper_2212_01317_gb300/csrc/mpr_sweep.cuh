@@ -461,6 +461,140 @@ __device__ __forceinline__ void energy_item(const SweepArgs& a, int item, int wi
     if (v[5] != 0.0) atomicAdd(ea - up + 1, v[5]);
 }
 
+// The stop test after sweep t_sweep, on the items of the sweep's worklist
+// (every running (block, realization) pair belongs to one of them), in two
+// parts: the second needs the final per-realization count of running
+// targeted blocks, which the first completes.
+//
+// Targeted part: E_b += the sweep's change (eacc, then cleared); e_b = E_b / N_b;
+// a targeted block stops once sigma (e_b(t) - e_s,b) >= 0. Entries
+// i = i0, i0 + step, ... < n of (item, lane) pairs (n = items * G).
+__device__ __forceinline__ void stop_targeted_range(const StopArgs& s, uint32_t t_sweep,
+                                                    const uint32_t* __restrict__ w, int64_t n,
+                                                    int64_t i0, int64_t step) {
+    for (int64_t i = i0; i < n; i += step) {
+        const uint32_t item = w[i / s.G];
+        const int b = (int)(item / (uint32_t)s.groups);
+        const int r = (int)(item % (uint32_t)s.groups) * s.G + (int)(i % s.G);
+        const size_t k = (size_t)b * s.Rp + r;
+        if (!s.running[k]) continue;
+        const double E = s.ecur[k] + (double)s.eacc[k];
+        s.eacc[k] = 0.0f;
+        s.ecur[k] = E;
+        const double e = E * s.inb[b];
+        s.e_last[k] = e;
+        if (s.Nsp[b] == 0) continue;
+        const int sg = s.sigma[k];
+        const bool reached = sg > 0 ? (e >= s.es[b]) : (sg < 0 ? (e <= s.es[b]) : true);
+        if (reached) {
+            s.running[k] = 0;
+            s.stop[k] = (int32_t)t_sweep;
+            atomicSub(&s.tcount[s.of_block[b] * s.Rp + r], 1);
+        }
+    }
+}
+
+// Closing part: blocks without sample bonds stop when no targeted block of
+// their realization runs; everything stops at n_max. Items with a lane still
+// running are appended to `out` (counter *n_out). Items i = i0, i0 + step,
+// ... < n of the worklist w (nullptr: every item). Returns this thread's
+// count of lanes still running.
+__device__ __forceinline__ unsigned stop_rest_range(const StopArgs& s, uint32_t t_sweep,
+                                                    const uint32_t* __restrict__ w, int64_t n,
+                                                    uint32_t* __restrict__ out, uint32_t* n_out,
+                                                    int64_t i0, int64_t step) {
+    unsigned cnt = 0;
+    for (int64_t i = i0; i < n; i += step) {
+        const uint32_t item = w ? w[i] : (uint32_t)i;
+        const int b = (int)(item / (uint32_t)s.groups), grp = (int)(item % (uint32_t)s.groups);
+        const int32_t* tc = s.tcount + (size_t)(s.of_block[b] < 0 ? 0 : s.of_block[b]) * s.Rp;
+        bool any = false;
+        for (int g = 0; g < s.G; ++g) {
+            const int r = grp * s.G + g;
+            const size_t k = (size_t)b * s.Rp + r;
+            if (!s.running[k]) continue;
+            if ((s.Nsp[b] == 0 && tc[r] == 0) || (int)t_sweep >= s.n_max) {
+                s.running[k] = 0;
+                s.stop[k] = (int32_t)t_sweep;
+            } else {
+                ++cnt;
+                any = true;
+            }
+        }
+        if (any) out[atomicAdd(n_out, 1u)] = item;
+    }
+    return cnt;
+}
+
+// ------------------------------------------------- grid-wide barrier --
+// For cooperative launches (the persistent calibration and the simulation's
+// stop tail). The barrier never waits forever: a CTA that has waited `limit`
+// polls sets the error flag and returns false, and every CTA that sees the
+// flag returns false too; the host then reports MPR_ETIMEOUT. A test hook
+// (`extra`) makes the barrier wait for arrivals that never come, to exercise
+// that path.
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier over all CTAs of the launch. `gen` is the generation this CTA last
+// passed (kept by thread 0). The last CTA to arrive runs last() (thread 0)
+// before it releases the others, so its writes are visible to every CTA
+// after the barrier. Returns false if the wait gave up here or elsewhere.
+template <typename F>
+__device__ bool grid_sync_then(GridBarrier* bar, unsigned int& gen, unsigned long long limit,
+                               F&& last) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = ld_acquire(&bar->err) == 0;
+        if (ok) {
+            const unsigned int target = gen + 1;
+            const unsigned int expect = gridDim.x + bar->extra;
+            __threadfence();
+            const unsigned int arrived = atomicAdd(&bar->arrive, 1u) + 1u;
+            if (arrived == expect) {
+                __threadfence();
+                last();
+                atomicExch(&bar->arrive, 0u);
+                __threadfence();
+                atomicExch(&bar->gen, target);
+            } else {
+                unsigned long long spins = 0;
+                while (ld_acquire(&bar->gen) != target) {
+                    if (ld_acquire(&bar->err) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (++spins > limit) {
+                        atomicExch(&bar->err, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            __threadfence();
+            gen = target;
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int& gen,
+                                          unsigned long long limit) {
+    return grid_sync_then(bar, gen, limit, [] {});
+}
+
 // Median of the targeted blocks' T by a radix select over the (positive)
 // float bit patterns, run by one CTA over the blocks of one slice (the block
 // rectangle bk = (by0, bx0, nby_s, nbx_s) of a canvas nbx blocks wide); k is

@@ -49,6 +49,7 @@ int main(void) {
   printf("mpr_grid3 %zu\\nmpr3_info %zu\\nmpr_tuning %zu\\nmpr_profile %zu\\n",
          sizeof(mpr_grid3), sizeof(mpr3_info), sizeof(mpr_tuning), sizeof(mpr_profile));
   O(mpr_options, cal_method); O(mpr_options, t_init); O(mpr_options, sim_graph);
+  O(mpr_options, cal_points); O(mpr_options, sim_tail);
   O(mpr_info, n_slices); O(mpr3_info, n_gap); O(mpr3_info, cal_gap_updates);
   O(mpr_tuning, ms);
   O(mpr_options, seed); O(mpr_options, slice_id); O(mpr_options, t_lo);

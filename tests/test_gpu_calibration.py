@@ -43,7 +43,10 @@ def test_persistent_equals_graph(H, W, lb, chains, kind):
 
 def test_barrier_timeout_is_reported_and_device_stays_usable():
     z, m = synth.small_problem(40, 40, 0.5, seed=3)
-    gf = make(z, m, 8, cal_mode=2, barrier_test=1, wait_ms=100, n_bisect=2, n_eq=2, n_meas=2)
+    # (sim_tail = 0: the hook applies to every grid barrier of the context,
+    # and the simulation below is to run the per-launch loop.)
+    gf = make(z, m, 8, cal_mode=2, barrier_test=1, wait_ms=100, n_bisect=2, n_eq=2, n_meas=2,
+              sim_tail=0)
     with pytest.raises(MprError) as e:
         gf.calibrate()
     assert e.value.status == MPR_ETIMEOUT

@@ -16,7 +16,8 @@ import pytest
 
 import oracle
 from paper_2212_01317_gb300 import synth
-from paper_2212_01317_gb300.mpr import GapFiller, MprError, MPR_ENOSAMPLES, MPR_EINVAL, MPR_ESTATE
+from paper_2212_01317_gb300.mpr import (GapFiller, MprError, MPR_ENOSAMPLES, MPR_EINVAL, MPR_ESTATE,
+                                        MPR_ETIMEOUT)
 
 from parity import TWO_PI, checkerboard, compare_site_updates
 
@@ -476,3 +477,51 @@ def test_context_memory_is_pooled_and_released():
     # energy atomics, which can only move a stop decision at an exact tie).
     for p in preds[1:]:
         assert np.mean(np.abs(p - preds[0])) < 1e-3 * (z.max() - z.min())
+
+
+# ------------------------------------------------------ stop tail launch --
+@pytest.mark.parametrize("group,R,storage", [(8, 20, 0), (2, 2, 0), (8, 12, 1)])
+def test_stop_tail_launch_equals_per_launch_loop(group, R, storage):
+    """mpr_simulate runs the sweeps after the running count falls below
+    sim_tail as one cooperative launch; the stop sweep of every (block,
+    realization) pair and the prediction equal those of the per-launch loop
+    (sim_tail = 0), up to the order of the FP32 energy atomics, which can only
+    move a stop decision at an exact tie."""
+    H, W, lb = 72, 64, 8
+    z, m = problem(H, W, 0.55, seed=23, kind="disc")
+    rng = np.random.default_rng(4)
+    T = None
+    out = {}
+    for tail in (0, 1 << 20, 64):
+        gf = make(z, m, lb, seed=77, group=group, storage=storage, n_max=120, sim_tail=tail)
+        if T is None:
+            T = rng.uniform(0.02, 0.5, gf.nblk).astype(np.float32)
+        gf.set_temperatures(T)
+        gf.simulate(R)
+        info = gf.refresh()
+        out[tail] = (gf.predict()[0], info.gap_updates)
+        gf.close()
+    base_pred, base_upd = out[0]
+    for tail in (1 << 20, 64):
+        pred, upd = out[tail]
+        assert abs(upd - base_upd) <= max(1, base_upd // 2000), (tail, upd, base_upd)
+        assert np.mean(np.abs(pred - base_pred)) < 1e-3 * (z.max() - z.min()), tail
+
+
+def test_stop_tail_barrier_wait_is_bounded():
+    """A grid-barrier wait that never completes (test hook: the barrier waits
+    for arrivals that never come) gives up after wait_ms and the call
+    reports MPR_ETIMEOUT; the context's stream stays usable."""
+    import torch
+    z, m = problem(40, 40, 0.5, seed=8)
+    gf = make(z, m, 8, seed=3, sim_tail=1 << 20, barrier_test=1, wait_ms=50)
+    gf.set_temperatures(np.full(gf.nblk, 0.2, np.float32))
+    with pytest.raises(MprError) as ei:
+        gf.simulate(4)
+    assert ei.value.status == MPR_ETIMEOUT
+    gf.close()
+    torch.cuda.synchronize()
+    gf = make(z, m, 8, seed=3)
+    gf.set_temperatures(np.full(gf.nblk, 0.2, np.float32))
+    gf.simulate(4)
+    gf.close()
