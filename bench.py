@@ -51,9 +51,10 @@ def parse():
                     help="element type of the realizations' angles (arithmetic stays FP32)")
     ap.add_argument("--cal-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="calibration launch form (3: every kernel from the host, for profilers)")
-    ap.add_argument("--cal-points", type=int, default=1, choices=[1, 2],
+    ap.add_argument("--cal-points", type=int, default=2, choices=[1, 2],
                     help="calibration temperatures per block and iteration (1 bisection, "
-                         "2 trisection); --cal-iters sets the iterations")
+                         "2 trisection, the default: the two temperatures run on the two "
+                         "lanes of a realization pair); --cal-iters sets the iterations")
     ap.add_argument("--cal-iters", type=int, default=None,
                     help="calibration iterations (default 24 for bisection, 16 for trisection)")
     ap.add_argument("--plain-sample", type=int, default=0,

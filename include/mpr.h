@@ -103,6 +103,9 @@ typedef struct {
                             (default: measured slower than the per-launch loop with
                             programmatic launches; ignored by sim_graph and where cooperative
                             launch is unavailable) */
+    int32_t sweep_form;  /* realizations' half-step: -1 automatic (default: one warp per
+                            realization pair while many pairs run, two, then four as fewer
+                            remain), 0, 1, 2: always one, two or four warps per pair */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 

@@ -107,7 +107,7 @@ struct mpr_ctx {
     size_t blk_cap = 0, lane_cap = 0, work_cap = 0;
     Control* ctl = nullptr;      // device loop state
     Control* h_ctl = nullptr;    // pinned mirror
-    int grid_cache[2][3][2] = {};  // full grid of k_sweep by (G = 2 / 8, storage, wide)
+    int grid_cache[2][3][3] = {};  // full grid of k_sweep by (G = 2 / 8, storage, form)
     unsigned long long bound = ~0ull;  // upper bound of the running pairs (from the last read)
     int wide_always = 0;         // autotuned: the wide sweep form for every sweep
     bool energy_dirty = false;
@@ -217,6 +217,8 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.cal_method != 0 && o.cal_method != 1) return fail(ctx, MPR_EINVAL, "cal_method must be 0 or 1");
     if (o.cal_points != 1 && o.cal_points != 2) return fail(ctx, MPR_EINVAL, "cal_points must be 1 or 2");
     if (o.sim_tail < 0) return fail(ctx, MPR_EINVAL, "sim_tail must be >= 0");
+    if (o.sweep_form < -1 || o.sweep_form > 2)
+        return fail(ctx, MPR_EINVAL, "sweep_form must be -1, 0, 1 or 2");
     if (o.n_newton < 0 || o.n_newton > 65533) return fail(ctx, MPR_EINVAL, "n_newton in [0, 65533]");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
@@ -324,16 +326,23 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
     return a;
 }
 
-// Few items left (the realizations' tail): the wide form, and a grid no
-// larger than the running pairs can fill.
-bool sweep_wide(mpr_ctx* ctx) {
-    return ctx->wide_always || ctx->bound < (unsigned long long)ctx->n_sm * 4;
+// Running pairs per SM below which the half-step takes four warps per
+// realization pair (form 2), and a grid no larger than the running pairs can
+// fill. (Measured on the 1024² bench batch: two warps per pair below 32 to
+// 512 pairs per SM made the batch 0.1 to 0.7 ms slower, one warp throughout
+// ties with this choice; the stop tail costs launches, not passes.)
+constexpr unsigned long long kForm2PairsPerSm = 4;
+
+int sweep_form(mpr_ctx* ctx) {
+    if (ctx->opt.sweep_form >= 0) return ctx->opt.sweep_form;
+    if (ctx->wide_always) return 2;
+    return ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm ? 2 : 0;
 }
 
-int sweep_grid(mpr_ctx* ctx, bool wide) {
-    int& full = ctx->grid_cache[ctx->G == 2 ? 0 : 1][ctx->storage][wide ? 1 : 0];
-    if (full == 0) full = ctx->n_sm * sweep_blocks_per_sm(ctx->G, ctx->storage, wide);
-    const unsigned long long ipc = (unsigned long long)sweep_items_per_cta(ctx->G, wide);
+int sweep_grid(mpr_ctx* ctx, int form) {
+    int& full = ctx->grid_cache[ctx->G == 2 ? 0 : 1][ctx->storage][form];
+    if (full == 0) full = ctx->n_sm * sweep_blocks_per_sm(ctx->G, ctx->storage, form);
+    const unsigned long long ipc = (unsigned long long)sweep_items_per_cta(ctx->G, form);
     const unsigned long long need = (ctx->bound + ipc - 1) / ipc;
     return (int)std::max<unsigned long long>(1, std::min<unsigned long long>(full, need));
 }
@@ -446,8 +455,8 @@ mpr_status sweep_once(mpr_ctx* ctx) {
         if (e0) cudaEventRecord(e0, ctx->s);
     }
     for (int c = 0; c < 2; ++c) {
-        const bool wide = sweep_wide(ctx);
-        launch_sweep(sweep_args(ctx, c, true), ctx->G, ctx->storage, wide, sweep_grid(ctx, wide),
+        const int form = sweep_form(ctx);
+        launch_sweep(sweep_args(ctx, c, true), ctx->G, ctx->storage, form, sweep_grid(ctx, form),
                      ctx->s);
         CKL();
         ++ctx->sim_halfstep_launches;
@@ -812,6 +821,7 @@ void mpr_default_options(mpr_options* o) {
     o->sim_graph = 0;
     o->cal_points = 1;
     o->sim_tail = 0;
+    o->sweep_form = -1;
     o->cuda_stream = nullptr;
 }
 
@@ -1630,7 +1640,7 @@ mpr_status mpr_halfstep(mpr_ctx* ctx, int32_t colour, int32_t t, int32_t tag) {
     a.energy = 0;
     const unsigned long long bound = ctx->bound;
     ctx->bound = ~0ull;
-    launch_sweep(a, ctx->G, ctx->storage, false, sweep_grid(ctx, false), ctx->s);
+    launch_sweep(a, ctx->G, ctx->storage, 0, sweep_grid(ctx, 0), ctx->s);
     ctx->bound = bound;
     CKL();
     CK(cudaStreamSynchronize(ctx->s));

@@ -336,7 +336,7 @@ __global__ void k_fill_samples(Geom g, const uint8_t* __restrict__ mask,
 //     items left at the end of a batch finish in one pass over their entries.
 //   G = 2 (one pair): WPI = 1, four items per CTA; tail form WPI = 4.
 template <int G, typename S, int WPI, int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 8 : 2) k_sweep(SweepArgs a) {
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_sweep(SweepArgs a) {
     grid_dep_launch();
     grid_dep_wait();
     const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
@@ -1066,49 +1066,62 @@ void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, 
 }
 
 namespace {
+// The three forms of the realizations' half-step, by warps per item (WPI)
+// and CTA size (all at 1024 threads per SM):
+//   form 0: one warp per realization pair (G = 8: WPI 4, one item per
+//           128-thread CTA; G = 2: WPI 1, four items per CTA);
+//   form 1: two warps per pair, splitting a block's entries (WPI 8, 256
+//           threads; G = 2: WPI 2, two items per CTA);
+//   form 2: four warps per pair (WPI 16, 512 threads; G = 2: WPI 4).
+// Fewer running pairs, more warps per pair: the few items left finish in
+// fewer passes over their entries.
 template <int G, typename S>
-void sweep_dispatch(const SweepArgs& a, bool wide, int grid, cudaStream_t s) {
+void sweep_dispatch(const SweepArgs& a, int form, int grid, cudaStream_t s) {
     if constexpr (G == 2) {
-        if (wide) launch_pdl(k_sweep<2, S, 4, 128>, grid, 128, s, a);
+        if (form == 2) launch_pdl(k_sweep<2, S, 4, 128>, grid, 128, s, a);
+        else if (form == 1) launch_pdl(k_sweep<2, S, 2, 128>, grid, 128, s, a);
         else launch_pdl(k_sweep<2, S, 1, 128>, grid, 128, s, a);
     } else {
-        if (wide) launch_pdl(k_sweep<8, S, 16, 512>, grid, 512, s, a);
+        if (form == 2) launch_pdl(k_sweep<8, S, 16, 512>, grid, 512, s, a);
+        else if (form == 1) launch_pdl(k_sweep<8, S, 8, 256>, grid, 256, s, a);
         else launch_pdl(k_sweep<8, S, 4, 128>, grid, 128, s, a);
     }
 }
 
 template <int G, typename S>
-int sweep_occupancy(bool wide) {
+int sweep_occupancy(int form) {
     int n = 0;
     if constexpr (G == 2) {
-        if (wide) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 4, 128>, 128, 0);
+        if (form == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 4, 128>, 128, 0);
+        else if (form == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 2, 128>, 128, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 1, 128>, 128, 0);
     } else {
-        if (wide) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 16, 512>, 512, 0);
+        if (form == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 16, 512>, 512, 0);
+        else if (form == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 8, 256>, 256, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 4, 128>, 128, 0);
     }
     return n > 0 ? n : 1;
 }
 }  // namespace
 
-void launch_sweep(const SweepArgs& a, int G, int storage, bool wide, int grid, cudaStream_t s) {
+void launch_sweep(const SweepArgs& a, int G, int storage, int form, int grid, cudaStream_t s) {
     with_storage(storage, [&](auto tag) {
         using S = typename decltype(tag)::type;
-        if (G == 2) sweep_dispatch<2, S>(a, wide, grid, s);
-        else sweep_dispatch<8, S>(a, wide, grid, s);
+        if (G == 2) sweep_dispatch<2, S>(a, form, grid, s);
+        else sweep_dispatch<8, S>(a, form, grid, s);
     });
 }
 
-int sweep_blocks_per_sm(int G, int storage, bool wide) {
+int sweep_blocks_per_sm(int G, int storage, int form) {
     int n = 1;
     with_storage(storage, [&](auto tag) {
         using S = typename decltype(tag)::type;
-        n = G == 2 ? sweep_occupancy<2, S>(wide) : sweep_occupancy<8, S>(wide);
+        n = G == 2 ? sweep_occupancy<2, S>(form) : sweep_occupancy<8, S>(form);
     });
     return n;
 }
 
-int sweep_items_per_cta(int G, bool wide) { return (G == 2 && !wide) ? 4 : 1; }
+int sweep_items_per_cta(int G, int form) { return G == 2 ? 4 >> form : 1; }
 
 void launch_energy(const SweepArgs& a, int G, int storage, int n_sm, cudaStream_t s) {
     with_storage(storage, [&](auto tag) {

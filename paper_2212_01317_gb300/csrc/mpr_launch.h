@@ -32,10 +32,11 @@ void launch_init(const Geom& g, const Slices& sl, const uint2* list, int64_t n_l
                  Rng rng, uint32_t r_even, cudaStream_t s);
 void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, void* ang,
                          int storage, int G, int groups, cudaStream_t s);
-// wide: the tail form with more warps per item (few items left).
-void launch_sweep(const SweepArgs& a, int G, int storage, bool wide, int grid, cudaStream_t s);
-int sweep_blocks_per_sm(int G, int storage, bool wide);
-int sweep_items_per_cta(int G, bool wide);
+// form 0, 1, 2: one, two or four warps per realization pair (more warps per
+// pair as fewer items are left).
+void launch_sweep(const SweepArgs& a, int G, int storage, int form, int grid, cudaStream_t s);
+int sweep_blocks_per_sm(int G, int storage, int form);
+int sweep_items_per_cta(int G, int form);
 void launch_energy(const SweepArgs& a, int G, int storage, int n_sm, cudaStream_t s);
 // fold: NULL, or the previous sweep's fold run by extra CTAs of this launch.
 void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s,

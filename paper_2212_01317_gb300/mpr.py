@@ -48,7 +48,7 @@ class mpr_options(C.Structure):
                 ("profile", C.c_int32), ("cal_mode", C.c_int32), ("wait_ms", C.c_int32),
                 ("barrier_test", C.c_int32), ("cal_method", C.c_int32), ("n_newton", C.c_int32),
                 ("t_init", C.c_float), ("sim_graph", C.c_int32), ("cal_points", C.c_int32),
-                ("sim_tail", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("sim_tail", C.c_int32), ("sweep_form", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):
