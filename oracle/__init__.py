@@ -46,7 +46,8 @@ class Model(C.Structure):
                 ("q", C.c_double), ("J", C.c_double),
                 ("key0", C.c_uint32), ("key1", C.c_uint32),
                 ("overrelax", C.c_int32), ("K", C.c_int32), ("threads", C.c_int32),
-                ("T_site", C.c_void_p), ("D", C.c_int32), ("nbz", C.c_int32)]
+                ("T_site", C.c_void_p), ("D", C.c_int32), ("nbz", C.c_int32),
+                ("storage", C.c_int32)]
 
 
 class Diag(C.Structure):
@@ -75,6 +76,7 @@ def lib():
             "orc_model_init": (None, [MP, i32, i32, i32, f64, f64, u64, u32]),
             "orc_philox4x32_10": (None, [P, P, P]),
             "orc_u01": (f64, [u32]),
+            "orc_round_store": (f64, [f64, i32]),
             "orc_site_uniforms": (None, [MP, i64, u32, u32, u32, P, P]),
             "orc_transform": (C.c_int, [i64, P, P, P, P, P]),
             "orc_backtransform": (None, [i64, P, P, P, f64, f64, P]),
@@ -130,6 +132,11 @@ def u01(x: int) -> float:
     return lib().orc_u01(int(x) & 0xFFFFFFFF)
 
 
+def round_store(v: float, storage: int) -> float:
+    """v rounded to the stored angle type (0 exact, 1 BF16, 2 FP16) via FP32."""
+    return lib().orc_round_store(float(v), int(storage))
+
+
 @dataclass
 class BlockStats:
     Es: np.ndarray
@@ -153,12 +160,13 @@ class Oracle:
 
     def __init__(self, H: int, W: int, lb: int, q: float = 0.5, J: float = 1.0,
                  seed: int = 0, slice_id: int = 0, overrelax: bool = True, K: int = 0,
-                 threads: int = 0):
+                 threads: int = 0, storage: int = 0):
         self.m = Model()
         lib().orc_model_init(C.byref(self.m), H, W, lb, q, J, seed & (2**64 - 1), slice_id)
         self.m.overrelax = 1 if overrelax else 0
         self.m.K = int(K)
         self.m.threads = int(threads)
+        self.m.storage = int(storage)     # 0 exact, 1 BF16, 2 FP16 stored gap angles
         self.H, self.W, self.lb = H, W, lb
 
     @property

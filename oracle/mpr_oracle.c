@@ -58,6 +58,42 @@ void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, do
     m->T_site = NULL;
     m->D = 1;
     m->nbz = 1;
+    m->storage = 0;
+}
+
+/* ------------------------------------------------------- stored angles -- */
+/* The precision form stores gap angles as BF16 (8 significant bits) or FP16
+ * (11, with subnormals below 2^-14) and computes in FP32: a value is first
+ * rounded to FP32, then to the stored type, each to the nearest
+ * representable value with ties to the even one. */
+static float bits_to_float(uint32_t u) {
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return f;
+}
+
+static uint32_t float_to_bits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+/* Keep the top 32 - drop bits of the FP32 pattern, rounding the dropped part
+ * to nearest, ties to even (exact while the exponent does not overflow). */
+static float round_pattern(float f, int drop) {
+    const uint32_t u = float_to_bits(f);
+    const uint32_t half = (1u << (drop - 1)) - 1u;
+    const uint32_t odd = (u >> drop) & 1u;
+    return bits_to_float((u + half + odd) & ~((1u << drop) - 1u));
+}
+
+double orc_round_store(double v, int32_t storage) {
+    if (storage == 0 || isnan(v)) return v;
+    const float f = (float)v;
+    if (storage == 1) return (double)round_pattern(f, 16);
+    /* FP16: spacing 2^-24 below 2^-14 (subnormals), else 10 fraction bits. */
+    if (fabsf(f) < 6.103515625e-05f) return (double)(nearbyintf(f * 16777216.0f) / 16777216.0f);
+    return (double)round_pattern(f, 13);
 }
 
 static int block_of(const orc_model* m, int y, int x) { return (y / m->lb) * m->nbx + x / m->lb; }
@@ -230,6 +266,10 @@ static void update_core(const orc_model* m, double* phi, int64_t i, const int64_
         int k = (int)floor((double)m->K * u0);
         if (k >= m->K) k = m->K - 1;
         phi_prop = TWO_PI * (double)k / (double)m->K;
+    } else if (m->storage != 0) {
+        /* Precision form: the FP32 product, rounded to the stored type. */
+        const float prop32 = 6.28318530717958647692f * (float)u0;
+        phi_prop = orc_round_store((double)prop32, m->storage);
     } else {
         phi_prop = TWO_PI * u0;
     }
@@ -260,7 +300,7 @@ static void update_core(const orc_model* m, double* phi, int64_t i, const int64_
             double psi = atan2(S, C);
             phi_or = (2.0 * psi - m->q * phi_new) / m->q;
             if (phi_or >= 0.0 && phi_or <= TWO_PI) {
-                phi_new = phi_or;
+                phi_new = orc_round_store(phi_or, m->storage);
                 or_applied = 1;
             }
         }

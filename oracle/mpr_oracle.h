@@ -29,7 +29,14 @@ typedef struct {
     const double* T_site;    /* NULL: block temperatures (BST); else H*W site
                                 temperatures (SST, Sec. 2.2.3) used by the updates */
     int32_t D, nbz;          /* 3-D grids (orc3_*): depth and block layers; 1 in 2-D */
+    int32_t storage;         /* stored gap angles (the precision form): 0 exact (FP64),
+                                1 BF16, 2 FP16. A proposal is the FP32 product of 2pi and
+                                u0, rounded to the stored type before its energy is taken;
+                                a reflected angle is rounded too (via FP32, ties to even). */
 } orc_model;
+
+/* v rounded to the stored type of `storage` (0: v itself), via FP32, ties to even. */
+double orc_round_store(double v, int32_t storage);
 
 void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, double J,
                     uint64_t seed, uint32_t slice);

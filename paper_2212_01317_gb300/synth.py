@@ -172,10 +172,54 @@ def _wl_field4096(seed: int = 0) -> Workload:
                     meta={"H": 4096, "W": 4096, "xi": [4, 64], "p": float(m.mean())})
 
 
+def grf_nonstationary_gpu(h: int, w: int, xi_min: float, xi_max: float, seed: int,
+                          n_levels: int = 8, device: str = "cuda") -> np.ndarray:
+    """grf_nonstationary's recipe on the GPU (torch FFTs; white noise from a
+    seeded torch generator, so the field differs from the numpy version's),
+    for grids whose host FFTs would take minutes. float32 numpy [h, w]."""
+    import torch
+    n = int(max(h, w, math.ceil(8 * xi_max)))
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    wf = torch.fft.rfft2(torch.randn((n, n), generator=gen, device=device))
+    d = torch.arange(n, device=device, dtype=torch.float32)
+    d = torch.minimum(d, n - d)
+    lx = np.linspace(math.log(xi_min), math.log(xi_max), n_levels)
+    x = np.arange(w, dtype=np.float64)
+    lxi = np.log(xi_min + (xi_max - xi_min) * x / max(w - 1, 1))
+    k = np.clip(np.searchsorted(lx, lxi, side="right") - 1, 0, n_levels - 2)
+    a = np.clip((lxi - lx[k]) / (lx[k + 1] - lx[k]), 0.0, 1.0)
+    out = torch.zeros((h, w), device=device, dtype=torch.float32)
+    for lev in range(n_levels):
+        wt = np.where(k == lev, 1.0 - a, 0.0) + np.where(k + 1 == lev, a, 0.0)
+        if not np.any(wt):
+            continue
+        r = torch.sqrt(d[:, None] ** 2 + d[None, :] ** 2)
+        spec = torch.fft.rfft2(torch.exp(-r / float(np.exp(lx[lev])))).real.clamp_min_(0.0)
+        del r
+        f = torch.fft.irfft2(torch.sqrt(spec) * wf, s=(n, n))[:h, :w]
+        del spec
+        f = (f - f.mean()) / f.std()
+        out += f * torch.as_tensor(wt, device=device, dtype=torch.float32)[None, :]
+        del f
+    out = (out - out.mean()) / out.std()
+    return out.cpu().numpy()
+
+
+def _wl_field16384(seed: int = 0) -> Workload:
+    """16384^2 non-stationary GRF (xi 8 -> 128), 70 % disc gaps, l_b = 64, R = 20,
+    BF16 state; generated on the GPU (needs CUDA)."""
+    z = grf_nonstationary_gpu(16384, 16384, 8.0, 128.0, seed)
+    m = mask_discs(16384, 16384, 0.7, seed + 1)
+    return Workload("field16384_xi8-128_disc70_lb64_R20", z, m, 64, 20, storage="bf16",
+                    meta={"H": 16384, "W": 16384, "xi": [8, 128], "p": float(m.mean())})
+
+
 WORKLOADS = {
     "field128": _wl_field128,
     "field1024": _wl_field1024,
     "field4096": _wl_field4096,
+    "field16384": _wl_field16384,
 }
 
 

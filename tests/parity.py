@@ -29,8 +29,13 @@ def checkerboard(H, W):
     return (yy + xx) & 1
 
 
-def compare_site_updates(gpu, ora, pre, diag, may_move):
-    """Returns (n_sites_checked, n_explained_flips, n_bad, message)."""
+def compare_site_updates(gpu, ora, pre, diag, may_move, storage=0):
+    """Returns (n_sites_checked, n_explained_flips, n_bad, message).
+
+    storage (1 BF16, 2 FP16): both sides round the reflected angle to the
+    stored type; a site whose reflected angle lies within rounding of the
+    midpoint between two stored values may round either way (the GPU takes
+    it from FP32 arithmetic, the oracle from FP64)."""
     gpu = np.asarray(gpu, np.float64)
     ora = np.asarray(ora, np.float64)
     pre = np.asarray(pre, np.float64)
@@ -47,8 +52,14 @@ def compare_site_updates(gpu, ora, pre, diag, may_move):
     or_tie[fin] = (np.abs(por[fin]) < TIE_PHI + tol[fin]) | \
                   (np.abs(por[fin] - TWO_PI) < TIE_PHI + tol[fin])
     acc_tie = np.abs(diag["dE"] - diag["theta"]) < TIE_E
-    explained = may_move & ~ok & (or_tie | acc_tie)
-    bad = may_move & ~ok & ~(or_tie | acc_tie)
+    round_tie = np.zeros_like(ok)
+    if storage:
+        import oracle
+        for idx in np.argwhere(may_move & ~ok & fin):
+            v, e = float(por[tuple(idx)]), float(tol[tuple(idx)])
+            round_tie[tuple(idx)] = oracle.round_store(v - e, storage) != oracle.round_store(v + e, storage)
+    explained = may_move & ~ok & (or_tie | acc_tie | round_tie)
+    bad = may_move & ~ok & ~(or_tie | acc_tie | round_tie)
     msg = ""
     if bad.any():
         idx = np.argwhere(bad)[:5]
@@ -60,3 +71,45 @@ def compare_site_updates(gpu, ora, pre, diag, may_move):
     if bad_still:
         msg += f" | {bad_still} sites moved that must not"
     return int(may_move.sum()), int(explained.sum()), int(bad.sum()) + bad_still, msg
+
+
+def sampled_sweep_parity(o, mask, T_of_site, pre, post, r, rng, n_sample, storage=0, t=1, tag=0):
+    """One sweep of realization r (colour 0 from `pre`, colour 1 from the
+    GPU's colour-0 result), recomputed by the oracle site by site at
+    n_sample sampled gap sites per colour and compared with the GPU's `post`.
+    Returns (checked, explained, bad, message); a mismatch is explained by a
+    decision within rounding of its threshold, as in compare_site_updates."""
+    import oracle
+    H, W = mask.shape
+    cb = checkerboard(H, W)
+    gaps = np.flatnonzero(mask.ravel())
+    checked = explained = bad = 0
+    msgs = []
+    post_f = post.ravel()
+    for colour in (0, 1):
+        cand = gaps[cb.ravel()[gaps] == colour]
+        if cand.size == 0:
+            continue
+        sample = rng.choice(cand, size=min(n_sample, cand.size), replace=False)
+        base = pre if colour == 0 else np.where(cb == 0, post, pre)
+        ph = base.astype(np.float64).ravel()
+        for i in sample:
+            d = o.update_site(ph, mask, int(i), float(T_of_site(int(i))), t, tag, r)
+            g = float(post_f[i])
+            tol = ATOL + RTOL_PSI / max(d.R, 1e-6)
+            checked += 1
+            if abs(g - ph[i]) <= tol:
+                continue
+            fin = np.isfinite(d.phi_or)
+            tie = abs(d.dE - d.theta) < TIE_E or (fin and (abs(d.phi_or) < TIE_PHI + tol or
+                                                           abs(d.phi_or - TWO_PI) < TIE_PHI + tol))
+            if storage and fin:
+                tie = tie or (oracle.round_store(d.phi_or - tol, storage) !=
+                              oracle.round_store(d.phi_or + tol, storage))
+            if tie:
+                explained += 1
+            else:
+                bad += 1
+                msgs.append(f"site {int(i)} colour {colour} gpu={g:.7f} ora={ph[i]:.7f} "
+                            f"dE={d.dE:.3e} th={d.theta:.3e} R={d.R:.3e}")
+    return checked, explained, bad, "; ".join(msgs[:5])

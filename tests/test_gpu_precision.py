@@ -117,3 +117,53 @@ def test_prediction_error_against_fp64_oracle(storage, record_property):
     record_property("aae_diff_mean", float(d.mean()))
     assert abs(d.mean()) <= 3 * se + 0.005 * abs(a_ref)
     assert np.mean(diffs) < 0.05
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("group,R", [(2, 2), (8, 11)])
+@pytest.mark.parametrize("colour", [0, 1])
+def test_halfstep_lockstep_precision_form(storage, group, R, colour):
+    """One half-step of the 16-bit forms against the oracle in the same
+    precision form (proposal = the FP32 product 2pi u0 rounded to the stored
+    type before its energy is taken; reflected angle rounded), element by
+    element from the same random states and Philox draws."""
+    from parity import checkerboard, compare_site_updates
+    H, W, lb = 45, 38, 8
+    st_code = STORE[storage]
+    z, m = synth.small_problem(H, W, 0.55, seed=7 + colour)
+    gf = make(z, m, lb, seed=0x1234567, storage=st_code, group=group)
+    o = oracle.Oracle(H, W, lb, seed=0x1234567, storage=st_code)
+    rng = np.random.default_rng(17)
+    T = rng.uniform(0.02, 1.2, gf.nblk).astype(np.float32)
+    gf.set_temperatures(T)
+    gf.sim_begin(R)
+    g = m != 0
+    pre = []
+    for r in range(R):
+        s = gf.get_state(r)
+        s[g] = rng.uniform(0, TWO_PI, int(g.sum())).astype(np.float32)
+        gf.set_state(r, s)
+        back = gf.get_state(r)            # as stored: rounded to the type
+        assert all(oracle.round_store(v, st_code) == v for v in back[g].astype(np.float64))
+        pre.append(back)
+    running = (rng.uniform(size=(R, gf.nblk)) < 0.75).astype(np.uint8)
+    gf.set_running(running)
+    t, tag = 9, 2
+    gf.halfstep(colour, t, tag)
+    blk = o.block_index()
+    cb = checkerboard(H, W)
+    total = flips = 0
+    for r in range(R):
+        post = gf.get_state(r)
+        ph = pre[r].astype(np.float64)
+        diag = o.halfstep(ph, m, colour, T.astype(np.float64), running[r], t=t, tag=tag, r=r,
+                          diag=True).reshape(H, W)
+        may = g & (cb == colour) & (running[r][blk] == 1)
+        n, f, bad, msg = compare_site_updates(post, ph, pre[r], diag, may, storage=st_code)
+        assert bad == 0, f"r={r}: {msg}"
+        total += n
+        flips += f
+    assert total > 100 * R
+    assert flips <= max(3, total // 500)
+    gf.sim_end()
+    gf.close()
