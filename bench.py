@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--calibration", default="bisection", choices=["bisection", "newton"],
                     help="per-block temperature fit: bisection (the plain form) or safeguarded "
                          "Newton steps from the fluctuation identity")
+    ap.add_argument("--pipeline", type=int, default=3,
+                    help="also time the fields with this many in flight (one CUDA stream and "
+                         "host thread each; 0 or 1: skip), reported as 'pipelined'")
     ap.add_argument("--shard", default="fields", choices=["fields", "realizations"],
                     help="fields: every rank its own field (weak scaling, no collective); "
                          "realizations: ranks share one field's realizations (strong scaling, "
@@ -355,6 +358,68 @@ def run_ours(args, world, rank, local):
                "d2h_bytes_per_step": int(out_pin.numel() * 4),
                "gap_filled_mpix_s": fields * P * args.steps / dt / 1e6}
 
+    # Fields in flight: the same per-field work (calibrate, R realizations,
+    # predict, each field its own context) with `pipeline` fields at a time,
+    # one CUDA stream and host thread each, so that one field's latency-bound
+    # phases (calibration, the stop tail) overlap another's. Device time over
+    # all K fields, between events that every stream waits on / joins.
+    pipelined = None
+    if args.pipeline > 1 and shard == "fields":
+        import threading
+        npipe = args.pipeline
+        pstreams = [torch.cuda.Stream(dev) for _ in range(npipe)]
+        pouts = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in range(npipe)]
+        pups = [0] * npipe
+
+        def pworker(w, ks):
+            for _ in ks:
+                o = options(0)
+                o.cuda_stream = pstreams[w].cuda_stream
+                ctx = mpr.mpr_create(H, W, wl.block, mask_d, values_d, o)
+                try:
+                    mpr.mpr_calibrate(ctx, None)
+                    mpr.mpr_simulate(ctx, R)
+                    mpr.mpr_predict(ctx, pouts[w])
+                    inf = mpr.mpr_get_info(ctx)
+                    pups[w] += inf.gap_updates + inf.cal_gap_updates
+                finally:
+                    mpr.mpr_destroy(ctx)
+
+        def prun(k_total):
+            for w in range(npipe):
+                pups[w] = 0
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for ps in pstreams:
+                ps.wait_event(e0)
+            th = [threading.Thread(target=pworker, args=(w, range(w, k_total, npipe)))
+                  for w in range(npipe)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            for ps in pstreams:
+                ev = torch.cuda.Event()
+                ev.record(ps)
+                stream.wait_event(ev)
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1), sum(pups)
+
+        prun(npipe)                                   # warm-up: one field per stream
+        barrier()
+        p_ms, p_ups = prun(args.steps)
+        p_ms = replicas.max_over_ranks(p_ms, dev)
+        p_ups = replicas.sum_over_ranks(p_ups, dev)
+        pipelined = {"fields_in_flight": npipe, "value": p_ups / (p_ms / 1e3),
+                     "unit": "updates/s", "ms_per_field": p_ms / args.steps,
+                     "gap_filled_mpix_s": world * P * args.steps / (p_ms / 1e3) / 1e6,
+                     "fields": args.steps,
+                     "form": "each field its own context, calibrate + simulate + predict; "
+                             f"{npipe} fields at a time on {npipe} CUDA streams"}
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -414,6 +479,7 @@ def run_ours(args, world, rank, local):
         "roofline": roofline,
         "clocks": clk,
         "e2e": e2e,
+        "pipelined": pipelined,
     }
     if world == 1 and not args.no_cpu:
         ctx = mpr.mpr_create(H, W, wl.block, mask_d, values_d, options(0))
