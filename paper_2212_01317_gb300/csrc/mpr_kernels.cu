@@ -378,6 +378,10 @@ __global__ void __launch_bounds__(kFlatThreads) k_sweep_flat(SweepArgs a, int64_
         }
         return;
     }
+    // The sweep index comes from the Control only when the launch does not
+    // fix it, and the Control may be written by the previous kernel: wait for
+    // it first then (the prologue overlap is for launches with a fixed index).
+    if (a.t_fixed <= 0) grid_dep_wait();
     const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
     sweep_flat<G>(a, n_list, t | (a.ctl->tag << 16));
 }
