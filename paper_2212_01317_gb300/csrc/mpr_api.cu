@@ -348,13 +348,17 @@ int sweep_grid(mpr_ctx* ctx, int form) {
 }
 
 // Grid of the stop kernels: a thread per (item, lane) or per item, at most
-// two CTAs per SM (the kernels loop; the closing kernel's CTAs each take one
-// ticket from a single counter, so fewer CTAs wait less on it).
-int stop_grid(mpr_ctx* ctx, int64_t per_item) {
+// `per_sm` CTAs per SM (the kernels loop). The closing kernel's CTAs each take
+// one ticket from a single counter, so it runs on fewer CTAs (two per SM);
+// the targeted part has no such counter.
+constexpr int kTargetedCtasPerSm = 8;
+constexpr int kClosingCtasPerSm = 2;
+
+int stop_grid(mpr_ctx* ctx, int64_t per_item, int per_sm) {
     const int64_t items = std::min<int64_t>((int64_t)ctx->g.nblk * ctx->groups,
                                             (int64_t)std::min<unsigned long long>(ctx->bound, 1ull << 40));
     const int64_t n = std::max<int64_t>(1, items * per_item);
-    return (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->n_sm * 2);
+    return (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->n_sm * per_sm);
 }
 
 cudaEvent_t get_event(mpr_ctx* ctx) {
@@ -465,13 +469,13 @@ mpr_status sweep_once(mpr_ctx* ctx) {
         cudaEventRecord(e1, ctx->s);
         ctx->ev_sim.emplace_back(e0, e1);
     }
-    launch_stop_targeted(ctx->G, ctx->groups, ctx->Rp, ctx->d_of_block, stop_grid(ctx, ctx->G),
+    launch_stop_targeted(ctx->G, ctx->groups, ctx->Rp, ctx->d_of_block, stop_grid(ctx, ctx->G, kTargetedCtasPerSm),
                          ctx->ctl, ctx->work,
                          ctx->work_stride, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
                          ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
     launch_stop_rest(g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
-                     stop_grid(ctx, 1), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp,
+                     stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp,
                      ctx->running, ctx->stop, ctx->tcount, ctx->sim_cond, ctx->s);
     CKL();
     ctx->t += 1;
@@ -1378,7 +1382,7 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
                      ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
     launch_stop_rest(ctx->g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
-                     stop_grid(ctx, 1), ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp,
+                     stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp,
                      ctx->running, ctx->stop, ctx->tcount, 0, ctx->s);
     CKL();
     ctx->energy_dirty = false;
