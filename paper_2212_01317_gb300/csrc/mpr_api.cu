@@ -279,7 +279,8 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group, int storag
         TRY(dalloc(ctx, &ctx->tcount, (size_t)Rp * ctx->n_slices));
         ctx->lane_cap = (size_t)Rp * ctx->n_slices;
     }
-    const size_t work_need = (size_t)g.nblk * groups;
+    // Worklist units: one realization pair of one block (Rp / 2 per block).
+    const size_t work_need = (size_t)g.nblk * (Rp / 2);
     if (work_need > ctx->work_cap) {
         dfree(ctx, ctx->work);
         ctx->work = nullptr;
@@ -343,7 +344,8 @@ int sweep_grid(mpr_ctx* ctx, int form) {
     int& full = ctx->grid_cache[ctx->G == 2 ? 0 : 1][ctx->storage][form];
     if (full == 0) full = ctx->n_sm * sweep_blocks_per_sm(ctx->G, ctx->storage, form);
     const unsigned long long ipc = (unsigned long long)sweep_items_per_cta(ctx->G, form);
-    const unsigned long long need = (ctx->bound + ipc - 1) / ipc;
+    // (bound is ~0 while unknown: round up without overflowing)
+    const unsigned long long need = ctx->bound / ipc + (ctx->bound % ipc != 0 ? 1 : 0);
     return (int)std::max<unsigned long long>(1, std::min<unsigned long long>(full, need));
 }
 
@@ -355,7 +357,7 @@ constexpr int kTargetedCtasPerSm = 8;
 constexpr int kClosingCtasPerSm = 2;
 
 int stop_grid(mpr_ctx* ctx, int64_t per_item, int per_sm) {
-    const int64_t items = std::min<int64_t>((int64_t)ctx->g.nblk * ctx->groups,
+    const int64_t items = std::min<int64_t>((int64_t)ctx->g.nblk * (ctx->Rp / 2),
                                             (int64_t)std::min<unsigned long long>(ctx->bound, 1ull << 40));
     const int64_t n = std::max<int64_t>(1, items * per_item);
     return (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->n_sm * per_sm);
@@ -417,7 +419,8 @@ mpr_status init_batch_state(mpr_ctx* ctx) {
 }
 
 // After the running flags were overwritten: per-realization counts of running
-// targeted blocks and the worklist of items with a running lane.
+// targeted blocks and the worklist of units (lane groups of G lanes; the
+// realizations' worklist uses pairs) with a running lane.
 __global__ void k_rebuild(int nblk, int groups, int G, int Rp, const int32_t* of_block,
                           const int32_t* Nsp, const uint8_t* running, int32_t* tcount, Control* ctl,
                           uint32_t* work_all, uint32_t work_stride) {
@@ -469,12 +472,14 @@ mpr_status sweep_once(mpr_ctx* ctx) {
         cudaEventRecord(e1, ctx->s);
         ctx->ev_sim.emplace_back(e0, e1);
     }
-    launch_stop_targeted(ctx->G, ctx->groups, ctx->Rp, ctx->d_of_block, stop_grid(ctx, ctx->G, kTargetedCtasPerSm),
+    // The stop kernels see the worklist's units as lane groups of two.
+    launch_stop_targeted(2, ctx->Rp / 2, ctx->Rp, ctx->d_of_block,
+                         stop_grid(ctx, 2, kTargetedCtasPerSm),
                          ctx->ctl, ctx->work,
                          ctx->work_stride, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
                          ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
-    launch_stop_rest(g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
+    launch_stop_rest(g.nblk, ctx->Rp / 2, 2, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
                      stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp,
                      ctx->running, ctx->stop, ctx->tcount, ctx->sim_cond, ctx->s);
     CKL();
@@ -1381,7 +1386,7 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
                      ctx->ecur,
                      ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
-    launch_stop_rest(ctx->g.nblk, ctx->groups, ctx->G, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
+    launch_stop_rest(ctx->g.nblk, ctx->Rp / 2, 2, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
                      stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp,
                      ctx->running, ctx->stop, ctx->tcount, 0, ctx->s);
     CKL();
@@ -1516,8 +1521,8 @@ mpr_status simulate_tail(mpr_ctx* ctx, bool* ran) {
         a.split[c] = ctx->split[c];
     }
     StopArgs& st = a.st;
-    st.G = ctx->G;
-    st.groups = ctx->groups;
+    st.G = 2;                       // the worklist's units: realization pairs
+    st.groups = ctx->Rp / 2;
     st.Rp = ctx->Rp;
     st.nblk = ctx->g.nblk;
     st.n_max = o.n_max;
@@ -1740,9 +1745,9 @@ mpr_status mpr_set_running(mpr_ctx* ctx, const uint8_t* running) {
     CK(cudaStreamSynchronize(ctx->s));
     const uint32_t par = ctx->h_ctl->t & 1u;
     CK(cudaMemsetAsync(&ctx->ctl->n_work[par], 0, sizeof(uint32_t), ctx->s));
-    const int64_t items = (int64_t)nb * ctx->groups;
+    const int64_t items = (int64_t)nb * (ctx->Rp / 2);
     k_rebuild<<<(int)std::min<int64_t>((items + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
-        nb, ctx->groups, ctx->G, ctx->Rp, ctx->d_of_block, ctx->Nsp, ctx->running, ctx->tcount,
+        nb, ctx->Rp / 2, 2, ctx->Rp, ctx->d_of_block, ctx->Nsp, ctx->running, ctx->tcount,
         ctx->ctl, ctx->work, ctx->work_stride);
     ctx->bound = ~0ull;
     CKL();

@@ -329,25 +329,31 @@ __global__ void k_fill_samples(Geom g, const uint8_t* __restrict__ mask,
 }
 
 // ----------------------------------------------------------------- sweep --
-// One half-step of the batch over the worklist of running items (or every
-// item). WPI warps per item, THREADS / (32 WPI) items per CTA:
-//   G = 8 (four realization pairs): WPI = 4, a CTA of 128 per item; the tail
-//     form WPI = 16 (512 threads) gives every pair four warps, so the few
-//     items left at the end of a batch finish in one pass over their entries.
-//   G = 2 (one pair): WPI = 1, four items per CTA; tail form WPI = 4.
-template <int G, typename S, int WPI, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_sweep(SweepArgs a) {
+// One half-step of the batch over the worklist of running units (or every
+// unit). A unit is one realization pair of one block: u = b * npairs + p
+// with npairs = Rp / 2 and pair p = group * (G/2) + q, so a pair whose two
+// realizations have stopped costs nothing. WPU warps take a unit (1: one
+// warp per pair; 2, 4: the pair's entries split between them, for the few
+// units left at the end of a batch), 128 / (32 WPU) units per CTA.
+template <int G, typename S, int WPU>
+__global__ void __launch_bounds__(128, 8) k_sweep(SweepArgs a) {
     grid_dep_launch();
     grid_dep_wait();
+    constexpr int NP = G / 2;
     const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
     const uint32_t ctr1 = t | (a.ctl->tag << 16);
     const uint32_t* work = a.work ? a.work + (size_t)(t & 1u) * a.work_stride : nullptr;
-    const int n_items = work ? (int)a.ctl->n_work[t & 1u] : a.g.nblk * a.groups;
-    constexpr int IPC = THREADS / 32 / WPI;
+    const int npairs = a.groups * NP;
+    const int n_units = work ? (int)a.ctl->n_work[t & 1u] : a.g.nblk * npairs;
+    constexpr int UPC = 4 / WPU;
     const int warp = threadIdx.x >> 5;
-    const int slot = warp / WPI, wi = warp % WPI;
-    for (int it = blockIdx.x * IPC + slot; it < n_items; it += gridDim.x * IPC)
-        sweep_item<G, S>(a, work ? (int)work[it] : it, wi, WPI, ctr1);
+    const int slot = warp / WPU, cw = warp % WPU;
+    for (int it = blockIdx.x * UPC + slot; it < n_units; it += gridDim.x * UPC) {
+        const int u = work ? (int)work[it] : it;
+        const int b = u / npairs, p = u - b * npairs;
+        const int grp = p / NP, q = p - grp * NP;
+        sweep_item<G, S>(a, b * a.groups + grp, q + NP * cw, NP * WPU, ctr1);
+    }
 }
 
 // The last f.ctas CTAs (of blockIdx.y = 0) fold the previous sweep's block
@@ -1070,40 +1076,22 @@ void launch_fill_samples(const Geom& g, const uint8_t* mask, const float* dang, 
 }
 
 namespace {
-// The three forms of the realizations' half-step, by warps per item (WPI)
-// and CTA size (all at 1024 threads per SM):
-//   form 0: one warp per realization pair (G = 8: WPI 4, one item per
-//           128-thread CTA; G = 2: WPI 1, four items per CTA);
-//   form 1: two warps per pair, splitting a block's entries (WPI 8, 256
-//           threads; G = 2: WPI 2, two items per CTA);
-//   form 2: four warps per pair (WPI 16, 512 threads; G = 2: WPI 4).
-// Fewer running pairs, more warps per pair: the few items left finish in
-// fewer passes over their entries.
+// The three forms of the realizations' half-step by warps per unit (one
+// realization pair of one block): form 0 one warp, form 1 two, form 2 four
+// (splitting the block's entries between them), in 128-thread CTAs.
 template <int G, typename S>
 void sweep_dispatch(const SweepArgs& a, int form, int grid, cudaStream_t s) {
-    if constexpr (G == 2) {
-        if (form == 2) launch_pdl(k_sweep<2, S, 4, 128>, grid, 128, s, a);
-        else if (form == 1) launch_pdl(k_sweep<2, S, 2, 128>, grid, 128, s, a);
-        else launch_pdl(k_sweep<2, S, 1, 128>, grid, 128, s, a);
-    } else {
-        if (form == 2) launch_pdl(k_sweep<8, S, 16, 512>, grid, 512, s, a);
-        else if (form == 1) launch_pdl(k_sweep<8, S, 8, 256>, grid, 256, s, a);
-        else launch_pdl(k_sweep<8, S, 4, 128>, grid, 128, s, a);
-    }
+    if (form == 2) launch_pdl(k_sweep<G, S, 4>, grid, 128, s, a);
+    else if (form == 1) launch_pdl(k_sweep<G, S, 2>, grid, 128, s, a);
+    else launch_pdl(k_sweep<G, S, 1>, grid, 128, s, a);
 }
 
 template <int G, typename S>
 int sweep_occupancy(int form) {
     int n = 0;
-    if constexpr (G == 2) {
-        if (form == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 4, 128>, 128, 0);
-        else if (form == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 2, 128>, 128, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, S, 1, 128>, 128, 0);
-    } else {
-        if (form == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 16, 512>, 512, 0);
-        else if (form == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 8, 256>, 256, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<8, S, 4, 128>, 128, 0);
-    }
+    if (form == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<G, S, 4>, 128, 0);
+    else if (form == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<G, S, 2>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<G, S, 1>, 128, 0);
     return n > 0 ? n : 1;
 }
 }  // namespace
@@ -1125,7 +1113,10 @@ int sweep_blocks_per_sm(int G, int storage, int form) {
     return n;
 }
 
-int sweep_items_per_cta(int G, int form) { return G == 2 ? 4 >> form : 1; }
+int sweep_items_per_cta(int G, int form) {
+    (void)G;
+    return 4 >> form;
+}
 
 void launch_energy(const SweepArgs& a, int G, int storage, int n_sm, cudaStream_t s) {
     with_storage(storage, [&](auto tag) {

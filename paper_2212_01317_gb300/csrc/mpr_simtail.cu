@@ -53,12 +53,13 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_sim_tail(SimTailArgs a) {
         const uint32_t ctr1 = t | (s_tag << 16);
         const uint32_t par = t & 1u, nxt = par ^ 1u;
         const uint32_t* work = a.work_all + (size_t)par * a.sw.work_stride;
-        // One warp per realization pair while the items fill the grid; two or
-        // four (splitting a block's entries) when they are few.
+        // The worklist holds units (one realization pair of one block): one
+        // warp per unit while they fill the grid; two or four (splitting a
+        // block's entries) when they are few.
         int k = 1;
-        while (k < 4 && (int64_t)n_items * NP * 2 * k <= nw) k *= 2;
-        const int wpi = NP * k;
-        const int ngrp = nw / wpi, gi = gw / wpi, wi = gw % wpi;
+        while (k < 4 && (int64_t)n_items * 2 * k <= nw) k *= 2;
+        const int npairs = a.sw.groups * NP;
+        const int ngrp = nw / k, gi = gw / k, cw = gw % k;
         for (int c = 0; c < 2; ++c) {
             SweepArgs s = a.sw;
             s.colour = c;
@@ -66,11 +67,15 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_sim_tail(SimTailArgs a) {
             s.start = a.start[c];
             s.split = a.split[c];
             if (gi < ngrp)
-                for (uint32_t it = (uint32_t)gi; it < n_items; it += (uint32_t)ngrp)
-                    sweep_item<G, S>(s, (int)work[it], wi, wpi, ctr1);
+                for (uint32_t it = (uint32_t)gi; it < n_items; it += (uint32_t)ngrp) {
+                    const int u = (int)work[it];
+                    const int b = u / npairs, p = u - b * npairs;
+                    const int grp = p / NP, q = p - grp * NP;
+                    sweep_item<G, S>(s, b * s.groups + grp, q + NP * cw, NP * k, ctr1);
+                }
             if (!grid_sync(a.bar, gen, lim)) return;
         }
-        stop_targeted_range(a.st, t, work, (int64_t)n_items * G, tid, nthr);
+        stop_targeted_range(a.st, t, work, (int64_t)n_items * a.st.G, tid, nthr);
         if (!grid_sync(a.bar, gen, lim)) return;
         unsigned cnt = stop_rest_range(a.st, t, work, (int64_t)n_items,
                                        a.work_all + (size_t)nxt * a.sw.work_stride,
