@@ -97,6 +97,7 @@ struct mpr_ctx {
     size_t ang_cap = 0;          // bytes
     float* eacc = nullptr;
     double* ecur = nullptr;      // [nblk][Rp] current E_b of every (block, realization)
+    double* ecur0 = nullptr;     // [nblk][Rp] calibration: E_b of the start state
     uint8_t* running = nullptr;
     int32_t* stop = nullptr;
     int8_t* sigma = nullptr;
@@ -259,13 +260,14 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group, int storag
     const size_t blk_need = (size_t)g.nblk * Rp;
     if (blk_need > ctx->blk_cap) {
         for (void* p : {(void*)ctx->eacc, (void*)ctx->running, (void*)ctx->stop, (void*)ctx->sigma,
-                        (void*)ctx->e_last, (void*)ctx->ecur})
+                        (void*)ctx->e_last, (void*)ctx->ecur, (void*)ctx->ecur0})
             dfree(ctx, p);
         ctx->eacc = nullptr; ctx->running = nullptr; ctx->stop = nullptr; ctx->sigma = nullptr;
-        ctx->e_last = nullptr; ctx->ecur = nullptr;
+        ctx->e_last = nullptr; ctx->ecur = nullptr; ctx->ecur0 = nullptr;
         ctx->blk_cap = 0;
         TRY(dalloc(ctx, &ctx->eacc, 2 * blk_need));   // two per-sweep buffers
         TRY(dalloc(ctx, &ctx->ecur, blk_need));
+        TRY(dalloc(ctx, &ctx->ecur0, blk_need));
         TRY(dalloc(ctx, &ctx->e_last, blk_need));
         TRY(dalloc(ctx, &ctx->running, blk_need));
         TRY(dalloc(ctx, &ctx->stop, blk_need));
@@ -595,10 +597,15 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
     CKL();
     TRY(init_batch_state(ctx));
-    TRY(energy_pass(ctx));
+    // Every iteration starts from the same state, so E_b of the start
+    // (computed once, before the first iteration) is copied, and no change is
+    // pending.
+    const size_t blk = (size_t)g.nblk * ctx->Rp;
+    CK(cudaMemcpyAsync(ctx->ecur, ctx->ecur0, blk * sizeof(double), cudaMemcpyDeviceToDevice,
+                       ctx->s));
+    CK(cudaMemsetAsync(ctx->eacc, 0, 2 * blk * sizeof(float), ctx->s));
     // Sweep sw's changes go to eacc buffer sw & 1; the colour-0 launch of
     // sweep sw + 1 folds them (extra CTAs), the last sweep's fold runs alone.
-    const size_t blk = (size_t)g.nblk * ctx->Rp;
     const int n_sw = o.n_eq + o.n_meas;
     for (int sw = 1; sw <= n_sw; ++sw) {
         for (int c = 0; c < 2; ++c) {
@@ -1335,6 +1342,13 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
         TRY(calibration_persistent(ctx, inv_count, &fallback));
         if (fallback && o.cal_mode == 2)
             return fail(ctx, MPR_ECUDA, "calibration: cooperative launch refused");
+    }
+    if (fallback && o.n_bisect > 0) {
+        // E_b of the start state of every iteration.
+        TRY(init_batch_state(ctx));
+        TRY(energy_pass(ctx));
+        CK(cudaMemcpyAsync(ctx->ecur0, ctx->ecur, (size_t)g.nblk * ctx->Rp * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->s));
     }
     if (fallback) {
         if (o.n_bisect > 0 && o.cal_mode == 3) {

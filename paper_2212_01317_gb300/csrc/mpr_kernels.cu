@@ -547,8 +547,13 @@ __global__ void k_cal_mid(int nblk, const int32_t* __restrict__ Nsp, const float
 __global__ void k_cal_fill(Slices sl, int nbx, const int32_t* __restrict__ Nsp,
                            float* __restrict__ T, float* __restrict__ beta) {
     const int4 bk = sl.blk[blockIdx.x];
-    const float med = median_targeted(T, Nsp, bk, nbx);
     const int nb = bk.z * bk.w;
+    // The median only serves blocks that do not calibrate: skip the select
+    // when the slice has none.
+    int fill = 0;
+    for (int j = threadIdx.x; j < nb && !fill; j += blockDim.x)
+        fill = Nsp[(bk.x + j / bk.w) * nbx + bk.y + j % bk.w] <= 0;
+    const float med = __syncthreads_or(fill) ? median_targeted(T, Nsp, bk, nbx) : 0.0f;
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         const int b = (bk.x + j / bk.w) * nbx + bk.y + j % bk.w;
         float tb = T[b];
