@@ -1563,7 +1563,11 @@ mpr_status simulate_tail(mpr_ctx* ctx, bool* ran) {
         e1 = get_event(ctx);
         if (e0) cudaEventRecord(e0, ctx->s);
     }
-    const cudaError_t le = launch_sim_tail(a, ctx->G, ctx->storage, ctx->n_sm * per_sm, ctx->s);
+    // A grid sized for the pairs still running (16 warps per CTA, about two
+    // units per warp at the switch): few CTAs make the grid barriers cheap.
+    const unsigned long long want = std::max<unsigned long long>(8, ctx->bound / 32);
+    const int grid = (int)std::min<unsigned long long>((unsigned long long)ctx->n_sm * per_sm, want);
+    const cudaError_t le = launch_sim_tail(a, ctx->G, ctx->storage, grid, ctx->s);
     if (le != cudaSuccess) {
         cudaGetLastError();
         if (e0) ctx->ev_pool.push_back(e0);

@@ -65,18 +65,38 @@ __global__ void k_minmax_field(const float* __restrict__ values, const uint8_t* 
 
 // z_min / z_max over the samples of every slice (Sec. 2.1: only the samples
 // are known): mm[2 s], mm[2 s + 1] as order-preserving integers.
+// One warp min / max per 32 sites when their samples share a slice (the
+// usual case), else an atomic per sample.
 __global__ void k_minmax(Geom g, const int32_t* __restrict__ of_block,
                          const float* __restrict__ values, const uint8_t* __restrict__ mask,
                          uint32_t* __restrict__ mm) {
     const int64_t n = (int64_t)g.H * g.W;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+    const int64_t n_warps = (n + 31) / 32 * 32;   // every lane of a warp runs every iteration
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_warps;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (mask[i]) continue;
-        const int y = (int)(i / g.W), x = (int)(i % g.W);
-        const int s = of_block[(y / g.lb) * g.nbx + x / g.lb];
-        const uint32_t o = f2ord(values[i]);
-        atomicMin(&mm[2 * s], o);
-        atomicMax(&mm[2 * s + 1], o);
+        int s = -1;
+        uint32_t lo = 0xffffffffu, hi = 0u;
+        if (i < n && !mask[i]) {
+            const int y = (int)(i / g.W), x = (int)(i % g.W);
+            s = of_block[(y / g.lb) * g.nbx + x / g.lb];
+            lo = hi = f2ord(values[i]);
+        }
+        int smax = s;
+        for (int d = 16; d > 0; d >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, d));
+        if (__all_sync(0xffffffffu, s < 0 || s == smax)) {
+            if (smax < 0) continue;
+            for (int d = 16; d > 0; d >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&mm[2 * smax], lo);
+                atomicMax(&mm[2 * smax + 1], hi);
+            }
+        } else if (s >= 0) {
+            atomicMin(&mm[2 * s], lo);
+            atomicMax(&mm[2 * s + 1], hi);
+        }
     }
 }
 
