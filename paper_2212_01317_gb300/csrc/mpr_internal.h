@@ -109,7 +109,7 @@ struct Control {
 };
 
 // One half-step over the gap sites of one colour, for every running
-// (block, lane group) item.
+// (block, realization pair) unit of the worklist.
 struct SweepArgs {
     Geom g;
     Model m;
@@ -127,7 +127,7 @@ struct SweepArgs {
     const uint8_t* running;   // [nblk][Rp] or nullptr (= every lane r < R runs)
     float* eacc;              // [nblk][Rp] energy change of this sweep (moves)
     double* ecur;             // [nblk][Rp] E_b (the energy pass adds into it)
-    const uint32_t* work;     // two worklists of items b * groups + group, or nullptr = all items
+    const uint32_t* work;     // two worklists of units b * (Rp / 2) + pair, or nullptr = all units
     uint32_t work_stride;     // elements per worklist
     const Control* ctl;
     int R, Rp, groups;        // realizations in the batch, padded lanes, lane groups

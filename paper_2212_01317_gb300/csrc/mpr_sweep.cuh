@@ -3,7 +3,8 @@
 // calibration kernel (mpr_persist.cu).
 //
 // A (block, lane group) item is one block of the grid for the G realizations
-// of one lane group. The state interleaves G realizations per site; each
+// of one lane group; the realizations' worklist hands out its realization
+// pairs one by one (units), the calibration's flat kernel every entry. The state interleaves G realizations per site; each
 // lane updates its site in both realizations of one realization pair, from
 // one Philox block: words 0, 1 for the even realization, 2, 3 for the odd.
 //
