@@ -177,18 +177,26 @@ def run_reference(args, world, rank):
                             bw.realizations)
     else:
         wl = synth.workload(args.workload)
-    H, W = wl.shape
     lb = wl.block
     cores = len(os.sched_getaffinity(0))
-    o = oracle.Oracle(H, W, lb, seed=2024, threads=cores)
-    phi, zmin, zmax, _ = o.transform(wl.truth, wl.mask)
+    if wl.truth.ndim == 3:                         # the 3-D extension
+        D, H, W = wl.shape
+        o = oracle.Oracle3(D, H, W, lb, seed=2024)
+        o.m.threads = cores
+        phi, _, _, _ = oracle.Oracle.transform(wl.truth.reshape(D * H, W),
+                                               wl.mask.reshape(D * H, W))
+        phi = phi.reshape(D, H, W)
+    else:
+        H, W = wl.shape
+        o = oracle.Oracle(H, W, lb, seed=2024, threads=cores)
+        phi, _, _, _ = o.transform(wl.truth, wl.mask)
     st = o.block_stats(phi, wl.mask)
     phi0 = o.init_block_mean(phi, wl.mask, st)
     T = np.full(o.nblk, 0.1)
 
     def step(r):
         t0 = time.perf_counter()
-        _, stop, _, _ = o.simulate_one(phi0, wl.mask, T, st, 200, r)
+        stop = o.simulate_one(phi0, wl.mask, T, st, 200, r)[1]
         dt = time.perf_counter() - t0
         return int(np.sum(stop.astype(np.int64) * st.n_gap)), dt
 
@@ -206,7 +214,7 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "H": H, "W": W, "block": lb,
+            "config": {"workload": wl.name, "shape": list(wl.shape), "block": lb,
                        "realizations": wl.realizations},
             "cpu_baseline": {"value": val, "unit": "updates/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
@@ -635,6 +643,120 @@ def run_ours_batch(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_ours_3d(args, world, rank, local):
+    """The 3-D extension (mpr3_*): calibrate, simulate, predict one D x H x W
+    field per step, inputs resident on the device; the roofline of its
+    half-step kernel (k3_sweep) from CUDA events around each sweep."""
+    import ctypes as C
+    import torch
+    from paper_2212_01317_gb300 import mpr, replicas, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lib = mpr.load()
+    wl = synth.workload(args.workload, seed=rank)
+    D, H, W = wl.shape
+    n = D * H * W
+    P = wl.n_gap
+    p = P / n
+    R = wl.realizations
+    stream = torch.cuda.current_stream(dev)
+    vals_d = torch.from_numpy(np.where(wl.mask != 0, np.nan, wl.truth).astype(np.float32)).to(dev)
+    mask_d = torch.from_numpy(wl.mask).to(dev)
+    out_d = torch.empty((D, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def check(ctx, st):
+        if st != mpr.MPR_OK:
+            raise mpr.MprError(st, lib.mpr3_last_error(ctx).decode() if ctx else "")
+
+    def step(profile=1):
+        o = mpr.mpr_default_options(seed=2024 + 7919 * rank, slice_id=rank, profile=profile,
+                                    n_bisect=cal_iters(args) if args.cal_points == 1 else 24,
+                                    cuda_stream=stream.cuda_stream)
+        ctx = C.c_void_p()
+        g = mpr.mpr_grid3(D, H, W, wl.block)
+        check(None, lib.mpr3_create(C.byref(g), mpr._ptr(mask_d), mpr._ptr(vals_d), C.byref(o),
+                                    C.byref(ctx)))
+        try:
+            check(ctx, lib.mpr3_calibrate(ctx, None))
+            check(ctx, lib.mpr3_simulate(ctx, R))
+            check(ctx, lib.mpr3_predict(ctx, mpr._ptr(out_d), None, None))
+            info = mpr.mpr3_info()
+            check(ctx, lib.mpr3_get_info(ctx, C.byref(info)))
+            prof = mpr.mpr_profile()
+            check(ctx, lib.mpr3_get_profile(ctx, C.byref(prof)))
+        finally:
+            lib.mpr3_destroy(ctx)
+        return info, prof
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, ups, sim_ups, launches, sim_ms, sim_launch, cal_ms = [], 0, 0, 0, 0.0, 0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info, prof = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ups += info.gap_updates + info.cal_gap_updates
+        sim_ups += info.gap_updates
+        launches += prof.kernel_launches
+        sim_ms += prof.sim_halfstep_ms
+        sim_launch += prof.sim_halfstep_launches
+        cal_ms += prof.cal_halfstep_ms
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = replicas.max_over_ranks(float(np.sum(step_ms)), dev)
+    ups_all = replicas.sum_over_ranks(ups, dev)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    bpu = bytes_per_gap_update(4.0, p)
+    achieved = sim_ups * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": ups_all / (total_ms / 1e3), "unit": "updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "D": D, "H": H, "W": W, "block": wl.block,
+                   "gap_fraction": p, "realizations": R, "storage": "f32",
+                   "calibration": "bisection x24",
+                   "l2": "inputs larger than L2; flushed between timed steps",
+                   "parallelism": f"replicas{world}"},
+        "gap_filled_mpix_s": world * P * args.steps / (total_ms / 1e3) / 1e6,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "k3_sweep (realizations)", "peak_kind": peak_kind,
+                     "bytes_per_gap_update": bpu,
+                     "avg_launch_us": 1e3 * sim_ms / max(sim_launch, 1),
+                     "sim_halfstep": {"ms": sim_ms / args.steps,
+                                      "launches": sim_launch // args.steps,
+                                      "updates_per_s": sim_ups / (sim_ms / 1e3) if sim_ms else None},
+                     "calibration_ms": cal_ms / args.steps},
+        "clocks": clk,
+        "e2e": None,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -644,6 +766,9 @@ def main():
     from paper_2212_01317_gb300 import synth
     if args.workload in synth.BATCH_WORKLOADS:
         run_ours_batch(args, world, rank, local)
+        return
+    if args.workload.startswith("cube"):
+        run_ours_3d(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

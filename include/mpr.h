@@ -429,6 +429,11 @@ mpr_status mpr3_create(const mpr_grid3* grid, const uint8_t* mask, const float* 
 void mpr3_destroy(mpr3_ctx* ctx);
 const char* mpr3_last_error(const mpr3_ctx* ctx);
 mpr_status mpr3_get_info(const mpr3_ctx* ctx, mpr3_info* info);
+/* Launch counts and, with mpr_options.profile = 1, the device time of the
+ * realizations' half-steps (CUDA events around each sweep's two half-step
+ * launches) and of the calibration's iterations (around all of them).
+ * Synchronises the stream. */
+mpr_status mpr3_get_profile(mpr3_ctx* ctx, mpr_profile* out);
 mpr_status mpr3_get_block_stats(mpr3_ctx* ctx, double* Es, int32_t* Nsp, int32_t* Nb,
                                 float* mean_angle, int32_t* n_gap);
 mpr_status mpr3_calibrate(mpr3_ctx* ctx, float* block_T_out);

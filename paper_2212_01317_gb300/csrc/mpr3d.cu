@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mpr.h"
@@ -487,6 +488,12 @@ struct mpr3_ctx {
     int64_t realizations = 0, gap_updates = 0, cal_updates = 0;
     int64_t r_next = 0;          // index of the next realization (batches start even)
     uint32_t pair_base = 0;
+    // profiling (opt.profile): event pairs around the realizations' sweeps
+    // (their two half-steps) and around the calibration's iterations
+    int64_t launches = 0, sim_hs = 0, cal_hs = 0;
+    double sim_ms = 0.0, cal_ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_sim, ev_cal;
+    unsigned long long* h_run = nullptr;   // pinned: running counts of two sweep chunks
 };
 
 namespace {
@@ -512,6 +519,7 @@ mpr_status fail3(mpr3_ctx* c, mpr_status st, const char* fmt, ...) {
     } while (0)
 #define CKL3()                                                                                \
     do {                                                                                      \
+        ++ctx->launches;                                                                      \
         cudaError_t e_ = cudaPeekAtLastError();                                               \
         if (e_ != cudaSuccess)                                                                \
             return fail3(ctx, MPR_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
@@ -636,9 +644,44 @@ mpr_status halfstep3(mpr3_ctx* ctx, int colour, uint32_t ctr1, bool simulate) {
     return MPR_OK;
 }
 
+// After a stream synchronisation: the recorded event pairs into the totals.
+void collect3(mpr3_ctx* ctx) {
+    for (int which = 0; which < 2; ++which) {
+        auto& v = which ? ctx->ev_cal : ctx->ev_sim;
+        double& acc = which ? ctx->cal_ms : ctx->sim_ms;
+        for (auto& pr : v) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) acc += ms;
+            else cudaGetLastError();
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        v.clear();
+    }
+}
+
+// An event pair on the context's stream when profiling (nullptr otherwise).
+std::pair<cudaEvent_t, cudaEvent_t> begin_timing3(mpr3_ctx* ctx) {
+    std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+    if (!ctx->opt.profile) return e;
+    if (cudaEventCreate(&e.first) != cudaSuccess || cudaEventCreate(&e.second) != cudaSuccess) {
+        cudaGetLastError();
+        if (e.first) cudaEventDestroy(e.first);
+        return {nullptr, nullptr};
+    }
+    cudaEventRecord(e.first, ctx->s);
+    return e;
+}
+
 mpr_status sweep3(mpr3_ctx* ctx) {
     ctx->t += 1;
+    const auto ev = begin_timing3(ctx);
     for (int c = 0; c < 2; ++c) TRY3(halfstep3(ctx, c, (uint32_t)ctx->t, true));
+    ctx->sim_hs += 2;
+    if (ev.first) {
+        cudaEventRecord(ev.second, ctx->s);
+        ctx->ev_sim.push_back(ev);
+    }
     const int64_t items = (int64_t)ctx->g.nblk * ctx->np;
     const int grid = (int)std::min<int64_t>((items * 2 + 255) / 256, 152 * 16);
     launch_stop_targeted(2, ctx->np, ctx->Rp, ctx->zero_slices, grid, ctx->ctl, ctx->work,
@@ -659,9 +702,24 @@ extern "C" {
 void mpr3_destroy(mpr3_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->s);
+    collect3(ctx);
     for (void* p : ctx->owned) pool_free(p, ctx->s);
     cudaStreamSynchronize(ctx->s);
+    pinned_release(ctx->h_run);
     delete ctx;
+}
+
+mpr_status mpr3_get_profile(mpr3_ctx* ctx, mpr_profile* p) {
+    if (!ctx || !p) return MPR_EINVAL;
+    if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return fail3(ctx, MPR_ECUDA, "sync failed");
+    collect3(ctx);
+    std::memset(p, 0, sizeof(*p));
+    p->kernel_launches = ctx->launches;
+    p->sim_halfstep_launches = ctx->sim_hs;
+    p->cal_halfstep_launches = ctx->cal_hs;
+    p->sim_halfstep_ms = ctx->sim_ms;
+    p->cal_halfstep_ms = ctx->cal_ms;
+    return MPR_OK;
 }
 
 const char* mpr3_last_error(const mpr3_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
@@ -854,8 +912,10 @@ mpr_status mpr3_calibrate(mpr3_ctx* ctx, float* T_out) {
         launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->ctl, ctx->s);
         CKL3();
         const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);
+        const auto ev = begin_timing3(ctx);
         for (int k = 0; k < o.n_bisect; ++k) {
             launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+            ++ctx->launches;
             launch_cal_fill(sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
             CKL3();
             TRY3(init3(ctx));
@@ -871,7 +931,13 @@ mpr_status mpr3_calibrate(mpr3_ctx* ctx, float* T_out) {
                               ctx->ebar, ctx->ctl, o.n_bisect, 0, ctx->s);
             CKL3();
         }
+        if (ev.first) {
+            cudaEventRecord(ev.second, ctx->s);
+            ctx->ev_cal.push_back(ev);
+        }
+        ctx->cal_hs += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * 2;
         launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
+        ++ctx->launches;
         launch_cal_fill(sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
         CKL3();
         ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains *
@@ -948,20 +1014,46 @@ mpr_status mpr3_sim_end(mpr3_ctx* ctx) {
     return MPR_OK;
 }
 
+// Sweeps are queued in chunks of four; after each chunk the running count is
+// copied to pinned memory, and the host checks the count of the chunk before
+// the one it just queued, so the GPU never waits for the host. Sweeps queued
+// after everything stopped find no running pair.
 mpr_status mpr3_simulate(mpr3_ctx* ctx, int32_t n) {
     if (!ctx) return MPR_EINVAL;
     mpr_status st = mpr3_sim_begin(ctx, n);
+    if (st != MPR_OK) return st;
+    if (!ctx->h_run) {
+        ctx->h_run = static_cast<unsigned long long*>(pinned_slot());
+        if (!ctx->h_run) return fail3(ctx, MPR_ENOMEM, "pinned memory");
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail3(ctx, MPR_ECUDA, "cudaEventCreate failed");
+    }
+    int c = 0;
     while (st == MPR_OK && ctx->t < ctx->opt.n_max) {
-        for (int i = 0; i < 8 && st == MPR_OK && ctx->t < ctx->opt.n_max; ++i) st = sweep3(ctx);
+        for (int i = 0; i < 4 && st == MPR_OK && ctx->t < ctx->opt.n_max; ++i) st = sweep3(ctx);
         if (st != MPR_OK) break;
-        Control h{};
-        if (cudaMemcpyAsync(&h, ctx->ctl, sizeof(h), cudaMemcpyDeviceToHost, ctx->s) ||
-            cudaStreamSynchronize(ctx->s)) {
+        if (cudaMemcpyAsync(ctx->h_run + (c & 1), &ctx->ctl->n_running, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, ctx->s) != cudaSuccess ||
+            cudaEventRecord(ev[c & 1], ctx->s) != cudaSuccess) {
             st = fail3(ctx, MPR_ECUDA, "reading the running count failed");
             break;
         }
-        if (h.n_running == 0) break;
+        if (c >= 1) {
+            if (cudaEventSynchronize(ev[(c - 1) & 1]) != cudaSuccess) {
+                st = fail3(ctx, MPR_ECUDA, "event synchronisation failed");
+                break;
+            }
+            if (ctx->h_run[(c - 1) & 1] == 0) break;
+        }
+        ++c;
     }
+    cudaStreamSynchronize(ctx->s);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
     if (st == MPR_OK) st = mpr3_sim_end(ctx);
     return st;
 }

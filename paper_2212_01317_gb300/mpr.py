@@ -30,7 +30,7 @@ EXPORTS = [
     "mpr_predict_batch", "mpr_get_slice_layout", "mpr_autotune", "mpr_release_cached_memory",
     "mpr3_create", "mpr3_destroy", "mpr3_last_error", "mpr3_get_info", "mpr3_get_block_stats",
     "mpr3_calibrate", "mpr3_set_temperatures", "mpr3_simulate", "mpr3_predict", "mpr3_sim_begin",
-    "mpr3_halfstep", "mpr3_get_state", "mpr3_set_state", "mpr3_sim_end",
+    "mpr3_halfstep", "mpr3_get_state", "mpr3_set_state", "mpr3_sim_end", "mpr3_get_profile",
 ]
 MPR_NOALLOC_MAX_BLOCKS = 65536
 
@@ -159,6 +159,7 @@ def load(path: str | None = None):
         "mpr3_set_temperatures": (st, [P, P]),
         "mpr3_simulate": (st, [P, i32]),
         "mpr3_predict": (st, [P, P, P, P]),
+        "mpr3_get_profile": (st, [P, C.POINTER(mpr_profile)]),
         "mpr3_sim_begin": (st, [P, i32]),
         "mpr3_halfstep": (st, [P, i32, i32, i32]),
         "mpr3_get_state": (st, [P, i32, P]),
@@ -564,6 +565,11 @@ class GapFiller3:
             raise MprError(st, load().mpr_status_string(st).decode())
         self.ctx = out
         self.info = self.refresh()
+
+    def profile(self) -> mpr_profile:
+        p = mpr_profile()
+        _check3(self.ctx, load().mpr3_get_profile(self.ctx, C.byref(p)))
+        return p
 
     def refresh(self) -> mpr3_info:
         info = mpr3_info()

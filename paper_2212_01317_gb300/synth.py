@@ -63,6 +63,22 @@ def grf(h: int, w: int, xi: float, seed: int) -> np.ndarray:
     return _standardise(f)
 
 
+def grf3(d: int, h: int, w: int, xi: float, seed: int) -> np.ndarray:
+    """Stationary zero-mean unit-variance 3-D GRF with exponential covariance
+    (spectral synthesis on a periodic cube of side max(d, h, w, 8 xi)), float64."""
+    n = int(max(d, h, w, math.ceil(8 * xi)))
+    ax = np.arange(n, dtype=np.float64)
+    ax = np.minimum(ax, n - ax)
+    r = np.sqrt(ax[:, None, None] ** 2 + ax[None, :, None] ** 2 + ax[None, None, :] ** 2)
+    spec = np.fft.rfftn(np.exp(-r / float(xi))).real
+    del r
+    np.maximum(spec, 0.0, out=spec)
+    rng = np.random.default_rng(seed)
+    f = np.fft.irfftn(np.sqrt(spec) * np.fft.rfftn(rng.standard_normal((n, n, n))),
+                      s=(n, n, n))[:d, :h, :w]
+    return _standardise(f)
+
+
 def grf_nonstationary(h: int, w: int, xi_min: float, xi_max: float, seed: int,
                       n_levels: int = 8) -> np.ndarray:
     """GRF whose correlation length grows linearly from xi_min (x=0) to xi_max (x=W-1)."""
@@ -215,8 +231,20 @@ def _wl_field16384(seed: int = 0) -> Workload:
                     meta={"H": 16384, "W": 16384, "xi": [8, 128], "p": float(m.mean())})
 
 
+def _wl_cube256(seed: int = 0) -> Workload:
+    """256^3 stationary 3-D GRF (xi = 8), 50 % random gaps, cubic blocks of side
+    16, R = 20 (the 3-D extension)."""
+    z = grf3(256, 256, 256, 8.0, seed).astype(np.float32)
+    rng = np.random.default_rng(seed + 1)
+    m = np.zeros(z.size, np.uint8)
+    m[rng.permutation(z.size)[:z.size // 2]] = 1
+    return Workload("cube256_xi8_p50_lb16_R20", z, m.reshape(z.shape), 16, 20,
+                    meta={"D": 256, "H": 256, "W": 256, "xi": 8, "p": 0.5})
+
+
 WORKLOADS = {
     "field128": _wl_field128,
+    "cube256": _wl_cube256,
     "field1024": _wl_field1024,
     "field4096": _wl_field4096,
     "field16384": _wl_field16384,

@@ -143,3 +143,23 @@ def test_one_layer_equals_the_2d_library():
     g3.close()
     scale = float(z[m == 0].max() - z[m == 0].min())
     assert (np.abs(p3[0] - p2) <= 1e-5 * scale)[m != 0].mean() >= 0.98
+
+
+def test_profile_counts_and_times_the_half_steps():
+    """mpr3_get_profile: with profile = 1 the realizations' half-steps and the
+    calibration are timed with CUDA events; the sweep loop's running-count
+    reads (one chunk late) end the batch like the per-sweep check would."""
+    D, H, W, lb, R = 8, 16, 12, 4, 6
+    z, m = field3(D, H, W, 0.5, 13)
+    gf = GapFiller3(values_of(z, m), m, lb, seed=3, n_max=30, profile=1, n_bisect=3,
+                    n_eq=3, n_meas=3)
+    gf.calibrate()
+    gf.simulate(R)
+    p = gf.profile()
+    info = gf.refresh()
+    assert p.sim_halfstep_launches >= 2 and p.sim_halfstep_launches % 2 == 0
+    assert p.sim_halfstep_ms > 0 and p.cal_halfstep_ms > 0
+    assert p.cal_halfstep_launches == 3 * 6 * 2
+    assert p.kernel_launches > p.sim_halfstep_launches
+    assert info.realizations == R and info.gap_updates > 0
+    gf.close()
