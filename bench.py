@@ -727,6 +727,15 @@ def run_ours_3d(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     bpu = bytes_per_gap_update(4.0, p)
     achieved = sim_ups * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+    # DRAM bytes per launch: the ncu-measured bytes per update of this
+    # workload's half-step (profiles/traffic.json) times the updates per launch.
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath) and sim_launch:
+        with open(tpath) as f:
+            rec = json.load(f).get(f"sim_{wl.name}")
+        if rec:
+            traffic = rec["bytes_per_update"] * sim_ups / sim_launch
     line = {
         "metric": METRIC, "value": ups_all / (total_ms / 1e3), "unit": "updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -740,7 +749,7 @@ def run_ours_3d(args, world, rank, local):
         "gap_filled_mpix_s": world * P * args.steps / (total_ms / 1e3) / 1e6,
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": "k3_sweep (realizations)", "peak_kind": peak_kind,
                      "bytes_per_gap_update": bpu,
                      "avg_launch_us": 1e3 * sim_ms / max(sim_launch, 1),
