@@ -686,11 +686,11 @@ mpr_status sweep3(mpr3_ctx* ctx) {
     const int grid = (int)std::min<int64_t>((items * 2 + 255) / 256, 152 * 16);
     launch_stop_targeted(2, ctx->np, ctx->Rp, ctx->zero_slices, grid, ctx->ctl, ctx->work,
                          (uint32_t)items, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
-                         ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
+                         ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, -1, ctx->s);
     CKL3();
     launch_stop_rest(ctx->g.nblk, ctx->np, 2, ctx->Rp, ctx->opt.n_max, ctx->zero_slices, grid,
                      ctx->ctl, ctx->work, ctx->work, (uint32_t)items, ctx->Nsp, ctx->running,
-                     ctx->stop, ctx->tcount, 0, ctx->s);
+                     ctx->stop, ctx->tcount, 0, -1, ctx->s);
     CKL3();
     return MPR_OK;
 }
@@ -975,7 +975,7 @@ mpr_status mpr3_sim_begin(mpr3_ctx* ctx, int32_t n) {
     launch_stop_rest(ctx->g.nblk, ctx->np, 2, ctx->Rp, ctx->opt.n_max, ctx->zero_slices,
                      (int)std::min<int64_t>((items + 255) / 256, 152 * 16), ctx->ctl, nullptr,
                      ctx->work, (uint32_t)items, ctx->Nsp, ctx->running, ctx->stop, ctx->tcount, 0,
-                     ctx->s);
+                     -1, ctx->s);
     CKL3();
     ctx->batch_open = 1;
     return MPR_OK;

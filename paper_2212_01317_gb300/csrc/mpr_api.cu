@@ -78,6 +78,7 @@ struct mpr_ctx {
     bool chains_valid = false;   // the batch state holds the calibration chains
     bool moments_valid = false;
     cudaGraphConditionalHandle sim_cond = 0;   // set while a sweep loop is being captured
+    bool sim_capture = false;                  // a sweep loop is being captured
     double* ebar = nullptr;
     double* sum = nullptr;  // [2][H][Wh] running sums of gap angles
     float* out_buf = nullptr;
@@ -463,10 +464,16 @@ mpr_status sweep_once(mpr_ctx* ctx) {
         e1 = get_event(ctx);
         if (e0) cudaEventRecord(e0, ctx->s);
     }
+    // The device's sweep index is the host's count plus one (the stop test at
+    // t = 0 set it to 1, and every sweep's closing CTA advances it), so the
+    // kernels take it as an argument instead of a dependent read; a captured
+    // loop body reads it on the device.
+    const int t_known = ctx->sim_capture ? -1 : ctx->t + 1;
     for (int c = 0; c < 2; ++c) {
         const int form = sweep_form(ctx);
-        launch_sweep(sweep_args(ctx, c, true), ctx->G, ctx->storage, form, sweep_grid(ctx, form),
-                     ctx->s);
+        SweepArgs a = sweep_args(ctx, c, true);
+        a.t_fixed = t_known > 0 ? t_known : 0;
+        launch_sweep(a, ctx->G, ctx->storage, form, sweep_grid(ctx, form), ctx->s);
         CKL();
         ++ctx->sim_halfstep_launches;
     }
@@ -479,11 +486,12 @@ mpr_status sweep_once(mpr_ctx* ctx) {
                          stop_grid(ctx, 2, kTargetedCtasPerSm),
                          ctx->ctl, ctx->work,
                          ctx->work_stride, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
-                         ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
+                         ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, t_known,
+                         ctx->s);
     CKL();
     launch_stop_rest(g.nblk, ctx->Rp / 2, 2, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
                      stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp,
-                     ctx->running, ctx->stop, ctx->tcount, ctx->sim_cond, ctx->s);
+                     ctx->running, ctx->stop, ctx->tcount, ctx->sim_cond, t_known, ctx->s);
     CKL();
     ctx->t += 1;
     return MPR_OK;
@@ -1402,7 +1410,7 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     CKL();
     launch_stop_rest(ctx->g.nblk, ctx->Rp / 2, 2, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
                      stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp,
-                     ctx->running, ctx->stop, ctx->tcount, 0, ctx->s);
+                     ctx->running, ctx->stop, ctx->tcount, 0, -1, ctx->s);
     CKL();
     ctx->energy_dirty = false;
     ctx->batch_open = 1;
@@ -1478,11 +1486,13 @@ mpr_status simulate_graph(mpr_ctx* ctx) {
         const int profile = ctx->opt.profile;
         ctx->s = ctx->cap;
         ctx->sim_cond = cond;
+        ctx->sim_capture = true;
         ctx->opt.profile = 0;
         ctx->bound = ~0ull;
         st = sweep_once(ctx);
         ctx->opt.profile = profile;
         ctx->sim_cond = 0;
+        ctx->sim_capture = false;
         ctx->s = user;
     }
     if (cudaStreamEndCapture(ctx->cap, &captured) != cudaSuccess && st == MPR_OK) goto cuda_fail;

@@ -364,12 +364,16 @@ __global__ void __launch_bounds__(128, 8) k_sweep(SweepArgs a) {
     const uint32_t ctr1 = t | (a.ctl->tag << 16);
     const uint32_t* work = a.work ? a.work + (size_t)(t & 1u) * a.work_stride : nullptr;
     const int npairs = a.groups * NP;
-    const int n_units = work ? (int)a.ctl->n_work[t & 1u] : a.g.nblk * npairs;
     constexpr int UPC = 4 / WPU;
     const int warp = threadIdx.x >> 5;
     const int slot = warp / WPU, cw = warp % WPU;
-    for (int it = blockIdx.x * UPC + slot; it < n_units; it += gridDim.x * UPC) {
-        const int u = work ? (int)work[it] : it;
+    const int it0 = blockIdx.x * UPC + slot;
+    // The worklist buffer is work_stride entries long whatever the count, so
+    // the first unit is read together with the count (stale past it).
+    int u = work ? (it0 < (int)a.work_stride ? (int)work[it0] : 0) : it0;
+    const int n_units = work ? (int)a.ctl->n_work[t & 1u] : a.g.nblk * npairs;
+    for (int it = it0; it < n_units; it += gridDim.x * UPC) {
+        if (it != it0) u = work ? (int)work[it] : it;
         const int b = u / npairs, p = u - b * npairs;
         const int grp = p / NP, q = p - grp * NP;
         sweep_item<G, S>(a, b * a.groups + grp, q + NP * cw, NP * WPU, ctr1);
@@ -470,14 +474,17 @@ __global__ void k_stop_init(int nblk, int Rp, const int32_t* __restrict__ of_blo
 // running targeted blocks, which the first completes.
 //
 // k_stop_targeted: one thread per (item, lane) of the sweep's worklist.
+// t_known >= 0: the sweep index (the host's loop knows it), else read from ctl.
 __global__ void k_stop_targeted(StopArgs sa, Control* __restrict__ ctl,
-                                const uint32_t* __restrict__ work, uint32_t work_stride) {
+                                const uint32_t* __restrict__ work, uint32_t work_stride,
+                                int t_known) {
     grid_dep_launch();
     grid_dep_wait();
-    const uint32_t t_sweep = ctl->t;
+    const uint32_t t_sweep = t_known >= 0 ? (uint32_t)t_known : ctl->t;
     const uint32_t* w = work + (size_t)(t_sweep & 1u) * work_stride;
     const int64_t n = (int64_t)ctl->n_work[t_sweep & 1u] * sa.G;
-    stop_targeted_range(sa, t_sweep, w, n, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+    stop_targeted_range(sa, t_sweep, w, n, (int64_t)work_stride * sa.G,
+                        blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                         (int64_t)gridDim.x * blockDim.x);
 }
 
@@ -488,16 +495,17 @@ __global__ void k_stop_targeted(StopArgs sa, Control* __restrict__ ctl,
 // after it.
 __global__ void k_stop_rest(StopArgs sa, cudaGraphConditionalHandle cond,
                             Control* __restrict__ ctl, const uint32_t* __restrict__ work,
-                            uint32_t* __restrict__ work_all, uint32_t work_stride) {
+                            uint32_t* __restrict__ work_all, uint32_t work_stride, int t_known) {
     grid_dep_launch();
     grid_dep_wait();
-    const uint32_t t_sweep = ctl->t;
+    const uint32_t t_sweep = t_known >= 0 ? (uint32_t)t_known : ctl->t;
     const uint32_t par = t_sweep & 1u, nxt = par ^ 1u;
     const uint32_t* w = work ? work + (size_t)par * work_stride : nullptr;
     uint32_t* out = work_all + (size_t)nxt * work_stride;
     const int64_t n = w ? (int64_t)ctl->n_work[par] : (int64_t)sa.nblk * sa.groups;
     const int n_max = sa.n_max;
-    unsigned cnt = stop_rest_range(sa, t_sweep, w, n, out, &ctl->n_work[nxt],
+    unsigned cnt = stop_rest_range(sa, t_sweep, w, n, (int64_t)work_stride, out,
+                                   &ctl->n_work[nxt],
                                    blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                                    (int64_t)gridDim.x * blockDim.x);
     for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
@@ -1187,7 +1195,7 @@ void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, in
                           Control* ctl, const uint32_t* work, uint32_t work_stride,
                           const double* es, const double* inb, const int32_t* Nsp, float* eacc,
                           double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
-                          int32_t* tcount, double* e_last, cudaStream_t s) {
+                          int32_t* tcount, double* e_last, int t_known, cudaStream_t s) {
     StopArgs sa{};
     sa.G = G;
     sa.groups = groups;
@@ -1203,13 +1211,14 @@ void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, in
     sa.stop = stop;
     sa.tcount = tcount;
     sa.e_last = e_last;
-    launch_pdl(k_stop_targeted, grid, 256, s, sa, ctl, work, work_stride);
+    launch_pdl(k_stop_targeted, grid, 256, s, sa, ctl, work, work_stride, t_known);
 }
 
 void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int32_t* of_block,
                       int grid, Control* ctl, const uint32_t* work, uint32_t* work_all,
                       uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
-                      const int32_t* tcount, cudaGraphConditionalHandle cond, cudaStream_t s) {
+                      const int32_t* tcount, cudaGraphConditionalHandle cond, int t_known,
+                      cudaStream_t s) {
     StopArgs sa{};
     sa.G = G;
     sa.groups = groups;
@@ -1221,7 +1230,7 @@ void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int3
     sa.running = running;
     sa.stop = stop;
     sa.tcount = const_cast<int32_t*>(tcount);
-    launch_pdl(k_stop_rest, grid, 256, s, sa, cond, ctl, work, work_all, work_stride);
+    launch_pdl(k_stop_rest, grid, 256, s, sa, cond, ctl, work, work_all, work_stride, t_known);
 }
 
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,

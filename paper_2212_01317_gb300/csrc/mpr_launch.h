@@ -52,13 +52,14 @@ void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, in
                           Control* ctl, const uint32_t* work, uint32_t work_stride,
                           const double* es, const double* inb, const int32_t* Nsp, float* eacc,
                           double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
-                          int32_t* tcount, double* e_last, cudaStream_t s);
+                          int32_t* tcount, double* e_last, int t_known, cudaStream_t s);
 // work == nullptr: every item (t = 0). Writes the next sweep's worklist into
 // work_all and advances ctl->t.
 void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int32_t* of_block,
                       int grid, Control* ctl, const uint32_t* work, uint32_t* work_all,
                       uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
-                      const int32_t* tcount, cudaGraphConditionalHandle cond, cudaStream_t s);
+                      const int32_t* tcount, cudaGraphConditionalHandle cond, int t_known,
+                      cudaStream_t s);
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
                           unsigned long long* total, cudaStream_t s);
 void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,

@@ -75,9 +75,10 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_sim_tail(SimTailArgs a) {
                 }
             if (!grid_sync(a.bar, gen, lim)) return;
         }
-        stop_targeted_range(a.st, t, work, (int64_t)n_items * a.st.G, tid, nthr);
+        stop_targeted_range(a.st, t, work, (int64_t)n_items * a.st.G, (int64_t)n_items * a.st.G,
+                            tid, nthr);
         if (!grid_sync(a.bar, gen, lim)) return;
-        unsigned cnt = stop_rest_range(a.st, t, work, (int64_t)n_items,
+        unsigned cnt = stop_rest_range(a.st, t, work, (int64_t)n_items, (int64_t)n_items,
                                        a.work_all + (size_t)nxt * a.sw.work_stride,
                                        &ctl->n_work[nxt], tid, nthr);
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);

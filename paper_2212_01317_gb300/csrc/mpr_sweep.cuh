@@ -469,52 +469,62 @@ __device__ __forceinline__ void energy_item(const SweepArgs& a, int item, int wi
 //
 // Targeted part: E_b += the sweep's change (eacc, then cleared); e_b = E_b / N_b;
 // a targeted block stops once sigma (e_b(t) - e_s,b) >= 0. Entries
-// i = i0, i0 + step, ... < n of (item, lane) pairs (n = items * G).
+// i = i0, i0 + step, ... < n of (item, lane) pairs (n = items * G). Entries
+// below `cap` are readable whatever n is (the worklist buffer's length times
+// G; past n they hold stale items), so the first item is read without waiting
+// for n; every value of an entry is then read at once, and only then tested.
 __device__ __forceinline__ void stop_targeted_range(const StopArgs& s, uint32_t t_sweep,
                                                     const uint32_t* __restrict__ w, int64_t n,
-                                                    int64_t i0, int64_t step) {
+                                                    int64_t cap, int64_t i0, int64_t step) {
+    uint32_t item = i0 < cap ? w[i0 / s.G] : 0u;
     for (int64_t i = i0; i < n; i += step) {
-        const uint32_t item = w[i / s.G];
+        if (i != i0) item = w[i / s.G];
         const int b = (int)(item / (uint32_t)s.groups);
         const int r = (int)(item % (uint32_t)s.groups) * s.G + (int)(i % s.G);
         const size_t k = (size_t)b * s.Rp + r;
-        if (!s.running[k]) continue;
+        const uint8_t run = s.running[k];
         const double E = s.ecur[k] + (double)s.eacc[k];
+        const double inb = s.inb[b], es = s.es[b];
+        const int32_t nsp = s.Nsp[b], ob = s.of_block[b];
+        const int sg = s.sigma[k];
+        if (!run) continue;
         s.eacc[k] = 0.0f;
         s.ecur[k] = E;
-        const double e = E * s.inb[b];
+        const double e = E * inb;
         s.e_last[k] = e;
-        if (s.Nsp[b] == 0) continue;
-        const int sg = s.sigma[k];
-        const bool reached = sg > 0 ? (e >= s.es[b]) : (sg < 0 ? (e <= s.es[b]) : true);
+        if (nsp == 0) continue;
+        const bool reached = sg > 0 ? (e >= es) : (sg < 0 ? (e <= es) : true);
         if (reached) {
             s.running[k] = 0;
             s.stop[k] = (int32_t)t_sweep;
-            atomicSub(&s.tcount[s.of_block[b] * s.Rp + r], 1);
+            atomicSub(&s.tcount[ob * s.Rp + r], 1);
         }
     }
 }
 
 // Closing part: blocks without sample bonds stop when no targeted block of
 // their realization runs; everything stops at n_max. Items with a lane still
-// running are appended to `out` (counter *n_out). Items i = i0, i0 + step,
-// ... < n of the worklist w (nullptr: every item). Returns this thread's
-// count of lanes still running.
+// running are appended to `out` (counter *n_out, one atomic per warp, items in
+// lane order). Items i = i0, i0 + step, ... < n of the worklist w (nullptr:
+// every item); `cap` as for the targeted part. Returns this thread's count of
+// lanes still running.
 __device__ __forceinline__ unsigned stop_rest_range(const StopArgs& s, uint32_t t_sweep,
                                                     const uint32_t* __restrict__ w, int64_t n,
-                                                    uint32_t* __restrict__ out, uint32_t* n_out,
-                                                    int64_t i0, int64_t step) {
+                                                    int64_t cap, uint32_t* __restrict__ out,
+                                                    uint32_t* n_out, int64_t i0, int64_t step) {
     unsigned cnt = 0;
+    uint32_t item = w ? (i0 < cap ? w[i0] : 0u) : (uint32_t)i0;
     for (int64_t i = i0; i < n; i += step) {
-        const uint32_t item = w ? w[i] : (uint32_t)i;
+        if (i != i0) item = w ? w[i] : (uint32_t)i;
         const int b = (int)(item / (uint32_t)s.groups), grp = (int)(item % (uint32_t)s.groups);
-        const int32_t* tc = s.tcount + (size_t)(s.of_block[b] < 0 ? 0 : s.of_block[b]) * s.Rp;
+        const int32_t ob = s.of_block[b], nsp = s.Nsp[b];
+        const int32_t* tc = s.tcount + (size_t)(ob < 0 ? 0 : ob) * s.Rp;
         bool any = false;
         for (int g = 0; g < s.G; ++g) {
             const int r = grp * s.G + g;
             const size_t k = (size_t)b * s.Rp + r;
             if (!s.running[k]) continue;
-            if ((s.Nsp[b] == 0 && tc[r] == 0) || (int)t_sweep >= s.n_max) {
+            if ((nsp == 0 && tc[r] == 0) || (int)t_sweep >= s.n_max) {
                 s.running[k] = 0;
                 s.stop[k] = (int32_t)t_sweep;
             } else {
@@ -522,7 +532,16 @@ __device__ __forceinline__ unsigned stop_rest_range(const StopArgs& s, uint32_t 
                 any = true;
             }
         }
-        if (any) out[atomicAdd(n_out, 1u)] = item;
+        const unsigned act = __activemask();
+        const unsigned vote = __ballot_sync(act, any);
+        if (vote) {
+            const int lane = threadIdx.x & 31;
+            const int leader = __ffs(vote) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(n_out, (uint32_t)__popc(vote));
+            base = __shfl_sync(act, base, leader);
+            if (any) out[base + __popc(vote & ((1u << lane) - 1u))] = item;
+        }
     }
     return cnt;
 }
