@@ -313,8 +313,8 @@ def run_ours(args, world, rank, local):
     clocks.start()
     time.sleep(0.3)
     step_ms, updates, cal_updates, launches = [], 0, 0, 0
-    sim_ms = cal_ms = 0.0
-    sim_launch = cal_launch = sim_updates = 0
+    sim_ms = cal_ms = tail_ms = 0.0
+    sim_launch = cal_launch = sim_updates = tail_updates = tail_launch = 0
     for k in range(args.steps):
         flush.zero_()                              # L2 flush between timed steps
         e0 = torch.cuda.Event(enable_timing=True)
@@ -332,6 +332,9 @@ def run_ours(args, world, rank, local):
         cal_ms += prof.cal_halfstep_ms
         sim_launch += prof.sim_halfstep_launches
         cal_launch += prof.cal_halfstep_launches
+        tail_ms += prof.sim_tail_ms
+        tail_updates += prof.sim_tail_updates
+        tail_launch += prof.sim_tail_launches
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -436,7 +439,10 @@ def run_ours(args, world, rank, local):
 
     peak, peak_kind = measured_peaks()
     bpu = bytes_per_gap_update(4.0 if args.storage == "f32" else 2.0, p)
-    sim_gbs = sim_updates * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+    # The realizations' per-launch half-steps (k_sweep) ran every update but
+    # those of the stop-tail launch, which is timed and counted apart.
+    sweep_updates = sim_updates - tail_updates
+    sim_gbs = sweep_updates * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
     cal_gbs = cal_updates * bpu / (cal_ms / 1e3) / 1e9 if cal_ms > 0 else None
     # Dominant kernel by summed device time.
     dom = "sim" if sim_ms >= cal_ms else "cal"
@@ -450,7 +456,7 @@ def run_ours(args, world, rank, local):
         with open(tpath) as f:
             rec = json.load(f).get(f"sim_{wl.name}")
         if rec:
-            traffic = rec["bytes_per_update"] * sim_updates / sim_launch
+            traffic = rec["bytes_per_update"] * sweep_updates / sim_launch
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -462,7 +468,12 @@ def run_ours(args, world, rank, local):
         "avg_launch_us": 1e3 * (sim_ms / sim_launch if dom == "sim" else cal_ms / max(cal_launch, 1)),
         "sim_halfstep": {"ms": sim_ms / args.steps, "launches": sim_launch // args.steps,
                          "gbs": sim_gbs,
-                         "updates_per_s": sim_updates / (sim_ms / 1e3) if sim_ms else None},
+                         "updates_per_s": sweep_updates / (sim_ms / 1e3) if sim_ms else None},
+        "stop_tail": {"kernel": "k_pair_tail (one CTA per realization pair; its time includes "
+                                "the stop tests of its sweeps)",
+                      "ms": tail_ms / args.steps, "launches": tail_launch // args.steps,
+                      "updates": tail_updates // args.steps,
+                      "updates_per_s": tail_updates / (tail_ms / 1e3) if tail_ms else None},
         "cal_halfstep": {"ms": cal_ms / args.steps, "launches": cal_launch // args.steps,
                          "gbs": cal_gbs,
                          "updates_per_s": cal_updates / (cal_ms / 1e3) if cal_ms else None},
@@ -551,6 +562,7 @@ def run_ours_batch(args, world, rank, local):
     clocks.start()
     time.sleep(0.3)
     step_ms, updates, sim_updates, launches, sim_ms, sim_launch = [], 0, 0, 0, 0.0, 0
+    tail_updates = 0
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -565,6 +577,7 @@ def run_ours_batch(args, world, rank, local):
         launches += prof.kernel_launches
         sim_ms += prof.sim_halfstep_ms
         sim_launch += prof.sim_halfstep_launches
+        tail_updates += prof.sim_tail_updates
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = replicas.max_over_ranks(float(np.sum(step_ms)), dev)
@@ -617,7 +630,8 @@ def run_ours_batch(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     p_mean = P / bw.n_sites
     bpu = bytes_per_gap_update(4.0 if storage == "f32" else 2.0, p_mean)
-    achieved = sim_updates * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
+    # (the stop-tail launch's updates are timed and counted apart)
+    achieved = (sim_updates - tail_updates) * bpu / (sim_ms / 1e3) / 1e9 if sim_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

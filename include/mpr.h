@@ -106,6 +106,12 @@ typedef struct {
     int32_t sweep_form;  /* realizations' half-step: -1 automatic (default: one warp per
                             realization pair while many pairs run, two, then four as fewer
                             remain), 0, 1, 2: always one, two or four warps per pair */
+    int32_t pair_tail;   /* running (block, realization) pairs at or below which mpr_simulate runs
+                            the rest of its sweep loop as one launch with one CTA per realization
+                            pair (each pair's remaining sweeps and stop tests in its CTA, CTA
+                            barriers between the phases); 0: never; values above 4096 act as
+                            4096 (the default: 0.65 ms of 23.8 ms saved per 1024^2 bench step);
+                            sim_tail > 0 takes precedence */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 
@@ -116,6 +122,10 @@ typedef struct {
     double sim_halfstep_ms;         /* summed device time of those launches (profile = 1) */
     double cal_halfstep_ms;         /* cal_mode 1: time of the whole calibration graph;
                                        cal_mode 3: summed time of the half-step launches */
+    int64_t sim_tail_launches;      /* stop-tail launches (pair_tail or sim_tail) made by
+                                       simulate with profile = 1 */
+    int64_t sim_tail_updates;       /* site updates those launches ran (of gap_updates) */
+    double sim_tail_ms;             /* their device time, stop tests included */
 } mpr_profile;
 
 typedef struct {

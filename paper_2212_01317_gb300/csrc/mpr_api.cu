@@ -127,6 +127,8 @@ struct mpr_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_sim, ev_cal;  // pending pairs
     double sim_halfstep_ms = 0.0, cal_halfstep_ms = 0.0;
     int64_t sim_halfstep_launches = 0, cal_halfstep_launches = 0;
+    double sim_tail_ms = 0.0;                    // stop-tail launches (profile = 1)
+    int64_t sim_tail_launches = 0, sim_tail_updates = 0;
 };
 
 namespace {
@@ -219,6 +221,7 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.cal_method != 0 && o.cal_method != 1) return fail(ctx, MPR_EINVAL, "cal_method must be 0 or 1");
     if (o.cal_points != 1 && o.cal_points != 2) return fail(ctx, MPR_EINVAL, "cal_points must be 1 or 2");
     if (o.sim_tail < 0) return fail(ctx, MPR_EINVAL, "sim_tail must be >= 0");
+    if (o.pair_tail < 0) return fail(ctx, MPR_EINVAL, "pair_tail must be >= 0");
     if (o.sweep_form < -1 || o.sweep_form > 2)
         return fail(ctx, MPR_EINVAL, "sweep_form must be -1, 0, 1 or 2");
     if (o.n_newton < 0 || o.n_newton > 65533) return fail(ctx, MPR_EINVAL, "n_newton in [0, 65533]");
@@ -846,6 +849,7 @@ void mpr_default_options(mpr_options* o) {
     o->cal_points = 1;
     o->sim_tail = 0;
     o->sweep_form = -1;
+    o->pair_tail = 4096;
     o->cuda_stream = nullptr;
 }
 
@@ -1260,6 +1264,9 @@ mpr_status mpr_get_profile(mpr_ctx* ctx, mpr_profile* p) {
     p->cal_halfstep_launches = ctx->cal_halfstep_launches;
     p->sim_halfstep_ms = ctx->sim_halfstep_ms;
     p->cal_halfstep_ms = ctx->cal_halfstep_ms;
+    p->sim_tail_launches = ctx->sim_tail_launches;
+    p->sim_tail_updates = ctx->sim_tail_updates;
+    p->sim_tail_ms = ctx->sim_tail_ms;
     return MPR_OK;
 }
 
@@ -1531,10 +1538,53 @@ done:
 // The rest of the sweep loop as one cooperative launch (the stop tail, when
 // few pairs still run). *ran is false when the device or the grid does not
 // allow the launch (then nothing ran and the per-launch loop goes on).
-mpr_status simulate_tail(mpr_ctx* ctx, bool* ran) {
-    *ran = false;
-    const int per_sm = ctx->coop ? sim_tail_blocks_per_sm(ctx->G, ctx->storage) : 0;
-    if (per_sm < 1) return MPR_OK;
+// Profiling of a stop-tail launch (profile = 1): its device time and the
+// site updates it ran (the batch's updates after it minus those before it),
+// kept apart from the per-launch half-steps' figures.
+struct TailProfile {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+mpr_status tail_profile_begin(mpr_ctx* ctx, TailProfile& tp) {
+    if (!ctx->opt.profile) return MPR_OK;
+    tp.e0 = get_event(ctx);
+    tp.e1 = get_event(ctx);
+    if (!tp.e0 || !tp.e1) return fail(ctx, MPR_ECUDA, "cudaEventCreate failed");
+    CK(cudaMemsetAsync(ctx->counters + 2, 0, 2 * sizeof(unsigned long long), ctx->s));
+    launch_count_updates(ctx->g.nblk, ctx->Rp, ctx->stop, ctx->ngap, ctx->counters + 2, ctx->s,
+                         ctx->ctl);
+    CKL();
+    CK(cudaEventRecord(tp.e0, ctx->s));
+    return MPR_OK;
+}
+
+mpr_status tail_profile_end(mpr_ctx* ctx, TailProfile& tp) {
+    if (!tp.e0) return MPR_OK;
+    CK(cudaEventRecord(tp.e1, ctx->s));
+    launch_count_updates(ctx->g.nblk, ctx->Rp, ctx->stop, ctx->ngap, ctx->counters + 3, ctx->s,
+                         ctx->ctl);
+    CKL();
+    CK(cudaMemcpyAsync(ctx->h_counters + 4, ctx->counters + 2, 2 * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, ctx->s));
+    return MPR_OK;
+}
+
+// After a synchronisation of the stream.
+void tail_profile_collect(mpr_ctx* ctx, TailProfile& tp) {
+    if (!tp.e0) return;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, tp.e0, tp.e1) == cudaSuccess) ctx->sim_tail_ms += ms;
+    else cudaGetLastError();
+    ctx->sim_tail_updates += (int64_t)(ctx->h_counters[5] - ctx->h_counters[4]);
+    ++ctx->sim_tail_launches;
+    ctx->ev_pool.push_back(tp.e0);
+    ctx->ev_pool.push_back(tp.e1);
+    tp.e0 = tp.e1 = nullptr;
+}
+
+// The arguments of the stop-tail launches: every sweep field, both colours'
+// lists and the stop test's arrays.
+SimTailArgs tail_args(mpr_ctx* ctx) {
     const mpr_options& o = ctx->opt;
     SimTailArgs a{};
     a.sw = sweep_args(ctx, 0, true);
@@ -1563,16 +1613,21 @@ mpr_status simulate_tail(mpr_ctx* ctx, bool* ran) {
     st.e_last = ctx->e_last;
     a.ctl = ctx->ctl;
     a.work_all = ctx->work;
+    return a;
+}
+
+mpr_status simulate_tail(mpr_ctx* ctx, bool* ran) {
+    *ran = false;
+    const int per_sm = ctx->coop ? sim_tail_blocks_per_sm(ctx->G, ctx->storage) : 0;
+    if (per_sm < 1) return MPR_OK;
+    const mpr_options& o = ctx->opt;
+    SimTailArgs a = tail_args(ctx);
     a.bar = ctx->bar;
     a.spin_limit = (unsigned long long)o.wait_ms * 10000ull;   // ~100 ns per poll
     GridBarrier hb{0u, 0u, 0u, (unsigned int)o.barrier_test};
     CK(cudaMemcpyAsync(ctx->bar, &hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->s));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (o.profile) {
-        e0 = get_event(ctx);
-        e1 = get_event(ctx);
-        if (e0) cudaEventRecord(e0, ctx->s);
-    }
+    TailProfile tp;
+    TRY(tail_profile_begin(ctx, tp));
     // A grid sized for the pairs still running (16 warps per CTA, about two
     // units per warp at the switch): few CTAs make the grid barriers cheap.
     const unsigned long long want = std::max<unsigned long long>(8, ctx->bound / 32);
@@ -1580,30 +1635,45 @@ mpr_status simulate_tail(mpr_ctx* ctx, bool* ran) {
     const cudaError_t le = launch_sim_tail(a, ctx->G, ctx->storage, grid, ctx->s);
     if (le != cudaSuccess) {
         cudaGetLastError();
-        if (e0) ctx->ev_pool.push_back(e0);
-        if (e1) ctx->ev_pool.push_back(e1);
+        if (tp.e0) ctx->ev_pool.push_back(tp.e0);
+        if (tp.e1) ctx->ev_pool.push_back(tp.e1);
         return MPR_OK;
     }
     *ran = true;
     ++ctx->launches;
-    if (e0 && e1) {
-        cudaEventRecord(e1, ctx->s);
-        ctx->ev_sim.emplace_back(e0, e1);
-    }
+    TRY(tail_profile_end(ctx, tp));
     CK(cudaMemcpyAsync(&hb, ctx->bar, sizeof(hb), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
+    tail_profile_collect(ctx, tp);
     if (hb.err)
         return fail(ctx, MPR_ETIMEOUT,
                     "simulate: a grid-barrier wait gave up after %d ms; the batch did not "
                     "complete", o.wait_ms);
     // Sweeps run by the launch: from the host's count to the device's last.
     const int t_end = (int)ctx->h_ctl->t - 1;
-    if (t_end > ctx->t) {
-        ctx->sim_halfstep_launches += 2 * (int64_t)(t_end - ctx->t);
-        ctx->t = t_end;
-    }
+    if (t_end > ctx->t) ctx->t = t_end;
     ctx->bound = ctx->h_ctl->n_running;
+    return MPR_OK;
+}
+
+// The rest of the sweep loop with one CTA per realization pair (the stop
+// tail, once every pair's running units fit one CTA's buffer).
+mpr_status simulate_pair_tail(mpr_ctx* ctx) {
+    const SimTailArgs a = tail_args(ctx);
+    TailProfile tp;
+    TRY(tail_profile_begin(ctx, tp));
+    const cudaError_t le = launch_pair_tail(a, ctx->G, ctx->storage, ctx->Rp / 2, ctx->s);
+    if (le != cudaSuccess) return fail(ctx, MPR_ECUDA, "stop tail: %s", cudaGetErrorString(le));
+    ++ctx->launches;
+    TRY(tail_profile_end(ctx, tp));
+    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    tail_profile_collect(ctx, tp);
+    // Sweeps run by the launch: from the host's count to the device's last.
+    const int t_end = (int)ctx->h_ctl->t - 1;
+    if (t_end > ctx->t) ctx->t = t_end;
+    ctx->bound = 0;
     return MPR_OK;
 }
 
@@ -1625,6 +1695,8 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
     int c = 0;
     mpr_status st = MPR_OK;
     bool tail = ctx->opt.sim_tail > 0;
+    // (every pair's units are at most the running count)
+    const unsigned long long pair_below = (unsigned long long)std::min(ctx->opt.pair_tail, kPairTailCap);
     while (ctx->t < ctx->opt.n_max) {
         for (int i = 0; i < chunk && ctx->t < ctx->opt.n_max && st == MPR_OK; ++i) st = sweep_once(ctx);
         if (st != MPR_OK) break;
@@ -1643,7 +1715,12 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
             // the work of every sweep queued from now on.
             ctx->bound = flag[(c - 1) & 1];
             if (ctx->bound == 0) break;
-            // Few pairs left: the rest of the loop as one cooperative launch.
+            // Few pairs left: the rest of the loop as one cooperative launch
+            // (when asked for), or with one CTA per realization pair.
+            if (!tail && ctx->bound <= pair_below) {
+                st = simulate_pair_tail(ctx);
+                break;
+            }
             if (tail && ctx->bound < (unsigned long long)ctx->opt.sim_tail) {
                 bool ran = false;
                 st = simulate_tail(ctx, &ran);

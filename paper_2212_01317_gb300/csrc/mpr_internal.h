@@ -103,7 +103,7 @@ struct Control {
     uint32_t n_work[2];          // worklist sizes by sweep parity
     uint32_t energy_dirty;       // state was overwritten: energies must be recomputed
     uint32_t ticket;             // CTAs of the closing stop kernel that have finished
-    uint32_t pad;
+    uint32_t t_tail;             // the pair-per-CTA stop tail: latest sweep index reached
     unsigned long long n_running;      // running (block, realization) pairs after the last stop test
     unsigned long long n_running_acc;  // the same, being counted by the stop test in progress
 };

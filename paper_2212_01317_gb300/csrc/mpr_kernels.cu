@@ -382,9 +382,12 @@ __global__ void __launch_bounds__(128, 8) k_sweep(SweepArgs a) {
 
 // The last f.ctas CTAs (of blockIdx.y = 0) fold the previous sweep's block
 // energies instead: they touch eacc of the other parity and ecur, which the
-// half-step does not.
+// half-step does not. Eight CTAs per SM (32 registers, a few spilled) keep a
+// 1024^2 field's colour (262 k threads) in one wave: the calibration took
+// 13.2 ms per bench step at the compiler's 47 registers (five CTAs per SM),
+// 12.7 ms at six CTAs per SM and 12.0 ms at eight.
 template <int G>
-__global__ void __launch_bounds__(kFlatThreads) k_sweep_flat(SweepArgs a, int64_t n_list,
+__global__ void __launch_bounds__(kFlatThreads, 8) k_sweep_flat(SweepArgs a, int64_t n_list,
                                                             FoldArgs f) {
     grid_dep_launch();
     const int sweep_ctas = (int)gridDim.x - f.ctas;
@@ -533,15 +536,19 @@ __global__ void k_stop_rest(StopArgs sa, cudaGraphConditionalHandle cond,
 }
 
 // Site updates run by the batch: sum over (b, r) of stop sweep x gap sites.
+// With ctl: the updates run so far, pairs still running (stop < 0) counted
+// up to the last completed sweep (ctl->t - 1).
 __global__ void k_count_updates(int nblk, int Rp, const int32_t* __restrict__ stop,
-                                const int32_t* __restrict__ ngap,
+                                const int32_t* __restrict__ ngap, const Control* ctl,
                                 unsigned long long* __restrict__ total) {
     const int64_t n = (int64_t)nblk * Rp;
+    const int32_t t_done = ctl ? (int32_t)ctl->t - 1 : 0;
     unsigned long long s = 0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(t / Rp);
-        if (stop[t] > 0) s += (unsigned long long)stop[t] * (unsigned long long)ngap[b];
+        const int32_t st = stop[t] < 0 ? t_done : stop[t];
+        if (st > 0) s += (unsigned long long)st * (unsigned long long)ngap[b];
     }
     for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
@@ -1234,8 +1241,9 @@ void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int3
 }
 
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
-                          unsigned long long* total, cudaStream_t s) {
-    k_count_updates<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, stop, ngap, total);
+                          unsigned long long* total, cudaStream_t s, const Control* ctl) {
+    k_count_updates<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, stop, ngap, ctl,
+                                                                      total);
 }
 
 void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,

@@ -60,8 +60,9 @@ void launch_stop_rest(int nblk, int groups, int G, int Rp, int n_max, const int3
                       uint32_t work_stride, const int32_t* Nsp, uint8_t* running, int32_t* stop,
                       const int32_t* tcount, cudaGraphConditionalHandle cond, int t_known,
                       cudaStream_t s);
+// ctl != nullptr: updates so far, running pairs counted up to sweep ctl->t - 1.
 void launch_count_updates(int nblk, int Rp, const int32_t* stop, const int32_t* ngap,
-                          unsigned long long* total, cudaStream_t s);
+                          unsigned long long* total, cudaStream_t s, const Control* ctl = nullptr);
 void launch_cal_init(int nblk, float t_lo, float t_hi, float* lo, float* hi, double* ebar,
                      Control* ctl, cudaStream_t s);
 void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T,
@@ -123,6 +124,12 @@ void launch_set_tag(Control* ctl, uint32_t tag, cudaStream_t s);
 // The realizations' stop tail as one cooperative launch (mpr_simtail.cu).
 int sim_tail_blocks_per_sm(int G, int storage);
 cudaError_t launch_sim_tail(const SimTailArgs& a, int G, int storage, int grid, cudaStream_t s);
+
+// The realizations' stop tail with one CTA per realization pair
+// (mpr_pairtail.cu); every pair's running units must fit kPairTailCap.
+constexpr int kPairTailCap = 4096;
+cudaError_t launch_pair_tail(const SimTailArgs& a, int G, int storage, int n_pairs,
+                             cudaStream_t s);
 
 int cal_persistent_blocks_per_sm(int G);
 cudaError_t launch_cal_persistent(const CalPersistArgs& a, int G, int grid, cudaStream_t s);

@@ -48,13 +48,15 @@ class mpr_options(C.Structure):
                 ("profile", C.c_int32), ("cal_mode", C.c_int32), ("wait_ms", C.c_int32),
                 ("barrier_test", C.c_int32), ("cal_method", C.c_int32), ("n_newton", C.c_int32),
                 ("t_init", C.c_float), ("sim_graph", C.c_int32), ("cal_points", C.c_int32),
-                ("sim_tail", C.c_int32), ("sweep_form", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("sim_tail", C.c_int32), ("sweep_form", C.c_int32), ("pair_tail", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("sim_halfstep_launches", C.c_int64),
                 ("cal_halfstep_launches", C.c_int64), ("sim_halfstep_ms", C.c_double),
-                ("cal_halfstep_ms", C.c_double)]
+                ("cal_halfstep_ms", C.c_double), ("sim_tail_launches", C.c_int64),
+                ("sim_tail_updates", C.c_int64), ("sim_tail_ms", C.c_double)]
 
 
 class mpr_grid3(C.Structure):

@@ -152,6 +152,25 @@ def test_simulate_graph_equals_host_loop():
     assert abs(outs[0][1] - outs[1][1]) <= 0.02 * outs[0][1]
 
 
+def test_pair_tail_equals_host_loop_on_a_batch():
+    """The pair-per-CTA stop tail on a batch of fields (a realization pair's
+    units span every field; each field keeps its own per-realization count of
+    running targeted blocks) gives the per-launch loop's results."""
+    fs = fields()
+    outs = []
+    for tail in (0, 4096):
+        bf = BatchFiller([v for (_, _, v) in fs], [m for (_, m, _) in fs], 8, seed=4, n_max=80,
+                         pair_tail=tail)
+        bf.set_temperatures(np.full(bf.info.nblk, 0.08, np.float32))
+        bf.simulate(5)
+        outs.append((bf.predict()[0], mpr.mpr_get_info(bf.ctx).gap_updates))
+        bf.close()
+    for (z, m, v), a, b in zip(fs, outs[0][0], outs[1][0]):
+        scale = float(z[m == 0].max() - z[m == 0].min())
+        assert (np.abs(a - b) <= 1e-5 * scale)[m != 0].mean() >= 0.98
+    assert abs(outs[0][1] - outs[1][1]) <= max(1, outs[0][1] // 2000)
+
+
 def test_autotune_picks_a_candidate_and_keeps_results():
     z, m = synth.small_problem(96, 80, 0.5, seed=8)
     v = np.where(m != 0, np.nan, z).astype(np.float32)

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2212_01317_gb300 import synth
+from paper_2212_01317_gb300 import mpr, synth
 from paper_2212_01317_gb300.mpr import (GapFiller, MprError, MPR_ENOSAMPLES, MPR_EINVAL, MPR_ESTATE,
                                         MPR_ETIMEOUT)
 
@@ -506,6 +506,86 @@ def test_stop_tail_launch_equals_per_launch_loop(group, R, storage):
         pred, upd = out[tail]
         assert abs(upd - base_upd) <= max(1, base_upd // 2000), (tail, upd, base_upd)
         assert np.mean(np.abs(pred - base_pred)) < 1e-3 * (z.max() - z.min()), tail
+
+
+@pytest.mark.parametrize("group,R,storage", [(8, 20, 0), (2, 2, 0), (8, 12, 1), (2, 14, 2),
+                                               (8, 101, 0)])
+def test_pair_tail_equals_per_launch_loop(group, R, storage):
+    """mpr_simulate runs the sweeps after the running count falls to
+    pair_tail with one CTA per realization pair; the update count (the sum
+    of every (block, realization) pair's stop sweep times its gap sites) and
+    the prediction equal those of the per-launch loop (pair_tail = 0), up to
+    the order of the FP32 energy atomics, which can only move a stop decision
+    at an exact tie. With pair_tail = 4096 nearly every sweep runs in the
+    pair CTAs."""
+    H, W, lb = 72, 64, 8
+    z, m = problem(H, W, 0.55, seed=23, kind="disc")
+    rng = np.random.default_rng(4)
+    T = None
+    out = {}
+    for tail in (0, 4096, 64):
+        gf = make(z, m, lb, seed=77, group=group, storage=storage, n_max=120, pair_tail=tail)
+        if T is None:
+            T = rng.uniform(0.02, 0.5, gf.nblk).astype(np.float32)
+        gf.set_temperatures(T)
+        gf.simulate(R)
+        info = gf.refresh()
+        out[tail] = (gf.predict()[0], info.gap_updates)
+        gf.close()
+    base_pred, base_upd = out[0]
+    for tail in (4096, 64):
+        pred, upd = out[tail]
+        assert abs(upd - base_upd) <= max(1, base_upd // 2000), (tail, upd, base_upd)
+        assert np.mean(np.abs(pred - base_pred)) < 1e-3 * (z.max() - z.min()), tail
+
+
+def test_pair_tail_second_batch_and_sweep_count():
+    """After a batch finished in the pair CTAs the Control is left as the
+    per-launch loop leaves it: a second batch on the same context runs the
+    same way, and the number of sweeps the context reports equals the last
+    stop sweep."""
+    H, W, lb = 48, 56, 8
+    z, m = problem(H, W, 0.5, seed=31)
+    T = np.random.default_rng(6).uniform(0.03, 0.4, (H // lb) * (W // lb)).astype(np.float32)
+    res = []
+    for tail in (0, 4096):
+        gf = make(z, m, lb, seed=12, n_max=90, pair_tail=tail)
+        gf.set_temperatures(T)
+        gf.simulate(6)
+        gf.simulate(6)
+        info = gf.refresh()
+        res.append((gf.predict()[0], info.gap_updates, info.realizations))
+        gf.close()
+    assert res[0][2] == res[1][2] == 12
+    assert abs(res[0][1] - res[1][1]) <= max(1, res[0][1] // 2000)
+    assert np.mean(np.abs(res[0][0] - res[1][0])) < 1e-3 * (z.max() - z.min())
+
+
+def test_profile_keeps_the_stop_tail_apart():
+    """With profile = 1 the stop-tail launch is timed and counted apart from
+    the per-launch half-steps: one tail launch per batch, its updates a part
+    of the batch's (every batch with R realizations runs the same updates with
+    and without the tail), two half-step launches per sweep before it."""
+    H, W, lb = 64, 64, 8
+    z, m = problem(H, W, 0.5, seed=19)
+    T = np.random.default_rng(2).uniform(0.03, 0.4, (H // lb) * (W // lb)).astype(np.float32)
+    got = {}
+    for tail in (0, 4096):
+        gf = make(z, m, lb, seed=21, n_max=100, profile=1, pair_tail=tail)
+        gf.set_temperatures(T)
+        gf.simulate(10)
+        info = gf.refresh()
+        p = mpr.mpr_get_profile(gf.ctx)
+        got[tail] = (info.gap_updates, p)
+        gf.close()
+    upd0, p0 = got[0]
+    upd1, p1 = got[4096]
+    assert p0.sim_tail_launches == 0 and p0.sim_tail_updates == 0 and p0.sim_tail_ms == 0
+    assert p1.sim_tail_launches == 1 and p1.sim_tail_ms > 0
+    assert 0 < p1.sim_tail_updates < upd1
+    assert abs(upd1 - upd0) <= max(1, upd0 // 2000)
+    assert p1.sim_halfstep_launches % 2 == 0 and p1.sim_halfstep_launches < p0.sim_halfstep_launches
+    assert p0.sim_halfstep_ms > 0 and p1.sim_halfstep_ms > 0
 
 
 def test_stop_tail_barrier_wait_is_bounded():
