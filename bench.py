@@ -639,7 +639,9 @@ def run_ours_batch(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": bw.name, "fields": len(bw.masks), "sites": bw.n_sites,
                    "gap_sites": P, "block": bw.block, "realizations": R, "storage": storage,
-                   "form": "batched: every field in one context", "calibration": args.calibration,
+                   "form": "batched: every field in one context",
+                   "calibration": args.calibration if args.calibration == "newton" else
+                   ("bisection" if args.cal_points == 1 else "trisection") + f" x{cal_iters(args)}",
                    "l2": "inputs larger than L2; flushed between timed steps",
                    "parallelism": f"replicas{world}"},
         "gap_filled_mpix_s": mpix, "aae": aae,
