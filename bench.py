@@ -460,7 +460,7 @@ def run_ours(args, world, rank, local):
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-        "kernel": ("k_sweep (realizations)" if dom == "sim"
+        "kernel": ("k_sweep_half / k_sweep (realizations' per-launch half-steps)" if dom == "sim"
                    else ("k_sweep_flat (calibration)" if args.cal_mode == 3
                          else "calibration graph (k_sweep_flat + bookkeeping)")),
         "peak_kind": peak_kind,
@@ -648,7 +648,7 @@ def run_ours_batch(args, world, rank, local):
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": "k_sweep (realizations)", "peak_kind": peak_kind,
+                     "kernel": "k_sweep_half / k_sweep (realizations)", "peak_kind": peak_kind,
                      "bytes_per_gap_update": bpu,
                      "avg_launch_us": 1e3 * sim_ms / sim_launch if sim_launch else None},
         "clocks": clk, "e2e": None, "plain_form": plain,

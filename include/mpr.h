@@ -103,9 +103,11 @@ typedef struct {
                             (default: measured slower than the per-launch loop with
                             programmatic launches; ignored by sim_graph and where cooperative
                             launch is unavailable) */
-    int32_t sweep_form;  /* realizations' half-step: -1 automatic (default: one warp per
-                            realization pair while many pairs run, two, then four as fewer
-                            remain), 0, 1, 2: always one, two or four warps per pair */
+    int32_t sweep_form;  /* realizations' half-step: -1 automatic (default: while many pairs
+                            run, two realization pairs per warp when the blocks hold at most 96
+                            gap sites per colour on average, else one warp per pair; four warps
+                            per pair when few remain), 0, 1, 2: always one, two or four warps
+                            per pair, 3: two pairs per warp (16 lanes each) */
     int32_t pair_tail;   /* running (block, realization) pairs at or below which mpr_simulate runs
                             the rest of its sweep loop as one launch with one CTA per realization
                             pair (each pair's remaining sweeps and stop tests in its CTA, CTA

@@ -109,7 +109,7 @@ struct mpr_ctx {
     size_t blk_cap = 0, lane_cap = 0, work_cap = 0;
     Control* ctl = nullptr;      // device loop state
     Control* h_ctl = nullptr;    // pinned mirror
-    int grid_cache[2][3][3] = {};  // full grid of k_sweep by (G = 2 / 8, storage, form)
+    int grid_cache[2][3][4] = {};  // full grid of k_sweep by (G = 2 / 8, storage, form)
     unsigned long long bound = ~0ull;  // upper bound of the running pairs (from the last read)
     int wide_always = 0;         // autotuned: the wide sweep form for every sweep
     bool energy_dirty = false;
@@ -222,8 +222,8 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.cal_points != 1 && o.cal_points != 2) return fail(ctx, MPR_EINVAL, "cal_points must be 1 or 2");
     if (o.sim_tail < 0) return fail(ctx, MPR_EINVAL, "sim_tail must be >= 0");
     if (o.pair_tail < 0) return fail(ctx, MPR_EINVAL, "pair_tail must be >= 0");
-    if (o.sweep_form < -1 || o.sweep_form > 2)
-        return fail(ctx, MPR_EINVAL, "sweep_form must be -1, 0, 1 or 2");
+    if (o.sweep_form < -1 || o.sweep_form > 3)
+        return fail(ctx, MPR_EINVAL, "sweep_form must be -1, 0, 1, 2 or 3");
     if (o.n_newton < 0 || o.n_newton > 65533) return fail(ctx, MPR_EINVAL, "n_newton in [0, 65533]");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
@@ -339,11 +339,18 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
 // 512 pairs per SM made the batch 0.1 to 0.7 ms slower, one warp throughout
 // ties with this choice; the stop tail costs launches, not passes.)
 constexpr unsigned long long kForm2PairsPerSm = 4;
+// Mean gap entries per block and colour at or below which two realization
+// pairs share a warp (form 3). Measured: 1024^2, l_b = 16, 64 entries:
+// simulate 23.10 -> 21.24 ms; 4096^2, l_b = 32, about 307 entries: 127.3 ->
+// 131.4 ms.
+constexpr double kHalfFormEntries = 96.0;
 
 int sweep_form(mpr_ctx* ctx) {
     if (ctx->opt.sweep_form >= 0) return ctx->opt.sweep_form;
     if (ctx->wide_always) return 2;
-    return ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm ? 2 : 0;
+    if (ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm) return 2;
+    const double per_block = (double)(ctx->n_gap[0] + ctx->n_gap[1]) / (2.0 * ctx->g.nblk);
+    return per_block <= kHalfFormEntries ? 3 : 0;
 }
 
 int sweep_grid(mpr_ctx* ctx, int form) {

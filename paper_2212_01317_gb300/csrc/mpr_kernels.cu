@@ -380,6 +380,32 @@ __global__ void __launch_bounds__(128, 8) k_sweep(SweepArgs a) {
     }
 }
 
+// The same half-step with two units per warp (sweep_item_half), eight per
+// CTA: for short per-block entry lists.
+template <int G, typename S>
+__global__ void __launch_bounds__(128, 8) k_sweep_half(SweepArgs a) {
+    grid_dep_launch();
+    grid_dep_wait();
+    constexpr int NP = G / 2;
+    const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
+    const uint32_t ctr1 = t | (a.ctl->tag << 16);
+    const uint32_t* work = a.work ? a.work + (size_t)(t & 1u) * a.work_stride : nullptr;
+    const int npairs = a.groups * NP;
+    const int warp = threadIdx.x >> 5, half = (threadIdx.x >> 4) & 1;
+    const int it0 = blockIdx.x * 8 + warp * 2 + half;
+    int u = work ? (it0 < (int)a.work_stride ? (int)work[it0] : 0) : it0;
+    const int n_units = work ? (int)a.ctl->n_work[t & 1u] : a.g.nblk * npairs;
+    // The loop bound is the warp's (both halves share the energy shuffles).
+    for (int base = blockIdx.x * 8 + warp * 2; base < n_units; base += gridDim.x * 8) {
+        const int it = base + half;
+        const bool have = it < n_units;
+        if (it != it0) u = have ? (work ? (int)work[it] : it) : 0;
+        const int b = u / npairs, p = u - b * npairs;
+        const int grp = p / NP, q = p - grp * NP;
+        sweep_item_half<G, S>(a, b * a.groups + grp, q, have, ctr1);
+    }
+}
+
 // The last f.ctas CTAs (of blockIdx.y = 0) fold the previous sweep's block
 // energies instead: they touch eacc of the other parity and ecur, which the
 // half-step does not. Eight CTAs per SM (32 registers, a few spilled) keep a
@@ -1121,7 +1147,8 @@ namespace {
 // (splitting the block's entries between them), in 128-thread CTAs.
 template <int G, typename S>
 void sweep_dispatch(const SweepArgs& a, int form, int grid, cudaStream_t s) {
-    if (form == 2) launch_pdl(k_sweep<G, S, 4>, grid, 128, s, a);
+    if (form == 3) launch_pdl(k_sweep_half<G, S>, grid, 128, s, a);
+    else if (form == 2) launch_pdl(k_sweep<G, S, 4>, grid, 128, s, a);
     else if (form == 1) launch_pdl(k_sweep<G, S, 2>, grid, 128, s, a);
     else launch_pdl(k_sweep<G, S, 1>, grid, 128, s, a);
 }
@@ -1129,7 +1156,8 @@ void sweep_dispatch(const SweepArgs& a, int form, int grid, cudaStream_t s) {
 template <int G, typename S>
 int sweep_occupancy(int form) {
     int n = 0;
-    if (form == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<G, S, 4>, 128, 0);
+    if (form == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_half<G, S>, 128, 0);
+    else if (form == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<G, S, 4>, 128, 0);
     else if (form == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<G, S, 2>, 128, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<G, S, 1>, 128, 0);
     return n > 0 ? n : 1;
@@ -1155,7 +1183,7 @@ int sweep_blocks_per_sm(int G, int storage, int form) {
 
 int sweep_items_per_cta(int G, int form) {
     (void)G;
-    return 4 >> form;
+    return form == 3 ? 8 : 4 >> form;
 }
 
 void launch_energy(const SweepArgs& a, int G, int storage, int n_sm, cudaStream_t s) {

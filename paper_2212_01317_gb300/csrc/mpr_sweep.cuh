@@ -267,6 +267,92 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
     flush_pair(ea - (size_t)a.g.nbx * a.Rp, au0, au1);
 }
 
+// Energy flush of one half-warp's unit: sums over its 16 lanes, then its
+// lane 0 adds them (act: the half has a running unit). Every lane of the warp
+// calls it.
+__device__ __forceinline__ void flush_pair_half(float* ea, float v0, float v1, bool act) {
+    if (!__any_sync(0xffffffffu, v0 != 0.0f || v1 != 0.0f)) return;
+#pragma unroll
+    for (int s = 8; s > 0; s >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, s);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, s);
+    }
+    if ((threadIdx.x & 15) != 0 || !act) return;
+    if (v0 != 0.0f) atomicAdd(ea, v0);
+    if (v1 != 0.0f) atomicAdd(ea + 1, v1);
+}
+
+// Two units per warp: lanes 0-15 take one (block, realization pair) unit,
+// lanes 16-31 another, each half 16 gap entries at a time. For blocks whose
+// colour holds few entries (about 64 at l_b = 16 and half the sites missing)
+// the last, partial pass wastes fewer lanes, and the warp's per-unit work
+// (bounds, flags, energy sums) serves two units. have: this half has a unit
+// (item, pair q within its lane group); every lane of the warp calls this.
+template <int G, typename S>
+__device__ __forceinline__ void sweep_item_half(const SweepArgs& a, int item, int q, bool have,
+                                                uint32_t ctr1) {
+    const int hl = threadIdx.x & 15;
+    const size_t plane = (size_t)a.g.H * a.g.Wh;
+    const int c = a.colour, co = c ^ 1;
+    const int b = have ? item / a.groups : 0, grp = have ? item - b * a.groups : 0;
+    int e0 = 0, e1 = 0;
+    bool run0 = false, run1 = false;
+    const int rl = grp * G + 2 * q;
+    if (have) {
+        e0 = a.start[b];
+        e1 = a.start[b + 1];
+        pair_running(a, b, rl, run0, run1);
+    }
+    const bool act = have && e0 < e1 && (run0 || run1);
+    float ao0 = 0.f, ao1 = 0.f, al0 = 0.f, al1 = 0.f, au0 = 0.f, au1 = 0.f;
+    if (act) {
+        S* own = static_cast<S*>(a.ang) + (size_t)(grp * 2 + c) * plane * G + 2 * q;
+        const S* oth = static_cast<const S*>(a.ang) + (size_t)(grp * 2 + co) * plane * G + 2 * q;
+        const float beta = a.beta[b];
+        const float J = a.m.J;
+        const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
+        const int sl = slice_of(a.sl, b);
+        const int4 rc = slice_rect(a.sl, sl);
+        const uint32_t key1 = slice_key1(a.sl, sl);
+        int e = e0 + hl;
+        uint2 nx = e < e1 ? a.list[e] : make_uint2(0u, 0u);
+        for (; e < e1; e += 16) {
+            const uint2 en = nx;
+            if (e + 16 < e1) nx = a.list[e + 16];
+            const int y = en.x >> 16, x = en.x & 0xffff;
+            const uint32_t f = en.y;
+            const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
+            uint32_t w[4];
+            philox4x32_10(local_index(rc, y, x), ctr1, rpair, 0u, a.rng.key0, key1, w);
+            const float2 ph = Store<S>::load2(own + (size_t)hs * G);
+            float nc0[4], ns0[4], nc1[4], ns1[4];
+            neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
+            const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
+            const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
+            const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
+            const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
+            const float bt = a.beta_site ? a.beta_site[(size_t)y * a.g.W + x] : beta;
+            float2 out = ph;
+            if (run0) {
+                const SiteNew n = site_update<S>(ph.x, C0, S0, u01(w[0]), u01(w[1]), bt, a.m);
+                out.x = n.phi;
+                add_energy(n, f, C0, S0, nc0, ns0, J, ao0, al0, au0);
+            }
+            if (run1) {
+                const SiteNew n = site_update<S>(ph.y, C1, S1, u01(w[2]), u01(w[3]), bt, a.m);
+                out.y = n.phi;
+                add_energy(n, f, C1, S1, nc1, ns1, J, ao1, al1, au1);
+            }
+            Store<S>::store2(own + (size_t)hs * G, out);
+        }
+    }
+    if (!a.energy) return;
+    float* ea = a.eacc + (size_t)b * a.Rp + rl;
+    flush_pair_half(ea, ao0, ao1, act);
+    flush_pair_half(ea - a.Rp, al0, al1, act);
+    flush_pair_half(ea - (size_t)a.g.nbx * a.Rp, au0, au1, act);
+}
+
 // One half-step over the whole list of one colour, flat: one thread per
 // (gap entry, realization pair), 32 / (G/2) entries per warp, one lane group
 // per blockIdx.y (a CTA never mixes lane groups). For calibration, where every

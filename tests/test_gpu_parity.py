@@ -610,16 +610,16 @@ def test_stop_tail_barrier_wait_is_bounded():
 # ---------------------------------------------------------- sweep forms --
 @pytest.mark.parametrize("group,R", [(8, 13), (2, 2)])
 def test_sweep_forms_agree(group, R):
-    """The three forms of the realizations' half-step (one, two or four
-    warps per realization pair) update every site with the same arithmetic
-    and random numbers; only the order of the FP32 energy sums differs. After
-    a few sweeps the stop sweeps agree and, when all of them do, the states
-    are bit-identical."""
+    """The four forms of the realizations' half-step (one, two or four
+    warps per realization pair, or two pairs per warp) update every site with
+    the same arithmetic and random numbers; only the order of the FP32 energy
+    sums differs. After a few sweeps the stop sweeps agree and, when all of
+    them do, the states are bit-identical."""
     H, W, lb = 56, 48, 8
     z, m = problem(H, W, 0.6, seed=41, kind="disc")
     T = np.random.default_rng(9).uniform(0.03, 0.4, (H // lb) * (W // lb)).astype(np.float32)
     res = []
-    for form in (0, 1, 2):
+    for form in (0, 1, 2, 3):
         gf = make(z, m, lb, seed=5, group=group, sweep_form=form, n_max=40)
         gf.set_temperatures(T)
         gf.sim_begin(R)
