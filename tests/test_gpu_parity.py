@@ -608,19 +608,19 @@ def test_stop_tail_barrier_wait_is_bounded():
 
 
 # ---------------------------------------------------------- sweep forms --
-@pytest.mark.parametrize("group,R", [(8, 13), (2, 2)])
-def test_sweep_forms_agree(group, R):
+@pytest.mark.parametrize("group,R,storage", [(8, 13, 0), (2, 2, 0), (8, 13, 1), (8, 9, 2)])
+def test_sweep_forms_agree(group, R, storage):
     """The four forms of the realizations' half-step (one, two or four
     warps per realization pair, or two pairs per warp) update every site with
     the same arithmetic and random numbers; only the order of the FP32 energy
     sums differs. After a few sweeps the stop sweeps agree and, when all of
-    them do, the states are bit-identical."""
+    them do, the states are bit-identical; in the FP32, BF16 and FP16 state."""
     H, W, lb = 56, 48, 8
     z, m = problem(H, W, 0.6, seed=41, kind="disc")
     T = np.random.default_rng(9).uniform(0.03, 0.4, (H // lb) * (W // lb)).astype(np.float32)
     res = []
     for form in (0, 1, 2, 3):
-        gf = make(z, m, lb, seed=5, group=group, sweep_form=form, n_max=40)
+        gf = make(z, m, lb, seed=5, group=group, sweep_form=form, n_max=40, storage=storage)
         gf.set_temperatures(T)
         gf.sim_begin(R)
         gf.sim_sweep(12)
