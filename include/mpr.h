@@ -285,7 +285,13 @@ mpr_status mpr_get_site_temperatures(mpr_ctx* ctx, float* T_site);
  * (Sec. 2.2.2 block temperatures, Sec. 3.3.3 block-mean start, Sec. 3.4 stop)
  * and adds their final states to the running mean. Realization indices
  * continue from earlier calls, so calling it twice with R equals one call
- * with 2R. Errors: ESTATE (no temperatures yet), EINVAL (n < 1), ENOMEM, ECUDA. */
+ * with 2R. The sweeps run as a kernel per phase over the worklist of running
+ * (block, realization pair) units; once at most pair_tail (block, realization)
+ * pairs run, the rest runs in one launch with one CTA per realization pair
+ * (options sim_graph, sim_tail and sweep_form choose other schedules; every
+ * schedule computes the same states up to the order of the FP32 energy sums).
+ * Errors: ESTATE (no temperatures yet), EINVAL (n < 1), ENOMEM, ECUDA,
+ * ETIMEOUT (sim_tail only: a grid-barrier wait gave up). */
 mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n_realizations);
 
 /* Conditional mean back-transformed (Sec. 2.1, Sec. 3.2): out[H*W] (host or
