@@ -405,6 +405,24 @@ mpr_status energy_pass(mpr_ctx* ctx) {
     return MPR_OK;
 }
 
+// E_b(0) when every realization starts from the same state (the block-mean
+// start, Sec. 3.3.3): the bond sums of the first lane group only, copied to
+// the other lanes.
+mpr_status energy_pass_shared_start(mpr_ctx* ctx) {
+    launch_ecur_reset(ctx->g.nblk, ctx->Rp, ctx->Es, ctx->ecur, ctx->eacc, ctx->s);
+    CKL();
+    for (int c = 0; c < 2; ++c) {
+        SweepArgs a = sweep_args(ctx, c, false);
+        a.R = ctx->Rp;
+        a.groups = 1;
+        launch_energy(a, ctx->G, ctx->storage, ctx->n_sm, ctx->s);
+        CKL();
+    }
+    launch_ecur_broadcast(ctx->g.nblk, ctx->Rp, ctx->G, ctx->ecur, ctx->s);
+    CKL();
+    return MPR_OK;
+}
+
 // After a stream synchronisation: fold the recorded pairs into the totals.
 void collect_events(mpr_ctx* ctx) {
     for (int which = 0; which < 2; ++which) {
@@ -1417,7 +1435,8 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     CK(cudaMemsetAsync(ctx->tcount, 0, (size_t)ctx->Rp * ctx->n_slices * sizeof(int32_t), ctx->s));
     // E_b(0): bond energies of the initial state (no moves), t = 0 stops,
     // worklist of the first sweep.
-    TRY(energy_pass(ctx));
+    if (ctx->opt.init == MPR_INIT_RANDOM || ctx->groups == 1) TRY(energy_pass(ctx));
+    else TRY(energy_pass_shared_start(ctx));
     launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->d_of_block, ctx->es, ctx->inb, ctx->Nsp, ctx->ngap,
                      ctx->ecur,
                      ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);

@@ -1213,6 +1213,21 @@ void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s
     else launch_pdl(k_sweep_flat<8>, grid, kFlatThreads, s, a, n_list, f);
 }
 
+// Lanes G.. Rp-1 of every block take the E_b of lane r mod G (all lanes hold
+// the same state).
+__global__ void k_ecur_broadcast(int nblk, int Rp, int G, double* __restrict__ ecur) {
+    const int64_t n = (int64_t)nblk * Rp;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t % Rp);
+        if (r >= G) ecur[t] = ecur[t - r + r % G];
+    }
+}
+
+void launch_ecur_broadcast(int nblk, int Rp, int G, double* ecur, cudaStream_t s) {
+    k_ecur_broadcast<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, G, ecur);
+}
+
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
                        cudaStream_t s) {
     k_ecur_reset<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, Es, ecur, eacc);
