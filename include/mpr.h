@@ -396,13 +396,18 @@ mpr_status mpr_block_energy(mpr_ctx* ctx, int32_t r, double* E);
  * library keeps on every device that loads it, until the process exits.
  *   mask, values: H*W device arrays (as mpr_create); Es, Nsp, Nb, mean_angle,
  *   n_gap: nblk device arrays (as mpr_get_block_stats); zrange: 2 device
- *   doubles (z_min, z_max; both 0 without samples). Host pointers are
- *   rejected.
+ *   doubles (z_min, z_max; both 0 without samples). Every pointer must be
+ *   device memory of the current device, or managed memory: host pointers
+ *   and device memory of another GPU are rejected before anything runs.
  *   The grid may have at most MPR_NOALLOC_MAX_BLOCKS blocks; larger grids
  *   return MPR_EINVAL without touching the outputs.
  *   Work is queued on cuda_stream (NULL = default stream) and not awaited.
- *   The first call on a device looks up the scratch array's device address;
- *   make that first call before any stream capture.
+ *   Every call looks up the scratch array's device address (a lookup that
+ *   allocates nothing, and stays right after a device reset). The module that
+ *   holds the array may be loaded onto a device only at its first use (lazy
+ *   module loading), and loading it takes device memory: make one warm-up
+ *   call on each device at start-up, before reserving the pool and before
+ *   any stream capture, so that no later call needs memory.
  *   All calls share the one scratch array: calls that may overlap on the GPU
  *   (different streams, or different host threads) race and must be
  *   serialised by the caller.

@@ -7,10 +7,8 @@ sample energy e_s,b. ``BlockEnergy.apply(beta, handle, ...)`` runs the
 chains at ``beta`` (mpr_energy_moments) and returns y; its backward is the
 library's vector-Jacobian-product kernel (mpr_energy_vjp), built on the
 fluctuation identity d y_a / d beta_b = -Cov(E_a, E_b) / N_a with the
-covariances measured by the same run. ``newton_calibrate`` is a plain
-diagonal Newton loop on top of it, for callers that want to drive the
-calibration themselves (the library's own is mpr_calibrate with
-cal_method = 1).
+covariances measured by the same run. The Newton calibration built on the
+same moments runs inside the library: mpr_calibrate with cal_method = 1.
 """
 from __future__ import annotations
 
@@ -49,17 +47,3 @@ def block_moments(handle, beta, n_eq: int, n_meas: int, tag: int, restart: bool)
     outs = [torch.empty(b.numel(), dtype=torch.float64, device=b.device) for _ in range(4)]
     mpr.mpr_energy_moments(handle, b, n_eq, n_meas, tag, restart, *outs)
     return outs
-
-
-def newton_calibrate(handle, e_s, n_b, beta0, iters: int = 6, n_eq: int = 25, n_meas: int = 20):
-    """Diagonal Newton on beta: beta <- beta + (y - e_s) N_b / Var(E_b), with the
-    step capped to a factor of 4 either way (no bracket; the library's
-    mpr_calibrate with cal_method = 1 adds the bisection safeguard and the
-    median for blocks without sample bonds). e_s, n_b: float64 CUDA tensors."""
-    beta = beta0.detach().to(torch.float32).clone()
-    for k in range(iters):
-        y, var, _, _ = block_moments(handle, beta, n_eq, n_meas, 1 + k, k == 0)
-        step = torch.where(var > 0, (y - e_s) * n_b / var.clamp_min(1e-300), torch.zeros_like(y))
-        new = (beta.double() + step).clamp(beta.double() / 4, beta.double() * 4)
-        beta = new.to(torch.float32)
-    return beta

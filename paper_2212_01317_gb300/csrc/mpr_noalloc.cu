@@ -12,11 +12,11 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "mpr.h"
 #include "mpr_internal.h"
 #include "mpr_launch.h"
+#include "mpr_ptrcheck.h"
 
 using namespace mpr;
 
@@ -50,25 +50,16 @@ Scratch carve(unsigned char* base) {
     return s;
 }
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device; looked up once
-// per device (the host-side symbol is only a stand-in, not a device address).
+// Device address of the scratch array on the current device (the host-side
+// symbol is only a stand-in, not a device address). It is looked up on every
+// call: the lookup allocates nothing, and an address kept from an earlier call
+// would dangle after the device was reset (cudaDeviceReset) and its context
+// re-created.
 cudaError_t scratch_address(unsigned char** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_addr[dev];
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 
@@ -189,13 +180,14 @@ __global__ void k_na_finalize(int nblk, Scratch sc, float* __restrict__ mean_ang
     }
 }
 
-bool on_device(const void* p) {
+// The pointer is device memory of `device` (the current one) or managed memory.
+bool on_device(const void* p, int device) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return noalloc_pointer_ok(at.type, at.device, device);
 }
 
 }  // namespace
@@ -219,9 +211,14 @@ extern "C" mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_
     g.nby = (H + lb - 1) / lb;
     if ((int64_t)g.nbx * g.nby > kMaxBlocks) return MPR_EINVAL;  // beyond the scratch array
     g.nblk = g.nbx * g.nby;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return MPR_ECUDA;
+    }
     const void* ptrs[] = {mask, values, Es, Nsp, Nb, mean_angle, n_gap, zrange};
     for (const void* p : ptrs)
-        if (!on_device(p)) return MPR_EINVAL;
+        if (!on_device(p, device)) return MPR_EINVAL;
     unsigned char* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return MPR_ECUDA;
     const Scratch sc = carve(base);

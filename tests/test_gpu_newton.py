@@ -173,7 +173,7 @@ def test_newton_step_is_the_update_rule(torch):
 
 
 def test_autograd_function(torch):
-    from paper_2212_01317_gb300.autograd import BlockEnergy, block_moments, newton_calibrate
+    from paper_2212_01317_gb300.autograd import BlockEnergy, block_moments
     H, W, lb = 32, 40, 8
     z, m = synth.small_problem(H, W, 0.5, seed=4)
     gf = make(z, m, lb, seed=5, cal_chains=2)
@@ -189,17 +189,19 @@ def test_autograd_function(torch):
     mpr.mpr_energy_vjp(gf.ctx, w.cpu().numpy(), g)
     np.testing.assert_allclose(beta.grad.cpu().numpy(), g.astype(np.float32), rtol=1e-4,
                                atol=1e-6 * np.abs(g).max())
-    # the plain Newton loop moves the energies towards their targets
+    # the library's Newton calibration (mpr_calibrate, cal_method = 1) moves
+    # the chains' energies, measured through the autograd module, towards
+    # their targets
     Es, Nsp, Nb, _, _ = gf.block_stats()
     t = Nsp > 0
-    es = torch.tensor(np.where(t, Es / np.maximum(Nsp, 1), 0.0), device="cuda")
-    nb = torch.tensor(Nb.astype(np.float64), device="cuda")
-    b1 = newton_calibrate(gf.ctx, es, nb, torch.full((gf.nblk,), 20.0, device="cuda"), iters=5,
-                          n_eq=10, n_meas=20)
+    e = np.where(t, Es / np.maximum(Nsp, 1), 0.0)
+    gn = make(z, m, lb, seed=5, cal_chains=2, cal_method=1, n_newton=5, n_eq=10, n_meas=20,
+              t_init=0.05)
+    b1 = torch.tensor(1.0 / gn.calibrate(), dtype=torch.float32, device="cuda")
+    gn.close()
     y_end = block_moments(gf.ctx, b1, 10, 40, 9, True)[0].cpu().numpy()
     y_start = block_moments(gf.ctx, torch.full((gf.nblk,), 20.0, device="cuda"), 10, 40, 9,
                             True)[0].cpu().numpy()
-    e = es.cpu().numpy()
     assert np.mean(np.abs(y_end - e)[t]) < 0.5 * np.mean(np.abs(y_start - e)[t])
     gf.close()
 
