@@ -30,6 +30,7 @@ import numpy as np
 __all__ = [
     "grf", "grf_nonstationary", "mask_random", "mask_discs", "Workload",
     "workload", "WORKLOADS", "BatchWorkload", "batch_workload", "BATCH_WORKLOADS",
+    "batch_sides", "batch_field", "batch_name",
 ]
 
 
@@ -275,25 +276,69 @@ class BatchWorkload:
         return int(sum(m.size for m in self.masks))
 
 
-def _slices(n: int, seed: int) -> BatchWorkload:
-    """n square slices, side round(exp(U(ln 256, ln 2048))), each its own seeded
-    stationary GRF (xi ~ U(4, 32)), its own gap fraction p ~ U(0.1, 0.9), a
-    uniformly random or disc mask with probability 1/2 each; l_b = 32, R = 50."""
+def _slice_params(n: int, seed: int) -> list:
+    """Per-slice recipe of _slices: (side, xi, p, disc, field seed) for each of
+    the n slices, drawn in order from one seeded generator (cheap: no field is
+    generated)."""
     rng = np.random.default_rng(seed)
-    truths, masks, sides = [], [], []
+    out = []
     for k in range(n):
         L = int(round(math.exp(rng.uniform(math.log(256), math.log(2048)))))
         xi = float(rng.uniform(4.0, 32.0))
         p = float(rng.uniform(0.1, 0.9))
         disc = bool(rng.uniform() < 0.5)
-        s = seed * 1000003 + 17 * k
-        truths.append(grf(L, L, xi, s).astype(np.float32))
-        masks.append(mask_discs(L, L, p, s + 1) if disc else mask_random(L, L, p, s + 1))
-        sides.append(L)
-    return BatchWorkload(f"slices{n}_256-2048_xi4-32_p10-90_lb32_R50", truths, masks, 32, 50,
+        out.append((L, xi, p, disc, seed * 1000003 + 17 * k))
+    return out
+
+
+def _slice_field(prm) -> tuple[np.ndarray, np.ndarray]:
+    L, xi, p, disc, s = prm
+    z = grf(L, L, xi, s).astype(np.float32)
+    m = mask_discs(L, L, p, s + 1) if disc else mask_random(L, L, p, s + 1)
+    return z, m
+
+
+SLICES_BLOCK = 32        # temperature block side of the batch workloads
+SLICES_R = 50            # realizations per field of the batch workloads
+
+
+def _slices_name(n: int) -> str:
+    return f"slices{n}_256-2048_xi4-32_p10-90_lb{SLICES_BLOCK}_R{SLICES_R}"
+
+
+def _slices(n: int, seed: int) -> BatchWorkload:
+    """n square slices, side round(exp(U(ln 256, ln 2048))), each its own seeded
+    stationary GRF (xi ~ U(4, 32)), its own gap fraction p ~ U(0.1, 0.9), a
+    uniformly random or disc mask with probability 1/2 each; l_b = 32, R = 50."""
+    truths, masks, sides = [], [], []
+    for prm in _slice_params(n, seed):
+        z, m = _slice_field(prm)
+        truths.append(z)
+        masks.append(m)
+        sides.append(prm[0])
+    return BatchWorkload(_slices_name(n), truths, masks, SLICES_BLOCK, SLICES_R,
                          meta={"slices": n, "sides": [min(sides), max(sides)],
                                "sites": int(sum(x * x for x in sides))})
 
+
+def batch_sides(name: str, seed: int = 0) -> list:
+    """Field sides of a batch workload, without generating its fields."""
+    n = _BATCH_SIZES[name]
+    return [prm[0] for prm in _slice_params(n, seed)]
+
+
+def batch_field(name: str, k: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """(truth, mask) of field k of a batch workload, generated alone (the same
+    arrays batch_workload(name, seed) holds at position k)."""
+    n = _BATCH_SIZES[name]
+    return _slice_field(_slice_params(n, seed)[k])
+
+
+def batch_name(name: str) -> str:
+    return _slices_name(_BATCH_SIZES[name])
+
+
+_BATCH_SIZES = {"slices256": 256, "slices32": 32}
 
 BATCH_WORKLOADS = {
     "slices256": lambda seed=0: _slices(256, seed),

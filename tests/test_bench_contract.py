@@ -64,3 +64,21 @@ def test_reference_arm_prints_the_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == pytest.approx(d["value"]) and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_batch_reference_arm_runs_our_config():
+    """On a batch workload the reference arm (the oracle on the batch's
+    smallest field) prints the config dict our own arm prints, so that the two
+    lines describe one workload."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "slices32", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    args = bench.parse_args_for_tests(["--workload", "slices32"])
+    assert d["config"] == bench.batch_config(args, 1)
+    assert d["config"]["storage"] == "bf16" and d["config"]["fields"] == 32
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == pytest.approx(d["value"])
+    assert "smallest" in d["cpu_baseline"]["sample"]
