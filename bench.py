@@ -72,6 +72,8 @@ def parse(argv=None):
                     help="steps of the end-to-end measurement (host buffers, copies timed)")
     ap.add_argument("--sim-graph", type=int, default=0, choices=[0, 1],
                     help="batch workloads: the sweep loop as one CUDA graph")
+    ap.add_argument("--sweep-form", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
+                    help="realizations' half-step form (-1 automatic; 4 the staged half-step)")
     ap.add_argument("--calibration", default="bisection", choices=["bisection", "newton"],
                     help="per-block temperature fit: bisection (the plain form) or safeguarded "
                          "Newton steps from the fluctuation identity")
@@ -405,6 +407,7 @@ def run_ours(args, world, rank, local):
                                        storage=STORAGE[storage], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
+                                       sweep_form=args.sweep_form,
                                        cuda_stream=stream.cuda_stream)
 
     sim_ev = []
@@ -687,7 +690,8 @@ def run_ours_batch(args, world, rank, local):
                                        storage=STORAGE[st], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
-                                       sim_graph=args.sim_graph, cuda_stream=stream.cuda_stream)
+                                       sim_graph=args.sim_graph, sweep_form=args.sweep_form,
+                                       cuda_stream=stream.cuda_stream)
 
     def timed_event():
         return torch.cuda.Event(enable_timing=True)

@@ -107,7 +107,11 @@ typedef struct {
                             run, two realization pairs per warp when the blocks hold at most 96
                             gap sites per colour on average, else one warp per pair; four warps
                             per pair when few remain), 0, 1, 2: always one, two or four warps
-                            per pair, 3: two pairs per warp (16 lanes each) */
+                            per pair, 3: two pairs per warp (16 lanes each), 4: the staged
+                            half-step (the other colour's (cos, sin) of q phi staged in shared
+                            memory per tile of at most 16 x 32 sites, one thread per gap site
+                            and realization pair; batches of lane groups of eight only, other
+                            batches take form 0) */
     int32_t pair_tail;   /* running (block, realization) pairs at or below which mpr_simulate runs
                             the rest of its sweep loop as one launch with one CTA per realization
                             pair (each pair's remaining sweeps and stop tests in its CTA, CTA

@@ -110,6 +110,13 @@ struct mpr_ctx {
     Control* ctl = nullptr;      // device loop state
     Control* h_ctl = nullptr;    // pinned mirror
     int grid_cache[2][3][4] = {};  // full grid of k_sweep by (G = 2 / 8, storage, form)
+    // The staged half-step's tiles (built at the first batch that uses them).
+    Tiles tiles{};
+    float* stab = nullptr;         // [2][H][Wh] staging table
+    int32_t* tstart[2] = {nullptr, nullptr};
+    uint2* tlist[2] = {nullptr, nullptr};
+    int tile_grid = 0;             // resident CTAs of the staged kernel (by storage at build)
+    int tile_grid_storage = -1;
     unsigned long long bound = ~0ull;  // upper bound of the running pairs (from the last read)
     int wide_always = 0;         // autotuned: the wide sweep form for every sweep
     bool energy_dirty = false;
@@ -222,8 +229,8 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.cal_points != 1 && o.cal_points != 2) return fail(ctx, MPR_EINVAL, "cal_points must be 1 or 2");
     if (o.sim_tail < 0) return fail(ctx, MPR_EINVAL, "sim_tail must be >= 0");
     if (o.pair_tail < 0) return fail(ctx, MPR_EINVAL, "pair_tail must be >= 0");
-    if (o.sweep_form < -1 || o.sweep_form > 3)
-        return fail(ctx, MPR_EINVAL, "sweep_form must be -1, 0, 1, 2 or 3");
+    if (o.sweep_form < -1 || o.sweep_form > 4)
+        return fail(ctx, MPR_EINVAL, "sweep_form must be -1, 0, 1, 2, 3 or 4");
     if (o.n_newton < 0 || o.n_newton > 65533) return fail(ctx, MPR_EINVAL, "n_newton in [0, 65533]");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
@@ -330,8 +337,58 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
     a.groups = ctx->groups;
     a.r_base = ctx->r_even;
     a.energy = 1;
+    if (ctx->tiles.n > 0) {
+        a.tl = ctx->tiles;
+        a.tl.start = ctx->tstart[colour];
+        a.tl.list = ctx->tlist[colour];
+        a.tl.stab = ctx->stab;
+    }
     return a;
 }
+
+// The staged half-step (form 4) needs lane groups of eight and its tiles.
+bool tile_form_ok(const mpr_ctx* ctx) { return ctx->G == 8 && ctx->tiles.n > 0; }
+
+// The options ask for the staged half-step.
+bool tiles_wanted(const mpr_ctx* ctx) { return ctx->opt.sweep_form == 4; }
+
+// Tiles, tile-major lists and staging table of the staged half-step, built
+// once per context.
+mpr_status ensure_tiles(mpr_ctx* ctx) {
+    if (ctx->tiles.n > 0) return MPR_OK;
+    const Geom& g = ctx->g;
+    Tiles t = tile_shape(g);
+    const size_t plane = (size_t)g.H * g.Wh;
+    int32_t* cnt[2] = {nullptr, nullptr};
+    TRY(dalloc(ctx, &ctx->stab, 2 * plane));
+    for (int c = 0; c < 2; ++c) {
+        TRY(dalloc(ctx, &ctx->tstart[c], (size_t)t.n + 1));
+        TRY(dalloc(ctx, &ctx->tlist[c], (size_t)std::max<int64_t>(1, ctx->n_gap[c])));
+        TRY(dalloc(ctx, &cnt[c], (size_t)t.n));
+    }
+    launch_stage_table(g, ctx->mask, ctx->dang, ctx->stab, ctx->s);
+    launch_tile_count(g, t, ctx->d_of_block, ctx->mask, cnt[0], cnt[1], ctx->s);
+    launch_scan(cnt[0], t.n, ctx->tstart[0], ctx->s);
+    launch_scan(cnt[1], t.n, ctx->tstart[1], ctx->s);
+    launch_tile_lists(g, t, ctx->d_of_block, ctx->mask, ctx->tstart[0], ctx->tstart[1],
+                      ctx->tlist[0], ctx->tlist[1], ctx->s);
+    ctx->launches += 5;
+    CKL();
+    dfree(ctx, cnt[0]);
+    dfree(ctx, cnt[1]);
+    ctx->tiles = t;
+    return MPR_OK;
+}
+
+int tile_grid(mpr_ctx* ctx) {
+    if (ctx->tile_grid_storage != ctx->storage) {
+        ctx->tile_grid = ctx->n_sm * tile_blocks_per_sm(ctx->storage);
+        ctx->tile_grid_storage = ctx->storage;
+    }
+    const int64_t items = (int64_t)ctx->tiles.n * ctx->groups;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->tile_grid, items));
+}
+
 
 // Running pairs per SM below which the half-step takes four warps per
 // realization pair (form 2), and a grid no larger than the running pairs can
@@ -346,6 +403,7 @@ constexpr unsigned long long kForm2PairsPerSm = 4;
 constexpr double kHalfFormEntries = 96.0;
 
 int sweep_form(mpr_ctx* ctx) {
+    if (ctx->opt.sweep_form == 4) return tile_form_ok(ctx) ? 4 : 0;
     if (ctx->opt.sweep_form >= 0) return ctx->opt.sweep_form;
     if (ctx->wide_always) return 2;
     if (ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm) return 2;
@@ -360,6 +418,15 @@ int sweep_grid(mpr_ctx* ctx, int form) {
     // (bound is ~0 while unknown: round up without overflowing)
     const unsigned long long need = ctx->bound / ipc + (ctx->bound % ipc != 0 ? 1 : 0);
     return (int)std::max<unsigned long long>(1, std::min<unsigned long long>(full, need));
+}
+
+// One realization half-step of the batch in sweep form `form` (4: staged).
+void launch_halfstep(mpr_ctx* ctx, const SweepArgs& a, int form) {
+    if (form == 4) {
+        launch_sweep_tile(a, ctx->storage, tile_grid(ctx), ctx->s);
+        return;
+    }
+    launch_sweep(a, ctx->G, ctx->storage, form, sweep_grid(ctx, form), ctx->s);
 }
 
 // Grid of the stop kernels: a thread per (item, lane) or per item, at most
@@ -501,7 +568,7 @@ mpr_status sweep_once(mpr_ctx* ctx) {
         const int form = sweep_form(ctx);
         SweepArgs a = sweep_args(ctx, c, true);
         a.t_fixed = t_known > 0 ? t_known : 0;
-        launch_sweep(a, ctx->G, ctx->storage, form, sweep_grid(ctx, form), ctx->s);
+        launch_halfstep(ctx, a, form);
         CKL();
         ++ctx->sim_halfstep_launches;
     }
@@ -1421,6 +1488,7 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     ctx->r_off = (int)(r_base & 1);
     ctx->r_even = (uint32_t)(r_base - ctx->r_off);
     TRY(ensure_batch(ctx, n + ctx->r_off, ctx->opt.group, ctx->opt.storage));
+    if (ctx->G == 8 && tiles_wanted(ctx)) TRY(ensure_tiles(ctx));
     ctx->R = n;
     ctx->chains_valid = false;
     ctx->t = 0;
@@ -1780,7 +1848,10 @@ mpr_status mpr_halfstep(mpr_ctx* ctx, int32_t colour, int32_t t, int32_t tag) {
     a.energy = 0;
     const unsigned long long bound = ctx->bound;
     ctx->bound = ~0ull;
-    launch_sweep(a, ctx->G, ctx->storage, 0, sweep_grid(ctx, 0), ctx->s);
+    // The form the options ask for (the automatic choice: one warp per pair).
+    int form = ctx->opt.sweep_form >= 0 ? ctx->opt.sweep_form : 0;
+    if (form == 4 && !tile_form_ok(ctx)) form = 0;
+    launch_halfstep(ctx, a, form);
     ctx->bound = bound;
     CKL();
     CK(cudaStreamSynchronize(ctx->s));

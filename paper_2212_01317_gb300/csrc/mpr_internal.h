@@ -108,6 +108,27 @@ struct Control {
     unsigned long long n_running_acc;  // the same, being counted by the stop test in progress
 };
 
+// Tiles of the staged half-step: every block is cut into tiles of th rows and
+// tw columns (the last ones of a block partial), numbered block-major, then
+// row-major within the block. Each colour has its own list of gap entries in
+// tile order (within a tile: the block-edge entries first, then row-major)
+// with segment starts per tile.
+constexpr int kTileRows = 16;          // th = min(l_b, kTileRows)
+constexpr int kTileCols = 32;          // tw = min(l_b, kTileCols)
+constexpr int kTileStageRows = kTileRows + 2;
+constexpr int kTileStageCols = kTileCols / 2 + 2;   // staged half-columns, at most
+
+struct Tiles {
+    int th, tw;                // tile rows / columns in sites
+    int tpx, tpy;              // tiles per block across / down
+    int n;                     // tiles of the canvas: nblk * tpx * tpy
+    const int32_t* start;      // [n + 1] segments of this colour's tile list
+    const uint2* list;         // gap entries of this colour, tile-major
+    const float* stab;         // [2][H][Wh] staging table: the sample angle at a
+                               // sample site, NaN at a gap site, -1 at an absent
+                               // site and at the padding half-site of odd widths
+};
+
 // One half-step over the gap sites of one colour, for every running
 // (block, realization pair) unit of the worklist.
 struct SweepArgs {
@@ -134,6 +155,7 @@ struct SweepArgs {
     uint32_t r_base;          // global index of lane 0 (even)
     int energy;               // 1: accumulate energy increments of the moves
     int t_fixed;              // > 0: sweep index of this launch (else read from ctl)
+    Tiles tl;                 // the staged half-step's tiles (tl.n == 0: not built)
 };
 
 // Per-(block, realization) bookkeeping of the stop test (Sec. 3.4 reading):

@@ -15,6 +15,7 @@
 #include "mpr_device.cuh"
 #include "mpr_internal.h"
 #include "mpr_launch.h"
+#include "mpr_lists.cuh"
 #include "mpr_sweep.cuh"
 
 namespace mpr {
@@ -238,48 +239,26 @@ __global__ void k_build_lists(Geom g, const int32_t* __restrict__ of_block,
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= g.nblk) return;
-    const int b = warp;
-    const int by = b / g.nbx, bx = b % g.nbx;
-    const int y0 = by * g.lb, x0 = bx * g.lb;
-    const int y1 = min(g.H, y0 + g.lb), x1 = min(g.W, x0 + g.lb);
-    const int bw = x1 - x0, nsite = (y1 - y0) * bw;
-    const int s = of_block[b];
     // Neighbours across the block's left / right / upper / lower edge exist
     // only in the same slice; within the slice, absent sites have no bonds.
-    const bool l_ok = bx > 0 && of_block[b - 1] == s;
-    const bool r_ok = bx + 1 < g.nbx && of_block[b + 1] == s;
-    const bool u_ok = by > 0 && of_block[b - g.nbx] == s;
-    const bool d_ok = by + 1 < g.nby && of_block[b + g.nbx] == s;
-    int o0 = start0[b], o1 = start1[b];
+    const BlockFrame fr = block_frame(g, of_block, warp);
+    const int bw = fr.x1 - fr.x0, nsite = (fr.y1 - fr.y0) * bw;
+    int o0 = start0[fr.b], o1 = start1[fr.b];
     for (int pass = 0; pass < 2; ++pass) {
         for (int j0 = 0; j0 < nsite; j0 += 32) {
             const int j = j0 + lane;
             bool take = false;
             int y = 0, x = 0, c = 0;
             if (j < nsite) {
-                y = y0 + j / bw;
-                x = x0 + j % bw;
-                const bool edge = (x == x0 && l_ok) || (y == y0 && u_ok);
-                take = mask[(int64_t)y * g.W + x] == MASK_GAP && edge == (pass == 0);
+                y = fr.y0 + j / bw;
+                x = fr.x0 + j % bw;
+                take = mask[(int64_t)y * g.W + x] == MASK_GAP && block_edge(fr, y, x) == (pass == 0);
                 c = (x + y) & 1;
             }
             const unsigned m0 = __ballot_sync(0xffffffffu, take && c == 0);
             const unsigned m1 = __ballot_sync(0xffffffffu, take && c == 1);
             if (take) {
-                const int64_t i = (int64_t)y * g.W + x;
-                uint32_t f = 0;
-                const bool hl = (x > x0 || l_ok) && mask[i - 1] != MASK_ABSENT;
-                const bool hr = (x + 1 < x1 || r_ok) && mask[i + 1] != MASK_ABSENT;
-                const bool hu = (y > y0 || u_ok) && mask[i - g.W] != MASK_ABSENT;
-                const bool hd = (y + 1 < y1 || d_ok) && mask[i + g.W] != MASK_ABSENT;
-                if (hl) { f |= NB_L; if (mask[i - 1] == MASK_GAP) f |= GAP_L; }
-                if (hr) { f |= NB_R; if (mask[i + 1] == MASK_GAP) f |= GAP_R; }
-                if (hu) { f |= NB_U; if (mask[i - g.W] == MASK_GAP) f |= GAP_U; }
-                if (hd) { f |= NB_D; if (mask[i + g.W] == MASK_GAP) f |= GAP_D; }
-                if (hl && x == x0) f |= EDGE_L;
-                if (hu && y == y0) f |= EDGE_U;
-                const uint2 e = make_uint2(((uint32_t)y << 16) | (uint32_t)x,
-                                           ((uint32_t)b << META_SHIFT) | f);
+                const uint2 e = gap_entry(g, mask, fr, y, x);
                 const unsigned below = (1u << lane) - 1u;
                 if (c == 0) list0[o0 + __popc(m0 & below)] = e;
                 else list1[o1 + __popc(m1 & below)] = e;
@@ -288,8 +267,8 @@ __global__ void k_build_lists(Geom g, const int32_t* __restrict__ of_block,
             o1 += __popc(m1);
         }
         if (pass == 0 && lane == 0) {
-            split0[b] = o0;   // end of the block's edge entries
-            split1[b] = o1;
+            split0[fr.b] = o0;   // end of the block's edge entries
+            split1[fr.b] = o1;
         }
     }
 }

@@ -132,6 +132,20 @@ constexpr int kPairTailCap = 4096;
 cudaError_t launch_pair_tail(const SimTailArgs& a, int G, int storage, int n_pairs,
                              cudaStream_t s);
 
+// The staged half-step (mpr_tile.cu): tile shape of a geometry, the staging
+// table, the tile-major lists (count, scan with launch_scan, then write), the
+// kernel (G = 8 only) and its resident CTAs per SM.
+Tiles tile_shape(const Geom& g);
+void launch_stage_table(const Geom& g, const uint8_t* mask, const float* dang, float* stab,
+                        cudaStream_t s);
+void launch_tile_count(const Geom& g, const Tiles& tl, const int32_t* of_block,
+                       const uint8_t* mask, int32_t* cnt0, int32_t* cnt1, cudaStream_t s);
+void launch_tile_lists(const Geom& g, const Tiles& tl, const int32_t* of_block,
+                       const uint8_t* mask, const int32_t* start0, const int32_t* start1,
+                       uint2* list0, uint2* list1, cudaStream_t s);
+int tile_blocks_per_sm(int storage);
+void launch_sweep_tile(const SweepArgs& a, int storage, int grid, cudaStream_t s);
+
 int cal_persistent_blocks_per_sm(int G);
 cudaError_t launch_cal_persistent(const CalPersistArgs& a, int G, int grid, cudaStream_t s);
 

@@ -121,11 +121,11 @@ __device__ __forceinline__ void flush_pair(float* ea, float v0, float v1) {
     if (v1 != 0.0f) atomicAdd(ea + 1, v1);
 }
 
-// Bond-by-bond split of a move at a block edge (used by the flat kernel,
-// which keeps all four neighbours' (cos, sin)).
-__device__ __forceinline__ void add_energy(const SiteNew& n, uint32_t f, float C, float S,
-                                           const float* nc, const float* ns, float J, float& ao,
-                                           float& al, float& au) {
+// Bond-by-bond split of a move at a block edge: (lc, ls) and (uc, us) are the
+// left and upper neighbours' (cos, sin) of q phi_j.
+__device__ __forceinline__ void add_energy_lu(const SiteNew& n, uint32_t f, float C, float S,
+                                              float lc, float ls, float uc, float us, float J,
+                                              float& ao, float& al, float& au) {
     if (!(f & (EDGE_L | EDGE_U))) {
         ao += n.dE;
         return;
@@ -133,11 +133,19 @@ __device__ __forceinline__ void add_energy(const SiteNew& n, uint32_t f, float C
     float cn, sn;
     final_cs(n, C, S, cn, sn);
     const float dc = cn - n.co, ds = sn - n.so;
-    const float dl = -J * (dc * nc[0] + ds * ns[0]);
-    const float du = -J * (dc * nc[2] + ds * ns[2]);
+    const float dl = -J * (dc * lc + ds * ls);
+    const float du = -J * (dc * uc + ds * us);
     ao += n.dE;
     if (f & EDGE_L) { ao -= dl; al += dl; }
     if (f & EDGE_U) { ao -= du; au += du; }
+}
+
+// The same with the four neighbours' (cos, sin) in arrays (left, right, up,
+// down), as the kernels that keep all four use it.
+__device__ __forceinline__ void add_energy(const SiteNew& n, uint32_t f, float C, float S,
+                                           const float* nc, const float* ns, float J, float& ao,
+                                           float& al, float& au) {
+    add_energy_lu(n, f, C, S, nc[0], ns[0], nc[2], ns[2], J, ao, al, au);
 }
 
 // Angles of the four neighbours of a site in both realizations of the pair.
