@@ -185,7 +185,7 @@ struct Args3 {
     float2* ang;             // [2][D][H][Wh][np]
     const float* beta;       // [nblk]
     const uint8_t* running;  // [nblk][Rp] or nullptr (every lane r < R)
-    float* eacc;             // [nblk][Rp]
+    double* eacc;            // [nblk][Rp] FP64 per-sweep changes
     double* ecur;            // [nblk][Rp] (energy pass)
     int np, R, Rp;
     uint32_t pair_base;      // Philox counter word 2 of lane pair 0 (realization base / 2)
@@ -320,9 +320,9 @@ __global__ void __launch_bounds__(256) k3_sweep(Args3 a) {
             if (lane != 0) continue;
         }
         if (b < 0 || (v0 == 0.0f && v1 == 0.0f)) continue;
-        float* ea = a.eacc + ((size_t)b - off[k]) * a.Rp + 2 * p;
-        if (v0 != 0.0f) atomicAdd(ea, v0);
-        if (v1 != 0.0f) atomicAdd(ea + 1, v1);
+        double* ea = a.eacc + ((size_t)b - off[k]) * a.Rp + 2 * p;
+        if (v0 != 0.0f) atomicAdd(ea, (double)v0);
+        if (v1 != 0.0f) atomicAdd(ea + 1, (double)v1);
     }
 }
 
@@ -476,7 +476,7 @@ struct mpr3_ctx {
     int np = 0, R = 0, Rp = 0, batch_open = 0, t = 0;
     size_t ang_cap = 0, blk_cap = 0;
     float2* ang = nullptr;
-    float* eacc = nullptr;
+    double* eacc = nullptr;
     double *ecur = nullptr, *e_last = nullptr;
     uint8_t* running = nullptr;
     int32_t *stop = nullptr, *tcount = nullptr;
@@ -586,7 +586,7 @@ mpr_status ensure3(mpr3_ctx* ctx, int lanes) {
     }
     ctx->np = np;
     ctx->Rp = Rp;
-    CK3(cudaMemsetAsync(ctx->eacc, 0, blk * sizeof(float), ctx->s));
+    CK3(cudaMemsetAsync(ctx->eacc, 0, blk * sizeof(double), ctx->s));
     CK3(cudaMemsetAsync(ctx->ctl, 0, sizeof(Control), ctx->s));
     return MPR_OK;
 }

@@ -96,7 +96,7 @@ struct mpr_ctx {
     int storage = 0;             // element type of the batch state (an mpr_storage)
     void* ang = nullptr;
     size_t ang_cap = 0;          // bytes
-    float* eacc = nullptr;
+    double* eacc = nullptr;
     double* ecur = nullptr;      // [nblk][Rp] current E_b of every (block, realization)
     double* ecur0 = nullptr;     // [nblk][Rp] calibration: E_b of the start state
     uint8_t* running = nullptr;
@@ -307,7 +307,7 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group, int storag
     ctx->G = G;
     ctx->groups = groups;
     ctx->Rp = Rp;
-    CK(cudaMemsetAsync(ctx->eacc, 0, 2 * blk_need * sizeof(float), ctx->s));
+    CK(cudaMemsetAsync(ctx->eacc, 0, 2 * blk_need * sizeof(double), ctx->s));
     CK(cudaMemsetAsync(ctx->ctl, 0, sizeof(Control), ctx->s));
     return MPR_OK;
 }
@@ -706,7 +706,7 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     const size_t blk = (size_t)g.nblk * ctx->Rp;
     CK(cudaMemcpyAsync(ctx->ecur, ctx->ecur0, blk * sizeof(double), cudaMemcpyDeviceToDevice,
                        ctx->s));
-    CK(cudaMemsetAsync(ctx->eacc, 0, 2 * blk * sizeof(float), ctx->s));
+    CK(cudaMemsetAsync(ctx->eacc, 0, 2 * blk * sizeof(double), ctx->s));
     // Sweep sw's changes go to eacc buffer sw & 1; the colour-0 launch of
     // sweep sw + 1 folds them (extra CTAs), the last sweep's fold runs alone.
     const int n_sw = o.n_eq + o.n_meas;
@@ -1032,6 +1032,7 @@ mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
     ctx->m.overrelax = ctx->opt.overrelax ? 1 : 0;
     ctx->rng.key0 = (uint32_t)(ctx->opt.seed & 0xffffffffu);
     ctx->rng.key1 = (uint32_t)(ctx->opt.seed >> 32) ^ ctx->opt.slice_id;
+    for (int r = 0; r < 10; ++r) ctx->rng.rk0[r] = ctx->rng.key0 + (uint32_t)r * 0x9E3779B9u;
     ctx->s = (cudaStream_t)ctx->opt.cuda_stream;
 
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(MPR_ECUDA);

@@ -30,12 +30,34 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     out[3] = c3;
 }
 
+// The same generator with the round keys of key word 0 given (k0 + r W0 for
+// r = 0 .. 9, taken from kernel parameters, where the XOR reads them
+// directly); key word 1 advances in the loop.
+__device__ __forceinline__ void philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 const uint32_t (&rk0)[10], uint32_t k1,
+                                                 uint32_t out[4]) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t pa = (uint64_t)0xD2511F53u * c0;
+        const uint64_t pb = (uint64_t)0xCD9E8D57u * c2;
+        c0 = (uint32_t)(pb >> 32) ^ c1 ^ rk0[round];
+        c1 = (uint32_t)pb;
+        c2 = (uint32_t)(pa >> 32) ^ c3 ^ (k1 + (uint32_t)round * 0xBB67AE85u);
+        c3 = (uint32_t)pa;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
 // (((x >> 8) | 1) * 2^-24): an odd multiple of 2^-24 in (0,1), exact in FP32
-// and equal to the oracle's value. Built from the bits: 1 + (x >> 9) * 2^-23
-// is a float with mantissa x >> 9; subtracting 1 is exact (Sterbenz) and
-// adding 2^-24 lands on the representable (2 (x >> 9) + 1) * 2^-24.
+// and equal to the oracle's value. Built from the bits: f = 1 + (x >> 9) 2^-23
+// is a float with mantissa x >> 9, and f - (1 - 2^-24) = (2 (x >> 9) + 1)
+// 2^-24 has at most 24 significant bits, so the one subtraction is exact
+// (1 - 2^-24 is itself a float, 0x3F7FFFFF).
 __device__ __forceinline__ float u01(uint32_t x) {
-    return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 5.9604644775390625e-08f;
+    return __uint_as_float(0x3F800000u | (x >> 9)) - 0.999999940395355224609375f;
 }
 
 // psi = atan2(S, C) for S >= 0, psi in [0, pi]: atan(t) = t P(t^2) on

@@ -10,7 +10,7 @@
 //                             r % G of group r / G; the FP32 form also holds
 //                             the sample angles there, the 16-bit forms read
 //                             samples from dang only
-//   eacc   [nblk][Rp] float   per-sweep energy change of each block (Rp = groups * G)
+//   eacc   [nblk][Rp] double  per-sweep energy change of each block (Rp = groups * G)
 //   ecur   [nblk][Rp] double  current block energy E_b
 //   running[nblk][Rp] uint8   1 while block b of realization r still sweeps
 // Wh = ceil(W/2); site (y,x) of colour c = (x+y)&1 sits at half index x >> 1.
@@ -44,6 +44,7 @@ struct Geom {
 
 struct Rng {
     uint32_t key0, key1;
+    uint32_t rk0[10];          // round keys of key word 0: key0 + r * 0x9E3779B9
 };
 
 // Mask values of the canvas: 0 sample, 1 gap (prediction site), 2 absent
@@ -146,7 +147,7 @@ struct SweepArgs {
     const float* beta_site;   // [H*W] 1 / T_i (site temperatures, Sec. 2.2.3) or nullptr
     const float* beta_odd;    // [nblk] 1 / T_b of odd lanes (trisection's second point) or nullptr
     const uint8_t* running;   // [nblk][Rp] or nullptr (= every lane r < R runs)
-    float* eacc;              // [nblk][Rp] energy change of this sweep (moves)
+    double* eacc;             // [nblk][Rp] energy change of this sweep (moves)
     double* ecur;             // [nblk][Rp] E_b (the energy pass adds into it)
     const uint32_t* work;     // two worklists of units b * (Rp / 2) + pair, or nullptr = all units
     uint32_t work_stride;     // elements per worklist
@@ -166,7 +167,7 @@ struct StopArgs {
     const double* es;         // [nblk] e_s,b
     const double* inb;       // [nblk] 1 / N_b
     const int32_t* Nsp;       // [nblk] sample bonds (0: not targeted)
-    float* eacc;              // [nblk][Rp] the sweep's change (folded and cleared)
+    double* eacc;             // [nblk][Rp] the sweep's change (folded and cleared)
     double* ecur;             // [nblk][Rp] E_b
     const int8_t* sigma;      // [nblk][Rp] side of e_s,b at t = 0
     uint8_t* running;         // [nblk][Rp]
@@ -182,7 +183,7 @@ struct FoldArgs {
     int nblk, Rp, chains, measure;
     int points;               // 2: even / odd lanes are the trisection's two points
     const double* inb;        // [nblk] 1 / N_b
-    float* eacc;              // [nblk][Rp] change of the sweep being folded (cleared)
+    double* eacc;             // [nblk][Rp] change of the sweep being folded (cleared)
     double* ecur;             // [nblk][Rp]
     double* ebar;             // [nblk] (even lanes when points == 2)
     double* ebar_odd;         // [nblk] odd lanes (points == 2)
@@ -219,7 +220,7 @@ struct CalPersistArgs {
     const int32_t* start[2];
     const int32_t* split[2];
     int64_t n_list[2];
-    float* eacc2[2];           // per-sweep energy changes, by sweep parity
+    double* eacc2[2];          // per-sweep energy changes, by sweep parity
     const double* Es;
     const double* es;
     const double* inb;

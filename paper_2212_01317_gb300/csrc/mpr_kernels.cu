@@ -404,9 +404,9 @@ __global__ void __launch_bounds__(kFlatThreads, 8) k_sweep_flat(SweepArgs a, int
             double s[2] = {0.0, 0.0};
             for (int r = 0; r < f.chains * f.points; ++r) {
                 const size_t k = (size_t)b * f.Rp + r;
-                const double E = f.ecur[k] + (double)f.eacc[k];
+                const double E = f.ecur[k] + f.eacc[k];
                 f.ecur[k] = E;
-                f.eacc[k] = 0.0f;
+                f.eacc[k] = 0.0;
                 s[f.points == 2 ? (r & 1) : 0] += E * f.inb[b];
             }
             if (f.measure) {
@@ -441,12 +441,12 @@ template __global__ void k_sweep_flat<8>(SweepArgs, int64_t, FoldArgs);
 // E_b <- E_s,b for every (block, lane): the constant sample-sample part; the
 // energy pass then adds the bonds that touch a gap site.
 __global__ void k_ecur_reset(int nblk, int Rp, const double* __restrict__ Es,
-                             double* __restrict__ ecur, float* __restrict__ eacc) {
+                             double* __restrict__ ecur, double* __restrict__ eacc) {
     const int64_t n = (int64_t)nblk * Rp;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         ecur[t] = Es[t / Rp];
-        eacc[t] = 0.0f;
+        eacc[t] = 0.0;
     }
 }
 
@@ -609,16 +609,16 @@ __global__ void k_cal_fill(Slices sl, int nbx, const int32_t* __restrict__ Nsp,
 // sweeps add e_b of every chain to the running sum.
 __global__ void k_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed,
                            const Control* __restrict__ ctl, const double* __restrict__ inb,
-                           float* __restrict__ eacc, double* __restrict__ ecur,
+                           double* __restrict__ eacc, double* __restrict__ ecur,
                            double* __restrict__ ebar, int points, double* __restrict__ ebar_odd) {
     const bool measure = (t_fixed > 0 ? t_fixed : (int)ctl->t) > n_eq;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
         double s[2] = {0.0, 0.0};
         for (int r = 0; r < chains * points; ++r) {
             const size_t k = (size_t)b * Rp + r;
-            const double E = ecur[k] + (double)eacc[k];
+            const double E = ecur[k] + eacc[k];
             ecur[k] = E;
-            eacc[k] = 0.0f;
+            eacc[k] = 0.0;
             s[points == 2 ? (r & 1) : 0] += E * inb[b];
         }
         if (measure) {
@@ -1207,7 +1207,7 @@ void launch_ecur_broadcast(int nblk, int Rp, int G, double* ecur, cudaStream_t s
     k_ecur_broadcast<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, G, ecur);
 }
 
-void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
+void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, double* eacc,
                        cudaStream_t s) {
     k_ecur_reset<<<grid_for((int64_t)nblk * Rp, 256), 256, 0, s>>>(nblk, Rp, Es, ecur, eacc);
 }
@@ -1222,7 +1222,7 @@ void launch_stop_init(int nblk, int Rp, const int32_t* of_block, const double* e
 
 void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, int grid,
                           Control* ctl, const uint32_t* work, uint32_t work_stride,
-                          const double* es, const double* inb, const int32_t* Nsp, float* eacc,
+                          const double* es, const double* inb, const int32_t* Nsp, double* eacc,
                           double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
                           int32_t* tcount, double* e_last, int t_known, cudaStream_t s) {
     StopArgs sa{};
@@ -1284,7 +1284,7 @@ void launch_cal_fill(const Slices& sl, int nbx, const int32_t* Nsp, float* T, fl
 }
 
 void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
-                     const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s,
+                     const double* inb, double* eacc, double* ecur, double* ebar, cudaStream_t s,
                      int points, double* ebar_odd) {
     k_cal_step<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Rp, chains, n_eq, t_fixed, ctl, inb, eacc,
                                                   ecur, ebar, points, ebar_odd);

@@ -42,7 +42,7 @@ void launch_energy(const SweepArgs& a, int G, int storage, int n_sm, cudaStream_
 void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s,
                        const FoldArgs* fold = nullptr);
 void launch_ecur_broadcast(int nblk, int Rp, int G, double* ecur, cudaStream_t s);
-void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, float* eacc,
+void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, double* eacc,
                        cudaStream_t s);
 // tcount is [n_slices][Rp]: running targeted blocks per slice and realization.
 void launch_stop_init(int nblk, int Rp, const int32_t* of_block, const double* es,
@@ -51,7 +51,7 @@ void launch_stop_init(int nblk, int Rp, const int32_t* of_block, const double* e
                       double* e_last, cudaStream_t s);
 void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, int grid,
                           Control* ctl, const uint32_t* work, uint32_t work_stride,
-                          const double* es, const double* inb, const int32_t* Nsp, float* eacc,
+                          const double* es, const double* inb, const int32_t* Nsp, double* eacc,
                           double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
                           int32_t* tcount, double* e_last, int t_known, cudaStream_t s);
 // work == nullptr: every item (t = 0). Writes the next sweep's worklist into
@@ -72,7 +72,7 @@ void launch_cal_fill(const Slices& sl, int nbx, const int32_t* Nsp, float* T, fl
                      cudaStream_t s);
 // points = 2: even lanes' energies go to ebar, odd lanes' to ebar_odd.
 void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
-                     const double* inb, float* eacc, double* ecur, double* ebar, cudaStream_t s,
+                     const double* inb, double* eacc, double* ecur, double* ebar, cudaStream_t s,
                      int points = 1, double* ebar_odd = nullptr);
 // Trisection (two temperatures per block per iteration).
 void launch_kcal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T0,

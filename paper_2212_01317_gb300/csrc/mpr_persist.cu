@@ -31,14 +31,14 @@ __device__ __forceinline__ SweepArgs colour_args(const CalPersistArgs& a, int c)
 // adds e_b of every chain to the running sum of the iteration.
 __device__ __forceinline__ void fold_sweep(const CalPersistArgs& a, int sweep, int tid, int nthr) {
     const int Rp = a.sw.Rp;
-    float* ea = a.eacc2[sweep & 1];
+    double* ea = a.eacc2[sweep & 1];
     for (int b = tid; b < a.sw.g.nblk; b += nthr) {
         double s = 0.0;
         for (int r = 0; r < a.chains; ++r) {
             const size_t k = (size_t)b * Rp + r;
-            const double E = a.sw.ecur[k] + (double)ea[k];
+            const double E = a.sw.ecur[k] + ea[k];
             a.sw.ecur[k] = E;
-            ea[k] = 0.0f;
+            ea[k] = 0.0;
             s += E * a.inb[b];
         }
         if (sweep > a.n_eq) a.ebar[b] += s;
@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(512, 1) k_cal_persistent(CalPersistArgs a) {
         }
         for (int64_t t = tid; t < (int64_t)nblk * Rp; t += nthr) {
             a.sw.ecur[t] = a.Es[t / Rp];
-            a.eacc2[0][t] = 0.0f;
-            a.eacc2[1][t] = 0.0f;
+            a.eacc2[0][t] = 0.0;
+            a.eacc2[1][t] = 0.0;
         }
         if (!grid_sync(a.bar, gen, lim)) return;
         // E_b of the start state from scratch.

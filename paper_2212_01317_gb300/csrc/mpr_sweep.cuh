@@ -107,18 +107,20 @@ __device__ __forceinline__ SiteNew site_update(float phi, float C, float Sn, flo
     return n;
 }
 
-// Interior sites: warp sum of a block's change, FP32 atomics into eacc (the
-// stop test folds eacc into the FP64 block energy once per sweep).
-__device__ __forceinline__ void flush_pair(float* ea, float v0, float v1) {
+// A block's change: each lane's FP32 partial (its own few entries) is summed
+// over the warp in FP64 and added to eacc with an FP64 atomic (the stop test
+// and the calibration fold eacc into the FP64 block energy once per sweep).
+__device__ __forceinline__ void flush_pair(double* ea, float v0, float v1) {
     if (!__any_sync(0xffffffffu, v0 != 0.0f || v1 != 0.0f)) return;
+    double d0 = v0, d1 = v1;
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, s);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, s);
+        d0 += __shfl_xor_sync(0xffffffffu, d0, s);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, s);
     }
     if ((threadIdx.x & 31) != 0) return;
-    if (v0 != 0.0f) atomicAdd(ea, v0);
-    if (v1 != 0.0f) atomicAdd(ea + 1, v1);
+    if (d0 != 0.0) atomicAdd(ea, d0);
+    if (d1 != 0.0) atomicAdd(ea + 1, d1);
 }
 
 // Bond-by-bond split of a move at a block edge: (lc, ls) and (uc, us) are the
@@ -246,7 +248,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
         const uint32_t f = en.y;
         const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
         uint32_t w[4];
-        philox4x32_10(local_index(rc, y, x), ctr1, rpair, 0u, a.rng.key0, key1, w);
+        philox4x32_10_rk(local_index(rc, y, x), ctr1, rpair, 0u, a.rng.rk0, key1, w);
         const float2 ph = Store<S>::load2(own + (size_t)hs * G);
         float nc0[4], ns0[4], nc1[4], ns1[4];
         neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
@@ -269,25 +271,26 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
         Store<S>::store2(own + (size_t)hs * G, out);
     }
     if (!a.energy) return;
-    float* ea = a.eacc + (size_t)b * a.Rp + rl;
+    double* ea = a.eacc + (size_t)b * a.Rp + rl;
     flush_pair(ea, ao0, ao1);
     flush_pair(ea - a.Rp, al0, al1);
     flush_pair(ea - (size_t)a.g.nbx * a.Rp, au0, au1);
 }
 
-// Energy flush of one half-warp's unit: sums over its 16 lanes, then its
-// lane 0 adds them (act: the half has a running unit). Every lane of the warp
-// calls it.
-__device__ __forceinline__ void flush_pair_half(float* ea, float v0, float v1, bool act) {
+// Energy flush of one half-warp's unit: FP64 sums over its 16 lanes' FP32
+// partials, then its lane 0 adds them (act: the half has a running unit).
+// Every lane of the warp calls it.
+__device__ __forceinline__ void flush_pair_half(double* ea, float v0, float v1, bool act) {
     if (!__any_sync(0xffffffffu, v0 != 0.0f || v1 != 0.0f)) return;
+    double d0 = v0, d1 = v1;
 #pragma unroll
     for (int s = 8; s > 0; s >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, s);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, s);
+        d0 += __shfl_xor_sync(0xffffffffu, d0, s);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, s);
     }
     if ((threadIdx.x & 15) != 0 || !act) return;
-    if (v0 != 0.0f) atomicAdd(ea, v0);
-    if (v1 != 0.0f) atomicAdd(ea + 1, v1);
+    if (d0 != 0.0) atomicAdd(ea, d0);
+    if (d1 != 0.0) atomicAdd(ea + 1, d1);
 }
 
 // Two units per warp: lanes 0-15 take one (block, realization pair) unit,
@@ -331,7 +334,7 @@ __device__ __forceinline__ void sweep_item_half(const SweepArgs& a, int item, in
             const uint32_t f = en.y;
             const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
             uint32_t w[4];
-            philox4x32_10(local_index(rc, y, x), ctr1, rpair, 0u, a.rng.key0, key1, w);
+            philox4x32_10_rk(local_index(rc, y, x), ctr1, rpair, 0u, a.rng.rk0, key1, w);
             const float2 ph = Store<S>::load2(own + (size_t)hs * G);
             float nc0[4], ns0[4], nc1[4], ns1[4];
             neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
@@ -355,7 +358,7 @@ __device__ __forceinline__ void sweep_item_half(const SweepArgs& a, int item, in
         }
     }
     if (!a.energy) return;
-    float* ea = a.eacc + (size_t)b * a.Rp + rl;
+    double* ea = a.eacc + (size_t)b * a.Rp + rl;
     flush_pair_half(ea, ao0, ao1, act);
     flush_pair_half(ea - a.Rp, al0, al1, act);
     flush_pair_half(ea - (size_t)a.g.nbx * a.Rp, au0, au1, act);
@@ -369,6 +372,7 @@ __device__ __forceinline__ void sweep_item_half(const SweepArgs& a, int item, in
 // shared memory (the list is block-major, so a CTA spans few blocks) and
 // flushed with one atomic per (block, realization); changes that belong to
 // another block (left / up bonds of edge sites) go straight to global memory.
+// A warp's FP32 sum covers at most 32 entries; every sum beyond is FP64.
 constexpr int kFlatThreads = 256;
 constexpr int kFlatBlocks = 64;     // local blocks summed in shared memory per CTA
 
@@ -389,13 +393,13 @@ __device__ __forceinline__ void grid_dep_launch() {
 template <int G>
 __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, uint32_t ctr1) {
     constexpr int NP = G / 2;
-    __shared__ float acc[kFlatBlocks * G];
+    __shared__ double acc[kFlatBlocks * G];
     const int grp = blockIdx.y;
     const int64_t t0 = (int64_t)blockIdx.x * kFlatThreads;
     const int64_t t = t0 + threadIdx.x;
     const int64_t e = t / NP;
     const int q = (int)(t % NP);
-    for (int i = threadIdx.x; i < kFlatBlocks * G; i += kFlatThreads) acc[i] = 0.0f;
+    for (int i = threadIdx.x; i < kFlatBlocks * G; i += kFlatThreads) acc[i] = 0.0;
     const int b0 = (int)(a.list[t0 / NP].y >> META_SHIFT);
     const bool live = e < n_list;
     const int rl = grp * G + 2 * q;
@@ -408,8 +412,8 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
         b = (int)(en.y >> META_SHIFT);
         const int y = en.x >> 16, x = en.x & 0xffff;
         const int sl = slice_of(a.sl, b);
-        philox4x32_10(local_index(slice_rect(a.sl, sl), y, x), ctr1,
-                      (a.r_base + (uint32_t)rl) >> 1, 0u, a.rng.key0, slice_key1(a.sl, sl), w);
+        philox4x32_10_rk(local_index(slice_rect(a.sl, sl), y, x), ctr1,
+                         (a.r_base + (uint32_t)rl) >> 1, 0u, a.rng.rk0, slice_key1(a.sl, sl), w);
         beta = a.beta[b];
         beta1 = a.beta_odd ? a.beta_odd[b] : beta;
     }
@@ -465,38 +469,38 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
         if (lane < NP) {
             const int loc = b - b0;
             if (loc < kFlatBlocks) {
-                if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane], ao0);
-                if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane + 1], ao1);
+                if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane], (double)ao0);
+                if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane + 1], (double)ao1);
             } else {
-                float* ea = a.eacc + (size_t)b * a.Rp + grp * G + 2 * lane;
-                if (ao0 != 0.0f) atomicAdd(ea, ao0);
-                if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
+                double* ea = a.eacc + (size_t)b * a.Rp + grp * G + 2 * lane;
+                if (ao0 != 0.0f) atomicAdd(ea, (double)ao0);
+                if (ao1 != 0.0f) atomicAdd(ea + 1, (double)ao1);
             }
         }
     } else if (live) {
         const int loc = b - b0;
         if (loc < kFlatBlocks) {
-            if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * q], ao0);
-            if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * q + 1], ao1);
+            if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * q], (double)ao0);
+            if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * q + 1], (double)ao1);
         } else {
-            float* ea = a.eacc + (size_t)b * a.Rp + rl;
-            if (ao0 != 0.0f) atomicAdd(ea, ao0);
-            if (ao1 != 0.0f) atomicAdd(ea + 1, ao1);
+            double* ea = a.eacc + (size_t)b * a.Rp + rl;
+            if (ao0 != 0.0f) atomicAdd(ea, (double)ao0);
+            if (ao1 != 0.0f) atomicAdd(ea + 1, (double)ao1);
         }
     }
     // Left / up bonds of edge sites belong to the neighbouring blocks.
     if (f & (EDGE_L | EDGE_U)) {
-        float* ea = a.eacc + (size_t)b * a.Rp + rl;
-        if (al0 != 0.0f) atomicAdd(ea - a.Rp, al0);
-        if (al1 != 0.0f) atomicAdd(ea - a.Rp + 1, al1);
+        double* ea = a.eacc + (size_t)b * a.Rp + rl;
+        if (al0 != 0.0f) atomicAdd(ea - a.Rp, (double)al0);
+        if (al1 != 0.0f) atomicAdd(ea - a.Rp + 1, (double)al1);
         const size_t up = (size_t)a.g.nbx * a.Rp;
-        if (au0 != 0.0f) atomicAdd(ea - up, au0);
-        if (au1 != 0.0f) atomicAdd(ea - up + 1, au1);
+        if (au0 != 0.0f) atomicAdd(ea - up, (double)au0);
+        if (au1 != 0.0f) atomicAdd(ea - up + 1, (double)au1);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kFlatBlocks * G; i += kFlatThreads) {
-        const float v = acc[i];
-        if (v != 0.0f) atomicAdd(&a.eacc[(size_t)(b0 + i / G) * a.Rp + grp * G + (i % G)], v);
+        const double v = acc[i];
+        if (v != 0.0) atomicAdd(&a.eacc[(size_t)(b0 + i / G) * a.Rp + grp * G + (i % G)], v);
     }
 }
 
@@ -577,12 +581,12 @@ __device__ __forceinline__ void stop_targeted_range(const StopArgs& s, uint32_t 
         const int r = (int)(item % (uint32_t)s.groups) * s.G + (int)(i % s.G);
         const size_t k = (size_t)b * s.Rp + r;
         const uint8_t run = s.running[k];
-        const double E = s.ecur[k] + (double)s.eacc[k];
+        const double E = s.ecur[k] + s.eacc[k];
         const double inb = s.inb[b], es = s.es[b];
         const int32_t nsp = s.Nsp[b], ob = s.of_block[b];
         const int sg = s.sigma[k];
         if (!run) continue;
-        s.eacc[k] = 0.0f;
+        s.eacc[k] = 0.0;
         s.ecur[k] = E;
         const double e = E * inb;
         s.e_last[k] = e;

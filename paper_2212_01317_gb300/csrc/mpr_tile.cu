@@ -156,7 +156,7 @@ template <typename S>
 __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
     grid_dep_launch();
     __shared__ float4 stage[kStageSites * 4];       // [site][pair]: (c0, s0, c1, s1)
-    __shared__ float red[kTileWarps][4][6];
+    __shared__ double red[kTileWarps][4][6];
     grid_dep_wait();
     constexpr int G = 8;
     const Geom& g = a.g;
@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
             const float2 ph = Store<S>::load2(po);
             const int rl = grp * G + 2 * q;
             uint32_t w[4];
-            philox4x32_10(local_index(rc, y, x), ctr1, (a.r_base + (uint32_t)rl) >> 1, 0u,
-                          a.rng.key0, key1, w);
+            philox4x32_10_rk(local_index(rc, y, x), ctr1, (a.r_base + (uint32_t)rl) >> 1, 0u,
+                             a.rng.rk0, key1, w);
             const float bt = a.beta_site ? a.beta_site[(size_t)y * g.W + x] : beta;
             float2 out = ph;
             if (run0) {
@@ -266,11 +266,12 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
             Store<S>::store2(po, out);
         }
 
-        // The tile's energy changes: sums over the lanes of one pair (lanes
-        // q, q + 4, ...), over the warps, then one atomic per (block,
+        // The tile's energy changes: each thread's FP32 partial (its few
+        // entries) summed in FP64 over the lanes of one pair (lanes q, q + 4,
+        // ...) and over the warps, then one FP64 atomic per (block,
         // realization) for the own, left and upper blocks.
         if (a.energy) {
-            float v[6] = {ao0, ao1, al0, al1, au0, au1};
+            double v[6] = {ao0, ao1, al0, al1, au0, au1};
 #pragma unroll
             for (int d = 4; d < 32; d <<= 1)
 #pragma unroll
@@ -281,18 +282,18 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
             __syncthreads();
             if (threadIdx.x < 4) {
                 const int q = threadIdx.x;
-                float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
                 for (int w = 0; w < kTileWarps; ++w)
 #pragma unroll
                     for (int k = 0; k < 6; ++k) s[k] += red[w][q][k];
-                float* ea = a.eacc + (size_t)b * a.Rp + grp * G + 2 * q;
+                double* ea = a.eacc + (size_t)b * a.Rp + grp * G + 2 * q;
                 const size_t up = (size_t)g.nbx * a.Rp;
-                if (s[0] != 0.0f) atomicAdd(ea, s[0]);
-                if (s[1] != 0.0f) atomicAdd(ea + 1, s[1]);
-                if (s[2] != 0.0f) atomicAdd(ea - a.Rp, s[2]);
-                if (s[3] != 0.0f) atomicAdd(ea - a.Rp + 1, s[3]);
-                if (s[4] != 0.0f) atomicAdd(ea - up, s[4]);
-                if (s[5] != 0.0f) atomicAdd(ea - up + 1, s[5]);
+                if (s[0] != 0.0) atomicAdd(ea, s[0]);
+                if (s[1] != 0.0) atomicAdd(ea + 1, s[1]);
+                if (s[2] != 0.0) atomicAdd(ea - a.Rp, s[2]);
+                if (s[3] != 0.0) atomicAdd(ea - a.Rp + 1, s[3]);
+                if (s[4] != 0.0) atomicAdd(ea - up, s[4]);
+                if (s[5] != 0.0) atomicAdd(ea - up + 1, s[5]);
             }
         }
         __syncthreads();   // the next item restages

@@ -113,3 +113,18 @@ def sampled_sweep_parity(o, mask, T_of_site, pre, post, r, rng, n_sample, storag
                 msgs.append(f"site {int(i)} colour {colour} gpu={g:.7f} ora={ph[i]:.7f} "
                             f"dE={d.dE:.3e} th={d.theta:.3e} R={d.R:.3e}")
     return checked, explained, bad, "; ".join(msgs[:5])
+
+
+def paired_over_seeds(run, seeds, floor_rel=1e-3):
+    """run(seed) -> (AAE of the GPU run, AAE of the oracle's run) of one
+    configuration and seed: both sides draw the same random numbers, so most
+    seeds agree to rounding and a seed whose chains separated after a
+    decision flip differs by Monte Carlo noise. Asserts that the mean paired
+    difference is within 3 standard errors (plus floor_rel of the AAE, for a
+    spread of zero) and returns the differences."""
+    pairs = [run(s) for s in seeds]
+    d = np.array([g - o for g, o in pairs])
+    ref = float(np.mean([o for _, o in pairs]))
+    se = float(d.std(ddof=1) / np.sqrt(len(d))) if len(d) > 1 else 0.0
+    assert abs(d.mean()) <= 3.0 * se + floor_rel * ref, (d, se, ref)
+    return d

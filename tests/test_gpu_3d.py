@@ -14,7 +14,7 @@ import oracle
 from paper_2212_01317_gb300 import synth
 from paper_2212_01317_gb300.mpr import GapFiller, GapFiller3
 
-from parity import TWO_PI, compare_site_updates
+from parity import TWO_PI, compare_site_updates, paired_over_seeds
 
 pytestmark = pytest.mark.gpu
 
@@ -109,10 +109,19 @@ def test_pipeline_matches_oracle_given_T():
     if close[g].all():
         assert abs(aae - a_ref) <= 1e-4 * a_ref
         assert gf.refresh().gap_updates == ref.gap_updates
+        gf.close()
     else:
-        assert close[g].mean() > 0.9
-        assert abs(aae - a_ref) <= 0.05 * a_ref
-    gf.close()
+        gf.close()
+        # chains separated after a decision flip: paired comparison over seeds
+        def run(seed):
+            g2 = GapFiller3(values_of(z, m), m, lb, seed=seed, n_max=40)
+            g2.set_temperatures(T)
+            g2.simulate(R)
+            p2, _ = g2.predict(z)
+            g2.close()
+            r2 = oracle.gapfill3(z, m, lb, R=R, seed=seed, n_max=40, T_blk=T.astype(np.float64))
+            return np.abs(p2 - z)[g].mean(), np.abs(r2.pred - z)[g].mean()
+        paired_over_seeds(run, range(22, 34))
 
 
 def test_calibration_matches_oracle():

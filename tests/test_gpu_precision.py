@@ -5,7 +5,8 @@ What must hold exactly, whatever the storage:
   * the incremental block energies equal the energies recomputed in FP64
     from the stored state (the kernels round every proposal and reflection
     to the stored type before taking its energy, and account the reflection's
-    rounding);
+    rounding), also after 200 sweeps of 64 x 64 blocks against the oracle's
+    block energy;
   * stored gap angles are values of the storage type, in [0, 2pi];
   * sample sites keep their FP32 angle bit for bit.
 What is stated, not exact: the error of the predictions against the FP64
@@ -167,3 +168,91 @@ def test_halfstep_lockstep_precision_form(storage, group, R, colour):
     assert flips <= max(3, total // 500)
     gf.sim_end()
     gf.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_energy_drift_over_200_sweeps_at_large_blocks(storage):
+    """The block energies that drive the stop test stay those of the state
+    over a long run with large blocks (l_b = 64: about 8 k bonds per block):
+    every (block, realization) pair is kept running for 200 sweeps, and the
+    incrementally summed e_b (FP32 move energies, FP64 sums) is compared with
+    the block energy the oracle computes in FP64 from the stored state.
+    Bound: each move's dE carries the error of FP32 arithmetic on hardware
+    sin/cos (|error| <~ 1e-6); over 200 sweeps of ~2.9 k gap sites per block
+    and colour the errors add like a random walk to ~1e-3 in E_b, ~1e-7 per
+    bond; the test allows 1e-6 per bond."""
+    H, W, lb, R = 128, 192, 64, 8
+    z, m = synth.small_problem(H, W, 0.7, seed=23, kind="disc")
+    gf = make(z, m, lb, seed=17, storage=STORE[storage], group=8, n_max=65535)
+    gf.set_temperatures(np.random.default_rng(4).uniform(0.05, 0.4, gf.nblk).astype(np.float32))
+    gf.sim_begin(R)
+    Es, Nsp, Nb, _, _ = gf.block_stats()
+    every = np.ones((R, gf.nblk), np.uint8)
+    for _ in range(200):
+        gf.sim_sweep(1)
+        gf.set_running(every)
+    e = gf.block_e(R)
+    o = oracle.Oracle(H, W, lb, seed=17)
+    worst = 0.0
+    for r in range(R):
+        E_o = o.block_energy(gf.get_state(r).astype(np.float64))
+        ok = Nb > 0
+        worst = max(worst, float(np.max(np.abs(e[r][ok] - E_o[ok] / Nb[ok]))))
+    gf.sim_end()
+    gf.close()
+    assert worst <= 1e-6, worst
+
+
+def test_stated_error_against_fp64_oracle_config3(record_property):
+    """The precision form's error against the FP64 oracle, stated on the
+    4096 x 4096 precision workload's recipe (lognormal non-stationary GRF,
+    correlation 4 -> 64 cells, disc gaps covering 60 %, l_b = 32, R = 10): a
+    band of 384 rows across the whole width (every correlation length). The
+    block temperatures are calibrated once on the GPU (FP32) and given to both
+    sides; each storage form runs the realizations on the GPU and the oracle
+    runs them in FP64 with the same random streams, for two seeds. Stated
+    per form: the mean |pred_gpu - pred_oracle| over the gap sites divided by
+    the value range, and the AAE and RASE differences. The FP32 form's figures
+    are the floor (chains separate where an FP32 decision flips); the 16-bit
+    forms must stay within the Monte Carlo spread: equal AAE within 1 %."""
+    import json
+    import os
+    wl = synth.workload("field4096")
+    z = np.ascontiguousarray(wl.truth[1856:2240, :])
+    m = np.ascontiguousarray(wl.mask[1856:2240, :])
+    lb, R = wl.block, wl.realizations
+    H, W = m.shape
+    cal = make(z, m, lb, seed=99, cal_points=2, n_bisect=16)
+    T = cal.calibrate()
+    cal.close()
+    g = m != 0
+    zr = float(z[~g].max() - z[~g].min())
+    out = {}
+    for seed in (901, 902):
+        ref = oracle.gapfill(z, m, lb, R=R, seed=seed, T_blk=T.astype(np.float64), threads=0)
+        a_o, r_o = oracle.Oracle.scores(ref.pred, z, m)
+        for storage in ("f32", "bf16", "f16"):
+            gf = make(z, m, lb, seed=seed, storage=STORE[storage])
+            gf.set_temperatures(T)
+            gf.simulate(R)
+            pred, (aae, rase) = gf.predict(truth=z)
+            gf.close()
+            d = out.setdefault(storage, {"pred_diff_over_range": [], "aae_diff": [],
+                                         "rase_diff": [], "aae_oracle": []})
+            d["pred_diff_over_range"].append(float(np.abs(pred[g] - ref.pred[g]).mean() / zr))
+            d["aae_diff"].append(float(aae - a_o))
+            d["rase_diff"].append(float(rase - r_o))
+            d["aae_oracle"].append(float(a_o))
+    for storage, d in out.items():
+        for k, v in d.items():
+            record_property(f"{storage}_{k}", float(np.mean(v)))
+    rec = os.environ.get("MPR_RECORD_DIR")
+    if rec:
+        os.makedirs(rec, exist_ok=True)
+        with open(os.path.join(rec, "precision_error_field4096.json"), "w") as f:
+            json.dump({"workload": f"{wl.name} rows 1856-2239 (384 x 4096)", "R": R,
+                       "seeds": [901, 902], "forms": out}, f, indent=1)
+    for storage in ("bf16", "f16"):
+        d = out[storage]
+        assert abs(np.mean(d["aae_diff"])) <= 0.01 * np.mean(d["aae_oracle"])
+        assert np.mean(d["pred_diff_over_range"]) < 0.02

@@ -12,7 +12,7 @@ import oracle
 from paper_2212_01317_gb300 import synth
 from paper_2212_01317_gb300.mpr import GapFiller, MprError
 
-from parity import TWO_PI, checkerboard, compare_site_updates
+from parity import TWO_PI, checkerboard, compare_site_updates, paired_over_seeds
 
 pytestmark = pytest.mark.gpu
 
@@ -103,12 +103,22 @@ def test_pipeline_matches_oracle_with_sst(group):
     g = m != 0
     scale = gf.info.zmax - gf.info.zmin
     close = np.abs(pred - ref.pred) <= 1e-4 * scale
+    gf.close()
     if close[g].all():
         assert abs(aae - a_ref) <= 1e-4 * a_ref and abs(rase - r_ref) <= 1e-4 * r_ref
     else:
-        assert close[g].mean() > 0.9
-        assert abs(aae - a_ref) <= 0.05 * a_ref
-    gf.close()
+        # chains separated after a decision flip: paired comparison over seeds
+        def run(seed):
+            g2 = make(z, m, lb, seed=seed, group=group, n_max=60)
+            g2.set_temperatures(T)
+            g2.smooth_temperatures(4, 5)
+            g2.simulate(R)
+            _, (a2, _) = g2.predict(truth=z)
+            g2.close()
+            r2 = oracle.gapfill(z, m, lb, R=R, seed=seed, T_blk=T.astype(np.float64), n_max=60,
+                                sst=(4, 5))
+            return a2, oracle.Oracle.scores(r2.pred, z, m)[0]
+        paired_over_seeds(run, range(78, 90))
 
 
 def test_sst_state_rules():

@@ -121,12 +121,17 @@ def test_newton_finds_the_exact_root():
             hi = mid
     T_star = 0.5 * (lo + hi)
     phi0 = o.init_block_mean(phi, mask, st)
-    T, tr = o.calibrate_newton(phi0, mask, st, n_eq=10, n_meas=60, n_newton=8, chains=16,
+    T, tr = o.calibrate_newton(phi0, mask, st, n_eq=10, n_meas=60, n_newton=8, chains=64,
                                T0=0.1, trace=True)
     assert abs(T[0] - T_star) / T_star < 0.03, (T[0], T_star, tr[:, 0])
     # Newton steps converge fast: the last three iterates agree within the
-    # Monte Carlo noise of one iteration's estimate (a few per cent).
-    assert np.ptp(tr[-3:, 0]) / T_star < 0.06
+    # Monte Carlo noise of one iteration's estimate. One iterate's spread is
+    # sigma_T = T*^2 / sqrt(n Var(E_b)) times sqrt(tau) (the fluctuation
+    # identity turns the noise of the measured mean energy into noise of T;
+    # n = 64 chains x 60 sweeps; tau, the energy's autocorrelation time,
+    # a few sweeps): about 0.5 % x sqrt(tau) here, so 4 % holds the range of
+    # three iterates with a wide margin.
+    assert np.ptp(tr[-3:, 0]) / T_star < 0.04
     # every step stays within a factor 2 of the previous temperature
     r = tr[1:, 0] / tr[:-1, 0]
     assert np.all((r >= 0.5 - 1e-12) & (r <= 2 + 1e-12))
