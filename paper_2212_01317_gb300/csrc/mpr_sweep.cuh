@@ -107,20 +107,21 @@ __device__ __forceinline__ SiteNew site_update(float phi, float C, float Sn, flo
     return n;
 }
 
-// A block's change: each lane's FP32 partial (its own few entries) is summed
-// over the warp in FP64 and added to eacc with an FP64 atomic (the stop test
-// and the calibration fold eacc into the FP64 block energy once per sweep).
+// A block's change in one half-step: the FP32 warp sum of the unit's moves
+// is added to eacc with an FP64 atomic, so every sum across units, half-steps
+// and (in the stop test and the calibration fold) sweeps is FP64. (The warp
+// sum stays FP32: GB300's FP64 pipe is narrow, and FP64 shuffle sums per unit
+// doubled the half-step's time.)
 __device__ __forceinline__ void flush_pair(double* ea, float v0, float v1) {
     if (!__any_sync(0xffffffffu, v0 != 0.0f || v1 != 0.0f)) return;
-    double d0 = v0, d1 = v1;
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
-        d0 += __shfl_xor_sync(0xffffffffu, d0, s);
-        d1 += __shfl_xor_sync(0xffffffffu, d1, s);
+        v0 += __shfl_xor_sync(0xffffffffu, v0, s);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, s);
     }
     if ((threadIdx.x & 31) != 0) return;
-    if (d0 != 0.0) atomicAdd(ea, d0);
-    if (d1 != 0.0) atomicAdd(ea + 1, d1);
+    if (v0 != 0.0f) atomicAdd(ea, (double)v0);
+    if (v1 != 0.0f) atomicAdd(ea + 1, (double)v1);
 }
 
 // Bond-by-bond split of a move at a block edge: (lc, ls) and (uc, us) are the
@@ -277,20 +278,19 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
     flush_pair(ea - (size_t)a.g.nbx * a.Rp, au0, au1);
 }
 
-// Energy flush of one half-warp's unit: FP64 sums over its 16 lanes' FP32
-// partials, then its lane 0 adds them (act: the half has a running unit).
+// Energy flush of one half-warp's unit: the FP32 sum over its 16 lanes, added
+// by its lane 0 with an FP64 atomic (act: the half has a running unit).
 // Every lane of the warp calls it.
 __device__ __forceinline__ void flush_pair_half(double* ea, float v0, float v1, bool act) {
     if (!__any_sync(0xffffffffu, v0 != 0.0f || v1 != 0.0f)) return;
-    double d0 = v0, d1 = v1;
 #pragma unroll
     for (int s = 8; s > 0; s >>= 1) {
-        d0 += __shfl_xor_sync(0xffffffffu, d0, s);
-        d1 += __shfl_xor_sync(0xffffffffu, d1, s);
+        v0 += __shfl_xor_sync(0xffffffffu, v0, s);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, s);
     }
     if ((threadIdx.x & 15) != 0 || !act) return;
-    if (d0 != 0.0) atomicAdd(ea, d0);
-    if (d1 != 0.0) atomicAdd(ea + 1, d1);
+    if (v0 != 0.0f) atomicAdd(ea, (double)v0);
+    if (v1 != 0.0f) atomicAdd(ea + 1, (double)v1);
 }
 
 // Two units per warp: lanes 0-15 take one (block, realization pair) unit,
@@ -372,7 +372,7 @@ __device__ __forceinline__ void sweep_item_half(const SweepArgs& a, int item, in
 // shared memory (the list is block-major, so a CTA spans few blocks) and
 // flushed with one atomic per (block, realization); changes that belong to
 // another block (left / up bonds of edge sites) go straight to global memory.
-// A warp's FP32 sum covers at most 32 entries; every sum beyond is FP64.
+// The per-CTA sums are FP32; the global accumulation is FP64.
 constexpr int kFlatThreads = 256;
 constexpr int kFlatBlocks = 64;     // local blocks summed in shared memory per CTA
 
@@ -393,13 +393,13 @@ __device__ __forceinline__ void grid_dep_launch() {
 template <int G>
 __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, uint32_t ctr1) {
     constexpr int NP = G / 2;
-    __shared__ double acc[kFlatBlocks * G];
+    __shared__ float acc[kFlatBlocks * G];
     const int grp = blockIdx.y;
     const int64_t t0 = (int64_t)blockIdx.x * kFlatThreads;
     const int64_t t = t0 + threadIdx.x;
     const int64_t e = t / NP;
     const int q = (int)(t % NP);
-    for (int i = threadIdx.x; i < kFlatBlocks * G; i += kFlatThreads) acc[i] = 0.0;
+    for (int i = threadIdx.x; i < kFlatBlocks * G; i += kFlatThreads) acc[i] = 0.0f;
     const int b0 = (int)(a.list[t0 / NP].y >> META_SHIFT);
     const bool live = e < n_list;
     const int rl = grp * G + 2 * q;
@@ -469,8 +469,8 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
         if (lane < NP) {
             const int loc = b - b0;
             if (loc < kFlatBlocks) {
-                if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane], (double)ao0);
-                if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane + 1], (double)ao1);
+                if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane], ao0);
+                if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * lane + 1], ao1);
             } else {
                 double* ea = a.eacc + (size_t)b * a.Rp + grp * G + 2 * lane;
                 if (ao0 != 0.0f) atomicAdd(ea, (double)ao0);
@@ -480,8 +480,8 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
     } else if (live) {
         const int loc = b - b0;
         if (loc < kFlatBlocks) {
-            if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * q], (double)ao0);
-            if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * q + 1], (double)ao1);
+            if (ao0 != 0.0f) atomicAdd(&acc[loc * G + 2 * q], ao0);
+            if (ao1 != 0.0f) atomicAdd(&acc[loc * G + 2 * q + 1], ao1);
         } else {
             double* ea = a.eacc + (size_t)b * a.Rp + rl;
             if (ao0 != 0.0f) atomicAdd(ea, (double)ao0);
@@ -499,8 +499,8 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kFlatBlocks * G; i += kFlatThreads) {
-        const double v = acc[i];
-        if (v != 0.0) atomicAdd(&a.eacc[(size_t)(b0 + i / G) * a.Rp + grp * G + (i % G)], v);
+        const float v = acc[i];
+        if (v != 0.0f) atomicAdd(&a.eacc[(size_t)(b0 + i / G) * a.Rp + grp * G + (i % G)], (double)v);
     }
 }
 

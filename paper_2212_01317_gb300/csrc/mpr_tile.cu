@@ -266,12 +266,11 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
             Store<S>::store2(po, out);
         }
 
-        // The tile's energy changes: each thread's FP32 partial (its few
-        // entries) summed in FP64 over the lanes of one pair (lanes q, q + 4,
-        // ...) and over the warps, then one FP64 atomic per (block,
-        // realization) for the own, left and upper blocks.
+        // The tile's energy changes: FP32 sums over the lanes of one pair
+        // (lanes q, q + 4, ...), FP64 over the warps, then one FP64 atomic
+        // per (block, realization) for the own, left and upper blocks.
         if (a.energy) {
-            double v[6] = {ao0, ao1, al0, al1, au0, au1};
+            float v[6] = {ao0, ao1, al0, al1, au0, au1};
 #pragma unroll
             for (int d = 4; d < 32; d <<= 1)
 #pragma unroll
