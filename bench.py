@@ -902,6 +902,14 @@ def run_ours_batch(args, world, rank, local):
         "clocks": clk,
         "e2e": e2e,
     }
+    # The storage forms' error against the FP64 oracle, measured on the
+    # 4096^2 precision workload's recipe by the GPU test suite
+    # (profiles/precision_error.json): mean |pred - pred_oracle| / value
+    # range and the AAE / RASE differences per form.
+    ppath = os.path.join(ROOT, "profiles", "precision_error.json")
+    if os.path.exists(ppath):
+        with open(ppath) as f:
+            line["precision_error"] = json.load(f)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"], _ = oracle_batch_leg(args, 1, None, args.cpu_seconds,
                                                    len(os.sched_getaffinity(0)))

@@ -156,7 +156,7 @@ template <typename S>
 __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
     grid_dep_launch();
     __shared__ float4 stage[kStageSites * 4];       // [site][pair]: (c0, s0, c1, s1)
-    __shared__ double red[kTileWarps][4][6];
+    __shared__ float red[kTileWarps][4][6];
     grid_dep_wait();
     constexpr int G = 8;
     const Geom& g = a.g;
@@ -267,8 +267,8 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
         }
 
         // The tile's energy changes: FP32 sums over the lanes of one pair
-        // (lanes q, q + 4, ...), FP64 over the warps, then one FP64 atomic
-        // per (block, realization) for the own, left and upper blocks.
+        // (lanes q, q + 4, ...) and over the warps, then one FP64 atomic per
+        // (block, realization) for the own, left and upper blocks.
         if (a.energy) {
             float v[6] = {ao0, ao1, al0, al1, au0, au1};
 #pragma unroll
@@ -281,18 +281,18 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
             __syncthreads();
             if (threadIdx.x < 4) {
                 const int q = threadIdx.x;
-                double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 for (int w = 0; w < kTileWarps; ++w)
 #pragma unroll
                     for (int k = 0; k < 6; ++k) s[k] += red[w][q][k];
                 double* ea = a.eacc + (size_t)b * a.Rp + grp * G + 2 * q;
                 const size_t up = (size_t)g.nbx * a.Rp;
-                if (s[0] != 0.0) atomicAdd(ea, s[0]);
-                if (s[1] != 0.0) atomicAdd(ea + 1, s[1]);
-                if (s[2] != 0.0) atomicAdd(ea - a.Rp, s[2]);
-                if (s[3] != 0.0) atomicAdd(ea - a.Rp + 1, s[3]);
-                if (s[4] != 0.0) atomicAdd(ea - up, s[4]);
-                if (s[5] != 0.0) atomicAdd(ea - up + 1, s[5]);
+                if (s[0] != 0.0f) atomicAdd(ea, (double)s[0]);
+                if (s[1] != 0.0f) atomicAdd(ea + 1, (double)s[1]);
+                if (s[2] != 0.0f) atomicAdd(ea - a.Rp, (double)s[2]);
+                if (s[3] != 0.0f) atomicAdd(ea - a.Rp + 1, (double)s[3]);
+                if (s[4] != 0.0f) atomicAdd(ea - up, (double)s[4]);
+                if (s[5] != 0.0f) atomicAdd(ea - up + 1, (double)s[5]);
             }
         }
         __syncthreads();   // the next item restages
