@@ -74,6 +74,10 @@ def parse(argv=None):
                     help="batch workloads: the sweep loop as one CUDA graph")
     ap.add_argument("--sweep-form", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="realizations' half-step form (-1 automatic; 4 the staged half-step)")
+    ap.add_argument("--autotune", type=int, default=16,
+                    help="batch workloads: every step times the half-step decompositions on a "
+                         "trial batch of this many realizations (one sweep) before simulating, "
+                         "inside the timed step (0: off)")
     ap.add_argument("--calibration", default="bisection", choices=["bisection", "newton"],
                     help="per-block temperature fit: bisection (the plain form) or safeguarded "
                          "Newton steps from the fluctuation identity")
@@ -702,6 +706,10 @@ def run_ours_batch(args, world, rank, local):
         ctx = mpr.mpr_create_batch(grids, masks, values, options(profile, seed))
         try:
             mpr.mpr_calibrate(ctx, None)
+            tune = None
+            if args.autotune > 0 and args.sweep_form < 0:
+                tune = mpr.mpr_autotune(ctx, min(args.autotune, R), 1)
+                tunes.append(tune)
             ev = (timed_event(), timed_event())
             ev[0].record(stream)
             mpr.mpr_simulate(ctx, R)
@@ -713,6 +721,8 @@ def run_ours_batch(args, world, rank, local):
         finally:
             mpr.mpr_destroy(ctx)
         return info, prof, ev, (None if ar is None else ar[0::2])
+
+    tunes = []
 
     def plain_step(seed):
         """One step of the plain form: every field alone, FP32, in turn (field j
@@ -747,10 +757,12 @@ def run_ours_batch(args, world, rank, local):
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
+    tunes.clear()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     step_ms, sim_evs, aae_c = [], [], []
+    n_tunes_timed = 0
     sim_updates = cal_updates = launches = sim_launch = tail_updates = tail_launch = 0
     hs_ms = tail_ms = cal_ms = 0.0
     for k in range(args.steps):
@@ -763,6 +775,7 @@ def run_ours_batch(args, world, rank, local):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         sim_evs.append(ev)
+        n_tunes_timed = len(tunes)
         aae_c.append(float(np.dot(aae, ngap) / P))
         sim_updates += info.gap_updates
         cal_updates += info.cal_gap_updates
@@ -862,6 +875,21 @@ def run_ours_batch(args, world, rank, local):
             dist.destroy_process_group()
         return
     peak, peak_kind = measured_peaks()
+    # The shape the per-step autotuner chose (timed steps only) and its cost,
+    # which is inside the steps' time.
+    autotune = None
+    timed_tunes = tunes[:n_tunes_timed]
+    if timed_tunes:
+        names = ["G8 one warp per pair", "G8 two pairs per warp", "G8 staged tiles",
+                 "G2 one warp per pair"]
+        last = timed_tunes[-1]
+        autotune = {"chosen": {"group": last.group, "form": last.form,
+                               "name": names[[(8, 0), (8, 3), (8, 4), (2, 0)].index(
+                                   (last.group, last.form))]},
+                    "candidates_ms": {names[k]: float(np.mean([t.ms[k] for t in timed_tunes]))
+                                      for k in range(4)},
+                    "trial_ms_per_step": float(np.mean([t.trial_ms for t in timed_tunes])),
+                    "trial": f"{min(args.autotune, R)} realizations, one sweep, every field"}
     p_mean = P / bw.n_sites
     bpu = bytes_per_gap_update(4.0 if storage == "f32" else 2.0, p_mean)
     # The realizations' per-launch half-steps ran every update but those of the
@@ -897,6 +925,7 @@ def run_ours_batch(args, world, rank, local):
         "simulate_ms_per_step": simulate_ms / args.steps,
         "gap_sites": P,
         "plain_form": plain, "fixed_mae": fixed_mae, "chosen_vs_plain": chosen_vs_plain,
+        "autotune": autotune,
         "gpu_launches": int(launches),
         "roofline": roofline,
         "clocks": clk,

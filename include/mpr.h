@@ -306,21 +306,26 @@ mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n_realizations);
 mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae_rase);
 
 /* ---- launch-shape autotuning ----
- * mpr_autotune times the sweep kernel's work decompositions on trial batches
- * of n_realizations realizations (their first n_sweeps sweeps, every block
- * running, CUDA events on the context's stream) and keeps the fastest for
- * the context's later simulations: lane-group width G (2 or 8 realizations
- * interleaved per site) and the sweep form (four warps per item of G = 8 /
- * one warp per item of G = 2, or the wide form with four times as many
- * warps per item). The results do not depend on the choice (the random
- * streams are keyed by realization, not by lane). The trial batches are
- * discarded: nothing is accumulated or counted. Needs temperatures; no batch
- * may be open. out->ms[k]: time of candidate k = (2, normal), (2, wide),
- * (8, normal), (8, wide). Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+ * mpr_autotune times the realizations' half-step decompositions on trial
+ * batches of n_realizations realizations (their first n_sweeps sweeps, every
+ * block running, CUDA events on the context's stream) and keeps the fastest
+ * for the context's later simulations (sweep_form = -1; once few pairs run,
+ * the four-warps-per-pair form still takes over). Candidates k:
+ *   0: G = 8, one warp per (block, realization pair) unit (sweep form 0);
+ *   1: G = 8, two units per warp (form 3);
+ *   2: G = 8, the staged half-step on tiles of at most 16 x 32 sites (form 4);
+ *   3: G = 2, one warp per unit (form 0).
+ * G is the lane-group width (realizations interleaved per site). The results
+ * do not depend on the choice (the random streams are keyed by realization,
+ * not by lane or form). The trial batches are discarded: nothing is
+ * accumulated or counted. Needs temperatures; no batch may be open.
+ * out->ms[k]: time of candidate k; out->trial_ms: the whole call.
+ * Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
 typedef struct {
     int32_t group;   /* chosen lane-group width */
-    int32_t wide;    /* 1: the wide form for every sweep */
+    int32_t form;    /* chosen half-step form (0, 3 or 4) */
     float ms[4];     /* timed candidates */
+    float trial_ms;  /* device time of all trial batches */
 } mpr_tuning;
 mpr_status mpr_autotune(mpr_ctx* ctx, int32_t n_realizations, int32_t n_sweeps, mpr_tuning* out);
 

@@ -118,7 +118,8 @@ struct mpr_ctx {
     int tile_grid = 0;             // resident CTAs of the staged kernel (by storage at build)
     int tile_grid_storage = -1;
     unsigned long long bound = ~0ull;  // upper bound of the running pairs (from the last read)
-    int wide_always = 0;         // autotuned: the wide sweep form for every sweep
+    int tuned_form = -1;         // autotuned half-step form (-1: the built-in choice)
+    bool tuning_tiles = false;   // an autotune trial of the staged form is running
     bool energy_dirty = false;
     GridBarrier* bar = nullptr;  // grid barrier of the persistent calibration
     float* med = nullptr;
@@ -349,8 +350,10 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
 // The staged half-step (form 4) needs lane groups of eight and its tiles.
 bool tile_form_ok(const mpr_ctx* ctx) { return ctx->G == 8 && ctx->tiles.n > 0; }
 
-// The options ask for the staged half-step.
-bool tiles_wanted(const mpr_ctx* ctx) { return ctx->opt.sweep_form == 4; }
+// The options, the autotuner's choice or its trial ask for the staged half-step.
+bool tiles_wanted(const mpr_ctx* ctx) {
+    return ctx->opt.sweep_form == 4 || ctx->tuned_form == 4 || ctx->tuning_tiles;
+}
 
 // Tiles, tile-major lists and staging table of the staged half-step, built
 // once per context.
@@ -405,8 +408,9 @@ constexpr double kHalfFormEntries = 96.0;
 int sweep_form(mpr_ctx* ctx) {
     if (ctx->opt.sweep_form == 4) return tile_form_ok(ctx) ? 4 : 0;
     if (ctx->opt.sweep_form >= 0) return ctx->opt.sweep_form;
-    if (ctx->wide_always) return 2;
     if (ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm) return 2;
+    if (ctx->tuned_form == 4) return tile_form_ok(ctx) ? 4 : 0;
+    if (ctx->tuned_form >= 0) return ctx->tuned_form;
     const double per_block = (double)(ctx->n_gap[0] + ctx->n_gap[1]) / (2.0 * ctx->g.nblk);
     return per_block <= kHalfFormEntries ? 3 : 0;
 }
@@ -2097,22 +2101,32 @@ mpr_status mpr_autotune(mpr_ctx* ctx, int32_t n_realizations, int32_t n_sweeps,
     if (n_realizations < 1 || n_sweeps < 1 || n_sweeps > 64)
         return fail(ctx, MPR_EINVAL, "need n_realizations >= 1 and 1 <= n_sweeps <= 64");
     std::memset(out, 0, sizeof(*out));
-    const int saved_group = ctx->opt.group, saved_wide = ctx->wide_always;
+    const int saved_group = ctx->opt.group, saved_form = ctx->tuned_form;
     const int saved_profile = ctx->opt.profile;
     const int64_t saved[4] = {ctx->gap_updates, ctx->launches, ctx->sim_halfstep_launches,
                               ctx->realizations};
-    const int cand[4][2] = {{2, 0}, {2, 1}, {8, 0}, {8, 1}};
+    const int cand[4][2] = {{8, 0}, {8, 3}, {8, 4}, {2, 0}};
     float best = 0.0f;
     int best_k = -1;
     mpr_status st = MPR_OK;
     ctx->opt.profile = 0;
+    cudaEvent_t t0 = get_event(ctx), t1 = get_event(ctx);
+    if (!t0 || !t1) return fail(ctx, MPR_ECUDA, "cudaEventCreate failed");
+    cudaEventRecord(t0, ctx->s);
     for (int k = 0; k < 4 && st == MPR_OK; ++k) {
         ctx->opt.group = cand[k][0];
-        ctx->wide_always = cand[k][1];
+        ctx->tuned_form = cand[k][1];
+        ctx->tuning_tiles = cand[k][1] == 4;
         // A trial batch: the first sweeps (every pair running), timed on the
         // stream; discarded afterwards (nothing is accumulated or counted).
         st = mpr_sim_begin(ctx, n_realizations);
+        ctx->tuning_tiles = false;
         if (st != MPR_OK) break;
+        if (cand[k][1] == 4 && !tile_form_ok(ctx)) {   // (lane groups of two: no staged form)
+            ctx->batch_open = 0;
+            out->ms[k] = -1.0f;
+            continue;
+        }
         cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
         if (!e0 || !e1) { st = fail(ctx, MPR_ECUDA, "cudaEventCreate failed"); break; }
         cudaEventRecord(e0, ctx->s);
@@ -2127,21 +2141,26 @@ mpr_status mpr_autotune(mpr_ctx* ctx, int32_t n_realizations, int32_t n_sweeps,
         out->ms[k] = ms;
         if (st == MPR_OK && (best_k < 0 || ms < best)) { best = ms; best_k = k; }
     }
+    cudaEventRecord(t1, ctx->s);
+    if (cudaEventSynchronize(t1) == cudaSuccess) cudaEventElapsedTime(&out->trial_ms, t0, t1);
+    else cudaGetLastError();
+    ctx->ev_pool.push_back(t0);
+    ctx->ev_pool.push_back(t1);
     ctx->opt.profile = saved_profile;
     ctx->gap_updates = saved[0];
     ctx->launches = saved[1];
     ctx->sim_halfstep_launches = saved[2];
     ctx->realizations = saved[3];
     ctx->chains_valid = false;
-    if (st != MPR_OK) {
+    if (st != MPR_OK || best_k < 0) {
         ctx->opt.group = saved_group;
-        ctx->wide_always = saved_wide;
-        return st;
+        ctx->tuned_form = saved_form;
+        return st != MPR_OK ? st : fail(ctx, MPR_ECUDA, "autotune: no candidate ran");
     }
     ctx->opt.group = cand[best_k][0];
-    ctx->wide_always = cand[best_k][1];
+    ctx->tuned_form = cand[best_k][1];
     out->group = cand[best_k][0];
-    out->wide = cand[best_k][1];
+    out->form = cand[best_k][1];
     return MPR_OK;
 }
 

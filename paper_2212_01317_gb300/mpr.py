@@ -72,7 +72,8 @@ class mpr3_info(C.Structure):
 
 
 class mpr_tuning(C.Structure):
-    _fields_ = [("group", C.c_int32), ("wide", C.c_int32), ("ms", C.c_float * 4)]
+    _fields_ = [("group", C.c_int32), ("form", C.c_int32), ("ms", C.c_float * 4),
+                ("trial_ms", C.c_float)]
 
 
 class mpr_info(C.Structure):

@@ -181,8 +181,8 @@ def test_autotune_picks_a_candidate_and_keeps_results():
         gf.set_temperatures(T)
         if tune:
             t = mpr.mpr_autotune(gf.ctx, 12, 3)
-            assert (t.group, t.wide) in {(2, 0), (2, 1), (8, 0), (8, 1)}
-            assert all(x > 0 for x in t.ms)
+            assert (t.group, t.form) in {(8, 0), (8, 3), (8, 4), (2, 0)}
+            assert all(x > 0 for x in t.ms) and t.trial_ms >= sum(t.ms)
             assert gf.refresh().realizations == 0 and gf.info.gap_updates == 0
         gf.simulate(12)
         preds.append(gf.predict()[0])
