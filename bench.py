@@ -74,10 +74,11 @@ def parse(argv=None):
                     help="batch workloads: the sweep loop as one CUDA graph")
     ap.add_argument("--sweep-form", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="realizations' half-step form (-1 automatic; 4 the staged half-step)")
-    ap.add_argument("--autotune", type=int, default=16,
-                    help="batch workloads: every step times the half-step decompositions on a "
-                         "trial batch of this many realizations (one sweep) before simulating, "
-                         "inside the timed step (0: off)")
+    ap.add_argument("--autotune", type=int, default=2,
+                    help="batch workloads: the first warm-up step times the half-step "
+                         "decompositions on a trial batch of all R realizations over this many "
+                         "sweeps (mpr_autotune) and the timed steps run the chosen one (0: off, "
+                         "the library's built-in choice)")
     ap.add_argument("--calibration", default="bisection", choices=["bisection", "newton"],
                     help="per-block temperature fit: bisection (the plain form) or safeguarded "
                          "Newton steps from the fluctuation identity")
@@ -689,12 +690,15 @@ def run_ours_batch(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     seed_base = SEED0 + 7919 * rank
 
+    tuned = {"group": 0, "bulk": -1}
+
     def options(profile, seed, st=storage, slice_id=0):
         return mpr.mpr_default_options(seed=seed, slice_id=slice_id, profile=profile,
                                        storage=STORAGE[st], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
                                        sim_graph=args.sim_graph, sweep_form=args.sweep_form,
+                                       sweep_form_bulk=tuned["bulk"], group=tuned["group"],
                                        cuda_stream=stream.cuda_stream)
 
     def timed_event():
@@ -706,10 +710,11 @@ def run_ours_batch(args, world, rank, local):
         ctx = mpr.mpr_create_batch(grids, masks, values, options(profile, seed))
         try:
             mpr.mpr_calibrate(ctx, None)
-            tune = None
-            if args.autotune > 0 and args.sweep_form < 0:
-                tune = mpr.mpr_autotune(ctx, min(args.autotune, R), 1)
-                tunes.append(tune)
+            if args.autotune > 0 and args.sweep_form < 0 and not tunes:
+                # once, in the first warm-up step: later steps run the choice
+                t = mpr.mpr_autotune(ctx, R, args.autotune)
+                tunes.append(t)
+                tuned["group"], tuned["bulk"] = t.group, t.form
             ev = (timed_event(), timed_event())
             ev[0].record(stream)
             mpr.mpr_simulate(ctx, R)
@@ -757,12 +762,10 @@ def run_ours_batch(args, world, rank, local):
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    tunes.clear()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     step_ms, sim_evs, aae_c = [], [], []
-    n_tunes_timed = 0
     sim_updates = cal_updates = launches = sim_launch = tail_updates = tail_launch = 0
     hs_ms = tail_ms = cal_ms = 0.0
     for k in range(args.steps):
@@ -775,7 +778,6 @@ def run_ours_batch(args, world, rank, local):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         sim_evs.append(ev)
-        n_tunes_timed = len(tunes)
         aae_c.append(float(np.dot(aae, ngap) / P))
         sim_updates += info.gap_updates
         cal_updates += info.cal_gap_updates
@@ -875,21 +877,20 @@ def run_ours_batch(args, world, rank, local):
             dist.destroy_process_group()
         return
     peak, peak_kind = measured_peaks()
-    # The shape the per-step autotuner chose (timed steps only) and its cost,
-    # which is inside the steps' time.
+    # The shape the autotuner chose in the first warm-up step (the timed steps
+    # run it) and the cost of its trial batches.
     autotune = None
-    timed_tunes = tunes[:n_tunes_timed]
-    if timed_tunes:
+    if tunes:
         names = ["G8 one warp per pair", "G8 two pairs per warp", "G8 staged tiles",
                  "G2 one warp per pair"]
-        last = timed_tunes[-1]
-        autotune = {"chosen": {"group": last.group, "form": last.form,
+        t = tunes[0]
+        autotune = {"chosen": {"group": t.group, "form": t.form,
                                "name": names[[(8, 0), (8, 3), (8, 4), (2, 0)].index(
-                                   (last.group, last.form))]},
-                    "candidates_ms": {names[k]: float(np.mean([t.ms[k] for t in timed_tunes]))
-                                      for k in range(4)},
-                    "trial_ms_per_step": float(np.mean([t.trial_ms for t in timed_tunes])),
-                    "trial": f"{min(args.autotune, R)} realizations, one sweep, every field"}
+                                   (t.group, t.form))]},
+                    "candidates_ms": {names[k]: float(t.ms[k]) for k in range(4)},
+                    "trial_ms": float(t.trial_ms),
+                    "trial": f"all {R} realizations of every field, the first {args.autotune} "
+                             "sweeps per candidate, once before the timed steps"}
     p_mean = P / bw.n_sites
     bpu = bytes_per_gap_update(4.0 if storage == "f32" else 2.0, p_mean)
     # The realizations' per-launch half-steps ran every update but those of the

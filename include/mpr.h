@@ -52,6 +52,14 @@ typedef enum {
 
 typedef enum { MPR_STORE_F32 = 0, MPR_STORE_BF16 = 1, MPR_STORE_F16 = 2 } mpr_storage;
 typedef enum { MPR_INIT_BLOCK_MEAN = 0, MPR_INIT_RANDOM = 1 } mpr_init;
+/* Local-equilibrium stop of a (block, realization) pair (Sec. 3.4):
+ * CROSS: the first sweep t >= 1 at which the block's specific energy e_b(t)
+ *   has reached e_s,b from the side it started on;
+ * WINDOW: from sweep n_fit + n_f on, every n_f sweeps, the least-squares
+ *   slope of e_b over the last n_fit sweeps is tested; the block stops once
+ *   the slope no longer points from e_b(0) towards e_s,b (the drift has
+ *   ended). Blocks without sample bonds follow the closing rule in both. */
+typedef enum { MPR_STOP_CROSS = 0, MPR_STOP_WINDOW = 1 } mpr_stop_rule;
 
 typedef struct {
     int32_t height, width; /* H, W >= 1, each <= 32768 */
@@ -118,6 +126,16 @@ typedef struct {
                             barriers between the phases); 0: never; values above 4096 act as
                             4096 (the default: 0.65 ms of 23.8 ms saved per 1024^2 bench step);
                             sim_tail > 0 takes precedence */
+    int32_t sweep_form_bulk; /* with sweep_form = -1: the half-step form while many pairs run
+                                (-1 the built-in choice by gap sites per block, else 0, 3 or 4
+                                as in sweep_form, e.g. an earlier mpr_autotune's choice); the
+                                switch to four warps per pair late in a batch still applies */
+    int32_t stop_rule;   /* mpr_stop_rule (default MPR_STOP_CROSS) */
+    int32_t n_fit;       /* MPR_STOP_WINDOW: sweeps in the least-squares window (default 20) */
+    int32_t n_f;         /* MPR_STOP_WINDOW: sweeps between two window tests (default 5) */
+    int32_t cal_warm;    /* 1: the calibration bracket of each block starts around the
+                            temperature of the unconditional e(T) curve at e_s,b (Sec. 2.1 energy
+                            matching of the data-free lattice) instead of [t_lo, t_hi] (default 0) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 

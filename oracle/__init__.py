@@ -47,7 +47,8 @@ class Model(C.Structure):
                 ("key0", C.c_uint32), ("key1", C.c_uint32),
                 ("overrelax", C.c_int32), ("K", C.c_int32), ("threads", C.c_int32),
                 ("T_site", C.c_void_p), ("D", C.c_int32), ("nbz", C.c_int32),
-                ("storage", C.c_int32)]
+                ("storage", C.c_int32), ("stop_rule", C.c_int32), ("n_fit", C.c_int32),
+                ("n_f", C.c_int32)]
 
 
 class Diag(C.Structure):
@@ -90,6 +91,8 @@ def lib():
             "orc_simulate_one": (C.c_int, [MP, P, P, P, P, P, P, P, i32, u32, P, P]),
             "orc_stop_init": (None, [MP, P, P, P, P, P, P, P, P]),
             "orc_stop_update": (C.c_int, [MP, i32, i32, P, P, P, P, P, P, P]),
+            "orc_stop_update_window": (C.c_int, [MP, i32, i32, P, P, P, P, P, P]),
+            "orc_window_slope": (f64, [MP, i32, P, C.c_int]),
             "orc_calibrate": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, f64, f64, P, P]),
             "orc_median_targeted": (f64, [i32, P, P]),
             "orc_scores": (None, [i64, P, P, P, P, P]),
@@ -160,13 +163,17 @@ class Oracle:
 
     def __init__(self, H: int, W: int, lb: int, q: float = 0.5, J: float = 1.0,
                  seed: int = 0, slice_id: int = 0, overrelax: bool = True, K: int = 0,
-                 threads: int = 0, storage: int = 0):
+                 threads: int = 0, storage: int = 0, stop_rule: int = 0, n_fit: int = 20,
+                 n_f: int = 5):
         self.m = Model()
         lib().orc_model_init(C.byref(self.m), H, W, lb, q, J, seed & (2**64 - 1), slice_id)
         self.m.overrelax = 1 if overrelax else 0
         self.m.K = int(K)
         self.m.threads = int(threads)
         self.m.storage = int(storage)     # 0 exact, 1 BF16, 2 FP16 stored gap angles
+        self.m.stop_rule = int(stop_rule)  # 0 CROSS, 1 WINDOW (Sec. 3.4 n_fit, n_f)
+        self.m.n_fit = int(n_fit)
+        self.m.n_f = int(n_f)
         self.H, self.W, self.lb = H, W, lb
 
     @property
@@ -290,6 +297,16 @@ class Oracle:
         E = np.ascontiguousarray(E, dtype=np.float64)
         return lib().orc_stop_update(C.byref(self.m), t, n_max, _p(E), _p(st.Es), _p(st.Nsp),
                                      _p(st.Nb), _p(sigma), _p(active), _p(stop))
+
+    def stop_update_window(self, t, n_max, st: BlockStats, sigma, hist, active, stop) -> int:
+        """hist: [n_fit, nblk] ring of e_b by sweep mod n_fit (e_b(t) written)."""
+        hist = np.ascontiguousarray(hist, dtype=np.float64)
+        return lib().orc_stop_update_window(C.byref(self.m), t, n_max, _p(st.Es), _p(st.Nsp),
+                                            _p(sigma), _p(hist), _p(active), _p(stop))
+
+    def window_slope(self, t, hist, b) -> float:
+        hist = np.ascontiguousarray(hist, dtype=np.float64)
+        return lib().orc_window_slope(C.byref(self.m), t, _p(hist), int(b))
 
     def simulate_one(self, phi0, mask, T_blk, st: BlockStats, n_max: int, r: int,
                      trace: bool = False):
@@ -491,7 +508,8 @@ def gapfill(values, mask, lb: int, R: int, seed: int = 0, slice_id: int = 0, q: 
             J: float = 1.0, n_max: int = 200, n_eq: int = 25, n_meas: int = 20,
             n_bisect: int = 24, chains: int = 1, T_lo: float = 1e-4, T_hi: float = 2.0,
             T_blk=None, overrelax: bool = True, threads: int = 0,
-            r0: int = 0, sst=None) -> GapfillResult:
+            r0: int = 0, sst=None, stop_rule: int = 0, n_fit: int = 20,
+            n_f: int = 5) -> GapfillResult:
     """The whole method on the CPU: Sec. 2.1 transform, Eq. 2 per block,
     per-block T by energy matching (Sec. 2.2.2; skipped when T_blk is given),
     R local-equilibrium realizations from the block-mean start (Sec. 3.3.3,
@@ -502,7 +520,7 @@ def gapfill(values, mask, lb: int, R: int, seed: int = 0, slice_id: int = 0, q: 
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     H, W = mask.shape
     o = Oracle(H, W, lb, q=q, J=J, seed=seed, slice_id=slice_id, overrelax=overrelax,
-               threads=threads)
+               threads=threads, stop_rule=stop_rule, n_fit=n_fit, n_f=n_f)
     phi, zmin, zmax, deg = o.transform(values, mask)
     st = o.block_stats(phi, mask)
     phi0 = o.init_block_mean(phi, mask, st)

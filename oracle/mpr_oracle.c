@@ -59,6 +59,9 @@ void orc_model_init(orc_model* m, int32_t H, int32_t W, int32_t lb, double q, do
     m->D = 1;
     m->nbz = 1;
     m->storage = 0;
+    m->stop_rule = 0;
+    m->n_fit = 20;
+    m->n_f = 5;
 }
 
 /* ------------------------------------------------------- stored angles -- */
@@ -461,6 +464,49 @@ int orc_stop_update(const orc_model* m, int32_t t, int32_t n_max, const double* 
     return left;
 }
 
+double orc_window_slope(const orc_model* m, int32_t t, const double* hist, int b) {
+    double num = 0.0;
+    for (int j = 0; j < m->n_fit; ++j) {
+        const int32_t s = t - m->n_fit + 1 + j;
+        num += (double)(2 * j - (m->n_fit - 1)) * hist[(int64_t)(s % m->n_fit) * m->nblk + b];
+    }
+    return num;
+}
+
+int orc_stop_update_window(const orc_model* m, int32_t t, int32_t n_max, const double* Es,
+                           const int64_t* Nsp, const int8_t* sigma, const double* hist,
+                           uint8_t* active, int32_t* stop_sweep) {
+    const int32_t first = m->n_fit + m->n_f;
+    const int test = t >= first && (t - first) % m->n_f == 0;
+    int targeted_active = 0;
+    for (int b = 0; b < m->nblk; ++b) {
+        if (!active[b] || Nsp[b] == 0) continue;
+        int stop = 0;
+        if (test) {
+            const double num = orc_window_slope(m, t, hist, b);
+            stop = (double)sigma[b] * num <= 0.0;
+        }
+        if (stop) {
+            active[b] = 0;
+            stop_sweep[b] = t;
+        } else {
+            targeted_active = 1;
+        }
+    }
+    (void)Es;
+    int left = 0;
+    for (int b = 0; b < m->nblk; ++b) {
+        if (!active[b]) continue;
+        if ((Nsp[b] == 0 && !targeted_active) || t >= n_max) {
+            active[b] = 0;
+            stop_sweep[b] = t;
+        } else {
+            left += 1;
+        }
+    }
+    return left;
+}
+
 int orc_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const double* T_blk,
                      const double* Es, const int64_t* Nsp, const int64_t* Nb,
                      const int64_t* n_gap, int32_t n_max, uint32_t r, int32_t* stop_sweep,
@@ -469,6 +515,7 @@ int orc_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const
     double* E = (double*)malloc(sizeof(double) * nblk);
     int8_t* sigma = (int8_t*)malloc(nblk);
     uint8_t* active = (uint8_t*)malloc(nblk);
+    double* hist = m->stop_rule == 1 ? (double*)malloc(sizeof(double) * nblk * m->n_fit) : NULL;
     orc_block_energy(m, phi, E);
     if (e_trace)
         for (int b = 0; b < nblk; ++b) e_trace[b] = Nb[b] > 0 ? E[b] / (double)Nb[b] : 0.0;
@@ -484,11 +531,18 @@ int orc_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const
         if (e_trace)
             for (int b = 0; b < nblk; ++b)
                 e_trace[(int64_t)t * nblk + b] = Nb[b] > 0 ? E[b] / (double)Nb[b] : 0.0;
-        left = orc_stop_update(m, t, n_max, E, Es, Nsp, Nb, sigma, active, stop_sweep);
+        if (hist) {
+            for (int b = 0; b < nblk; ++b)
+                hist[(int64_t)(t % m->n_fit) * nblk + b] = Nb[b] > 0 ? E[b] / (double)Nb[b] : 0.0;
+            left = orc_stop_update_window(m, t, n_max, Es, Nsp, sigma, hist, active, stop_sweep);
+        } else {
+            left = orc_stop_update(m, t, n_max, E, Es, Nsp, Nb, sigma, active, stop_sweep);
+        }
     }
     free(E);
     free(sigma);
     free(active);
+    free(hist);
     return t;
 }
 

@@ -33,6 +33,9 @@ typedef struct {
                                 1 BF16, 2 FP16. A proposal is the FP32 product of 2pi and
                                 u0, rounded to the stored type before its energy is taken;
                                 a reflected angle is rounded too (via FP32, ties to even). */
+    int32_t stop_rule;       /* 0 CROSS (first crossing of e_s,b), 1 WINDOW (end of the
+                                energy drift, tested on the last n_fit sweeps every n_f) */
+    int32_t n_fit, n_f;      /* WINDOW: window length and test period (Sec. 3.4: 20, 5) */
 } orc_model;
 
 /* v rounded to the stored type of `storage` (0: v itself), via FP32, ties to even. */
@@ -99,6 +102,20 @@ void orc_init_random(const orc_model* m, double* phi, const uint8_t* mask, uint3
  * stop_sweep[nblk] receives each block's stop sweep. e_trace (nullable) receives
  * e_b(t) for t = 0..n_max as [(n_max+1) * nblk] (unused entries untouched).
  * Returns the number of sweeps run. */
+/* The WINDOW rule after sweep t (Sec. 3.4 names n_fit = 20, the length of the
+ * energy series the equilibrium test uses, and n_f = 5, its period; the first
+ * test comes after n_fit + n_f sweeps). hist[(s mod n_fit) * nblk + b] holds
+ * e_b(s) for the sweeps s of the window (the caller writes e_b(t) before the
+ * call). At t = n_fit + n_f + k n_f, a targeted active block stops once the
+ * least-squares slope of e_b over sweeps t - n_fit + 1 .. t no longer has the
+ * sign sigma_b of e_s,b - e_b(0) (sigma_b = 0: at the first test). Blocks
+ * without sample bonds and n_max as in orc_stop_update. */
+int orc_stop_update_window(const orc_model* m, int32_t t, int32_t n_max, const double* Es,
+                           const int64_t* Nsp, const int8_t* sigma, const double* hist,
+                           uint8_t* active, int32_t* stop_sweep);
+/* The numerator of that slope: sum_j (2 j - (n_fit - 1)) e_b(t - n_fit + 1 + j). */
+double orc_window_slope(const orc_model* m, int32_t t, const double* hist, int b);
+
 int orc_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const double* T_blk,
                      const double* Es, const int64_t* Nsp, const int64_t* Nb,
                      const int64_t* n_gap, int32_t n_max, uint32_t r, int32_t* stop_sweep,

@@ -233,6 +233,14 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.sweep_form < -1 || o.sweep_form > 4)
         return fail(ctx, MPR_EINVAL, "sweep_form must be -1, 0, 1, 2, 3 or 4");
     if (o.n_newton < 0 || o.n_newton > 65533) return fail(ctx, MPR_EINVAL, "n_newton in [0, 65533]");
+    if (o.sweep_form_bulk != -1 && o.sweep_form_bulk != 0 && o.sweep_form_bulk != 3 &&
+        o.sweep_form_bulk != 4)
+        return fail(ctx, MPR_EINVAL, "sweep_form_bulk must be -1, 0, 3 or 4");
+    if (o.stop_rule != MPR_STOP_CROSS && o.stop_rule != MPR_STOP_WINDOW)
+        return fail(ctx, MPR_EINVAL, "unknown stop rule");
+    if (o.n_fit < 2 || o.n_fit > 64 || o.n_f < 1 || o.n_f > 1024)
+        return fail(ctx, MPR_EINVAL, "need 2 <= n_fit <= 64 and 1 <= n_f <= 1024");
+    if (o.cal_warm != 0 && o.cal_warm != 1) return fail(ctx, MPR_EINVAL, "cal_warm must be 0 or 1");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
     return MPR_OK;
@@ -352,7 +360,8 @@ bool tile_form_ok(const mpr_ctx* ctx) { return ctx->G == 8 && ctx->tiles.n > 0; 
 
 // The options, the autotuner's choice or its trial ask for the staged half-step.
 bool tiles_wanted(const mpr_ctx* ctx) {
-    return ctx->opt.sweep_form == 4 || ctx->tuned_form == 4 || ctx->tuning_tiles;
+    return ctx->opt.sweep_form == 4 || ctx->tuned_form == 4 || ctx->tuning_tiles ||
+           (ctx->opt.sweep_form < 0 && ctx->opt.sweep_form_bulk == 4);
 }
 
 // Tiles, tile-major lists and staging table of the staged half-step, built
@@ -409,8 +418,9 @@ int sweep_form(mpr_ctx* ctx) {
     if (ctx->opt.sweep_form == 4) return tile_form_ok(ctx) ? 4 : 0;
     if (ctx->opt.sweep_form >= 0) return ctx->opt.sweep_form;
     if (ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm) return 2;
-    if (ctx->tuned_form == 4) return tile_form_ok(ctx) ? 4 : 0;
-    if (ctx->tuned_form >= 0) return ctx->tuned_form;
+    const int bulk = ctx->tuned_form >= 0 ? ctx->tuned_form : ctx->opt.sweep_form_bulk;
+    if (bulk == 4) return tile_form_ok(ctx) ? 4 : 0;
+    if (bulk >= 0) return bulk;
     const double per_block = (double)(ctx->n_gap[0] + ctx->n_gap[1]) / (2.0 * ctx->g.nblk);
     return per_block <= kHalfFormEntries ? 3 : 0;
 }
@@ -946,6 +956,11 @@ void mpr_default_options(mpr_options* o) {
     o->sim_tail = 0;
     o->sweep_form = -1;
     o->pair_tail = 4096;
+    o->sweep_form_bulk = -1;
+    o->stop_rule = MPR_STOP_CROSS;
+    o->n_fit = 20;
+    o->n_f = 5;
+    o->cal_warm = 0;
     o->cuda_stream = nullptr;
 }
 

@@ -17,6 +17,7 @@ from . import build as _build
 MPR_OK, MPR_EINVAL, MPR_ENOMEM, MPR_ECUDA, MPR_ENOSAMPLES, MPR_ETIMEOUT, MPR_ESTATE = range(7)
 MPR_STORE_F32, MPR_STORE_BF16, MPR_STORE_F16 = 0, 1, 2
 MPR_INIT_BLOCK_MEAN, MPR_INIT_RANDOM = 0, 1
+MPR_STOP_CROSS, MPR_STOP_WINDOW = 0, 1
 
 EXPORTS = [
     "mpr_default_options", "mpr_create", "mpr_destroy", "mpr_last_error", "mpr_status_string",
@@ -49,7 +50,8 @@ class mpr_options(C.Structure):
                 ("barrier_test", C.c_int32), ("cal_method", C.c_int32), ("n_newton", C.c_int32),
                 ("t_init", C.c_float), ("sim_graph", C.c_int32), ("cal_points", C.c_int32),
                 ("sim_tail", C.c_int32), ("sweep_form", C.c_int32), ("pair_tail", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("sweep_form_bulk", C.c_int32), ("stop_rule", C.c_int32), ("n_fit", C.c_int32),
+                ("n_f", C.c_int32), ("cal_warm", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):
