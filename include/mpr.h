@@ -455,8 +455,9 @@ mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_t* mask, co
  * from the block-mean start with the per-block stop (Sec. 3.4), the mean
  * back-transformed. Random numbers: counter (site index, t | tag << 16,
  * r / 2, 0), words 2 (r mod 2) and 2 (r mod 2) + 1, key (seed_lo, seed_hi ^
- * slice_id). FP32 state; the storage, group, cal_mode / cal_method, SST and
- * sim_graph options do not apply. Realizations of one call carry indices
+ * slice_id). FP32 state; the storage, group, cal_mode / cal_method, SST,
+ * sim_graph and sweep_form options do not apply; stop_rule must be
+ * MPR_STOP_CROSS and cal_warm 0 (else EINVAL). Realizations of one call carry indices
  * r_next, r_next + 1, ... with r_next the accumulated count rounded up to
  * even. Arrays are D*H*W (sites, row-major) or nblk (blocks); pointers
  * host or device. Errors: as the 2-D calls. */

@@ -110,6 +110,9 @@ struct mpr_ctx {
     Control* ctl = nullptr;      // device loop state
     Control* h_ctl = nullptr;    // pinned mirror
     int grid_cache[2][3][4] = {};  // full grid of k_sweep by (G = 2 / 8, storage, form)
+    // The WINDOW stop rule's ring of e_b (allocated when the rule is chosen).
+    double* whist = nullptr;
+    size_t whist_cap = 0;          // elements
     // The staged half-step's tiles (built at the first batch that uses them).
     Tiles tiles{};
     float* stab = nullptr;         // [2][H][Wh] staging table
@@ -311,6 +314,16 @@ mpr_status ensure_batch(mpr_ctx* ctx, int lanes, int requested_group, int storag
         ctx->work_cap = work_need;
     }
     ctx->work_stride = (uint32_t)work_need;
+    if (ctx->opt.stop_rule == MPR_STOP_WINDOW) {
+        const size_t wneed = (size_t)ctx->opt.n_fit * blk_need;
+        if (wneed > ctx->whist_cap) {
+            dfree(ctx, ctx->whist);
+            ctx->whist = nullptr;
+            ctx->whist_cap = 0;
+            TRY(dalloc(ctx, &ctx->whist, wneed));
+            ctx->whist_cap = wneed;
+        }
+    }
     ctx->storage = storage;
     ctx->bound = ~0ull;
     ctx->G = G;
@@ -353,6 +366,17 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
         a.tl.stab = ctx->stab;
     }
     return a;
+}
+
+// The stop rule of the realizations' stop tests.
+StopWindow stop_window(const mpr_ctx* ctx) {
+    StopWindow w{};
+    w.rule = ctx->opt.stop_rule;
+    w.n_fit = ctx->opt.n_fit;
+    w.n_f = ctx->opt.n_f;
+    w.hist = ctx->whist;
+    w.stride = (size_t)ctx->g.nblk * ctx->Rp;
+    return w;
 }
 
 // The staged half-step (form 4) needs lane groups of eight and its tiles.
@@ -591,12 +615,13 @@ mpr_status sweep_once(mpr_ctx* ctx) {
         ctx->ev_sim.emplace_back(e0, e1);
     }
     // The stop kernels see the worklist's units as lane groups of two.
+    const StopWindow win = stop_window(ctx);
     launch_stop_targeted(2, ctx->Rp / 2, ctx->Rp, ctx->d_of_block,
                          stop_grid(ctx, 2, kTargetedCtasPerSm),
                          ctx->ctl, ctx->work,
                          ctx->work_stride, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
                          ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, t_known,
-                         ctx->s);
+                         ctx->s, &win);
     CKL();
     launch_stop_rest(g.nblk, ctx->Rp / 2, 2, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
                      stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp,
@@ -1725,6 +1750,7 @@ SimTailArgs tail_args(mpr_ctx* ctx) {
     st.stop = ctx->stop;
     st.tcount = ctx->tcount;
     st.e_last = ctx->e_last;
+    st.win = stop_window(ctx);
     a.ctl = ctx->ctl;
     a.work_all = ctx->work;
     return a;

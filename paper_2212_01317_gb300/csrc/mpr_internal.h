@@ -159,6 +159,15 @@ struct SweepArgs {
     Tiles tl;                 // the staged half-step's tiles (tl.n == 0: not built)
 };
 
+// The WINDOW stop rule (Sec. 3.4: n_fit, n_f): e_b of the last n_fit sweeps
+// of every (block, realization), a ring indexed by sweep mod n_fit.
+struct StopWindow {
+    int rule;                 // 0 CROSS, 1 WINDOW
+    int n_fit, n_f;
+    double* hist;             // [n_fit][nblk * Rp]
+    size_t stride;            // nblk * Rp
+};
+
 // Per-(block, realization) bookkeeping of the stop test (Sec. 3.4 reading):
 // the operands of the targeted and the closing parts of a sweep's test.
 struct StopArgs {
@@ -174,6 +183,7 @@ struct StopArgs {
     int32_t* stop;            // [nblk][Rp] stop sweep
     int32_t* tcount;          // [n_slices][Rp] running targeted blocks
     double* e_last;           // [nblk][Rp] e_b after the last test
+    StopWindow win;           // the stop rule (win.rule == 0: first crossing)
 };
 
 // The calibration's per-sweep fold (E_b += the sweep's change; the measured

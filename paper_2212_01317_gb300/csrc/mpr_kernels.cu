@@ -1224,8 +1224,10 @@ void launch_stop_targeted(int G, int groups, int Rp, const int32_t* of_block, in
                           Control* ctl, const uint32_t* work, uint32_t work_stride,
                           const double* es, const double* inb, const int32_t* Nsp, double* eacc,
                           double* ecur, const int8_t* sigma, uint8_t* running, int32_t* stop,
-                          int32_t* tcount, double* e_last, int t_known, cudaStream_t s) {
+                          int32_t* tcount, double* e_last, int t_known, cudaStream_t s,
+                          const StopWindow* win) {
     StopArgs sa{};
+    if (win) sa.win = *win;
     sa.G = G;
     sa.groups = groups;
     sa.Rp = Rp;

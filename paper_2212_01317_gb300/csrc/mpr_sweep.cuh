@@ -566,7 +566,10 @@ __device__ __forceinline__ void energy_item(const SweepArgs& a, int item, int wi
 // targeted blocks, which the first completes.
 //
 // Targeted part: E_b += the sweep's change (eacc, then cleared); e_b = E_b / N_b;
-// a targeted block stops once sigma (e_b(t) - e_s,b) >= 0. Entries
+// a targeted block stops once sigma (e_b(t) - e_s,b) >= 0 (CROSS), or, under the
+// WINDOW rule, at a test sweep t = n_fit + n_f + k n_f once the least-squares
+// slope of e_b over sweeps t - n_fit + 1 .. t no longer has the sign sigma
+// (its numerator sum_j (2 j - (n_fit - 1)) e_b(t - n_fit + 1 + j)). Entries
 // i = i0, i0 + step, ... < n of (item, lane) pairs (n = items * G). Entries
 // below `cap` are readable whatever n is (the worklist buffer's length times
 // G; past n they hold stale items), so the first item is read without waiting
@@ -590,8 +593,24 @@ __device__ __forceinline__ void stop_targeted_range(const StopArgs& s, uint32_t 
         s.ecur[k] = E;
         const double e = E * inb;
         s.e_last[k] = e;
-        if (nsp == 0) continue;
-        const bool reached = sg > 0 ? (e >= es) : (sg < 0 ? (e <= es) : true);
+        bool reached;
+        if (s.win.rule == 1) {
+            const int nf = s.win.n_fit;
+            s.win.hist[(size_t)(t_sweep % (uint32_t)nf) * s.win.stride + k] = e;
+            if (nsp == 0) continue;
+            const uint32_t first = (uint32_t)(nf + s.win.n_f);
+            if (t_sweep < first || (t_sweep - first) % (uint32_t)s.win.n_f != 0) continue;
+            double num = 0.0;
+            for (int j = 0; j < nf; ++j) {
+                const uint32_t sw = t_sweep - (uint32_t)nf + 1u + (uint32_t)j;
+                num += (double)(2 * j - (nf - 1)) *
+                       s.win.hist[(size_t)(sw % (uint32_t)nf) * s.win.stride + k];
+            }
+            reached = (double)sg * num <= 0.0;
+        } else {
+            if (nsp == 0) continue;
+            reached = sg > 0 ? (e >= es) : (sg < 0 ? (e <= es) : true);
+        }
         if (reached) {
             s.running[k] = 0;
             s.stop[k] = (int32_t)t_sweep;
