@@ -690,7 +690,7 @@ def run_ours_batch(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     seed_base = SEED0 + 7919 * rank
 
-    tuned = {"group": 0, "bulk": -1}
+    tuned = {"bulk": -1}
 
     def options(profile, seed, st=storage, slice_id=0):
         return mpr.mpr_default_options(seed=seed, slice_id=slice_id, profile=profile,
@@ -698,7 +698,7 @@ def run_ours_batch(args, world, rank, local):
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
                                        sim_graph=args.sim_graph, sweep_form=args.sweep_form,
-                                       sweep_form_bulk=tuned["bulk"], group=tuned["group"],
+                                       sweep_form_bulk=tuned["bulk"],
                                        cuda_stream=stream.cuda_stream)
 
     def timed_event():
@@ -714,7 +714,10 @@ def run_ours_batch(args, world, rank, local):
                 # once, in the first warm-up step: later steps run the choice
                 t = mpr.mpr_autotune(ctx, R, args.autotune)
                 tunes.append(t)
-                tuned["group"], tuned["bulk"] = t.group, t.form
+                # (the lane-group width stays the library's choice: it also
+                # sets the calibration chains' width, where eight lanes for two
+                # temperatures cost 3.6x)
+                tuned["bulk"] = t.form if t.group == 8 else -1
             ev = (timed_event(), timed_event())
             ev[0].record(stream)
             mpr.mpr_simulate(ctx, R)

@@ -442,9 +442,16 @@ int sweep_form(mpr_ctx* ctx) {
     if (ctx->opt.sweep_form == 4) return tile_form_ok(ctx) ? 4 : 0;
     if (ctx->opt.sweep_form >= 0) return ctx->opt.sweep_form;
     if (ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm) return 2;
+    // An autotuned (or asked-for) form holds while at least half of the pairs
+    // run: the autotuner times the first sweeps, where every pair runs. (On
+    // the 256-field batch the first two sweeps ran 7 % faster with two pairs
+    // per warp, the whole run 2.5 % slower.)
     const int bulk = ctx->tuned_form >= 0 ? ctx->tuned_form : ctx->opt.sweep_form_bulk;
-    if (bulk == 4) return tile_form_ok(ctx) ? 4 : 0;
-    if (bulk >= 0) return bulk;
+    const unsigned long long pairs = (unsigned long long)ctx->g.nblk * (ctx->Rp / 2);
+    if (bulk >= 0 && ctx->bound >= pairs / 2) {
+        if (bulk == 4) return tile_form_ok(ctx) ? 4 : 0;
+        return bulk;
+    }
     const double per_block = (double)(ctx->n_gap[0] + ctx->n_gap[1]) / (2.0 * ctx->g.nblk);
     return per_block <= kHalfFormEntries ? 3 : 0;
 }
