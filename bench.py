@@ -59,7 +59,7 @@ def parse(argv=None):
                          "default bf16 for batch workloads (the chosen form), f32 otherwise")
     ap.add_argument("--cal-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="calibration launch form (3: every kernel from the host, for profilers)")
-    ap.add_argument("--cal-points", type=int, default=2, choices=[1, 2],
+    ap.add_argument("--cal-points", type=int, default=2, choices=[1, 2, 4, 8],
                     help="calibration temperatures per block and iteration (1 bisection, "
                          "2 trisection, the default: the two temperatures run on the two "
                          "lanes of a realization pair); --cal-iters sets the iterations")
@@ -112,10 +112,11 @@ def dist_env():
 
 def cal_iters(args) -> int:
     """Calibration iterations: 24 bisection steps, or 16 trisection steps (a
-    narrower final bracket: 2 / 3^16 < 2 / 2^24)."""
+    narrower final bracket: 2 / 3^16 < 2 / 2^24), 11 steps of 4 points
+    (5^11 > 3^16), 8 of 8 points (9^8 = 3^16)."""
     if args.cal_iters is not None:
         return args.cal_iters
-    return 16 if args.cal_points == 2 else 24
+    return {1: 24, 2: 16, 4: 11, 8: 8}[args.cal_points]
 
 
 def bytes_per_gap_update(s_bytes: float, p: float) -> float:
@@ -201,7 +202,8 @@ SEED0 = 2024            # Philox seed of step j is SEED0 + j (+ 7919 per rank)
 def cal_label(args) -> str:
     if args.calibration == "newton":
         return "newton"
-    return ("bisection" if args.cal_points == 1 else "trisection") + f" x{cal_iters(args)}"
+    name = {1: "bisection", 2: "trisection", 4: "4-point section", 8: "8-point section"}
+    return name[args.cal_points] + f" x{cal_iters(args)}"
 
 
 def batch_config(args, world) -> dict:
@@ -245,7 +247,7 @@ def oracle_calibrate(o, phi0, mask, st, args):
         return o.calibrate_newton(phi0, mask, st)
     if args.cal_points == 1:
         return o.calibrate(phi0, mask, st, n_bisect=cal_iters(args))
-    return o.calibrate_points(phi0, mask, st, n_iter=cal_iters(args), points=2)
+    return o.calibrate_points(phi0, mask, st, n_iter=cal_iters(args), points=args.cal_points)
 
 
 ORACLE_R_PER_STEP = 5     # realizations of the oracle's sample field per step
@@ -326,7 +328,7 @@ def oracle_field_T(args, wl, threads):
     if args.cal_points == 1:
         T = o.calibrate(phi0, wl.mask, st, n_bisect=4)
     else:
-        T = o.calibrate_points(phi0, wl.mask, st, n_iter=4, points=2)
+        T = o.calibrate_points(phi0, wl.mask, st, n_iter=4, points=args.cal_points)
     return o, phi0, st, T
 
 

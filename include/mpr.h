@@ -104,7 +104,10 @@ typedef struct {
     int32_t cal_points;  /* temperatures tried per block and calibration iteration: 1 bisection
                             (default), 2 trisection (the two on the two lanes of a realization
                             pair; n_bisect iterations shrink each bracket 3x; 16 of them leave
-                            it narrower than 24 bisection steps) */
+                            it narrower than 24 bisection steps), 4 or 8 (k-section on the lanes
+                            of a lane group, lane r of the chains at point r mod k: each
+                            iteration shrinks the bracket (k + 1)x; 8 iterations of 8 points
+                            equal 16 trisection steps) */
     int32_t sim_tail;    /* running (block, realization) pairs below which mpr_simulate runs the
                             rest of its sweep loop (half-steps and stop tests, separated by
                             bounded grid-wide barriers) as one cooperative launch; 0: never
@@ -133,9 +136,6 @@ typedef struct {
     int32_t stop_rule;   /* mpr_stop_rule (default MPR_STOP_CROSS) */
     int32_t n_fit;       /* MPR_STOP_WINDOW: sweeps in the least-squares window (default 20) */
     int32_t n_f;         /* MPR_STOP_WINDOW: sweeps between two window tests (default 5) */
-    int32_t cal_warm;    /* 1: the calibration bracket of each block starts around the
-                            temperature of the unconditional e(T) curve at e_s,b (Sec. 2.1 energy
-                            matching of the data-free lattice) instead of [t_lo, t_hi] (default 0) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 
@@ -457,7 +457,7 @@ mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_t* mask, co
  * r / 2, 0), words 2 (r mod 2) and 2 (r mod 2) + 1, key (seed_lo, seed_hi ^
  * slice_id). FP32 state; the storage, group, cal_mode / cal_method, SST,
  * sim_graph and sweep_form options do not apply; stop_rule must be
- * MPR_STOP_CROSS and cal_warm 0 (else EINVAL). Realizations of one call carry indices
+ * MPR_STOP_CROSS (else EINVAL). Realizations of one call carry indices
  * r_next, r_next + 1, ... with r_next the accumulated count rounded up to
  * even. Arrays are D*H*W (sites, row-major) or nblk (blocks); pointers
  * host or device. Errors: as the 2-D calls. */

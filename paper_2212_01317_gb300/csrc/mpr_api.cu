@@ -69,6 +69,8 @@ struct mpr_ctx {
     float* init_angle = nullptr;
     float *T = nullptr, *beta = nullptr, *lo = nullptr, *hi = nullptr;
     float *T2 = nullptr, *beta2 = nullptr;   // trisection's second point
+    float *Tk = nullptr, *betak = nullptr;   // [points][nblk] of the 4- or 8-point calibration
+    double* ebark = nullptr;                 // [points][nblk]
     double* ebar2 = nullptr;
     float* T_site = nullptr;     // [H*W] site temperatures (SST), allocated on first use
     float* beta_site = nullptr;  // [H*W] 1 / T_site
@@ -230,7 +232,8 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.wait_ms < 1) return fail(ctx, MPR_EINVAL, "wait_ms must be >= 1");
     if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
     if (o.cal_method != 0 && o.cal_method != 1) return fail(ctx, MPR_EINVAL, "cal_method must be 0 or 1");
-    if (o.cal_points != 1 && o.cal_points != 2) return fail(ctx, MPR_EINVAL, "cal_points must be 1 or 2");
+    if (o.cal_points != 1 && o.cal_points != 2 && o.cal_points != 4 && o.cal_points != 8)
+        return fail(ctx, MPR_EINVAL, "cal_points must be 1, 2, 4 or 8");
     if (o.sim_tail < 0) return fail(ctx, MPR_EINVAL, "sim_tail must be >= 0");
     if (o.pair_tail < 0) return fail(ctx, MPR_EINVAL, "pair_tail must be >= 0");
     if (o.sweep_form < -1 || o.sweep_form > 4)
@@ -243,7 +246,6 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
         return fail(ctx, MPR_EINVAL, "unknown stop rule");
     if (o.n_fit < 2 || o.n_fit > 64 || o.n_f < 1 || o.n_f > 1024)
         return fail(ctx, MPR_EINVAL, "need 2 <= n_fit <= 64 and 1 <= n_f <= 1024");
-    if (o.cal_warm != 0 && o.cal_warm != 1) return fail(ctx, MPR_EINVAL, "cal_warm must be 0 or 1");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
     return MPR_OK;
@@ -734,7 +736,15 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     const Geom& g = ctx->g;
     const mpr_options& o = ctx->opt;
     const int pts = o.cal_points;
-    if (pts == 2) {
+    if (pts > 2) {
+        launch_kpts_mid(g.nblk, pts, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->Tk, ctx->ctl, ctx->s);
+        CKL();
+        for (int p = 0; p < pts; ++p) {
+            launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->Tk + (size_t)p * g.nblk,
+                            ctx->betak + (size_t)p * g.nblk, ctx->s);
+            CKL();
+        }
+    } else if (pts == 2) {
         launch_kcal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->T2, ctx->ctl, ctx->s);
         CKL();
         launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T2, ctx->beta2, ctx->s);
@@ -743,8 +753,10 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
         launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
         CKL();
     }
-    launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
-    CKL();
+    if (pts <= 2) {
+        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
+        CKL();
+    }
     TRY(init_batch_state(ctx));
     // Every iteration starts from the same state, so E_b of the start
     // (computed once, before the first iteration) is copied, and no change is
@@ -762,6 +774,8 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
             a.t_fixed = sw;
             a.eacc = ctx->eacc + (size_t)(sw & 1) * blk;
             a.beta_odd = pts == 2 ? ctx->beta2 : nullptr;
+            a.beta_pts = pts > 2 ? ctx->betak : nullptr;
+            a.n_pts = pts;
             FoldArgs f{};
             if (c == 0 && sw > 1) {
                 f.ctas = (g.nblk + 255) / 256;
@@ -770,6 +784,7 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
                 f.chains = o.cal_chains;
                 f.points = pts;
                 f.ebar_odd = ctx->ebar2;
+                f.ebar_pts = ctx->ebark;
                 f.measure = (sw - 1) > o.n_eq;
                 f.inb = ctx->inb;
                 f.eacc = ctx->eacc + (size_t)((sw - 1) & 1) * blk;
@@ -793,9 +808,12 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     }
     launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, n_sw, ctx->ctl, ctx->inb,
                     ctx->eacc + (size_t)(n_sw & 1) * blk, ctx->ecur, ctx->ebar, ctx->s, pts,
-                    ctx->ebar2);
+                    ctx->ebar2, ctx->ebark);
     CKL();
-    if (pts == 2)
+    if (pts > 2)
+        launch_kpts_update(g.nblk, pts, inv_count, ctx->es, ctx->Nsp_cal, ctx->Tk, ctx->lo,
+                           ctx->hi, ctx->ebark, ctx->ctl, o.n_bisect, cond, ctx->s);
+    else if (pts == 2)
         launch_kcal_update(g.nblk, inv_count, ctx->es, ctx->Nsp_cal, ctx->T, ctx->T2, ctx->lo, ctx->hi,
                            ctx->ebar, ctx->ebar2, ctx->ctl, o.n_bisect, cond, ctx->s);
     else
@@ -992,7 +1010,6 @@ void mpr_default_options(mpr_options* o) {
     o->stop_rule = MPR_STOP_CROSS;
     o->n_fit = 20;
     o->n_f = 5;
-    o->cal_warm = 0;
     o->cuda_stream = nullptr;
 }
 
@@ -1486,6 +1503,14 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     ctx->R = chains * o.cal_points;
     ctx->chains_valid = true;
     CK(cudaMemsetAsync(ctx->ebar2, 0, (size_t)g.nblk * sizeof(double), ctx->s));
+    if (o.cal_points > 2) {
+        if (!ctx->Tk) {
+            TRY(dalloc(ctx, &ctx->Tk, (size_t)8 * g.nblk));
+            TRY(dalloc(ctx, &ctx->betak, (size_t)8 * g.nblk));
+            TRY(dalloc(ctx, &ctx->ebark, (size_t)8 * g.nblk));
+        }
+        CK(cudaMemsetAsync(ctx->ebark, 0, (size_t)8 * g.nblk * sizeof(double), ctx->s));
+    }
     launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->ctl, ctx->s);
     CKL();
     const double inv_count = 1.0 / ((double)o.n_meas * (double)chains);

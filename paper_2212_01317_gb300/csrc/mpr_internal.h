@@ -146,6 +146,9 @@ struct SweepArgs {
     const float* beta;        // [nblk] 1 / T_b
     const float* beta_site;   // [H*W] 1 / T_i (site temperatures, Sec. 2.2.3) or nullptr
     const float* beta_odd;    // [nblk] 1 / T_b of odd lanes (trisection's second point) or nullptr
+    const float* beta_pts;    // [n_pts][nblk] 1 / T of the k-point calibration (lane r takes
+                              // point r mod n_pts) or nullptr
+    int n_pts;
     const uint8_t* running;   // [nblk][Rp] or nullptr (= every lane r < R runs)
     double* eacc;             // [nblk][Rp] energy change of this sweep (moves)
     double* ecur;             // [nblk][Rp] E_b (the energy pass adds into it)
@@ -197,6 +200,7 @@ struct FoldArgs {
     double* ecur;             // [nblk][Rp]
     double* ebar;             // [nblk] (even lanes when points == 2)
     double* ebar_odd;         // [nblk] odd lanes (points == 2)
+    double* ebar_pts;         // [points][nblk] (points > 2: lane r adds to point r mod points)
 };
 
 // Grid-wide barrier state of a cooperative launch (zeroed before each launch).

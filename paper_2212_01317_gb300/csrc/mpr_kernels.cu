@@ -401,17 +401,21 @@ __global__ void __launch_bounds__(kFlatThreads, 8) k_sweep_flat(SweepArgs a, int
         if (blockIdx.y != 0) return;
         for (int b = ((int)blockIdx.x - sweep_ctas) * kFlatThreads + threadIdx.x; b < f.nblk;
              b += f.ctas * kFlatThreads) {
-            double s[2] = {0.0, 0.0};
+            double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             for (int r = 0; r < f.chains * f.points; ++r) {
                 const size_t k = (size_t)b * f.Rp + r;
                 const double E = f.ecur[k] + f.eacc[k];
                 f.ecur[k] = E;
                 f.eacc[k] = 0.0;
-                s[f.points == 2 ? (r & 1) : 0] += E * f.inb[b];
+                s[r % f.points] += E * f.inb[b];
             }
             if (f.measure) {
-                f.ebar[b] += s[0];
-                if (f.points == 2) f.ebar_odd[b] += s[1];
+                if (f.points > 2) {
+                    for (int p = 0; p < f.points; ++p) f.ebar_pts[(size_t)p * f.nblk + b] += s[p];
+                } else {
+                    f.ebar[b] += s[0];
+                    if (f.points == 2) f.ebar_odd[b] += s[1];
+                }
             }
         }
         return;
@@ -610,21 +614,80 @@ __global__ void k_cal_fill(Slices sl, int nbx, const int32_t* __restrict__ Nsp,
 __global__ void k_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed,
                            const Control* __restrict__ ctl, const double* __restrict__ inb,
                            double* __restrict__ eacc, double* __restrict__ ecur,
-                           double* __restrict__ ebar, int points, double* __restrict__ ebar_odd) {
+                           double* __restrict__ ebar, int points, double* __restrict__ ebar_odd,
+                           double* __restrict__ ebar_pts) {
     const bool measure = (t_fixed > 0 ? t_fixed : (int)ctl->t) > n_eq;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
-        double s[2] = {0.0, 0.0};
+        double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int r = 0; r < chains * points; ++r) {
             const size_t k = (size_t)b * Rp + r;
             const double E = ecur[k] + eacc[k];
             ecur[k] = E;
             eacc[k] = 0.0;
-            s[points == 2 ? (r & 1) : 0] += E * inb[b];
+            s[r % points] += E * inb[b];
         }
         if (measure) {
-            ebar[b] += s[0];
-            if (points == 2) ebar_odd[b] += s[1];
+            if (points > 2) {
+                for (int p = 0; p < points; ++p) ebar_pts[(size_t)p * nblk + b] += s[p];
+            } else {
+                ebar[b] += s[0];
+                if (points == 2) ebar_odd[b] += s[1];
+            }
         }
+    }
+}
+
+// k-point calibration (4 or 8 temperatures per block and iteration, lane r
+// of the chains at point r mod points): T_p = lo + (p + 1) (hi - lo) / (points
+// + 1), p = 0 .. points - 1, for every targeted block (untargeted: 0, the
+// median fills them in).
+__global__ void k_kpts_mid(int nblk, int points, const int32_t* __restrict__ Nsp,
+                           const float* __restrict__ lo, const float* __restrict__ hi,
+                           float* __restrict__ Tk, Control* ctl) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        const bool t = Nsp[b] > 0;
+        const float w = (hi[b] - lo[b]) / (float)(points + 1);
+        for (int p = 0; p < points; ++p)
+            Tk[(size_t)p * nblk + b] = t ? lo[b] + (float)(p + 1) * w : 0.0f;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->tag = 1u + ctl->k;
+        ctl->t = 0;
+    }
+}
+
+// k-point step: the new bracket runs from the highest point whose mean e_b is
+// below e_s,b to the lowest point whose mean is not (<e_b> grows with T); the
+// points' span when noise makes those cross.
+__global__ void k_kpts_update(int nblk, int points, double inv_count, const double* __restrict__ es,
+                              const int32_t* __restrict__ Nsp, const float* __restrict__ Tk,
+                              float* __restrict__ lo, float* __restrict__ hi,
+                              double* __restrict__ ebar_pts, Control* ctl, int n_iter,
+                              cudaGraphConditionalHandle cond) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        float nlo = lo[b], nhi = hi[b];
+        const bool t = Nsp[b] > 0;
+        for (int p = 0; p < points; ++p) {
+            const size_t i = (size_t)p * nblk + b;
+            const double e = ebar_pts[i] * inv_count;
+            ebar_pts[i] = 0.0;
+            if (!t) continue;
+            const float tp = Tk[i];
+            if (e < es[b]) { if (tp > nlo) nlo = tp; }
+            else if (tp < nhi) nhi = tp;
+        }
+        if (!t) continue;
+        if (nlo > nhi) {
+            nlo = Tk[b];
+            nhi = Tk[(size_t)(points - 1) * nblk + b];
+        }
+        lo[b] = nlo;
+        hi[b] = nhi;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t k = ctl->k + 1;
+        ctl->k = k;
+        if (cond) cudaGraphSetConditional(cond, k < (uint32_t)n_iter ? 1u : 0u);
     }
 }
 
@@ -1287,9 +1350,22 @@ void launch_cal_fill(const Slices& sl, int nbx, const int32_t* Nsp, float* T, fl
 
 void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
                      const double* inb, double* eacc, double* ecur, double* ebar, cudaStream_t s,
-                     int points, double* ebar_odd) {
+                     int points, double* ebar_odd, double* ebar_pts) {
     k_cal_step<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, Rp, chains, n_eq, t_fixed, ctl, inb, eacc,
-                                                  ecur, ebar, points, ebar_odd);
+                                                  ecur, ebar, points, ebar_odd, ebar_pts);
+}
+
+void launch_kpts_mid(int nblk, int points, const int32_t* Nsp, const float* lo, const float* hi,
+                     float* Tk, Control* ctl, cudaStream_t s) {
+    k_kpts_mid<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, points, Nsp, lo, hi, Tk, ctl);
+}
+
+void launch_kpts_update(int nblk, int points, double inv_count, const double* es,
+                        const int32_t* Nsp, const float* Tk, float* lo, float* hi,
+                        double* ebar_pts, Control* ctl, int n_iter,
+                        cudaGraphConditionalHandle cond, cudaStream_t s) {
+    k_kpts_update<<<grid_for(nblk, 256), 256, 0, s>>>(nblk, points, inv_count, es, Nsp, Tk, lo,
+                                                     hi, ebar_pts, ctl, n_iter, cond);
 }
 
 void launch_kcal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T0,

@@ -71,10 +71,19 @@ void launch_cal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* 
                     Control* ctl, cudaStream_t s);
 void launch_cal_fill(const Slices& sl, int nbx, const int32_t* Nsp, float* T, float* beta,
                      cudaStream_t s);
-// points = 2: even lanes' energies go to ebar, odd lanes' to ebar_odd.
+// points = 2: even lanes' energies go to ebar, odd lanes' to ebar_odd; points
+// > 2: lane r's to ebar_pts[r mod points].
 void launch_cal_step(int nblk, int Rp, int chains, int n_eq, int t_fixed, const Control* ctl,
                      const double* inb, double* eacc, double* ecur, double* ebar, cudaStream_t s,
-                     int points = 1, double* ebar_odd = nullptr);
+                     int points = 1, double* ebar_odd = nullptr, double* ebar_pts = nullptr);
+// k-point calibration (points = 4 or 8): the points of every bracket, and the
+// bracket update from the points' mean energies (Tk, ebar_pts: [points][nblk]).
+void launch_kpts_mid(int nblk, int points, const int32_t* Nsp, const float* lo, const float* hi,
+                     float* Tk, Control* ctl, cudaStream_t s);
+void launch_kpts_update(int nblk, int points, double inv_count, const double* es,
+                        const int32_t* Nsp, const float* Tk, float* lo, float* hi,
+                        double* ebar_pts, Control* ctl, int n_iter,
+                        cudaGraphConditionalHandle cond, cudaStream_t s);
 // Trisection (two temperatures per block per iteration).
 void launch_kcal_mid(int nblk, const int32_t* Nsp, const float* lo, const float* hi, float* T0,
                      float* T1, Control* ctl, cudaStream_t s);

@@ -414,8 +414,13 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
         const int sl = slice_of(a.sl, b);
         philox4x32_10_rk(local_index(slice_rect(a.sl, sl), y, x), ctr1,
                          (a.r_base + (uint32_t)rl) >> 1, 0u, a.rng.rk0, slice_key1(a.sl, sl), w);
-        beta = a.beta[b];
-        beta1 = a.beta_odd ? a.beta_odd[b] : beta;
+        if (a.beta_pts) {
+            beta = a.beta_pts[(size_t)(rl % a.n_pts) * a.g.nblk + b];
+            beta1 = a.beta_pts[(size_t)((rl + 1) % a.n_pts) * a.g.nblk + b];
+        } else {
+            beta = a.beta[b];
+            beta1 = a.beta_odd ? a.beta_odd[b] : beta;
+        }
     }
     grid_dep_wait();
     __syncthreads();

@@ -51,7 +51,7 @@ int main(void) {
   O(mpr_options, cal_method); O(mpr_options, t_init); O(mpr_options, sim_graph);
   O(mpr_options, cal_points); O(mpr_options, sim_tail); O(mpr_options, sweep_form);
   O(mpr_options, pair_tail); O(mpr_options, sweep_form_bulk); O(mpr_options, stop_rule);
-  O(mpr_options, n_fit); O(mpr_options, n_f); O(mpr_options, cal_warm);
+  O(mpr_options, n_fit); O(mpr_options, n_f);
   O(mpr_tuning, trial_ms);
   O(mpr_info, n_slices); O(mpr3_info, n_gap); O(mpr3_info, cal_gap_updates);
   O(mpr_tuning, ms); O(mpr_profile, sim_tail_updates); O(mpr_profile, sim_tail_ms);
@@ -83,7 +83,7 @@ def test_default_options_without_gpu():
     assert (o.q, o.J, o.n_max, o.n_eq, o.n_meas, o.n_bisect) == (0.5, 1.0, 200, 25, 20, 24)
     assert o.t_hi == 2.0 and abs(o.t_lo - 1e-4) < 1e-9 and o.overrelax == 1
     assert o.sweep_form == -1 and o.sim_tail == 0 and o.cal_points == 1 and o.pair_tail == 4096
-    assert (o.sweep_form_bulk, o.stop_rule, o.n_fit, o.n_f, o.cal_warm) == (-1, 0, 20, 5, 0)
+    assert (o.sweep_form_bulk, o.stop_rule, o.n_fit, o.n_f) == (-1, 0, 20, 5)
     assert mpr.load().mpr_status_string(4) == b"no sample pair"
     with pytest.raises(TypeError):
         mpr.mpr_default_options(nonsense=1)

@@ -85,3 +85,32 @@ def test_trisection_matches_oracle(chains, kind):
     gf = make(z, m, lb, cal_points=2, cal_mode=3, **opts)
     np.testing.assert_allclose(gf.calibrate(), T, rtol=1e-6)
     gf.close()
+
+
+@pytest.mark.parametrize("points,chains", [(4, 1), (8, 1), (4, 2)])
+def test_k_point_calibration_matches_oracle(points, chains):
+    """Calibration with 4 or 8 temperatures per block and iteration (lane r of
+    the chains at point r mod points; the bracket shrinks to the span between
+    the highest point whose mean energy is below e_s,b and the lowest point
+    whose mean is not) against the oracle's k-point calibration on the same
+    random streams; the graph and the host-launched forms agree."""
+    import oracle
+    H, W, lb = 48, 40, 8
+    z, m = synth.small_problem(H, W, 0.5, seed=H + points, kind="random")
+    n_iter = 6
+    opts = dict(seed=37, n_eq=6, n_meas=6, n_bisect=n_iter, cal_chains=chains)
+    gf = make(z, m, lb, cal_points=points, **opts)
+    T = gf.calibrate()
+    gf.close()
+    o = oracle.Oracle(H, W, lb, seed=37)
+    phi, *_ = o.transform(z, m)
+    st = o.block_stats(phi, m)
+    phi0 = o.init_block_mean(phi, m, st)
+    To = o.calibrate_points(phi0, m, st, n_eq=6, n_meas=6, n_iter=n_iter, chains=chains,
+                            points=points)
+    used = st.n_gap > 0
+    assert (np.abs(T - To) <= 1e-4 * To)[used].mean() >= 0.9
+    assert np.all((T > 1e-4) & (T < 2.0))
+    gf = make(z, m, lb, cal_points=points, cal_mode=3, **opts)
+    np.testing.assert_allclose(gf.calibrate(), T, rtol=1e-6)
+    gf.close()
