@@ -902,9 +902,19 @@ def run_ours_batch(args, world, rank, local):
     # stop-tail launch, which is timed and counted apart.
     sweep_updates = sim_updates - tail_updates
     achieved = sweep_updates * bpu / (hs_ms / 1e3) / 1e9 if hs_ms > 0 else None
+    # DRAM bytes per launch: the ncu-measured bytes per update of this kernel
+    # (profiles/traffic.json, captured on the 32-field batch of the same
+    # recipe) times the average updates per launch of this run.
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath) and sim_launch and storage == "bf16":
+        with open(tpath) as f:
+            rec = json.load(f).get(f"sim_{bw.name}")
+        if rec:
+            traffic = rec["bytes_per_update"] * sweep_updates / sim_launch
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-        "frac": (achieved / peak) if achieved else None, "traffic": None,
+        "frac": (achieved / peak) if achieved else None, "traffic": traffic,
         "kernel": "realizations' per-launch half-steps (k_sweep_half / k_sweep)",
         "peak_kind": peak_kind, "bytes_per_gap_update": bpu,
         "bytes_basis": "(s (1 + 2 p) + 1/8) / p at the batch's mean gap fraction p",
