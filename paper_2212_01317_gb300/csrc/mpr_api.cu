@@ -54,7 +54,6 @@ struct mpr_ctx {
     uint8_t* mask = nullptr;
     float* dang = nullptr;
     uint2* list[2] = {nullptr, nullptr};
-    float2* sfield[2] = {nullptr, nullptr};  // per list entry: its sample neighbours' (cos, sin) sum
     int32_t* start[2] = {nullptr, nullptr};
     int32_t* split[2] = {nullptr, nullptr};
     double* Es = nullptr;
@@ -345,7 +344,6 @@ SweepArgs sweep_args(mpr_ctx* ctx, int colour, bool simulate) {
     a.sl = ctx->sl;
     a.colour = colour;
     a.list = ctx->list[colour];
-    a.sfield = ctx->sfield[colour];
     a.start = ctx->start[colour];
     a.split = ctx->split[colour];
     a.ang = ctx->ang;
@@ -842,7 +840,6 @@ mpr_status calibration_persistent(mpr_ctx* ctx, double inv_count, bool* fallback
     a.sw.energy = 1;
     for (int c = 0; c < 2; ++c) {
         a.list[c] = ctx->list[c];
-        a.sfield[c] = ctx->sfield[c];
         a.start[c] = ctx->start[c];
         a.split[c] = ctx->split[c];
         a.n_list[c] = ctx->n_gap[c];
@@ -1299,12 +1296,6 @@ mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
     launch_build_lists(g, ctx->d_of_block, ctx->mask, ctx->start[0], ctx->start[1], ctx->list[0],
                        ctx->list[1], ctx->split[0], ctx->split[1], ctx->s);
     ++ctx->launches;
-    for (int c = 0; c < 2; ++c) {
-        ST(dalloc(ctx, &ctx->sfield[c], (size_t)std::max<int64_t>(1, ctx->n_gap[c])));
-        launch_sample_field(g, ctx->list[c], ctx->n_gap[c], c, ctx->dang, ctx->m.q, ctx->sfield[c],
-                            ctx->s);
-        ++ctx->launches;
-    }
     if (cudaMemsetAsync(ctx->sum, 0, 2 * plane * sizeof(double), ctx->s) ||
         cudaMemsetAsync(ctx->ctl, 0, sizeof(Control), ctx->s) ||
         cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), ctx->s) ||
@@ -1771,7 +1762,6 @@ SimTailArgs tail_args(mpr_ctx* ctx) {
     a.sw.energy = 1;
     for (int c = 0; c < 2; ++c) {
         a.list[c] = ctx->list[c];
-        a.sfield[c] = ctx->sfield[c];
         a.start[c] = ctx->start[c];
         a.split[c] = ctx->split[c];
     }

@@ -139,8 +139,6 @@ struct SweepArgs {
     Slices sl;
     int colour;
     const uint2* list;        // gap entries of this colour
-    const float2* sfield;     // per entry: sum over its sample neighbours of (cos, sin) of
-                              // q phi_j, in the order (left + right) + (up + down)
     const int32_t* start;     // [nblk + 1]
     const int32_t* split;     // [nblk] end of each block's edge entries
     void* ang;                // batch state [groups][2][H][Wh][G] (FP32, FP16 or BF16)
@@ -220,7 +218,6 @@ struct GridBarrier {
 struct SimTailArgs {
     SweepArgs sw;              // colour-independent sweep fields
     const uint2* list[2];
-    const float2* sfield[2];
     const int32_t* start[2];
     const int32_t* split[2];
     StopArgs st;
@@ -234,7 +231,6 @@ struct SimTailArgs {
 struct CalPersistArgs {
     SweepArgs sw;              // colour-independent sweep fields (ecur, ang, beta, ...)
     const uint2* list[2];
-    const float2* sfield[2];
     const int32_t* start[2];
     const int32_t* split[2];
     int64_t n_list[2];

@@ -273,34 +273,6 @@ __global__ void k_build_lists(Geom g, const int32_t* __restrict__ of_block,
     }
 }
 
-// Per gap entry of colour c: the sum over its sample neighbours (they never
-// change) of (cos q phi_j, sin q phi_j), in the order (left + right) + (up +
-// down) with 0 for a gap or missing neighbour; the half-steps add their gap
-// neighbours' terms to it.
-__global__ void k_sample_field(Geom g, const uint2* __restrict__ list, int64_t n_list, int colour,
-                               const float* __restrict__ dang, float q, float2* __restrict__ out) {
-    const float* dn = dang + (size_t)(colour ^ 1) * g.H * g.Wh;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_list;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const uint2 en = list[e];
-        const int y = en.x >> 16, x = en.x & 0xffff;
-        const uint32_t f = en.y;
-        const uint32_t hs = (uint32_t)y * (uint32_t)g.Wh + (uint32_t)(x >> 1);
-        const uint32_t o = (uint32_t)(x & 1);
-        const uint32_t hn[4] = {hs + o - 1u, hs + o, hs - (uint32_t)g.Wh, hs + (uint32_t)g.Wh};
-        float c[4], sn[4];
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const bool smp = (f & (NB_L << d)) && !(f & (GAP_L << d));
-            float sv = 0.0f, cv = 0.0f;
-            if (smp) __sincosf(q * dn[hn[d]], &sv, &cv);
-            c[d] = smp ? cv : 0.0f;
-            sn[d] = smp ? sv : 0.0f;
-        }
-        out[e] = make_float2((c[0] + c[1]) + (c[2] + c[3]), (sn[0] + sn[1]) + (sn[2] + sn[3]));
-    }
-}
-
 // ------------------------------------------------------------------ init --
 // Sec. 3.3.3: every gap site starts from the sample mean angle of its block
 // (global sample mean when the block has no sample); random start (plain
@@ -1149,12 +1121,6 @@ void launch_block_stats(const Geom& g, const Slices& sl, const float* values, co
 
 void launch_scan(const int32_t* cnt, int n, int32_t* out, cudaStream_t s) {
     k_scan_counts<<<1, 1024, 0, s>>>(cnt, n, out);
-}
-
-void launch_sample_field(const Geom& g, const uint2* list, int64_t n_list, int colour,
-                         const float* dang, float q, float2* out, cudaStream_t s) {
-    if (n_list == 0) return;
-    k_sample_field<<<grid_for(n_list, 256), 256, 0, s>>>(g, list, n_list, colour, dang, q, out);
 }
 
 void launch_build_lists(const Geom& g, const int32_t* of_block, const uint8_t* mask,

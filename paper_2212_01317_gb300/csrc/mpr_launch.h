@@ -25,10 +25,6 @@ void launch_scan(const int32_t* cnt, int n, int32_t* out, cudaStream_t s);
 void launch_build_lists(const Geom& g, const int32_t* of_block, const uint8_t* mask,
                         const int32_t* start0, const int32_t* start1, uint2* list0, uint2* list1,
                         int32_t* split0, int32_t* split1, cudaStream_t s);
-// Per gap entry of a colour's list: the sum of its sample neighbours' (cos,
-// sin) of q phi (SweepArgs::sfield).
-void launch_sample_field(const Geom& g, const uint2* list, int64_t n_list, int colour,
-                         const float* dang, float q, float2* out, cudaStream_t s);
 // `storage` is an mpr_storage value (0 FP32, 1 BF16, 2 FP16): the element
 // type of the batch state `ang`.
 void launch_init(const Geom& g, const Slices& sl, const uint2* list, int64_t n_list, int colour,

@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_tail(SimTailArgs a) {
             SweepArgs s = a.sw;
             s.colour = c;
             s.list = a.list[c];
-            s.sfield = a.sfield[c];
             s.start = a.start[c];
             s.split = a.split[c];
             for (uint32_t it = slot; it < n; it += nslot) {

@@ -22,7 +22,6 @@ __device__ __forceinline__ SweepArgs colour_args(const CalPersistArgs& a, int c)
     SweepArgs s = a.sw;
     s.colour = c;
     s.list = a.list[c];
-    s.sfield = a.sfield[c];
     s.start = a.start[c];
     s.split = a.split[c];
     return s;

@@ -64,7 +64,6 @@ __global__ void __launch_bounds__(kTailThreads, 2) k_sim_tail(SimTailArgs a) {
             SweepArgs s = a.sw;
             s.colour = c;
             s.list = a.list[c];
-            s.sfield = a.sfield[c];
             s.start = a.start[c];
             s.split = a.split[c];
             if (gi < ngrp)

@@ -197,78 +197,6 @@ __device__ __forceinline__ void neighbour_field(const SweepArgs& a, const S* __r
     }
 }
 
-// The half-index offsets of the four neighbours (left, right, up, down) of
-// the site at half index hs and column x.
-__device__ __forceinline__ void neighbour_index(const SweepArgs& a, uint32_t hs, int x,
-                                                uint32_t hn[4]) {
-    const uint32_t o = (uint32_t)(x & 1);
-    hn[0] = hs + o - 1u;
-    hn[1] = hs + o;
-    hn[2] = hs - (uint32_t)a.g.Wh;
-    hn[3] = hs + (uint32_t)a.g.Wh;
-}
-
-// (cos, sin) of q phi_j of the gap neighbours of both realizations of the
-// pair (0 at sample and missing neighbours: the samples' sum comes with the
-// list entry, see neighbour_sums), and, where the site's left / up bond
-// belongs to the neighbouring block and that neighbour is a sample, that
-// sample's (cos, sin) (the bond-by-bond energy split needs it).
-template <typename S>
-__device__ __forceinline__ void gap_neighbour_field(const SweepArgs& a, const S* __restrict__ oth,
-                                                    int G, uint32_t hs, int x, uint32_t f,
-                                                    float* nc0, float* ns0, float* nc1,
-                                                    float* ns1) {
-    uint32_t hn[4];
-    neighbour_index(a, hs, x, hn);
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        const bool gp = (f & (GAP_L << d)) != 0;
-        const float2 v = gp ? Store<S>::load2(oth + (size_t)hn[d] * G) : make_float2(0.0f, 0.0f);
-        float s0, c0, s1, c1;
-        __sincosf(a.m.q * v.x, &s0, &c0);
-        __sincosf(a.m.q * v.y, &s1, &c1);
-        nc0[d] = gp ? c0 : 0.0f;
-        ns0[d] = gp ? s0 : 0.0f;
-        nc1[d] = gp ? c1 : 0.0f;
-        ns1[d] = gp ? s1 : 0.0f;
-    }
-}
-
-// The local field of both realizations: the entry's sample sum plus the gap
-// neighbours' (cos, sin) summed (left + right) + (up + down).
-__device__ __forceinline__ void neighbour_sums(float2 sf, const float* nc0, const float* ns0,
-                                               const float* nc1, const float* ns1, float& C0,
-                                               float& S0, float& C1, float& S1) {
-    C0 = sf.x + ((nc0[0] + nc0[1]) + (nc0[2] + nc0[3]));
-    S0 = sf.y + ((ns0[0] + ns0[1]) + (ns0[2] + ns0[3]));
-    C1 = sf.x + ((nc1[0] + nc1[1]) + (nc1[2] + nc1[3]));
-    S1 = sf.y + ((ns1[0] + ns1[1]) + (ns1[2] + ns1[3]));
-}
-
-// For a block-edge entry: the left / up sample neighbour's (cos, sin), put
-// where the energy split reads them (index 0 left, 2 up). Sample angles come
-// from the FP32 per-colour table, so both forms of the state see one value.
-__device__ __forceinline__ void edge_sample_field(const SweepArgs& a, uint32_t hs, int x, uint32_t f,
-                                                  float* nc0, float* ns0, float* nc1,
-                                                  float* ns1) {
-    if (!(f & (EDGE_L | EDGE_U))) return;
-    uint32_t hn[4];
-    neighbour_index(a, hs, x, hn);
-    const float* dn = a.dang + (size_t)(a.colour ^ 1) * a.g.H * a.g.Wh;
-    if ((f & EDGE_L) && !(f & GAP_L)) {
-        float s, c;
-        __sincosf(a.m.q * dn[hn[0]], &s, &c);
-        nc0[0] = nc1[0] = c;
-        ns0[0] = ns1[0] = s;
-    }
-    if ((f & EDGE_U) && !(f & GAP_U)) {
-        float s, c;
-        __sincosf(a.m.q * dn[hn[2]], &s, &c);
-        nc0[2] = nc1[2] = c;
-        ns0[2] = ns1[2] = s;
-    }
-}
-
 __device__ __forceinline__ void pair_running(const SweepArgs& a, int b, int rl, bool& run0,
                                              bool& run1) {
     if (a.running) {
@@ -323,12 +251,12 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
         uint32_t w[4];
         philox4x32_10_rk(local_index(rc, y, x), ctr1, rpair, 0u, a.rng.rk0, key1, w);
         const float2 ph = Store<S>::load2(own + (size_t)hs * G);
-        const float2 sf = a.sfield[e];
         float nc0[4], ns0[4], nc1[4], ns1[4];
-        gap_neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
-        float C0, S0, C1, S1;
-        neighbour_sums(sf, nc0, ns0, nc1, ns1, C0, S0, C1, S1);
-        edge_sample_field(a, hs, x, f, nc0, ns0, nc1, ns1);
+        neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
+        const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
+        const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
+        const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
+        const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
         const float bt = a.beta_site ? a.beta_site[(size_t)y * a.g.W + x] : beta;
         float2 out = ph;
         if (run0) {
@@ -408,12 +336,12 @@ __device__ __forceinline__ void sweep_item_half(const SweepArgs& a, int item, in
             uint32_t w[4];
             philox4x32_10_rk(local_index(rc, y, x), ctr1, rpair, 0u, a.rng.rk0, key1, w);
             const float2 ph = Store<S>::load2(own + (size_t)hs * G);
-            const float2 sf = a.sfield[e];
             float nc0[4], ns0[4], nc1[4], ns1[4];
-            gap_neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
-            float C0, S0, C1, S1;
-            neighbour_sums(sf, nc0, ns0, nc1, ns1, C0, S0, C1, S1);
-            edge_sample_field(a, hs, x, f, nc0, ns0, nc1, ns1);
+            neighbour_field<S>(a, oth, G, hs, x, f, nc0, ns0, nc1, ns1);
+            const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
+            const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
+            const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
+            const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
             const float bt = a.beta_site ? a.beta_site[(size_t)y * a.g.W + x] : beta;
             float2 out = ph;
             if (run0) {
@@ -476,13 +404,11 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
     const bool live = e < n_list;
     const int rl = grp * G + 2 * q;
     uint2 en = make_uint2(0u, 0u);
-    float2 sf = make_float2(0.0f, 0.0f);
     int b = b0;
     uint32_t w[4] = {0u, 0u, 0u, 0u};
     float beta = 0.0f, beta1 = 0.0f;
     if (live) {
         en = a.list[e];
-        sf = a.sfield[e];
         b = (int)(en.y >> META_SHIFT);
         const int y = en.x >> 16, x = en.x & 0xffff;
         const int sl = slice_of(a.sl, b);
@@ -514,11 +440,12 @@ __device__ __forceinline__ void sweep_flat(const SweepArgs& a, int64_t n_list, u
             const uint32_t hs = (uint32_t)y * (uint32_t)a.g.Wh + (uint32_t)(x >> 1);
             const float2 ph = own[(size_t)hs * NP];
             float nc0[4], ns0[4], nc1[4], ns1[4];
-            gap_neighbour_field<float>(a, reinterpret_cast<const float*>(oth), G, hs, x, f, nc0,
-                                       ns0, nc1, ns1);
-            float C0, S0, C1, S1;
-            neighbour_sums(sf, nc0, ns0, nc1, ns1, C0, S0, C1, S1);
-            edge_sample_field(a, hs, x, f, nc0, ns0, nc1, ns1);
+            neighbour_field<float>(a, reinterpret_cast<const float*>(oth), G, hs, x, f, nc0, ns0,
+                                   nc1, ns1);
+            const float C0 = (nc0[0] + nc0[1]) + (nc0[2] + nc0[3]);
+            const float S0 = (ns0[0] + ns0[1]) + (ns0[2] + ns0[3]);
+            const float C1 = (nc1[0] + nc1[1]) + (nc1[2] + nc1[3]);
+            const float S1 = (ns1[0] + ns1[1]) + (ns1[2] + ns1[3]);
             float2 out = ph;
             if (run0) {
                 const SiteNew n = site_update<float>(ph.x, C0, S0, u01(w[0]), u01(w[1]), beta, a.m);

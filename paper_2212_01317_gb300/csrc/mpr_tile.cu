@@ -240,16 +240,10 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_sweep_tile(SweepArgs a) {
             const float4 R = stage[(r * ncol + kr) * 4 + q];
             const float4 U = stage[((r - 1) * ncol + hc) * 4 + q];
             const float4 D = stage[((r + 1) * ncol + hc) * 4 + q];
-            // The local field as the warp forms sum it: the sample neighbours'
-            // part (their precomputed sum there) plus the gap neighbours'.
-            const bool gl = (f & GAP_L) != 0, gr = (f & GAP_R) != 0;
-            const bool gu = (f & GAP_U) != 0, gd = (f & GAP_D) != 0;
-            const float sc = ((gl ? 0.f : L.x) + (gr ? 0.f : R.x)) + ((gu ? 0.f : U.x) + (gd ? 0.f : D.x));
-            const float ss = ((gl ? 0.f : L.y) + (gr ? 0.f : R.y)) + ((gu ? 0.f : U.y) + (gd ? 0.f : D.y));
-            const float C0 = sc + (((gl ? L.x : 0.f) + (gr ? R.x : 0.f)) + ((gu ? U.x : 0.f) + (gd ? D.x : 0.f)));
-            const float S0 = ss + (((gl ? L.y : 0.f) + (gr ? R.y : 0.f)) + ((gu ? U.y : 0.f) + (gd ? D.y : 0.f)));
-            const float C1 = sc + (((gl ? L.z : 0.f) + (gr ? R.z : 0.f)) + ((gu ? U.z : 0.f) + (gd ? D.z : 0.f)));
-            const float S1 = ss + (((gl ? L.w : 0.f) + (gr ? R.w : 0.f)) + ((gu ? U.w : 0.f) + (gd ? D.w : 0.f)));
+            const float C0 = (L.x + R.x) + (U.x + D.x);
+            const float S0 = (L.y + R.y) + (U.y + D.y);
+            const float C1 = (L.z + R.z) + (U.z + D.z);
+            const float S1 = (L.w + R.w) + (U.w + D.w);
             const uint32_t hs = (uint32_t)y * (uint32_t)g.Wh + (uint32_t)(x >> 1);
             S* po = own + (size_t)hs * G + 2 * q;
             const float2 ph = Store<S>::load2(po);
