@@ -183,10 +183,10 @@ def test_field16384_bf16_sampled_sites(field16384):
 
 
 def test_field16384_energy_derivative_against_central_differences(field16384):
-    """d<e_b>/d beta_b from the fluctuation identity (the Newton calibration's
-    Jacobian diagonal) at full size, against central differences of the
-    chains' mean block energy with common random numbers, on the blocks whose
-    diagonal dominates (many gap sites)."""
+    """d<e_b>/d beta from the fluctuation identity (the Newton calibration's
+    Jacobian: the diagonal and the neighbouring blocks' covariances) at full
+    size, against central differences of the chains' mean block energy with
+    common random numbers, on the blocks with many gap sites."""
     import torch
     wl = field16384
     gf = GapFiller(wl.values, wl.mask, wl.block, seed=5, cal_chains=1)
@@ -198,7 +198,17 @@ def test_field16384_energy_derivative_against_central_differences(field16384):
     outs = [torch.empty(nb, dtype=torch.float64, device=dev) for _ in range(4)]
     mpr.mpr_energy_moments(gf.ctx, beta, n_eq, n_meas, 1, True, *outs)
     y, var = outs[0].cpu().numpy(), outs[1].cpu().numpy()
-    dy_fluct = -var / np.maximum(Nb, 1)
+    cr, cd = outs[2].cpu().numpy(), outs[3].cpu().numpy()
+    # Every beta moves at once below, so the difference measures a row sum of
+    # the Jacobian: -(Var(E_b) + the covariances with the four neighbouring
+    # blocks) / N_b by the fluctuation identity (blocks further away couple
+    # only through these).
+    nbx = gf.info.nbx
+    bx = np.arange(nb) % nbx
+    row = var + cr + cd
+    row[bx > 0] += cr[np.flatnonzero(bx > 0) - 1]
+    row[nbx:] += cd[:nb - nbx]
+    dy_fluct = -row / np.maximum(Nb, 1)
     h = 0.03 * float(beta[0])
     ys = []
     for sgn in (+1, -1):
@@ -206,10 +216,9 @@ def test_field16384_energy_derivative_against_central_differences(field16384):
         mpr.mpr_energy_moments(gf.ctx, beta + sgn * h, n_eq, n_meas, 1, True, mean_e=o2)
         ys.append(o2.cpu().numpy())
     dy_fd = (ys[0] - ys[1]) / (2 * h)
-    # Every beta moved at once: the difference is the Jacobian's row sum, the
-    # identity's diagonal plus the neighbouring blocks' covariances (a few per
-    # cent for 64 x 64 blocks). Compared on the mean over the blocks with many
-    # gap sites, within the spread over blocks.
+    # Compared on the mean over the blocks with many gap sites, within the
+    # spread over blocks plus 15 % (the identity is exact for the equilibrium
+    # Gibbs law; the chains measure after 30 sweeps from the block-mean start).
     sel = (ng > 0.5 * wl.block * wl.block) & (Nb > 0)
     assert sel.sum() > 100
     assert np.all(np.isfinite(y[Nb > 0]))
