@@ -129,7 +129,7 @@ typedef struct {
                             barriers between the phases); 0: never; values above 4096 act as
                             4096 (the default: 0.65 ms of 23.8 ms saved per 1024^2 bench step);
                             sim_tail > 0 takes precedence */
-    int32_t sweep_form_bulk; /* with sweep_form = -1: the half-step form while at least half
+    int32_t sweep_form_bulk; /* with sweep_form = -1: the half-step form while at least 7/8
                                 of the (block, realization) pairs run (-1 the built-in choice by
                                 gap sites per block, else 0, 3 or 4 as in sweep_form, e.g. an
                                 earlier mpr_autotune's choice); afterwards the built-in choice */
@@ -327,7 +327,7 @@ mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae
  * mpr_autotune times the realizations' half-step decompositions on trial
  * batches of n_realizations realizations (their first n_sweeps sweeps, every
  * block running, CUDA events on the context's stream) and keeps the fastest
- * for the context's later simulations while at least half of the pairs run
+ * for the context's later simulations while at least 7/8 of the pairs run
  * (sweep_form = -1; afterwards the built-in choice). Candidates k:
  *   0: G = 8, one warp per (block, realization pair) unit (sweep form 0);
  *   1: G = 8, two units per warp (form 3);

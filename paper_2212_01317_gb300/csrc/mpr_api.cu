@@ -444,13 +444,14 @@ int sweep_form(mpr_ctx* ctx) {
     if (ctx->opt.sweep_form == 4) return tile_form_ok(ctx) ? 4 : 0;
     if (ctx->opt.sweep_form >= 0) return ctx->opt.sweep_form;
     if (ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm) return 2;
-    // An autotuned (or asked-for) form holds while at least half of the pairs
+    // An autotuned (or asked-for) form holds while at least 7/8 of the pairs
     // run: the autotuner times the first sweeps, where every pair runs. (On
     // the 256-field batch the first two sweeps ran 7 % faster with two pairs
-    // per warp, the whole run 2.5 % slower.)
+    // per warp, the whole run 2.5 % slower, and still 1.7 % slower with the
+    // form held while half of the pairs ran.)
     const int bulk = ctx->tuned_form >= 0 ? ctx->tuned_form : ctx->opt.sweep_form_bulk;
     const unsigned long long pairs = (unsigned long long)ctx->g.nblk * (ctx->Rp / 2);
-    if (bulk >= 0 && ctx->bound >= pairs / 2) {
+    if (bulk >= 0 && ctx->bound >= pairs - pairs / 8) {
         if (bulk == 4) return tile_form_ok(ctx) ? 4 : 0;
         return bulk;
     }
