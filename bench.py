@@ -64,7 +64,12 @@ def parse(argv=None):
                          "2 trisection, the default: the two temperatures run on the two "
                          "lanes of a realization pair); --cal-iters sets the iterations")
     ap.add_argument("--cal-iters", type=int, default=None,
-                    help="calibration iterations (default 24 for bisection, 16 for trisection)")
+                    help="calibration iterations (default 24 for bisection, 16 for trisection; "
+                         "with --cal-warm two fewer for trisection)")
+    ap.add_argument("--cal-warm", type=float, default=1.5,
+                    help="warm start of the calibration from the unconditional e(T) curve: the "
+                         "first iteration's points on [T0/w, T0 w] (default 1.5; 0: off; "
+                         "ignored for bisection)")
     ap.add_argument("--plain-steps", type=int, default=3,
                     help="batch workloads: steps of the plain form (one FP32 context per "
                          "field, every field of the batch) timed after the chosen form")
@@ -74,11 +79,13 @@ def parse(argv=None):
                     help="batch workloads: the sweep loop as one CUDA graph")
     ap.add_argument("--sweep-form", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="realizations' half-step form (-1 automatic; 4 the staged half-step)")
-    ap.add_argument("--autotune", type=int, default=2,
+    ap.add_argument("--autotune", type=int, default=8,
                     help="batch workloads: the first warm-up step times the half-step "
                          "decompositions on a trial batch of all R realizations over this many "
                          "sweeps (mpr_autotune) and the timed steps run the chosen one (0: off, "
-                         "the library's built-in choice)")
+                         "the library's built-in choice). The default, 8, is the window the "
+                         "chosen form is sure to run: the loop learns the running count two "
+                         "chunks of four sweeps late")
     ap.add_argument("--calibration", default="bisection", choices=["bisection", "newton"],
                     help="per-block temperature fit: bisection (the plain form) or safeguarded "
                          "Newton steps from the fluctuation identity")
@@ -110,12 +117,25 @@ def dist_env():
     return world, rank, local
 
 
+def warm_w(args) -> float:
+    """The warm-start factor the library gets: --cal-warm for the k-point
+    calibrations (2, 4, 8 points), 0 for bisection and Newton."""
+    if getattr(args, "calibration", "bisection") != "bisection" or args.cal_points < 2:
+        return 0.0
+    return float(getattr(args, "cal_warm", 0.0))
+
+
 def cal_iters(args) -> int:
     """Calibration iterations: 24 bisection steps, or 16 trisection steps (a
     narrower final bracket: 2 / 3^16 < 2 / 2^24), 11 steps of 4 points
-    (5^11 > 3^16), 8 of 8 points (9^8 = 3^16)."""
+    (5^11 > 3^16), 8 of 8 points (9^8 = 3^16). The warm start's first step
+    leaves (w - 1/w) T0 = 0.83 T0 (w = 1.5) around a root near the curve's T0,
+    so 14 trisection steps (0.83 T0 / 3^13), 10 of 4 points, 7 of 8 points
+    end about as narrow as the cold ones for T0 near 0.1."""
     if args.cal_iters is not None:
         return args.cal_iters
+    if warm_w(args) > 0:
+        return {2: 14, 4: 10, 8: 7}[args.cal_points]
     return {1: 24, 2: 16, 4: 11, 8: 8}[args.cal_points]
 
 
@@ -203,7 +223,8 @@ def cal_label(args) -> str:
     if args.calibration == "newton":
         return "newton"
     name = {1: "bisection", 2: "trisection", 4: "4-point section", 8: "8-point section"}
-    return name[args.cal_points] + f" x{cal_iters(args)}"
+    warm = f"warm (w = {warm_w(args):g}) " if warm_w(args) > 0 else ""
+    return warm + name[args.cal_points] + f" x{cal_iters(args)}"
 
 
 def batch_config(args, world) -> dict:
@@ -247,7 +268,15 @@ def oracle_calibrate(o, phi0, mask, st, args):
         return o.calibrate_newton(phi0, mask, st)
     if args.cal_points == 1:
         return o.calibrate(phi0, mask, st, n_bisect=cal_iters(args))
-    return o.calibrate_points(phi0, mask, st, n_iter=cal_iters(args), points=args.cal_points)
+    T0 = None
+    if warm_w(args) > 0:
+        # the library's default curve: 40 temperatures geometric on [0.002, 1.25],
+        # the calibration's 25 + 20 sweeps, key (0, 0)
+        import oracle
+        Tc = np.geomspace(0.002, 1.25, 40).astype(np.float32).astype(np.float64)
+        T0 = o.warm_T0(st, Tc, oracle.energy_curve(Tc, L=64, n_eq=25, n_meas=20, seed=0))
+    return o.calibrate_points(phi0, mask, st, n_iter=cal_iters(args), points=args.cal_points,
+                              T0_warm=T0, warm=warm_w(args) if T0 is not None else 1.5)
 
 
 ORACLE_R_PER_STEP = 5     # realizations of the oracle's sample field per step
@@ -414,7 +443,7 @@ def run_ours(args, world, rank, local):
                                        storage=STORAGE[storage], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
-                                       sweep_form=args.sweep_form,
+                                       cal_warm=warm_w(args), sweep_form=args.sweep_form,
                                        cuda_stream=stream.cuda_stream)
 
     sim_ev = []
@@ -699,7 +728,8 @@ def run_ours_batch(args, world, rank, local):
                                        storage=STORAGE[st], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
-                                       sim_graph=args.sim_graph, sweep_form=args.sweep_form,
+                                       cal_warm=warm_w(args), sim_graph=args.sim_graph,
+                                       sweep_form=args.sweep_form,
                                        sweep_form_bulk=tuned["bulk"],
                                        cuda_stream=stream.cuda_stream)
 

@@ -96,7 +96,10 @@ typedef struct {
     int32_t barrier_test; /* test hook: extra arrivals the grid barrier waits for (default 0);
                              > 0 makes every wait give up after wait_ms */
     int32_t cal_method;  /* 0 bisection (default), 1 damped Newton steps on beta_b with
-                            d<e_b>/d beta_b = -Var(E_b)/N_b (see mpr_energy_moments) */
+                            d<e_b>/d beta_b = -Var(E_b)/N_b (see mpr_energy_moments),
+                            2 the unconditional curve: T_b = T0_b, where the data-free curve
+                            e(T) reaches e_s,b (see mpr_get_energy_curve; no simulation of
+                            the field) */
     int32_t n_newton;    /* Newton iterations (default 6), each n_eq + n_meas sweeps */
     float t_init;        /* Newton starting temperature (default 0.1) */
     int32_t sim_graph;   /* 1: mpr_simulate runs its sweep loop as one CUDA graph (a device-side
@@ -129,13 +132,24 @@ typedef struct {
                             barriers between the phases); 0: never; values above 4096 act as
                             4096 (the default: 0.65 ms of 23.8 ms saved per 1024^2 bench step);
                             sim_tail > 0 takes precedence */
-    int32_t sweep_form_bulk; /* with sweep_form = -1: the half-step form while at least 7/8
-                                of the (block, realization) pairs run (-1 the built-in choice by
-                                gap sites per block, else 0, 3 or 4 as in sweep_form, e.g. an
-                                earlier mpr_autotune's choice); afterwards the built-in choice */
+    int32_t sweep_form_bulk; /* with sweep_form = -1: the half-step form while the running
+                                count is unknown (-1 the built-in choice by gap sites per block,
+                                else 0, 3 or 4 as in sweep_form, e.g. an earlier mpr_autotune's
+                                choice): mpr_simulate's first 8 sweeps (its loop reads the count
+                                two chunks of four sweeps late), every sweep of the graph form
+                                and of mpr_sim_sweep; afterwards the built-in choice */
     int32_t stop_rule;   /* mpr_stop_rule (default MPR_STOP_CROSS) */
     int32_t n_fit;       /* MPR_STOP_WINDOW: sweeps in the least-squares window (default 20) */
     int32_t n_f;         /* MPR_STOP_WINDOW: sweeps between two window tests (default 5) */
+    float cal_warm;      /* 0: off (default). w > 1 (at most 100): warm start of the calibration
+                            from the unconditional curve (see mpr_get_energy_curve): the first
+                            iteration's cal_points points lie evenly on [T0_b / w, T0_b w]; the
+                            k-point rule then keeps [t_lo, first point], the span between two
+                            points, or [last point, t_hi], and the other n_bisect - 1
+                            iterations k-section it. Needs cal_points >= 2, cal_method 0, a
+                            cal_mode other than 2, and the curve's first temperature / w above
+                            t_lo and its last one * w below t_hi (the default curve and bracket
+                            allow w < 1.6) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 
@@ -245,7 +259,9 @@ mpr_status mpr_get_profile(mpr_ctx* ctx, mpr_profile* out);
  * every targeted block moves to beta_b + (y_b - e_s,b) N_b / Var(E_b), the
  * new T kept within a factor 2 of the old one and within [t_lo, t_hi] (T
  * doubled when that beta is <= 0; without variance, doubled or halved
- * towards e_s,b). Starts at t_init.
+ * towards e_s,b). Starts at t_init. With cal_warm > 1 the first iteration's
+ * points come from the unconditional curve (see cal_warm); with
+ * cal_method = 2 T_b is read off that curve without simulating the field.
  * block_T_out: NULL or nblk floats (host or device), row-major blocks.
  * Errors: EINVAL, ECUDA. A degenerate field (z_max == z_min) skips the
  * iterations and sets every T_b to t_lo. */
@@ -254,6 +270,34 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out);
 /* Sets the block temperatures directly (nblk floats > 0, host or device). */
 mpr_status mpr_set_temperatures(mpr_ctx* ctx, const float* block_T);
 mpr_status mpr_get_temperatures(mpr_ctx* ctx, float* block_T_out);
+
+/* ---- the unconditional e(T) curve ----
+ * Plain MPR (Sec. 2.1) matches e_s against the specific energy of the
+ * simulated grid. On a lattice without data that energy depends on T alone:
+ * the unconditional curve e(T). The library measures it the way the
+ * calibration measures a block: a data-free 64 x 64 lattice (open
+ * boundaries), every angle started at pi, n_eq sweeps, then
+ * E / N_bonds (N_bonds = 2 * 64 * 63) averaged over n_meas sweeps (the
+ * context's n_eq, n_meas, q, J and over-relaxation); temperature k is
+ * realization k of the random-stream tag 0xFFFE under the fixed key (0, 0),
+ * so the curve depends on those five parameters only and is measured once
+ * per process for each set of them. The measured curve has MPR_CURVE_POINTS
+ * temperatures, geometric from 0.002 to 1.25 (as floats). T0_b is the temperature at which the
+ * curve's non-decreasing envelope (each e raised to the largest before it)
+ * reaches e_s,b, by linear interpolation, clamped to the first and last point.
+ * The curve feeds cal_warm and cal_method = 2.
+ *
+ * mpr_get_energy_curve: measures the curve if the context has none, then
+ * copies its n points into T_out (floats) and e_out (doubles), host or
+ * device, each with room for `capacity`; *n_out = n. Errors: EINVAL (a NULL
+ * pointer, capacity < n), ECUDA.
+ * mpr_set_energy_curve: replaces the context's curve by n caller points
+ * (2 <= n <= 64; host or device): T > 0, finite and strictly increasing,
+ * e finite. Copied. Errors: EINVAL. */
+#define MPR_CURVE_POINTS 40
+mpr_status mpr_get_energy_curve(mpr_ctx* ctx, float* T_out, double* e_out, int32_t capacity,
+                                int32_t* n_out);
+mpr_status mpr_set_energy_curve(mpr_ctx* ctx, const float* T, const double* e, int32_t n);
 
 /* ---- differentiable energy matching ----
  * The calibration (Sec. 2.1, applied per block in Sec. 2.2.2) matches the
@@ -327,8 +371,10 @@ mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae
  * mpr_autotune times the realizations' half-step decompositions on trial
  * batches of n_realizations realizations (their first n_sweeps sweeps, every
  * block running, CUDA events on the context's stream) and keeps the fastest
- * for the context's later simulations while at least 7/8 of the pairs run
- * (sweep_form = -1; afterwards the built-in choice). Candidates k:
+ * for the context's later simulations while their running count is unknown
+ * (sweep_form = -1; see sweep_form_bulk: mpr_simulate's first 8 sweeps, so
+ * n_sweeps = 8 times exactly the sweeps the choice governs; afterwards the
+ * built-in choice). Candidates k:
  *   0: G = 8, one warp per (block, realization pair) unit (sweep form 0);
  *   1: G = 8, two units per warp (form 3);
  *   2: G = 8, the staged half-step on tiles of at most 16 x 32 sites (form 4);
@@ -455,8 +501,8 @@ mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_t* mask, co
  * from the block-mean start with the per-block stop (Sec. 3.4), the mean
  * back-transformed. Random numbers: counter (site index, t | tag << 16,
  * r / 2, 0), words 2 (r mod 2) and 2 (r mod 2) + 1, key (seed_lo, seed_hi ^
- * slice_id). FP32 state; the storage, group, cal_mode / cal_method, SST,
- * sim_graph and sweep_form options do not apply; stop_rule must be
+ * slice_id). FP32 state; the storage, group, cal_mode / cal_method /
+ * cal_warm, SST, sim_graph and sweep_form options do not apply; stop_rule must be
  * MPR_STOP_CROSS (else EINVAL). Realizations of one call carry indices
  * r_next, r_next + 1, ... with r_next the accumulated count rounded up to
  * even. Arrays are D*H*W (sites, row-major) or nblk (blocks); pointers

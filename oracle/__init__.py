@@ -98,7 +98,9 @@ def lib():
             "orc_scores": (None, [i64, P, P, P, P, P]),
             "orc_sst_temperatures": (None, [MP, P, i32, i32, P]),
             "orc_calibrate_points": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, i32, f64, f64,
-                                            P]),
+                                            P, f64, P]),
+            "orc_energy_curve": (None, [f64, f64, u64, i32, i32, i32, P, i32, i32, P]),
+            "orc_curve_T0": (f64, [i32, P, P, f64]),
             "orc3_model_init": (None, [MP, i32, i32, i32, i32, f64, f64, u64, u32]),
             "orc3_block_stats": (None, [MP, P, P, P, P, P, P, P, P, P]),
             "orc3_block_energy": (None, [MP, P, P]),
@@ -357,14 +359,23 @@ class Oracle:
         return (T, tr) if trace else T
 
     def calibrate_points(self, phi_init, mask, st: BlockStats, n_eq=25, n_meas=20, n_iter=16,
-                         chains=1, points=2, T_lo=1e-4, T_hi=2.0):
+                         chains=1, points=2, T_lo=1e-4, T_hi=2.0, T0_warm=None, warm=1.5):
+        """k-point calibration; T0_warm (per block, from curve_T0) starts the
+        first iteration's points on [T0 / warm, T0 * warm]."""
         ph = np.ascontiguousarray(phi_init, dtype=np.float64)
         mk = np.ascontiguousarray(mask, dtype=np.uint8)
         T = np.zeros(self.nblk)
+        t0 = None if T0_warm is None else np.ascontiguousarray(T0_warm, dtype=np.float64)
         lib().orc_calibrate_points(C.byref(self.m), _p(ph), _p(mk), _p(st.Es), _p(st.Nsp),
                                    _p(st.Nb), n_eq, n_meas, n_iter, chains, points, T_lo, T_hi,
-                                   _p(T))
+                                   None if t0 is None else _p(t0), float(warm), _p(T))
         return T
+
+    def warm_T0(self, st: BlockStats, T_curve, e_curve) -> np.ndarray:
+        """Per-block T0 = curve_T0(e_s,b) (0 for blocks without sample bonds)."""
+        es = st.es
+        return np.array([curve_T0(T_curve, e_curve, es[b]) if st.Nsp[b] > 0 else 0.0
+                         for b in range(self.nblk)])
 
     @staticmethod
     def median_targeted(T, Nsp) -> float:
@@ -380,6 +391,23 @@ class Oracle:
         a, r = C.c_double(), C.c_double()
         lib().orc_scores(p.size, _p(p), _p(t), _p(mk), C.byref(a), C.byref(r))
         return a.value, r.value
+
+
+def energy_curve(T, L: int = 64, n_eq: int = 25, n_meas: int = 20, seed: int = 0,
+                 q: float = 0.5, J: float = 1.0, overrelax: bool = True) -> np.ndarray:
+    """Unconditional e(T) of a data-free L x L lattice (orc_energy_curve)."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    e = np.zeros(T.size)
+    lib().orc_energy_curve(q, J, seed & (2**64 - 1), 1 if overrelax else 0, L, T.size, _p(T),
+                           n_eq, n_meas, _p(e))
+    return e
+
+
+def curve_T0(T, e, e_s: float) -> float:
+    """T where the non-decreasing envelope of the curve reaches e_s."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    return lib().orc_curve_T0(T.size, _p(T), _p(e), float(e_s))
 
 
 class Oracle3:

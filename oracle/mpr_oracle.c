@@ -649,7 +649,8 @@ void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* ma
 void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint8_t* mask,
                           const double* Es, const int64_t* Nsp_all, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_iter, int32_t chains, int32_t points,
-                          double T_lo, double T_hi, double* T_out) {
+                          double T_lo, double T_hi, const double* T0_warm, double warm,
+                          double* T_out) {
     int64_t* Nsp = calib_targets(m, mask, Nsp_all, 0);
     const int nblk = m->nblk;
     const int64_t n = (int64_t)m->H * m->W;
@@ -663,8 +664,15 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
     for (int k = 0; k < n_iter; ++k) {
         for (int p = 0; p < points; ++p) {
             double* Tp = T + (int64_t)p * nblk;
-            for (int b = 0; b < nblk; ++b)
-                Tp[b] = lo[b] + (double)(p + 1) * (hi[b] - lo[b]) / (double)(points + 1);
+            for (int b = 0; b < nblk; ++b) {
+                if (k == 0 && T0_warm && points > 1) {
+                    /* warm start: the points evenly spaced on [T0 / w, T0 w] */
+                    const double a = T0_warm[b] / warm, c = T0_warm[b] * warm;
+                    Tp[b] = a + (double)p * (c - a) / (double)(points - 1);
+                } else {
+                    Tp[b] = lo[b] + (double)(p + 1) * (hi[b] - lo[b]) / (double)(points + 1);
+                }
+            }
             const double med = orc_median_targeted(nblk, Tp, Nsp);
             for (int b = 0; b < nblk; ++b) {
                 if (Nsp[b] == 0) Tp[b] = med;
@@ -709,6 +717,61 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
         if (Nsp[b] == 0) T_out[b] = med;
     free(lo); free(hi); free(T); free(ebar); free(E); free(phi);
     free(Nsp);
+}
+
+/* ------------------------------------------ unconditional e(T) curve -- */
+
+/* Specific energy of the data-free lattice: plain MPR matches e_s against the
+ * equilibrium energy of the whole grid (Sec. 2.1); with no data at all that
+ * energy is a function of T alone, the unconditional curve e(T). Here it is
+ * measured the way the calibration measures a block: an L x L lattice of gap
+ * sites (open boundaries), every angle started at pi (the middle of the
+ * range: a data-free stand-in for the block-mean start), n_eq sweeps, then
+ * E / N_bonds (N_bonds = 2 L (L - 1)) averaged over n_meas sweeps.
+ * Temperature k runs as realization k with tag 0xFFFE (key: seed, slice 0);
+ * overrelax as in the model (1: Metropolis then the reflection). */
+void orc_energy_curve(double q, double J, uint64_t seed, int32_t overrelax, int32_t L, int32_t n_T,
+                      const double* T, int32_t n_eq, int32_t n_meas, double* e_out) {
+    orc_model lm;
+    orc_model_init(&lm, L, L, L, q, J, seed, 0u);
+    lm.overrelax = overrelax;
+    const int64_t n = (int64_t)L * L;
+    const double n_bonds = 2.0 * (double)L * (double)(L - 1);
+    double* phi = (double*)malloc(sizeof(double) * n);
+    uint8_t* mask = (uint8_t*)malloc((size_t)n);
+    memset(mask, 1, (size_t)n);
+    for (int k = 0; k < n_T; ++k) {
+        const double Tk[1] = {T[k]};
+        for (int64_t i = 0; i < n; ++i) phi[i] = 0.5 * TWO_PI;
+        double acc = 0.0;
+        for (int s = 1; s <= n_eq + n_meas; ++s) {
+            orc_halfstep(&lm, phi, mask, 0, Tk, NULL, (uint32_t)s, 0xFFFEu, (uint32_t)k, NULL);
+            orc_halfstep(&lm, phi, mask, 1, Tk, NULL, (uint32_t)s, 0xFFFEu, (uint32_t)k, NULL);
+            if (s > n_eq) acc += orc_total_energy(&lm, phi) / n_bonds;
+        }
+        e_out[k] = n_meas > 0 ? acc / (double)n_meas : 0.0;
+    }
+    free(phi);
+    free(mask);
+}
+
+/* The temperature at which the curve reaches e_s. The curve is first made
+ * non-decreasing (each value raised to the largest one before it: Monte Carlo
+ * noise can make neighbouring points cross, while <e> grows with T), then read
+ * by linear interpolation between the two points around e_s; clamped to the
+ * first and last temperature. */
+double orc_curve_T0(int32_t n, const double* T, const double* e, double e_s) {
+    double prev = e[0];
+    if (!(e_s > prev)) return T[0];
+    for (int k = 1; k < n; ++k) {
+        const double ek = e[k] > prev ? e[k] : prev;
+        if (e_s <= ek) {
+            const double f = (e_s - prev) / (ek - prev);
+            return T[k - 1] + (T[k] - T[k - 1]) * f;
+        }
+        prev = ek;
+    }
+    return T[n - 1];
 }
 
 /* --------------------------------------------- moments and Newton (f1) -- */

@@ -147,11 +147,25 @@ void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* ma
  * the bracket between the highest point whose mean e_b is below e_s,b and
  * the lowest point whose mean is not (between the first and last point if
  * noise makes those cross). T_out: bracket midpoints, untargeted blocks at
- * the median. */
+ * the median. Warm start (T0_warm != NULL, points >= 2): the first
+ * iteration's points are evenly spaced on [T0_warm[b] / warm, T0_warm[b] warm]
+ * instead (T0 from the unconditional curve, orc_curve_T0); the same rule then
+ * keeps [T_lo, first point], a span between points, or [last point, T_hi]. */
 void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint8_t* mask,
                           const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_iter, int32_t chains, int32_t points,
-                          double T_lo, double T_hi, double* T_out);
+                          double T_lo, double T_hi, const double* T0_warm, double warm,
+                          double* T_out);
+
+/* Unconditional specific energy e(T[k]) of a data-free L x L lattice (Sec. 2.1
+ * energy matching without data): angles start at pi, n_eq sweeps, then the
+ * mean of E / (2 L (L - 1)) over n_meas sweeps; temperature k is realization
+ * k of tag 0xFFFE under key (seed, slice 0). */
+void orc_energy_curve(double q, double J, uint64_t seed, int32_t overrelax, int32_t L, int32_t n_T,
+                      const double* T, int32_t n_eq, int32_t n_meas, double* e_out);
+/* T where the non-decreasing envelope of the curve (T[k], e[k]) reaches e_s,
+ * by linear interpolation, clamped to [T[0], T[n-1]]. */
+double orc_curve_T0(int32_t n, const double* T, const double* e, double e_s);
 
 /* Energy moments of the calibration chains at block temperatures T[nblk]
  * (the energy matching of Sec. 2.1 / 2.2.2, with the fluctuation identity

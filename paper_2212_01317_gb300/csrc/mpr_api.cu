@@ -7,10 +7,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "mpr.h"
+#include "mpr_curve.h"
 #include "mpr_internal.h"
 #include "mpr_launch.h"
 #include "mpr_memory.h"
@@ -72,6 +75,10 @@ struct mpr_ctx {
     float *Tk = nullptr, *betak = nullptr;   // [points][nblk] of the 4- or 8-point calibration
     double* ebark = nullptr;                 // [points][nblk]
     double* ebar2 = nullptr;
+    // The unconditional e(T) curve (measured or set on first use).
+    float* curve_T = nullptr;
+    double* curve_e = nullptr;
+    int curve_n = 0;
     float* T_site = nullptr;     // [H*W] site temperatures (SST), allocated on first use
     float* beta_site = nullptr;  // [H*W] 1 / T_site
     int sst = 0;                 // 1: realizations use the site temperatures
@@ -231,7 +238,7 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.cal_mode < 0 || o.cal_mode > 3) return fail(ctx, MPR_EINVAL, "cal_mode must be 0 ... 3");
     if (o.wait_ms < 1) return fail(ctx, MPR_EINVAL, "wait_ms must be >= 1");
     if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
-    if (o.cal_method != 0 && o.cal_method != 1) return fail(ctx, MPR_EINVAL, "cal_method must be 0 or 1");
+    if (o.cal_method < 0 || o.cal_method > 2) return fail(ctx, MPR_EINVAL, "cal_method must be 0, 1 or 2");
     if (o.cal_points != 1 && o.cal_points != 2 && o.cal_points != 4 && o.cal_points != 8)
         return fail(ctx, MPR_EINVAL, "cal_points must be 1, 2, 4 or 8");
     if (o.sim_tail < 0) return fail(ctx, MPR_EINVAL, "sim_tail must be >= 0");
@@ -248,6 +255,12 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
         return fail(ctx, MPR_EINVAL, "need 2 <= n_fit <= 64 and 1 <= n_f <= 1024");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
+    if (!(o.cal_warm == 0.0f || (o.cal_warm > 1.0f && o.cal_warm <= 100.0f)))
+        return fail(ctx, MPR_EINVAL, "cal_warm must be 0 or in (1, 100]");
+    if (o.cal_warm > 0.0f && (o.cal_points < 2 || o.cal_method != 0 || o.cal_mode == 2))
+        return fail(ctx, MPR_EINVAL,
+                    "the warm start (cal_warm) needs cal_points >= 2, cal_method 0 and a cal_mode "
+                    "other than 2");
     return MPR_OK;
 }
 
@@ -444,14 +457,14 @@ int sweep_form(mpr_ctx* ctx) {
     if (ctx->opt.sweep_form == 4) return tile_form_ok(ctx) ? 4 : 0;
     if (ctx->opt.sweep_form >= 0) return ctx->opt.sweep_form;
     if (ctx->bound < (unsigned long long)ctx->n_sm * kForm2PairsPerSm) return 2;
-    // An autotuned (or asked-for) form holds while at least 7/8 of the pairs
-    // run: the autotuner times the first sweeps, where every pair runs. (On
-    // the 256-field batch the first two sweeps ran 7 % faster with two pairs
-    // per warp, the whole run 2.5 % slower, and still 1.7 % slower with the
-    // form held while half of the pairs ran.)
+    // An autotuned (or asked-for) form holds while the running count is
+    // unknown: the sweeps the autotuner's trial reproduces (a fresh batch, no
+    // count read yet), which in the per-launch loop are its first two chunks
+    // of four sweeps. (On the 256-field batch two pairs per warp ran the first
+    // 8 sweeps 3.9 % faster, and the whole run 1.3 % slower when the form was
+    // held for as long as 7/8 of the pairs ran, the count read late.)
     const int bulk = ctx->tuned_form >= 0 ? ctx->tuned_form : ctx->opt.sweep_form_bulk;
-    const unsigned long long pairs = (unsigned long long)ctx->g.nblk * (ctx->Rp / 2);
-    if (bulk >= 0 && ctx->bound >= pairs - pairs / 8) {
+    if (bulk >= 0 && ctx->bound == ~0ull) {
         if (bulk == 4) return tile_form_ok(ctx) ? 4 : 0;
         return bulk;
     }
@@ -732,22 +745,94 @@ mpr_status calibration_newton(mpr_ctx* ctx) {
     return MPR_OK;
 }
 
+// Temperatures of the default unconditional curve: geometric from
+// kCurveTmin to kCurveTmax.
+constexpr double kCurveTmin = 0.002, kCurveTmax = 1.25;
+
+// Measured curves, kept for the process: the curve depends on q, J, the
+// over-relaxation switch, n_eq and n_meas only (its random streams use the
+// fixed key (0, 0)), so every context with the same parameters reads the
+// same numbers, and the kernel runs once per parameter set.
+struct CurveEntry {
+    double q, J;
+    int overrelax, n_eq, n_meas;
+    float T[MPR_CURVE_POINTS];
+    double e[MPR_CURVE_POINTS];
+};
+std::mutex g_curve_mu;
+std::deque<CurveEntry> g_curves;
+
+// The context's e(T) curve: set by the caller, or the default curve
+// (MPR_CURVE_POINTS temperatures, the calibration's n_eq and n_meas),
+// measured on the context's stream unless this process measured it before.
+mpr_status ensure_curve(mpr_ctx* ctx) {
+    if (!ctx->curve_T) {
+        TRY(dalloc(ctx, &ctx->curve_T, (size_t)kCurveMaxPoints));
+        TRY(dalloc(ctx, &ctx->curve_e, (size_t)kCurveMaxPoints));
+    }
+    if (ctx->curve_n > 0) return MPR_OK;
+    const mpr_options& o = ctx->opt;
+    std::lock_guard<std::mutex> lock(g_curve_mu);
+    const CurveEntry* hit = nullptr;
+    for (const CurveEntry& c : g_curves)
+        if (c.q == o.q && c.J == o.J && c.overrelax == ctx->m.overrelax && c.n_eq == o.n_eq &&
+            c.n_meas == o.n_meas)
+            hit = &c;
+    CurveEntry fresh{};
+    if (!hit) {
+        fresh.q = o.q;
+        fresh.J = o.J;
+        fresh.overrelax = ctx->m.overrelax;
+        fresh.n_eq = o.n_eq;
+        fresh.n_meas = o.n_meas;
+        for (int k = 0; k < MPR_CURVE_POINTS; ++k)
+            fresh.T[k] = (float)(kCurveTmin * std::pow(kCurveTmax / kCurveTmin,
+                                                       (double)k / (double)(MPR_CURVE_POINTS - 1)));
+        CK(cudaMemcpyAsync(ctx->curve_T, fresh.T, sizeof(fresh.T), cudaMemcpyHostToDevice, ctx->s));
+        launch_energy_curve(ctx->curve_T, MPR_CURVE_POINTS, o.n_eq, o.n_meas, ctx->m, 0ull,
+                            ctx->curve_e, ctx->s);
+        CKL();
+        CK(cudaMemcpyAsync(fresh.e, ctx->curve_e, sizeof(fresh.e), cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        g_curves.push_back(fresh);
+    } else {
+        CK(cudaMemcpyAsync(ctx->curve_T, hit->T, sizeof(hit->T), cudaMemcpyHostToDevice, ctx->s));
+        CK(cudaMemcpyAsync(ctx->curve_e, hit->e, sizeof(hit->e), cudaMemcpyHostToDevice, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+    }
+    ctx->curve_n = MPR_CURVE_POINTS;
+    return MPR_OK;
+}
+
+// warm_first: the iteration's points come from the curve (launch_warm_points)
+// instead of the bracket.
 mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphConditionalHandle cond,
-                                 bool timed) {
+                                 bool timed, bool warm_first = false) {
     const Geom& g = ctx->g;
     const mpr_options& o = ctx->opt;
     const int pts = o.cal_points;
-    if (pts > 2) {
-        launch_kpts_mid(g.nblk, pts, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->Tk, ctx->ctl, ctx->s);
+    if (warm_first) {
+        launch_warm_points(g.nblk, pts, ctx->Nsp_cal, ctx->es, ctx->curve_T, ctx->curve_e,
+                           ctx->curve_n, (double)o.cal_warm, ctx->T, ctx->T2, ctx->Tk, ctx->ctl,
+                           ctx->s);
         CKL();
+    }
+    if (pts > 2) {
+        if (!warm_first) {
+            launch_kpts_mid(g.nblk, pts, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->Tk, ctx->ctl, ctx->s);
+            CKL();
+        }
         for (int p = 0; p < pts; ++p) {
             launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->Tk + (size_t)p * g.nblk,
                             ctx->betak + (size_t)p * g.nblk, ctx->s);
             CKL();
         }
     } else if (pts == 2) {
-        launch_kcal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->T2, ctx->ctl, ctx->s);
-        CKL();
+        if (!warm_first) {
+            launch_kcal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->T2, ctx->ctl,
+                            ctx->s);
+            CKL();
+        }
         launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T2, ctx->beta2, ctx->s);
         CKL();
     } else {
@@ -898,10 +983,11 @@ mpr_status calibration_persistent(mpr_ctx* ctx, double inv_count, bool* fallback
     return MPR_OK;
 }
 
-// All n_bisect iterations as one CUDA graph: a device-side WHILE loop whose
-// body is one iteration (captured once); k_cal_update ends it. One launch, no
-// host round trip per iteration.
-mpr_status calibration_graph(mpr_ctx* ctx, double inv_count) {
+// The calibration's remaining n_iter iterations (up to n_bisect in all) as
+// one CUDA graph: a device-side WHILE loop whose body is one iteration
+// (captured once); the update kernel ends it once ctl->k reaches n_bisect.
+// One launch, no host round trip per iteration.
+mpr_status calibration_graph(mpr_ctx* ctx, double inv_count, int n_iter) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     mpr_status st = MPR_OK;
@@ -938,8 +1024,8 @@ mpr_status calibration_graph(mpr_ctx* ctx, double inv_count) {
     {
         const int64_t per_iter_launches = ctx->launches - launches0;
         const int64_t per_iter_hs = ctx->cal_halfstep_launches - hs0;
-        ctx->launches = launches0 + per_iter_launches * ctx->opt.n_bisect;
-        ctx->cal_halfstep_launches = hs0 + per_iter_hs * ctx->opt.n_bisect;
+        ctx->launches = launches0 + per_iter_launches * n_iter;
+        ctx->cal_halfstep_launches = hs0 + per_iter_hs * n_iter;
     }
     if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) goto cuda_fail;
     if (ctx->opt.profile) {
@@ -1011,6 +1097,7 @@ void mpr_default_options(mpr_options* o) {
     o->stop_rule = MPR_STOP_CROSS;
     o->n_fit = 20;
     o->n_f = 5;
+    o->cal_warm = 0.0f;
     o->cuda_stream = nullptr;
 }
 
@@ -1472,6 +1559,49 @@ mpr_status mpr_get_temperatures(mpr_ctx* ctx, float* T) {
     return copy_out(ctx, T, ctx->T, (size_t)ctx->g.nblk * 4);
 }
 
+mpr_status mpr_get_energy_curve(mpr_ctx* ctx, float* T_out, double* e_out, int32_t capacity,
+                                int32_t* n_out) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!T_out || !e_out || !n_out) return fail(ctx, MPR_EINVAL, "T_out, e_out and n_out are required");
+    TRY(ensure_curve(ctx));
+    if (capacity < ctx->curve_n)
+        return fail(ctx, MPR_EINVAL, "capacity %d is below the curve's %d points", capacity,
+                    ctx->curve_n);
+    TRY(copy_out(ctx, T_out, ctx->curve_T, (size_t)ctx->curve_n * 4));
+    TRY(copy_out(ctx, e_out, ctx->curve_e, (size_t)ctx->curve_n * 8));
+    *n_out = ctx->curve_n;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_energy_curve(mpr_ctx* ctx, const float* T, const double* e, int32_t n) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (!T || !e) return fail(ctx, MPR_EINVAL, "T and e are required");
+    if (n < 2 || n > kCurveMaxPoints)
+        return fail(ctx, MPR_EINVAL, "a curve has 2 to %d points", kCurveMaxPoints);
+    std::vector<float> hT(n);
+    std::vector<double> he(n);
+    CK(cudaMemcpyAsync(hT.data(), T, (size_t)n * 4, cudaMemcpyDefault, ctx->s));
+    CK(cudaMemcpyAsync(he.data(), e, (size_t)n * 8, cudaMemcpyDefault, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (int k = 0; k < n; ++k) {
+        if (!(hT[k] > 0.0f) || !std::isfinite(hT[k]) || !std::isfinite(he[k]))
+            return fail(ctx, MPR_EINVAL, "curve point %d: T must be > 0 and finite, e finite", k);
+        if (k > 0 && !(hT[k] > hT[k - 1]))
+            return fail(ctx, MPR_EINVAL, "curve temperatures must increase strictly (point %d)", k);
+    }
+    if (!ctx->curve_T) {
+        TRY(dalloc(ctx, &ctx->curve_T, (size_t)kCurveMaxPoints));
+        TRY(dalloc(ctx, &ctx->curve_e, (size_t)kCurveMaxPoints));
+    }
+    CK(cudaMemcpyAsync(ctx->curve_T, hT.data(), (size_t)n * 4, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(ctx->curve_e, he.data(), (size_t)n * 8, cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->curve_n = n;
+    return MPR_OK;
+}
+
 mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     if (!ctx) return MPR_EINVAL;
     ctx->err.clear();
@@ -1489,6 +1619,34 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
         return MPR_OK;
     }
     const int chains = o.cal_chains;
+    if (o.cal_method == 2) {
+        // T_b where the unconditional curve reaches e_s,b; the median for
+        // blocks without a target.
+        TRY(ensure_curve(ctx));
+        launch_curve_T(g.nblk, ctx->Nsp_cal, ctx->es, ctx->curve_T, ctx->curve_e, ctx->curve_n,
+                       ctx->T, ctx->s);
+        CKL();
+        launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
+        CKL();
+        ctx->calibrated = 1;
+        ctx->sst = 0;
+        if (block_T_out) TRY(copy_out(ctx, block_T_out, ctx->T, (size_t)g.nblk * 4));
+        CK(cudaStreamSynchronize(ctx->s));
+        return MPR_OK;
+    }
+    const bool warm = o.cal_warm > 0.0f && o.n_bisect > 0;
+    if (warm) {
+        TRY(ensure_curve(ctx));
+        float ends[2];
+        CK(cudaMemcpyAsync(&ends[0], ctx->curve_T, 4, cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaMemcpyAsync(&ends[1], ctx->curve_T + ctx->curve_n - 1, 4, cudaMemcpyDeviceToHost,
+                           ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        if (!((double)ends[0] / o.cal_warm > o.t_lo && (double)ends[1] * o.cal_warm < o.t_hi))
+            return fail(ctx, MPR_EINVAL,
+                        "warm start: the curve's temperatures [%g, %g] widened by cal_warm = %g "
+                        "leave the bracket (%g, %g)", ends[0], ends[1], o.cal_warm, o.t_lo, o.t_hi);
+    }
     if (o.cal_method == 1) {
         TRY(calibration_newton(ctx));
         ctx->calibrated = 1;
@@ -1537,9 +1695,13 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     }
     if (fallback) {
         if (o.n_bisect > 0 && o.cal_mode == 3) {
-            for (int k = 0; k < o.n_bisect; ++k) TRY(calibration_iteration(ctx, inv_count, 0, true));
+            for (int k = 0; k < o.n_bisect; ++k)
+                TRY(calibration_iteration(ctx, inv_count, 0, true, warm && k == 0));
         } else if (o.n_bisect > 0) {
-            TRY(calibration_graph(ctx, inv_count));
+            // The warm start's first iteration runs ahead of the graph.
+            if (warm) TRY(calibration_iteration(ctx, inv_count, 0, true, true));
+            const int rest = o.n_bisect - (warm ? 1 : 0);
+            if (rest > 0) TRY(calibration_graph(ctx, inv_count, rest));
         }
         launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
         CKL();

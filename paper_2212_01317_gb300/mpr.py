@@ -18,6 +18,7 @@ MPR_OK, MPR_EINVAL, MPR_ENOMEM, MPR_ECUDA, MPR_ENOSAMPLES, MPR_ETIMEOUT, MPR_EST
 MPR_STORE_F32, MPR_STORE_BF16, MPR_STORE_F16 = 0, 1, 2
 MPR_INIT_BLOCK_MEAN, MPR_INIT_RANDOM = 0, 1
 MPR_STOP_CROSS, MPR_STOP_WINDOW = 0, 1
+MPR_CURVE_POINTS = 40
 
 EXPORTS = [
     "mpr_default_options", "mpr_create", "mpr_destroy", "mpr_last_error", "mpr_status_string",
@@ -28,6 +29,7 @@ EXPORTS = [
     "mpr_block_stats_noalloc", "mpr_set_realization_base", "mpr_get_accumulator",
     "mpr_set_accumulator", "mpr_smooth_temperatures", "mpr_set_site_temperatures",
     "mpr_get_site_temperatures", "mpr_energy_moments", "mpr_energy_vjp", "mpr_create_batch",
+    "mpr_get_energy_curve", "mpr_set_energy_curve",
     "mpr_predict_batch", "mpr_get_slice_layout", "mpr_autotune", "mpr_release_cached_memory",
     "mpr3_create", "mpr3_destroy", "mpr3_last_error", "mpr3_get_info", "mpr3_get_block_stats",
     "mpr3_calibrate", "mpr3_set_temperatures", "mpr3_simulate", "mpr3_predict", "mpr3_sim_begin",
@@ -51,7 +53,7 @@ class mpr_options(C.Structure):
                 ("t_init", C.c_float), ("sim_graph", C.c_int32), ("cal_points", C.c_int32),
                 ("sim_tail", C.c_int32), ("sweep_form", C.c_int32), ("pair_tail", C.c_int32),
                 ("sweep_form_bulk", C.c_int32), ("stop_rule", C.c_int32), ("n_fit", C.c_int32),
-                ("n_f", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("n_f", C.c_int32), ("cal_warm", C.c_float), ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):
@@ -155,6 +157,8 @@ def load(path: str | None = None):
         "mpr_predict_batch": (st, [P, P, P, P]),
         "mpr_get_slice_layout": (st, [P, P]),
         "mpr_autotune": (st, [P, i32, i32, C.POINTER(mpr_tuning)]),
+        "mpr_get_energy_curve": (st, [P, P, P, i32, C.POINTER(i32)]),
+        "mpr_set_energy_curve": (st, [P, P, P, i32]),
         "mpr3_create": (st, [C.POINTER(mpr_grid3), P, P, C.POINTER(mpr_options), C.POINTER(P)]),
         "mpr3_destroy": (None, [P]),
         "mpr3_last_error": (C.c_char_p, [P]),
@@ -269,6 +273,22 @@ def mpr_get_info(ctx) -> mpr_info:
 
 def mpr_calibrate(ctx, block_T_out=None):
     _check(ctx, load().mpr_calibrate(ctx, _ptr(block_T_out)))
+
+
+def mpr_get_energy_curve(ctx, capacity: int = 64):
+    """The context's unconditional e(T) curve (measured on first use):
+    (T float32[n], e float64[n])."""
+    T = np.zeros(capacity, np.float32)
+    e = np.zeros(capacity, np.float64)
+    n = C.c_int32()
+    _check(ctx, load().mpr_get_energy_curve(ctx, _ptr(T), _ptr(e), capacity, C.byref(n)))
+    return T[:n.value].copy(), e[:n.value].copy()
+
+
+def mpr_set_energy_curve(ctx, T, e):
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    _check(ctx, load().mpr_set_energy_curve(ctx, _ptr(T), _ptr(e), int(T.size)))
 
 
 def mpr_set_temperatures(ctx, T):
@@ -424,6 +444,12 @@ class GapFiller:
 
     def set_temperatures(self, T):
         mpr_set_temperatures(self.ctx, np.ascontiguousarray(T, dtype=np.float32))
+
+    def energy_curve(self):
+        return mpr_get_energy_curve(self.ctx)
+
+    def set_energy_curve(self, T, e):
+        mpr_set_energy_curve(self.ctx, T, e)
 
     def simulate(self, n: int):
         mpr_simulate(self.ctx, n)

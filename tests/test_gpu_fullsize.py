@@ -10,7 +10,8 @@ checked in test_gpu_parity.py.
     sampled sites against the oracle in the same precision form;
   * 256 fields of 256² to 2048² in one batched context, l_b = 32, R = 50,
     BF16 state: sampled sites of several fields, each against the oracle of
-    its own field (own transform, random-stream key and site numbering);
+    its own field (own transform, random-stream key and site numbering), and
+    the first iteration of the warm-started calibration the benchmark runs;
   * 16384², 70 % disc gaps, l_b = 64, R = 20, BF16 state: sampled sites, and
     the energy-matching derivative of the Newton calibration at full size
     against central differences with common random numbers.
@@ -117,8 +118,13 @@ def test_field4096_bf16_sampled_sites():
     gf.close()
 
 
-def test_slices256_batched_bf16_sampled_sites():
-    bw = synth.batch_workload("slices256")
+@pytest.fixture(scope="module")
+def slices256():
+    return synth.batch_workload("slices256")
+
+
+def test_slices256_batched_bf16_sampled_sites(slices256):
+    bw = slices256
     R = bw.realizations
     vals = [np.where(m != 0, np.nan, z).astype(np.float32) for z, m in zip(bw.truths, bw.masks)]
     bf = BatchFiller(vals, bw.masks, bw.block, seed=256, storage=STORE["bf16"])
@@ -158,6 +164,55 @@ def test_slices256_batched_bf16_sampled_sites():
     assert explained <= max(3, checked // TIES)
     mpr.mpr_sim_end(bf.ctx)
     bf.close()
+
+
+def test_slices256_warm_calibration_first_iteration(slices256):
+    """The benchmark's calibration of the 256-field batch (warm-started
+    trisection) at full size, its first iteration: with the oracle's curve
+    given to the library, every targeted block of three fields takes the
+    midpoint of [t_lo, T0/w], [T0/w, T0 w] or [T0 w, t_hi] with T0 the
+    oracle's inverse of its own curve at its own e_s,b; on the smallest field
+    the side agrees with the oracle's own first iteration (same random
+    streams) except where the measured energies lay within rounding of e_s,b
+    (at most 10 % of the blocks, each then one interval over)."""
+    bw = slices256
+    vals = [np.where(m != 0, np.nan, z).astype(np.float32) for z, m in zip(bw.truths, bw.masks)]
+    w = 1.5
+    Tc = np.geomspace(0.002, 1.25, mpr.MPR_CURVE_POINTS).astype(np.float32)
+    ec = oracle.energy_curve(Tc.astype(np.float64), L=64, n_eq=25, n_meas=20, seed=0)
+    bf = BatchFiller(vals, bw.masks, bw.block, seed=256, storage=STORE["bf16"], cal_points=2,
+                     cal_warm=w, n_bisect=1)
+    bf.set_energy_curve(Tc, ec)
+    T = bf.calibrate()
+    bf.close()
+    small = int(np.argmin([m.shape[0] for m in bw.masks]))
+    for k in (0, 97, 255, small):
+        y0, x0, h, wd = bf.layout[k]
+        m = bw.masks[k]
+        o = oracle.Oracle(h, wd, bw.block, seed=256, slice_id=k)
+        phi, *_ = o.transform(bw.truths[k], m)
+        st = o.block_stats(phi, m)
+        T0 = o.warm_T0(st, Tc.astype(np.float64), ec)
+        Tk = bf.block_slice(k, T)
+        tgt = (st.Nsp > 0) & (st.n_gap > 0)
+        side = np.full(o.nblk, -1)
+        for b in np.flatnonzero(tgt):
+            a, c = np.float32(T0[b] / w), np.float32(T0[b] * w)
+            mids = [np.float32(0.5) * (np.float32(1e-4) + a), np.float32(0.5) * (a + c),
+                    np.float32(0.5) * (c + np.float32(2.0))]
+            d = [abs(float(x) - float(Tk[b])) for x in mids]
+            side[b] = int(np.argmin(d))
+            assert d[side[b]] <= 1e-6 * float(Tk[b]), (k, b, Tk[b], mids)
+        if k == small:
+            phi0 = o.init_block_mean(phi, m, st)
+            To = o.calibrate_points(phi0, m, st, n_iter=1, points=2, T0_warm=T0, warm=w)
+            same = np.abs(Tk - To) <= 1e-6 * To
+            assert same[tgt].mean() >= 0.9
+            for b in np.flatnonzero(tgt & ~same):
+                a, c = T0[b] / w, T0[b] * w
+                so = int(np.argmin([abs(To[b] - 0.5 * (1e-4 + a)), abs(To[b] - 0.5 * (a + c)),
+                                    abs(To[b] - 0.5 * (c + 2.0))]))
+                assert abs(so - side[b]) == 1, (b, so, side[b])
 
 
 @pytest.fixture(scope="module")
