@@ -552,6 +552,12 @@ class BatchFiller:
     def set_temperatures(self, T):
         mpr_set_temperatures(self.ctx, np.ascontiguousarray(T, dtype=np.float32))
 
+    def energy_curve(self):
+        return mpr_get_energy_curve(self.ctx)
+
+    def set_energy_curve(self, T, e):
+        mpr_set_energy_curve(self.ctx, T, e)
+
     def simulate(self, n: int):
         mpr_simulate(self.ctx, n)
 
