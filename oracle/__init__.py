@@ -98,7 +98,7 @@ def lib():
             "orc_scores": (None, [i64, P, P, P, P, P]),
             "orc_sst_temperatures": (None, [MP, P, i32, i32, P]),
             "orc_calibrate_points": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, i32, f64, f64,
-                                            P, f64, P]),
+                                            P, f64, P, P, P]),
             "orc_energy_curve": (None, [f64, f64, u64, i32, i32, i32, P, i32, i32, P]),
             "orc_curve_T0": (f64, [i32, P, P, f64]),
             "orc3_model_init": (None, [MP, i32, i32, i32, i32, f64, f64, u64, u32]),
@@ -359,17 +359,23 @@ class Oracle:
         return (T, tr) if trace else T
 
     def calibrate_points(self, phi_init, mask, st: BlockStats, n_eq=25, n_meas=20, n_iter=16,
-                         chains=1, points=2, T_lo=1e-4, T_hi=2.0, T0_warm=None, warm=1.5):
+                         chains=1, points=2, T_lo=1e-4, T_hi=2.0, T0_warm=None, warm=1.5,
+                         trace=False):
         """k-point calibration; T0_warm (per block, from curve_T0) starts the
-        first iteration's points on [T0 / warm, T0 * warm]."""
+        first iteration's points on [T0 / warm, T0 * warm]. trace=True also
+        returns the per-iteration mean e_b and temperatures of every point,
+        each [n_iter, points, nblk]."""
         ph = np.ascontiguousarray(phi_init, dtype=np.float64)
         mk = np.ascontiguousarray(mask, dtype=np.uint8)
         T = np.zeros(self.nblk)
         t0 = None if T0_warm is None else np.ascontiguousarray(T0_warm, dtype=np.float64)
+        et = np.zeros((n_iter, points, self.nblk)) if trace else None
+        pt = np.zeros((n_iter, points, self.nblk)) if trace else None
         lib().orc_calibrate_points(C.byref(self.m), _p(ph), _p(mk), _p(st.Es), _p(st.Nsp),
                                    _p(st.Nb), n_eq, n_meas, n_iter, chains, points, T_lo, T_hi,
-                                   None if t0 is None else _p(t0), float(warm), _p(T))
-        return T
+                                   None if t0 is None else _p(t0), float(warm), _p(T),
+                                   None if et is None else _p(et), None if pt is None else _p(pt))
+        return (T, et, pt) if trace else T
 
     def warm_T0(self, st: BlockStats, T_curve, e_curve) -> np.ndarray:
         """Per-block T0 = curve_T0(e_s,b) (0 for blocks without sample bonds)."""

@@ -650,7 +650,7 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
                           const double* Es, const int64_t* Nsp_all, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_iter, int32_t chains, int32_t points,
                           double T_lo, double T_hi, const double* T0_warm, double warm,
-                          double* T_out) {
+                          double* T_out, double* ebar_trace, double* pts_trace) {
     int64_t* Nsp = calib_targets(m, mask, Nsp_all, 0);
     const int nblk = m->nblk;
     const int64_t n = (int64_t)m->H * m->W;
@@ -700,6 +700,9 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
             for (int p = 0; p < points; ++p) {
                 const double e = ebar[(int64_t)p * nblk + b] / ((double)n_meas * (double)chains);
                 const double tp = T[(int64_t)p * nblk + b];
+                const int64_t at = ((int64_t)k * points + p) * nblk + b;
+                if (ebar_trace) ebar_trace[at] = e;
+                if (pts_trace) pts_trace[at] = tp;
                 if (e < es) { if (tp > nlo) nlo = tp; }
                 else if (tp < nhi) nhi = tp;
             }

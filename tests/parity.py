@@ -128,3 +128,70 @@ def paired_over_seeds(run, seeds, floor_rel=1e-3):
     se = float(d.std(ddof=1) / np.sqrt(len(d))) if len(d) > 1 else 0.0
     assert abs(d.mean()) <= 3.0 * se + floor_rel * ref, (d, se, ref)
     return d
+
+
+# ------------------------------------------------------------ calibration --
+def kpoint_brackets(et, pt, es, target, t_lo=1e-4, t_hi=2.0):
+    """The oracle's k-point brackets after every iteration, rebuilt from its
+    trace (mean e_b and temperature of every point, [n_iter, points, nblk])
+    by the rule of the calibration: from the highest point whose mean is
+    below e_s,b to the lowest point whose mean is not; the points' span when
+    noise makes those cross. Returns [n_iter, 2, nblk] (lo, hi)."""
+    n_iter, points, nblk = et.shape
+    lo = np.full(nblk, float(t_lo))
+    hi = np.full(nblk, float(t_hi))
+    out = np.zeros((n_iter, 2, nblk))
+    for k in range(n_iter):
+        nlo, nhi = lo.copy(), hi.copy()
+        for p in range(points):
+            below = et[k, p] < es
+            nlo = np.where(below & (pt[k, p] > nlo), pt[k, p], nlo)
+            nhi = np.where(~below & (pt[k, p] < nhi), pt[k, p], nhi)
+        cross = nlo > nhi
+        nlo = np.where(cross, pt[k, 0], nlo)
+        nhi = np.where(cross, pt[k, points - 1], nhi)
+        lo = np.where(target, nlo, lo)
+        hi = np.where(target, nhi, hi)
+        out[k, 0], out[k, 1] = lo, hi
+    return out
+
+
+def explain_calibration(o, phi0, mask, st, T_gpu, T_ora, et, pt, n_meas, chains, target,
+                        rtol=1e-4, n_sigma=8.0, max_parted=0.25):
+    """Every targeted block of a k-point calibration (any number of points,
+    warm or cold) is checked: either the GPU's T agrees with the oracle's
+    (both run the same chains on the same random streams), or it left the
+    oracle's brackets at an iteration k* where one of the oracle's points
+    measured a mean e_b within n_sigma standard errors of e_s,b: there a
+    comparison can come out either way between FP32 and FP64 chains. The
+    standard error is that of an uncorrelated mean over the n_meas measured
+    sweeps of the chains (from the oracle's energy variance at that point's
+    temperature); successive sweeps are correlated over a few sweeps, so
+    8 of them are about 3.5 standard errors of the correlated mean. Returns
+    the parted blocks [(b, k*, point)]."""
+    es = st.es
+    br = kpoint_brackets(et, pt, es, target)
+    mid = 0.5 * (br[-1, 0] + br[-1, 1])
+    np.testing.assert_allclose(np.where(target, mid, T_ora), T_ora, rtol=1e-12)
+    parted = []
+    for b in np.flatnonzero(target):
+        if abs(T_gpu[b] - T_ora[b]) <= rtol * T_ora[b]:
+            continue
+        tol = 1e-6 * float(T_gpu[b])
+        inside = (br[:, 0, b] - tol <= T_gpu[b]) & (T_gpu[b] <= br[:, 1, b] + tol)
+        ks = np.flatnonzero(~inside)
+        assert ks.size, f"block {b}: T differs ({T_gpu[b]} vs {T_ora[b]}) inside every bracket"
+        k = int(ks[0])
+        j = int(np.argmin(np.abs(et[k, :, b] - es[b])))
+        parted.append((int(b), k, j))
+    if parted:
+        Tk = np.ascontiguousarray(T_ora, dtype=np.float64).copy()
+        for b, k, j in parted:
+            Tk[b] = pt[k, j, b]
+        _, var_E, _, _ = o.energy_moments(np.ascontiguousarray(phi0[None].copy()), mask, Tk,
+                                          200, 400, 7, st)
+        for b, k, j in parted:
+            se = np.sqrt(var_E[b] / (n_meas * chains)) / st.Nb[b]
+            assert abs(et[k, j, b] - es[b]) <= n_sigma * se, (b, k, j, et[k, j, b], es[b], se)
+    assert len(parted) <= max(1, int(max_parted * target.sum())), parted
+    return parted

@@ -13,6 +13,8 @@ import pytest
 from paper_2212_01317_gb300 import synth
 from paper_2212_01317_gb300.mpr import GapFiller, MprError, MPR_ETIMEOUT
 
+from parity import explain_calibration
+
 pytestmark = pytest.mark.gpu
 
 
@@ -75,12 +77,15 @@ def test_trisection_matches_oracle(chains, kind):
     phi, *_ = o.transform(z, m)
     st = o.block_stats(phi, m)
     phi0 = o.init_block_mean(phi, m, st)
-    To = o.calibrate_points(phi0, m, st, n_eq=6, n_meas=6, n_iter=10, chains=chains, points=2)
+    To, et, pt = o.calibrate_points(phi0, m, st, n_eq=6, n_meas=6, n_iter=10, chains=chains,
+                                    points=2, trace=True)
     # A targeted block without gap sites has e_b = e_s,b exactly, so its
     # comparisons (and its T, which no site uses) follow the last bit of two
-    # equal numbers computed in different orders: compare the others.
-    used = st.n_gap > 0
-    assert (np.abs(T - To) <= 1e-4 * To)[used].mean() >= 0.9
+    # equal numbers computed in different orders: it takes the median instead.
+    target = (st.Nsp > 0) & (st.n_gap > 0)
+    explain_calibration(o, phi0, m, st, T, To, et, pt, 6, chains, target)
+    med = np.float32(np.median(T[target]))
+    np.testing.assert_allclose(T[~target], med, rtol=1e-6)
     # the graph and the host-launched forms agree
     gf = make(z, m, lb, cal_points=2, cal_mode=3, **opts)
     np.testing.assert_allclose(gf.calibrate(), T, rtol=1e-6)
@@ -93,7 +98,8 @@ def test_k_point_calibration_matches_oracle(points, chains):
     the chains at point r mod points; the bracket shrinks to the span between
     the highest point whose mean energy is below e_s,b and the lowest point
     whose mean is not) against the oracle's k-point calibration on the same
-    random streams; the graph and the host-launched forms agree."""
+    random streams, block by block (tests/parity.py explain_calibration); the
+    graph and the host-launched forms agree."""
     import oracle
     H, W, lb = 48, 40, 8
     z, m = synth.small_problem(H, W, 0.5, seed=H + points, kind="random")
@@ -106,10 +112,10 @@ def test_k_point_calibration_matches_oracle(points, chains):
     phi, *_ = o.transform(z, m)
     st = o.block_stats(phi, m)
     phi0 = o.init_block_mean(phi, m, st)
-    To = o.calibrate_points(phi0, m, st, n_eq=6, n_meas=6, n_iter=n_iter, chains=chains,
-                            points=points)
-    used = st.n_gap > 0
-    assert (np.abs(T - To) <= 1e-4 * To)[used].mean() >= 0.9
+    To, et, pt = o.calibrate_points(phi0, m, st, n_eq=6, n_meas=6, n_iter=n_iter, chains=chains,
+                                    points=points, trace=True)
+    target = (st.Nsp > 0) & (st.n_gap > 0)
+    explain_calibration(o, phi0, m, st, T, To, et, pt, 6, chains, target)
     assert np.all((T > 1e-4) & (T < 2.0))
     gf = make(z, m, lb, cal_points=points, cal_mode=3, **opts)
     np.testing.assert_allclose(gf.calibrate(), T, rtol=1e-6)

@@ -19,6 +19,8 @@ import oracle
 from paper_2212_01317_gb300 import mpr, synth
 from paper_2212_01317_gb300.mpr import GapFiller, MprError, MPR_EINVAL
 
+from parity import explain_calibration
+
 pytestmark = pytest.mark.gpu
 
 
@@ -85,10 +87,10 @@ def test_warm_calibration_matches_oracle(points, chains, mode):
     T = gf.calibrate()
     gf.close()
     T0 = o.warm_T0(st, Tc.astype(np.float64), ec)
-    To = o.calibrate_points(phi0, m, st, n_eq=6, n_meas=6, n_iter=n_iter, chains=chains,
-                            points=points, T0_warm=T0, warm=w)
-    used = st.n_gap > 0
-    assert (np.abs(T - To) <= 1e-4 * To)[used].mean() >= 0.9
+    To, et, pt = o.calibrate_points(phi0, m, st, n_eq=6, n_meas=6, n_iter=n_iter, chains=chains,
+                                    points=points, T0_warm=T0, warm=w, trace=True)
+    target = (st.Nsp > 0) & (st.n_gap > 0)
+    explain_calibration(o, phi0, m, st, T, To, et, pt, 6, chains, target)
     assert np.all((T > 1e-4) & (T < 2.0))
     if mode == 1:
         # the host-launched form runs the same launches

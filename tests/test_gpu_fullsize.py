@@ -23,7 +23,8 @@ import oracle
 from paper_2212_01317_gb300 import mpr, synth
 from paper_2212_01317_gb300.mpr import BatchFiller, GapFiller
 
-from parity import TWO_PI, checkerboard, compare_site_updates, sampled_sweep_parity
+from parity import (TWO_PI, checkerboard, compare_site_updates, explain_calibration,
+                    sampled_sweep_parity)
 
 pytestmark = pytest.mark.gpu
 STORE = {"f32": 0, "bf16": 1, "f16": 2}
@@ -172,9 +173,9 @@ def test_slices256_warm_calibration_first_iteration(slices256):
     given to the library, every targeted block of three fields takes the
     midpoint of [t_lo, T0/w], [T0/w, T0 w] or [T0 w, t_hi] with T0 the
     oracle's inverse of its own curve at its own e_s,b; on the smallest field
-    the side agrees with the oracle's own first iteration (same random
-    streams) except where the measured energies lay within rounding of e_s,b
-    (at most 10 % of the blocks, each then one interval over)."""
+    every block agrees with the oracle's own first iteration (same random
+    streams) or parted from it where the oracle measured e_b within Monte
+    Carlo error of e_s,b (tests/parity.py explain_calibration)."""
     bw = slices256
     vals = [np.where(m != 0, np.nan, z).astype(np.float32) for z, m in zip(bw.truths, bw.masks)]
     w = 1.5
@@ -205,14 +206,9 @@ def test_slices256_warm_calibration_first_iteration(slices256):
             assert d[side[b]] <= 1e-6 * float(Tk[b]), (k, b, Tk[b], mids)
         if k == small:
             phi0 = o.init_block_mean(phi, m, st)
-            To = o.calibrate_points(phi0, m, st, n_iter=1, points=2, T0_warm=T0, warm=w)
-            same = np.abs(Tk - To) <= 1e-6 * To
-            assert same[tgt].mean() >= 0.9
-            for b in np.flatnonzero(tgt & ~same):
-                a, c = T0[b] / w, T0[b] * w
-                so = int(np.argmin([abs(To[b] - 0.5 * (1e-4 + a)), abs(To[b] - 0.5 * (a + c)),
-                                    abs(To[b] - 0.5 * (c + 2.0))]))
-                assert abs(so - side[b]) == 1, (b, so, side[b])
+            To, et, pt = o.calibrate_points(phi0, m, st, n_iter=1, points=2, T0_warm=T0,
+                                            warm=w, trace=True)
+            explain_calibration(o, phi0, m, st, Tk, To, et, pt, 20, 1, tgt, rtol=1e-6)
 
 
 @pytest.fixture(scope="module")
