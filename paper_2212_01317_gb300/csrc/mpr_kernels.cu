@@ -16,6 +16,7 @@
 #include "mpr_internal.h"
 #include "mpr_launch.h"
 #include "mpr_lists.cuh"
+#include "mpr_stats.cuh"
 #include "mpr_sweep.cuh"
 
 namespace mpr {
@@ -137,7 +138,6 @@ __global__ void k_block_stats(Geom g, Slices sl, const float* __restrict__ value
     const int by = warp / g.nbx, bx = warp % g.nbx;
     const int y0 = by * g.lb, x0 = bx * g.lb;
     const int y1 = min(g.H, y0 + g.lb), x1 = min(g.W, x0 + g.lb);
-    const int bw = x1 - x0, nsite = (y1 - y0) * bw;
     const int s = sl.of_block[warp];
     const double zmin = s >= 0 ? sl.zmin[s] : 0.0, zmax = s >= 0 ? sl.zmax[s] : 1.0;
     const double scale = (s < 0 || sl.degenerate[s]) ? 0.0 : 6.283185307179586476925 / (zmax - zmin);
@@ -145,60 +145,16 @@ __global__ void k_block_stats(Geom g, Slices sl, const float* __restrict__ value
     // and in the same slice (blocks never straddle slices).
     const bool right_ok = x1 < g.W && bx + 1 < g.nbx && sl.of_block[warp + 1] == s;
     const bool down_ok = y1 < g.H && by + 1 < g.nby && sl.of_block[warp + g.nbx] == s;
-    double es = 0.0, sm = 0.0;
-    int nsp = 0, nb = 0, ns = 0, g0 = 0, g1 = 0;
-    for (int j = lane; j < nsite && s >= 0; j += 32) {
-        const int y = y0 + j / bw, x = x0 + j % bw;
-        const int64_t i = (int64_t)y * g.W + x;
-        if (mask[i] == MASK_ABSENT) continue;
-        const bool gap = mask[i] == MASK_GAP;
-        const double pi = gap ? 0.0 : ((double)values[i] - zmin) * scale;
-        if (gap) {
-            if (((x + y) & 1) == 0) ++g0; else ++g1;
-        } else {
-            sm += pi;
-            ++ns;
-        }
-        if (x + 1 < x1 || right_ok) {
-            const uint8_t mj = mask[i + 1];
-            if (mj != MASK_ABSENT) {
-                ++nb;
-                if (!gap && mj == 0) {
-                    const double pj = ((double)values[i + 1] - zmin) * scale;
-                    es += -J * cos(q * (pi - pj));
-                    ++nsp;
-                }
-            }
-        }
-        if (y + 1 < y1 || down_ok) {
-            const uint8_t mj = mask[i + g.W];
-            if (mj != MASK_ABSENT) {
-                ++nb;
-                if (!gap && mj == 0) {
-                    const double pj = ((double)values[i + g.W] - zmin) * scale;
-                    es += -J * cos(q * (pi - pj));
-                    ++nsp;
-                }
-            }
-        }
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        es += __shfl_xor_sync(0xffffffffu, es, d);
-        sm += __shfl_xor_sync(0xffffffffu, sm, d);
-        nsp += __shfl_xor_sync(0xffffffffu, nsp, d);
-        nb += __shfl_xor_sync(0xffffffffu, nb, d);
-        ns += __shfl_xor_sync(0xffffffffu, ns, d);
-        g0 += __shfl_xor_sync(0xffffffffu, g0, d);
-        g1 += __shfl_xor_sync(0xffffffffu, g1, d);
-    }
+    const BlockSums r = block_sums<true>(values, mask, g.W, y0, x0, y1, x1, right_ok, down_ok,
+                                         zmin, scale, q, J, s >= 0);
     if (lane == 0) {
-        Es[warp] = es;
-        Nsp[warp] = nsp;
-        Nb[warp] = nb;
-        ssum[warp] = sm;
-        nsamp[warp] = ns;
-        ngap0[warp] = g0;
-        ngap1[warp] = g1;
+        Es[warp] = r.es;
+        Nsp[warp] = r.nsp;
+        Nb[warp] = r.nb;
+        ssum[warp] = r.sm;
+        nsamp[warp] = r.ns;
+        ngap0[warp] = r.g0;
+        ngap1[warp] = r.g1;
     }
 }
 

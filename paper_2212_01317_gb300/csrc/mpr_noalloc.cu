@@ -17,6 +17,7 @@
 #include "mpr_internal.h"
 #include "mpr_launch.h"
 #include "mpr_ptrcheck.h"
+#include "mpr_stats.cuh"
 
 using namespace mpr;
 
@@ -100,53 +101,19 @@ __global__ void k_na_block_stats(Geom g, const float* __restrict__ values,
     const int by = warp / g.nbx, bx = warp % g.nbx;
     const int y0 = by * g.lb, x0 = bx * g.lb;
     const int y1 = min(g.H, y0 + g.lb), x1 = min(g.W, x0 + g.lb);
-    const int bw = x1 - x0, nsite = (y1 - y0) * bw;
     const double scale = degenerate ? 0.0 : 6.283185307179586476925 / (zmax - zmin);
-    double es = 0.0, sm = 0.0;
-    int nsp = 0, nb = 0, ns = 0, g0 = 0, g1 = 0;
-    for (int j = lane; j < nsite; j += 32) {
-        const int y = y0 + j / bw, x = x0 + j % bw;
-        const int64_t i = (int64_t)y * g.W + x;
-        const bool gap = mask[i] != 0;
-        const double pi = gap ? 0.0 : ((double)values[i] - zmin) * scale;
-        if (gap) {
-            if (((x + y) & 1) == 0) ++g0; else ++g1;
-        } else {
-            sm += pi;
-            ++ns;
-        }
-        if (x + 1 < g.W) {
-            ++nb;
-            if (!gap && !mask[i + 1]) {
-                es += -J * cos(q * (pi - ((double)values[i + 1] - zmin) * scale));
-                ++nsp;
-            }
-        }
-        if (y + 1 < g.H) {
-            ++nb;
-            if (!gap && !mask[i + g.W]) {
-                es += -J * cos(q * (pi - ((double)values[i + g.W] - zmin) * scale));
-                ++nsp;
-            }
-        }
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        es += __shfl_xor_sync(0xffffffffu, es, d);
-        sm += __shfl_xor_sync(0xffffffffu, sm, d);
-        nsp += __shfl_xor_sync(0xffffffffu, nsp, d);
-        nb += __shfl_xor_sync(0xffffffffu, nb, d);
-        ns += __shfl_xor_sync(0xffffffffu, ns, d);
-        g0 += __shfl_xor_sync(0xffffffffu, g0, d);
-        g1 += __shfl_xor_sync(0xffffffffu, g1, d);
-    }
+    // (no absent sites: a bond crosses the block's right / lower edge unless
+    // that edge is the grid's)
+    const BlockSums r = block_sums<false>(values, mask, g.W, y0, x0, y1, x1, x1 < g.W, y1 < g.H,
+                                          zmin, scale, q, J, true);
     if (lane == 0) {
-        Es[warp] = es;
-        Nsp[warp] = nsp;
-        Nb[warp] = nb;
-        sc.ssum[warp] = sm;
-        sc.nsamp[warp] = ns;
-        sc.ng0[warp] = g0;
-        sc.ng1[warp] = g1;
+        Es[warp] = r.es;
+        Nsp[warp] = r.nsp;
+        Nb[warp] = r.nb;
+        sc.ssum[warp] = r.sm;
+        sc.nsamp[warp] = r.ns;
+        sc.ng0[warp] = r.g0;
+        sc.ng1[warp] = r.g1;
     }
 }
 
