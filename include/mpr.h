@@ -429,6 +429,20 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n_realizations);
 mpr_status mpr_sim_sweep(mpr_ctx* ctx, int32_t n_sweeps, int64_t* n_active);
 mpr_status mpr_sim_end(mpr_ctx* ctx);
 
+/* ---- sampling variant of the conditional mean ----
+ * Sec. 2.1 predicts with the mean of the conditional distribution; mpr_simulate
+ * estimates it from independent realizations, each stopped at local
+ * equilibrium. This variant takes it from n_chains chains instead: each
+ * starts like a realization (init option; realization indices continue from
+ * the accumulated count), runs n_equil sweeps with every block active (no
+ * stop test), then n_samples further sweeps, and its state after each of
+ * those is one sample added to the running mean (which mpr_predict reads,
+ * together with any realizations). Random streams: chain j is realization
+ * r_next + j, tag 0, sweeps t = 1 .. n_equil + n_samples. Needs temperatures
+ * and no open batch; n_chains >= 1, n_equil >= 0, n_samples >= 1,
+ * n_equil + n_samples <= 65535. Errors: EINVAL, ESTATE, ECUDA, ENOMEM. */
+mpr_status mpr_sample_chains(mpr_ctx* ctx, int32_t n_chains, int32_t n_equil, int32_t n_samples);
+
 /* One checkerboard half-step (Sec. 2.2.2) of every realization of the batch:
  * Metropolis (+ over-relaxation) on the gap sites of `colour` whose block is
  * running, with the random-number tag `tag` (0 = simulation, 1 + k =

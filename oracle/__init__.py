@@ -99,6 +99,7 @@ def lib():
             "orc_sst_temperatures": (None, [MP, P, i32, i32, P]),
             "orc_calibrate_points": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, i32, f64, f64,
                                             P, f64, P, P, P]),
+            "orc_sample_chain": (None, [MP, P, P, P, i32, i32, u32, P]),
             "orc_energy_curve": (None, [f64, f64, u64, i32, i32, i32, P, i32, i32, P]),
             "orc_curve_T0": (f64, [i32, P, P, f64]),
             "orc3_model_init": (None, [MP, i32, i32, i32, i32, f64, f64, u64, u32]),
@@ -321,6 +322,19 @@ class Oracle:
                                    _p(st.Nsp), _p(st.Nb), _p(st.n_gap), n_max, r, _p(stop),
                                    None if tr is None else _p(tr))
         return phi, stop, n, tr
+
+    def sample_chain(self, phi0, mask, T_blk, n_equil: int, n_samples: int, r: int,
+                     sum_out=None) -> np.ndarray:
+        """Sampling variant: the chain's states after sweeps n_equil + 1 ..
+        n_equil + n_samples summed at the gap sites (added to sum_out)."""
+        ph = np.ascontiguousarray(phi0, dtype=np.float64).copy()
+        mk = np.ascontiguousarray(mask, dtype=np.uint8)
+        T = np.ascontiguousarray(T_blk, dtype=np.float64)
+        out = np.zeros(self.H * self.W) if sum_out is None else sum_out
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.H * self.W
+        lib().orc_sample_chain(C.byref(self.m), _p(ph), _p(mk), _p(T), int(n_equil),
+                               int(n_samples), int(r), _p(out))
+        return out
 
     def calibrate(self, phi_init, mask, st: BlockStats, n_eq=25, n_meas=20, n_bisect=24,
                   chains=1, T_lo=1e-4, T_hi=2.0, trace=False):

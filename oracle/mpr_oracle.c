@@ -546,6 +546,24 @@ int orc_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const
     return t;
 }
 
+/* The sampling variant of the conditional mean (Sec. 2.1 predicts with the
+ * mean of the conditional distribution): instead of independent realizations
+ * each stopped at local equilibrium, one chain from phi (the block-mean
+ * start) runs n_equil sweeps with every block active, then n_samples further
+ * sweeps, and its state after each of those is one sample: sum[i] += phi_i
+ * at every gap site. Realization index r, tag 0, sweeps t = 1, 2, ... */
+void orc_sample_chain(const orc_model* m, double* phi, const uint8_t* mask, const double* T_blk,
+                      int32_t n_equil, int32_t n_samples, uint32_t r, double* sum) {
+    const int64_t n = (int64_t)m->H * m->W;
+    for (int t = 1; t <= n_equil + n_samples; ++t) {
+        orc_halfstep(m, phi, mask, 0, T_blk, NULL, (uint32_t)t, 0u, r, NULL);
+        orc_halfstep(m, phi, mask, 1, T_blk, NULL, (uint32_t)t, 0u, r, NULL);
+        if (t <= n_equil) continue;
+        for (int64_t i = 0; i < n; ++i)
+            if (mask[i]) sum[i] += phi[i];
+    }
+}
+
 /* ------------------------------------------------------------ calibration -- */
 static int cmp_double(const void* a, const void* b) {
     double x = *(const double*)a, y = *(const double*)b;

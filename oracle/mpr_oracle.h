@@ -121,6 +121,12 @@ int orc_simulate_one(const orc_model* m, double* phi, const uint8_t* mask, const
                      const int64_t* n_gap, int32_t n_max, uint32_t r, int32_t* stop_sweep,
                      double* e_trace);
 
+/* Sampling variant: one chain from phi (modified) runs n_equil sweeps with
+ * every block active, then n_samples sweeps, adding its state after each to
+ * sum[i] at the gap sites (realization r, tag 0, sweeps 1, 2, ...). */
+void orc_sample_chain(const orc_model* m, double* phi, const uint8_t* mask, const double* T_blk,
+                      int32_t n_equil, int32_t n_samples, uint32_t r, double* sum);
+
 /* Stop bookkeeping shared by orc_simulate_one and step-wise callers:
  * decide stops after sweep t given block energies E[nblk]. */
 void orc_stop_init(const orc_model* m, const double* E0, const double* Es, const int64_t* Nsp,

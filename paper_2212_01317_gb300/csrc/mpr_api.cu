@@ -1796,6 +1796,59 @@ mpr_status mpr_sim_end(mpr_ctx* ctx) {
     return MPR_OK;
 }
 
+mpr_status mpr_sample_chains(mpr_ctx* ctx, int32_t n_chains, int32_t n_equil, int32_t n_samples) {
+    if (!ctx) return MPR_EINVAL;
+    ctx->err.clear();
+    if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
+    if (n_chains < 1 || n_equil < 0 || n_samples < 1 || (int64_t)n_equil + n_samples > 65535)
+        return fail(ctx, MPR_EINVAL,
+                    "need n_chains >= 1, n_equil >= 0, n_samples >= 1, n_equil + n_samples <= 65535");
+    // The start state and realization indices of a batch of n_chains; the
+    // stop test is not used: every (block, chain) of the batch runs.
+    TRY(mpr_sim_begin(ctx, n_chains));
+    const int64_t nbr = (int64_t)ctx->g.nblk * ctx->Rp;
+    k_fill_valid<<<(int)std::min<int64_t>((nbr + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
+        ctx->running, nbr, ctx->Rp, ctx->r_off, ctx->R);
+    CKL();
+    launch_set_tag(ctx->ctl, 0u, ctx->s);
+    CKL();
+    const unsigned long long bound = ctx->bound;
+    ctx->bound = ~0ull;
+    int form = ctx->opt.sweep_form >= 0 ? ctx->opt.sweep_form : 0;
+    if (form == 4 && !tile_form_ok(ctx)) form = 0;
+    mpr_status st = MPR_OK;
+    for (int t = 1; t <= n_equil + n_samples && st == MPR_OK; ++t) {
+        for (int c = 0; c < 2 && st == MPR_OK; ++c) {
+            SweepArgs a = sweep_args(ctx, c, true);
+            a.work = nullptr;   // every unit; the running flags (all set) decide
+            a.energy = 0;
+            a.t_fixed = t;
+            launch_halfstep(ctx, a, form);
+            ++ctx->launches;
+            ++ctx->sim_halfstep_launches;
+            if (cudaPeekAtLastError() != cudaSuccess)
+                st = fail(ctx, MPR_ECUDA, "sample_chains: half-step launch failed");
+        }
+        if (t <= n_equil) continue;
+        for (int c = 0; c < 2 && st == MPR_OK; ++c) {
+            launch_accumulate(ctx->g, ctx->list[c], ctx->n_gap[c], c, ctx->ang, ctx->storage,
+                              ctx->G, ctx->groups, ctx->r_off, ctx->R, ctx->sum, ctx->s);
+            ++ctx->launches;
+            if (cudaPeekAtLastError() != cudaSuccess)
+                st = fail(ctx, MPR_ECUDA, "sample_chains: accumulate launch failed");
+        }
+    }
+    ctx->bound = bound;
+    ctx->batch_open = 0;
+    ctx->energy_dirty = true;
+    if (st != MPR_OK) return st;
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->gap_updates += (int64_t)n_chains * (n_equil + n_samples) * (ctx->n_gap[0] + ctx->n_gap[1]);
+    ctx->realizations += (int64_t)n_chains * n_samples;
+    ctx->r_next += n_chains;
+    return MPR_OK;
+}
+
 // The whole sweep loop as one CUDA graph: a conditional WHILE node whose body
 // is one sweep (two half-steps, the two stop kernels); the stop test's last
 // CTA sets the loop condition on the device. Grids are the full ones (the

@@ -29,7 +29,7 @@ EXPORTS = [
     "mpr_block_stats_noalloc", "mpr_set_realization_base", "mpr_get_accumulator",
     "mpr_set_accumulator", "mpr_smooth_temperatures", "mpr_set_site_temperatures",
     "mpr_get_site_temperatures", "mpr_energy_moments", "mpr_energy_vjp", "mpr_create_batch",
-    "mpr_get_energy_curve", "mpr_set_energy_curve",
+    "mpr_get_energy_curve", "mpr_set_energy_curve", "mpr_sample_chains",
     "mpr_predict_batch", "mpr_get_slice_layout", "mpr_autotune", "mpr_release_cached_memory",
     "mpr3_create", "mpr3_destroy", "mpr3_last_error", "mpr3_get_info", "mpr3_get_block_stats",
     "mpr3_calibrate", "mpr3_set_temperatures", "mpr3_simulate", "mpr3_predict", "mpr3_sim_begin",
@@ -159,6 +159,7 @@ def load(path: str | None = None):
         "mpr_autotune": (st, [P, i32, i32, C.POINTER(mpr_tuning)]),
         "mpr_get_energy_curve": (st, [P, P, P, i32, C.POINTER(i32)]),
         "mpr_set_energy_curve": (st, [P, P, P, i32]),
+        "mpr_sample_chains": (st, [P, i32, i32, i32]),
         "mpr3_create": (st, [C.POINTER(mpr_grid3), P, P, C.POINTER(mpr_options), C.POINTER(P)]),
         "mpr3_destroy": (None, [P]),
         "mpr3_last_error": (C.c_char_p, [P]),
@@ -289,6 +290,10 @@ def mpr_set_energy_curve(ctx, T, e):
     T = np.ascontiguousarray(T, dtype=np.float32)
     e = np.ascontiguousarray(e, dtype=np.float64)
     _check(ctx, load().mpr_set_energy_curve(ctx, _ptr(T), _ptr(e), int(T.size)))
+
+
+def mpr_sample_chains(ctx, n_chains: int, n_equil: int, n_samples: int):
+    _check(ctx, load().mpr_sample_chains(ctx, int(n_chains), int(n_equil), int(n_samples)))
 
 
 def mpr_set_temperatures(ctx, T):
@@ -448,6 +453,9 @@ class GapFiller:
     def energy_curve(self):
         return mpr_get_energy_curve(self.ctx)
 
+    def sample_chains(self, n_chains: int, n_equil: int, n_samples: int):
+        mpr_sample_chains(self.ctx, n_chains, n_equil, n_samples)
+
     def set_energy_curve(self, T, e):
         mpr_set_energy_curve(self.ctx, T, e)
 
@@ -554,6 +562,9 @@ class BatchFiller:
 
     def energy_curve(self):
         return mpr_get_energy_curve(self.ctx)
+
+    def sample_chains(self, n_chains: int, n_equil: int, n_samples: int):
+        mpr_sample_chains(self.ctx, n_chains, n_equil, n_samples)
 
     def set_energy_curve(self, T, e):
         mpr_set_energy_curve(self.ctx, T, e)
