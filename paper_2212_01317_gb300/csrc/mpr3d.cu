@@ -302,17 +302,11 @@ __global__ void __launch_bounds__(256) k3_sweep(Args3 a) {
         }
     }
     if (!a.energy) return;
-    // Block changes. The lanes of one (block, pair) key sum their changes in
-    // FP32 and the key's lowest lane adds the sums to eacc with FP64 atomics:
-    // a tree of shuffles when the whole warp shares one key, else each lane
-    // gathers its key's other lanes (pairs vary fastest along the thread
-    // index, so a warp holds a few lanes of each of a few keys).
+    // Block changes: one warp sum when every lane works on the same block
+    // and pair (block-major lists make that the common case), else atomics.
     const int key = b < 0 ? -1 : b * a.np + p;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const bool uni = peers == 0xffffffffu;
-    const unsigned others = peers & ~(1u << lane);
-    const int rounds = uni ? 0 : (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(others));
-    const bool leader = __ffs(peers) - 1 == lane;
+    const int k0 = __shfl_sync(0xffffffffu, key, 0);
+    const bool uni = __all_sync(0xffffffffu, key == k0) && k0 >= 0;
     const size_t off[4] = {0, 1, (size_t)g.nbx, (size_t)g.nbx * g.nby};
     float vals[4][2] = {{ao0, ao1}, {ae[0][0], ae[0][1]}, {ae[1][0], ae[1][1]}, {ae[2][0], ae[2][1]}};
 #pragma unroll
@@ -323,20 +317,9 @@ __global__ void __launch_bounds__(256) k3_sweep(Args3 a) {
                 v0 += __shfl_xor_sync(0xffffffffu, v0, d);
                 v1 += __shfl_xor_sync(0xffffffffu, v1, d);
             }
-        } else {
-            unsigned o = others;
-            for (int i = 0; i < rounds; ++i) {
-                const int src = o ? __ffs(o) - 1 : lane;
-                const float x0 = __shfl_sync(0xffffffffu, vals[k][0], src);
-                const float x1 = __shfl_sync(0xffffffffu, vals[k][1], src);
-                if (o) {
-                    v0 += x0;
-                    v1 += x1;
-                    o &= o - 1;
-                }
-            }
+            if (lane != 0) continue;
         }
-        if (!leader || b < 0 || (v0 == 0.0f && v1 == 0.0f)) continue;
+        if (b < 0 || (v0 == 0.0f && v1 == 0.0f)) continue;
         double* ea = a.eacc + ((size_t)b - off[k]) * a.Rp + 2 * p;
         if (v0 != 0.0f) atomicAdd(ea, (double)v0);
         if (v1 != 0.0f) atomicAdd(ea + 1, (double)v1);
