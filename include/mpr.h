@@ -150,6 +150,10 @@ typedef struct {
                             cal_mode other than 2, and the curve's first temperature / w above
                             t_lo and its last one * w below t_hi (the default curve and bracket
                             allow w < 1.6) */
+    int32_t alloc_test;  /* test hook: > 0 makes the context's alloc_test-th device allocation
+                            (counting from 1, those of create included) fail with MPR_ENOMEM
+                            without calling the allocator; the call that needed it returns
+                            MPR_ENOMEM and a later call allocates again (default 0) */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 

@@ -475,6 +475,7 @@ struct mpr3_ctx {
     // batch
     int np = 0, R = 0, Rp = 0, batch_open = 0, t = 0;
     size_t ang_cap = 0, blk_cap = 0;
+    int64_t n_allocs = 0;      // allocations seen by the alloc_test hook
     float2* ang = nullptr;
     double* eacc = nullptr;
     double *ecur = nullptr, *e_last = nullptr;
@@ -533,6 +534,10 @@ mpr_status fail3(mpr3_ctx* c, mpr_status st, const char* fmt, ...) {
 template <class T>
 mpr_status alloc3(mpr3_ctx* ctx, T** p, size_t count) {
     *p = nullptr;
+    // Test hook: the alloc_test-th allocation of the context is refused.
+    if (ctx->opt.alloc_test > 0 && ++ctx->n_allocs == ctx->opt.alloc_test)
+        return fail3(ctx, MPR_ENOMEM, "allocation %d refused by the alloc_test hook",
+                     ctx->opt.alloc_test);
     void* q = nullptr;
     if (pool_alloc(&q, std::max<size_t>(count, 1) * sizeof(T), ctx->device, ctx->s) !=
         cudaSuccess) {
@@ -564,8 +569,12 @@ Slices slices3(mpr3_ctx* ctx) {
 mpr_status ensure3(mpr3_ctx* ctx, int lanes) {
     const int np = (lanes + 1) / 2, Rp = 2 * np;
     const size_t ang_need = 2 * (size_t)ctx->g.D * ctx->g.H * ctx->g.Wh * np;
+    // (a failed allocation leaves the capacity at 0 and every pointer of its
+    // group null, so the next call allocates the group again)
     if (ang_need > ctx->ang_cap) {
         free3(ctx, ctx->ang);
+        ctx->ang = nullptr;
+        ctx->ang_cap = 0;
         TRY3(alloc3(ctx, &ctx->ang, ang_need));
         ctx->ang_cap = ang_need;
     }
@@ -574,6 +583,9 @@ mpr_status ensure3(mpr3_ctx* ctx, int lanes) {
         for (void* p : {(void*)ctx->eacc, (void*)ctx->ecur, (void*)ctx->e_last, (void*)ctx->running,
                         (void*)ctx->stop, (void*)ctx->sigma, (void*)ctx->work, (void*)ctx->tcount})
             free3(ctx, p);
+        ctx->eacc = nullptr; ctx->ecur = nullptr; ctx->e_last = nullptr; ctx->running = nullptr;
+        ctx->stop = nullptr; ctx->sigma = nullptr; ctx->work = nullptr; ctx->tcount = nullptr;
+        ctx->blk_cap = 0;
         TRY3(alloc3(ctx, &ctx->eacc, blk));
         TRY3(alloc3(ctx, &ctx->ecur, blk));
         TRY3(alloc3(ctx, &ctx->e_last, blk));
@@ -742,7 +754,8 @@ mpr_status mpr3_create(const mpr_grid3* grid, const uint8_t* mask_in, const floa
     if (!(o.q > 0.0 && o.q <= 0.5) || !(o.J > 0.0) || o.n_max < 1 || o.n_max > 65535 ||
         o.n_eq < 0 || o.n_meas < 1 || o.n_eq + o.n_meas > 65535 || o.n_bisect < 0 ||
         o.cal_chains < 1 || o.cal_chains > 4096 || !(o.t_lo > 0.0f && o.t_hi > o.t_lo) ||
-        o.stop_rule != MPR_STOP_CROSS)   // (3-D: the first-crossing stop only)
+        o.stop_rule != MPR_STOP_CROSS ||   // (3-D: the first-crossing stop only)
+        o.alloc_test < 0)
         return bail(MPR_EINVAL);
     Geom3& g = ctx->g;
     g.D = D; g.H = H; g.W = W; g.Wh = (W + 1) / 2; g.lb = lb;

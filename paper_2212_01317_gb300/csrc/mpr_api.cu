@@ -51,6 +51,7 @@ struct mpr_ctx {
 
     std::vector<void*> owned;  // every device allocation, freed at destroy
     int64_t device_bytes = 0;
+    int64_t n_allocs = 0;      // allocations seen by the alloc_test hook
 
     // field
     float* values = nullptr;
@@ -193,6 +194,10 @@ template <class T>
 mpr_status dalloc(mpr_ctx* ctx, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    // Test hook: the alloc_test-th allocation of the context is refused.
+    if (ctx->opt.alloc_test > 0 && ++ctx->n_allocs == ctx->opt.alloc_test)
+        return fail(ctx, MPR_ENOMEM, "allocation %d of %zu bytes refused by the alloc_test hook",
+                    ctx->opt.alloc_test, count * sizeof(T));
     void* q = nullptr;
     cudaError_t e = pool_alloc(&q, count * sizeof(T), ctx->device, ctx->s);
     if (e != cudaSuccess) {
@@ -238,6 +243,7 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.cal_mode < 0 || o.cal_mode > 3) return fail(ctx, MPR_EINVAL, "cal_mode must be 0 ... 3");
     if (o.wait_ms < 1) return fail(ctx, MPR_EINVAL, "wait_ms must be >= 1");
     if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
+    if (o.alloc_test < 0) return fail(ctx, MPR_EINVAL, "alloc_test must be >= 0");
     if (o.cal_method < 0 || o.cal_method > 2) return fail(ctx, MPR_EINVAL, "cal_method must be 0, 1 or 2");
     if (o.cal_points != 1 && o.cal_points != 2 && o.cal_points != 4 && o.cal_points != 8)
         return fail(ctx, MPR_EINVAL, "cal_points must be 1, 2, 4 or 8");
@@ -766,10 +772,8 @@ std::deque<CurveEntry> g_curves;
 // (MPR_CURVE_POINTS temperatures, the calibration's n_eq and n_meas),
 // measured on the context's stream unless this process measured it before.
 mpr_status ensure_curve(mpr_ctx* ctx) {
-    if (!ctx->curve_T) {
-        TRY(dalloc(ctx, &ctx->curve_T, (size_t)kCurveMaxPoints));
-        TRY(dalloc(ctx, &ctx->curve_e, (size_t)kCurveMaxPoints));
-    }
+    if (!ctx->curve_T) TRY(dalloc(ctx, &ctx->curve_T, (size_t)kCurveMaxPoints));
+    if (!ctx->curve_e) TRY(dalloc(ctx, &ctx->curve_e, (size_t)kCurveMaxPoints));
     if (ctx->curve_n > 0) return MPR_OK;
     const mpr_options& o = ctx->opt;
     std::lock_guard<std::mutex> lock(g_curve_mu);
@@ -1098,6 +1102,7 @@ void mpr_default_options(mpr_options* o) {
     o->n_fit = 20;
     o->n_f = 5;
     o->cal_warm = 0.0f;
+    o->alloc_test = 0;
     o->cuda_stream = nullptr;
 }
 
@@ -1591,10 +1596,8 @@ mpr_status mpr_set_energy_curve(mpr_ctx* ctx, const float* T, const double* e, i
         if (k > 0 && !(hT[k] > hT[k - 1]))
             return fail(ctx, MPR_EINVAL, "curve temperatures must increase strictly (point %d)", k);
     }
-    if (!ctx->curve_T) {
-        TRY(dalloc(ctx, &ctx->curve_T, (size_t)kCurveMaxPoints));
-        TRY(dalloc(ctx, &ctx->curve_e, (size_t)kCurveMaxPoints));
-    }
+    if (!ctx->curve_T) TRY(dalloc(ctx, &ctx->curve_T, (size_t)kCurveMaxPoints));
+    if (!ctx->curve_e) TRY(dalloc(ctx, &ctx->curve_e, (size_t)kCurveMaxPoints));
     CK(cudaMemcpyAsync(ctx->curve_T, hT.data(), (size_t)n * 4, cudaMemcpyHostToDevice, ctx->s));
     CK(cudaMemcpyAsync(ctx->curve_e, he.data(), (size_t)n * 8, cudaMemcpyHostToDevice, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
@@ -1663,11 +1666,9 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     ctx->chains_valid = true;
     CK(cudaMemsetAsync(ctx->ebar2, 0, (size_t)g.nblk * sizeof(double), ctx->s));
     if (o.cal_points > 2) {
-        if (!ctx->Tk) {
-            TRY(dalloc(ctx, &ctx->Tk, (size_t)8 * g.nblk));
-            TRY(dalloc(ctx, &ctx->betak, (size_t)8 * g.nblk));
-            TRY(dalloc(ctx, &ctx->ebark, (size_t)8 * g.nblk));
-        }
+        if (!ctx->Tk) TRY(dalloc(ctx, &ctx->Tk, (size_t)8 * g.nblk));
+        if (!ctx->betak) TRY(dalloc(ctx, &ctx->betak, (size_t)8 * g.nblk));
+        if (!ctx->ebark) TRY(dalloc(ctx, &ctx->ebark, (size_t)8 * g.nblk));
         CK(cudaMemsetAsync(ctx->ebark, 0, (size_t)8 * g.nblk * sizeof(double), ctx->s));
     }
     launch_cal_init(g.nblk, o.t_lo, o.t_hi, ctx->lo, ctx->hi, ctx->ebar, ctx->ctl, ctx->s);
