@@ -1,6 +1,7 @@
 // C-ABI of libmpr (include/mpr.h): context lifetime, device memory, and the
 // order of kernel launches for create / calibrate / simulate / predict.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -153,6 +154,16 @@ struct mpr_ctx {
 };
 
 namespace {
+
+// An NVTX range around an entry point (create, calibrate, simulate, sample,
+// predict, autotune), so that profilers can attribute kernels to the phase
+// that launched them; without a profiler attached it costs a pointer check.
+struct PhaseRange {
+    explicit PhaseRange(const char* name) { nvtxRangePushA(name); }
+    ~PhaseRange() { nvtxRangePop(); }
+    PhaseRange(const PhaseRange&) = delete;
+    PhaseRange& operator=(const PhaseRange&) = delete;
+};
 
 mpr_status fail(mpr_ctx* c, mpr_status st, const char* fmt, ...) {
     if (c) {
@@ -1405,6 +1416,7 @@ extern "C" {
 
 mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float* values_in,
                       const mpr_options* opt_in, mpr_ctx** out) {
+    PhaseRange phase_range("mpr_create");
     if (!out) return MPR_EINVAL;
     *out = nullptr;
     if (!grid || !mask_in || !values_in) return MPR_EINVAL;
@@ -1421,6 +1433,7 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask_in, const float*
 mpr_status mpr_create_batch(int32_t n, const mpr_grid* grids, const uint8_t* const* masks,
                             const float* const* values, const mpr_options* opt_in,
                             mpr_ctx** out) {
+    PhaseRange phase_range("mpr_create_batch");
     if (!out) return MPR_EINVAL;
     *out = nullptr;
     if (n < 1 || !grids || !masks || !values) return MPR_EINVAL;
@@ -1606,6 +1619,7 @@ mpr_status mpr_set_energy_curve(mpr_ctx* ctx, const float* T, const double* e, i
 }
 
 mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
+    PhaseRange phase_range("mpr_calibrate");
     if (!ctx) return MPR_EINVAL;
     ctx->err.clear();
     const Geom& g = ctx->g;
@@ -1798,6 +1812,7 @@ mpr_status mpr_sim_end(mpr_ctx* ctx) {
 }
 
 mpr_status mpr_sample_chains(mpr_ctx* ctx, int32_t n_chains, int32_t n_equil, int32_t n_samples) {
+    PhaseRange phase_range("mpr_sample_chains");
     if (!ctx) return MPR_EINVAL;
     ctx->err.clear();
     if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
@@ -2067,6 +2082,7 @@ mpr_status simulate_pair_tail(mpr_ctx* ctx) {
 }
 
 mpr_status mpr_simulate(mpr_ctx* ctx, int32_t n) {
+    PhaseRange phase_range("mpr_simulate");
     if (!ctx) return MPR_EINVAL;
     TRY(mpr_sim_begin(ctx, n));
     if (ctx->opt.sim_graph && !ctx->opt.profile) {
@@ -2384,6 +2400,7 @@ mpr_status mpr_energy_vjp(mpr_ctx* ctx, const double* grad_e, double* grad_beta)
 
 mpr_status mpr_autotune(mpr_ctx* ctx, int32_t n_realizations, int32_t n_sweeps,
                         mpr_tuning* out) {
+    PhaseRange phase_range("mpr_autotune");
     if (!ctx || !out) return MPR_EINVAL;
     ctx->err.clear();
     if (ctx->batch_open) return fail(ctx, MPR_ESTATE, "a batch is open");
@@ -2527,6 +2544,7 @@ mpr_status predict_canvas(mpr_ctx* ctx, bool with_truth) {
 }
 
 mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae_rase) {
+    PhaseRange phase_range("mpr_predict");
     if (!ctx || !out) return MPR_EINVAL;
     ctx->err.clear();
     const size_t n = (size_t)ctx->g.H * ctx->g.W;
@@ -2550,6 +2568,7 @@ mpr_status mpr_predict(mpr_ctx* ctx, float* out, const float* truth, double* aae
 
 mpr_status mpr_predict_batch(mpr_ctx* ctx, float* const* outs, const float* const* truths,
                              double* aae_rase) {
+    PhaseRange phase_range("mpr_predict_batch");
     if (!ctx || !outs) return MPR_EINVAL;
     ctx->err.clear();
     const Geom& g = ctx->g;
