@@ -1172,6 +1172,53 @@ struct SliceDesc {
     int y0, x0, H, W;
 };
 
+
+// Host memory (pinned or pageable), as opposed to device or managed memory.
+bool is_host_pointer(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+// Copies a caller's h x w field (contiguous rows, es-byte elements) into the
+// canvas at element offset `off` (to_canvas) or out of it. Device or managed
+// memory: one row-strided copy. Host memory goes through `stage`, a device
+// buffer of at least h w es bytes, so that the host link carries one
+// contiguous copy: a row-strided copy straight from or to host memory moves
+// one row (a few KB) per transfer and measured a few GB/s (0.2-0.3 s for the
+// 1.3 GB of the 256-field batch's inputs).
+mpr_status canvas_copy(mpr_ctx* ctx, bool to_canvas, void* canvas, size_t off, const void* in,
+                       void* out, int h, int w, size_t es, void* stage) {
+    const size_t pitch = (size_t)ctx->g.W * es, row = (size_t)w * es;
+    uint8_t* c = static_cast<uint8_t*>(canvas) + off * es;
+    if (to_canvas) {
+        if (stage) {
+            CK(cudaMemcpyAsync(stage, in, row * h, cudaMemcpyDefault, ctx->s));
+            in = stage;
+        }
+        CK(cudaMemcpy2DAsync(c, pitch, in, row, row, h, cudaMemcpyDefault, ctx->s));
+    } else {
+        CK(cudaMemcpy2DAsync(stage ? stage : out, row, c, pitch, row, h, cudaMemcpyDefault, ctx->s));
+        if (stage) CK(cudaMemcpyAsync(out, stage, row * h, cudaMemcpyDefault, ctx->s));
+    }
+    return MPR_OK;
+}
+
+// A device staging buffer for canvas_copy when one of the n pointers is host
+// memory (nullptr otherwise): room for the largest of the context's fields.
+mpr_status host_stage(mpr_ctx* ctx, const void* const* ptrs, int n, size_t es, uint8_t** stage) {
+    *stage = nullptr;
+    bool host = false;
+    for (int k = 0; k < n && !host; ++k) host = is_host_pointer(ptrs[k]);
+    if (!host) return MPR_OK;
+    size_t big = 0;
+    for (const int4& rc : ctx->h_rect) big = std::max(big, (size_t)rc.z * rc.w);
+    return dalloc(ctx, stage, big * es);
+}
+
 // Allocation, slice tables, transform, Eq. 2 statistics and gap lists of a
 // canvas holding `desc` fields; `upload` copies the inputs into ctx->values
 // and ctx->mask (canvas layout; mask is normalised afterwards).
@@ -1294,7 +1341,10 @@ mpr_status create_impl(const mpr_options* opt_in, int H, int W, int lb,
     ctx->sl = Slices{ns,          rect[0],     key1[0],    ctx->d_rect, ctx->d_blk, ctx->d_of_block,
                      ctx->d_key1, ctx->d_zmin, ctx->d_zmax, ctx->d_degen};
 
-    if (upload(ctx) != MPR_OK) return bail(MPR_ECUDA);
+    {
+        const mpr_status us = upload(ctx);
+        if (us != MPR_OK) return bail(us);
+    }
     k_mask_normalize<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
         g, ctx->sl, ctx->mask);
     ++ctx->launches;
@@ -1479,17 +1529,21 @@ mpr_status mpr_create_batch(int32_t n, const mpr_grid* grids, const uint8_t* con
         if (cudaMemsetAsync(ctx->mask, 0, nc, ctx->s) != cudaSuccess ||
             cudaMemsetAsync(ctx->values, 0, nc * sizeof(float), ctx->s) != cudaSuccess)
             return MPR_ECUDA;
-        for (int k = 0; k < n; ++k) {
+        uint8_t *sv = nullptr, *sm = nullptr;
+        TRY(host_stage(ctx, reinterpret_cast<const void* const*>(values), n, sizeof(float), &sv));
+        TRY(host_stage(ctx, reinterpret_cast<const void* const*>(masks), n, 1, &sm));
+        mpr_status st = MPR_OK;
+        for (int k = 0; k < n && st == MPR_OK; ++k) {
             const SliceDesc& d = desc[k];
             const size_t off = (size_t)d.y0 * ctx->g.W + d.x0;
-            if (cudaMemcpy2DAsync(ctx->values + off, (size_t)ctx->g.W * sizeof(float), values[k],
-                                  (size_t)d.W * sizeof(float), (size_t)d.W * sizeof(float), d.H,
-                                  cudaMemcpyDefault, ctx->s) != cudaSuccess ||
-                cudaMemcpy2DAsync(ctx->mask + off, (size_t)ctx->g.W, masks[k], (size_t)d.W,
-                                  (size_t)d.W, d.H, cudaMemcpyDefault, ctx->s) != cudaSuccess)
-                return MPR_ECUDA;
+            st = canvas_copy(ctx, true, ctx->values, off, values[k], nullptr, d.H, d.W,
+                             sizeof(float), sv);
+            if (st == MPR_OK)
+                st = canvas_copy(ctx, true, ctx->mask, off, masks[k], nullptr, d.H, d.W, 1, sm);
         }
-        return MPR_OK;
+        dfree(ctx, sv);
+        dfree(ctx, sm);
+        return st;
     };
     return create_impl(opt_in, Hc, Wc, lb, desc, upload, out);
 }
@@ -2578,18 +2632,29 @@ mpr_status mpr_predict_batch(mpr_ctx* ctx, float* const* outs, const float* cons
     if (truths) {
         if (!ctx->truth_buf) TRY(dalloc(ctx, &ctx->truth_buf, n));
         CK(cudaMemsetAsync(ctx->truth_buf, 0, n * 4, ctx->s));
-        for (int k = 0; k < ctx->n_slices; ++k) {
+        uint8_t* st = nullptr;
+        TRY(host_stage(ctx, reinterpret_cast<const void* const*>(truths), ctx->n_slices, 4, &st));
+        mpr_status s2 = MPR_OK;
+        for (int k = 0; k < ctx->n_slices && s2 == MPR_OK; ++k) {
             const int4 rc = ctx->h_rect[k];
-            CK(cudaMemcpy2DAsync(ctx->truth_buf + (size_t)rc.x * g.W + rc.y, (size_t)g.W * 4,
-                                 truths[k], (size_t)rc.w * 4, (size_t)rc.w * 4, rc.z,
-                                 cudaMemcpyDefault, ctx->s));
+            s2 = canvas_copy(ctx, true, ctx->truth_buf, (size_t)rc.x * g.W + rc.y, truths[k],
+                             nullptr, rc.z, rc.w, 4, st);
         }
+        dfree(ctx, st);
+        TRY(s2);
     }
     TRY(predict_canvas(ctx, truths != nullptr));
-    for (int k = 0; k < ctx->n_slices; ++k) {
-        const int4 rc = ctx->h_rect[k];
-        CK(cudaMemcpy2DAsync(outs[k], (size_t)rc.w * 4, ctx->out_buf + (size_t)rc.x * g.W + rc.y,
-                             (size_t)g.W * 4, (size_t)rc.w * 4, rc.z, cudaMemcpyDefault, ctx->s));
+    {
+        uint8_t* st = nullptr;
+        TRY(host_stage(ctx, reinterpret_cast<const void* const*>(outs), ctx->n_slices, 4, &st));
+        mpr_status s2 = MPR_OK;
+        for (int k = 0; k < ctx->n_slices && s2 == MPR_OK; ++k) {
+            const int4 rc = ctx->h_rect[k];
+            s2 = canvas_copy(ctx, false, ctx->out_buf, (size_t)rc.x * g.W + rc.y, nullptr, outs[k],
+                             rc.z, rc.w, 4, st);
+        }
+        dfree(ctx, st);
+        TRY(s2);
     }
     CK(cudaStreamSynchronize(ctx->s));
     if (truths && aae_rase) {

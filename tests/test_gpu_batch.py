@@ -189,3 +189,57 @@ def test_autotune_picks_a_candidate_and_keeps_results():
         gf.close()
     scale = float(z[m == 0].max() - z[m == 0].min())
     assert (np.abs(preds[0] - preds[1]) <= 1e-5 * scale)[m != 0].mean() >= 0.98
+
+
+@pytest.mark.parametrize("kind", ["device", "pinned", "mixed"])
+def test_host_and_device_buffers_give_the_same_batch(kind):
+    """Inputs and outputs in pageable host, pinned host or device memory (host
+    buffers go through a contiguous device staging copy, device ones straight
+    into the canvas): the same temperatures and predictions, bit for bit."""
+    import torch
+    fs = fields()
+    grids = [(m.shape[0], m.shape[1], 8) for (_, m, _) in fs]
+    opts = dict(seed=17, group=8, n_bisect=4, n_eq=3, n_meas=3, n_max=40)
+
+    def run(values, masks, outs_of, truths):
+        ctx = mpr.mpr_create_batch(grids, masks, values, mpr.mpr_default_options(**opts))
+        try:
+            info = mpr.mpr_get_info(ctx)
+            T = np.zeros(info.nblk, np.float32)
+            mpr.mpr_calibrate(ctx, T)
+            mpr.mpr_simulate(ctx, 6)
+            outs = outs_of()
+            err = np.zeros(2 * len(fs))
+            mpr.mpr_predict_batch(ctx, outs, truths, err)
+            torch.cuda.synchronize()
+            preds = [o.cpu().numpy() if hasattr(o, "cpu") else o for o in outs]
+        finally:
+            mpr.mpr_destroy(ctx)
+        return T, preds, err
+
+    host = run([v for (_, _, v) in fs], [m for (_, m, _) in fs],
+               lambda: [np.zeros(m.shape, np.float32) for (_, m, _) in fs],
+               [z for (z, _, _) in fs])
+    dev = torch.device("cuda", 0)
+    if kind == "device":
+        vals = [torch.from_numpy(v).to(dev) for (_, _, v) in fs]
+        masks = [torch.from_numpy(m).to(dev) for (_, m, _) in fs]
+        truths = [torch.from_numpy(z).to(dev) for (z, _, _) in fs]
+        outs_of = lambda: [torch.zeros(m.shape, dtype=torch.float32, device=dev) for (_, m, _) in fs]
+    elif kind == "pinned":
+        vals = [torch.from_numpy(v).pin_memory() for (_, _, v) in fs]
+        masks = [torch.from_numpy(m).pin_memory() for (_, m, _) in fs]
+        truths = [torch.from_numpy(z).pin_memory() for (z, _, _) in fs]
+        outs_of = lambda: [torch.zeros(m.shape, dtype=torch.float32).pin_memory() for (_, m, _) in fs]
+    else:   # fields alternate between device and pageable host memory
+        vals = [torch.from_numpy(v).to(dev) if k % 2 else v for k, (_, _, v) in enumerate(fs)]
+        masks = [m if k % 2 else torch.from_numpy(m).to(dev) for k, (_, m, _) in enumerate(fs)]
+        truths = [z for (z, _, _) in fs]
+        outs_of = lambda: [torch.zeros(m.shape, dtype=torch.float32, device=dev) if k % 3 == 0
+                           else np.zeros(m.shape, np.float32) for k, (_, m, _) in enumerate(fs)]
+    other = run(vals, masks, outs_of, truths)
+    assert np.array_equal(host[0], other[0])
+    for a, b in zip(host[1], other[1]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    # (AAE / RASE: FP64 sums over atomics, equal up to their order)
+    np.testing.assert_allclose(host[2], other[2], rtol=1e-12)
