@@ -63,6 +63,10 @@ def parse(argv=None):
                     help="calibration temperatures per block and iteration (1 bisection, "
                          "2 trisection, the default: the two temperatures run on the two "
                          "lanes of a realization pair); --cal-iters sets the iterations")
+    ap.add_argument("--cal-continue", type=int, default=-1,
+                    help="calibration chains continue from one iteration to the next with this "
+                         "many equilibration sweeps after the first iteration (-1: every "
+                         "iteration restarts its chains, the default)")
     ap.add_argument("--cal-iters", type=int, default=None,
                     help="calibration iterations (default 24 for bisection, 16 for trisection; "
                          "with --cal-warm two fewer for trisection)")
@@ -123,6 +127,14 @@ def warm_w(args) -> float:
     if getattr(args, "calibration", "bisection") != "bisection" or args.cal_points < 2:
         return 0.0
     return float(getattr(args, "cal_warm", 0.0))
+
+
+def cont_n(args) -> int:
+    """Equilibration sweeps of continued calibration chains (-1: restart),
+    for the bisection-type calibrations only."""
+    if getattr(args, "calibration", "bisection") != "bisection":
+        return -1
+    return int(getattr(args, "cal_continue", -1))
 
 
 def cal_iters(args) -> int:
@@ -224,7 +236,9 @@ def cal_label(args) -> str:
         return "newton"
     name = {1: "bisection", 2: "trisection", 4: "4-point section", 8: "8-point section"}
     warm = f"warm (w = {warm_w(args):g}) " if warm_w(args) > 0 else ""
-    return warm + name[args.cal_points] + f" x{cal_iters(args)}"
+    cont = (f", chains continued ({args.cal_continue} + n_meas sweeps after the first)"
+            if getattr(args, "cal_continue", -1) >= 0 else "")
+    return warm + name[args.cal_points] + f" x{cal_iters(args)}" + cont
 
 
 def batch_config(args, world) -> dict:
@@ -266,7 +280,7 @@ def oracle_calibrate(o, phi0, mask, st, args):
     """The GPU arm's calibration form in the oracle."""
     if args.calibration == "newton":
         return o.calibrate_newton(phi0, mask, st)
-    if args.cal_points == 1:
+    if args.cal_points == 1 and args.cal_continue < 0:
         return o.calibrate(phi0, mask, st, n_bisect=cal_iters(args))
     T0 = None
     if warm_w(args) > 0:
@@ -276,7 +290,8 @@ def oracle_calibrate(o, phi0, mask, st, args):
         Tc = np.geomspace(0.002, 1.25, 40).astype(np.float32).astype(np.float64)
         T0 = o.warm_T0(st, Tc, oracle.energy_curve(Tc, L=64, n_eq=25, n_meas=20, seed=0))
     return o.calibrate_points(phi0, mask, st, n_iter=cal_iters(args), points=args.cal_points,
-                              T0_warm=T0, warm=warm_w(args) if T0 is not None else 1.5)
+                              T0_warm=T0, warm=warm_w(args) if T0 is not None else 1.5,
+                              n_eq_next=args.cal_continue)
 
 
 ORACLE_R_PER_STEP = 5     # realizations of the oracle's sample field per step
@@ -443,7 +458,8 @@ def run_ours(args, world, rank, local):
                                        storage=STORAGE[storage], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
-                                       cal_warm=warm_w(args), sweep_form=args.sweep_form,
+                                       cal_warm=warm_w(args), cal_continue=cont_n(args),
+                                       sweep_form=args.sweep_form,
                                        cuda_stream=stream.cuda_stream)
 
     sim_ev = []
@@ -728,7 +744,8 @@ def run_ours_batch(args, world, rank, local):
                                        storage=STORAGE[st], cal_mode=args.cal_mode,
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
-                                       cal_warm=warm_w(args), sim_graph=args.sim_graph,
+                                       cal_warm=warm_w(args), cal_continue=cont_n(args),
+                                       sim_graph=args.sim_graph,
                                        sweep_form=args.sweep_form,
                                        sweep_form_bulk=tuned["bulk"],
                                        cuda_stream=stream.cuda_stream)

@@ -154,6 +154,13 @@ typedef struct {
                             (counting from 1, those of create included) fail with MPR_ENOMEM
                             without calling the allocator; the call that needed it returns
                             MPR_ENOMEM and a later call allocates again (default 0) */
+    int32_t cal_continue; /* -1 (default): every calibration iteration restarts its chains from
+                             the initial state and runs n_eq + n_meas sweeps. >= 0: only the
+                             first does; later iterations continue each (chain, point) lane
+                             from the state the previous iteration left at its previous
+                             temperature, with cal_continue equilibration sweeps before the
+                             n_meas measured ones. Needs cal_method 0 and a cal_mode other
+                             than 2 */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 

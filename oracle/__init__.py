@@ -98,7 +98,7 @@ def lib():
             "orc_scores": (None, [i64, P, P, P, P, P]),
             "orc_sst_temperatures": (None, [MP, P, i32, i32, P]),
             "orc_calibrate_points": (None, [MP, P, P, P, P, P, i32, i32, i32, i32, i32, f64, f64,
-                                            P, f64, P, P, P]),
+                                            P, f64, i32, P, P, P]),
             "orc_sample_chain": (None, [MP, P, P, P, i32, i32, u32, P]),
             "orc_energy_curve": (None, [f64, f64, u64, i32, i32, i32, P, i32, i32, P]),
             "orc_curve_T0": (f64, [i32, P, P, f64]),
@@ -374,9 +374,11 @@ class Oracle:
 
     def calibrate_points(self, phi_init, mask, st: BlockStats, n_eq=25, n_meas=20, n_iter=16,
                          chains=1, points=2, T_lo=1e-4, T_hi=2.0, T0_warm=None, warm=1.5,
-                         trace=False):
+                         trace=False, n_eq_next=-1):
         """k-point calibration; T0_warm (per block, from curve_T0) starts the
-        first iteration's points on [T0 / warm, T0 * warm]. trace=True also
+        first iteration's points on [T0 / warm, T0 * warm]. n_eq_next >= 0
+        keeps every chain's state across iterations (n_eq_next equilibration
+        sweeps after the first iteration). trace=True also
         returns the per-iteration mean e_b and temperatures of every point,
         each [n_iter, points, nblk]."""
         ph = np.ascontiguousarray(phi_init, dtype=np.float64)
@@ -387,7 +389,8 @@ class Oracle:
         pt = np.zeros((n_iter, points, self.nblk)) if trace else None
         lib().orc_calibrate_points(C.byref(self.m), _p(ph), _p(mk), _p(st.Es), _p(st.Nsp),
                                    _p(st.Nb), n_eq, n_meas, n_iter, chains, points, T_lo, T_hi,
-                                   None if t0 is None else _p(t0), float(warm), _p(T),
+                                   None if t0 is None else _p(t0), float(warm),
+                                   int(n_eq_next), _p(T),
                                    None if et is None else _p(et), None if pt is None else _p(pt))
         return (T, et, pt) if trace else T
 

@@ -668,10 +668,14 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
                           const double* Es, const int64_t* Nsp_all, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_iter, int32_t chains, int32_t points,
                           double T_lo, double T_hi, const double* T0_warm, double warm,
-                          double* T_out, double* ebar_trace, double* pts_trace) {
+                          int32_t n_eq_next, double* T_out, double* ebar_trace,
+                          double* pts_trace) {
     int64_t* Nsp = calib_targets(m, mask, Nsp_all, 0);
     const int nblk = m->nblk;
     const int64_t n = (int64_t)m->H * m->W;
+    /* continued chains: one state per (chain, point), kept across iterations */
+    const int keep = n_eq_next >= 0;
+    double* states = keep ? (double*)malloc(sizeof(double) * n * (size_t)chains * points) : NULL;
     double* lo = (double*)malloc(sizeof(double) * nblk);
     double* hi = (double*)malloc(sizeof(double) * nblk);
     double* T = (double*)malloc(sizeof(double) * nblk * (size_t)points);
@@ -701,12 +705,14 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
             for (int p = 0; p < points; ++p) {
                 const double* Tp = T + (int64_t)p * nblk;
                 const uint32_t r = (uint32_t)(c * points + p);
-                memcpy(phi, phi_init, sizeof(double) * n);
-                for (int s = 1; s <= n_eq + n_meas; ++s) {
-                    orc_halfstep(m, phi, mask, 0, Tp, NULL, (uint32_t)s, (uint32_t)(1 + k), r, NULL);
-                    orc_halfstep(m, phi, mask, 1, Tp, NULL, (uint32_t)s, (uint32_t)(1 + k), r, NULL);
-                    if (s <= n_eq) continue;
-                    orc_block_energy(m, phi, E);
+                double* ph = keep ? states + (int64_t)r * n : phi;
+                if (!keep || k == 0) memcpy(ph, phi_init, sizeof(double) * n);
+                const int neq = (keep && k > 0) ? n_eq_next : n_eq;
+                for (int s = 1; s <= neq + n_meas; ++s) {
+                    orc_halfstep(m, ph, mask, 0, Tp, NULL, (uint32_t)s, (uint32_t)(1 + k), r, NULL);
+                    orc_halfstep(m, ph, mask, 1, Tp, NULL, (uint32_t)s, (uint32_t)(1 + k), r, NULL);
+                    if (s <= neq) continue;
+                    orc_block_energy(m, ph, E);
                     for (int b = 0; b < nblk; ++b)
                         if (Nb[b] > 0) ebar[(int64_t)p * nblk + b] += E[b] / (double)Nb[b];
                 }
@@ -736,7 +742,7 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
     const double med = orc_median_targeted(nblk, T_out, Nsp);
     for (int b = 0; b < nblk; ++b)
         if (Nsp[b] == 0) T_out[b] = med;
-    free(lo); free(hi); free(T); free(ebar); free(E); free(phi);
+    free(lo); free(hi); free(T); free(ebar); free(E); free(phi); free(states);
     free(Nsp);
 }
 

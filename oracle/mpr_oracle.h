@@ -157,6 +157,10 @@ void orc_calibrate(const orc_model* m, const double* phi_init, const uint8_t* ma
  * iteration's points are evenly spaced on [T0_warm[b] / warm, T0_warm[b] warm]
  * instead (T0 from the unconditional curve, orc_curve_T0); the same rule then
  * keeps [T_lo, first point], a span between points, or [last point, T_hi].
+ * n_eq_next < 0: every iteration restarts its chains from phi_init and runs
+ * n_eq + n_meas sweeps; n_eq_next >= 0: each (chain, point) keeps its state
+ * from one iteration to the next (the first starts from phi_init with n_eq
+ * sweeps of equilibration, later ones run n_eq_next, then n_meas).
  * ebar_trace / pts_trace: NULL, or n_iter * points * nblk doubles receiving,
  * at ((k * points + p) * nblk + b), iteration k's mean e_b and temperature at
  * point p of every targeted block. */
@@ -164,7 +168,8 @@ void orc_calibrate_points(const orc_model* m, const double* phi_init, const uint
                           const double* Es, const int64_t* Nsp, const int64_t* Nb, int32_t n_eq,
                           int32_t n_meas, int32_t n_iter, int32_t chains, int32_t points,
                           double T_lo, double T_hi, const double* T0_warm, double warm,
-                          double* T_out, double* ebar_trace, double* pts_trace);
+                          int32_t n_eq_next, double* T_out, double* ebar_trace,
+                          double* pts_trace);
 
 /* Unconditional specific energy e(T[k]) of a data-free L x L lattice (Sec. 2.1
  * energy matching without data): angles start at pi, n_eq sweeps, then the

@@ -272,6 +272,11 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
         return fail(ctx, MPR_EINVAL, "need 2 <= n_fit <= 64 and 1 <= n_f <= 1024");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
+    if (o.cal_continue < -1 || o.cal_continue > 65535 - o.n_meas)
+        return fail(ctx, MPR_EINVAL, "cal_continue must be -1 or in [0, 65535 - n_meas]");
+    if (o.cal_continue >= 0 && (o.cal_method != 0 || o.cal_mode == 2))
+        return fail(ctx, MPR_EINVAL, "continued calibration chains need cal_method 0 and a "
+                                     "cal_mode other than 2");
     if (!(o.cal_warm == 0.0f || (o.cal_warm > 1.0f && o.cal_warm <= 100.0f)))
         return fail(ctx, MPR_EINVAL, "cal_warm must be 0 or in (1, 100]");
     if (o.cal_warm > 0.0f && (o.cal_points < 2 || o.cal_method != 0 || o.cal_mode == 2))
@@ -820,9 +825,11 @@ mpr_status ensure_curve(mpr_ctx* ctx) {
 }
 
 // warm_first: the iteration's points come from the curve (launch_warm_points)
-// instead of the bracket.
+// instead of the bracket. first: the iteration is the calibration's first
+// (with cal_continue >= 0 only the first restarts the chains; the others
+// continue them and run cal_continue equilibration sweeps instead of n_eq).
 mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphConditionalHandle cond,
-                                 bool timed, bool warm_first = false) {
+                                 bool timed, bool warm_first = false, bool first = true) {
     const Geom& g = ctx->g;
     const mpr_options& o = ctx->opt;
     const int pts = o.cal_points;
@@ -858,17 +865,21 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
         launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
         CKL();
     }
-    TRY(init_batch_state(ctx));
-    // Every iteration starts from the same state, so E_b of the start
-    // (computed once, before the first iteration) is copied, and no change is
-    // pending.
     const size_t blk = (size_t)g.nblk * ctx->Rp;
-    CK(cudaMemcpyAsync(ctx->ecur, ctx->ecur0, blk * sizeof(double), cudaMemcpyDeviceToDevice,
-                       ctx->s));
+    const bool restart = first || o.cal_continue < 0;
+    if (restart) {
+        TRY(init_batch_state(ctx));
+        // Every restart is from the same state, so E_b of the start (computed
+        // once, before the first iteration) is copied. Continued chains keep
+        // their state and the E_b the last sweep's fold left in ecur.
+        CK(cudaMemcpyAsync(ctx->ecur, ctx->ecur0, blk * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->s));
+    }
     CK(cudaMemsetAsync(ctx->eacc, 0, 2 * blk * sizeof(double), ctx->s));
     // Sweep sw's changes go to eacc buffer sw & 1; the colour-0 launch of
     // sweep sw + 1 folds them (extra CTAs), the last sweep's fold runs alone.
-    const int n_sw = o.n_eq + o.n_meas;
+    const int n_eq = restart ? o.n_eq : o.cal_continue;
+    const int n_sw = n_eq + o.n_meas;
     for (int sw = 1; sw <= n_sw; ++sw) {
         for (int c = 0; c < 2; ++c) {
             SweepArgs a = sweep_args(ctx, c, false);
@@ -886,7 +897,7 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
                 f.points = pts;
                 f.ebar_odd = ctx->ebar2;
                 f.ebar_pts = ctx->ebark;
-                f.measure = (sw - 1) > o.n_eq;
+                f.measure = (sw - 1) > n_eq;
                 f.inb = ctx->inb;
                 f.eacc = ctx->eacc + (size_t)((sw - 1) & 1) * blk;
                 f.ecur = ctx->ecur;
@@ -907,7 +918,7 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
             ++ctx->cal_halfstep_launches;
         }
     }
-    launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, o.n_eq, n_sw, ctx->ctl, ctx->inb,
+    launch_cal_step(g.nblk, ctx->Rp, o.cal_chains, n_eq, n_sw, ctx->ctl, ctx->inb,
                     ctx->eacc + (size_t)(n_sw & 1) * blk, ctx->ecur, ctx->ebar, ctx->s, pts,
                     ctx->ebar2, ctx->ebark);
     CKL();
@@ -1029,7 +1040,8 @@ mpr_status calibration_graph(mpr_ctx* ctx, double inv_count, int n_iter) {
     {
         cudaStream_t user = ctx->s;
         ctx->s = ctx->cap;
-        st = calibration_iteration(ctx, inv_count, cond, false);
+        st = calibration_iteration(ctx, inv_count, cond, false, false,
+                                   ctx->opt.n_bisect - n_iter == 0);
         ctx->s = user;
     }
     if (cudaStreamEndCapture(ctx->cap, &captured) != cudaSuccess && st == MPR_OK) goto cuda_fail;
@@ -1114,6 +1126,7 @@ void mpr_default_options(mpr_options* o) {
     o->n_f = 5;
     o->cal_warm = 0.0f;
     o->alloc_test = 0;
+    o->cal_continue = -1;
     o->cuda_stream = nullptr;
 }
 
@@ -1765,11 +1778,14 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
     if (fallback) {
         if (o.n_bisect > 0 && o.cal_mode == 3) {
             for (int k = 0; k < o.n_bisect; ++k)
-                TRY(calibration_iteration(ctx, inv_count, 0, true, warm && k == 0));
+                TRY(calibration_iteration(ctx, inv_count, 0, true, warm && k == 0, k == 0));
         } else if (o.n_bisect > 0) {
-            // The warm start's first iteration runs ahead of the graph.
-            if (warm) TRY(calibration_iteration(ctx, inv_count, 0, true, true));
-            const int rest = o.n_bisect - (warm ? 1 : 0);
+            // A first iteration that differs from the others (the warm start's
+            // points, or the only restart of continued chains) runs ahead of
+            // the graph, whose body is one of the others.
+            const bool ahead = warm || o.cal_continue >= 0;
+            if (ahead) TRY(calibration_iteration(ctx, inv_count, 0, true, warm, true));
+            const int rest = o.n_bisect - (ahead ? 1 : 0);
             if (rest > 0) TRY(calibration_graph(ctx, inv_count, rest));
         }
         launch_cal_mid(g.nblk, ctx->Nsp_cal, ctx->lo, ctx->hi, ctx->T, ctx->ctl, ctx->s);
@@ -1777,8 +1793,12 @@ mpr_status mpr_calibrate(mpr_ctx* ctx, float* block_T_out) {
         launch_cal_fill(ctx->sl, g.nbx, ctx->Nsp_cal, ctx->T, ctx->beta, ctx->s);
         CKL();
     }
-    ctx->cal_updates += (int64_t)o.n_bisect * (o.n_eq + o.n_meas) * chains * o.cal_points *
-                        (ctx->n_gap[0] + ctx->n_gap[1]);
+    const int64_t cal_sweeps =
+        o.n_bisect <= 0 ? 0
+        : o.cal_continue < 0 ? (int64_t)o.n_bisect * (o.n_eq + o.n_meas)
+                             : (int64_t)(o.n_eq + o.n_meas) +
+                                   (int64_t)(o.n_bisect - 1) * (o.cal_continue + o.n_meas);
+    ctx->cal_updates += cal_sweeps * chains * o.cal_points * (ctx->n_gap[0] + ctx->n_gap[1]);
     ctx->calibrated = 1;
     ctx->sst = 0;
     if (block_T_out) TRY(copy_out(ctx, block_T_out, ctx->T, (size_t)g.nblk * 4));

@@ -120,3 +120,76 @@ def test_k_point_calibration_matches_oracle(points, chains):
     gf = make(z, m, lb, cal_points=points, cal_mode=3, **opts)
     np.testing.assert_allclose(gf.calibrate(), T, rtol=1e-6)
     gf.close()
+
+
+def _continued(points, chains, warm, n_next, n_iter, seed, H=48, W=40, lb=8, modes=(1, 3)):
+    import oracle
+    z, m = synth.small_problem(H, W, 0.5, seed=H + points + n_next, kind="disc")
+    o = oracle.Oracle(H, W, lb, seed=seed)
+    phi, *_ = o.transform(z, m)
+    st = o.block_stats(phi, m)
+    phi0 = o.init_block_mean(phi, m, st)
+    opts = dict(seed=seed, n_eq=6, n_meas=6, n_bisect=n_iter, cal_chains=chains,
+                cal_points=points, cal_continue=n_next, cal_warm=warm)
+    Tc = np.geomspace(0.002, 1.25, 40).astype(np.float32)
+    ec = oracle.energy_curve(Tc.astype(np.float64), L=64, n_eq=6, n_meas=6, seed=seed)
+    Ts = []
+    for mode in modes:
+        gf = make(z, m, lb, cal_mode=mode, **opts)
+        gf.set_energy_curve(Tc, ec)
+        Ts.append(gf.calibrate())
+        gf.close()
+    T0 = o.warm_T0(st, Tc.astype(np.float64), ec) if warm > 0 else None
+    return o, z, m, st, phi0, Ts, T0
+
+
+@pytest.mark.parametrize("points,chains,warm,n_next", [(1, 1, 0.0, 5), (2, 1, 0.0, 0),
+                                                       (2, 2, 1.5, 4), (4, 1, 1.5, 3)])
+def test_continued_chains_match_oracle(points, chains, warm, n_next):
+    """Calibration whose chains continue from one iteration to the next
+    (cal_continue: only the first iteration restarts; later ones run n_next
+    equilibration sweeps from where the previous stopped) against the
+    oracle's, block by block, over the first two iterations (the first
+    continued one included): the chains still run in lockstep there. Later,
+    a Metropolis decision that FP32 and FP64 took differently carries over
+    into every later iteration of its chain, so longer runs are compared in
+    distribution (next test). Graph and host-launched forms agree."""
+    seed = 53
+    o, z, m, st, phi0, Ts, T0 = _continued(points, chains, warm, n_next, 2, seed)
+    np.testing.assert_allclose(Ts[0], Ts[1], rtol=1e-6)
+    To, et, pt = o.calibrate_points(phi0, m, st, n_eq=6, n_meas=6, n_iter=2, chains=chains,
+                                    points=points, T0_warm=T0, warm=warm or 1.5,
+                                    n_eq_next=n_next, trace=True)
+    target = (st.Nsp > 0) & (st.n_gap > 0)
+    explain_calibration(o, phi0, m, st, Ts[0], To, et, pt, 6, chains, target)
+
+
+@pytest.mark.parametrize("points,warm,n_next", [(2, 1.5, 5), (1, 0.0, 5)])
+def test_continued_chains_agree_with_oracle_in_distribution(points, warm, n_next):
+    """Over a whole calibration the GPU's per-block temperatures differ from
+    the oracle's (same random streams, chains continued) by no more than two
+    runs of the oracle with different seeds differ from each other."""
+    seed, n_iter = 61, 10
+    o, z, m, st, phi0, Ts, T0 = _continued(points, 1, warm, n_next, n_iter, seed, H=64, W=64,
+                                           modes=(1,))
+    kw = dict(n_eq=6, n_meas=6, n_iter=n_iter, points=points, T0_warm=T0, warm=warm or 1.5,
+              n_eq_next=n_next)
+    To = o.calibrate_points(phi0, m, st, **kw)
+    import oracle
+    o2 = oracle.Oracle(*m.shape, 8, seed=seed + 1)
+    To2 = o2.calibrate_points(phi0, m, st, **kw)
+    target = (st.Nsp > 0) & (st.n_gap > 0)
+    d_gpu = np.abs(np.log(Ts[0][target] / To[target]))
+    d_seed = np.abs(np.log(To2[target] / To[target]))
+    assert np.median(d_gpu) <= 2 * np.median(d_seed) + 1e-3, (np.median(d_gpu), np.median(d_seed))
+    assert np.mean(d_gpu) <= 2 * np.mean(d_seed) + 1e-3
+
+
+def test_continued_chains_count_their_sweeps():
+    z, m = synth.small_problem(40, 40, 0.5, seed=4)
+    gf = make(z, m, 8, seed=1, n_eq=6, n_meas=4, n_bisect=5, cal_points=2, cal_continue=2)
+    gf.calibrate()
+    info = gf.refresh()
+    gf.close()
+    sweeps = (6 + 4) + 4 * (2 + 4)
+    assert info.cal_gap_updates == sweeps * 2 * int(m.sum())

@@ -15,7 +15,8 @@ The curve is pinned to what the mathematics fixes, not to itself:
 The curve's inverse and the warm start's first-iteration points are pinned
 to their definitions on constructed curves, and the warm-started calibration
 to the exact energy matching of isolated gaps (quadrature), also when the
-warm guess is wrong.
+warm guess is wrong, and so is the calibration whose chains continue from one
+iteration to the next.
 """
 import math
 
@@ -192,3 +193,34 @@ def test_warm_start_from_the_curve_runs_end_to_end():
     assert np.all((T > 1e-4) & (T < 2.0))
     med = oracle.Oracle.median_targeted(T, np.where(st.n_gap > 0, st.Nsp, 0))
     assert np.all(T[~tgt] == med)
+
+
+@pytest.mark.parametrize("n_eq_next", [0, 5])
+def test_continued_chains_match_exact_energy_matching(n_eq_next):
+    """Chains that continue from one calibration iteration to the next (only
+    the first restarts from the initial state) land on the exact root of the
+    isolated-gap energy matching as the restarting ones do, cold and warm."""
+    o, phi, mask, st = _isolated_problem()
+    exact = _exact_roots(o, phi, mask, st)
+    phi0 = o.init_block_mean(phi, mask, st)
+    for T0 in (None, exact * 1.1):
+        T = o.calibrate_points(phi0, mask, st, n_eq=20, n_meas=40, n_iter=16, chains=8,
+                               points=2, T0_warm=T0, warm=1.5, n_eq_next=n_eq_next)
+        assert np.all(np.abs(T - exact) < 0.25 * exact + 5e-3), (T, exact)
+
+
+def test_continued_chains_restart_only_once():
+    """One iteration is the same with or without continuation (the first
+    iteration always restarts); later iterations start where the earlier ones
+    stopped, so their measured energies differ from restarted chains'."""
+    o, phi, mask, st = _isolated_problem()
+    phi0 = o.init_block_mean(phi, mask, st)
+    a = o.calibrate_points(phi0, mask, st, n_eq=5, n_meas=5, n_iter=1, points=2)
+    b = o.calibrate_points(phi0, mask, st, n_eq=5, n_meas=5, n_iter=1, points=2, n_eq_next=0)
+    np.testing.assert_array_equal(a, b)
+    _, et_r, pt_r = o.calibrate_points(phi0, mask, st, n_eq=5, n_meas=5, n_iter=3, points=2,
+                                       trace=True)
+    _, et_c, pt_c = o.calibrate_points(phi0, mask, st, n_eq=5, n_meas=5, n_iter=3, points=2,
+                                       n_eq_next=5, trace=True)
+    np.testing.assert_array_equal(et_r[0], et_c[0])      # the first iteration restarts
+    assert not np.array_equal(et_r[1:], et_c[1:])        # later ones continue
