@@ -228,6 +228,10 @@ mpr_status mpr_create(const mpr_grid* grid, const uint8_t* mask, const float* va
  * mpr_predict_batch: outs[k] (H_s*W_s floats, host or device) for every
  *   field; truths: NULL or n pointers; aae_rase: NULL or 2n doubles (host),
  *   AAE and RASE (Eqs. 3-4) of every field.
+ * Host buffers (pinned or pageable) of either call move as one contiguous
+ * copy per field through a device staging buffer the size of the largest
+ * field (allocated for the call, freed after it); device buffers are copied
+ * into or out of the canvas directly.
  * mpr_get_slice_layout: rects[4n] (host) = (y0, x0, H_s, W_s) of every field
  *   in the canvas. */
 mpr_status mpr_create_batch(int32_t n, const mpr_grid* grids, const uint8_t* const* masks,
