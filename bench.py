@@ -63,6 +63,10 @@ def parse(argv=None):
                     help="calibration temperatures per block and iteration (1 bisection, "
                          "2 trisection, the default: the two temperatures run on the two "
                          "lanes of a realization pair); --cal-iters sets the iterations")
+    ap.add_argument("--stop-rule", default="cross", choices=["cross", "window"],
+                    help="local-equilibrium stop: first crossing of the sample energy (cross, "
+                         "the default) or the end of the energy drift over a window of 20 sweeps "
+                         "tested every 5 (window)")
     ap.add_argument("--cal-continue", type=int, default=-1,
                     help="calibration chains continue from one iteration to the next with this "
                          "many equilibration sweeps after the first iteration (-1: every "
@@ -119,6 +123,9 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+STOP_RULES = {"cross": 0, "window": 1}   # mpr_stop_rule values
 
 
 def warm_w(args) -> float:
@@ -252,7 +259,7 @@ def batch_config(args, world) -> dict:
             "storage": default_storage(args),
             "form": "chosen: every field in one context (one launch per half-step for all "
                     "fields); plain: one FP32 context per field, one after another",
-            "calibration": cal_label(args),
+            "calibration": cal_label(args), "stop_rule": args.stop_rule,
             "l2": "inputs larger than L2; flushed between timed steps",
             "parallelism": f"replicas{world}"}
 
@@ -262,7 +269,8 @@ def field_config(args, wl, world) -> dict:
     return {"workload": wl.name, "H": H, "W": W, "block": wl.block,
             "gap_fraction": wl.n_gap / (H * W), "realizations": wl.realizations,
             "storage": default_storage(args), "cal_mode": args.cal_mode,
-            "calibration": cal_label(args), "l2": "flushed between timed steps",
+            "calibration": cal_label(args), "stop_rule": args.stop_rule,
+            "l2": "flushed between timed steps",
             "parallelism": f"replicas{world}"}
 
 
@@ -313,7 +321,8 @@ class OracleBatchSample:
         t0 = time.perf_counter()
         oc = oracle.Oracle(H, W, synth.SLICES_BLOCK, seed=seed, slice_id=k, threads=threads)
         self.o = oracle.Oracle(H, W, synth.SLICES_BLOCK, seed=seed, slice_id=k, threads=threads,
-                               storage=STORAGE[default_storage(args)])
+                               storage=STORAGE[default_storage(args)],
+                               stop_rule=STOP_RULES[args.stop_rule])
         phi, _, _, _ = oc.transform(v, m)
         self.st = oc.block_stats(phi, m)
         self.phi0 = oc.init_block_mean(phi, m, self.st)
@@ -364,7 +373,8 @@ def oracle_field_T(args, wl, threads):
     untimed, by both oracle legs."""
     import oracle
     H, W = wl.shape
-    o = oracle.Oracle(H, W, wl.block, seed=SEED0, threads=threads)
+    o = oracle.Oracle(H, W, wl.block, seed=SEED0, threads=threads,
+                      stop_rule=STOP_RULES[args.stop_rule])
     v = np.where(wl.mask != 0, np.nan, wl.truth).astype(np.float32)
     phi, *_ = o.transform(v, wl.mask)
     st = o.block_stats(phi, wl.mask)
@@ -459,6 +469,7 @@ def run_ours(args, world, rank, local):
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
                                        cal_warm=warm_w(args), cal_continue=cont_n(args),
+                                       stop_rule=STOP_RULES[args.stop_rule],
                                        sweep_form=args.sweep_form,
                                        cuda_stream=stream.cuda_stream)
 
@@ -745,6 +756,7 @@ def run_ours_batch(args, world, rank, local):
                                        cal_method=1 if args.calibration == "newton" else 0,
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
                                        cal_warm=warm_w(args), cal_continue=cont_n(args),
+                                       stop_rule=STOP_RULES[args.stop_rule],
                                        sim_graph=args.sim_graph,
                                        sweep_form=args.sweep_form,
                                        sweep_form_bulk=tuned["bulk"],
