@@ -67,9 +67,6 @@ def parse(argv=None):
                     help="local-equilibrium stop: first crossing of the sample energy (cross, "
                          "the default) or the end of the energy drift over a window of 20 sweeps "
                          "tested every 5 (window)")
-    ap.add_argument("--stop-edge", type=int, default=0, choices=[0, 1],
-                    help="1: blocks whose calibrated temperature sits at an end of the bracket "
-                         "stop like blocks without sample bonds")
     ap.add_argument("--cal-continue", type=int, default=-1,
                     help="calibration chains continue from one iteration to the next with this "
                          "many equilibration sweeps after the first iteration (-1: every "
@@ -263,7 +260,6 @@ def batch_config(args, world) -> dict:
             "form": "chosen: every field in one context (one launch per half-step for all "
                     "fields); plain: one FP32 context per field, one after another",
             "calibration": cal_label(args), "stop_rule": args.stop_rule,
-            "stop_edge": args.stop_edge,
             "l2": "inputs larger than L2; flushed between timed steps",
             "parallelism": f"replicas{world}"}
 
@@ -331,11 +327,6 @@ class OracleBatchSample:
         self.st = oc.block_stats(phi, m)
         self.phi0 = oc.init_block_mean(phi, m, self.st)
         self.T = oracle_calibrate(oc, self.phi0, m, self.st, args)
-        if args.stop_edge:
-            # blocks at an end of the bracket stop like blocks without sample bonds
-            import dataclasses
-            edge = (self.T <= 1e-4 * 1.001) | (self.T >= 2.0 * 0.999)
-            self.st = dataclasses.replace(self.st, Nsp=np.where(edge, 0, self.st.Nsp))
         self.cal_s = time.perf_counter() - t0
         self.r = 0
 
@@ -479,7 +470,6 @@ def run_ours(args, world, rank, local):
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
                                        cal_warm=warm_w(args), cal_continue=cont_n(args),
                                        stop_rule=STOP_RULES[args.stop_rule],
-                                       stop_edge=args.stop_edge,
                                        sweep_form=args.sweep_form,
                                        cuda_stream=stream.cuda_stream)
 
@@ -767,7 +757,6 @@ def run_ours_batch(args, world, rank, local):
                                        cal_points=args.cal_points, n_bisect=cal_iters(args),
                                        cal_warm=warm_w(args), cal_continue=cont_n(args),
                                        stop_rule=STOP_RULES[args.stop_rule],
-                                       stop_edge=args.stop_edge,
                                        sim_graph=args.sim_graph,
                                        sweep_form=args.sweep_form,
                                        sweep_form_bulk=tuned["bulk"],

@@ -161,11 +161,6 @@ typedef struct {
                              temperature, with cal_continue equilibration sweeps before the
                              n_meas measured ones. Needs cal_method 0 and a cal_mode other
                              than 2 */
-    int32_t stop_edge;    /* 0 (default): the stop rule as above. 1: a block whose temperature
-                             lies within 0.1 % of t_lo or t_hi (its calibration ran into the end
-                             of the bracket: no temperature reaches its sample energy) stops like
-                             a block without sample bonds, i.e. once no other targeted block of
-                             its field and realization runs */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 
@@ -537,7 +532,7 @@ mpr_status mpr_block_stats_noalloc(const mpr_grid* grid, const uint8_t* mask, co
  * r / 2, 0), words 2 (r mod 2) and 2 (r mod 2) + 1, key (seed_lo, seed_hi ^
  * slice_id). FP32 state; the storage, group, cal_mode / cal_method /
  * cal_warm, SST, sim_graph and sweep_form options do not apply; stop_rule must be
- * MPR_STOP_CROSS and stop_edge 0 (else EINVAL). Realizations of one call carry indices
+ * MPR_STOP_CROSS (else EINVAL). Realizations of one call carry indices
  * r_next, r_next + 1, ... with r_next the accumulated count rounded up to
  * even. Arrays are D*H*W (sites, row-major) or nblk (blocks); pointers
  * host or device. Errors: as the 2-D calls. */

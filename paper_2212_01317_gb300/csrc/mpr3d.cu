@@ -755,7 +755,7 @@ mpr_status mpr3_create(const mpr_grid3* grid, const uint8_t* mask_in, const floa
         o.n_eq < 0 || o.n_meas < 1 || o.n_eq + o.n_meas > 65535 || o.n_bisect < 0 ||
         o.cal_chains < 1 || o.cal_chains > 4096 || !(o.t_lo > 0.0f && o.t_hi > o.t_lo) ||
         o.stop_rule != MPR_STOP_CROSS ||   // (3-D: the first-crossing stop only)
-        o.alloc_test < 0 || o.stop_edge != 0)
+        o.alloc_test < 0)
         return bail(MPR_EINVAL);
     Geom3& g = ctx->g;
     g.D = D; g.H = H; g.W = W; g.Wh = (W + 1) / 2; g.lb = lb;

@@ -70,9 +70,6 @@ struct mpr_ctx {
     // others, which take the median (a block with sample bonds and no gap
     // site has e_b = e_s,b exactly and nothing to fill).
     int32_t* Nsp_cal = nullptr;
-    // Blocks the stop rule treats as targeted: Nsp, or with stop_edge Nsp
-    // zeroed where the block temperature sits at an end of the bracket.
-    int32_t* Nsp_stop = nullptr;
     double* ssum = nullptr;
     float* init_angle = nullptr;
     float *T = nullptr, *beta = nullptr, *lo = nullptr, *hi = nullptr;
@@ -258,7 +255,6 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
     if (o.wait_ms < 1) return fail(ctx, MPR_EINVAL, "wait_ms must be >= 1");
     if (o.barrier_test < 0) return fail(ctx, MPR_EINVAL, "barrier_test must be >= 0");
     if (o.alloc_test < 0) return fail(ctx, MPR_EINVAL, "alloc_test must be >= 0");
-    if (o.stop_edge != 0 && o.stop_edge != 1) return fail(ctx, MPR_EINVAL, "stop_edge must be 0 or 1");
     if (o.cal_method < 0 || o.cal_method > 2) return fail(ctx, MPR_EINVAL, "cal_method must be 0, 1 or 2");
     if (o.cal_points != 1 && o.cal_points != 2 && o.cal_points != 4 && o.cal_points != 8)
         return fail(ctx, MPR_EINVAL, "cal_points must be 1, 2, 4 or 8");
@@ -626,29 +622,12 @@ __global__ void k_rebuild(int nblk, int groups, int G, int Rp, const int32_t* of
     }
 }
 
-// stop_edge: a block whose temperature lies within 0.1 % of t_lo or t_hi has a
-// target its chains cannot reach (the calibration ran into the end of the
-// bracket); the stop rule treats it as a block without sample bonds.
-__global__ void k_stop_targets(int nblk, const int32_t* __restrict__ Nsp, const float* __restrict__ T,
-                               float t_lo, float t_hi, int32_t* __restrict__ out) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
-        const float tb = T[b];
-        const bool edge = tb <= t_lo * 1.001f || tb >= t_hi * 0.999f;
-        out[b] = edge ? 0 : Nsp[b];
-    }
-}
-
 __global__ void k_fill_valid(uint8_t* running, int64_t n, int Rp, int r_off, int R) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(t % Rp);
         running[t] = (r >= r_off && r < r_off + R) ? 1 : 0;
     }
-}
-
-// The sample-bond counts the stop rule reads.
-const int32_t* stop_targets(const mpr_ctx* ctx) {
-    return ctx->opt.stop_edge ? ctx->Nsp_stop : ctx->Nsp;
 }
 
 // One sweep of the batch: colour 0, colour 1, block energies, stop tests,
@@ -685,12 +664,12 @@ mpr_status sweep_once(mpr_ctx* ctx) {
     launch_stop_targeted(2, ctx->Rp / 2, ctx->Rp, ctx->d_of_block,
                          stop_grid(ctx, 2, kTargetedCtasPerSm),
                          ctx->ctl, ctx->work,
-                         ctx->work_stride, ctx->es, ctx->inb, stop_targets(ctx), ctx->eacc, ctx->ecur,
+                         ctx->work_stride, ctx->es, ctx->inb, ctx->Nsp, ctx->eacc, ctx->ecur,
                          ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, t_known,
                          ctx->s, &win);
     CKL();
     launch_stop_rest(g.nblk, ctx->Rp / 2, 2, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
-                     stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, stop_targets(ctx),
+                     stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, ctx->work, ctx->work, ctx->work_stride, ctx->Nsp,
                      ctx->running, ctx->stop, ctx->tcount, ctx->sim_cond, t_known, ctx->s);
     CKL();
     ctx->t += 1;
@@ -1148,7 +1127,6 @@ void mpr_default_options(mpr_options* o) {
     o->cal_warm = 0.0f;
     o->alloc_test = 0;
     o->cal_continue = -1;
-    o->stop_edge = 0;
     o->cuda_stream = nullptr;
 }
 
@@ -1856,18 +1834,12 @@ mpr_status mpr_sim_begin(mpr_ctx* ctx, int32_t n) {
     // worklist of the first sweep.
     if (ctx->opt.init == MPR_INIT_RANDOM || ctx->groups == 1) TRY(energy_pass(ctx));
     else TRY(energy_pass_shared_start(ctx));
-    if (ctx->opt.stop_edge) {
-        if (!ctx->Nsp_stop) TRY(dalloc(ctx, &ctx->Nsp_stop, (size_t)ctx->g.nblk));
-        k_stop_targets<<<(ctx->g.nblk + 255) / 256, 256, 0, ctx->s>>>(
-            ctx->g.nblk, ctx->Nsp, ctx->T, ctx->opt.t_lo, ctx->opt.t_hi, ctx->Nsp_stop);
-        CKL();
-    }
-    launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->d_of_block, ctx->es, ctx->inb, stop_targets(ctx), ctx->ngap,
+    launch_stop_init(ctx->g.nblk, ctx->Rp, ctx->d_of_block, ctx->es, ctx->inb, ctx->Nsp, ctx->ngap,
                      ctx->ecur,
                      ctx->sigma, ctx->running, ctx->stop, ctx->tcount, ctx->e_last, ctx->s);
     CKL();
     launch_stop_rest(ctx->g.nblk, ctx->Rp / 2, 2, ctx->Rp, ctx->opt.n_max, ctx->d_of_block,
-                     stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, nullptr, ctx->work, ctx->work_stride, stop_targets(ctx),
+                     stop_grid(ctx, 1, kClosingCtasPerSm), ctx->ctl, nullptr, ctx->work, ctx->work_stride, ctx->Nsp,
                      ctx->running, ctx->stop, ctx->tcount, 0, -1, ctx->s);
     CKL();
     ctx->energy_dirty = false;
@@ -2108,7 +2080,7 @@ SimTailArgs tail_args(mpr_ctx* ctx) {
     st.of_block = ctx->d_of_block;
     st.es = ctx->es;
     st.inb = ctx->inb;
-    st.Nsp = stop_targets(ctx);
+    st.Nsp = ctx->Nsp;
     st.eacc = ctx->eacc;
     st.ecur = ctx->ecur;
     st.sigma = ctx->sigma;
@@ -2362,7 +2334,7 @@ mpr_status mpr_set_running(mpr_ctx* ctx, const uint8_t* running) {
     CK(cudaMemsetAsync(&ctx->ctl->n_work[par], 0, sizeof(uint32_t), ctx->s));
     const int64_t items = (int64_t)nb * (ctx->Rp / 2);
     k_rebuild<<<(int)std::min<int64_t>((items + 255) / 256, 152 * 16), 256, 0, ctx->s>>>(
-        nb, ctx->Rp / 2, 2, ctx->Rp, ctx->d_of_block, stop_targets(ctx), ctx->running, ctx->tcount,
+        nb, ctx->Rp / 2, 2, ctx->Rp, ctx->d_of_block, ctx->Nsp, ctx->running, ctx->tcount,
         ctx->ctl, ctx->work, ctx->work_stride);
     ctx->bound = ~0ull;
     CKL();

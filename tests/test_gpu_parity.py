@@ -140,23 +140,14 @@ def test_halfstep_is_independent_of_group_width():
 
 
 # ----------------------------------------------------- sweeps with stop --
-def _lockstep_sweeps(group, R, H=48, W=40, lb=8, p=0.5, seed=5, n_sweeps=30, kind="random",
-                     stop_edge=0):
+def _lockstep_sweeps(group, R, H=48, W=40, lb=8, p=0.5, seed=5, n_sweeps=30, kind="random"):
     z, m = problem(H, W, p, seed=seed, kind=kind)
-    gf = make(z, m, lb, seed=seed * 7 + 1, group=group, n_max=n_sweeps, stop_edge=stop_edge)
+    gf = make(z, m, lb, seed=seed * 7 + 1, group=group, n_max=n_sweeps)
     o = ora_for(gf, lb, seed=seed * 7 + 1)
     phi, zmin, zmax, _ = o.transform(z, m)
     st = o.block_stats(phi, m)
     rng = np.random.default_rng(seed)
     T = rng.uniform(0.03, 0.6, gf.nblk).astype(np.float32)
-    if stop_edge:
-        # blocks whose temperature sits at an end of the bracket [1e-4, 2]
-        # stop like blocks without sample bonds: the oracle's stop rule reads
-        # their sample-bond count as 0 (the half-steps are unchanged)
-        edge = rng.uniform(size=gf.nblk) < 0.3
-        T[edge] = np.where(rng.uniform(size=edge.sum()) < 0.5, 1e-4, 2.0).astype(np.float32)
-        import dataclasses
-        st = dataclasses.replace(st, Nsp=np.where(edge, 0, st.Nsp))
     T64 = T.astype(np.float64)
     gf.set_temperatures(T)
     gf.sim_begin(R)
@@ -228,17 +219,6 @@ def _lockstep_sweeps(group, R, H=48, W=40, lb=8, p=0.5, seed=5, n_sweeps=30, kin
                                           (8, 33, "disc"), (8, 9, "disc")])
 def test_sweeps_energy_and_stop_lockstep(group, R, kind):
     checked, flips, stop_checked = _lockstep_sweeps(group, R, kind=kind, p=0.6 if kind == "disc" else 0.5)
-    assert checked > 0 and stop_checked > 0
-    assert flips <= max(3, checked // 2000)
-
-
-@pytest.mark.parametrize("group,R", [(2, 4), (8, 9)])
-def test_stop_edge_lockstep(group, R):
-    """stop_edge = 1: blocks whose temperature sits at an end of the bracket
-    stop like blocks without sample bonds, decision by decision against the
-    oracle's stop rule with those blocks' sample-bond count read as 0."""
-    checked, flips, stop_checked = _lockstep_sweeps(group, R, kind="disc", p=0.6, seed=9,
-                                                    stop_edge=1)
     assert checked > 0 and stop_checked > 0
     assert flips <= max(3, checked // 2000)
 
