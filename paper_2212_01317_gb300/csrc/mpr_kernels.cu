@@ -451,7 +451,7 @@ __global__ void k_stop_targeted(StopArgs sa, Control* __restrict__ ctl,
     const uint32_t t_sweep = t_known >= 0 ? (uint32_t)t_known : ctl->t;
     const uint32_t* w = work + (size_t)(t_sweep & 1u) * work_stride;
     const int64_t n = (int64_t)ctl->n_work[t_sweep & 1u] * sa.G;
-    stop_targeted_range(sa, t_sweep, w, n, (int64_t)work_stride * sa.G,
+    stop_targeted_range<4>(sa, t_sweep, w, n, (int64_t)work_stride * sa.G,
                         blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                         (int64_t)gridDim.x * blockDim.x);
 }

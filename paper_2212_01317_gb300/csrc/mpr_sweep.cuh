@@ -579,47 +579,71 @@ __device__ __forceinline__ void energy_item(const SweepArgs& a, int item, int wi
 // below `cap` are readable whatever n is (the worklist buffer's length times
 // G; past n they hold stale items), so the first item is read without waiting
 // for n; every value of an entry is then read at once, and only then tested.
+// U entries per pass: a pass reads all of its entries' values before it tests
+// any of them, so U loads of each kind are in flight per thread (the test is
+// latency-bound: an entry's loads wait for the worklist word naming its
+// block). Entries are independent (each (block, realization) appears once).
+template <int U = 1>
 __device__ __forceinline__ void stop_targeted_range(const StopArgs& s, uint32_t t_sweep,
                                                     const uint32_t* __restrict__ w, int64_t n,
                                                     int64_t cap, int64_t i0, int64_t step) {
-    uint32_t item = i0 < cap ? w[i0 / s.G] : 0u;
-    for (int64_t i = i0; i < n; i += step) {
-        if (i != i0) item = w[i / s.G];
-        const int b = (int)(item / (uint32_t)s.groups);
-        const int r = (int)(item % (uint32_t)s.groups) * s.G + (int)(i % s.G);
-        const size_t k = (size_t)b * s.Rp + r;
-        const uint8_t run = s.running[k];
-        const double E = s.ecur[k] + s.eacc[k];
-        const double inb = s.inb[b], es = s.es[b];
-        const int32_t nsp = s.Nsp[b], ob = s.of_block[b];
-        const int sg = s.sigma[k];
-        if (!run) continue;
-        s.eacc[k] = 0.0;
-        s.ecur[k] = E;
-        const double e = E * inb;
-        s.e_last[k] = e;
-        bool reached;
-        if (s.win.rule == 1) {
-            const int nf = s.win.n_fit;
-            s.win.hist[(size_t)(t_sweep % (uint32_t)nf) * s.win.stride + k] = e;
-            if (nsp == 0) continue;
-            const uint32_t first = (uint32_t)(nf + s.win.n_f);
-            if (t_sweep < first || (t_sweep - first) % (uint32_t)s.win.n_f != 0) continue;
-            double num = 0.0;
-            for (int j = 0; j < nf; ++j) {
-                const uint32_t sw = t_sweep - (uint32_t)nf + 1u + (uint32_t)j;
-                num += (double)(2 * j - (nf - 1)) *
-                       s.win.hist[(size_t)(sw % (uint32_t)nf) * s.win.stride + k];
-            }
-            reached = (double)sg * num <= 0.0;
-        } else {
-            if (nsp == 0) continue;
-            reached = sg > 0 ? (e >= es) : (sg < 0 ? (e <= es) : true);
+    for (int64_t ib = i0; ib < n; ib += (int64_t)U * step) {
+        uint32_t item[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = ib + (int64_t)u * step;
+            item[u] = i < cap ? w[i / s.G] : 0u;
         }
-        if (reached) {
-            s.running[k] = 0;
-            s.stop[k] = (int32_t)t_sweep;
-            atomicSub(&s.tcount[ob * s.Rp + r], 1);
+        size_t k[U];
+        int b[U], r[U], sg[U];
+        int32_t nsp[U], ob[U];
+        uint8_t run[U];
+        double E[U], inb[U], es[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = ib + (int64_t)u * step;
+            b[u] = (int)(item[u] / (uint32_t)s.groups);
+            r[u] = (int)(item[u] % (uint32_t)s.groups) * s.G + (int)(i % s.G);
+            k[u] = (size_t)b[u] * s.Rp + r[u];
+            const bool v = i < n;
+            run[u] = v ? s.running[k[u]] : (uint8_t)0;
+            E[u] = v ? s.ecur[k[u]] + s.eacc[k[u]] : 0.0;
+            inb[u] = v ? s.inb[b[u]] : 0.0;
+            es[u] = v ? s.es[b[u]] : 0.0;
+            nsp[u] = v ? s.Nsp[b[u]] : 0;
+            ob[u] = v ? s.of_block[b[u]] : 0;
+            sg[u] = v ? s.sigma[k[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!run[u]) continue;
+            s.eacc[k[u]] = 0.0;
+            s.ecur[k[u]] = E[u];
+            const double e = E[u] * inb[u];
+            s.e_last[k[u]] = e;
+            bool reached;
+            if (s.win.rule == 1) {
+                const int nf = s.win.n_fit;
+                s.win.hist[(size_t)(t_sweep % (uint32_t)nf) * s.win.stride + k[u]] = e;
+                if (nsp[u] == 0) continue;
+                const uint32_t first = (uint32_t)(nf + s.win.n_f);
+                if (t_sweep < first || (t_sweep - first) % (uint32_t)s.win.n_f != 0) continue;
+                double num = 0.0;
+                for (int j = 0; j < nf; ++j) {
+                    const uint32_t sw = t_sweep - (uint32_t)nf + 1u + (uint32_t)j;
+                    num += (double)(2 * j - (nf - 1)) *
+                           s.win.hist[(size_t)(sw % (uint32_t)nf) * s.win.stride + k[u]];
+                }
+                reached = (double)sg[u] * num <= 0.0;
+            } else {
+                if (nsp[u] == 0) continue;
+                reached = sg[u] > 0 ? (e >= es[u]) : (sg[u] < 0 ? (e <= es[u]) : true);
+            }
+            if (reached) {
+                s.running[k[u]] = 0;
+                s.stop[k[u]] = (int32_t)t_sweep;
+                atomicSub(&s.tcount[ob[u] * s.Rp + r[u]], 1);
+            }
         }
     }
 }
