@@ -272,6 +272,8 @@ mpr_status check_opts(mpr_ctx* ctx, const mpr_options& o) {
         return fail(ctx, MPR_EINVAL, "need 2 <= n_fit <= 64 and 1 <= n_f <= 1024");
     if (o.cal_method == 1 && !(o.t_init > o.t_lo && o.t_init < o.t_hi))
         return fail(ctx, MPR_EINVAL, "need t_lo < t_init < t_hi");
+    if (o.cal_sweep < 0 || o.cal_sweep > 2)
+        return fail(ctx, MPR_EINVAL, "cal_sweep must be 0, 1 or 2");
     if (o.cal_continue < -1 || o.cal_continue > 65535 - o.n_meas)
         return fail(ctx, MPR_EINVAL, "cal_continue must be -1 or in [0, 65535 - n_meas]");
     if (o.cal_continue >= 0 && (o.cal_method != 0 || o.cal_mode == 2))
@@ -880,6 +882,10 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     // sweep sw + 1 folds them (extra CTAs), the last sweep's fold runs alone.
     const int n_eq = restart ? o.n_eq : o.cal_continue;
     const int n_sw = n_eq + o.n_meas;
+    // Half-step form: one thread per (entry, pair) while a colour's list is a
+    // few waves, one warp per (block, pair) unit for longer lists.
+    const int64_t flat_threads = std::max(ctx->n_gap[0], ctx->n_gap[1]) * (ctx->G / 2);
+    const bool warp_form = o.cal_sweep == 2 || (o.cal_sweep == 0 && flat_threads >= (1 << 20));
     for (int sw = 1; sw <= n_sw; ++sw) {
         for (int c = 0; c < 2; ++c) {
             SweepArgs a = sweep_args(ctx, c, false);
@@ -909,7 +915,8 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
                 e1 = get_event(ctx);
                 if (e0) cudaEventRecord(e0, ctx->s);
             }
-            launch_sweep_flat(a, ctx->G, ctx->n_gap[c], ctx->s, f.ctas ? &f : nullptr);
+            if (warp_form) launch_sweep_cal(a, ctx->G, ctx->s, f.ctas ? &f : nullptr);
+            else launch_sweep_flat(a, ctx->G, ctx->n_gap[c], ctx->s, f.ctas ? &f : nullptr);
             CKL();
             if (e0 && e1) {
                 cudaEventRecord(e1, ctx->s);
@@ -1127,6 +1134,7 @@ void mpr_default_options(mpr_options* o) {
     o->cal_warm = 0.0f;
     o->alloc_test = 0;
     o->cal_continue = -1;
+    o->cal_sweep = 0;
     o->cuda_stream = nullptr;
 }
 

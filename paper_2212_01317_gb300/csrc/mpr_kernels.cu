@@ -341,9 +341,34 @@ __global__ void __launch_bounds__(128, 8) k_sweep_half(SweepArgs a) {
     }
 }
 
+// Fold of the previous sweep's block energies by CTA `cta` of f.ctas: E_b of
+// every (block, chain lane) gains the sweep's change, and during the measured
+// sweeps each point's mean e_b gains E_b / N_b. It touches eacc of the other
+// parity and ecur, which the half-step does not. kThreads: the CTA size.
+template <int kThreads>
+__device__ __forceinline__ void fold_block_energies(const FoldArgs& f, int cta) {
+    for (int b = cta * kThreads + (int)threadIdx.x; b < f.nblk; b += f.ctas * kThreads) {
+        double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int r = 0; r < f.chains * f.points; ++r) {
+            const size_t k = (size_t)b * f.Rp + r;
+            const double E = f.ecur[k] + f.eacc[k];
+            f.ecur[k] = E;
+            f.eacc[k] = 0.0;
+            s[r % f.points] += E * f.inb[b];
+        }
+        if (f.measure) {
+            if (f.points > 2) {
+                for (int p = 0; p < f.points; ++p) f.ebar_pts[(size_t)p * f.nblk + b] += s[p];
+            } else {
+                f.ebar[b] += s[0];
+                if (f.points == 2) f.ebar_odd[b] += s[1];
+            }
+        }
+    }
+}
+
 // The last f.ctas CTAs (of blockIdx.y = 0) fold the previous sweep's block
-// energies instead: they touch eacc of the other parity and ecur, which the
-// half-step does not. Eight CTAs per SM (32 registers, a few spilled) keep a
+// energies instead (fold_block_energies). Eight CTAs per SM (32 registers, a few spilled) keep a
 // 1024^2 field's colour (262 k threads) in one wave: the calibration took
 // 13.2 ms per bench step at the compiler's 47 registers (five CTAs per SM),
 // 12.7 ms at six CTAs per SM and 12.0 ms at eight.
@@ -355,25 +380,7 @@ __global__ void __launch_bounds__(kFlatThreads, 8) k_sweep_flat(SweepArgs a, int
     if ((int)blockIdx.x >= sweep_ctas) {
         grid_dep_wait();
         if (blockIdx.y != 0) return;
-        for (int b = ((int)blockIdx.x - sweep_ctas) * kFlatThreads + threadIdx.x; b < f.nblk;
-             b += f.ctas * kFlatThreads) {
-            double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-            for (int r = 0; r < f.chains * f.points; ++r) {
-                const size_t k = (size_t)b * f.Rp + r;
-                const double E = f.ecur[k] + f.eacc[k];
-                f.ecur[k] = E;
-                f.eacc[k] = 0.0;
-                s[r % f.points] += E * f.inb[b];
-            }
-            if (f.measure) {
-                if (f.points > 2) {
-                    for (int p = 0; p < f.points; ++p) f.ebar_pts[(size_t)p * f.nblk + b] += s[p];
-                } else {
-                    f.ebar[b] += s[0];
-                    if (f.points == 2) f.ebar_odd[b] += s[1];
-                }
-            }
-        }
+        fold_block_energies<kFlatThreads>(f, (int)blockIdx.x - sweep_ctas);
         return;
     }
     // The sweep index comes from the Control only when the launch does not
@@ -382,6 +389,34 @@ __global__ void __launch_bounds__(kFlatThreads, 8) k_sweep_flat(SweepArgs a, int
     if (a.t_fixed <= 0) grid_dep_wait();
     const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
     sweep_flat<G>(a, n_list, t | (a.ctl->tag << 16));
+}
+
+// The calibration's half-step in the warp form: one warp per (block, pair)
+// unit over every unit (the chains never stop), each lane at its point's
+// temperature, and f.ctas trailing CTAs that fold the previous sweep as in
+// k_sweep_flat. For lists of many waves, where the flat kernel's per-thread
+// setup (entry, random block, temperatures, block sums) weighs on every
+// update; the flat form stays for lists of a few waves, which it covers in
+// one latency chain.
+template <int G>
+__global__ void __launch_bounds__(128, 8) k_sweep_cal(SweepArgs a, FoldArgs f) {
+    grid_dep_launch();
+    grid_dep_wait();
+    const int sweep_ctas = (int)gridDim.x - f.ctas;
+    if ((int)blockIdx.x >= sweep_ctas) {
+        fold_block_energies<128>(f, (int)blockIdx.x - sweep_ctas);
+        return;
+    }
+    constexpr int NP = G / 2;
+    const uint32_t t = a.t_fixed > 0 ? (uint32_t)a.t_fixed : a.ctl->t;
+    const uint32_t ctr1 = t | (a.ctl->tag << 16);
+    const int npairs = a.groups * NP;
+    const int n_units = a.g.nblk * npairs;
+    for (int u = blockIdx.x * 4 + (int)(threadIdx.x >> 5); u < n_units; u += sweep_ctas * 4) {
+        const int b = u / npairs, p = u - b * npairs;
+        const int grp = p / NP, q = p - grp * NP;
+        sweep_item<G, float, true>(a, b * a.groups + grp, q, NP, ctr1);
+    }
 }
 
 template <int G, typename S>
@@ -393,6 +428,8 @@ __global__ void __launch_bounds__(128) k_energy(SweepArgs a) {
 
 template __global__ void k_sweep_flat<2>(SweepArgs, int64_t, FoldArgs);
 template __global__ void k_sweep_flat<8>(SweepArgs, int64_t, FoldArgs);
+template __global__ void k_sweep_cal<2>(SweepArgs, FoldArgs);
+template __global__ void k_sweep_cal<8>(SweepArgs, FoldArgs);
 
 // ------------------------------------------------------------------ stop --
 // es[b] = E_s,b / N_SP,b (0 without sample bonds) and inb[b] = 1 / N_b (0 for
@@ -1209,6 +1246,15 @@ void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s
     // previous launch's tail (the kernel waits before touching its output).
     if (G == 2) launch_pdl(k_sweep_flat<2>, grid, kFlatThreads, s, a, n_list, f);
     else launch_pdl(k_sweep_flat<8>, grid, kFlatThreads, s, a, n_list, f);
+}
+
+void launch_sweep_cal(const SweepArgs& a, int G, cudaStream_t s, const FoldArgs* fold) {
+    FoldArgs f{};
+    if (fold) f = *fold;
+    const int64_t units = (int64_t)a.g.nblk * a.groups * (G / 2);
+    const dim3 grid((unsigned)((units + 3) / 4 + f.ctas));
+    if (G == 2) launch_pdl(k_sweep_cal<2>, grid, 128, s, a, f);
+    else launch_pdl(k_sweep_cal<8>, grid, 128, s, a, f);
 }
 
 // Lanes G.. Rp-1 of every block take the E_b of lane r mod G (all lanes hold

@@ -41,6 +41,9 @@ void launch_energy(const SweepArgs& a, int G, int storage, int n_sm, cudaStream_
 // fold: NULL, or the previous sweep's fold run by extra CTAs of this launch.
 void launch_sweep_flat(const SweepArgs& a, int G, int64_t n_list, cudaStream_t s,
                        const FoldArgs* fold = nullptr);
+// The same half-step of the calibration's chains in the warp form (one warp
+// per (block, pair) unit).
+void launch_sweep_cal(const SweepArgs& a, int G, cudaStream_t s, const FoldArgs* fold = nullptr);
 void launch_ecur_broadcast(int nblk, int Rp, int G, double* ecur, cudaStream_t s);
 void launch_ecur_reset(int nblk, int Rp, const double* Es, double* ecur, double* eacc,
                        cudaStream_t s);

@@ -214,8 +214,11 @@ __device__ __forceinline__ void pair_running(const SweepArgs& a, int b, int rl, 
 // and the wpi / (G/2) warps of a pair split the entries 32 at a time. The
 // next entry of a lane is loaded while the current one is updated. The
 // block's list puts its edge entries first, so the branch that splits an
-// edge move bond by bond diverges in the first 32 entries only.
-template <int G, typename S>
+// edge move bond by bond diverges in the first 32 entries only. kCal: the
+// calibration's chains, whose two lanes of a pair may sit at different
+// temperatures (the trisection's two points, or the k-point section's lane r
+// at point r mod n_pts), as in sweep_flat.
+template <int G, typename S, bool kCal = false>
 __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi, int wpi,
                                            uint32_t ctr1) {
     constexpr int NP = G / 2;
@@ -232,7 +235,15 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
     if (!(run0 || run1)) return;
     S* own = static_cast<S*>(a.ang) + (size_t)(grp * 2 + c) * plane * G + 2 * q;
     const S* oth = static_cast<const S*>(a.ang) + (size_t)(grp * 2 + co) * plane * G + 2 * q;
-    const float beta = a.beta[b];
+    float beta = a.beta[b], beta_odd = beta;
+    if constexpr (kCal) {
+        if (a.beta_pts) {
+            beta = a.beta_pts[(size_t)(rl % a.n_pts) * a.g.nblk + b];
+            beta_odd = a.beta_pts[(size_t)((rl + 1) % a.n_pts) * a.g.nblk + b];
+        } else if (a.beta_odd) {
+            beta_odd = a.beta_odd[b];
+        }
+    }
     const float J = a.m.J;
     const uint32_t rpair = (a.r_base + (uint32_t)rl) >> 1;
     const int sl = slice_of(a.sl, b);
@@ -265,7 +276,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs& a, int item, int wi,
             add_energy(n, f, C0, S0, nc0, ns0, J, ao0, al0, au0);
         }
         if (run1) {
-            const SiteNew n = site_update<S>(ph.y, C1, S1, u01(w[2]), u01(w[3]), bt, a.m);
+            const SiteNew n = site_update<S>(ph.y, C1, S1, u01(w[2]), u01(w[3]),
+                                             kCal ? beta_odd : bt, a.m);
             out.y = n.phi;
             add_energy(n, f, C1, S1, nc1, ns1, J, ao1, al1, au1);
         }

@@ -54,7 +54,8 @@ class mpr_options(C.Structure):
                 ("sim_tail", C.c_int32), ("sweep_form", C.c_int32), ("pair_tail", C.c_int32),
                 ("sweep_form_bulk", C.c_int32), ("stop_rule", C.c_int32), ("n_fit", C.c_int32),
                 ("n_f", C.c_int32), ("cal_warm", C.c_float), ("alloc_test", C.c_int32),
-                ("cal_continue", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("cal_continue", C.c_int32), ("cal_sweep", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
 
 
 class mpr_profile(C.Structure):

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2212_01317_gb300 import synth
-from paper_2212_01317_gb300.mpr import GapFiller, MprError, MPR_ETIMEOUT
+from paper_2212_01317_gb300.mpr import GapFiller, MprError, MPR_EINVAL, MPR_ETIMEOUT
 
 from parity import explain_calibration
 
@@ -64,12 +64,14 @@ def test_barrier_timeout_is_reported_and_device_stays_usable():
     gf2.close()
 
 
+# cal_sweep 0 picks the flat half-step at these sizes; 2 forces the warp form.
+@pytest.mark.parametrize("cal_sweep", [0, 2])
 @pytest.mark.parametrize("chains,kind", [(1, "random"), (3, "disc")])
-def test_trisection_matches_oracle(chains, kind):
+def test_trisection_matches_oracle(chains, kind, cal_sweep):
     import oracle
     H, W, lb = 48, 40, 8
     z, m = synth.small_problem(H, W, 0.5, seed=H + chains, kind=kind)
-    opts = dict(seed=31, n_eq=6, n_meas=6, n_bisect=10, cal_chains=chains)
+    opts = dict(seed=31, n_eq=6, n_meas=6, n_bisect=10, cal_chains=chains, cal_sweep=cal_sweep)
     gf = make(z, m, lb, cal_points=2, **opts)
     T = gf.calibrate()
     gf.close()
@@ -92,8 +94,9 @@ def test_trisection_matches_oracle(chains, kind):
     gf.close()
 
 
+@pytest.mark.parametrize("cal_sweep", [0, 2])
 @pytest.mark.parametrize("points,chains", [(4, 1), (8, 1), (4, 2)])
-def test_k_point_calibration_matches_oracle(points, chains):
+def test_k_point_calibration_matches_oracle(points, chains, cal_sweep):
     """Calibration with 4 or 8 temperatures per block and iteration (lane r of
     the chains at point r mod points; the bracket shrinks to the span between
     the highest point whose mean energy is below e_s,b and the lowest point
@@ -104,7 +107,7 @@ def test_k_point_calibration_matches_oracle(points, chains):
     H, W, lb = 48, 40, 8
     z, m = synth.small_problem(H, W, 0.5, seed=H + points, kind="random")
     n_iter = 6
-    opts = dict(seed=37, n_eq=6, n_meas=6, n_bisect=n_iter, cal_chains=chains)
+    opts = dict(seed=37, n_eq=6, n_meas=6, n_bisect=n_iter, cal_chains=chains, cal_sweep=cal_sweep)
     gf = make(z, m, lb, cal_points=points, **opts)
     T = gf.calibrate()
     gf.close()
@@ -193,3 +196,24 @@ def test_continued_chains_count_their_sweeps():
     gf.close()
     sweeps = (6 + 4) + 4 * (2 + 4)
     assert info.cal_gap_updates == sweeps * 2 * int(m.sum())
+
+
+def test_calibration_sweep_forms():
+    """cal_sweep: an unknown form is refused at create; the flat and the warp
+    half-steps make the same moves from the same random numbers and differ
+    only in the FP32 order of the block sums, so their temperatures agree
+    block by block unless a comparison sat at a tie (the oracle tests above
+    explain each form's blocks); the sweep count is the same."""
+    z, m = synth.small_problem(64, 64, 0.5, seed=9, kind="disc")
+    with pytest.raises(MprError) as e:
+        make(z, m, 8, cal_sweep=3)
+    assert e.value.status == MPR_EINVAL
+    Ts, ups = [], []
+    for form in (1, 2):
+        gf = make(z, m, 8, seed=3, n_eq=6, n_meas=6, n_bisect=8, cal_points=2, cal_sweep=form)
+        Ts.append(gf.calibrate())
+        ups.append(gf.refresh().cal_gap_updates)
+        gf.close()
+    assert ups[0] == ups[1]
+    close = np.abs(Ts[0] - Ts[1]) <= 1e-5 * Ts[0]
+    assert close.mean() >= 0.9, close.mean()
