@@ -162,11 +162,12 @@ typedef struct {
                              n_meas measured ones. Needs cal_method 0 and a cal_mode other
                              than 2 */
     int32_t cal_sweep;   /* form of the calibration's half-steps (cal_mode 1 and 3): 0 (default)
-                            picks by size: one thread per (gap entry, realization pair) while a
-                            colour's list takes a few waves of the GPU (under 2^20 such threads),
-                            one warp per (block, realization pair) beyond; 1 always the former,
-                            2 always the latter. Both compute the same moves from the same
-                            random numbers; only the FP32 order of the block sums differs */
+                            picks by size: one warp per (block, realization pair) when a
+                            colour's list needs 2^20 or more threads in the other form and the
+                            grid holds at least 64 such units per SM, else one thread per (gap
+                            entry, realization pair); 1 always the latter, 2 always the former.
+                            Both compute the same moves from the same random numbers; only the
+                            FP32 order of the block sums differs */
     void* cuda_stream;   /* cudaStream_t to issue work on (NULL = default stream) */
 } mpr_options;
 

@@ -826,6 +826,11 @@ mpr_status ensure_curve(mpr_ctx* ctx) {
     return MPR_OK;
 }
 
+// The calibration's warp-form half-step needs this many (block, chain pair)
+// units per SM (two waves of 32 resident warps) before it replaces the flat
+// form on a long list.
+constexpr int kCalWarpUnitsPerSm = 64;
+
 // warm_first: the iteration's points come from the curve (launch_warm_points)
 // instead of the bracket. first: the iteration is the calibration's first
 // (with cal_continue >= 0 only the first restarts the chains; the others
@@ -883,9 +888,14 @@ mpr_status calibration_iteration(mpr_ctx* ctx, double inv_count, cudaGraphCondit
     const int n_eq = restart ? o.n_eq : o.cal_continue;
     const int n_sw = n_eq + o.n_meas;
     // Half-step form: one thread per (entry, pair) while a colour's list is a
-    // few waves, one warp per (block, pair) unit for longer lists.
+    // few waves, one warp per (block, pair) unit for longer lists that also
+    // hold enough units to fill the GPU with warps (a large field of few
+    // blocks would leave it a fraction of a wave of long-running warps).
     const int64_t flat_threads = std::max(ctx->n_gap[0], ctx->n_gap[1]) * (ctx->G / 2);
-    const bool warp_form = o.cal_sweep == 2 || (o.cal_sweep == 0 && flat_threads >= (1 << 20));
+    const int64_t units = (int64_t)g.nblk * ctx->groups * (ctx->G / 2);
+    const bool warp_form =
+        o.cal_sweep == 2 || (o.cal_sweep == 0 && flat_threads >= (1 << 20) &&
+                             units >= (int64_t)kCalWarpUnitsPerSm * ctx->n_sm);
     for (int sw = 1; sw <= n_sw; ++sw) {
         for (int c = 0; c < 2; ++c) {
             SweepArgs a = sweep_args(ctx, c, false);
